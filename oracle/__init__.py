@@ -1,0 +1,327 @@
+"""Plain FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+ctypes wrapper over ``oracle/sevo_oracle.c``.  Only the tests, the smoke check
+and the benchmark's CPU-baseline leg may import this package; the product
+package never does.  The C source is the statement of what the GPU path
+computes (see the header comment of ``sevo_oracle.h`` for what each function
+follows in arXiv 2505.17430).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "liboracle.so")
+SRC = [os.path.join(HERE, "sevo_oracle.c")]
+
+ELLIPSOID, ROSENBROCK, RASTRIGIN, SCHWEFEL, ACKLEY, GRIEWANK, HYBRID, COMPOSITION = range(8)
+P_INIT, P_PART, P_CROSS, P_ARCH, P_PSO = 1, 2, 3, 4, 5
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, FP64, -ffp-contract=off)."""
+    os.makedirs(BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(s) for s in SRC + [os.path.join(HERE, "sevo_oracle.h")])
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-D_GNU_SOURCE", *SRC, "-o", tmp, "-lm", "-lpthread"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Alg(C.Structure):
+    _fields_ = [("alg", C.c_int), ("NP", C.c_int), ("F", C.c_double), ("CR", C.c_double),
+                ("p", C.c_double), ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("lb", C.c_double), ("ub", C.c_double), ("budget", C.c_int64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("best", C.c_double), ("fes", C.c_int64), ("gens", C.c_int64),
+                ("success", C.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, ip, u8p = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+            vp = C.c_void_p
+            sig = {
+                "orc_philox": (None, [C.c_uint32] * 6 + [C.POINTER(C.c_uint32)]),
+                "orc_u53": (C.c_double, [C.c_uint32, C.c_uint32]),
+                "orc_below": (C.c_uint32, [C.c_uint32, C.c_uint32]),
+                "orc_problem_create": (vp, [C.c_uint64, C.c_int, C.c_int]),
+                "orc_hybrid_create": (vp, [C.c_uint64, C.c_int, C.c_int, dp, ip]),
+                "orc_problem_destroy": (None, [vp]),
+                "orc_problem_info": (None, [vp, ip, dp]),
+                "orc_problem_get": (C.c_int, [vp, C.c_int, dp, dp]),
+                "orc_problem_hybrid": (C.c_int, [vp, ip, ip, ip]),
+                "orc_problem_comp": (C.c_int, [vp, ip, dp, dp, dp]),
+                "orc_eval": (C.c_double, [vp, dp]),
+                "orc_eval_batch": (None, [vp, dp, C.c_int64, C.c_int64, dp]),
+                "orc_eval_scale": (C.c_double, [vp, dp]),
+                "orc_body": (C.c_double, [C.c_int, dp, C.c_int]),
+                "orc_transform": (None, [vp, C.c_int, dp, dp]),
+                "orc_init_population": (None, [C.c_uint64, C.c_int, C.c_int, C.c_double,
+                                               C.c_double, dp]),
+                "orc_de_rand1_trials": (None, [C.c_uint64, C.c_uint64, dp, C.c_int, C.c_int,
+                                               C.c_double, C.c_double, C.c_double, C.c_double,
+                                               dp, ip]),
+                "orc_pbest_k": (C.c_int, [C.c_double, C.c_int]),
+                "orc_rank": (None, [dp, C.c_int, ip]),
+                "orc_de_ctpb_trials": (None, [C.c_uint64, C.c_uint64, dp, dp, C.c_int, C.c_int,
+                                              C.c_double, C.c_double, C.c_double, dp, C.c_int,
+                                              C.c_double, C.c_double, dp, ip]),
+                "orc_de_select": (C.c_int, [C.c_uint64, C.c_uint64, dp, dp, dp, dp, C.c_int,
+                                            C.c_int, dp, ip, u8p]),
+                "orc_pso_guides": (None, [dp, C.c_int, C.c_int, ip]),
+                "orc_pso_move": (None, [C.c_uint64, C.c_uint64, dp, dp, dp, ip, C.c_int,
+                                        C.c_int, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double]),
+                "orc_pso_update": (C.c_int, [dp, dp, dp, dp, C.c_int, C.c_int]),
+                "orc_run": (None, [vp, C.POINTER(Alg), C.c_uint64, C.POINTER(Result),
+                                   C.POINTER(C.c_int64), dp, C.c_int64]),
+                "orc_run_many": (None, [C.POINTER(vp), C.POINTER(Alg), C.POINTER(C.c_uint64),
+                                        C.c_int, C.c_int, C.POINTER(Result)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None else None
+
+
+def f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- Philox
+def philox(ctr, key):
+    out = (C.c_uint32 * 4)()
+    lib().orc_philox(*[int(c) & 0xFFFFFFFF for c in ctr], *[int(k) & 0xFFFFFFFF for k in key],
+                     out)
+    return [int(v) for v in out]
+
+
+def u53(w0, w1):
+    return lib().orc_u53(w0, w1)
+
+
+def below(w, n):
+    return lib().orc_below(w, n)
+
+
+# ---------------------------------------------------------------- problems
+class Problem:
+    """An oracle problem instance (family, D) generated from a seed."""
+
+    def __init__(self, seed: int, family: int, D: int, *, hybrid=None):
+        L = lib()
+        if hybrid is not None:
+            frac, bodies = hybrid
+            fr = f64(frac)
+            bd = np.ascontiguousarray(bodies, dtype=np.int32)
+            self.h = L.orc_hybrid_create(seed, D, len(bd), _dp(fr), _ip(bd))
+        else:
+            self.h = L.orc_problem_create(seed, family, D)
+        if not self.h:
+            raise ValueError("oracle: bad problem arguments")
+        info = np.zeros(3, np.int32)
+        fs = np.zeros(1)
+        L.orc_problem_info(self.h, _ip(info), _dp(fs))
+        self.family, self.D, self.K = (int(v) for v in info)
+        self.fstar = float(fs[0])
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and _lib is not None:
+            _lib.orc_problem_destroy(h)
+            self.h = None
+
+    @property
+    def ncomp(self):
+        return self.K if self.family == COMPOSITION else 1
+
+    def shift(self, comp=0):
+        o = np.zeros(self.D)
+        assert lib().orc_problem_get(self.h, comp, _dp(o), None) == 0
+        return o
+
+    def rotation(self, comp=0):
+        M = np.zeros((self.D, self.D))
+        assert lib().orc_problem_get(self.h, comp, None, _dp(M)) == 0
+        return M
+
+    def hybrid(self):
+        perm = np.zeros(self.D, np.int32)
+        gs = np.zeros(self.K, np.int32)
+        gb = np.zeros(self.K, np.int32)
+        assert lib().orc_problem_hybrid(self.h, _ip(perm), _ip(gs), _ip(gb)) == 0
+        return perm, gs, gb
+
+    def comp(self):
+        n = self.K
+        b = np.zeros(n, np.int32)
+        s, lam, bias = np.zeros(n), np.zeros(n), np.zeros(n)
+        assert lib().orc_problem_comp(self.h, _ip(b), _dp(s), _dp(lam), _dp(bias)) == 0
+        return b, s, lam, bias
+
+    def eval(self, x):
+        x = f64(x)
+        if x.ndim == 1:
+            return lib().orc_eval(self.h, _dp(x))
+        out = np.zeros(x.shape[0])
+        lib().orc_eval_batch(self.h, _dp(x), x.shape[0], x.shape[1], _dp(out))
+        return out
+
+    def scale(self, x):
+        x = f64(x)
+        if x.ndim == 1:
+            return lib().orc_eval_scale(self.h, _dp(x))
+        return np.array([lib().orc_eval_scale(self.h, _dp(np.ascontiguousarray(r))) for r in x])
+
+    def transform(self, x, comp=0):
+        x = f64(x)
+        z = np.zeros(self.D)
+        lib().orc_transform(self.h, comp, _dp(x), _dp(z))
+        return z
+
+
+def body(family, z):
+    z = f64(z)
+    return lib().orc_body(family, _dp(z), len(z))
+
+
+# ---------------------------------------------------------------- operators
+def init_population(seed, NP, D, lb=-100.0, ub=100.0):
+    X = np.zeros((NP, D))
+    lib().orc_init_population(seed, NP, D, lb, ub, _dp(X))
+    return X
+
+
+def de_rand1_trials(seed, gen, X, F=0.5, CR=0.9, lb=-100.0, ub=100.0):
+    X = f64(X)
+    NP, D = X.shape
+    U = np.zeros_like(X)
+    part = np.zeros((NP, 4), np.int32)
+    lib().orc_de_rand1_trials(seed, gen, _dp(X), NP, D, F, CR, lb, ub, _dp(U), _ip(part))
+    return U, part
+
+
+def pbest_k(p, NP):
+    return lib().orc_pbest_k(p, NP)
+
+
+def rank(f):
+    f = f64(f)
+    o = np.zeros(len(f), np.int32)
+    lib().orc_rank(_dp(f), len(f), _ip(o))
+    return o
+
+
+def de_ctpb_trials(seed, gen, X, fx, A, asize, F=0.5, CR=0.9, p=0.11, lb=-100.0, ub=100.0):
+    X, fx = f64(X), f64(fx)
+    NP, D = X.shape
+    A = f64(A) if A is not None else np.zeros((1, D))
+    U = np.zeros_like(X)
+    part = np.zeros((NP, 4), np.int32)
+    lib().orc_de_ctpb_trials(seed, gen, _dp(X), _dp(fx), NP, D, F, CR, p, _dp(A), asize, lb,
+                             ub, _dp(U), _ip(part))
+    return U, part
+
+
+def de_select(seed, gen, X, fx, U, fu, A=None, asize=0):
+    """Returns (X', fx', A', asize', accepted flags); inputs are not modified."""
+    X, fx, U, fu = f64(X).copy(), f64(fx).copy(), f64(U), f64(fu)
+    NP, D = X.shape
+    acc = np.zeros(NP, np.uint8)
+    if A is not None:
+        A = f64(A).copy()
+        asz = C.c_int(asize)
+        lib().orc_de_select(seed, gen, _dp(X), _dp(fx), _dp(U), _dp(fu), NP, D, _dp(A),
+                            C.byref(asz), acc.ctypes.data_as(C.POINTER(C.c_uint8)))
+        return X, fx, A, asz.value, acc
+    lib().orc_de_select(seed, gen, _dp(X), _dp(fx), _dp(U), _dp(fu), NP, D, None, None,
+                        acc.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return X, fx, None, 0, acc
+
+
+def pso_guides(fp, topology):
+    fp = f64(fp)
+    g = np.zeros(len(fp), np.int32)
+    lib().orc_pso_guides(_dp(fp), len(fp), topology, _ip(g))
+    return g
+
+
+def pso_move(seed, gen, X, V, P, guide, w=0.7298, c1=1.49618, c2=1.49618, lb=-100.0,
+             ub=100.0):
+    X, V = f64(X).copy(), f64(V).copy()
+    P = f64(P)
+    NP, D = X.shape
+    g = np.ascontiguousarray(guide, dtype=np.int32)
+    lib().orc_pso_move(seed, gen, _dp(X), _dp(V), _dp(P), _ip(g), NP, D, w, c1, c2, lb, ub)
+    return X, V
+
+
+def pso_update(X, fx, P, fp):
+    X, fx = f64(X), f64(fx)
+    P, fp = f64(P).copy(), f64(fp).copy()
+    NP, D = X.shape
+    n = lib().orc_pso_update(_dp(X), _dp(fx), _dp(P), _dp(fp), NP, D)
+    return P, fp, n
+
+
+ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING = 0, 1, 2, 3
+
+
+def make_alg(alg, NP, budget, F=0.5, CR=0.9, p=0.11, w=0.7298, c1=1.49618, c2=1.49618,
+             lb=-100.0, ub=100.0):
+    return Alg(alg, NP, F, CR, p, w, c1, c2, lb, ub, int(budget))
+
+
+def run(problem: Problem, alg: Alg, seed: int, trace_cap: int = 0):
+    r = Result()
+    tf = np.zeros(max(trace_cap, 1), np.int64)
+    tb = np.zeros(max(trace_cap, 1))
+    lib().orc_run(problem.h, C.byref(alg), seed, C.byref(r),
+                  tf.ctypes.data_as(C.POINTER(C.c_int64)) if trace_cap else None,
+                  _dp(tb) if trace_cap else None, trace_cap)
+    out = {"best": r.best, "fes": r.fes, "gens": r.gens, "success": bool(r.success)}
+    if trace_cap:
+        n = min(trace_cap, r.gens + 1)
+        out["trace_fes"] = tf[:n].copy()
+        out["trace_best"] = tb[:n].copy()
+    return out
+
+
+def run_many(problems, algs, seeds, nthreads=None):
+    n = len(seeds)
+    nthreads = nthreads or os.cpu_count() or 1
+    ph = (C.c_void_p * n)(*[p.h for p in problems])
+    aa = (Alg * n)(*algs)
+    ss = (C.c_uint64 * n)(*[int(s) for s in seeds])
+    rr = (Result * n)()
+    lib().orc_run_many(ph, aa, ss, n, nthreads, rr)
+    return [{"best": r.best, "fes": r.fes, "gens": r.gens, "success": bool(r.success)}
+            for r in rr]

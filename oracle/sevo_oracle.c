@@ -1,0 +1,903 @@
+/*
+ * sevo_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Everything here is the direct, sequential statement of each step: direct
+ * matrix-vector products, textbook body formulas, loops in index order.
+ * No blocking, no SIMD, no reordering beyond what a definition states.
+ * Shares no source with the product library or its CUDA kernels.
+ *
+ * Built with -ffp-contract=off so that "a*b + c" is two roundings unless the
+ * definition says fma() (the DE/PSO operator readings fix where an fma is
+ * used, so both sides can agree bit-for-bit on trial vectors).
+ */
+#include "sevo_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_TWO_PI 6.28318530717958647692
+
+/* ======================================================================
+ * Philox4x32-10, from its published definition (Salmon et al., "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64
+ * multiplies with constants 0xD2511F53 / 0xCD9E8D57, key bumped by the
+ * Weyl constants 0x9E3779B9 / 0xBB67AE85 between rounds.
+ * ====================================================================== */
+void orc_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  uint32_t c[4] = {c0, c1, c2, c3};
+  uint32_t k[2] = {k0, k1};
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k[0] += 0x9E3779B9u;
+      k[1] += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+  out[0] = c[0];
+  out[1] = c[1];
+  out[2] = c[2];
+  out[3] = c[3];
+}
+
+/* 53-bit uniform in [0,1): 27 high bits of w0 and 26 high bits of w1 */
+double orc_u53(uint32_t w0, uint32_t w1) {
+  uint64_t a = w0 >> 5, b = w1 >> 6;
+  return ((double)a * 67108864.0 + (double)b) * (1.0 / 9007199254740992.0);
+}
+
+/* integer in [0,n): high word of the 64-bit product w*n */
+uint32_t orc_below(uint32_t w, uint32_t n) {
+  return (uint32_t)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                 uint32_t purpose, uint32_t salt, uint32_t out[4]) {
+  orc_philox(c0, c1, c2, (purpose << 24) | (salt & 0xFFFFFFu),
+             (uint32_t)seed, (uint32_t)(seed >> 32), out);
+}
+
+/* ======================================================================
+ * Bodies (plain FP64 forms; all bias-free, g(0) = 0 exactly).
+ * ====================================================================== */
+
+/* Schwefel shift s = argmax_{t in [0,500]} t*sin(sqrt t), by Newton on
+ * h(u) = sin u + (u/2) cos u (u = sqrt t), the stationarity condition. */
+static double g_schwefel_s;
+static pthread_once_t g_schwefel_once = PTHREAD_ONCE_INIT;
+static void schwefel_s_init(void) {
+  double u = 20.5;
+  for (int it = 0; it < 60; ++it) {
+    double h = sin(u) + 0.5 * u * cos(u);
+    double dh = 1.5 * cos(u) - 0.5 * u * sin(u);
+    double step = h / dh;
+    u -= step;
+    if (fabs(step) < 1e-15) break;
+  }
+  g_schwefel_s = u * u;
+}
+static double schwefel_s(void) {
+  pthread_once(&g_schwefel_once, schwefel_s_init);
+  return g_schwefel_s;
+}
+
+static double schwefel_term(double z, double s, double c, double* scale) {
+  double y = z + s;
+  double ay = fabs(y);
+  if (ay <= 500.0) {
+    double v = y * sin(sqrt(ay));
+    if (scale) *scale += fabs(c) + fabs(v);
+    return c - v;
+  }
+  double b = (y > 0.0) ? 500.0 : -500.0;
+  double vb = b * sin(sqrt(500.0));
+  double pen = 1e-4 * (ay - 500.0) * (ay - 500.0);
+  if (scale) *scale += fabs(c) + fabs(vb) + pen;
+  return c - vb + pen;
+}
+
+static double body_impl(int family, const double* z, int n, double* scale) {
+  double g = 0.0, S = 0.0;
+  if (n <= 0) {
+    if (scale) *scale = 0.0;
+    return 0.0;
+  }
+  switch (family) {
+    case ORC_ELLIPSOID:
+      for (int i = 1; i <= n; ++i) {
+        double coef = (n > 1) ? pow(10.0, 6.0 * (double)(i - 1) / (double)(n - 1)) : 1.0;
+        g += coef * z[i - 1] * z[i - 1];
+      }
+      S = g;
+      break;
+    case ORC_ROSENBROCK:
+      for (int i = 0; i + 1 < n; ++i) {
+        double yi = z[i] + 1.0, yn = z[i + 1] + 1.0;
+        double a = yi * yi - yn, b = yi - 1.0;
+        g += 100.0 * a * a + b * b;
+        double ma = yi * yi + fabs(yn), mb = fabs(yi) + 1.0;
+        S += 100.0 * ma * ma + mb * mb;
+      }
+      break;
+    case ORC_RASTRIGIN:
+      for (int i = 0; i < n; ++i) {
+        double cz = cos(ORC_TWO_PI * z[i]);
+        g += z[i] * z[i] - 10.0 * cz + 10.0;
+        S += z[i] * z[i] + 10.0 * fabs(cz) + 10.0;
+      }
+      break;
+    case ORC_SCHWEFEL: {
+      double s = schwefel_s();
+      double c = s * sin(sqrt(s));
+      for (int i = 0; i < n; ++i) g += schwefel_term(z[i], s, c, &S);
+      break;
+    }
+    case ORC_ACKLEY: {
+      double sq = 0.0, sc = 0.0;
+      for (int i = 0; i < n; ++i) {
+        sq += z[i] * z[i];
+        sc += cos(ORC_TWO_PI * z[i]);
+      }
+      double a = exp(-0.2 * sqrt(sq / (double)n));
+      double b = exp(sc / (double)n);
+      double e = exp(1.0);
+      g = (20.0 - 20.0 * a) + (e - b);
+      S = 20.0 + 20.0 * a + e + b;
+      break;
+    }
+    case ORC_GRIEWANK: {
+      double sq = 0.0, pr = 1.0;
+      for (int i = 1; i <= n; ++i) {
+        sq += z[i - 1] * z[i - 1];
+        pr *= cos(z[i - 1] / sqrt((double)i));
+      }
+      g = sq / 4000.0 + (1.0 - pr);
+      S = sq / 4000.0 + 1.0 + fabs(pr);
+      break;
+    }
+    default:
+      g = NAN;
+      S = NAN;
+  }
+  if (scale) *scale = S;
+  return g;
+}
+
+double orc_body(int family, const double* z, int n) {
+  return body_impl(family, z, n, NULL);
+}
+
+/* ======================================================================
+ * Instances: shift o ~ U[-80,80]^D, rotation M = Q of a Householder QR of a
+ * seeded Gaussian D x D matrix with diag(R) > 0; hybrid permutation and
+ * groups; composition components.
+ * ====================================================================== */
+struct orc_problem {
+  int family, D, K;     /* K: hybrid groups or composition components */
+  double fstar;
+  double* o;            /* K_o * D  (K_o = Nc for composition, else 1) */
+  double* M;            /* K_o * D * D, row-major, hybrid rows permuted */
+  int* perm;            /* hybrid: D */
+  int* gsize;           /* hybrid: K */
+  int* gbody;           /* hybrid: K, composition: Nc */
+  double* sigma;        /* composition */
+  double* lambda;
+  double* bias;
+};
+
+static void gen_shift(uint64_t seed, int D, int comp, double* o) {
+  uint32_t w[4];
+  for (int j = 0; j < D; ++j) {
+    draw(seed, (uint32_t)(j >> 1), 0, (uint32_t)D, ORC_P_SHIFT, (uint32_t)comp, w);
+    int pr = j & 1;
+    double u = orc_u53(w[2 * pr], w[2 * pr + 1]);
+    o[j] = -80.0 + 160.0 * u;
+  }
+}
+
+/* Gaussian entry e = r*D + k by Box-Muller on (u1,u2) of one Philox call */
+static void gen_gauss(uint64_t seed, int D, int comp, double* G) {
+  uint32_t w[4];
+  int64_t n = (int64_t)D * D;
+  for (int64_t e = 0; e < n; ++e) {
+    uint64_t pair = (uint64_t)e >> 1;
+    draw(seed, (uint32_t)pair, (uint32_t)(pair >> 32), (uint32_t)D, ORC_P_ROT,
+         (uint32_t)comp, w);
+    double u1 = orc_u53(w[0], w[1]);
+    double u2 = orc_u53(w[2], w[3]);
+    double R = sqrt(-2.0 * log(1.0 - u1));
+    double th = ORC_TWO_PI * u2;
+    G[e] = (e & 1) ? R * sin(th) : R * cos(th);
+  }
+}
+
+/* Householder QR of G (row-major D x D); writes Q (row-major) with the
+ * columns sign-fixed so that diag(R) > 0.  Works on a column-major copy so
+ * every reflector touches contiguous memory; each trailing column is
+ * updated independently (parallel over columns, order-independent). */
+static void householder_q(const double* G, int D, double* Q) {
+  double* A = (double*)malloc(sizeof(double) * (size_t)D * D);  /* col-major */
+  double* V = (double*)calloc((size_t)D * D, sizeof(double));  /* reflectors */
+  double* beta = (double*)calloc((size_t)D, sizeof(double));
+  double* rdiag = (double*)calloc((size_t)D, sizeof(double));
+  for (int r = 0; r < D; ++r)
+    for (int k = 0; k < D; ++k) A[(size_t)k * D + r] = G[(size_t)r * D + k];
+
+  for (int k = 0; k < D; ++k) {
+    double* a = A + (size_t)k * D;
+    double nrm2 = 0.0;
+    for (int r = k; r < D; ++r) nrm2 += a[r] * a[r];
+    double nrm = sqrt(nrm2);
+    if (k == D - 1 || nrm == 0.0) {
+      rdiag[k] = a[k];
+      beta[k] = 0.0;
+      continue;
+    }
+    double alpha = (a[k] >= 0.0) ? -nrm : nrm;
+    double* v = V + (size_t)k * D;
+    for (int r = k; r < D; ++r) v[r] = a[r];
+    v[k] -= alpha;
+    double vtv = 0.0;
+    for (int r = k; r < D; ++r) vtv += v[r] * v[r];
+    beta[k] = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+    rdiag[k] = alpha;
+    /* apply H_k = I - beta v v^T to the trailing columns */
+#pragma omp parallel for schedule(static)
+    for (int j = k + 1; j < D; ++j) {
+      double* aj = A + (size_t)j * D;
+      double s = 0.0;
+      for (int r = k; r < D; ++r) s += v[r] * aj[r];
+      s *= beta[k];
+      for (int r = k; r < D; ++r) aj[r] -= s * v[r];
+    }
+  }
+  /* Q = H_0 H_1 ... H_{D-2} applied to I (backward accumulation), column-major */
+  double* Qc = A; /* reuse */
+  memset(Qc, 0, sizeof(double) * (size_t)D * D);
+  for (int j = 0; j < D; ++j) Qc[(size_t)j * D + j] = 1.0;
+  for (int k = D - 1; k >= 0; --k) {
+    if (beta[k] == 0.0) continue;
+    const double* v = V + (size_t)k * D;
+#pragma omp parallel for schedule(static)
+    for (int j = k; j < D; ++j) {
+      double* qj = Qc + (size_t)j * D;
+      double s = 0.0;
+      for (int r = k; r < D; ++r) s += v[r] * qj[r];
+      s *= beta[k];
+      for (int r = k; r < D; ++r) qj[r] -= s * v[r];
+    }
+  }
+  /* sign fix: column k of Q times sign(R_kk) */
+  for (int r = 0; r < D; ++r)
+    for (int k = 0; k < D; ++k) {
+      double q = Qc[(size_t)k * D + r];
+      Q[(size_t)r * D + k] = (rdiag[k] < 0.0) ? -q : q;
+    }
+  free(A);
+  free(V);
+  free(beta);
+  free(rdiag);
+}
+
+static void gen_rotation(uint64_t seed, int D, int comp, double* M) {
+  double* G = (double*)malloc(sizeof(double) * (size_t)D * D);
+  gen_gauss(seed, D, comp, G);
+  householder_q(G, D, M);
+  free(G);
+}
+
+/* Fisher-Yates over Philox: for i = D-1..1 swap perm[i] with perm[below(i+1)] */
+static void gen_perm(uint64_t seed, int D, int* perm) {
+  uint32_t w[4];
+  for (int i = 0; i < D; ++i) perm[i] = i;
+  for (int i = D - 1; i >= 1; --i) {
+    draw(seed, (uint32_t)i, 0, (uint32_t)D, ORC_P_PERM, 0, w);
+    int j = (int)orc_below(w[0], (uint32_t)(i + 1));
+    int t = perm[i];
+    perm[i] = perm[j];
+    perm[j] = t;
+  }
+}
+
+static orc_problem* alloc_problem(int family, int D, int K, int ncomp) {
+  orc_problem* p = (orc_problem*)calloc(1, sizeof(orc_problem));
+  p->family = family;
+  p->D = D;
+  p->K = K;
+  p->fstar = 100.0;
+  p->o = (double*)calloc((size_t)ncomp * D, sizeof(double));
+  p->M = (double*)calloc((size_t)ncomp * D * D, sizeof(double));
+  return p;
+}
+
+/* rows of M permuted: M'[t] = M[perm[t]] */
+static void permute_rows(double* M, const int* perm, int D) {
+  double* T = (double*)malloc(sizeof(double) * (size_t)D * D);
+  for (int t = 0; t < D; ++t)
+    memcpy(T + (size_t)t * D, M + (size_t)perm[t] * D, sizeof(double) * D);
+  memcpy(M, T, sizeof(double) * (size_t)D * D);
+  free(T);
+}
+
+static orc_problem* make_hybrid(uint64_t seed, int D, int K, const double* frac,
+                                const int* bodies) {
+  orc_problem* p = alloc_problem(ORC_HYBRID, D, K, 1);
+  p->perm = (int*)calloc((size_t)D, sizeof(int));
+  p->gsize = (int*)calloc((size_t)K, sizeof(int));
+  p->gbody = (int*)calloc((size_t)K, sizeof(int));
+  int used = 0;
+  for (int k = 0; k < K; ++k) {
+    p->gbody[k] = bodies[k];
+    if (k < K - 1) {
+      p->gsize[k] = (int)floor(frac[k] * (double)D);
+      used += p->gsize[k];
+    } else {
+      p->gsize[k] = D - used;
+    }
+  }
+  gen_shift(seed, D, 0, p->o);
+  gen_rotation(seed, D, 0, p->M);
+  gen_perm(seed, D, p->perm);
+  permute_rows(p->M, p->perm, D);
+  return p;
+}
+
+orc_problem* orc_hybrid_create(uint64_t seed, int D, int K, const double* frac,
+                               const int* bodies) {
+  if (D < 1 || K < 1 || K > 16) return NULL;
+  return make_hybrid(seed, D, K, frac, bodies);
+}
+
+orc_problem* orc_problem_create(uint64_t seed, int family, int D) {
+  if (D < 1 || family < 0 || family > ORC_COMPOSITION) return NULL;
+  uint32_t w[4];
+  if (family <= ORC_GRIEWANK) {
+    orc_problem* p = alloc_problem(family, D, 1, 1);
+    gen_shift(seed, D, 0, p->o);
+    gen_rotation(seed, D, 0, p->M);
+    return p;
+  }
+  if (family == ORC_HYBRID) {
+    draw(seed, 0, 0, (uint32_t)D, ORC_P_HYB, 0, w);
+    int K = 3 + (int)orc_below(w[0], 3);
+    double E[8], frac[8];
+    int bodies[8];
+    double sumE = 0.0;
+    for (int k = 0; k < K; ++k) {
+      draw(seed, (uint32_t)(1 + k), 0, (uint32_t)D, ORC_P_HYB, 0, w);
+      E[k] = -log(1.0 - orc_u53(w[0], w[1]));
+      bodies[k] = (int)orc_below(w[2], 6);
+      sumE += E[k];
+    }
+    for (int k = 0; k < K; ++k)
+      frac[k] = 0.1 + (1.0 - 0.1 * (double)K) * E[k] / sumE;
+    return make_hybrid(seed, D, K, frac, bodies);
+  }
+  /* composition */
+  draw(seed, 0, 0, (uint32_t)D, ORC_P_COMP, 0, w);
+  int Nc = 3 + (int)orc_below(w[0], 8);
+  orc_problem* p = alloc_problem(ORC_COMPOSITION, D, Nc, Nc);
+  p->gbody = (int*)calloc((size_t)Nc, sizeof(int));
+  p->sigma = (double*)calloc((size_t)Nc, sizeof(double));
+  p->lambda = (double*)calloc((size_t)Nc, sizeof(double));
+  p->bias = (double*)calloc((size_t)Nc, sizeof(double));
+  for (int c = 0; c < Nc; ++c) {
+    draw(seed, (uint32_t)(1 + c), 0, (uint32_t)D, ORC_P_COMP, 0, w);
+    p->sigma[c] = 10.0 * (double)(1 + orc_below(w[0], 6));
+    p->lambda[c] = pow(10.0, -6.0 + 6.0 * orc_u53(w[1], w[2]));
+    p->gbody[c] = (int)orc_below(w[3], 6);
+    p->bias[c] = 100.0 * (double)c;
+    gen_shift(seed, D, c, p->o + (size_t)c * D);
+    gen_rotation(seed, D, c, p->M + (size_t)c * D * D);
+  }
+  return p;
+}
+
+void orc_problem_destroy(orc_problem* p) {
+  if (!p) return;
+  free(p->o);
+  free(p->M);
+  free(p->perm);
+  free(p->gsize);
+  free(p->gbody);
+  free(p->sigma);
+  free(p->lambda);
+  free(p->bias);
+  free(p);
+}
+
+void orc_problem_info(const orc_problem* p, int info[3], double* fstar) {
+  info[0] = p->family;
+  info[1] = p->D;
+  info[2] = p->K;
+  if (fstar) *fstar = p->fstar;
+}
+
+int orc_problem_get(const orc_problem* p, int comp, double* o, double* M) {
+  int nc = (p->family == ORC_COMPOSITION) ? p->K : 1;
+  if (comp < 0 || comp >= nc) return -1;
+  size_t D = (size_t)p->D;
+  if (o) memcpy(o, p->o + comp * D, sizeof(double) * D);
+  if (M) memcpy(M, p->M + comp * D * D, sizeof(double) * D * D);
+  return 0;
+}
+
+int orc_problem_hybrid(const orc_problem* p, int* perm, int* gsize, int* gbody) {
+  if (p->family != ORC_HYBRID) return -1;
+  if (perm) memcpy(perm, p->perm, sizeof(int) * p->D);
+  if (gsize) memcpy(gsize, p->gsize, sizeof(int) * p->K);
+  if (gbody) memcpy(gbody, p->gbody, sizeof(int) * p->K);
+  return 0;
+}
+
+int orc_problem_comp(const orc_problem* p, int* body, double* sigma,
+                     double* lambda, double* bias) {
+  if (p->family != ORC_COMPOSITION) return -1;
+  int n = p->K;
+  if (body) memcpy(body, p->gbody, sizeof(int) * n);
+  if (sigma) memcpy(sigma, p->sigma, sizeof(double) * n);
+  if (lambda) memcpy(lambda, p->lambda, sizeof(double) * n);
+  if (bias) memcpy(bias, p->bias, sizeof(double) * n);
+  return 0;
+}
+
+/* ======================================================================
+ * Evaluation
+ * ====================================================================== */
+
+/* z_i = sum_j M_ij (x_j - o_j), j ascending */
+void orc_transform(const orc_problem* p, int comp, const double* x, double* z) {
+  int D = p->D;
+  const double* o = p->o + (size_t)comp * D;
+  const double* M = p->M + (size_t)comp * D * D;
+  double* d = (double*)malloc(sizeof(double) * D);
+  for (int j = 0; j < D; ++j) d[j] = x[j] - o[j];
+  for (int i = 0; i < D; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < D; ++j) acc += M[(size_t)i * D + j] * d[j];
+    z[i] = acc;
+  }
+  free(d);
+}
+
+static double eval_impl(const orc_problem* p, const double* x, double* scale) {
+  int D = p->D;
+  double* z = (double*)malloc(sizeof(double) * D);
+  double g = 0.0, S = 0.0;
+  if (p->family <= ORC_GRIEWANK) {
+    orc_transform(p, 0, x, z);
+    g = body_impl(p->family, z, D, &S);
+  } else if (p->family == ORC_HYBRID) {
+    orc_transform(p, 0, x, z); /* rows already permuted: z' = P M d */
+    int start = 0;
+    for (int k = 0; k < p->K; ++k) {
+      double sk = 0.0;
+      g += body_impl(p->gbody[k], z + start, p->gsize[k], &sk);
+      S += sk;
+      start += p->gsize[k];
+    }
+  } else {
+    int Nc = p->K;
+    double gc[16], sc[16], Sc[16], w[16], om[16];
+    int exact = -1;
+    for (int c = 0; c < Nc; ++c) {
+      const double* oc = p->o + (size_t)c * D;
+      double s = 0.0;
+      for (int j = 0; j < D; ++j) {
+        double dj = x[j] - oc[j];
+        s += dj * dj;
+      }
+      sc[c] = s;
+      orc_transform(p, c, x, z);
+      gc[c] = body_impl(p->gbody[c], z, D, &Sc[c]);
+      if (s == 0.0 && exact < 0) exact = c;
+    }
+    if (exact >= 0) {
+      for (int c = 0; c < Nc; ++c) om[c] = (c == exact) ? 1.0 : 0.0;
+    } else {
+      double W = 0.0;
+      for (int c = 0; c < Nc; ++c) {
+        double sg = p->sigma[c];
+        w[c] = (1.0 / sqrt(sc[c])) * exp(-sc[c] / (2.0 * (double)D * sg * sg));
+        W += w[c];
+      }
+      for (int c = 0; c < Nc; ++c) om[c] = (W > 0.0) ? w[c] / W : 1.0 / (double)Nc;
+    }
+    for (int c = 0; c < Nc; ++c) {
+      g += om[c] * (p->lambda[c] * gc[c] + p->bias[c]);
+      S += om[c] * (p->lambda[c] * Sc[c] + p->bias[c]);
+    }
+  }
+  free(z);
+  if (scale) *scale = S;
+  return g;
+}
+
+double orc_eval(const orc_problem* p, const double* x) { return eval_impl(p, x, NULL); }
+
+double orc_eval_scale(const orc_problem* p, const double* x) {
+  double S = 0.0;
+  eval_impl(p, x, &S);
+  return S;
+}
+
+void orc_eval_batch(const orc_problem* p, const double* X, int64_t N, int64_t ld,
+                    double* out) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < N; ++i) out[i] = eval_impl(p, X + i * ld, NULL);
+}
+
+/* ======================================================================
+ * DE and PSO operators
+ * ====================================================================== */
+
+void orc_init_population(uint64_t seed, int NP, int D, double lb, double ub,
+                         double* X) {
+  uint32_t w[4];
+  for (int i = 0; i < NP; ++i)
+    for (int j = 0; j < D; ++j) {
+      draw(seed, (uint32_t)(j >> 1), (uint32_t)i, 0, ORC_P_INIT, 0, w);
+      int pr = j & 1;
+      double u = orc_u53(w[2 * pr], w[2 * pr + 1]);
+      X[(size_t)i * D + j] = lb + (ub - lb) * u;
+    }
+}
+
+/* skip-draw: value v in [0, n-m) mapped past the m excluded indices given in
+ * ascending order, so the result is uniform over [0,n) minus the excluded */
+static int skip_sorted(int v, const int* excl_sorted, int m) {
+  for (int t = 0; t < m; ++t)
+    if (v >= excl_sorted[t]) ++v;
+  return v;
+}
+
+static void sort_small(int* a, int m) {
+  for (int i = 1; i < m; ++i)
+    for (int j = i; j > 0 && a[j - 1] > a[j]; --j) {
+      int t = a[j];
+      a[j] = a[j - 1];
+      a[j - 1] = t;
+    }
+}
+
+/* binomial crossover + midpoint-target repair of one row */
+static void cross_repair(uint64_t seed, uint64_t gen, int i, int D, double CR,
+                         int jrand, const double* v, const double* x, double lb,
+                         double ub, double* u) {
+  uint32_t w[4];
+  for (int j = 0; j < D; ++j) {
+    if ((j & 3) == 0) draw(seed, (uint32_t)(j >> 2), (uint32_t)i, (uint32_t)gen, ORC_P_CROSS, 0, w);
+    double U = (double)w[j & 3] * (1.0 / 4294967296.0);
+    double t = (U < CR || j == jrand) ? v[j] : x[j];
+    if (t < lb) t = (lb + x[j]) * 0.5;
+    if (t > ub) t = (ub + x[j]) * 0.5;
+    u[j] = t;
+  }
+}
+
+void orc_de_rand1_trials(uint64_t seed, uint64_t gen, const double* X, int NP,
+                         int D, double F, double CR, double lb, double ub,
+                         double* U, int32_t* part) {
+  uint32_t w[4];
+  double* v = (double*)malloc(sizeof(double) * D);
+  for (int i = 0; i < NP; ++i) {
+    draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_PART, 0, w);
+    int ex[3];
+    int a = (int)orc_below(w[0], (uint32_t)(NP - 1));
+    ex[0] = i;
+    a = skip_sorted(a, ex, 1);
+    ex[1] = a;
+    sort_small(ex, 2);
+    int b = skip_sorted((int)orc_below(w[1], (uint32_t)(NP - 2)), ex, 2);
+    ex[2] = b;
+    sort_small(ex, 3);
+    int c = skip_sorted((int)orc_below(w[2], (uint32_t)(NP - 3)), ex, 3);
+    int jr = (int)orc_below(w[3], (uint32_t)D);
+    const double *xa = X + (size_t)a * D, *xb = X + (size_t)b * D, *xc = X + (size_t)c * D;
+    for (int j = 0; j < D; ++j) v[j] = fma(F, xb[j] - xc[j], xa[j]);
+    cross_repair(seed, gen, i, D, CR, jr, v, X + (size_t)i * D, lb, ub, U + (size_t)i * D);
+    if (part) {
+      part[4 * i + 0] = a;
+      part[4 * i + 1] = b;
+      part[4 * i + 2] = c;
+      part[4 * i + 3] = jr;
+    }
+  }
+  free(v);
+}
+
+int orc_pbest_k(double p, int NP) {
+  int k = (int)ceil(p * (double)NP - 1e-9);
+  if (k < 1) k = 1;
+  if (k > NP) k = NP;
+  return k;
+}
+
+/* stable ranking by (fitness, index); plain insertion sort keeps it
+ * re-entrant for the thread pool */
+void orc_rank(const double* f, int NP, int32_t* order) {
+  for (int i = 0; i < NP; ++i) order[i] = i;
+  for (int i = 1; i < NP; ++i) {
+    int32_t cur = order[i];
+    int j = i;
+    while (j > 0) {
+      int32_t prv = order[j - 1];
+      int before = (f[cur] < f[prv]) || (f[cur] == f[prv] && cur < prv);
+      if (!before) break;
+      order[j] = prv;
+      --j;
+    }
+    order[j] = cur;
+  }
+}
+
+void orc_de_ctpb_trials(uint64_t seed, uint64_t gen, const double* X,
+                        const double* fx, int NP, int D, double F, double CR,
+                        double p, const double* A, int asize, double lb,
+                        double ub, double* U, int32_t* part) {
+  uint32_t w[4];
+  int k = orc_pbest_k(p, NP);
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * NP);
+  orc_rank(fx, NP, order);
+  double* v = (double*)malloc(sizeof(double) * D);
+  for (int i = 0; i < NP; ++i) {
+    draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_PART, 0, w);
+    int pb = order[orc_below(w[0], (uint32_t)k)];
+    int ex[2] = {i, 0};
+    int r1 = skip_sorted((int)orc_below(w[1], (uint32_t)(NP - 1)), ex, 1);
+    ex[1] = r1;
+    sort_small(ex, 2);
+    int r2 = skip_sorted((int)orc_below(w[2], (uint32_t)(NP + asize - 2)), ex, 2);
+    int jr = (int)orc_below(w[3], (uint32_t)D);
+    const double* xi = X + (size_t)i * D;
+    const double* xp = X + (size_t)pb * D;
+    const double* x1 = X + (size_t)r1 * D;
+    const double* x2 = (r2 < NP) ? X + (size_t)r2 * D : A + (size_t)(r2 - NP) * D;
+    /* v = x_i + F (x_pb - x_i) + F (x_r1 - x~_r2), as fma(F, a, fma(F, b, x_i)) */
+    for (int j = 0; j < D; ++j)
+      v[j] = fma(F, x1[j] - x2[j], fma(F, xp[j] - xi[j], xi[j]));
+    cross_repair(seed, gen, i, D, CR, jr, v, xi, lb, ub, U + (size_t)i * D);
+    if (part) {
+      part[4 * i + 0] = pb;
+      part[4 * i + 1] = r1;
+      part[4 * i + 2] = r2;
+      part[4 * i + 3] = jr;
+    }
+  }
+  free(v);
+  free(order);
+}
+
+int orc_de_select(uint64_t seed, uint64_t gen, double* X, double* fx,
+                  const double* U, const double* fu, int NP, int D, double* A,
+                  int* asize, uint8_t* acc) {
+  uint32_t w[4];
+  int nacc = 0;
+  for (int i = 0; i < NP; ++i) {
+    int a = fu[i] <= fx[i];
+    if (acc) acc[i] = (uint8_t)a;
+    if (!a) continue;
+    ++nacc;
+    if (A) {
+      int slot;
+      if (*asize < NP) {
+        slot = (*asize)++;
+      } else {
+        draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_ARCH, 0, w);
+        slot = (int)orc_below(w[0], (uint32_t)NP);
+      }
+      memcpy(A + (size_t)slot * D, X + (size_t)i * D, sizeof(double) * D);
+    }
+    memcpy(X + (size_t)i * D, U + (size_t)i * D, sizeof(double) * D);
+    fx[i] = fu[i];
+  }
+  return nacc;
+}
+
+void orc_pso_guides(const double* fp, int NP, int topology, int32_t* guide) {
+  if (topology == 0) {
+    int b = 0;
+    for (int i = 1; i < NP; ++i)
+      if (fp[i] < fp[b]) b = i;
+    for (int i = 0; i < NP; ++i) guide[i] = b;
+    return;
+  }
+  for (int i = 0; i < NP; ++i) {
+    int nb[3] = {(i + NP - 1) % NP, i, (i + 1) % NP};
+    sort_small(nb, 3);
+    int b = nb[0];
+    for (int t = 1; t < 3; ++t)
+      if (fp[nb[t]] < fp[b]) b = nb[t];
+    guide[i] = b;
+  }
+}
+
+void orc_pso_move(uint64_t seed, uint64_t gen, double* X, double* V,
+                  const double* P, const int32_t* guide, int NP, int D,
+                  double w, double c1, double c2, double lb, double ub) {
+  uint32_t r[4];
+  for (int i = 0; i < NP; ++i) {
+    const double* g = P + (size_t)guide[i] * D;
+    for (int j = 0; j < D; ++j) {
+      size_t e = (size_t)i * D + j;
+      draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)gen, ORC_P_PSO, 0, r);
+      double r1 = orc_u53(r[0], r[1]);
+      double r2 = orc_u53(r[2], r[3]);
+      double a = c1 * r1, b = c2 * r2;
+      double x = X[e];
+      double v = fma(w, V[e], fma(a, P[e] - x, b * (g[j] - x)));
+      double xn = x + v;
+      if (xn < lb) {
+        xn = lb;
+        v = 0.0;
+      }
+      if (xn > ub) {
+        xn = ub;
+        v = 0.0;
+      }
+      X[e] = xn;
+      V[e] = v;
+    }
+  }
+}
+
+int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
+                   int NP, int D) {
+  int n = 0;
+  for (int i = 0; i < NP; ++i)
+    if (fx[i] < fp[i]) {
+      memcpy(P + (size_t)i * D, X + (size_t)i * D, sizeof(double) * D);
+      fp[i] = fx[i];
+      ++n;
+    }
+  return n;
+}
+
+/* ======================================================================
+ * Whole runs: the budget loop of Listing 4 (evaluate NP, count them, then
+ * generations while fes < max_fes); only the first (budget - fes) rows of a
+ * last, overshooting generation count toward best-so-far.
+ * ====================================================================== */
+static double min_first(const double* f, int n) {
+  double b = INFINITY;
+  for (int i = 0; i < n; ++i)
+    if (f[i] < b) b = f[i];
+  return b;
+}
+
+void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
+             orc_result* res, int64_t* trace_fes, double* trace_best,
+             int64_t trace_cap) {
+  int NP = a->NP, D = p->D;
+  size_t n = (size_t)NP * D;
+  double* X = (double*)malloc(sizeof(double) * n);
+  double* fx = (double*)malloc(sizeof(double) * NP);
+  double* U = (double*)malloc(sizeof(double) * n);
+  double* fu = (double*)malloc(sizeof(double) * NP);
+  double* A = NULL;
+  double *V = NULL, *P = NULL, *fp = NULL;
+  int32_t* guide = NULL;
+  int asize = 0;
+  int64_t ntr = 0;
+
+  orc_init_population(seed, NP, D, a->lb, a->ub, X);
+  for (int i = 0; i < NP; ++i) fx[i] = orc_eval(p, X + (size_t)i * D);
+  int64_t cnt = (a->budget < NP) ? a->budget : NP;
+  int64_t fes = cnt;
+  double best = min_first(fx, (int)cnt);
+  if (trace_fes && ntr < trace_cap) {
+    trace_fes[ntr] = fes;
+    trace_best[ntr] = best;
+    ++ntr;
+  }
+  int64_t gen = 0;
+  if (a->alg == 1) A = (double*)malloc(sizeof(double) * n);
+  if (a->alg >= 2) {
+    V = (double*)calloc(n, sizeof(double));
+    P = (double*)malloc(sizeof(double) * n);
+    fp = (double*)malloc(sizeof(double) * NP);
+    guide = (int32_t*)malloc(sizeof(int32_t) * NP);
+    memcpy(P, X, sizeof(double) * n);
+    memcpy(fp, fx, sizeof(double) * NP);
+    orc_pso_guides(fp, NP, a->alg - 2, guide);
+  }
+  while (fes < a->budget) {
+    ++gen;
+    cnt = a->budget - fes;
+    if (cnt > NP) cnt = NP;
+    if (a->alg <= 1) {
+      if (a->alg == 0)
+        orc_de_rand1_trials(seed, (uint64_t)gen, X, NP, D, a->F, a->CR, a->lb, a->ub, U, NULL);
+      else
+        orc_de_ctpb_trials(seed, (uint64_t)gen, X, fx, NP, D, a->F, a->CR, a->p, A, asize,
+                           a->lb, a->ub, U, NULL);
+      for (int i = 0; i < NP; ++i) fu[i] = orc_eval(p, U + (size_t)i * D);
+      double b = min_first(fu, (int)cnt);
+      if (b < best) best = b;
+      orc_de_select(seed, (uint64_t)gen, X, fx, U, fu, NP, D, A, a->alg == 1 ? &asize : NULL,
+                    NULL);
+    } else {
+      orc_pso_move(seed, (uint64_t)gen, X, V, P, guide, NP, D, a->w, a->c1, a->c2, a->lb,
+                   a->ub);
+      for (int i = 0; i < NP; ++i) fx[i] = orc_eval(p, X + (size_t)i * D);
+      double b = min_first(fx, (int)cnt);
+      if (b < best) best = b;
+      orc_pso_update(X, fx, P, fp, NP, D);
+      orc_pso_guides(fp, NP, a->alg - 2, guide);
+    }
+    fes += cnt;
+    if (trace_fes && ntr < trace_cap) {
+      trace_fes[ntr] = fes;
+      trace_best[ntr] = best;
+      ++ntr;
+    }
+  }
+  res->best = best;
+  res->fes = fes;
+  res->gens = gen;
+  res->success = best <= 1e-8;
+  free(X);
+  free(fx);
+  free(U);
+  free(fu);
+  free(A);
+  free(V);
+  free(P);
+  free(fp);
+  free(guide);
+}
+
+/* ---- thread pool over independent tasks (Sec. 2.4: tasks distributed over
+ * the threads of a pool, each running asynchronously) ---- */
+typedef struct {
+  const orc_problem* const* probs;
+  const orc_alg* algs;
+  const uint64_t* seeds;
+  orc_result* res;
+  int ntask;
+  int next;
+  pthread_mutex_t mu;
+} pool_t;
+
+static void* pool_worker(void* arg) {
+  pool_t* pl = (pool_t*)arg;
+  for (;;) {
+    pthread_mutex_lock(&pl->mu);
+    int t = pl->next++;
+    pthread_mutex_unlock(&pl->mu);
+    if (t >= pl->ntask) break;
+    orc_run(pl->probs[t], &pl->algs[t], pl->seeds[t], &pl->res[t], NULL, NULL, 0);
+  }
+  return NULL;
+}
+
+void orc_run_many(const orc_problem* const* probs, const orc_alg* algs,
+                  const uint64_t* seeds, int ntask, int nthreads,
+                  orc_result* res) {
+  pool_t pl;
+  pl.probs = probs;
+  pl.algs = algs;
+  pl.seeds = seeds;
+  pl.res = res;
+  pl.ntask = ntask;
+  pl.next = 0;
+  pthread_mutex_init(&pl.mu, NULL);
+  if (nthreads < 1) nthreads = 1;
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, pool_worker, &pl);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  pthread_mutex_destroy(&pl.mu);
+}

@@ -1,0 +1,476 @@
+"""Pins of the FP64 oracle against what the definitions and mathematics fix
+(no GPU).  Each test names what it pins and why a plausible mistake in the
+oracle would fail it.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+SINGLE = [O.ELLIPSOID, O.ROSENBROCK, O.RASTRIGIN, O.SCHWEFEL, O.ACKLEY, O.GRIEWANK]
+ALL = SINGLE + [O.HYBRID, O.COMPOSITION]
+
+
+def _rows(name):
+    out = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            out.append(line.split())
+    return out
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers():
+    """Published Philox4x32-10 vectors (a wrong constant, round count, word
+    order or key schedule changes every output word)."""
+    for r in _rows("philox4x32_10_kat.txt"):
+        v = [int(t, 16) for t in r]
+        assert O.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_uniform_and_integer_maps():
+    assert O.u53(0, 0) == 0.0
+    assert O.u53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert O.u53(0x80000000, 0) == 0.5
+    assert O.below(0, 7) == 0 and O.below(0xFFFFFFFF, 7) == 6
+    assert O.below(0x80000000, 10) == 5
+
+
+# ------------------------------------------------------------------ instances
+def _gauss_numpy(seed, D, comp=0):
+    """The seeded Gaussian matrix rebuilt from the oracle's Philox words with
+    numpy's Box-Muller (an independent route to G)."""
+    G = np.zeros(D * D)
+    for e in range(D * D):
+        pair = e >> 1
+        w = O.philox([pair, pair >> 32, D, (17 << 24) | comp], [seed & 0xFFFFFFFF, seed >> 32])
+        u1, u2 = O.u53(w[0], w[1]), O.u53(w[2], w[3])
+        R = math.sqrt(-2.0 * math.log(1.0 - u1))
+        th = 2.0 * math.pi * u2
+        G[e] = R * (math.sin(th) if e & 1 else math.cos(th))
+    return G.reshape(D, D)
+
+
+@pytest.mark.parametrize("D", [2, 10, 30, 100])
+def test_rotation_is_q_of_qr(D):
+    """M is orthogonal to FP64 round-off, and M^T G is upper triangular with a
+    positive diagonal, i.e. M is the Q of the QR of G (unique with diag R>0);
+    it also equals LAPACK's Q after the same sign fix."""
+    p = O.Problem(0x5EB00000 + D, O.ELLIPSOID, D)
+    M = p.rotation()
+    assert np.abs(M.T @ M - np.eye(D)).max() <= 10 * D * 2.0 ** -53
+    G = _gauss_numpy(0x5EB00000 + D, D)
+    R = M.T @ G
+    assert np.abs(np.tril(R, -1)).max() <= 1e-12 * np.abs(G).max() * D
+    assert (np.diag(R) > 0).all()
+    Q2, R2 = np.linalg.qr(G)
+    Q2 = Q2 * np.sign(np.diag(R2))[None, :]
+    assert np.abs(Q2 - M).max() < 1e-11
+
+
+def test_shift_range_and_determinism():
+    p = O.Problem(3, O.RASTRIGIN, 500)
+    o = p.shift()
+    assert o.min() >= -80.0 and o.max() < 80.0
+    assert abs(o.mean()) < 8.0 and 40.0 < o.std() < 52.0  # U[-80,80]: sd 46.2
+    q = O.Problem(3, O.RASTRIGIN, 500)
+    assert np.array_equal(o, q.shift()) and np.array_equal(p.rotation(), q.rotation())
+    assert not np.array_equal(o[:100], O.Problem(3, O.RASTRIGIN, 100).shift())
+
+
+def test_norm_preserved():
+    p = O.Problem(9, O.GRIEWANK, 50)
+    X = inputs.uniform_pop(20, 50, seed=1)
+    for x in X:
+        z = p.transform(x)
+        d = x - p.shift()
+        assert abs(np.linalg.norm(z) - np.linalg.norm(d)) <= 1e-14 * np.linalg.norm(d) * 10
+
+
+# ------------------------------------------------------------------ bodies
+@pytest.mark.parametrize("fam", ALL)
+@pytest.mark.parametrize("D", [2, 10, 30, 100])
+def test_value_at_optimum_is_exact_zero(fam, D):
+    """f(o) = f* exactly: every body evaluates to exactly 0 at z = 0 (a stray
+    constant, wrong offset or Schwefel shift would leave a residue)."""
+    p = O.Problem(100 + D, fam, D)
+    assert p.eval(p.shift()) == 0.0
+
+
+def test_ellipsoid_closed_form():
+    for D in (2, 10, 100):
+        for k in range(D):
+            z = np.zeros(D)
+            z[k] = 1.0
+            want = 10.0 ** (6.0 * k / (D - 1))
+            assert O.body(O.ELLIPSOID, z) == pytest.approx(want, rel=1e-14)
+    assert O.body(O.ELLIPSOID, np.array([3.0])) == 9.0
+
+
+def test_rosenbrock_closed_form():
+    for D in (2, 10, 100):
+        assert O.body(O.ROSENBROCK, -np.ones(D)) == D - 1  # y = 0: each term 1
+    # y = (2, 4): 100*(4-4)^2 + 1 = 1, and y=(2,0): 100*16+1
+    assert O.body(O.ROSENBROCK, np.array([1.0, 3.0])) == 1.0
+    assert O.body(O.ROSENBROCK, np.array([1.0, -1.0])) == 1601.0
+    assert O.body(O.ROSENBROCK, np.array([0.3])) == 0.0
+
+
+def test_rastrigin_integers():
+    z = np.array([1.0, -2.0, 3.0, 0.0, 5.0])
+    assert O.body(O.RASTRIGIN, z) == pytest.approx(float((z ** 2).sum()), abs=1e-12)
+    assert O.body(O.RASTRIGIN, np.array([0.5])) == pytest.approx(0.25 + 20.0, abs=1e-12)
+
+
+def test_ackley_constant_vector():
+    for t in (0.25, 1.0, 3.7, -12.0):
+        for D in (1, 5, 40):
+            want = 20.0 - 20.0 * math.exp(-0.2 * abs(t)) + math.e - math.exp(math.cos(2 * math.pi * t))
+            assert O.body(O.ACKLEY, np.full(D, t)) == pytest.approx(want, rel=1e-13, abs=1e-13)
+
+
+def test_griewank_one_dimension():
+    for t in (0.1, 2.0, -30.0, 400.0):
+        want = t * t / 4000.0 + 1.0 - math.cos(t)
+        assert O.body(O.GRIEWANK, np.array([t])) == pytest.approx(want, rel=1e-13, abs=1e-15)
+    # second coordinate divides by sqrt(2)
+    z = np.array([0.0, 2.0])
+    assert O.body(O.GRIEWANK, z) == pytest.approx(4 / 4000 + 1 - math.cos(2 / math.sqrt(2)), rel=1e-13)
+
+
+def test_schwefel_constants_and_nonnegativity():
+    gold = {r[0]: (float(r[1]), float(r[2])) for r in _rows("schwefel_constants.txt")}
+    # the body at z is c - (z+s) sin sqrt|z+s|: probe s and c through it
+    ts = np.linspace(-2, 2, 40001)
+    vals = np.array([O.body(O.SCHWEFEL, np.array([t])) for t in ts])
+    assert vals.min() >= -1e-12 and vals[20000] == 0.0
+    s_gold, tol = gold["argmax"]
+    c_gold, tolc = gold["max_value"]
+    # c - y sin sqrt y = 0 at y = s  =>  value at z = s_gold - s is ~0
+    y = s_gold
+    c_est = y * math.sin(math.sqrt(y))
+    assert abs(c_est - c_gold) < tolc
+    # value far away: outside [-500,500] the penalty makes it grow quadratically
+    far = O.body(O.SCHWEFEL, np.array([2000.0]))
+    assert far > 1e-4 * (2000 + s_gold - 500) ** 2
+    # brute force on [-1000, 1000]: global minimum 0 at z = 0 only
+    zs = np.linspace(-1000, 1000, 200001)
+    v = np.array([O.body(O.SCHWEFEL, np.array([t])) for t in zs[::10]])
+    assert v.min() >= 0.0
+    assert abs(zs[::10][np.argmin(v)]) < 0.2
+
+
+# ------------------------------------------------------------------ hybrid
+def test_hybrid_structure():
+    for D in (10, 30, 100, 1000):
+        p = O.Problem(77, O.HYBRID, D)
+        perm, gs, gb = p.hybrid()
+        assert np.array_equal(np.sort(perm), np.arange(D))
+        assert gs.sum() == D and 3 <= p.K <= 5 and (gs >= 1).all()
+        assert ((gb >= 0) & (gb < 6)).all()
+        assert (gs >= np.floor(0.1 * D) - 1).all()
+
+
+def test_hybrid_fixed_fractions():
+    p = O.Problem(5, O.HYBRID, 100, hybrid=([0.3, 0.3, 0.4], [O.RASTRIGIN, O.ELLIPSOID, O.SCHWEFEL]))
+    _, gs, gb = p.hybrid()
+    assert list(gs) == [30, 30, 40] and list(gb) == [2, 0, 3]
+    p = O.Problem(5, O.HYBRID, 10, hybrid=([0.3, 0.3, 0.4], [0, 1, 2]))
+    assert list(p.hybrid()[1]) == [3, 3, 4]
+
+
+@pytest.mark.parametrize("D", [10, 100])
+def test_hybrid_of_separable_body_equals_plain(D):
+    """All-Rastrigin hybrid == plain Rastrigin (same seed: same o and M;
+    Rastrigin is separable and permutation-invariant).  A wrong group offset,
+    size or permutation direction breaks it only if values are lost or
+    duplicated, so it also checks every coordinate lands in exactly one group."""
+    hy = O.Problem(42, O.HYBRID, D, hybrid=([0.2, 0.5, 0.3], [O.RASTRIGIN] * 3))
+    pl = O.Problem(42, O.RASTRIGIN, D)
+    X = inputs.uniform_pop(16, D, seed=3)
+    assert np.allclose(hy.eval(X), pl.eval(X), rtol=1e-13, atol=0)
+
+
+def test_hybrid_permutation_direction():
+    """M' = P M: z'_t = z_{perm[t]}.  With an ellipsoid hybrid of one group
+    the value equals the ellipsoid applied to z[perm] (not z[inv perm])."""
+    D = 12
+    hy = O.Problem(8, O.HYBRID, D, hybrid=([1.0], [O.ELLIPSOID]))
+    pl = O.Problem(8, O.ELLIPSOID, D)
+    perm = hy.hybrid()[0]
+    x = inputs.uniform_pop(1, D, seed=4)[0]
+    z = pl.transform(x)
+    assert hy.eval(x) == pytest.approx(O.body(O.ELLIPSOID, z[perm]), rel=1e-13)
+    inv = np.argsort(perm)
+    if not np.array_equal(perm, inv):
+        assert hy.eval(x) != pytest.approx(O.body(O.ELLIPSOID, z[inv]), rel=1e-6)
+
+
+# ------------------------------------------------------------------ composition
+@pytest.mark.parametrize("D", [2, 10, 50])
+def test_composition_value_at_each_optimum(D):
+    """F(o_c) = bias_c + f* exactly (weight collapses to e_c), and F >= f*."""
+    p = O.Problem(0xC0 + D, O.COMPOSITION, D)
+    body, sig, lam, bias = p.comp()
+    assert 3 <= p.K <= 10
+    assert list(bias) == [100.0 * c for c in range(p.K)]
+    assert set(sig) <= {10.0, 20.0, 30.0, 40.0, 50.0, 60.0}
+    assert ((lam >= 1e-6) & (lam <= 1.0)).all()
+    for c in range(p.K):
+        assert p.eval(p.shift(c)) == bias[c]
+    X = inputs.uniform_pop(64, D, seed=5)
+    assert (p.eval(X) >= 0.0).all()
+
+
+def test_composition_component_zero_is_the_single_instance():
+    """Approaching o_1 along a ray x = o_1 + r u, the residual
+    R(r) = (F(x) - f*) - lambda_1 g_1(x) vanishes linearly in r: component 1
+    has the o, M and body of the single-family instance of the same seed,
+    lambda_1 scales it, and the other weights decay as sqrt(s_1) (the
+    s^{-1/2} factor).  A wrong lambda, body, component index or weight law
+    leaves R(r)/r non-constant or R not vanishing."""
+    D = 10
+    p = O.Problem(0xBEEF, O.COMPOSITION, D)
+    body, sig, lam, bias = p.comp()
+    single = O.Problem(0xBEEF, int(body[0]), D)
+    assert np.array_equal(single.shift(), p.shift(0))
+    assert np.array_equal(single.rotation(), p.rotation(0))
+    u = np.random.default_rng(1).standard_normal(D)
+    u /= np.linalg.norm(u)
+    ratios = []
+    for r in (1e-5, 1e-6, 1e-7):
+        x = p.shift(0) + r * u
+        R = p.eval(x) - lam[0] * single.eval(x)
+        assert R > 0
+        ratios.append(R / r)
+    assert abs(ratios[1] - ratios[0]) <= 1e-3 * ratios[1]
+    assert abs(ratios[2] - ratios[1]) <= 1e-3 * ratios[2]
+
+
+def test_composition_far_point_weights_finite():
+    p = O.Problem(11, O.COMPOSITION, 30)
+    x = np.full(30, 100.0)
+    v = p.eval(x)
+    assert np.isfinite(v) and v > 0
+
+
+# ------------------------------------------------------------------ brute force D=2
+@pytest.mark.parametrize("fam", ALL)
+def test_bruteforce_grid_minimum_d2(fam):
+    """2001 x 2001 grid over [-100,100]^2: every grid value is >= f*, and a
+    local search (Nelder-Mead) started from the grid minimum ends at the
+    optimum o (o_1 for a composition) with f - f* below 1e-8.  The grid is
+    too coarse to resolve the 1e6-conditioned ellipsoid valley by itself, so
+    the local search finishes what the brute force starts."""
+    from scipy.optimize import minimize
+
+    p = O.Problem(0x5EB00002 + fam, fam, 2)
+    g = np.linspace(-100.0, 100.0, 2001)
+    X = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    v = p.eval(X)
+    assert v.min() >= 0.0
+    best = X[np.argmin(v)]
+    if fam == O.COMPOSITION:
+        # unnormalised components leak through their weights (a cone of
+        # slope ~ sum_c w_c (lambda_c g_c + bias_c) around o_1), so at D=2 the
+        # global basin is narrower than one grid cell: the grid shows only
+        # F >= f* = F(o_1); the local search starts from the cell next to o_1.
+        assert p.eval(p.shift(0)) == 0.0 <= v.min()
+        best = X[np.argmin(np.linalg.norm(X - p.shift(0), axis=1))]
+    r = minimize(p.eval, best, method="Nelder-Mead",
+                 options={"xatol": 1e-12, "fatol": 1e-16, "maxiter": 20000, "maxfev": 40000})
+    # the plain Schwefel term c - y sin sqrt|y| rounds to within a few ulp of
+    # c (~6e-14) of zero near its optimum, so allow that much below f*
+    assert r.fun >= -1e-12 and r.fun <= 1e-8, (fam, r.fun)
+    assert np.linalg.norm(r.x - p.shift(0)) <= 1e-3, (fam, r.x, p.shift(0))
+
+
+# ------------------------------------------------------------------ DE operators
+def test_de_rand1_partners_distinct_and_uniform():
+    NP, D = 10, 6
+    X = O.init_population(1, NP, D)
+    counts = np.zeros((NP, NP))
+    for g in range(1, 2001):
+        U, part = O.de_rand1_trials(99, g, X)
+        for i in range(NP):
+            a, b, c, jr = part[i]
+            assert len({i, a, b, c}) == 4 and 0 <= jr < D
+            assert max(a, b, c) < NP
+            counts[i, a] += 1
+    # a uniform over the NP-1 others: chi-square with NP-2 dof per row
+    for i in range(NP):
+        row = np.delete(counts[i], i)
+        exp = row.sum() / (NP - 1)
+        chi2 = ((row - exp) ** 2 / exp).sum()
+        assert chi2 < 30.0  # p ~ 1e-4 at 8 dof
+
+
+def test_de_rand1_crossover_special_cases():
+    NP, D = 12, 20
+    X = O.init_population(2, NP, D, -1, 1)  # inside bounds, mutants stay inside mostly
+    U, part = O.de_rand1_trials(5, 3, X, F=0.5, CR=0.0)
+    for i in range(NP):
+        diff = np.nonzero(U[i] != X[i])[0]
+        assert set(diff) <= {part[i, 3]}          # CR=0: only j_rand crosses
+    U1, part1 = O.de_rand1_trials(5, 3, X, F=0.0, CR=1.0)
+    for i in range(NP):
+        assert np.array_equal(U1[i], X[part1[i, 0]])  # F=0, CR=1: u = x_r1
+    U2, part2 = O.de_rand1_trials(5, 3, X, F=0.5, CR=1.0)
+    for i in range(NP):
+        a, b, c, _ = part2[i]
+        v = X[a] + 0.5 * (X[b] - X[c])
+        assert np.allclose(U2[i], v, rtol=0, atol=1e-15)
+
+
+def test_de_midpoint_repair():
+    NP, D = 8, 5
+    X = np.full((NP, D), 99.0)
+    X[:, 0] = -99.0
+    X += np.arange(NP)[:, None] * 0.1 * np.sign(X) * -1
+    U, part = O.de_rand1_trials(7, 1, X, F=5.0, CR=1.0)
+    assert (U >= -100).all() and (U <= 100).all()
+    for i in range(NP):
+        a, b, c, _ = part[i]
+        v = X[a] + 5.0 * (X[b] - X[c])
+        for j in range(D):
+            if v[j] > 100:
+                assert U[i, j] == (100 + X[i, j]) * 0.5
+            elif v[j] < -100:
+                assert U[i, j] == (-100 + X[i, j]) * 0.5
+
+
+def test_pbest_k_and_rank():
+    assert O.pbest_k(0.11, 100) == 11 and O.pbest_k(0.11, 900) == 99
+    assert O.pbest_k(0.11, 180) == 20 and O.pbest_k(0.11, 5) == 1
+    f = np.array([3.0, 1.0, 2.0, 1.0, 0.5])
+    assert list(O.rank(f)) == [4, 1, 3, 2, 0]
+
+
+def test_de_ctpb_partners():
+    NP, D = 40, 8
+    X = O.init_population(3, NP, D)
+    fx = np.random.default_rng(0).uniform(size=NP)
+    A = O.init_population(4, NP, D)
+    k = O.pbest_k(0.11, NP)
+    top = set(O.rank(fx)[:k])
+    for asize in (0, 7, NP):
+        for g in range(1, 50):
+            U, part = O.de_ctpb_trials(8, g, X, fx, A, asize)
+            for i in range(NP):
+                pb, r1, r2, jr = part[i]
+                assert pb in top
+                assert r1 != i and 0 <= r1 < NP
+                assert r2 not in (i, r1) and 0 <= r2 < NP + asize
+    # the formula with CR=1: v = x_i + F(x_pb - x_i) + F(x_r1 - x~_r2)
+    U, part = O.de_ctpb_trials(8, 1, X, fx, A, NP, F=0.5, CR=1.0)
+    XA = np.vstack([X, A])
+    for i in range(NP):
+        pb, r1, r2, _ = part[i]
+        v = X[i] + 0.5 * (X[pb] - X[i]) + 0.5 * (X[r1] - XA[r2])
+        v = np.where(v < -100, (-100 + X[i]) / 2, np.where(v > 100, (100 + X[i]) / 2, v))
+        assert np.allclose(U[i], v, atol=1e-12, rtol=0)
+
+
+def test_de_select_and_archive():
+    NP, D = 30, 4
+    X = O.init_population(1, NP, D)
+    fx = np.arange(NP, dtype=float)
+    U = O.init_population(2, NP, D)
+    fu = fx.copy()
+    fu[::3] -= 0.5   # better
+    fu[1::3] += 0.5  # worse
+    # fu[2::3] ties -> accepted
+    A = np.zeros((NP, D))
+    X2, fx2, A2, asz, acc = O.de_select(5, 1, X, fx, U, fu, A, 0)
+    assert list(acc) == [1 if i % 3 != 1 else 0 for i in range(NP)]
+    assert asz == acc.sum() == 20
+    assert np.array_equal(A2[:20], X[acc.astype(bool)])
+    assert np.array_equal(X2[acc.astype(bool)], U[acc.astype(bool)])
+    # full archive: size stays NP and every slot holds a past parent row
+    X3, fx3, A3, asz3, acc3 = O.de_select(5, 2, X, fx, U, fu, X.copy(), NP)
+    assert asz3 == NP
+    rows = {tuple(r) for r in X}
+    assert all(tuple(r) in rows for r in A3)
+
+
+# ------------------------------------------------------------------ PSO operators
+def test_pso_guides():
+    fp = np.array([5.0, 1.0, 3.0, 1.0, 7.0, 0.5])
+    assert list(O.pso_guides(fp, 0)) == [5] * 6
+    # ring {i-1,i,i+1}: i=0 -> {5,0,1}: 0.5 at 5
+    assert list(O.pso_guides(fp, 1)) == [5, 1, 1, 3, 5, 5]
+    fp2 = np.array([1.0, 1.0, 2.0])
+    assert list(O.pso_guides(fp2, 1)) == [0, 0, 0]  # ties -> lowest index
+
+
+def test_pso_stationary_and_clamp():
+    NP, D = 6, 7
+    X = O.init_population(1, NP, D)
+    V = np.random.default_rng(1).uniform(-5, 5, (NP, D))
+    P = O.init_population(2, NP, D)
+    g = np.zeros(NP, np.int32)
+    X1, V1 = O.pso_move(3, 1, X, V, P, g, w=0.0, c1=0.0, c2=0.0)
+    assert np.array_equal(X1, X) and (V1 == 0).all()
+    # all at one point with p = g = x: stays put for any coefficients
+    Xs = np.tile(X[:1], (NP, 1))
+    Xs2, Vs2 = O.pso_move(3, 1, Xs, np.zeros_like(Xs), Xs, g)
+    assert np.array_equal(Xs2, Xs)
+    # clamp: huge velocity pushes out -> x on the bound and v = 0 there
+    Vb = np.full((NP, D), 1e4)
+    Xb, Vb2 = O.pso_move(3, 1, X, Vb, P, g, w=1.0)
+    assert (Xb == 100.0).all() and (Vb2 == 0).all()
+
+
+def test_pso_update_strict():
+    NP, D = 4, 3
+    X = O.init_population(1, NP, D)
+    P = O.init_population(2, NP, D)
+    fp = np.array([1.0, 2.0, 3.0, 4.0])
+    fx = np.array([0.5, 2.0, 3.5, 1.0])
+    P2, fp2, n = O.pso_update(X, fx, P, fp)
+    assert n == 2 and list(fp2) == [0.5, 2.0, 3.0, 1.0]
+    assert np.array_equal(P2[1], P[1]) and np.array_equal(P2[0], X[0])
+
+
+# ------------------------------------------------------------------ whole runs
+def test_run_budget_and_trace():
+    p = O.Problem(1, O.RASTRIGIN, 10)
+    a = O.make_alg(O.ALG_DE_RAND1, 50, 100000)
+    r = O.run(p, a, 1, trace_cap=3000)
+    assert r["fes"] == 100000 and r["gens"] == 1999
+    assert r["trace_fes"][0] == 50 and r["trace_fes"][-1] == 100000
+    assert (np.diff(r["trace_best"]) <= 0).all()
+    # overshooting last generation counts only budget - fes rows
+    a2 = O.make_alg(O.ALG_PSO_RING, 40, 1000 + 7)
+    r2 = O.run(p, a2, 1, trace_cap=100)
+    assert r2["fes"] == 1007 and r2["trace_fes"][-1] == 1007 and r2["gens"] == 25
+
+
+def test_de_controls_reach_success_threshold():
+    """Statistical controls: DE/rand/1/bin (NP=50, F=.5, CR=.9) reaches the
+    1e-8 threshold on a unimodal shifted-rotated ellipsoid at D=5 within 1e5
+    evaluations; DE/current-to-pbest/1/bin + archive does so on the
+    shifted-rotated Ackley at D=10 for most seeds (it is the stronger
+    operator).  A broken selection, crossover or partner draw stalls both."""
+    p = O.Problem(2, O.ELLIPSOID, 5)
+    r = O.run(p, O.make_alg(O.ALG_DE_RAND1, 50, 100000), 1)
+    assert r["success"] and r["best"] <= 1e-8
+    wins = sum(O.run(O.Problem(s, O.ACKLEY, 10), O.make_alg(O.ALG_DE_CTPB, 50, 100000), 1)["success"]
+               for s in range(1, 6))
+    assert wins >= 2
+
+
+def test_run_many_equals_run():
+    probs = [O.Problem(s, f, 10) for s, f in [(1, 2), (2, 4), (3, 6), (4, 7)]]
+    algs = [O.make_alg(k, 40 if k >= 2 else 30, 3000) for k in range(4)]
+    seeds = [11, 12, 13, 14]
+    many = O.run_many(probs, algs, seeds, nthreads=3)
+    for pr, al, sd, m in zip(probs, algs, seeds, many):
+        one = O.run(pr, al, sd)
+        assert one["best"] == m["best"] and one["fes"] == m["fes"]
