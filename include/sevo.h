@@ -1,0 +1,246 @@
+/*
+ * sevo.h -- C ABI of the GB300 batched evolutionary-benchmark hot path.
+ *
+ * What the library computes (SEvoBench, arXiv 2505.17430):
+ *   - problems are (suite, dimension, instance) triples with seeded random
+ *     instances (Sec. 1; Sec. 2.3, Listing 2): here a family, a dimension D
+ *     and a 64-bit seed give a shifted-rotated, hybrid or composition
+ *     instance;
+ *   - an algorithm is a callable over the fitness function with an
+ *     evaluation budget (Sec. 2.2; Sec. 4, Listing 4): here DE
+ *     (rand/1/bin, current-to-pbest/1/bin with an external archive,
+ *     binomial crossover, midpoint-target repair -- Listing 1) and PSO
+ *     (inertia weight, global or ring "lbest" topology -- Listing 1);
+ *   - the runner takes (algorithm, suite, observer, independent runs)
+ *     (Sec. 2.4, Listing 3) and records the best-so-far error
+ *     (Sec. 2.4, Sec. 3.2).
+ * The paper prints no formula for any body, transform or operator; the
+ * readings this library implements are listed, one by one, in the project's
+ * design notes, and each function below says which it uses.
+ *
+ * Conventions for every call:
+ *   - returns int32 status: SEVO_OK (0) or a negative SEVO_ERR_* code; the
+ *     library never aborts, traps or exits; sevo_strerror() explains a code;
+ *   - "device" pointers are CUDA global-memory pointers on the device that was
+ *     current when the object was created; "host" pointers are ordinary CPU
+ *     memory;
+ *   - streams are caller-owned cudaStream_t passed as void* (NULL = legacy
+ *     default stream); calls that only launch work are asynchronous on that
+ *     stream; calls that return results to the host synchronize it;
+ *   - FP64 populations are row-major N x D with a leading dimension ld >= D
+ *     (in elements); ld * 8 must be a multiple of 16 bytes for the tensor-core
+ *     paths (ld even); row pointers must be 16-byte aligned.
+ */
+#ifndef SEVO_H
+#define SEVO_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SEVO_OK 0
+#define SEVO_ERR_ARG -1          /* bad argument (range, NULL, alignment)  */
+#define SEVO_ERR_CUDA -2         /* a CUDA runtime call failed             */
+#define SEVO_ERR_OOM -3          /* device or host allocation failed       */
+#define SEVO_ERR_TIMEOUT -4      /* a bounded device wait gave up          */
+#define SEVO_ERR_NAN -5          /* NaN/Inf in an input population         */
+#define SEVO_ERR_UNSUPPORTED -6  /* size or mode not supported             */
+#define SEVO_ERR_STATE -7        /* object in the wrong state for the call */
+
+const char* sevo_strerror(int32_t status);
+/* library version, e.g. 100 for 0.1.0 */
+int32_t sevo_version(void);
+
+/* ---- problem families and precision modes ----------------------------- */
+enum sevo_family {
+  SEVO_ELLIPSOID = 0,   /* sum 10^{6(i-1)/(n-1)} z_i^2                      */
+  SEVO_ROSENBROCK = 1,  /* y=z+1: sum 100(y_i^2-y_{i+1})^2 + (y_i-1)^2        */
+  SEVO_RASTRIGIN = 2,   /* sum z^2 - 10 cos(2 pi z) + 10                       */
+  SEVO_SCHWEFEL = 3,    /* y=z+s: sum c - y sin sqrt|y| (+ outside penalty)   */
+  SEVO_ACKLEY = 4,      /* 20 - 20 e^{-0.2 rms(z)} + e - e^{mean cos 2 pi z}  */
+  SEVO_GRIEWANK = 5,    /* sum z^2/4000 + 1 - prod cos(z_i/sqrt i)            */
+  SEVO_HYBRID = 6,      /* permuted z split into 3..5 groups, a body each     */
+  SEVO_COMPOSITION = 7  /* 3..10 shifted-rotated components, distance weights */
+};
+
+enum sevo_prec {
+  SEVO_FP64 = 0,     /* plain FP64 path: DFMA rotation, FP64 bodies           */
+  SEVO_TF32 = 1,     /* tcgen05 TF32 rotation GEMM, FP32 bodies, FP64 refine   */
+  SEVO_BF16X3 = 2,   /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi), FP64 refine */
+  SEVO_FP32 = 3      /* CUDA-core FP32 rotation, FP32 bodies, FP64 refine      */
+};
+
+/* rows whose mixed-precision error is below this are re-evaluated in FP64 */
+#define SEVO_REFINE_THRESHOLD 1e-4
+/* a run succeeds when its best-so-far FP64 error is at most this */
+#define SEVO_SUCCESS_THRESHOLD 1e-8
+#define SEVO_MAX_D 5000
+#define SEVO_MAX_GROUPS 8
+#define SEVO_MAX_COMPONENTS 10
+
+/* ---- problems -------------------------------------------------------- */
+typedef struct sevo_problem sevo_problem; /* opaque, library-owned */
+
+/* Create a seeded random instance of `family` in dimension D (2..5000)
+ * (Sec. 1: random instances per problem; Sec. 2.3).  The instance is built
+ * on the host; its device copy is made on first device use, on the device
+ * current then (later use from another device returns SEVO_ERR_STATE).
+ *   shift o ~ U[-80,80]^D; rotation M = Q of the QR (diag R > 0) of a D x D
+ *   standard-normal matrix (Box-Muller over Philox4x32-10); hybrid: K in
+ *   {3,4,5} groups, fractions 0.1 + (1-0.1K) E_k / sum E (E ~ Exp(1)), a
+ *   Fisher-Yates permutation P folded into M' = P M, a body per group;
+ *   composition: Nc in [3,10] components with their own o_c, M_c, body,
+ *   sigma_c in {10..60}, lambda_c = 10^{U[-6,0]}, bias_c = 100 c.
+ *   f* = 100 for every instance.  Host cost O(D^3) (QR); device memory
+ *   ~ 16 D^2 bytes per rotation.
+ * out: receives a handle owned by the caller until sevo_problem_destroy. */
+int32_t sevo_problem_create(uint64_t seed, int32_t family, int32_t D, sevo_problem** out);
+
+/* Hybrid with caller-fixed groups: K (1..8) fractions frac[k] (group k gets
+ * floor(frac[k] D) coordinates, the last one the remainder) and bodies[k]
+ * (SEVO_ELLIPSOID..SEVO_GRIEWANK).  Permutation and rotation are still drawn
+ * from the seed (same o and M as the single-family instance of that seed). */
+int32_t sevo_hybrid_create(uint64_t seed, int32_t D, int32_t K, const double* frac,
+                           const int32_t* bodies, sevo_problem** out);
+
+int32_t sevo_problem_destroy(sevo_problem* p);
+
+/* family, D, K (hybrid groups) or Nc (components) else 1, and f* (host) */
+int32_t sevo_problem_info(const sevo_problem* p, int32_t* family, int32_t* D,
+                          int32_t* ncomp, double* fstar);
+
+/* Copy instance data to host buffers (any may be NULL): component `comp`'s
+ * shift o (D) and rotation M (D*D row-major, hybrid: permuted M'); hybrid
+ * perm (D), gsize and gbody (K); composition body, sigma, lambda, bias (Nc). */
+int32_t sevo_problem_export(const sevo_problem* p, int32_t comp, double* o, double* M,
+                            int32_t* perm, int32_t* gsize, int32_t* gbody, double* sigma,
+                            double* lambda, double* bias);
+
+/* ---- batched fitness evaluation (the hot path) ------------------------ */
+/* Evaluate N individuals: out[i] = f(pop_i) - f*, FP64 (Sec. 2.3 problem
+ * module; best-so-far error of Sec. 2.4 is this value).
+ *   pop: device, N x D row-major FP64, leading dimension ld >= D;
+ *   out: device, N doubles; prec: enum sevo_prec.
+ * Mixed modes (TF32, BF16X3, FP32) compute z = M (x - o) with the shift in
+ * FP64, the product in reduced precision with FP32 accumulation and the
+ * bodies in FP32; every row whose result is below SEVO_REFINE_THRESHOLD is
+ * recomputed on the FP64 path before the call's work completes.
+ * Scratch memory comes from a per-problem, per-device pool the library
+ * allocates on first use (rows x D x 4 bytes for large D).
+ * Errors: SEVO_ERR_ARG for bad sizes/pointers, SEVO_ERR_UNSUPPORTED for a
+ * mode/size combination not built.  Asynchronous on `stream`. */
+int32_t sevo_evaluate(const sevo_problem* p, const double* pop, int64_t N, int32_t D,
+                      int64_t ld, double* out, int32_t prec, void* stream);
+
+/* Same as sevo_evaluate, and also returns (host, after synchronizing the
+ * stream) how many rows were refined in FP64 and how many rows held NaN/Inf
+ * (those rows get NaN in out and the call returns SEVO_ERR_NAN). */
+int32_t sevo_evaluate_sync(const sevo_problem* p, const double* pop, int64_t N, int32_t D,
+                           int64_t ld, double* out, int32_t prec, void* stream,
+                           int64_t* refined, int64_t* nonfinite);
+
+/* ---- algorithms and runs ---------------------------------------------- */
+enum sevo_alg {
+  SEVO_DE_RAND1 = 0,     /* DE/rand/1/bin                                  */
+  SEVO_DE_CTPB = 1,      /* DE/current-to-pbest/1/bin + external archive   */
+  SEVO_PSO_GBEST = 2,    /* inertia-weight PSO, global topology            */
+  SEVO_PSO_RING = 3      /* inertia-weight PSO, ring {i-1,i,i+1} topology  */
+};
+
+typedef struct {
+  int32_t alg;        /* enum sevo_alg                                   */
+  int32_t NP;         /* population size (DE >= 4, PSO >= 2)              */
+  double F, CR, p;    /* DE scale, crossover rate, pbest fraction         */
+  double w, c1, c2;   /* PSO inertia and acceleration coefficients        */
+  double lb, ub;      /* box bounds of every coordinate                   */
+  int64_t budget;     /* evaluation budget (Listing 4's max_fes)          */
+  int32_t prec;       /* enum sevo_prec used for every evaluation         */
+} sevo_alg_params;
+
+typedef struct sevo_state sevo_state; /* opaque, library-owned */
+
+/* Allocate one run's device state for problem p, draw the initial
+ * population x_ij = lb + (ub-lb) u (Philox, generation 0), evaluate it and
+ * count NP evaluations (Listing 4's initial evaluate + add_fes).  The state
+ * keeps a pointer to p, which must outlive it. */
+int32_t sevo_state_create(const sevo_problem* p, const sevo_alg_params* a, uint64_t seed,
+                          void* stream, sevo_state** out);
+int32_t sevo_state_destroy(sevo_state* s);
+
+/* One DE generation (DE algorithms only): trials from the Philox stream at
+ * counter `philox_counter` (mutation, binomial crossover, midpoint-target
+ * repair -- Listing 1), their evaluation, one-to-one selection f(u) <= f(x)
+ * and, for current-to-pbest, archive insertion of replaced parents.
+ * Counts min(NP, budget - fes) evaluations toward best-so-far.
+ * SEVO_ERR_STATE if the budget is already spent or the algorithm is PSO. */
+int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
+
+/* One PSO generation (PSO algorithms only): velocity and position update
+ * with per-coordinate r1, r2 from the Philox stream at `philox_counter`,
+ * clamp to [lb,ub] (velocity zeroed where clamped), evaluation, strict pbest
+ * update and guide (gbest or ring lbest) refresh. */
+int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter);
+
+/* Synchronize the state's stream and read the run's bookkeeping (host). */
+int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes, int64_t* gens,
+                          int64_t* refined);
+
+/* Host copies of the state arrays (any pointer may be NULL):
+ * X, fx (current population and fitness), A (archive rows, asize of them),
+ * V, P, fp (PSO velocity, pbest, pbest fitness), U, fu, part (last
+ * generation's trial vectors, their fitness and the per-row draws:
+ * DE r1,r2,r3,jrand or pbest,r1,r2,jrand; PSO: guide in part[4i]).
+ * Arrays are NP x D row-major (ld = D). Synchronizes. */
+int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A, int32_t* asize,
+                       double* V, double* P, double* fp, double* U, double* fu, int32_t* part);
+/* Overwrite the state arrays from host copies (NULL = leave as is); fes is
+ * set to `fes` (>= 0) and guides are recomputed for PSO. */
+int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx, const double* A,
+                       int32_t asize, const double* V, const double* P, const double* fp,
+                       int64_t fes);
+/* Serialize the whole state (arrays + counters) into buf; *size in: buffer
+ * capacity, out: bytes needed/written.  buf == NULL queries the size.
+ * Because every draw is counter-based, load + the same counters resumes the
+ * run bit-for-bit. */
+int32_t sevo_state_save(const sevo_state* s, void* buf, size_t* size);
+int32_t sevo_state_load(sevo_state* s, const void* buf, size_t size);
+
+/* ---- experiment grid (Sec. 2.4, Listing 3: evo_bench over runs) -------- */
+typedef struct {
+  int32_t problem;    /* index into sevo_grid.problems */
+  int32_t alg;        /* index into sevo_grid.algs     */
+  uint64_t seed;      /* run seed (Philox key)         */
+} sevo_task;
+
+typedef struct {
+  int32_t nproblems;
+  const sevo_problem* const* problems;
+  int32_t nalgs;
+  const sevo_alg_params* algs;
+  int32_t ntasks;
+  const sevo_task* tasks;
+  int32_t gens_per_graph;  /* generations captured per CUDA graph (0 = auto) */
+} sevo_grid;
+
+typedef struct {          /* caller-allocated host arrays, ntasks entries each */
+  double* best;           /* best-so-far error (FP64)                          */
+  int64_t* fes;           /* evaluations counted (== budget)                   */
+  int64_t* gens;          /* generations after the initial one                 */
+  int32_t* success;       /* best <= SEVO_SUCCESS_THRESHOLD                     */
+  double wall_ms;         /* device wall time of the whole grid                */
+  int64_t evals;          /* total evaluations performed                        */
+} sevo_grid_result;
+
+/* Run every task to its budget.  Tasks with equal (alg kind, D, NP, budget,
+ * prec) advance together: one batched launch per kernel per generation over
+ * all their runs, generations captured into CUDA graphs.  Results equal the
+ * single-run state API's for the same (problem, alg, seed).  Synchronous. */
+int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

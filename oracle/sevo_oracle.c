@@ -175,6 +175,54 @@ static double body_impl(int family, const double* z, int n, double* scale) {
   return g;
 }
 
+/* First-order sensitivity of a body to absolute errors in z:
+ * sum_i |d body / d z_i| * za_i, where za_i = sum_j |M_ij d_j| bounds how
+ * much a rounding of z_i can move it (used only to state tolerances). */
+static double body_sens(int family, const double* z, const double* za, int n) {
+  double S = 0.0;
+  if (n <= 0) return 0.0;
+  switch (family) {
+    case ORC_ELLIPSOID:
+      for (int i = 1; i <= n; ++i) {
+        double coef = (n > 1) ? pow(10.0, 6.0 * (double)(i - 1) / (double)(n - 1)) : 1.0;
+        S += 2.0 * coef * fabs(z[i - 1]) * za[i - 1];
+      }
+      break;
+    case ORC_ROSENBROCK:
+      for (int i = 0; i + 1 < n; ++i) {
+        double yi = z[i] + 1.0, yn = z[i + 1] + 1.0, a = yi * yi - yn;
+        S += (fabs(400.0 * yi * a) + fabs(2.0 * (yi - 1.0))) * za[i] + fabs(200.0 * a) * za[i + 1];
+      }
+      break;
+    case ORC_RASTRIGIN:
+      for (int i = 0; i < n; ++i)
+        S += (2.0 * fabs(z[i]) + 20.0 * ORC_PI * fabs(sin(ORC_TWO_PI * z[i]))) * za[i];
+      break;
+    case ORC_SCHWEFEL: {
+      double s = schwefel_s();
+      for (int i = 0; i < n; ++i) {
+        double ay = fabs(z[i] + s), r = sqrt(ay);
+        double dv = (ay <= 500.0) ? fabs(sin(r)) + 0.5 * r * fabs(cos(r)) : 2e-4 * (ay - 500.0);
+        S += dv * za[i];
+      }
+      break;
+    }
+    case ORC_ACKLEY: {
+      double sq = 0.0;
+      for (int i = 0; i < n; ++i) sq += z[i] * z[i];
+      double r = sqrt(sq / (double)n) + 1e-300;
+      for (int i = 0; i < n; ++i)
+        S += (4.0 * fabs(z[i]) / ((double)n * r) + ORC_TWO_PI * 3.0 / (double)n) * za[i];
+      break;
+    }
+    case ORC_GRIEWANK:
+      for (int i = 1; i <= n; ++i)
+        S += (fabs(z[i - 1]) / 2000.0 + 1.0 / sqrt((double)i)) * za[i - 1];
+      break;
+  }
+  return S;
+}
+
 double orc_body(int family, const double* z, int n) {
   return body_impl(family, z, n, NULL);
 }
@@ -472,20 +520,39 @@ void orc_transform(const orc_problem* p, int comp, const double* x, double* z) {
   free(d);
 }
 
+/* za_i = sum_j |M_ij (x_j - o_j)| for component comp */
+static void transform_abs(const orc_problem* p, int comp, const double* x, double* za) {
+  int D = p->D;
+  const double* o = p->o + (size_t)comp * D;
+  const double* M = p->M + (size_t)comp * D * D;
+  for (int i = 0; i < D; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < D; ++j) acc += fabs(M[(size_t)i * D + j] * (x[j] - o[j]));
+    za[i] = acc;
+  }
+}
+
 static double eval_impl(const orc_problem* p, const double* x, double* scale) {
   int D = p->D;
   double* z = (double*)malloc(sizeof(double) * D);
+  double* za = scale ? (double*)malloc(sizeof(double) * D) : NULL;
   double g = 0.0, S = 0.0;
   if (p->family <= ORC_GRIEWANK) {
     orc_transform(p, 0, x, z);
     g = body_impl(p->family, z, D, &S);
+    if (za) {
+      transform_abs(p, 0, x, za);
+      S += body_sens(p->family, z, za, D);
+    }
   } else if (p->family == ORC_HYBRID) {
     orc_transform(p, 0, x, z); /* rows already permuted: z' = P M d */
+    if (za) transform_abs(p, 0, x, za);
     int start = 0;
     for (int k = 0; k < p->K; ++k) {
       double sk = 0.0;
       g += body_impl(p->gbody[k], z + start, p->gsize[k], &sk);
       S += sk;
+      if (za) S += body_sens(p->gbody[k], z + start, za + start, p->gsize[k]);
       start += p->gsize[k];
     }
   } else {
@@ -502,6 +569,10 @@ static double eval_impl(const orc_problem* p, const double* x, double* scale) {
       sc[c] = s;
       orc_transform(p, c, x, z);
       gc[c] = body_impl(p->gbody[c], z, D, &Sc[c]);
+      if (za) {
+        transform_abs(p, c, x, za);
+        Sc[c] += body_sens(p->gbody[c], z, za, D);
+      }
       if (s == 0.0 && exact < 0) exact = c;
     }
     if (exact >= 0) {
@@ -521,6 +592,7 @@ static double eval_impl(const orc_problem* p, const double* x, double* scale) {
     }
   }
   free(z);
+  free(za);
   if (scale) *scale = S;
   return g;
 }

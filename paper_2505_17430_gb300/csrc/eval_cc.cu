@@ -1,0 +1,284 @@
+// eval_cc.cu -- CUDA-core evaluation kernels.
+//
+//   T = double : the plain FP64 GPU path (DFMA rotation, FP64 bodies); also
+//                the FP64 refinement of rows listed by a mixed pass.
+//   T = float  : FP32 CUDA-core rotation with FP32 bodies (the small-D mixed
+//                path); rows below the refinement threshold are listed.
+//
+// Work split: a CTA of 256 threads takes a tile of 8 rows.  For each chunk of
+// 256 outputs i, thread i accumulates z_i for the 8 rows over 256-wide input
+// chunks of d = x - o staged in shared memory (M read as M^T, coalesced).
+// Warp r then reduces the chunk's body terms of row r group by group in a
+// fixed shuffle order (deterministic), carrying the Rosenbrock pair across
+// chunk borders.
+#include "bodies.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int TR = 8;    // rows per tile (one warp each in the epilogue)
+constexpr int NT = 256;  // threads
+constexpr int CH = 256;  // chunk width (outputs and inputs)
+
+template <typename T>
+struct AccT;
+template <>
+struct AccT<double> {
+  using type = Acc64;
+};
+template <>
+struct AccT<float> {
+  using type = Acc32;
+};
+
+__device__ __forceinline__ void acc_init(int body, Acc64& a) { acc64_init(body, a); }
+__device__ __forceinline__ void acc_init(int, Acc32& a) { acc32_init(a); }
+
+__device__ __forceinline__ void term(int body, double z, double aux, bool hn, double zn,
+                                     const ProblemDev& P, Acc64& a) {
+  term64(body, z, aux, hn, zn, P, a);
+}
+__device__ __forceinline__ void term(int body, float z, float aux, bool hn, float zn,
+                                     const ProblemDev& P, Acc32& a) {
+  term32(body, z, aux, hn, zn, P, a);
+}
+
+__device__ __forceinline__ void combine(int body, Acc64& a, const Acc64& b) {
+  a.a0 += b.a0;
+  if (slot1_is_product64(body))
+    a.a1 *= b.a1;
+  else
+    a.a1 += b.a1;
+  a.a2 += b.a2;
+}
+__device__ __forceinline__ void combine(int, Acc32& a, const Acc32& b) {
+  a.a0 += b.a0;
+  a.a1 += b.a1;
+  a.a2 += b.a2;
+}
+
+template <typename A>
+__device__ __forceinline__ void warp_reduce(int body, A& a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    A b;
+    b.a0 = __shfl_xor_sync(0xffffffffu, a.a0, m);
+    b.a1 = __shfl_xor_sync(0xffffffffu, a.a1, m);
+    b.a2 = __shfl_xor_sync(0xffffffffu, a.a2, m);
+    combine(body, a, b);
+  }
+}
+
+__device__ __forceinline__ double finalize(int body, const Acc64& a, int n) {
+  return finalize64(body, a, n);
+}
+__device__ __forceinline__ double finalize(int body, const Acc32& a, int n) {
+  return (double)finalize32(body, a, n);
+}
+
+template <typename T>
+__device__ __forceinline__ const T* mt_ptr(const ProblemDev& P, int c);
+template <>
+__device__ __forceinline__ const double* mt_ptr<double>(const ProblemDev& P, int c) {
+  return P.MT64[c];
+}
+template <>
+__device__ __forceinline__ const float* mt_ptr<float>(const ProblemDev& P, int c) {
+  return P.MT32[c];
+}
+__device__ __forceinline__ double aux_of(const ProblemDev& P, int c, int i, double) {
+  return P.aux64[c][i];
+}
+__device__ __forceinline__ float aux_of(const ProblemDev& P, int c, int i, float) {
+  return P.aux32[c][i];
+}
+
+template <typename T, bool LIST>
+__global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restrict__ Pg,
+                                                     const double* __restrict__ X, int64_t ld,
+                                                     int64_t N, const int32_t* __restrict__ list,
+                                                     const int32_t* __restrict__ list_count,
+                                                     double* __restrict__ out, EvalAux aux) {
+  using Acc = typename AccT<T>::type;
+  __shared__ ProblemDev P;
+  __shared__ T dS[TR][CH];
+  __shared__ T zS[TR][CH + 1];
+  __shared__ Acc tot[TR][SV_MAXG];
+  __shared__ T prevz[TR];
+  __shared__ int64_t rowS[TR];
+  __shared__ double gS[TR][SV_MAXC];
+  __shared__ double sS[TR][SV_MAXC];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const int* src = (const int*)Pg;
+    int* dst = (int*)&P;
+    for (int k = tid; k < (int)(sizeof(ProblemDev) / 4); k += NT) dst[k] = src[k];
+  }
+  __syncthreads();
+  // c = s sin sqrt s with the same device sin as the terms, so that the
+  // Schwefel term is exactly 0 at z = 0
+  if (tid == 0) P.sch_c = P.sch_s * sin(sqrt(P.sch_s));
+  __syncthreads();
+  const int D = P.D;
+  const int nchunks = (D + CH - 1) / CH;
+  const int64_t total = LIST ? (int64_t)(*list_count) : N;
+
+  for (int64_t tile = blockIdx.x; tile * TR < total; tile += gridDim.x) {
+    __syncthreads();
+    if (tid < TR) {
+      int64_t k = tile * TR + tid;
+      rowS[tid] = (k < total) ? (LIST ? (int64_t)list[k] : k) : -1;
+    }
+    __syncthreads();
+    for (int c = 0; c < P.ncomp; ++c) {
+      const double* __restrict__ o = P.o[c];
+      const T* __restrict__ MT = mt_ptr<T>(P, c);
+      const int32_t* __restrict__ gid = P.gid[c];
+      const int ng = P.ngroups;
+      if (tid < TR * SV_MAXG) {
+        int r = tid / SV_MAXG, g = tid % SV_MAXG;
+        int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+        acc_init(body, tot[r][g]);
+      }
+      // composition distance s_c = |x - o_c|^2 in FP64 (warp r, row r)
+      if (P.family == SEVO_COMPOSITION) {
+        int64_t row = rowS[warp];
+        double s = 0.0;
+        if (row >= 0)
+          for (int j = lane; j < D; j += 32) {
+            double dv = X[row * ld + j] - o[j];
+            s += dv * dv;
+          }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+        if (lane == 0) sS[warp][c] = s;
+      }
+      for (int ic = 0; ic < nchunks; ++ic) {
+        const int i = ic * CH + tid;
+        T accz[TR];
+#pragma unroll
+        for (int r = 0; r < TR; ++r) accz[r] = T(0);
+        for (int jc = 0; jc < nchunks; ++jc) {
+          __syncthreads();
+          const int j = jc * CH + tid;
+#pragma unroll
+          for (int r = 0; r < TR; ++r) {
+            int64_t row = rowS[r];
+            double dv = 0.0;
+            if (row >= 0 && j < D) dv = X[row * ld + j] - o[j];
+            dS[r][tid] = (T)dv;
+          }
+          __syncthreads();
+          if (i < D) {
+            const int jn = min(CH, D - jc * CH);
+            const T* mcol = MT + (size_t)(jc * CH) * D + i;
+            for (int jj = 0; jj < jn; ++jj) {
+              const T m = mcol[(size_t)jj * D];
+#pragma unroll
+              for (int r = 0; r < TR; ++r) accz[r] = fma(m, dS[r][jj], accz[r]);
+            }
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < TR; ++r) zS[r][tid] = accz[r];
+        __syncthreads();
+        // epilogue: warp r reduces row r's terms of this chunk
+        const int r = warp;
+        if (rowS[r] >= 0) {
+          const int c0 = ic * CH, c1 = min(D, c0 + CH);
+          if (ic > 0 && lane == 0) {  // Rosenbrock pair across the chunk border
+            const int ip = c0 - 1, g = gid[ip];
+            const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+            if (body == SEVO_ROSENBROCK && ip + 1 < P.gstart[g + 1]) {
+              Acc a;
+              acc_init(body, a);
+              term(body, prevz[r], T(0), true, zS[r][0], P, a);
+              combine(body, tot[r][g], a);
+            }
+          }
+          for (int g = 0; g < ng; ++g) {
+            const int lo = max(c0, P.gstart[g]), hi = min(c1, P.gstart[g + 1]);
+            if (lo >= hi) continue;
+            const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+            Acc a;
+            acc_init(body, a);
+            for (int e = lo + lane; e < hi; e += 32) {
+              const T z = zS[r][e - c0];
+              const bool hn = (e + 1 < P.gstart[g + 1]);
+              if (hn && e + 1 >= c1) continue;  // pair finished in the next chunk
+              const T zn = hn ? zS[r][e + 1 - c0] : T(0);
+              term(body, z, aux_of(P, c, e, T(0)), hn, zn, P, a);
+            }
+            warp_reduce(body, a);
+            if (lane == 0) combine(body, tot[r][g], a);
+          }
+          if (lane == 0) prevz[r] = zS[r][c1 - 1 - c0];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      if (lane == 0 && rowS[warp] >= 0) {
+        double gsum = 0.0;
+        for (int g = 0; g < ng; ++g) {
+          const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+          gsum += finalize(body, tot[warp][g], P.gstart[g + 1] - P.gstart[g]);
+        }
+        gS[warp][c] = gsum;
+      }
+      __syncthreads();
+    }
+    if (lane == 0 && rowS[warp] >= 0) {
+      const int64_t row = rowS[warp];
+      double err = (P.family == SEVO_COMPOSITION) ? compose(P, sS[warp], gS[warp]) : gS[warp][0];
+      if (!isfinite(err)) {
+        err = __longlong_as_double(0x7ff8000000000000ll);
+        if (aux.nonfinite) atomicAdd(aux.nonfinite, 1u);
+      } else if (!std::is_same<T, double>::value && aux.refine_list && err < SEVO_REFINE_THRESHOLD) {
+        int k = atomicAdd(aux.refine_count, 1);
+        aux.refine_list[k] = (int32_t)row;
+      }
+      out[row] = err;
+    }
+  }
+}
+
+}  // namespace
+
+int sv_num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t N,
+                       double* out, EvalAux aux, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  int64_t tiles = (N + TR - 1) / TR;
+  int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 8);
+  if (prec == SEVO_FP64)
+    eval_cc_kernel<double, false><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, N, nullptr, nullptr,
+                                                                  out, aux);
+  else
+    eval_cc_kernel<float, false><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, N, nullptr, nullptr,
+                                                                 out, aux);
+  return cudaGetLastError();
+}
+
+cudaError_t sv_eval_refine(const ProblemDev* Pd, const double* X, int64_t ld, int64_t Nmax,
+                           const int32_t* list, const int32_t* count, double* out,
+                           cudaStream_t st) {
+  if (Nmax <= 0) return cudaSuccess;
+  int64_t tiles = (Nmax + TR - 1) / TR;
+  int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 4);
+  EvalAux none{};
+  eval_cc_kernel<double, true><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, Nmax, list, count, out,
+                                                               none);
+  return cudaGetLastError();
+}

@@ -1,0 +1,129 @@
+// sevo_internal.cuh -- types and helpers shared by the library's translation
+// units (host and device).  Nothing here is shared with the CPU oracle.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/sevo.h"
+
+#define SV_MAXG SEVO_MAX_GROUPS
+#define SV_MAXC SEVO_MAX_COMPONENTS
+
+// Philox purposes: high byte of counter word 3 (the low 24 bits carry a salt,
+// the component index for instance data).
+enum : uint32_t {
+  SV_P_INIT = 1, SV_P_PART = 2, SV_P_CROSS = 3, SV_P_ARCH = 4, SV_P_PSO = 5,
+  SV_P_SHIFT = 16, SV_P_ROT = 17, SV_P_PERM = 18, SV_P_HYB = 19, SV_P_COMP = 20
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds; each round multiplies
+// words 0 and 2 by 0xD2511F53 / 0xCD9E8D57 (64-bit products split hi/lo),
+// xors the high halves into words 1 and 3 with the key, and the key advances
+// by 0x9E3779B9 / 0xBB67AE85 after every round.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t sv_mulhi(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 sv_philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = sv_mulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = sv_mulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// draw(seed; c0, c1, c2, purpose, salt)
+__host__ __device__ __forceinline__ uint4 sv_draw(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                  uint32_t c2, uint32_t purpose,
+                                                  uint32_t salt = 0) {
+  return sv_philox(make_uint4(c0, c1, c2, (purpose << 24) | (salt & 0xFFFFFFu)),
+                   (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// 53-bit uniform in [0,1) from two words (27 + 26 high bits), exact.
+__host__ __device__ __forceinline__ double sv_u53(uint32_t w0, uint32_t w1) {
+  const uint64_t m = ((uint64_t)(w0 >> 5) << 26) | (uint64_t)(w1 >> 6);
+#ifdef __CUDA_ARCH__
+  return __ull2double_rn(m) * 0x1p-53;
+#else
+  return (double)m * 0x1p-53;
+#endif
+}
+
+// integer in [0,n): high word of w*n
+__host__ __device__ __forceinline__ uint32_t sv_below(uint32_t w, uint32_t n) {
+  return sv_mulhi(w, n);
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident instance descriptor.  A single-family instance is one
+// component with one group; a hybrid is one component with K groups; a
+// composition is Nc components of one group each.
+// ---------------------------------------------------------------------------
+struct ProblemDev {
+  int32_t family, D, ncomp, ngroups;
+  int32_t kpad;   // K (input) extent padded for the tensor-core operands
+  int32_t npad;   // N (output) extent padded for the tensor-core operands
+  double fstar;
+  double sch_s, sch_c;                  // Schwefel shift s and c = s sin sqrt s
+  float sch_s32, sch_B32, sch_sinB32, sch_cosB32, sch_h032, sch_c32;
+  const double* o[SV_MAXC];             // D
+  const double* MT64[SV_MAXC];          // D x D, MT[j*D+i] = M_ij
+  const float* MT32[SV_MAXC];           // D x D, FP32 copy of MT
+  const float* M32[SV_MAXC];            // npad x kpad row-major, TF32-rounded, zero pad
+  const __nv_bfloat16* Mhi[SV_MAXC];    // npad x kpad
+  const __nv_bfloat16* Mlo[SV_MAXC];    // npad x kpad
+  const double* aux64[SV_MAXC];         // D: ellipsoid coefficient or sqrt(position)
+  const float* aux32[SV_MAXC];
+  const int32_t* gid[SV_MAXC];          // D: group index of output coordinate i
+  int32_t gstart[SV_MAXG + 1];          // group ranges [gstart[g], gstart[g+1])
+  int32_t gbody[SV_MAXG];
+  int32_t cbody[SV_MAXC];
+  double sigma[SV_MAXC], lambda[SV_MAXC], bias[SV_MAXC];
+};
+
+struct sevo_problem {
+  int32_t family, D, ncomp, ngroups, device;
+  double fstar;
+  // host copies
+  double* o_h;      // ncomp x D
+  double* M_h;      // ncomp x D x D (row-major; hybrid rows permuted)
+  int32_t* perm_h;  // D (hybrid)
+  int32_t gsize[SV_MAXG], gbody[SV_MAXG];
+  int32_t cbody[SV_MAXC];
+  double sigma[SV_MAXC], lambda[SV_MAXC], bias[SV_MAXC];
+  // device
+  ProblemDev host_desc;   // descriptor with device pointers (host copy)
+  ProblemDev* desc_d;     // same, in device memory
+  void* dev_block;        // one allocation holding all device arrays
+  size_t dev_bytes;
+};
+
+// status helpers --------------------------------------------------------
+#define SV_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) {                              \
+      sv_set_last_cuda_error(_e);                         \
+      return _e == cudaErrorMemoryAllocation ? SEVO_ERR_OOM : SEVO_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+
+void sv_set_last_cuda_error(cudaError_t e);
+// upload the instance to the current device on first use (thread-safe);
+// SEVO_ERR_STATE if it already lives on another device
+int32_t sv_problem_ready(const sevo_problem* p);
+
+// error flags set by device code (bitmask in a device word)
+enum : uint32_t { SV_DEVERR_TIMEOUT = 1u, SV_DEVERR_BOUNDS = 2u, SV_DEVERR_NAN = 4u };

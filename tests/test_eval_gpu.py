@@ -1,0 +1,129 @@
+"""GPU parity of sevo_evaluate against the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+from tests.gpu_util import to_dev, tol64
+
+pytestmark = pytest.mark.gpu
+
+FAMS = list(range(8))
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2505_17430_gb300 as S
+    S.build()
+    return S
+
+
+def _inputs(q, N, D, seed):
+    X = inputs.uniform_pop(N, D, seed=seed)
+    o = q.shift(0)
+    near = inputs.near(o, 6, 1e-3, seed=seed + 1)
+    tiny = inputs.near(o, 3, 1e-7, seed=seed + 2)
+    return np.vstack([X, near, tiny, o[None, :]])
+
+
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("D", [2, 10, 30, 100, 257])
+def test_fp64_path_matches_oracle(S, fam, D):
+    """FP64 GPU path: |f_gpu - f_oracle| <= 1e-12 * max(|f|, S(x)) on random,
+    near-optimum and optimum rows; 37+10 rows span several 8-row tiles and a
+    ragged tail; D = 257 spans two 256-wide chunks (Rosenbrock carry)."""
+    seed = 1000 + 17 * fam + D
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = _inputs(q, 37, D, seed)
+    got = p.evaluate(to_dev(X), prec=S.FP64).cpu().numpy()
+    want = q.eval(X)
+    scale = q.scale(X)
+    err = np.abs(got - want)
+    assert (err <= tol64(want, scale)).all(), (err / np.maximum(np.abs(want), scale)).max()
+    assert got[-1] == 0.0  # f(o) = f* exactly
+
+
+@pytest.mark.parametrize("fam", FAMS)
+def test_fp64_path_d1000_sampled(S, fam):
+    D = 1000
+    seed = 77 + fam
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = _inputs(q, 20, D, seed)
+    got = p.evaluate(to_dev(X), prec=S.FP64).cpu().numpy()
+    want = q.eval(X)
+    assert (np.abs(got - want) <= tol64(want, q.scale(X))).all()
+
+
+@pytest.mark.parametrize("prec", ["FP32"])
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("D", [10, 100])
+def test_mixed_path_refines_and_tracks_oracle(S, prec, fam, D):
+    """Mixed path: rows whose mixed error is below 1e-4 come back from the
+    FP64 path (FP64 tolerance); all other rows are within the mixed
+    tolerance 2e-3 * max(|f|, S) of the oracle."""
+    seed = 555 + fam + D
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = np.vstack([_inputs(q, 40, D, seed), inputs.mixed_scales(q.shift(0), 40, D, seed)])
+    pm = getattr(S, prec)
+    got, info = p.evaluate(to_dev(X), prec=pm, sync=True)
+    got = got.cpu().numpy()
+    want, scale = q.eval(X), q.scale(X)
+    small = want < 0.5e-4
+    assert info["refined"] >= small.sum()
+    assert (np.abs(got - want)[small] <= tol64(want, scale)[small]).all()
+    assert (np.abs(got - want) <= 2e-3 * np.maximum(np.abs(want), scale) + 1e-12).all()
+
+
+def test_nonfinite_rows_reported(S):
+    p = S.Problem(3, S.RASTRIGIN, 20)
+    X = inputs.uniform_pop(16, 20, seed=3)
+    X[5, 7] = np.nan
+    X[9, 0] = np.inf
+    for prec in (S.FP64, S.FP32):
+        out, info = p.evaluate(to_dev(X), prec=prec, sync=True)
+        out = out.cpu().numpy()
+        assert np.isnan(out[5]) and np.isnan(out[9])
+        assert np.isfinite(np.delete(out, [5, 9])).all()
+        assert info["nonfinite"] == 2 and info["status"] == -5
+
+
+def test_empty_and_bad_args(S):
+    import ctypes as C
+    import torch
+    p = S.Problem(3, S.ACKLEY, 10)
+    X = torch.zeros((0, 10), dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lib = S.lib()
+    assert lib.sevo_evaluate(p.h, C.c_void_p(out.data_ptr()), 0, 10, 10,
+                             C.c_void_p(out.data_ptr()), 0, None) == 0
+    assert lib.sevo_evaluate(p.h, C.c_void_p(out.data_ptr()), 1, 11, 11,
+                             C.c_void_p(out.data_ptr()), 0, None) == -1  # wrong D
+    assert lib.sevo_evaluate(p.h, C.c_void_p(out.data_ptr()), 1, 10, 9,
+                             C.c_void_p(out.data_ptr()), 0, None) == -1  # ld < D
+
+
+def test_leading_dimension(S):
+    p, q = S.Problem(9, S.GRIEWANK, 30), O.Problem(9, S.GRIEWANK, 30)
+    X = inputs.uniform_pop(20, 30, seed=9)
+    Xp = np.zeros((20, 34))
+    Xp[:, :30] = X
+    Xp[:, 30:] = np.nan  # padding must never be read
+    import torch
+    xt = to_dev(Xp)
+    got = p.evaluate(xt[:, :30], prec=S.FP64).cpu().numpy()
+    assert np.allclose(got, q.eval(X), rtol=1e-12, atol=0)
+
+
+def test_bench_shape_sampled(S):
+    """N = 4096, D = 100 (the batched-evaluation workload), 6 families; 64
+    sampled rows compared with the oracle for FP64 and every mixed mode."""
+    X = inputs.uniform_pop(4096, 100, seed=12345)
+    rows = np.random.default_rng(0).choice(4096, 64, replace=False)
+    xt = to_dev(X)
+    for fam in range(6):
+        p, q = S.Problem(0x5EB00000 + fam, fam, 100), O.Problem(0x5EB00000 + fam, fam, 100)
+        want, scale = q.eval(X[rows]), q.scale(X[rows])
+        got = p.evaluate(xt, prec=S.FP64).cpu().numpy()[rows]
+        assert (np.abs(got - want) <= tol64(want, scale)).all()
+        got = p.evaluate(xt, prec=S.FP32).cpu().numpy()[rows]
+        assert (np.abs(got - want) <= 2e-3 * np.maximum(want, scale)).all()
