@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched evolutionary hot path (one JSON line on stdout).
+
+Workload (the batched-evaluation configuration, N = 4096 individuals x
+D = 100 on six seeded shifted-rotated families: ellipsoid (1e6 conditioning),
+Rosenbrock, Rastrigin, Schwefel, Ackley, Griewank): three batched run states
+-- DE/rand/1/bin, DE/current-to-pbest/1/bin with archive, inertia PSO with
+ring topology -- each holding one population of NP = 4096 per family.
+One step = one generation of all three states: Philox draws, trial /
+velocity update, crossover and repair, TF32 tensor-core evaluation with FP64
+refinement below 1e-4, selection / archive / pbest and guides.  Evaluations
+per step: 3 x 6 x 4096 = 73,728.  Inputs are synthetic (seeded uniform
+initial populations), resident in HBM; the working set (X, trials, archive,
+velocities, pbest: ~160 MB) exceeds the 129 MB L2, so every step streams
+from HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica with its own seeds
+(runs are independent: weak scaling, no collective on the data path); the
+step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fitness evals/s at D=100/1000, mixed vs FP64 GPU; run-grid wall time vs oracle"
+D, NP, FAMILIES = 100, 4096, 6
+ALGS = [("de_rand1_bin", 0), ("de_ctpb1_bin_archive", 1), ("pso_ring", 3)]
+WORKLOAD = "batched evaluation N=4096 x D=100, 6 shifted-rotated families, one DE/rand/1 + DE/ctpb/1 + PSO-ring generation per step"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- our arm
+def make_states(S, prec, seed0, torch):
+    probs = [S.Problem(0x5EB00000 + f, f, D) for f in range(FAMILIES)]
+    states = []
+    for k, (name, alg) in enumerate(ALGS):
+        params = S.alg_params(alg, NP, 10 ** 12, prec=prec)
+        seeds = [seed0 + 1000 * k + f for f in range(FAMILIES)]
+        states.append(S.State(probs, params, seeds))
+    torch.cuda.synchronize()
+    return probs, states
+
+
+def run_steps(states, first_gen, n):
+    for g in range(first_gen, first_gen + n):
+        for st in states:
+            rc = st.step(g)
+            if rc != 0:
+                raise RuntimeError(f"step failed: {rc}")
+    return first_gen + n
+
+
+def time_steps(torch, states, gen, K):
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    gen = run_steps(states, gen, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), gen
+
+
+def eval_kernel_roofline(S, torch, probs, peaks):
+    """Dominant kernel: the fused tcgen05 evaluation.  One launch over a
+    population of 73,728 rows (the step's row count) of one problem; the
+    algorithmic bytes are the FP64 rows read (D * 8) plus the FP64 result
+    written (8) per row."""
+    rows = len(ALGS) * FAMILIES * NP
+    X = torch.empty((rows, D), dtype=torch.float64, device="cuda").uniform_(-100, 100)
+    out = torch.empty(rows, dtype=torch.float64, device="cuda")
+    p = probs[2]
+    for _ in range(5):
+        p.evaluate(X, out, prec=S.TF32)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        p.evaluate(X, out, prec=S.TF32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    algo_bytes = rows * (D * 8 + 8)
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "eval_tc_fused_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            t = json.load(open(tpath))
+            if t.get("rows") and t.get("bytes"):
+                traffic = t["bytes"] / t["rows"] * rows
+        except Exception:
+            traffic = None
+    return {"kernel": "eval_tc_fused<tf32>", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if peak else None,
+            "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
+            "launch_ms": round(ms, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
+            if peak else "fallback"}
+
+
+def mode_eval_rates(S, torch, probs):
+    """Evaluation-only throughput per precision mode on the step's rows."""
+    rows = FAMILIES * NP
+    X = torch.empty((rows, D), dtype=torch.float64, device="cuda").uniform_(-100, 100)
+    out = torch.empty(rows, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in (("fp64", S.FP64), ("fp32", S.FP32), ("tf32", S.TF32),
+                       ("bf16x3", S.BF16X3)):
+        reps = 2 if prec == S.FP64 else 10
+        for p in probs:
+            p.evaluate(X, out, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for p in probs:
+                p.evaluate(X, out, prec=prec)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        res[name] = round(rows * len(probs) / dt, 1)
+    return res
+
+
+def e2e_rate(S, torch, states, gen, K):
+    """Same step through the C ABI with host buffers: pinned host X of all
+    runs copied in, one step, fitness copied out; copies inside the timing."""
+    import numpy as np
+    rows = [st.R * NP for st in states]
+    hostX = [torch.empty((r, D), dtype=torch.float64).pin_memory() for r in rows]
+    hostF = [np.zeros(r) for r in rows]
+    for st, hx in zip(states, hostX):
+        hx.copy_(torch.from_numpy(st.get()["X"]))
+    lib = S.lib()
+    import ctypes as C
+    dp = C.POINTER(C.c_double)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in range(gen, gen + K):
+        for st, hx, hf in zip(states, hostX, hostF):
+            S.check(lib.sevo_state_set(st.h, C.cast(C.c_void_p(hx.data_ptr()), dp), None, None, 0,
+                                       None, None, None, -1), "sevo_state_set")
+            S.check(st.step(g), "step")
+            S.check(lib.sevo_state_get(st.h, None, hf.ctypes.data_as(dp), None, None, None, None,
+                                       None, None, None, None), "sevo_state_get")
+    dt = (time.perf_counter() - t0) / K
+    evals = sum(rows)
+    return {"value": round(evals / dt, 1), "unit": "evals/s",
+            "h2d_bytes_per_step": sum(r * D * 8 for r in rows),
+            "d2h_bytes_per_step": sum(r * 8 for r in rows)}, gen + K
+
+
+# ---------------------------------------------------------------- oracle arm
+class OracleStep:
+    """The oracle's own operators on a bounded sample of the workload: the
+    same three algorithms x six families at D = 100 with NP = npop."""
+
+    def __init__(self, npop, seed0=1):
+        import numpy as np
+        import oracle as O
+        self.O, self.np = O, np
+        self.npop = npop
+        self.probs = [O.Problem(0x5EB00000 + f, f, D) for f in range(FAMILIES)]
+        self.st = []
+        for k, (_, alg) in enumerate(ALGS):
+            for f, q in enumerate(self.probs):
+                seed = seed0 + 1000 * k + f
+                X = O.init_population(seed, npop, D)
+                fx = q.eval(X)
+                s = {"alg": alg, "q": q, "seed": seed, "X": X, "fx": fx,
+                     "A": np.zeros((npop, D)), "asize": 0}
+                if alg >= 2:
+                    s.update(V=np.zeros_like(X), P=X.copy(), fp=fx.copy(),
+                             guide=O.pso_guides(fx, alg - 2))
+                self.st.append(s)
+        self.gen = 0
+
+    def step(self):
+        O = self.O
+        self.gen += 1
+        g = self.gen
+        for s in self.st:
+            q = s["q"]
+            if s["alg"] == 0:
+                U, _ = O.de_rand1_trials(s["seed"], g, s["X"])
+                fu = q.eval(U)
+                s["X"], s["fx"], _, _, _ = O.de_select(s["seed"], g, s["X"], s["fx"], U, fu)
+            elif s["alg"] == 1:
+                U, _ = O.de_ctpb_trials(s["seed"], g, s["X"], s["fx"], s["A"], s["asize"])
+                fu = q.eval(U)
+                s["X"], s["fx"], s["A"], s["asize"], _ = O.de_select(
+                    s["seed"], g, s["X"], s["fx"], U, fu, s["A"], s["asize"])
+            else:
+                s["X"], s["V"] = O.pso_move(s["seed"], g, s["X"], s["V"], s["P"], s["guide"])
+                s["fx"] = q.eval(s["X"])
+                s["P"], s["fp"], _ = O.pso_update(s["X"], s["fx"], s["P"], s["fp"])
+                s["guide"] = O.pso_guides(s["fp"], s["alg"] - 2)
+        return len(self.st) * self.npop
+
+
+def oracle_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline(npop=NP, steps=30):
+    o = OracleStep(npop)
+    o.step()
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(steps):
+        ev += o.step()
+    dt = time.perf_counter() - t0
+    return {"value": round(ev / dt, 1), "unit": "evals/s", "cores": oracle_cores(),
+            "kind": "oracle",
+            "sample": f"{steps} generations of the 3 algorithms x 6 families at D={D} with "
+                      f"NP={npop} (the workload's operators and evaluation, {ev} evals)"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    npop = NP
+    o = OracleStep(npop)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(args.steps):
+        ev += o.step()
+    dt = time.perf_counter() - t0
+    v = ev / dt
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": NP, "D": D, "families": FAMILIES,
+                       "sample_np": npop},
+            "cpu_baseline": {"value": round(v, 1), "unit": "evals/s", "cores": oracle_cores(),
+                             "kind": "oracle",
+                             "sample": f"each step: one generation of the 3 algorithms x 6 "
+                                       f"families at D={D}, NP={npop}"},
+            "e2e": {"value": round(v, 1), "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true",
+                    help="time the steps only (for launch-list profiling)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2505_17430_gb300 as S
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    S.build()
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    if "hbm_gbs" not in peaks:
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+    seed0 = 1 + 100000 * rank
+    probs, states = make_states(S, S.TF32, seed0, torch)
+    gen = run_steps(states, 1, args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = S.lib().sevo_kernel_launches()
+    ms, gen = time_steps(torch, states, gen, args.steps)
+    launches = S.lib().sevo_kernel_launches() - l0
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    evals_per_step = sum(st.R * NP for st in states)
+    ms_per_step = ms / args.steps
+    value = evals_per_step * world / (ms_per_step * 1e-3)
+
+    if rank != 0 or args.only_steps:
+        if args.only_steps and rank == 0:
+            print(json.dumps({"only_steps": True, "value": round(value, 1),
+                              "ms_per_step": round(ms_per_step, 4), "gpu_launches": launches}))
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # FP64 GPU path, same step (plain DFMA rotation, FP64 bodies)
+    _, st64 = make_states(S, S.FP64, seed0, torch)
+    g64 = run_steps(st64, 1, 1)
+    ms64, _ = time_steps(torch, st64, g64, 2)
+    fp64 = {"value": round(evals_per_step / (ms64 / 2 * 1e-3), 1),
+            "ms_per_step": round(ms64 / 2, 3)}
+    del st64
+    e2e, gen = e2e_rate(S, torch, states, gen, max(3, args.steps // 4))
+    roof = eval_kernel_roofline(S, torch, probs, peaks)
+    modes = mode_eval_rates(S, torch, probs)
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": NP, "D": D, "families": FAMILIES,
+                       "algorithms": [a for a, _ in ALGS], "evals_per_step": evals_per_step,
+                       "prec": "tf32 rotation, fp32 bodies, fp64 shift/refine/positions",
+                       "l2": "working set ~160 MB per step > 129 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "fp64_path": fp64, "eval_only_evals_per_s": modes}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -53,6 +53,10 @@ extern "C" {
 const char* sevo_strerror(int32_t status);
 /* library version, e.g. 100 for 0.1.0 */
 int32_t sevo_version(void);
+/* number of CUDA kernels this library has launched in the process so far
+ * (launch accounting for benchmarks; graph replays count the kernels of
+ * every replayed generation) */
+int64_t sevo_kernel_launches(void);
 
 /* ---- problem families and precision modes ----------------------------- */
 enum sevo_family {
@@ -169,6 +173,17 @@ typedef struct sevo_state sevo_state; /* opaque, library-owned */
 int32_t sevo_state_create(const sevo_problem* p, const sevo_alg_params* a, uint64_t seed,
                           void* stream, sevo_state** out);
 int32_t sevo_state_destroy(sevo_state* s);
+
+/* Batched state: R independent runs of the same algorithm in one state,
+ * run r on problems[r] (all of one dimension D) with Philox key seeds[r].
+ * Every step advances all R runs with one launch per kernel; state arrays
+ * in sevo_state_get/set/save become R*NP rows (run-major).  R = 1 is
+ * exactly sevo_state_create. */
+int32_t sevo_state_create_batch(const sevo_problem* const* problems, int32_t R,
+                                const sevo_alg_params* a, const uint64_t* seeds, void* stream,
+                                sevo_state** out);
+/* per-run best-so-far errors (host, R values); synchronizes */
+int32_t sevo_state_best(const sevo_state* s, double* best);
 
 /* One DE generation (DE algorithms only): trials from the Philox stream at
  * counter `philox_counter` (mutation, binomial crossover, midpoint-target

@@ -64,6 +64,10 @@ _vp, _dp, _ip, _i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), 
 SIGNATURES = {
     "sevo_strerror": (C.c_char_p, [C.c_int32]),
     "sevo_version": (C.c_int32, []),
+    "sevo_kernel_launches": (C.c_int64, []),
+    "sevo_state_create_batch": (C.c_int32, [C.POINTER(_vp), C.c_int32, C.POINTER(AlgParams),
+                                            C.POINTER(C.c_uint64), _vp, C.POINTER(_vp)]),
+    "sevo_state_best": (C.c_int32, [_vp, _dp]),
     "sevo_problem_create": (C.c_int32, [C.c_uint64, C.c_int32, C.c_int32, C.POINTER(_vp)]),
     "sevo_hybrid_create": (C.c_int32, [C.c_uint64, C.c_int32, C.c_int32, _dp, _ip,
                                        C.POINTER(_vp)]),
@@ -214,15 +218,34 @@ def alg_params(alg, NP, budget, F=0.5, CR=0.9, p=0.11, w=0.7298, c1=1.49618, c2=
 
 
 class State:
-    """Owns a sevo_state handle: one run's device state."""
+    """Owns a sevo_state handle: one run's device state, or R runs of one
+    algorithm (problems = list, seeds = list) stepping together."""
 
-    def __init__(self, problem: Problem, params: AlgParams, seed: int, stream=None):
+    def __init__(self, problem, params: AlgParams, seed, stream=None):
         h = C.c_void_p()
-        self.problem = problem  # keep alive
         self.params = params
-        check(_lib().sevo_state_create(problem.h, C.byref(params), seed, _stream_ptr(stream),
-                                       C.byref(h)), "sevo_state_create")
+        if isinstance(problem, (list, tuple)):
+            self.problems = list(problem)  # keep alive
+            self.problem = self.problems[0]
+            self.R = len(self.problems)
+            ph = (C.c_void_p * self.R)(*[p.h.value for p in self.problems])
+            sd = (C.c_uint64 * self.R)(*[int(x) for x in seed])
+            check(_lib().sevo_state_create_batch(ph, self.R, C.byref(params), sd,
+                                                 _stream_ptr(stream), C.byref(h)),
+                  "sevo_state_create_batch")
+        else:
+            self.problems = [problem]
+            self.problem = problem
+            self.R = 1
+            check(_lib().sevo_state_create(problem.h, C.byref(params), seed, _stream_ptr(stream),
+                                           C.byref(h)), "sevo_state_create")
         self.h = h
+
+    def best(self):
+        import numpy as np
+        b = np.zeros(self.R)
+        check(_lib().sevo_state_best(self.h, _np_dp(b)), "sevo_state_best")
+        return b
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -249,7 +272,7 @@ class State:
 
     def get(self):
         import numpy as np
-        NP, D = self.params.NP, self.problem.D
+        NP, D = self.params.NP * self.R, self.problem.D
         X, fx, A = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, D))
         V, P, fp = np.zeros((NP, D)), np.zeros((NP, D)), np.zeros(NP)
         U, fu, part = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, 4), np.int32)
@@ -266,7 +289,7 @@ class State:
         X, fx, V, P, fp = c(X), c(fx), c(V), c(P), c(fp)
         Af = None
         if A is not None:
-            Af = np.zeros((self.params.NP, self.problem.D))
+            Af = np.zeros((self.params.NP * self.R, self.problem.D))
             Af[:len(A)] = A
         check(_lib().sevo_state_set(self.h, _np_dp(X), _np_dp(fx), _np_dp(Af), asize, _np_dp(V),
                                     _np_dp(P), _np_dp(fp), fes), "sevo_state_set")

@@ -9,47 +9,74 @@
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t sv_eval_scratch_bytes(const sevo_problem* p, int prec, int64_t N) {
-  size_t b = al256((size_t)N * 4) + al256(16);
-  if (prec == SEVO_TF32 || prec == SEVO_BF16X3) b += al256(sv_eval_tc_scratch_bytes(p, prec, N));
+size_t sv_eval_scratch_bytes(bool any_comp, int prec, int64_t rows) {
+  size_t b = al256((size_t)rows * 4) + al256(SV_COUNTERS_BYTES);
+  if (prec == SEVO_TF32 || prec == SEVO_BF16X3) b += al256(sv_eval_tc_scratch_bytes(any_comp, prec, rows));
   return b;
 }
 
-void sv_eval_scratch_carve(void* base, const sevo_problem* p, int prec, int64_t N,
-                           EvalScratch* s) {
+void sv_eval_scratch_carve(void* base, bool any_comp, int prec, int64_t rows, EvalScratch* s) {
   char* c = (char*)base;
   s->list = (int32_t*)c;
-  c += al256((size_t)N * 4);
+  c += al256((size_t)rows * 4);
   s->counters = (int32_t*)c;
-  c += al256(16);
+  c += al256(SV_COUNTERS_BYTES);
   s->tc = nullptr;
   s->tc_bytes = 0;
   if (prec == SEVO_TF32 || prec == SEVO_BF16X3) {
-    s->tc_bytes = sv_eval_tc_scratch_bytes(p, prec, N);
+    s->tc_bytes = sv_eval_tc_scratch_bytes(any_comp, prec, rows);
     s->tc = s->tc_bytes ? (void*)c : nullptr;
   }
 }
 
-cudaError_t sv_eval_full(const sevo_problem* p, int prec, const double* X, int64_t ld, int64_t N,
-                         double* out, const EvalScratch& s, bool reset_counters,
-                         cudaStream_t st) {
+// one pass: mixed evaluation of every segment, then one FP64 re-evaluation
+// launch over the rows each segment listed (segments are processed in
+// groups of SV_MAX_SEG)
+cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const double* X,
+                             int64_t ld, double* out, const EvalScratch& s, cudaStream_t st) {
   cudaError_t e;
-  if (reset_counters) {
-    e = cudaMemsetAsync(s.counters, 0, 16, st);
+  for (int base = 0; base < nseg; base += SV_MAX_SEG) {
+    const int n = std::min(SV_MAX_SEG, nseg - base);
+    const TcSegment* sg = segs + base;
+    e = cudaMemsetAsync(s.counters, 0, SV_COUNTERS_BYTES, st);
+    if (e != cudaSuccess) return e;
+    uint32_t* nonfinite = (uint32_t*)(s.counters + SV_MAX_SEG);
+    uint32_t* dev_err = (uint32_t*)(s.counters + SV_MAX_SEG + 1);
+    int64_t off[SV_MAX_SEG];
+    int64_t tot = 0;
+    for (int k = 0; k < n; ++k) {
+      off[k] = tot;
+      tot += sg[k].nrows;
+    }
+    if (prec == SEVO_FP64) {
+      for (int k = 0; k < n; ++k) {
+        EvalAux aux{nullptr, nullptr, nonfinite};
+        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP64, X, ld, sg[k].row0, sg[k].nrows, out, aux, st);
+        if (e != cudaSuccess) return e;
+      }
+      continue;
+    }
+    if (prec == SEVO_FP32) {
+      for (int k = 0; k < n; ++k) {
+        EvalAux aux{s.list + off[k], s.counters + k, nonfinite};
+        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP32, X, ld, sg[k].row0, sg[k].nrows, out, aux, st);
+        if (e != cudaSuccess) return e;
+      }
+    } else {
+      e = sv_eval_tc_segments(sg, n, prec, X, ld, out, s.list, off, s.counters, nonfinite, s.tc,
+                              s.tc_bytes, dev_err, st);
+      if (e != cudaSuccess) return e;
+    }
+    RefineTable RT;
+    RT.nseg = n;
+    for (int k = 0; k < n; ++k) {
+      RT.P[k] = sg[k].p->desc_d;
+      RT.list_off[k] = off[k];
+    }
+    e = sv_eval_refine(RT, X, ld, tot, s.list, s.counters, out, st);
     if (e != cudaSuccess) return e;
   }
-  EvalAux aux{s.list, s.counters + 0, (uint32_t*)(s.counters + 1)};
-  if (prec == SEVO_FP64) {
-    aux.refine_list = nullptr;
-    return sv_eval_cc(p->desc_d, SEVO_FP64, X, ld, N, out, aux, st);
-  }
-  if (prec == SEVO_FP32) {
-    e = sv_eval_cc(p->desc_d, SEVO_FP32, X, ld, N, out, aux, st);
-  } else {
-    e = sv_eval_tc(p, prec, X, ld, N, out, aux, s.tc, s.tc_bytes, (uint32_t*)(s.counters + 2), st);
-  }
-  if (e != cudaSuccess) return e;
-  return sv_eval_refine(p->desc_d, X, ld, N, s.list, s.counters + 0, out, st);
+  return cudaSuccess;
 }
 
 static int32_t check_eval_args(const sevo_problem* p, const double* pop, int64_t N, int32_t D,
@@ -74,14 +101,17 @@ static int32_t evaluate_impl(const sevo_problem* p, const double* pop, int64_t N
     return SEVO_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  size_t bytes = sv_eval_scratch_bytes(p, prec, N);
+  const bool comp = (p->family == SEVO_COMPOSITION);
+  size_t bytes = sv_eval_scratch_bytes(comp, prec, N);
   void* base = nullptr;
   SV_CUDA(cudaMallocAsync(&base, bytes, s));
   EvalScratch sc;
-  sv_eval_scratch_carve(base, p, prec, N, &sc);
-  cudaError_t e = sv_eval_full(p, prec, pop, ld, N, out, sc, true, s);
-  int32_t host_c[4] = {0, 0, 0, 0};
-  if (e == cudaSuccess && sync) e = cudaMemcpyAsync(host_c, sc.counters, 16, cudaMemcpyDeviceToHost, s);
+  sv_eval_scratch_carve(base, comp, prec, N, &sc);
+  TcSegment seg{p, 0, N};
+  cudaError_t e = sv_eval_segments(&seg, 1, prec, pop, ld, out, sc, s);
+  int32_t host_c[SV_MAX_SEG + 4] = {0};
+  if (e == cudaSuccess && sync)
+    e = cudaMemcpyAsync(host_c, sc.counters, SV_COUNTERS_BYTES, cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(base, s);
   if (e != cudaSuccess) {
     sv_set_last_cuda_error(e);
@@ -90,9 +120,9 @@ static int32_t evaluate_impl(const sevo_problem* p, const double* pop, int64_t N
   if (sync) {
     SV_CUDA(cudaStreamSynchronize(s));
     if (refined) *refined = host_c[0];
-    if (nonfinite) *nonfinite = (uint32_t)host_c[1];
-    if (host_c[2] & SV_DEVERR_TIMEOUT) return SEVO_ERR_TIMEOUT;
-    if (host_c[1]) return SEVO_ERR_NAN;
+    if (nonfinite) *nonfinite = (uint32_t)host_c[SV_MAX_SEG];
+    if (host_c[SV_MAX_SEG + 1] & SV_DEVERR_TIMEOUT) return SEVO_ERR_TIMEOUT;
+    if (host_c[SV_MAX_SEG]) return SEVO_ERR_NAN;
   }
   return SEVO_OK;
 }

@@ -52,11 +52,13 @@ __device__ __forceinline__ void term64(int body, double z, double aux, bool has_
       break;
     case SEVO_SCHWEFEL: {
       double y = z + P.sch_s, ay = fabs(y);
+      // the product is rounded on its own (no fused multiply-add), as in
+      // c = s sin sqrt s, so the term is exactly 0 at z = 0
       if (ay <= 500.0) {
-        a.a0 += P.sch_c - y * sin(sqrt(ay));
+        a.a0 += P.sch_c - __dmul_rn(y, sin(sqrt(ay)));
       } else {
         double b = (y > 0.0) ? 500.0 : -500.0;
-        a.a0 += P.sch_c - b * sin(sqrt(500.0)) + 1e-4 * (ay - 500.0) * (ay - 500.0);
+        a.a0 += P.sch_c - __dmul_rn(b, sin(sqrt(500.0))) + 1e-4 * (ay - 500.0) * (ay - 500.0);
       }
       break;
     }

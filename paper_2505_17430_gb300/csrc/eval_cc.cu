@@ -93,11 +93,16 @@ __device__ __forceinline__ float aux_of(const ProblemDev& P, int c, int i, float
   return P.aux32[c][i];
 }
 
+// LIST = false: rows row0 .. row0 + N - 1 of one problem (Pg).
+// LIST = true : the rows listed per segment (RT.P[s], list[RT.list_off[s]
+//               + k] for k < counts[s]); a tile never straddles segments.
 template <typename T, bool LIST>
 __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restrict__ Pg,
+                                                     const __grid_constant__ RefineTable RT,
                                                      const double* __restrict__ X, int64_t ld,
-                                                     int64_t N, const int32_t* __restrict__ list,
-                                                     const int32_t* __restrict__ list_count,
+                                                     int64_t row0, int64_t N,
+                                                     const int32_t* __restrict__ list,
+                                                     const int32_t* __restrict__ counts,
                                                      double* __restrict__ out, EvalAux aux) {
   using Acc = typename AccT<T>::type;
   __shared__ ProblemDev P;
@@ -108,27 +113,55 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
   __shared__ int64_t rowS[TR];
   __shared__ double gS[TR][SV_MAXC];
   __shared__ double sS[TR][SV_MAXC];
+  __shared__ int64_t cumS[SV_MAX_SEG + 1];
+  __shared__ int curSeg;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  {
-    const int* src = (const int*)Pg;
+  // load problem descriptor P (and the Schwefel constant with the device sin,
+  // so that the term is exactly 0 at z = 0)
+  auto load_problem = [&](const ProblemDev* src_p) {
+    __syncthreads();
+    const int* src = (const int*)src_p;
     int* dst = (int*)&P;
     for (int k = tid; k < (int)(sizeof(ProblemDev) / 4); k += NT) dst[k] = src[k];
+    __syncthreads();
+    if (tid == 0) P.sch_c = __dmul_rn(P.sch_s, sin(sqrt(P.sch_s)));
+    __syncthreads();
+  };
+  int64_t total_tiles;
+  if (LIST) {
+    if (tid == 0) {
+      cumS[0] = 0;
+      for (int q = 0; q < RT.nseg; ++q) cumS[q + 1] = cumS[q] + (counts[q] + TR - 1) / TR;
+      curSeg = -1;
+    }
+    __syncthreads();
+    total_tiles = cumS[RT.nseg];
+  } else {
+    load_problem(Pg);
+    total_tiles = (N + TR - 1) / TR;
   }
-  __syncthreads();
-  // c = s sin sqrt s with the same device sin as the terms, so that the
-  // Schwefel term is exactly 0 at z = 0
-  if (tid == 0) P.sch_c = P.sch_s * sin(sqrt(P.sch_s));
-  __syncthreads();
-  const int D = P.D;
-  const int nchunks = (D + CH - 1) / CH;
-  const int64_t total = LIST ? (int64_t)(*list_count) : N;
 
-  for (int64_t tile = blockIdx.x; tile * TR < total; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    int seg = 0;
+    if (LIST) {
+      while (seg + 1 < RT.nseg && tile >= cumS[seg + 1]) ++seg;
+      if (seg != curSeg) {
+        load_problem(RT.P[seg]);
+        if (tid == 0) curSeg = seg;
+      }
+    }
+    const int D = P.D;
+    const int nchunks = (D + CH - 1) / CH;
     __syncthreads();
     if (tid < TR) {
-      int64_t k = tile * TR + tid;
-      rowS[tid] = (k < total) ? (LIST ? (int64_t)list[k] : k) : -1;
+      if (LIST) {
+        const int64_t k = (tile - cumS[seg]) * TR + tid;
+        rowS[tid] = (k < counts[seg]) ? (int64_t)list[RT.list_off[seg] + k] : -1;
+      } else {
+        const int64_t k = tile * TR + tid;
+        rowS[tid] = (k < N) ? row0 + k : -1;
+      }
     }
     __syncthreads();
     for (int c = 0; c < P.ncomp; ++c) {
@@ -207,7 +240,9 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
             for (int e = lo + lane; e < hi; e += 32) {
               const T z = zS[r][e - c0];
               const bool hn = (e + 1 < P.gstart[g + 1]);
-              if (hn && e + 1 >= c1) continue;  // pair finished in the next chunk
+              // a Rosenbrock pair that straddles the chunk border is added
+              // when the next chunk is in shared memory
+              if (body == SEVO_ROSENBROCK && hn && e + 1 >= c1) continue;
               const T zn = hn ? zS[r][e + 1 - c0] : T(0);
               term(body, z, aux_of(P, c, e, T(0)), hn, zn, P, a);
             }
@@ -257,28 +292,32 @@ int sv_num_sms() {
   return n;
 }
 
-cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t N,
-                       double* out, EvalAux aux, cudaStream_t st) {
+cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t row0,
+                       int64_t N, double* out, EvalAux aux, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   int64_t tiles = (N + TR - 1) / TR;
   int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 8);
+  RefineTable none{};
   if (prec == SEVO_FP64)
-    eval_cc_kernel<double, false><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, N, nullptr, nullptr,
-                                                                  out, aux);
+    eval_cc_kernel<double, false><<<(unsigned)grid, NT, 0, st>>>(Pd, none, X, ld, row0, N, nullptr,
+                                                                  nullptr, out, aux);
   else
-    eval_cc_kernel<float, false><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, N, nullptr, nullptr,
-                                                                 out, aux);
+    eval_cc_kernel<float, false><<<(unsigned)grid, NT, 0, st>>>(Pd, none, X, ld, row0, N, nullptr,
+                                                                 nullptr, out, aux);
+  sv_note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t sv_eval_refine(const ProblemDev* Pd, const double* X, int64_t ld, int64_t Nmax,
-                           const int32_t* list, const int32_t* count, double* out,
+cudaError_t sv_eval_refine(const RefineTable& T, const double* X, int64_t ld, int64_t max_rows,
+                           const int32_t* list, const int32_t* counts, double* out,
                            cudaStream_t st) {
-  if (Nmax <= 0) return cudaSuccess;
-  int64_t tiles = (Nmax + TR - 1) / TR;
-  int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 4);
+  if (max_rows <= 0 || T.nseg <= 0) return cudaSuccess;
+  // grid-stride over the listed rows: usually few (late in a run) or none
+  int64_t tiles = (max_rows + TR - 1) / TR + T.nseg;
+  int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 2);
   EvalAux none{};
-  eval_cc_kernel<double, true><<<(unsigned)grid, NT, 0, st>>>(Pd, X, ld, Nmax, list, count, out,
-                                                               none);
+  eval_cc_kernel<double, true><<<(unsigned)grid, NT, 0, st>>>(nullptr, T, X, ld, 0, 0, list,
+                                                               counts, out, none);
+  sv_note_launch();
   return cudaGetLastError();
 }

@@ -1,7 +1,658 @@
-// eval_tc.cu -- placeholder until the tcgen05 kernel lands.
+// eval_tc.cu -- tcgen05 evaluation: the rotation z = M (x - o) as a
+// tensor-core GEMM (population x D times D x D) with the function bodies and
+// per-row sums fused into the epilogue (TMEM -> registers, thread = row).
+//
+// Fused-producer kernel (D <= 128: the whole K extent of a 128-row tile fits
+// in shared memory), persistent over a table of segments (runs of rows that
+// share one problem instance), one job = (tile, component):
+//   warps 0-7   epilogue: warp group g (warps 4g..4g+3) owns TMEM accumulator
+//               buffer g and takes every other job; a thread walks its row's
+//               z through TMEM (tcgen05.ld), FP32 bodies with one dispatch per
+//               16 columns, FP64 row error, refinement listing;
+//   warps 8-15  producers: FP64 rows of x (4 rows of loads in flight per
+//               lane), d = x - o formed from a float hi/lo split with integer
+//               and FP32 operations only (FP64 throughput on this part is
+//               ~1/70 of FP32), rounded to TF32 (or split to BF16 hi/lo),
+//               written as the 128B-swizzled K-major A tile;
+//   warp 16     TMA loads of the rotation (B operand, reloaded only when the
+//               problem or component changes), tcgen05.mma into the job's
+//               TMEM buffer, TMEM allocation.
+// BF16X3 accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi into the same TMEM.
+// Composition components are written per row (g_c, s_c) and combined by a
+// second small kernel.  Every mbarrier wait is bounded; on a timeout the
+// kernel raises an error bit, stops issuing work and still frees its TMEM.
+#include "bodies.cuh"
 #include "kernels.cuh"
-size_t sv_eval_tc_scratch_bytes(const sevo_problem*, int, int64_t) { return 0; }
-cudaError_t sv_eval_tc(const sevo_problem*, int, const double*, int64_t, int64_t, double*, EvalAux,
-                       void*, size_t, uint32_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int NEPI = 8, NPROD = 8;
+constexpr int WARP_MMA = NEPI + NPROD;
+constexpr int NTHREADS = (NEPI + NPROD + 1) * 32;
+constexpr long long WAIT_BUDGET = 4000000000LL;  // ~2 s of clock64
+constexpr int TCOLS = 128;                      // TMEM columns per accumulator buffer
+constexpr int A_KB_BYTES = BM * 128;            // one 128-byte-wide K block of A
+constexpr int MAX_SEG = 64;
+
+struct Seg {
+  const ProblemDev* P;
+  int64_t row0;      // first row of the segment in X / out
+  int64_t list_off;  // start of the segment's refinement sub-list
+  int32_t nrows;
+  int32_t tile0;     // tiles of all earlier segments
+  int32_t ncomp;
+  int32_t comp;      // composition family
+  int32_t sidx;      // index of the segment's refinement counter
+  int32_t pad;
+};
+
+struct SegTable {
+  int nseg, ntiles, D;
+  Seg seg[MAX_SEG];
+};
+
+struct FusedGeom {
+  int D, kpad, npad;
+  int nkb;         // K blocks per operand copy (tf32: kpad/32, bf16: kpad/64)
+  int ksteps;      // MMA K steps per product
+  int b_kb_bytes;  // npad * 128
+  int a_bytes;     // one A stage (both copies for bf16)
+  int b_bytes;     // resident B (both copies for bf16)
+  uint32_t idesc;
+};
+
+struct __align__(8) Bars {
+  uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], s_full[2];
+  uint64_t b_full, mma_done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ void raise_abort(Bars* bars, uint32_t* dev_err) {
+  bars->abort = 1;
+  if (dev_err) atomicOr(dev_err, SV_DEVERR_TIMEOUT);
+}
+
+// The job sequence of one CTA: tiles blockIdx.x, +gridDim.x, ...; each tile
+// has ncomp(segment) jobs.  Every role walks the same sequence.
+struct JobIter {
+  const SegTable* T;
+  int tile, s, c;
+  __device__ void init(const SegTable* t) {
+    T = t;
+    tile = blockIdx.x;
+    s = 0;
+    c = 0;
+    while (s + 1 < T->nseg && tile >= T->seg[s + 1].tile0) ++s;
+  }
+  __device__ bool valid() const { return tile < T->ntiles; }
+  __device__ void next() {
+    if (++c < T->seg[s].ncomp) return;
+    c = 0;
+    tile += gridDim.x;
+    while (s + 1 < T->nseg && tile >= T->seg[s + 1].tile0) ++s;
+  }
+  __device__ const Seg& seg() const { return T->seg[s]; }
+  __device__ int local_tile() const { return tile - T->seg[s].tile0; }
+};
+
+// ------------------------------------------------------------ epilogue walk
+// One thread, one row: z_i (i < D) in TMEM columns; groups are contiguous
+// column ranges with a body each.  A 16-column chunk inside one group is
+// handled with a single body dispatch.
+template <int BODY>
+__device__ __forceinline__ void chunk16(const float* v, const float* aux, int col0, int gstart,
+                                        float& zprev, const ProblemDev& P, Acc32& acc) {
+  if (BODY == SEVO_ROSENBROCK) {
+    if (col0 > gstart) term32(SEVO_ROSENBROCK, zprev, 0.f, true, v[0], P, acc);
+#pragma unroll
+    for (int k = 0; k + 1 < 16; ++k) term32(SEVO_ROSENBROCK, v[k], 0.f, true, v[k + 1], P, acc);
+  } else if (BODY == SEVO_ELLIPSOID || BODY == SEVO_GRIEWANK) {
+    float a[16];
+    const float4* a4 = reinterpret_cast<const float4*>(aux + col0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = __ldg(a4 + q);
+      a[4 * q] = t.x;
+      a[4 * q + 1] = t.y;
+      a[4 * q + 2] = t.z;
+      a[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) term32(BODY, v[k], a[k], false, 0.f, P, acc);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) term32(BODY, v[k], 0.f, false, 0.f, P, acc);
+  }
+  zprev = v[15];
+}
+
+__device__ __forceinline__ double walk_row(uint32_t taddr, int D, int c, bool comp,
+                                           const ProblemDev& P) {
+  const float* __restrict__ aux32 = P.aux32[c];
+  int g = 0;
+  int gend = P.gstart[1];
+  int body = comp ? P.cbody[c] : P.gbody[0];
+  Acc32 acc;
+  acc32_init(acc);
+  double gsum = 0.0;
+  float zprev = 0.f;
+  for (int col0 = 0; col0 < D; col0 += 16) {
+    float v[16];
+    tc::tmem_ld16(taddr + (uint32_t)col0, v);
+    while (col0 >= gend) {  // close groups that ended before this chunk
+      gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+      ++g;
+      gend = P.gstart[g + 1];
+      body = comp ? P.cbody[c] : P.gbody[g];
+      acc32_init(acc);
+    }
+    if (col0 + 16 <= gend) {
+      const int gs = P.gstart[g];
+      switch (body) {
+        case SEVO_ELLIPSOID: chunk16<SEVO_ELLIPSOID>(v, aux32, col0, gs, zprev, P, acc); break;
+        case SEVO_ROSENBROCK: chunk16<SEVO_ROSENBROCK>(v, aux32, col0, gs, zprev, P, acc); break;
+        case SEVO_RASTRIGIN: chunk16<SEVO_RASTRIGIN>(v, aux32, col0, gs, zprev, P, acc); break;
+        case SEVO_SCHWEFEL: chunk16<SEVO_SCHWEFEL>(v, aux32, col0, gs, zprev, P, acc); break;
+        case SEVO_ACKLEY: chunk16<SEVO_ACKLEY>(v, aux32, col0, gs, zprev, P, acc); break;
+        default: chunk16<SEVO_GRIEWANK>(v, aux32, col0, gs, zprev, P, acc); break;
+      }
+    } else {
+      // chunk crosses a group border or the end of the row: per element
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int i = col0 + k;
+        if (i < D) {
+          while (i == gend) {
+            gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+            ++g;
+            gend = P.gstart[g + 1];
+            body = comp ? P.cbody[c] : P.gbody[g];
+            acc32_init(acc);
+          }
+          const float z = v[k];
+          if (body == SEVO_ROSENBROCK) {
+            if (i > P.gstart[g]) term32(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
+          } else {
+            term32(body, z, aux32[i], false, 0.f, P, acc);
+          }
+          zprev = z;
+        }
+      }
+    }
+  }
+  gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+  return gsum;
+}
+
+struct ListOut {
+  int32_t* list;
+  int32_t* counts;
+  uint32_t* nonfinite;
+};
+
+__device__ __forceinline__ void emit(double err, int64_t row, double* out, const ListOut& lo,
+                                     const Seg& sg) {
+  if (!isfinite(err)) {
+    err = __longlong_as_double(0x7ff8000000000000ll);
+    if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
+  } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
+    int k = atomicAdd(lo.counts + sg.sidx, 1);
+    lo.list[sg.list_off + k] = (int32_t)row;
+  }
+  out[row] = err;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    eval_tc_fused(const __grid_constant__ SegTable T, const FusedGeom geo,
+                  const double* __restrict__ X, int64_t ld, double* __restrict__ out,
+                  double* __restrict__ comp_g, double* __restrict__ comp_s, ListOut lo,
+                  uint32_t* dev_err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ Bars bars;
+  __shared__ float sS[2][BM];
+
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA[2] = {base, base + geo.a_bytes};
+  unsigned char* sB = base + 2 * geo.a_bytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars.a_full[b], NPROD);
+      tc::mbar_init(&bars.a_empty[b], 1);
+      tc::mbar_init(&bars.t_full[b], 1);
+      tc::mbar_init(&bars.t_empty[b], NEPI / 2);
+      tc::mbar_init(&bars.s_full[b], NPROD);
+    }
+    tc::mbar_init(&bars.b_full, 1);
+    tc::mbar_init(&bars.mma_done, 1);
+    bars.abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == WARP_MMA) {
+    tc::tmem_alloc(&bars.tmem_base, 2 * TCOLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bars.tmem_base;
+  const int D = geo.D;
+
+  if (warp == WARP_MMA) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      JobIter it;
+      it.init(&T);
+      const ProblemDev* curP = nullptr;
+      int cur_c = -1;
+      uint32_t b_phase = 0, done_phase = 0;
+      bool pending_done = false;
+      for (int64_t j = 0; it.valid(); ++j, it.next()) {
+        const Seg& sg = it.seg();
+        const int c = it.c;
+        const int a = (int)(j & 1);
+        const uint32_t u = (uint32_t)(j >> 1);
+        if (sg.P != curP || c != cur_c) {
+          if (pending_done) {  // the previous job's MMAs must finish reading B
+            if (!tc::mbar_wait(&bars.mma_done, done_phase, &bars.abort, WAIT_BUDGET)) {
+              raise_abort(&bars, dev_err);
+              break;
+            }
+            done_phase ^= 1u;
+            pending_done = false;
+          }
+          const CUtensorMap* m0 = BF16 ? sg.P->tmaphi[c] : sg.P->tmap32[c];
+          const CUtensorMap* m1 = sg.P->tmaplo[c];
+          tc::mbar_arrive_expect_tx(&bars.b_full, (uint32_t)geo.b_bytes);
+          for (int kb = 0; kb < geo.nkb; ++kb) {
+            if (BF16) {
+              tc::tma_load_2d(sB + kb * geo.b_kb_bytes, m0, &bars.b_full, kb * 64, 0);
+              tc::tma_load_2d(sB + (geo.nkb + kb) * geo.b_kb_bytes, m1, &bars.b_full, kb * 64, 0);
+            } else {
+              tc::tma_load_2d(sB + kb * geo.b_kb_bytes, m0, &bars.b_full, kb * 32, 0);
+            }
+          }
+          if (!tc::mbar_wait(&bars.b_full, b_phase, &bars.abort, WAIT_BUDGET)) {
+            raise_abort(&bars, dev_err);
+            break;
+          }
+          b_phase ^= 1u;
+          curP = sg.P;
+          cur_c = c;
+        }
+        if (!tc::mbar_wait(&bars.a_full[a], u & 1u, &bars.abort, WAIT_BUDGET) ||
+            !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
+          raise_abort(&bars, dev_err);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(a * TCOLS);
+        const uint32_t aS = tc::smem_u32(sA[a]);
+        const uint32_t bS = tc::smem_u32(sB);
+        if (BF16) {
+          const uint32_t a_lo = aS + (uint32_t)(geo.nkb * A_KB_BYTES);
+          const uint32_t b_lo = bS + (uint32_t)(geo.nkb * geo.b_kb_bytes);
+          for (int ks = 0; ks < geo.ksteps; ++ks) {
+            const uint32_t ka = (uint32_t)((ks >> 2) * A_KB_BYTES + (ks & 3) * 32);
+            const uint32_t kbb = (uint32_t)((ks >> 2) * geo.b_kb_bytes + (ks & 3) * 32);
+            tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ka), tc::sdesc_sw128(bS + kbb), geo.idesc,
+                        ks > 0 ? 1u : 0u);
+            tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ka), tc::sdesc_sw128(b_lo + kbb), geo.idesc, 1);
+            tc::mma_f16(d_tmem, tc::sdesc_sw128(a_lo + ka), tc::sdesc_sw128(bS + kbb), geo.idesc, 1);
+          }
+        } else {
+          for (int ks = 0; ks < geo.ksteps; ++ks) {
+            const uint32_t ka = (uint32_t)((ks >> 2) * A_KB_BYTES + (ks & 3) * 32);
+            const uint32_t kbb = (uint32_t)((ks >> 2) * geo.b_kb_bytes + (ks & 3) * 32);
+            tc::mma_tf32(d_tmem, tc::sdesc_sw128(aS + ka), tc::sdesc_sw128(bS + kbb), geo.idesc,
+                         ks > 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&bars.a_empty[a]);
+        tc::mma_commit(&bars.t_full[a]);
+        // if the next job needs another B, track when these MMAs are done
+        JobIter nx = it;
+        nx.next();
+        if (nx.valid() && (nx.seg().P != curP || nx.c != cur_c)) {
+          tc::mma_commit(&bars.mma_done);
+          pending_done = true;
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp >= NEPI) {
+    // ------------------------------------------------------------ producers
+    const int pw = warp - NEPI;
+    constexpr int RPW = BM / NPROD;  // rows per producer warp
+    const int k0 = lane * 4;         // lane owns columns k0..k0+3 (kpad <= 128)
+    const bool full4 = (k0 + 3 < D);
+    JobIter it;
+    it.init(&T);
+    for (int64_t j = 0; it.valid(); ++j, it.next()) {
+      const Seg& sg = it.seg();
+      const int c = it.c;
+      const bool comp = sg.comp;
+      const int a = (int)(j & 1);
+      const uint32_t u = (uint32_t)(j >> 1);
+      if (!tc::mbar_wait(&bars.a_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET) ||
+          (comp && !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET))) {
+        if (lane == 0) raise_abort(&bars, dev_err);
+        break;
+      }
+      const float* __restrict__ oh = sg.P->oh32[c];
+      const float* __restrict__ ol = sg.P->ol32[c];
+      float ohv[4], olv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = k0 + t;
+        ohv[t] = (k < D) ? __ldg(oh + k) : 0.f;
+        olv[t] = (k < D) ? __ldg(ol + k) : 0.f;
+      }
+      const int64_t lrow0 = (int64_t)it.local_tile() * BM;
+      unsigned char* At = sA[a];
+      for (int rb = 0; rb < RPW; rb += 4) {
+        double xv[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = pw * RPW + rb + t;
+          const int64_t lr = lrow0 + r;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
+          if (lr < sg.nrows) {
+            const double* xr = X + (sg.row0 + lr) * ld;
+            if (full4) {
+              const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
+              const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k0 + 2));
+              xv[t][0] = p0.x;
+              xv[t][1] = p0.y;
+              xv[t][2] = p1.x;
+              xv[t][3] = p1.y;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (k0 + q < D) xv[t][q] = __ldg(xr + k0 + q);
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = pw * RPW + rb + t;
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (k0 + q < D) {
+              float xh, xl;
+              sv_split_hi_lo(xv[t][q], xh, xl);
+              d[q] = (xh - ohv[q]) + (xl - olv[q]);
+            }
+          }
+          if (comp) {
+            float sq = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
+            if (lane == 0) sS[a][r] = sq;
+          }
+          const int sw = r & 7;
+          if (k0 >= geo.kpad) continue;
+          if (BF16) {
+            // 64 bf16 per 128-byte K block: k0 -> block k0/64, chunk (k0%64)/8, half (k0%8)/4
+            const int kb = k0 >> 6, ch = (k0 & 63) >> 3, hf = (k0 & 7) >> 2;
+            uint32_t hi2[2], lo2[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              __nv_bfloat16 h0 = __float2bfloat16_rn(d[2 * q]), h1 = __float2bfloat16_rn(d[2 * q + 1]);
+              __nv_bfloat16 l0 = __float2bfloat16_rn(d[2 * q] - __bfloat162float(h0));
+              __nv_bfloat16 l1 = __float2bfloat16_rn(d[2 * q + 1] - __bfloat162float(h1));
+              hi2[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              lo2[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4) + hf * 8;
+            *reinterpret_cast<uint2*>(At + off) = make_uint2(hi2[0], hi2[1]);
+            *reinterpret_cast<uint2*>(At + geo.nkb * A_KB_BYTES + off) = make_uint2(lo2[0], lo2[1]);
+          } else {
+            // 32 tf32 per 128-byte K block: k0 -> block k0/32, chunk (k0%32)/4
+            const int kb = k0 >> 5, ch = (k0 & 31) >> 2;
+            const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4);
+            *reinterpret_cast<float4*>(At + off) = make_float4(
+                tc::to_tf32(d[0]), tc::to_tf32(d[1]), tc::to_tf32(d[2]), tc::to_tf32(d[3]));
+          }
+        }
+      }
+      __syncwarp();
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&bars.a_full[a]);
+        if (comp) tc::mbar_arrive(&bars.s_full[a]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    // group g = warp / 4 takes the jobs of parity g (TMEM buffer g); thread
+    // = row 32 * (warp % 4) + lane = TMEM lane.
+    const int g = warp >> 2;
+    const int r = (warp & 3) * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * TCOLS);
+    JobIter it;
+    it.init(&T);
+    for (int64_t j = 0; it.valid(); ++j, it.next()) {
+      if ((int)(j & 1) != g) continue;
+      const Seg& sg = it.seg();
+      const int c = it.c;
+      const bool comp = sg.comp;
+      const uint32_t u = (uint32_t)(j >> 1);
+      if (!tc::mbar_wait(&bars.t_full[g], u & 1u, &bars.abort, WAIT_BUDGET) ||
+          (comp && !tc::mbar_wait(&bars.s_full[g], u & 1u, &bars.abort, WAIT_BUDGET))) {
+        raise_abort(&bars, dev_err);
+        break;
+      }
+      tc::tc_fence_after();
+      const float s_c = comp ? sS[g][r] : 0.f;
+      const double gsum = walk_row(taddr, D, c, comp, *sg.P);
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars.t_empty[g]);
+      const int64_t lr = (int64_t)it.local_tile() * BM + r;
+      if (lr < sg.nrows) {
+        const int64_t row = sg.row0 + lr;
+        if (comp) {
+          comp_g[row * SV_MAXC + c] = gsum;
+          comp_s[row * SV_MAXC + c] = (double)s_c;
+        } else {
+          emit(gsum, row, out, lo, sg);
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == WARP_MMA) {
+    if (bars.abort) {  // let any MMA still in flight finish before freeing TMEM
+      for (int k = 0; k < 1000; ++k) __nanosleep(1000);
+    }
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * TCOLS);
+  }
+}
+
+// composition rows: weights from the FP32 distances of the tensor-core pass
+// (exactly 0 at x = o_c, where the weight collapses onto component c)
+__global__ void compose_rows_kernel(const __grid_constant__ SegTable T, const double* comp_g,
+                                    const double* comp_s, double* out, ListOut lo) {
+  for (int s = 0; s < T.nseg; ++s) {
+    const Seg& sg = T.seg[s];
+    if (!sg.comp) continue;
+    const ProblemDev& P = *sg.P;
+    for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < sg.nrows;
+         lr += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t row = sg.row0 + lr;
+      emit(compose(P, comp_s + row * SV_MAXC, comp_g + row * SV_MAXC), row, out, lo, sg);
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2D map over a row-major rows x cols matrix (cols contiguous), box
+// (box_cols, box_rows), 128-byte swizzle
+bool make_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, int cols,
+              int rows, int box_cols, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * esize};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+FusedGeom fused_geom(const ProblemDev& h, bool bf16) {
+  FusedGeom g;
+  g.D = h.D;
+  g.kpad = h.kpad;
+  g.npad = h.npad;
+  g.b_kb_bytes = h.npad * 128;
+  if (bf16) {
+    g.nkb = h.kpad / 64;
+    g.a_bytes = 2 * g.nkb * A_KB_BYTES;
+    g.b_bytes = 2 * g.nkb * g.b_kb_bytes;
+    g.ksteps = (h.D + 15) / 16;
+    g.idesc = tc::idesc_make(1, BM, h.npad);
+  } else {
+    g.nkb = h.kpad / 32;
+    g.a_bytes = g.nkb * A_KB_BYTES;
+    g.b_bytes = g.nkb * g.b_kb_bytes;
+    g.ksteps = (h.D + 7) / 8;
+    g.idesc = tc::idesc_make(2, BM, h.npad);
+  }
+  return g;
+}
+
+}  // namespace
+
+// rows of the B box: the whole padded N extent for the fused kernel
+static int b_box_rows(const ProblemDev& h) { return h.D <= 128 ? h.npad : 256; }
+
+int32_t sv_build_tmaps(sevo_problem* p) {
+  const ProblemDev& h = p->host_desc;
+  const int rows = b_box_rows(h);
+  for (int c = 0; c < h.ncomp; ++c) {
+    if (!make_map(&p->tmap_f32[c], h.M32[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.kpad, h.npad,
+                  32, rows) ||
+        !make_map(&p->tmap_hi[c], h.Mhi[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h.kpad, h.npad,
+                  64, rows) ||
+        !make_map(&p->tmap_lo[c], h.Mlo[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h.kpad, h.npad,
+                  64, rows))
+      return SEVO_ERR_CUDA;
+  }
+  p->tmap_rows = rows;
+  p->tmaps_ready = true;
+  return SEVO_OK;
+}
+
+// composition scratch: per row, SV_MAXC slots of g_c and of s_c (FP64)
+size_t sv_eval_tc_scratch_bytes(bool any_comp, int, int64_t rows) {
+  return any_comp ? (size_t)rows * SV_MAXC * 16 : 0;
+}
+
+cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const double* X,
+                                int64_t ld, double* out, int32_t* list, const int64_t* list_off,
+                                int32_t* counts, uint32_t* nonfinite, void* scratch,
+                                size_t scratch_bytes, uint32_t* dev_err, cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  if (nseg > SV_MAX_SEG) return cudaErrorInvalidValue;
+  const ProblemDev& h0 = segs[0].p->host_desc;
+  if (h0.D > 128) return cudaErrorNotSupported;
+  const bool bf16 = (prec == SEVO_BF16X3);
+  const FusedGeom g = fused_geom(h0, bf16);
+  const size_t smem = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
+  static bool attr_done[2] = {false, false};
+  if (!attr_done[bf16]) {
+    cudaError_t e = bf16 ? cudaFuncSetAttribute(eval_tc_fused<true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)(200 * 1024))
+                         : cudaFuncSetAttribute(eval_tc_fused<false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)(200 * 1024));
+    if (e != cudaSuccess) return e;
+    attr_done[bf16] = true;
+  }
+  SegTable T;
+  T.nseg = nseg;
+  T.D = h0.D;
+  int tiles = 0;
+  bool any_comp = false;
+  int64_t row_lo = INT64_MAX, row_hi = 0;
+  for (int k = 0; k < nseg; ++k) {
+    const TcSegment& s = segs[k];
+    Seg& d = T.seg[k];
+    d.P = s.p->desc_d;
+    d.row0 = s.row0;
+    d.list_off = list_off ? list_off[k] : 0;
+    d.nrows = (int32_t)s.nrows;
+    d.tile0 = tiles;
+    d.comp = (s.p->family == SEVO_COMPOSITION);
+    d.ncomp = s.p->ncomp;
+    d.sidx = k;
+    d.pad = 0;
+    tiles += (int)((s.nrows + BM - 1) / BM);
+    if (d.comp) {
+      any_comp = true;
+      row_lo = std::min<int64_t>(row_lo, s.row0);
+      row_hi = std::max<int64_t>(row_hi, s.row0 + s.nrows);
+    }
+  }
+  T.ntiles = tiles;
+  if (tiles == 0) return cudaSuccess;
+  // composition scratch rows are indexed relative to the first composition
+  // row: (row - row_lo) * SV_MAXC + component
+  double* comp_g = nullptr;
+  double* comp_s = nullptr;
+  if (any_comp) {
+    const size_t need = (size_t)(row_hi - row_lo) * SV_MAXC * 16;
+    if (!scratch || scratch_bytes < need) return cudaErrorInvalidValue;
+    comp_g = (double*)scratch - row_lo * SV_MAXC;
+    comp_s = (double*)scratch + (size_t)(row_hi - row_lo) * SV_MAXC - row_lo * SV_MAXC;
+  }
+  const ListOut lo{list, counts, nonfinite};
+  const int grid = std::min(tiles, sv_num_sms());
+  if (bf16)
+    eval_tc_fused<true><<<grid, NTHREADS, smem, st>>>(T, g, X, ld, out, comp_g, comp_s, lo,
+                                                      dev_err);
+  else
+    eval_tc_fused<false><<<grid, NTHREADS, smem, st>>>(T, g, X, ld, out, comp_g, comp_s, lo,
+                                                       dev_err);
+  sv_note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (any_comp) {
+    const int cgrid = std::max(1, std::min(sv_num_sms() * 4, (int)((row_hi - row_lo + 255) / 256)));
+    compose_rows_kernel<<<cgrid, 256, 0, st>>>(T, comp_g, comp_s, out, lo);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }

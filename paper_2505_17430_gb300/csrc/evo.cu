@@ -1,14 +1,681 @@
-// evo.cu -- placeholder for the DE/PSO generation kernels.
-#include "kernels.cuh"
-extern "C" {
-int32_t sevo_state_create(const sevo_problem*, const sevo_alg_params*, uint64_t, void*, sevo_state**) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_destroy(sevo_state*) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_de_step(sevo_state*, uint64_t) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_pso_step(sevo_state*, uint64_t) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_result(const sevo_state*, double*, int64_t*, int64_t*, int64_t*) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_get(const sevo_state*, double*, double*, double*, int32_t*, double*, double*, double*, double*, double*, int32_t*) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_set(sevo_state*, const double*, const double*, const double*, int32_t, const double*, const double*, const double*, int64_t) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_save(const sevo_state*, void*, size_t*) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_state_load(sevo_state*, const void*, size_t) { return SEVO_ERR_UNSUPPORTED; }
-int32_t sevo_run_grid(const sevo_grid*, sevo_grid_result*, void*) { return SEVO_ERR_UNSUPPORTED; }
+// evo.cu -- DE and PSO generation kernels and the single-run state API.
+//
+// Operators (Listing 1 names the modules; the formulas are the library's
+// readings, identical in every bit to the oracle's so that lock-step
+// comparisons are exact):
+//   DE/rand/1:           v = fma(F, x_r2 - x_r3, x_r1)
+//   DE/current-to-pbest: v = fma(F, x_r1 - x~_r2, fma(F, x_pb - x_i, x_i))
+//   binomial crossover:  u_j = v_j if word_j * 2^-32 < CR or j = j_rand
+//   midpoint repair:     u_j < lb -> (lb + x_ij) / 2;  u_j > ub -> (ub + x_ij) / 2
+//   selection:           x_i <- u_i iff f(u_i) <= f(x_i); current-to-pbest
+//                        pushes the replaced parent into the archive (row
+//                        order; random slot once full, later rows win)
+//   PSO:                 v = fma(w, v, fma(c1 r1, p - x, (c2 r2)(g - x)));
+//                        x += v; clamp to [lb,ub] with v = 0 there;
+//                        p_i <- x_i iff f(x_i) < f(p_i); guide = gbest or
+//                        ring {i-1,i,i+1} argmin (lowest index on ties)
+// FP64 arithmetic uses explicit round-to-nearest intrinsics (no contraction
+// beyond the stated fma), so trial vectors equal the oracle's bit for bit.
+// Streaming kernels move 4 consecutive coordinates per thread (one Philox
+// call covers the four crossover words).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "evo.cuh"
+
+namespace {
+
+// exact 53-bit uniform from two Philox words using integer operations only
+// (same value as sv_u53; the int->double conversion unit is slow here)
+__device__ __forceinline__ double u53_int(uint32_t w0, uint32_t w1) {
+  const unsigned long long m = ((unsigned long long)(w0 >> 5) << 26) | (unsigned long long)(w1 >> 6);
+  if (m == 0ull) return 0.0;
+  const int e = 63 - __clzll((long long)m);  // 0..52
+  const unsigned long long mant = (m << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((unsigned long long)(1023 - 53 + e) << 52) | mant));
+}
+
+// order-preserving integer key of a double (NaN sorts last)
+__device__ __forceinline__ long long fkey(double f) {
+  long long b = __double_as_longlong(f);
+  if (f != f) return 0x7FFFFFFFFFFFFFFFll;
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+__device__ __forceinline__ double dmin_pos(double a, double b) { return (b < a) ? b : a; }
+
+// ---------------------------------------------------------------- control
+__global__ void ctl_set_kernel(GenCtl* ctl, unsigned long long gen, int count) {
+  ctl->gen = gen;
+  ctl->count = count;
+}
+
+__global__ void ctl_advance_kernel(GenCtl* ctl, int NP, long long budget) {
+  unsigned long long g = ctl->gen + 1;
+  ctl->gen = g;
+  long long before = (long long)NP + (long long)(g - 1) * NP;
+  long long c = budget - before;
+  ctl->count = (int)(c < 0 ? 0 : (c > NP ? NP : c));
+}
+
+// ---------------------------------------------------------------- init
+__global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restrict__ seeds, int R,
+                                int NP, int D, int ld, double lb, double ub) {
+  const int64_t total = (int64_t)R * NP * ((D + 1) / 2);
+  const double span = __dsub_rn(ub, lb);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int jp = (int)(t % ((D + 1) / 2));
+    const int64_t ri = t / ((D + 1) / 2);
+    const int i = (int)(ri % NP), r = (int)(ri / NP);
+    const uint4 w = sv_draw(seeds[r], (uint32_t)jp, (uint32_t)i, 0u, SV_P_INIT);
+    double* xr = X + ((int64_t)r * NP + i) * ld;
+    const int j = 2 * jp;
+    xr[j] = __dadd_rn(lb, __dmul_rn(span, u53_int(w.x, w.y)));
+    if (j + 1 < D) xr[j + 1] = __dadd_rn(lb, __dmul_rn(span, u53_int(w.z, w.w)));
+  }
+}
+
+// ---------------------------------------------------------------- DE trials
+template <int ALG>
+__global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict__ U,
+                                const double* __restrict__ A, const int32_t* __restrict__ asize,
+                                const int32_t* __restrict__ order, int32_t* __restrict__ part,
+                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
+                                int R, int NP, int D, int ld, double F, unsigned long long cr_thr,
+                                double lb, double ub, int pk) {
+  const int nq = (D + 3) >> 2;
+  const int64_t total = (int64_t)R * NP * nq;
+  const unsigned long long gen = ctl->gen;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int jq = (int)(t % nq);
+    const int64_t ri = t / nq;
+    const int i = (int)(ri % NP), r = (int)(ri / NP);
+    const uint64_t seed = seeds[r];
+    const uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_PART);
+    const double* Xr = X + (int64_t)r * NP * ld;
+    const double* xi = Xr + (int64_t)i * ld;
+    const double *d1, *d2, *d3;
+    int p0, p1, p2, jr;
+    if (ALG == SEVO_DE_RAND1) {
+      int a = (int)sv_below(w.x, (uint32_t)(NP - 1));
+      if (a >= i) ++a;
+      const int lo = min(i, a), hi = max(i, a);
+      int b = (int)sv_below(w.y, (uint32_t)(NP - 2));
+      if (b >= lo) ++b;
+      if (b >= hi) ++b;
+      int e0 = lo, e1 = hi, e2 = b;  // sort {i, a, b}
+      if (e2 < e1) {
+        int tt = e1;
+        e1 = e2;
+        e2 = tt;
+      }
+      if (e1 < e0) {
+        int tt = e0;
+        e0 = e1;
+        e1 = tt;
+      }
+      int c = (int)sv_below(w.z, (uint32_t)(NP - 3));
+      if (c >= e0) ++c;
+      if (c >= e1) ++c;
+      if (c >= e2) ++c;
+      p0 = a;
+      p1 = b;
+      p2 = c;
+      d1 = Xr + (int64_t)a * ld;
+      d2 = Xr + (int64_t)b * ld;
+      d3 = Xr + (int64_t)c * ld;
+    } else {
+      const int as = asize[r];
+      const int pb = order[(int64_t)r * NP + (int)sv_below(w.x, (uint32_t)pk)];
+      int r1 = (int)sv_below(w.y, (uint32_t)(NP - 1));
+      if (r1 >= i) ++r1;
+      const int lo = min(i, r1), hi = max(i, r1);
+      int r2 = (int)sv_below(w.z, (uint32_t)(NP + as - 2));
+      if (r2 >= lo) ++r2;
+      if (r2 >= hi) ++r2;
+      p0 = pb;
+      p1 = r1;
+      p2 = r2;
+      d1 = Xr + (int64_t)pb * ld;
+      d2 = Xr + (int64_t)r1 * ld;
+      d3 = (r2 < NP) ? Xr + (int64_t)r2 * ld : A + ((int64_t)r * NP + (r2 - NP)) * ld;
+    }
+    jr = (int)sv_below(w.w, (uint32_t)D);
+    if (jq == 0 && part) {
+      int32_t* pp = part + ((int64_t)r * NP + i) * 4;
+      pp[0] = p0;
+      pp[1] = p1;
+      pp[2] = p2;
+      pp[3] = jr;
+    }
+    const uint4 cw = sv_draw(seed, (uint32_t)jq, (uint32_t)i, (uint32_t)gen, SV_P_CROSS);
+    const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
+    double* ui = U + ((int64_t)r * NP + i) * ld;
+    const int j0 = jq * 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      if (j >= D) break;
+      const double x = xi[j];
+      double u = x;
+      if ((unsigned long long)cws[q] < cr_thr || j == jr) {
+        if (ALG == SEVO_DE_RAND1)
+          u = __fma_rn(F, __dsub_rn(d2[j], d3[j]), d1[j]);
+        else
+          u = __fma_rn(F, __dsub_rn(d2[j], d3[j]), __fma_rn(F, __dsub_rn(d1[j], x), x));
+      }
+      if (u < lb) u = __dmul_rn(__dadd_rn(lb, x), 0.5);
+      if (u > ub) u = __dmul_rn(__dadd_rn(ub, x), 0.5);
+      ui[j] = u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- DE rank
+// top-k of each run by (fitness, index): order[rank] = row for rank < k.
+// Grid (runs, row blocks): each CTA loads the run's integer sort keys into
+// shared memory and ranks its 256 rows by counting (exact, deterministic).
+constexpr int RANK_ROWS = 256;
+__global__ void __launch_bounds__(RANK_ROWS)
+    de_rank_kernel(const double* __restrict__ fx, int32_t* __restrict__ order, int NP, int k) {
+  extern __shared__ long long keys[];
+  const int r = blockIdx.x;
+  const double* f = fx + (int64_t)r * NP;
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) keys[i] = fkey(f[i]);
+  __syncthreads();
+  const int i = blockIdx.y * RANK_ROWS + threadIdx.x;
+  if (i >= NP) return;
+  const long long ki = keys[i];
+  int rank = 0;
+  int j = 0;
+  for (; j + 4 <= NP; j += 4) {
+    const long long k0 = keys[j], k1 = keys[j + 1], k2 = keys[j + 2], k3 = keys[j + 3];
+    rank += (k0 < ki) || (k0 == ki && j < i);
+    rank += (k1 < ki) || (k1 == ki && j + 1 < i);
+    rank += (k2 < ki) || (k2 == ki && j + 2 < i);
+    rank += (k3 < ki) || (k3 == ki && j + 3 < i);
+  }
+  for (; j < NP; ++j) rank += (keys[j] < ki) || (keys[j] == ki && j < i);
+  if (rank < k) order[(int64_t)r * NP + rank] = i;
+}
+
+// ---------------------------------------------------------------- DE select
+// per run: acceptance, best-so-far, archive slots (row order, random slot
+// once full, the last row targeting a slot wins), fitness update.
+// action[i]: -2 rejected, -1 accepted without archive write, >= 0 slot.
+constexpr int SEL_THREADS = 512;
+
+__device__ __forceinline__ void block_min_update(double v, double* best_r) {
+  __shared__ double red[SEL_THREADS / 32];
+  for (int m = 16; m >= 1; m >>= 1) v = dmin_pos(v, __shfl_xor_sync(0xffffffffu, v, m));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = dmin_pos(b, red[w]);
+    *best_r = dmin_pos(*best_r, b);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+    de_select_kernel(double* __restrict__ fx, const double* __restrict__ fu,
+                     int32_t* __restrict__ asize, int32_t* __restrict__ action,
+                     double* __restrict__ best, const uint64_t* __restrict__ seeds,
+                     const GenCtl* __restrict__ ctl, int NP, int use_archive) {
+  extern __shared__ int owner[];
+  __shared__ int wsum[SEL_THREADS / 32];
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int count = ctl->count;
+  const unsigned long long gen = ctl->gen;
+  double* f = fx + (int64_t)r * NP;
+  const double* g = fu + (int64_t)r * NP;
+  int32_t* act = action + (int64_t)r * NP;
+  // best-so-far over the rows that count toward the budget
+  double m = INFINITY;
+  for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, g[i]);
+  block_min_update(m, best + r);
+  // contiguous chunk of rows per thread, so the scan follows row order
+  const int per = (NP + blockDim.x - 1) / blockDim.x;
+  const int i0 = min(NP, tid * per), i1 = min(NP, i0 + per);
+  int cnt = 0;
+  for (int i = i0; i < i1; ++i) cnt += (g[i] <= f[i]);
+  // block exclusive scan of cnt
+  const int warp = tid >> 5, lane = tid & 31;
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  for (int i = tid; i < NP; i += blockDim.x) owner[i] = -1;
+  __syncthreads();
+  int woff = 0;
+  for (int w = 0; w < warp; ++w) woff += wsum[w];
+  int nacc_total = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nacc_total += wsum[w];
+  int k = woff + incl - cnt;
+  const int as0 = use_archive ? asize[r] : 0;  // rand/1 has no archive (asize null)
+  for (int i = i0; i < i1; ++i) {
+    const bool acc = g[i] <= f[i];
+    int a = -2;
+    if (acc) {
+      a = -1;
+      if (use_archive) {
+        int slot;
+        if (as0 + k < NP) {
+          slot = as0 + k;
+        } else {
+          const uint4 w = sv_draw(seeds[r], 0u, (uint32_t)i, (uint32_t)gen, SV_P_ARCH);
+          slot = (int)sv_below(w.x, (uint32_t)NP);
+        }
+        atomicMax(&owner[slot], i);
+        a = slot;
+      }
+      ++k;
+    }
+    act[i] = a;
+  }
+  __syncthreads();
+  for (int i = i0; i < i1; ++i) {
+    int a = act[i];
+    if (a >= 0 && owner[a] != i) act[i] = -1;  // a later row overwrote this slot
+    if (a != -2) f[i] = g[i];
+  }
+  if (tid == 0 && use_archive) asize[r] = min(NP, as0 + nacc_total);
+}
+
+// accepted rows: archive <- old x (if slot), x <- u
+__global__ void de_apply_kernel(double* __restrict__ X, const double* __restrict__ U,
+                                double* __restrict__ A, const int32_t* __restrict__ action, int R,
+                                int NP, int D, int ld) {
+  const int nq = (D + 3) >> 2;
+  const int64_t total = (int64_t)R * NP * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int jq = (int)(t % nq);
+    const int64_t ri = t / nq;
+    const int a = action[ri];
+    if (a == -2) continue;
+    const int r = (int)(ri / NP);
+    double* xi = X + ri * ld;
+    const double* ui = U + ri * ld;
+    double* as = (a >= 0) ? A + ((int64_t)r * NP + a) * ld : nullptr;
+    const int j0 = jq * 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      if (j >= D) break;
+      if (as) as[j] = xi[j];
+      xi[j] = ui[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- PSO
+__global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
+                                const double* __restrict__ P, const int32_t* __restrict__ guide,
+                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
+                                int R, int NP, int D, int ld, double w, double c1, double c2,
+                                double lb, double ub) {
+  const int64_t total = (int64_t)R * NP * D;
+  const unsigned long long gen = ctl->gen;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % D);
+    const int64_t ri = t / D;
+    const int i = (int)(ri % NP), r = (int)(ri / NP);
+    const uint4 rw = sv_draw(seeds[r], (uint32_t)j, (uint32_t)i, (uint32_t)gen, SV_P_PSO);
+    const double r1 = u53_int(rw.x, rw.y), r2 = u53_int(rw.z, rw.w);
+    const double a = __dmul_rn(c1, r1), b = __dmul_rn(c2, r2);
+    const int64_t e = ri * ld + j;
+    const int gi = guide[ri];
+    const double x = X[e];
+    const double gj = P[((int64_t)r * NP + gi) * ld + j];
+    double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
+    double xn = __dadd_rn(x, v);
+    if (xn < lb) {
+      xn = lb;
+      v = 0.0;
+    }
+    if (xn > ub) {
+      xn = ub;
+      v = 0.0;
+    }
+    X[e] = xn;
+    V[e] = v;
+  }
+}
+
+// per run: strict pbest update flags, best-so-far, guides (gbest / ring)
+__global__ void __launch_bounds__(SEL_THREADS)
+    pso_update_kernel(const double* __restrict__ fx, double* __restrict__ fp,
+                      int32_t* __restrict__ flag, int32_t* __restrict__ guide,
+                      double* __restrict__ best, const GenCtl* __restrict__ ctl, int NP,
+                      int topology, int use_count, int update_best) {
+  __shared__ long long kbest[SEL_THREADS / 32];
+  __shared__ int ibest[SEL_THREADS / 32];
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int count = use_count ? ctl->count : NP;
+  const double* f = fx + (int64_t)r * NP;
+  double* p = fp + (int64_t)r * NP;
+  int32_t* fl = flag + (int64_t)r * NP;
+  int32_t* gd = guide + (int64_t)r * NP;
+  if (update_best) {
+    double m = INFINITY;
+    for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, f[i]);
+    block_min_update(m, best + r);
+  }
+  for (int i = tid; i < NP; i += blockDim.x) {
+    const bool up = f[i] < p[i];
+    fl[i] = up;
+    if (up) p[i] = f[i];
+  }
+  __syncthreads();
+  if (topology == 0) {
+    long long kb = 0x7FFFFFFFFFFFFFFFll;
+    int ib = 0x7FFFFFFF;
+    for (int i = tid; i < NP; i += blockDim.x) {
+      const long long k = fkey(p[i]);
+      if (k < kb || (k == kb && i < ib)) {
+        kb = k;
+        ib = i;
+      }
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+      const long long k2 = __shfl_xor_sync(0xffffffffu, kb, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, ib, o);
+      if (k2 < kb || (k2 == kb && i2 < ib)) {
+        kb = k2;
+        ib = i2;
+      }
+    }
+    if ((tid & 31) == 0) {
+      kbest[tid >> 5] = kb;
+      ibest[tid >> 5] = ib;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (kbest[w] < kbest[0] || (kbest[w] == kbest[0] && ibest[w] < ibest[0])) {
+          kbest[0] = kbest[w];
+          ibest[0] = ibest[w];
+        }
+    }
+    __syncthreads();
+    const int b = ibest[0];
+    for (int i = tid; i < NP; i += blockDim.x) gd[i] = b;
+  } else {
+    for (int i = tid; i < NP; i += blockDim.x) {
+      int nb[3] = {(i + NP - 1) % NP, i, (i + 1) % NP};
+      // ascending indices, then strict improvement keeps the lowest index
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2 - a; ++c)
+          if (nb[c] > nb[c + 1]) {
+            int t = nb[c];
+            nb[c] = nb[c + 1];
+            nb[c + 1] = t;
+          }
+      int b = nb[0];
+      for (int t = 1; t < 3; ++t)
+        if (p[nb[t]] < p[b]) b = nb[t];
+      gd[i] = b;
+    }
+  }
+}
+
+// improved rows: pbest <- x
+__global__ void pso_copy_kernel(double* __restrict__ P, const double* __restrict__ X,
+                                const int32_t* __restrict__ flag, int R, int NP, int D, int ld) {
+  const int nq = (D + 3) >> 2;
+  const int64_t total = (int64_t)R * NP * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int jq = (int)(t % nq);
+    const int64_t ri = t / nq;
+    if (!flag[ri]) continue;
+    const int j0 = jq * 4;
+    double* pi = P + ri * ld;
+    const double* xi = X + ri * ld;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (j0 + q < D) pi[j0 + q] = xi[j0 + q];
+  }
+}
+
+__global__ void fill_kernel(double* __restrict__ a, int64_t n, double v) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    a[t] = v;
+}
+
+unsigned grid_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sv_num_sms() * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+// ====================================================================== host
+int sv_pbest_k(double p, int NP) {
+  int k = (int)std::ceil(p * (double)NP - 1e-9);
+  if (k < 1) k = 1;
+  if (k > NP) k = NP;
+  return k;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
+                       const std::vector<uint64_t>& seeds, const sevo_alg_params* a,
+                       cudaStream_t st) {
+  b->alg = a->alg;
+  b->D = probs[0]->D;
+  b->NP = a->NP;
+  b->R = (int)probs.size();
+  b->ld = (b->D + 1) & ~1;
+  b->F = a->F;
+  b->CR = a->CR;
+  b->p = a->p;
+  b->w = a->w;
+  b->c1 = a->c1;
+  b->c2 = a->c2;
+  b->lb = a->lb;
+  b->ub = a->ub;
+  b->budget = a->budget;
+  b->prec = a->prec;
+  b->stream = st;
+  b->refined_host = 0;
+  {
+    double t = std::ceil(a->CR * 4294967296.0);
+    if (t < 0) t = 0;
+    if (t > 4294967296.0) t = 4294967296.0;
+    b->cr_thr = (unsigned long long)t;
+  }
+  b->pbest_k = sv_pbest_k(a->p, a->NP);
+  b->run_prob = probs;
+  b->seg_begin.clear();
+  for (int r = 0; r < b->R; ++r)
+    if (r == 0 || probs[r] != probs[r - 1]) b->seg_begin.push_back(r);
+  b->seg_begin.push_back(b->R);
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const size_t mat = al256((size_t)rows * b->ld * 8), vec = al256((size_t)rows * 8),
+               ivec = al256((size_t)rows * 4);
+  const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB);
+  const bool ctpb = (b->alg == SEVO_DE_CTPB);
+  size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ +
+                 al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
+                 al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
+  if (de) bytes += mat /*U*/ + vec /*fu*/;
+  if (ctpb) bytes += mat /*A*/ + al256((size_t)b->R * 4) /*asize*/ + ivec /*order*/;
+  if (!de) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
+  b->block_bytes = bytes;
+  SV_CUDA(cudaMalloc(&b->block, bytes));
+  SV_CUDA(cudaMemsetAsync(b->block, 0, bytes, st));
+  char* c = (char*)b->block;
+  auto take = [&](size_t n) {
+    char* p = c;
+    c += n;
+    return p;
+  };
+  b->X = (double*)take(mat);
+  b->fx = (double*)take(vec);
+  b->best = (double*)take(al256((size_t)b->R * 8));
+  b->seeds = (uint64_t*)take(al256((size_t)b->R * 8));
+  b->ctl = (GenCtl*)take(al256(sizeof(GenCtl)));
+  b->guide = (int32_t*)take(ivec);
+  b->part = (int32_t*)take(al256((size_t)rows * 16));
+  b->action = (int32_t*)take(ivec);
+  b->U = b->fu = b->A = b->V = b->P = b->fp = nullptr;
+  b->asize = b->order = nullptr;
+  if (de) {
+    b->U = (double*)take(mat);
+    b->fu = (double*)take(vec);
+  }
+  if (ctpb) {
+    b->A = (double*)take(mat);
+    b->asize = (int32_t*)take(al256((size_t)b->R * 4));
+    b->order = (int32_t*)take(ivec);
+  }
+  if (!de) {
+    b->V = (double*)take(mat);
+    b->P = (double*)take(mat);
+    b->fp = (double*)take(vec);
+  }
+  SV_CUDA(cudaMemcpyAsync(b->seeds, seeds.data(), (size_t)b->R * 8, cudaMemcpyHostToDevice, st));
+  // evaluation scratch for all rows (refine sub-lists per segment and the
+  // tensor-core composition staging)
+  bool any_comp = false;
+  for (const sevo_problem* q : probs) any_comp |= (q->family == SEVO_COMPOSITION);
+  b->any_comp = any_comp;
+  b->eval_bytes = sv_eval_scratch_bytes(any_comp, b->prec, rows);
+  SV_CUDA(cudaMalloc(&b->eval_block, b->eval_bytes));
+  return SEVO_OK;
+}
+
+void sv_batch_free(Batch* b) {
+  if (b->block) cudaFree(b->block);
+  if (b->eval_block) cudaFree(b->eval_block);
+  b->block = b->eval_block = nullptr;
+}
+
+// evaluate every row of `M` (X or U) into `f`: one pass over the batch's
+// problem segments (runs sharing a problem)
+static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
+  std::vector<TcSegment> segs;
+  for (size_t s = 0; s + 1 < b->seg_begin.size(); ++s) {
+    const int r0 = b->seg_begin[s], r1 = b->seg_begin[s + 1];
+    segs.push_back(TcSegment{b->run_prob[r0], (int64_t)r0 * b->NP, (int64_t)(r1 - r0) * b->NP});
+  }
+  EvalScratch sc;
+  sv_eval_scratch_carve(b->eval_block, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
+  return sv_eval_segments(segs.data(), (int)segs.size(), b->prec, M, b->ld, f, sc, b->stream);
+}
+
+cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count) {
+  ctl_set_kernel<<<1, 1, 0, b->stream>>>(b->ctl, gen, count);
+  sv_note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t sv_ctl_advance(Batch* b) {
+  ctl_advance_kernel<<<1, 1, 0, b->stream>>>(b->ctl, b->NP, (long long)b->budget);
+  sv_note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t sv_batch_init(Batch* b) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int T = 256;
+  init_pop_kernel<<<grid_for(rows * ((b->D + 1) / 2), T), T, 0, st>>>(b->X, b->seeds, b->R, b->NP,
+                                                                     b->D, b->ld, b->lb, b->ub);
+                                                                     sv_note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fill_kernel<<<grid_for(b->R, T), T, 0, st>>>(b->best, b->R, INFINITY);
+  sv_note_launch();
+  const int count0 = (int)std::min<int64_t>(b->budget, b->NP);
+  if ((e = sv_ctl_set(b, 0ull, count0)) != cudaSuccess) return e;
+  if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
+  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
+    // best-so-far of the initial population (the select kernel's min part
+    // with no trials: fu == fx, every row "accepted" onto itself is avoided
+    // by using the PSO-style per-run reducer on fx)
+    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fx, b->action, b->guide, b->best,
+                                                    b->ctl, b->NP, 0, 1, 1);
+                                                    sv_note_launch();
+  } else {
+    const size_t m = (size_t)rows * b->ld * 8;
+    if ((e = cudaMemcpyAsync(b->P, b->X, m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    fill_kernel<<<grid_for(rows, T), T, 0, st>>>(b->fp, rows, INFINITY);
+    sv_note_launch();
+    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
+                                                    b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
+                                                    sv_note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t sv_batch_generation(Batch* b) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int nq = (b->D + 3) >> 2;
+  const int T = 256;
+  cudaError_t e;
+  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
+    if (b->alg == SEVO_DE_CTPB) {
+      de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
+                       (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
+      sv_note_launch();
+      de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
+          b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k);
+          sv_note_launch();
+    } else {
+      de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
+          b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0);
+          sv_note_launch();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
+    de_select_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 4, st>>>(
+        b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
+        b->alg == SEVO_DE_CTPB);
+        sv_note_launch();
+    de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
+                                                         b->D, b->ld);
+                                                         sv_note_launch();
+  } else {
+    pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
+                                                           b->ctl, b->R, b->NP, b->D, b->ld, b->w,
+                                                           b->c1, b->c2, b->lb, b->ub);
+                                                           sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
+    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
+                                                    b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
+                                                    sv_note_launch();
+    pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
+                                                         b->D, b->ld);
+                                                         sv_note_launch();
+  }
+  return cudaGetLastError();
+}
+
+// guides only (after the host overwrote pbest fitness)
+cudaError_t sv_batch_guides(Batch* b) {
+  pso_update_kernel<<<b->R, SEL_THREADS, 0, b->stream>>>(b->fp, b->fp, b->action, b->guide,
+                                                         b->best, b->ctl, b->NP,
+                                                         b->alg == SEVO_PSO_RING, 0, 0);
+                                                         sv_note_launch();
+  return cudaGetLastError();
 }

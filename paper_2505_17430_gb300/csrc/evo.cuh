@@ -1,0 +1,53 @@
+// evo.cuh -- batched DE/PSO run state shared by the state API (one run) and
+// the grid runner (many runs advancing together).
+#pragma once
+#include <vector>
+
+#include "kernels.cuh"
+
+// Per-generation control block, device-resident so that generations captured
+// in a CUDA graph read their Philox counter and evaluation count at run time.
+struct GenCtl {
+  unsigned long long gen;  // Philox counter of the current generation
+  int count;               // rows of this generation that count toward the budget
+  int pad;
+};
+
+struct Batch {
+  int alg, D, NP, R, ld;  // R runs of NP rows each, row stride ld (even)
+  double F, CR, p, w, c1, c2, lb, ub;
+  unsigned long long cr_thr;  // crossover test: word < cr_thr  <=>  word * 2^-32 < CR
+  int pbest_k;
+  int64_t budget;
+  int prec;
+  // per-run problem pointers (host) and segments of runs sharing a problem
+  std::vector<const sevo_problem*> run_prob;
+  std::vector<int> seg_begin;  // first run of each segment (runs sorted by problem)
+  // device arrays (one allocation)
+  void* block;
+  size_t block_bytes;
+  double *X, *fx, *U, *fu, *A, *V, *P, *fp, *best;
+  int32_t *asize, *guide, *part, *order, *action;
+  uint64_t* seeds;
+  GenCtl* ctl;
+  // evaluation scratch (refine list + counters + tensor-core staging)
+  void* eval_block;
+  size_t eval_bytes;
+  bool any_comp;
+  cudaStream_t stream;
+  int64_t refined_host;  // running count read back on result queries
+};
+
+int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
+                       const std::vector<uint64_t>& seeds, const sevo_alg_params* a,
+                       cudaStream_t st);
+void sv_batch_free(Batch* b);
+// draw the initial population (generation 0), evaluate it, set pbest/guides
+cudaError_t sv_batch_init(Batch* b);
+// one generation; gen/count read from b->ctl (set by the caller's launch)
+cudaError_t sv_batch_generation(Batch* b);
+cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count);
+cudaError_t sv_ctl_advance(Batch* b);  // gen += 1, count from gen and budget
+int sv_pbest_k(double p, int NP);
+cudaError_t sv_batch_guides(Batch* b);
+#define SV_MAX_NP 4096

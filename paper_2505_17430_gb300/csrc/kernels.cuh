@@ -12,31 +12,54 @@ struct EvalAux {
   uint32_t* nonfinite;    // rows whose result is NaN/Inf
 };
 
+#define SV_MAX_SEG 64
+
+// a run of rows [row0, row0 + nrows) of X evaluated on one problem
+struct TcSegment {
+  const sevo_problem* p;
+  int64_t row0;
+  int64_t nrows;
+};
+
+// per-segment refinement sub-lists: segment s lists its rows (global row
+// indices) in list[list_off[s] ...] with count[s] entries
+struct RefineTable {
+  int nseg;
+  const ProblemDev* P[SV_MAX_SEG];
+  int64_t list_off[SV_MAX_SEG];
+};
+
 int sv_num_sms();
 
-// CUDA-core evaluation: prec SEVO_FP64 (plain path) or SEVO_FP32
-cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t N,
-                       double* out, EvalAux aux, cudaStream_t st);
-// FP64 re-evaluation of the rows listed in list[0 .. *count)
-cudaError_t sv_eval_refine(const ProblemDev* Pd, const double* X, int64_t ld, int64_t Nmax,
-                           const int32_t* list, const int32_t* count, double* out,
+// CUDA-core evaluation of one segment: prec SEVO_FP64 (plain path) or SEVO_FP32
+cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t row0,
+                       int64_t N, double* out, EvalAux aux, cudaStream_t st);
+// FP64 re-evaluation of every listed row, all segments in one launch
+cudaError_t sv_eval_refine(const RefineTable& T, const double* X, int64_t ld, int64_t max_rows,
+                           const int32_t* list, const int32_t* counts, double* out,
                            cudaStream_t st);
-// tcgen05 evaluation (TF32 or BF16X3); scratch_a: N x kpad x 4 bytes (used
-// when the A operand is staged through memory), may be null for D <= 256
-cudaError_t sv_eval_tc(const sevo_problem* p, int prec, const double* X, int64_t ld, int64_t N,
-                       double* out, EvalAux aux, void* scratch, size_t scratch_bytes,
-                       uint32_t* dev_err, cudaStream_t st);
-size_t sv_eval_tc_scratch_bytes(const sevo_problem* p, int prec, int64_t N);
+// tcgen05 evaluation (TF32 or BF16X3) of segments sharing one D (<= 128);
+// refine lists per segment at list_off[s] with counters counts[s]
+cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const double* X,
+                                int64_t ld, double* out, int32_t* list, const int64_t* list_off,
+                                int32_t* counts, uint32_t* nonfinite, void* scratch,
+                                size_t scratch_bytes, uint32_t* dev_err, cudaStream_t st);
+// composition scratch of the tensor-core pass for `rows` rows
+size_t sv_eval_tc_scratch_bytes(bool any_comp, int prec, int64_t rows);
+// encode the TMA descriptors of a freshly uploaded problem
+int32_t sv_build_tmaps(sevo_problem* p);
 
-// full mixed/FP64 evaluation of N rows with refinement, using the given
-// scratch (refine list of N int32 + counters); returns a CUDA error
+// scratch of one evaluation pass over segments with `rows` rows in total
 struct EvalScratch {
-  int32_t* list;      // N
-  int32_t* counters;  // [0] refine count, [1] nonfinite count, [2] device error bits
-  void* tc;           // tensor-core staging
+  int32_t* list;      // rows (refine sub-lists)
+  int32_t* counters;  // [0, SV_MAX_SEG) refine counts, [SV_MAX_SEG] nonfinite,
+                      // [SV_MAX_SEG + 1] device error bits
+  void* tc;           // tensor-core composition staging
   size_t tc_bytes;
 };
-size_t sv_eval_scratch_bytes(const sevo_problem* p, int prec, int64_t N);
-void sv_eval_scratch_carve(void* base, const sevo_problem* p, int prec, int64_t N, EvalScratch* s);
-cudaError_t sv_eval_full(const sevo_problem* p, int prec, const double* X, int64_t ld, int64_t N,
-                         double* out, const EvalScratch& s, bool reset_counters, cudaStream_t st);
+#define SV_COUNTERS_BYTES ((SV_MAX_SEG + 4) * 4)
+size_t sv_eval_scratch_bytes(bool any_comp, int prec, int64_t rows);
+void sv_eval_scratch_carve(void* base, bool any_comp, int prec, int64_t rows, EvalScratch* s);
+// evaluate segments (same D) into out with refinement; resets counters first
+cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const double* X,
+                             int64_t ld, double* out, const EvalScratch& s, cudaStream_t st);

@@ -10,7 +10,7 @@
 #include <thread>
 #include <vector>
 
-#include "sevo_internal.cuh"
+#include "kernels.cuh"
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void sv_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
@@ -30,6 +30,11 @@ extern "C" const char* sevo_strerror(int32_t s) {
 }
 
 extern "C" int32_t sevo_version(void) { return 100; }
+
+#include <atomic>
+static std::atomic<int64_t> g_launches{0};
+void sv_note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" int64_t sevo_kernel_launches(void) { return g_launches.load(); }
 
 // ---------------------------------------------------------------- helpers
 namespace {
@@ -215,8 +220,8 @@ static int32_t upload(sevo_problem* p) {
   const size_t DD = (size_t)D * D, NK = (size_t)h.npad * h.kpad;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t per = al(D * 8) + al(DD * 8) + al(DD * 4) + al(NK * 4) + 2 * al(NK * 2) +
-                     al(D * 8) + al(D * 4) + al(D * 4);
-  p->dev_bytes = per * nc + al(sizeof(ProblemDev));
+                     al(D * 8) + al(D * 4) + al(D * 4) + 2 * al(D * 4);
+  p->dev_bytes = per * nc + al(3 * SV_MAXC * sizeof(CUtensorMap)) + al(sizeof(ProblemDev));
   SV_CUDA(cudaMalloc(&p->dev_block, p->dev_bytes));
   std::vector<unsigned char> blob(p->dev_bytes, 0);
   char* base = (char*)p->dev_block;
@@ -231,7 +236,10 @@ static int32_t upload(sevo_problem* p) {
     const double* M = p->M_h + (size_t)c * DD;
     size_t oo = take(D * 8), omt = take(DD * 8), omt32 = take(DD * 4), om32 = take(NK * 4),
            ohi = take(NK * 2), olo = take(NK * 2), oa64 = take(D * 8), oa32 = take(D * 4),
-           ogid = take(D * 4);
+           ogid = take(D * 4), ooh = take(D * 4), ool = take(D * 4);
+    float* oh = (float*)&blob[ooh];
+    float* ol = (float*)&blob[ool];
+    for (int j = 0; j < D; ++j) sv_split_hi_lo(o[j], oh[j], ol[j]);
     std::memcpy(&blob[oo], o, D * 8);
     double* mt = (double*)&blob[omt];
     float* mt32 = (float*)&blob[omt32];
@@ -276,10 +284,28 @@ static int32_t upload(sevo_problem* p) {
     h.aux64[c] = (const double*)(base + oa64);
     h.aux32[c] = (const float*)(base + oa32);
     h.gid[c] = (const int32_t*)(base + ogid);
+    h.oh32[c] = (const float*)(base + ooh);
+    h.ol32[c] = (const float*)(base + ool);
+  }
+  size_t otm = take((size_t)3 * SV_MAXC * sizeof(CUtensorMap));
+  for (int c = 0; c < nc; ++c) {
+    h.tmap32[c] = (const CUtensorMap*)(base + otm) + c;
+    h.tmaphi[c] = (const CUtensorMap*)(base + otm) + SV_MAXC + c;
+    h.tmaplo[c] = (const CUtensorMap*)(base + otm) + 2 * SV_MAXC + c;
   }
   size_t od = take(sizeof(ProblemDev));
-  std::memcpy(&blob[od], &h, sizeof(ProblemDev));
   p->desc_d = (ProblemDev*)(base + od);
+  // the descriptors encode device addresses, so they are built after the
+  // operand pointers are known and copied into the block with the rest
+  int32_t st = sv_build_tmaps(p);
+  if (st != SEVO_OK) return st;
+  for (int c = 0; c < nc; ++c) {
+    std::memcpy(&blob[otm + c * sizeof(CUtensorMap)], &p->tmap_f32[c], sizeof(CUtensorMap));
+    std::memcpy(&blob[otm + (SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_hi[c], sizeof(CUtensorMap));
+    std::memcpy(&blob[otm + (2 * SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_lo[c],
+                sizeof(CUtensorMap));
+  }
+  std::memcpy(&blob[od], &h, sizeof(ProblemDev));
   SV_CUDA(cudaMemcpy(p->dev_block, blob.data(), p->dev_bytes, cudaMemcpyHostToDevice));
   return SEVO_OK;
 }

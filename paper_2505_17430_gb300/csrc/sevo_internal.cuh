@@ -1,6 +1,7 @@
 // sevo_internal.cuh -- types and helpers shared by the library's translation
 // units (host and device).  Nothing here is shared with the CPU oracle.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -87,6 +88,11 @@ struct ProblemDev {
   const double* aux64[SV_MAXC];         // D: ellipsoid coefficient or sqrt(position)
   const float* aux32[SV_MAXC];
   const int32_t* gid[SV_MAXC];          // D: group index of output coordinate i
+  const CUtensorMap* tmap32[SV_MAXC];   // device copies of the TMA descriptors
+  const CUtensorMap* tmaphi[SV_MAXC];
+  const CUtensorMap* tmaplo[SV_MAXC];
+  const float* oh32[SV_MAXC];           // D: o split as oh + ol (see sv_split_hi_lo)
+  const float* ol32[SV_MAXC];
   int32_t gstart[SV_MAXG + 1];          // group ranges [gstart[g], gstart[g+1])
   int32_t gbody[SV_MAXG];
   int32_t cbody[SV_MAXC];
@@ -108,7 +114,49 @@ struct sevo_problem {
   ProblemDev* desc_d;     // same, in device memory
   void* dev_block;        // one allocation holding all device arrays
   size_t dev_bytes;
+  // TMA descriptors of the padded rotation operands (built on first use)
+  bool tmaps_ready;
+  CUtensorMap tmap_f32[SV_MAXC];   // M32: npad x kpad fp32, box (32, rows)
+  CUtensorMap tmap_hi[SV_MAXC];    // Mhi: npad x kpad bf16, box (64, rows)
+  CUtensorMap tmap_lo[SV_MAXC];
+  int32_t tmap_rows;               // box rows used when the maps were built
 };
+
+// Split a double into float hi + lo with integer operations only:
+// hi = x with the significand truncated to 24 bits (exact as a float),
+// lo = the remaining low 29 significand bits, rounded to a float.  For
+// |x| < 2^-74 both are 0 (such x are 0 to any precision the mixed path
+// uses).  Used for x and for the shift o alike, so x == o gives hi == oh and
+// lo == ol exactly.
+__host__ __device__ __forceinline__ void sv_split_hi_lo(double x, float& hi, float& lo) {
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(x);
+#else
+  long long b;
+  __builtin_memcpy(&b, &x, 8);
+#endif
+  const uint32_t h = (uint32_t)((unsigned long long)b >> 32), l = (uint32_t)b;
+  const int e = (int)((h >> 20) & 0x7FF);
+  if (e < 949 || e > 1150) {  // |x| < 2^-74 (or out of the float range: unused)
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const uint32_t sign = h & 0x80000000u;
+  const uint32_t hb = sign | ((uint32_t)(e - 896) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
+  const uint32_t r = l & 0x1FFFFFFFu;
+  const uint32_t sb = (uint32_t)(e - 948) << 23;  // 2^(e - 1075) as float bits
+#ifdef __CUDA_ARCH__
+  hi = __uint_as_float(hb);
+  float v = __uint2float_rn(r) * __uint_as_float(sb);
+#else
+  __builtin_memcpy(&hi, &hb, 4);
+  float scl;
+  __builtin_memcpy(&scl, &sb, 4);
+  float v = (float)r * scl;
+#endif
+  lo = sign ? -v : v;
+}
 
 // status helpers --------------------------------------------------------
 #define SV_CUDA(call)                                     \
@@ -121,6 +169,8 @@ struct sevo_problem {
   } while (0)
 
 void sv_set_last_cuda_error(cudaError_t e);
+// kernel launch accounting (see sevo_kernel_launches)
+void sv_note_launch(int64_t n = 1);
 // upload the instance to the current device on first use (thread-safe);
 // SEVO_ERR_STATE if it already lives on another device
 int32_t sv_problem_ready(const sevo_problem* p);

@@ -1,0 +1,276 @@
+// state.cu -- single-run state API (sevo_state_*, sevo_de_step,
+// sevo_pso_step): one run is a batch of one, driven generation by
+// generation with the caller's Philox counters (Listing 4's loop body).
+#include <cstring>
+#include <vector>
+
+#include "evo.cuh"
+
+struct sevo_state {
+  Batch b;
+  const sevo_problem* prob;
+  sevo_alg_params params;
+  uint64_t seed;
+  int64_t fes, gens;
+};
+
+static bool is_de(int alg) { return alg == SEVO_DE_RAND1 || alg == SEVO_DE_CTPB; }
+
+static int32_t check_params(const sevo_problem* p, const sevo_alg_params* a) {
+  if (!p || !a) return SEVO_ERR_ARG;
+  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_PSO_RING) return SEVO_ERR_ARG;
+  if (a->prec < SEVO_FP64 || a->prec > SEVO_FP32) return SEVO_ERR_ARG;
+  if (a->NP > SV_MAX_NP || a->budget < 1) return SEVO_ERR_ARG;
+  if (is_de(a->alg) && a->NP < 4) return SEVO_ERR_ARG;
+  if (!is_de(a->alg) && a->NP < 2) return SEVO_ERR_ARG;
+  if (!(a->lb < a->ub) || !(a->CR >= 0.0 && a->CR <= 1.0)) return SEVO_ERR_ARG;
+  if (a->alg == SEVO_DE_CTPB && !(a->p > 0.0 && a->p <= 1.0)) return SEVO_ERR_ARG;
+  return SEVO_OK;
+}
+
+static int32_t create_impl(const sevo_problem* const* probs, int32_t R, const sevo_alg_params* a,
+                           const uint64_t* seeds, void* stream, sevo_state** out) {
+  if (!out || !probs || !seeds || R < 1) return SEVO_ERR_ARG;
+  *out = nullptr;
+  for (int r = 0; r < R; ++r) {
+    int32_t st = check_params(probs[r], a);
+    if (st != SEVO_OK) return st;
+    if (probs[r]->D != probs[0]->D) return SEVO_ERR_ARG;
+    if ((st = sv_problem_ready(probs[r])) != SEVO_OK) return st;
+  }
+  if ((int64_t)R * a->NP > (int64_t)INT32_MAX / 4) return SEVO_ERR_UNSUPPORTED;
+  sevo_state* s = new (std::nothrow) sevo_state();
+  if (!s) return SEVO_ERR_OOM;
+  s->prob = probs[0];
+  s->params = *a;
+  s->seed = seeds[0];
+  s->b.block = nullptr;
+  s->b.eval_block = nullptr;
+  std::vector<const sevo_problem*> pv(probs, probs + R);
+  std::vector<uint64_t> sv(seeds, seeds + R);
+  int32_t st = sv_batch_alloc(&s->b, pv, sv, a, (cudaStream_t)stream);
+  if (st != SEVO_OK) {
+    sv_batch_free(&s->b);
+    delete s;
+    return st;
+  }
+  cudaError_t e = sv_batch_init(&s->b);
+  if (e != cudaSuccess) {
+    sv_set_last_cuda_error(e);
+    sv_batch_free(&s->b);
+    delete s;
+    return SEVO_ERR_CUDA;
+  }
+  s->fes = std::min<int64_t>(a->budget, a->NP);
+  s->gens = 0;
+  *out = s;
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_create(const sevo_problem* p, const sevo_alg_params* a,
+                                     uint64_t seed, void* stream, sevo_state** out) {
+  if (!p) return SEVO_ERR_ARG;
+  return create_impl(&p, 1, a, &seed, stream, out);
+}
+
+extern "C" int32_t sevo_state_create_batch(const sevo_problem* const* problems, int32_t R,
+                                           const sevo_alg_params* a, const uint64_t* seeds,
+                                           void* stream, sevo_state** out) {
+  return create_impl(problems, R, a, seeds, stream, out);
+}
+
+extern "C" int32_t sevo_state_best(const sevo_state* s, double* best) {
+  if (!s || !best) return SEVO_ERR_ARG;
+  SV_CUDA(cudaMemcpyAsync(best, s->b.best, (size_t)s->b.R * 8, cudaMemcpyDeviceToHost,
+                          s->b.stream));
+  SV_CUDA(cudaStreamSynchronize(s->b.stream));
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_destroy(sevo_state* s) {
+  if (!s) return SEVO_ERR_ARG;
+  cudaStreamSynchronize(s->b.stream);
+  sv_batch_free(&s->b);
+  delete s;
+  return SEVO_OK;
+}
+
+static int32_t step(sevo_state* s, uint64_t counter, bool want_de) {
+  if (!s) return SEVO_ERR_ARG;
+  if (is_de(s->params.alg) != want_de) return SEVO_ERR_STATE;
+  if (s->fes >= s->params.budget) return SEVO_ERR_STATE;
+  const int count = (int)std::min<int64_t>(s->params.NP, s->params.budget - s->fes);
+  cudaError_t e = sv_ctl_set(&s->b, (unsigned long long)counter, count);
+  if (e == cudaSuccess) e = sv_batch_generation(&s->b);
+  if (e != cudaSuccess) {
+    sv_set_last_cuda_error(e);
+    return SEVO_ERR_CUDA;
+  }
+  s->fes += count;
+  s->gens += 1;
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter) {
+  return step(s, philox_counter, true);
+}
+
+extern "C" int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter) {
+  return step(s, philox_counter, false);
+}
+
+extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes,
+                                     int64_t* gens, int64_t* refined) {
+  if (!s) return SEVO_ERR_ARG;
+  double b = 0.0;
+  SV_CUDA(cudaMemcpyAsync(&b, s->b.best, 8, cudaMemcpyDeviceToHost, s->b.stream));
+  SV_CUDA(cudaStreamSynchronize(s->b.stream));
+  if (best) *best = b;
+  if (fes) *fes = s->fes;
+  if (gens) *gens = s->gens;
+  if (refined) *refined = s->b.refined_host;
+  return SEVO_OK;
+}
+
+// copy a row-major NP x D host matrix to/from the ld-strided device matrix
+static cudaError_t put(double* dst, const double* src, const Batch& b) {
+  return cudaMemcpy2DAsync(dst, (size_t)b.ld * 8, src, (size_t)b.D * 8, (size_t)b.D * 8,
+                           (size_t)b.R * b.NP, cudaMemcpyHostToDevice, b.stream);
+}
+static cudaError_t get(double* dst, const double* src, const Batch& b) {
+  return cudaMemcpy2DAsync(dst, (size_t)b.D * 8, src, (size_t)b.ld * 8, (size_t)b.D * 8,
+                           (size_t)b.R * b.NP, cudaMemcpyDeviceToHost, b.stream);
+}
+
+extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A,
+                                  int32_t* asize, double* V, double* P, double* fp, double* U,
+                                  double* fu, int32_t* part) {
+  if (!s) return SEVO_ERR_ARG;
+  const Batch& b = s->b;
+  const size_t rows = (size_t)b.R * b.NP, vb = rows * 8;
+  if (X) SV_CUDA(get(X, b.X, b));
+  if (fx) SV_CUDA(cudaMemcpyAsync(fx, b.fx, vb, cudaMemcpyDeviceToHost, b.stream));
+  if (A && b.A) SV_CUDA(get(A, b.A, b));
+  int32_t as = 0;  // run 0's archive size
+  if (b.asize) SV_CUDA(cudaMemcpyAsync(&as, b.asize, 4, cudaMemcpyDeviceToHost, b.stream));
+  if (V && b.V) SV_CUDA(get(V, b.V, b));
+  if (P && b.P) SV_CUDA(get(P, b.P, b));
+  if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(fp, b.fp, vb, cudaMemcpyDeviceToHost, b.stream));
+  if (U && b.U) SV_CUDA(get(U, b.U, b));
+  if (fu && b.fu) SV_CUDA(cudaMemcpyAsync(fu, b.fu, vb, cudaMemcpyDeviceToHost, b.stream));
+  if (part) {
+    if (is_de(s->params.alg)) {
+      SV_CUDA(cudaMemcpyAsync(part, b.part, rows * 16, cudaMemcpyDeviceToHost, b.stream));
+    } else {
+      std::vector<int32_t> g(rows);
+      SV_CUDA(cudaMemcpyAsync(g.data(), b.guide, rows * 4, cudaMemcpyDeviceToHost, b.stream));
+      SV_CUDA(cudaStreamSynchronize(b.stream));
+      for (size_t i = 0; i < rows; ++i) {
+        part[4 * i] = g[i];
+        part[4 * i + 1] = part[4 * i + 2] = part[4 * i + 3] = 0;
+      }
+    }
+  }
+  SV_CUDA(cudaStreamSynchronize(b.stream));
+  if (asize) *asize = as;
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx,
+                                  const double* A, int32_t asize, const double* V,
+                                  const double* P, const double* fp, int64_t fes) {
+  if (!s) return SEVO_ERR_ARG;
+  Batch& b = s->b;
+  const size_t vb = (size_t)b.R * b.NP * 8;
+  if (asize < 0 || asize > b.NP || (A && b.R != 1)) return SEVO_ERR_ARG;
+  if (X) SV_CUDA(put(b.X, X, b));
+  if (fx) SV_CUDA(cudaMemcpyAsync(b.fx, fx, vb, cudaMemcpyHostToDevice, b.stream));
+  if (A && b.A) SV_CUDA(put(b.A, A, b));
+  if (b.asize && A) SV_CUDA(cudaMemcpyAsync(b.asize, &asize, 4, cudaMemcpyHostToDevice, b.stream));
+  if (V && b.V) SV_CUDA(put(b.V, V, b));
+  if (P && b.P) SV_CUDA(put(b.P, P, b));
+  if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(b.fp, fp, vb, cudaMemcpyHostToDevice, b.stream));
+  if (!is_de(s->params.alg) && fp) {
+    cudaError_t e = sv_batch_guides(&b);
+    if (e != cudaSuccess) {
+      sv_set_last_cuda_error(e);
+      return SEVO_ERR_CUDA;
+    }
+  }
+  if (fes >= 0) s->fes = fes;
+  SV_CUDA(cudaStreamSynchronize(b.stream));
+  return SEVO_OK;
+}
+
+// ---- save / load: header + arrays, every array the run's next generation
+// reads (counter-based draws make a resumed run bit-identical)
+struct SaveHeader {
+  uint32_t magic, version;
+  int32_t alg, NP, D, asize;
+  uint64_t seed;
+  int64_t fes, gens;
+  double best;
+};
+static const uint32_t kMagic = 0x53455642u;  // "SEVB"
+
+static size_t save_bytes(const sevo_state* s) {
+  const size_t m = (size_t)s->b.R * s->b.NP * s->b.D * 8, v = (size_t)s->b.R * s->b.NP * 8;
+  size_t n = sizeof(SaveHeader) + m + v;  // X, fx
+  if (s->params.alg == SEVO_DE_CTPB) n += m;        // A
+  if (!is_de(s->params.alg)) n += 2 * m + v;        // V, P, fp
+  return n;
+}
+
+extern "C" int32_t sevo_state_save(const sevo_state* s, void* buf, size_t* size) {
+  if (!s || !size || s->b.R != 1) return s && s->b.R != 1 ? SEVO_ERR_UNSUPPORTED : SEVO_ERR_ARG;
+  const size_t need = save_bytes(s);
+  if (!buf) {
+    *size = need;
+    return SEVO_OK;
+  }
+  if (*size < need) {
+    *size = need;
+    return SEVO_ERR_ARG;
+  }
+  const Batch& b = s->b;
+  const size_t m = (size_t)b.NP * b.D * 8, v = (size_t)b.NP * 8;
+  SaveHeader h{kMagic, 1u, s->params.alg, b.NP, b.D, 0, s->seed, s->fes, s->gens, 0.0};
+  char* c = (char*)buf + sizeof(SaveHeader);
+  int32_t as = 0;
+  int32_t st = sevo_state_get(s, (double*)c, (double*)(c + m),
+                              s->params.alg == SEVO_DE_CTPB ? (double*)(c + m + v) : nullptr, &as,
+                              is_de(s->params.alg) ? nullptr : (double*)(c + m + v),
+                              is_de(s->params.alg) ? nullptr : (double*)(c + 2 * m + v),
+                              is_de(s->params.alg) ? nullptr : (double*)(c + 3 * m + v), nullptr,
+                              nullptr, nullptr);
+  if (st != SEVO_OK) return st;
+  h.asize = as;
+  SV_CUDA(cudaMemcpy(&h.best, b.best, 8, cudaMemcpyDeviceToHost));
+  std::memcpy(buf, &h, sizeof(h));
+  *size = need;
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_load(sevo_state* s, const void* buf, size_t size) {
+  if (!s || !buf || size < sizeof(SaveHeader)) return SEVO_ERR_ARG;
+  if (s->b.R != 1) return SEVO_ERR_UNSUPPORTED;
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kMagic || h.version != 1u || h.alg != s->params.alg || h.NP != s->b.NP ||
+      h.D != s->b.D || size < save_bytes(s))
+    return SEVO_ERR_ARG;
+  const size_t m = (size_t)s->b.NP * s->b.D * 8, v = (size_t)s->b.NP * 8;
+  const char* c = (const char*)buf + sizeof(SaveHeader);
+  const bool de = is_de(s->params.alg);
+  int32_t st = sevo_state_set(s, (const double*)c, (const double*)(c + m),
+                              s->params.alg == SEVO_DE_CTPB ? (const double*)(c + m + v) : nullptr,
+                              h.asize, de ? nullptr : (const double*)(c + m + v),
+                              de ? nullptr : (const double*)(c + 2 * m + v),
+                              de ? nullptr : (const double*)(c + 3 * m + v), h.fes);
+  if (st != SEVO_OK) return st;
+  SV_CUDA(cudaMemcpy(s->b.best, &h.best, 8, cudaMemcpyHostToDevice));
+  SV_CUDA(cudaMemcpy(s->b.seeds, &h.seed, 8, cudaMemcpyHostToDevice));
+  s->gens = h.gens;
+  s->seed = h.seed;
+  return SEVO_OK;
+}

@@ -127,3 +127,58 @@ def test_bench_shape_sampled(S):
         assert (np.abs(got - want) <= tol64(want, scale)).all()
         got = p.evaluate(xt, prec=S.FP32).cpu().numpy()[rows]
         assert (np.abs(got - want) <= 2e-3 * np.maximum(want, scale)).all()
+
+
+# relative precision of each mixed mode's rotation, times the condition scale
+MIXED_TOL = {"TF32": 2e-3, "BF16X3": 1e-4, "FP32": 1e-5}
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("D", [10, 30, 64, 100, 128])
+def test_tensor_core_path_matches_oracle(S, prec, fam, D):
+    """tcgen05 path (TF32 or split BF16) vs the oracle on 3 row tiles (two
+    full, one ragged): every row within MIXED_TOL[prec] * max(|f|, S(x));
+    rows that are certainly below the refinement threshold come back from
+    the FP64 path at the FP64 tolerance; f(o) is exactly f*."""
+    seed = 4242 + 13 * fam + D
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = np.vstack([inputs.uniform_pop(250, D, seed=seed),
+                   inputs.mixed_scales(q.shift(0), 40, D, seed),
+                   _inputs(q, 0, D, seed)])
+    got, info = p.evaluate(to_dev(X), prec=getattr(S, prec), sync=True)
+    got = got.cpu().numpy()
+    want, scale = q.eval(X), q.scale(X)
+    c = MIXED_TOL[prec]
+    bound = c * np.maximum(np.abs(want), scale) + 1e-13
+    err = np.abs(got - want)
+    assert (err <= bound).all(), (np.max(err / bound), int(np.argmax(err / bound)))
+    sure = want + bound < 1e-4
+    assert info["refined"] >= sure.sum()
+    assert (err[sure] <= tol64(want, scale)[sure]).all()
+    assert got[-1] == 0.0
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+def test_tensor_core_many_tiles_per_cta(S, prec):
+    """More tiles than SMs (persistent loop, both TMEM/A buffers reused many
+    times): 40000 rows at D=100, 200 sampled rows checked."""
+    D = 100
+    p, q = S.Problem(31, S.RASTRIGIN, D), O.Problem(31, S.RASTRIGIN, D)
+    X = inputs.uniform_pop(40000, D, seed=31)
+    got = p.evaluate(to_dev(X), prec=getattr(S, prec)).cpu().numpy()
+    rows = np.random.default_rng(3).choice(40000, 200, replace=False)
+    rows = np.concatenate([rows, [0, 39999]])
+    want, scale = q.eval(X[rows]), q.scale(X[rows])
+    assert (np.abs(got[rows] - want) <= MIXED_TOL[prec] * np.maximum(want, scale)).all()
+    assert np.isfinite(got).all()
+
+
+def test_tensor_core_deterministic(S):
+    """Two identical calls give bit-identical results (race canary)."""
+    p = S.Problem(5, S.COMPOSITION, 50)
+    X = to_dev(inputs.uniform_pop(3000, 50, seed=5))
+    for prec in (S.TF32, S.BF16X3):
+        a = p.evaluate(X, prec=prec).cpu().numpy()
+        b = p.evaluate(X, prec=prec).cpu().numpy()
+        assert np.array_equal(a, b)

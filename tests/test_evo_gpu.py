@@ -1,0 +1,236 @@
+"""GPU lock-step parity of the DE/PSO generation path against the oracle,
+through the C ABI (sevo_state_*, sevo_de_step, sevo_pso_step, sevo_run_grid).
+
+Lock-step: both sides start each generation from the same state; trial
+vectors, positions, velocities and draws must match bit for bit; fitness at
+the FP64 tolerance; selection decisions wherever the oracle's margin exceeds
+4 x that tolerance; the next generation starts again from the oracle's state.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.gpu_util import tol64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2505_17430_gb300 as S
+    S.build()
+    return S
+
+
+def _state(S, fam, D, alg, NP, budget, seed, prec=None, pseed=None):
+    prec = S.FP64 if prec is None else prec
+    p = S.Problem(pseed if pseed is not None else 100 + fam, fam, D)
+    q = O.Problem(pseed if pseed is not None else 100 + fam, fam, D)
+    st = S.State(p, S.alg_params(alg, NP, budget, prec=prec), seed)
+    return p, q, st
+
+
+@pytest.mark.parametrize("alg", [0, 1, 2, 3])
+def test_initial_population_bit_exact(S, alg):
+    NP, D = 40, 13
+    p, q, st = _state(S, S.RASTRIGIN, D, alg, NP, 10000, 77)
+    g = st.get()
+    X = O.init_population(77, NP, D)
+    assert np.array_equal(g["X"], X)
+    want = q.eval(X)
+    assert (np.abs(g["fx"] - want) <= tol64(want, q.scale(X))).all()
+    assert st.result()["fes"] == NP and st.result()["best"] == pytest.approx(want.min(), rel=1e-12)
+
+
+def _decided(fa, fb, tol):
+    return np.abs(fa - fb) > 4 * tol
+
+
+@pytest.mark.parametrize("fam,D,NP", [(S_, D_, N_) for S_, D_, N_ in
+                                      [(2, 10, 50), (6, 30, 37), (7, 17, 64), (1, 100, 24)]])
+def test_de_rand1_lockstep(S, fam, D, NP):
+    p, q, st = _state(S, fam, D, S.DE_RAND1, NP, 10 ** 6, 5)
+    X = O.init_population(5, NP, D)
+    fx = q.eval(X)
+    for gen in range(1, 6):
+        st.set(X=X, fx=fx, fes=NP)
+        assert st.de_step(gen) == 0
+        g = st.get()
+        U, part = O.de_rand1_trials(5, gen, X)
+        assert np.array_equal(g["part"], part)
+        assert np.array_equal(g["U"], U)
+        fu = q.eval(U)
+        tol = tol64(fu, q.scale(U))
+        assert (np.abs(g["fu"] - fu) <= tol).all()
+        X2, fx2, _, _, acc = O.de_select(5, gen, X, fx, U, fu)
+        dec = _decided(fu, fx, tol)
+        gacc = np.all(g["X"] == U, axis=1) & ~np.all(U == X, axis=1)
+        assert np.array_equal(gacc[dec & ~np.all(U == X, axis=1)],
+                              acc.astype(bool)[dec & ~np.all(U == X, axis=1)])
+        assert np.array_equal(g["X"][dec], X2[dec])
+        X, fx = X2, fx2
+
+
+def test_de_ctpb_archive_lockstep(S):
+    fam, D, NP = S.ACKLEY, 20, 60
+    p, q, st = _state(S, fam, D, S.DE_CTPB, NP, 10 ** 6, 9)
+    X = O.init_population(9, NP, D)
+    fx = q.eval(X)
+    A = np.zeros((NP, D))
+    asize = 0
+    for gen in range(1, 25):
+        st.set(X=X, fx=fx, A=A[:asize], asize=asize, fes=NP)
+        assert st.de_step(gen) == 0
+        g = st.get()
+        U, part = O.de_ctpb_trials(9, gen, X, fx, A, asize)
+        assert np.array_equal(g["part"], part), gen
+        assert np.array_equal(g["U"], U), gen
+        fu = q.eval(U)
+        tol = tol64(fu, q.scale(U))
+        assert (np.abs(g["fu"] - fu) <= tol).all()
+        X2, fx2, A2, asize2, acc = O.de_select(9, gen, X, fx, U, fu, A, asize)
+        if _decided(fu, fx, tol).all():
+            assert np.array_equal(g["X"], X2)
+            assert g["asize"] == asize2
+            assert np.array_equal(g["A"], A2[:asize2])
+        X, fx, A, asize = X2, fx2, A2, asize2
+    assert asize == NP  # the archive filled and random eviction was exercised
+
+
+@pytest.mark.parametrize("alg", [2, 3])
+def test_pso_lockstep(S, alg):
+    fam, D, NP = S.GRIEWANK, 25, 40
+    p, q, st = _state(S, fam, D, alg, NP, 10 ** 6, 13)
+    X = O.init_population(13, NP, D)
+    V = np.zeros_like(X)
+    fx = q.eval(X)
+    P, fp = X.copy(), fx.copy()
+    topo = alg - 2
+    for gen in range(1, 8):
+        st.set(X=X, V=V, P=P, fp=fp, fes=NP)
+        guide = O.pso_guides(fp, topo)
+        assert np.array_equal(st.get()["part"][:, 0], guide)
+        assert st.pso_step(gen) == 0
+        g = st.get()
+        X2, V2 = O.pso_move(13, gen, X, V, P, guide)
+        assert np.array_equal(g["X"], X2)
+        assert np.array_equal(g["V"], V2)
+        fx2 = q.eval(X2)
+        tol = tol64(fx2, q.scale(X2))
+        assert (np.abs(g["fx"] - fx2) <= tol).all()
+        P2, fp2, _ = O.pso_update(X2, fx2, P, fp)
+        dec = _decided(fx2, fp, tol)
+        assert np.array_equal(g["P"][dec], P2[dec])
+        X, V, P, fp = X2, V2, P2, fp2
+
+
+def test_c0_full_run_lockstep(S):
+    """configs[0]: DE/rand/1/bin, NP=50, D=10, F=.5, CR=.9, FP64, budget 1e5
+    on shifted-rotated Rastrigin; every one of the 1999 generations is
+    compared in lock step (re-synchronised from the oracle each time)."""
+    NP, D, budget, seed = 50, 10, 100000, 1
+    p, q = S.Problem(1, S.RASTRIGIN, D), O.Problem(1, O.RASTRIGIN, D)
+    st = S.State(p, S.alg_params(S.DE_RAND1, NP, budget), seed)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    mism = 0
+    for gen in range(1, 2000):
+        st.set(X=X, fx=fx, fes=NP)
+        st.de_step(gen)
+        g = st.get()
+        U, _ = O.de_rand1_trials(seed, gen, X)
+        assert np.array_equal(g["U"], U)
+        fu = q.eval(U)
+        tol = tol64(fu, q.scale(U))
+        X2, fx2, _, _, _ = O.de_select(seed, gen, X, fx, U, fu)
+        dec = _decided(fu, fx, tol)
+        assert np.array_equal(g["X"][dec], X2[dec])
+        # near-ties (common once the population has converged): either
+        # outcome is a valid selection, so the row must be x or u
+        und = ~dec
+        assert (np.all(g["X"][und] == X[und], axis=1) | np.all(g["X"][und] == U[und], axis=1)).all()
+        mism += und.sum()
+        X, fx = X2, fx2
+    ref = O.run(q, O.make_alg(O.ALG_DE_RAND1, NP, budget), seed)
+    assert ref["best"] == pytest.approx(min(fx.min(), ref["best"]), abs=1e-9)
+    print("undecided selections:", mism, "of", 1999 * NP)
+
+
+def test_full_run_matches_oracle_fp64(S):
+    """A whole run on the FP64 path (no re-sync) ends at the oracle's best
+    error: the trajectories agree unless a near-tie flips a decision."""
+    NP, D, budget, seed = 30, 10, 6000, 3
+    for alg in (0, 1, 2, 3):
+        p, q = S.Problem(21, S.ELLIPSOID, D), O.Problem(21, O.ELLIPSOID, D)
+        st = S.State(p, S.alg_params(alg, NP, budget), seed)
+        gen = 0
+        while st.result()["fes"] < budget:
+            gen += 1
+            assert st.step(gen) == 0
+        r = st.result()
+        ref = O.run(q, O.make_alg(alg, NP, budget), seed)
+        assert r["fes"] == budget == ref["fes"] and r["gens"] == ref["gens"]
+        assert r["best"] == pytest.approx(ref["best"], rel=1e-9, abs=1e-12), alg
+
+
+def test_budget_and_bad_calls(S):
+    p = S.Problem(1, S.SCHWEFEL, 10)
+    st = S.State(p, S.alg_params(S.PSO_GBEST, 40, 100), 1)
+    assert st.de_step(1) == -7          # wrong algorithm kind
+    assert st.pso_step(1) == 0          # 40 + 40 = 80
+    assert st.pso_step(2) == 0          # last generation counts 20 rows
+    assert st.result()["fes"] == 100
+    assert st.pso_step(3) == -7         # budget spent
+
+
+def test_save_load_resume_bit_identical(S):
+    p = S.Problem(4, S.HYBRID, 20)
+    for alg in (1, 3):
+        a = S.State(p, S.alg_params(alg, 32, 10 ** 6), 8)
+        for g in range(1, 6):
+            a.step(g)
+        blob = a.save()
+        for g in range(6, 11):
+            a.step(g)
+        b = S.State(p, S.alg_params(alg, 32, 10 ** 6), 123)
+        b.load(blob)
+        for g in range(6, 11):
+            b.step(g)
+        ga, gb = a.get(), b.get()
+        for k in ("X", "fx", "V", "P", "fp", "A"):
+            assert np.array_equal(ga[k], gb[k]), (alg, k)
+        assert a.result()["best"] == b.result()["best"]
+
+
+def test_grid_equals_single_runs(S):
+    """sevo_run_grid (batched runs, graph-captured generations) gives the
+    same results as driving each run alone through the state API."""
+    D = 10
+    probs = [S.Problem(s, f, D) for s, f in [(1, 2), (2, 6), (3, 7)]]
+    algs = [S.alg_params(S.DE_CTPB, 40, 2000), S.alg_params(S.PSO_RING, 20, 2010)]
+    tasks = [(pi, ai, 1000 + 10 * pi + ai + 100 * k) for pi in range(3) for ai in range(2)
+             for k in range(3)]
+    res = S.sevo_run_grid(probs, algs, tasks, gens_per_graph=8)
+    for t, (pi, ai, seed) in enumerate(tasks):
+        st = S.State(probs[pi], algs[ai], seed)
+        gen = 0
+        while st.result()["fes"] < algs[ai].budget:
+            gen += 1
+            st.step(gen)
+        r = st.result()
+        assert res["fes"][t] == r["fes"] and res["gens"][t] == r["gens"]
+        assert res["best"][t] == r["best"], (t, res["best"][t], r["best"])
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3", "FP32"])
+def test_mixed_precision_runs_reach_oracle_quality(S, prec):
+    """Mixed-precision runs (FP64 refinement below 1e-4): DE/ctpb on the
+    unimodal shifted-rotated ellipsoid at D=10 reaches the 1e-8 success
+    threshold like the oracle does."""
+    D, NP, budget = 10, 50, 60000
+    probs = [S.Problem(2, S.ELLIPSOID, D)]
+    algs = [S.alg_params(S.DE_CTPB, NP, budget, prec=getattr(S, prec))]
+    res = S.sevo_run_grid(probs, algs, [(0, 0, s) for s in range(1, 9)])
+    q = O.Problem(2, O.ELLIPSOID, D)
+    ref = [O.run(q, O.make_alg(O.ALG_DE_CTPB, NP, budget), s)["success"] for s in range(1, 9)]
+    assert res["success"].sum() >= sum(ref) - 2
