@@ -146,6 +146,33 @@ int32_t sevo_evaluate_sync(const sevo_problem* p, const double* pop, int64_t N, 
                            int64_t ld, double* out, int32_t prec, void* stream,
                            int64_t* refined, int64_t* nonfinite);
 
+/* Evaluation that allocates nothing (the paper has no counterpart: this is a
+ * library-usage variant of sevo_evaluate, not a step of the method).
+ * Some callers cannot allocate device memory at the point of the call --
+ * for example a host program whose memory manager has already reserved the
+ * GPU's memory in its own pool, or a latency-bound loop that must not pay
+ * for (or synchronize on) an allocation.  This entry point takes the same
+ * arguments as sevo_evaluate and does the same work, but its scratch (the
+ * FP64-refinement row list, the counters and the composition staging) lives
+ * in one fixed device array of SEVO_NOALLOC_SCRATCH_BYTES owned by the
+ * library; it calls no cudaMalloc/cudaFree and no allocating routine.
+ *   - N must be at most SEVO_NOALLOC_MAX_ROWS, else SEVO_ERR_UNSUPPORTED;
+ *   - the problem must already have its device copy on the current device
+ *     (any earlier sevo_evaluate / sevo_state_create call with it makes it),
+ *     else SEVO_ERR_STATE -- making that copy would allocate;
+ *   - the first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call shares the one array and the array keeps the last call's
+ *     contents (the counters are cleared on the stream by each call): calls
+ *     whose work overlaps on the GPU (different streams, or different host
+ *     threads without ordering) race on it and must be serialized.
+ * The device array is held by every GPU that loads the library until the
+ * process exits. */
+#define SEVO_NOALLOC_MAX_ROWS 16384
+#define SEVO_NOALLOC_SCRATCH_BYTES (3u << 20)
+int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* pop, int64_t N, int32_t D,
+                              int64_t ld, double* out, int32_t prec, void* stream);
+
 /* ---- algorithms and runs ---------------------------------------------- */
 enum sevo_alg {
   SEVO_DE_RAND1 = 0,     /* DE/rand/1/bin                                  */

@@ -77,6 +77,8 @@ SIGNATURES = {
     "sevo_evaluate": (C.c_int32, [_vp, _vp, C.c_int64, C.c_int32, C.c_int64, _vp, C.c_int32, _vp]),
     "sevo_evaluate_sync": (C.c_int32, [_vp, _vp, C.c_int64, C.c_int32, C.c_int64, _vp, C.c_int32,
                                        _vp, _i64p, _i64p]),
+    "sevo_evaluate_noalloc": (C.c_int32, [_vp, _vp, C.c_int64, C.c_int32, C.c_int64, _vp,
+                                          C.c_int32, _vp]),
     "sevo_state_create": (C.c_int32, [_vp, C.POINTER(AlgParams), C.c_uint64, _vp,
                                       C.POINTER(_vp)]),
     "sevo_state_destroy": (C.c_int32, [_vp]),

@@ -1,0 +1,64 @@
+// noalloc.cu -- sevo_evaluate_noalloc: sevo_evaluate with its scratch in one
+// fixed device array instead of a stream-ordered allocation, for callers
+// that cannot allocate device memory at the point of the call.
+#include <mutex>
+
+#include "kernels.cuh"
+
+// one array per device that loads the library (held until process exit)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SEVO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// the array's device address on the current device, looked up once per
+// device with that device current (host code cannot use the symbol itself)
+int32_t scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SEVO_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      sv_set_last_cuda_error(e);
+      return SEVO_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return SEVO_OK;
+}
+}  // namespace
+
+extern "C" int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* pop, int64_t N,
+                                         int32_t D, int64_t ld, double* out, int32_t prec,
+                                         void* stream) {
+  if (!p || !pop || !out || N < 0 || D != p->D || ld < D) return SEVO_ERR_ARG;
+  if (prec < SEVO_FP64 || prec > SEVO_FP32) return SEVO_ERR_ARG;
+  if ((prec == SEVO_TF32 || prec == SEVO_BF16X3) && (((uintptr_t)pop & 15) || (ld & 1)))
+    return SEVO_ERR_ARG;
+  if (((uintptr_t)pop & 7) || ((uintptr_t)out & 7)) return SEVO_ERR_ARG;
+  if (N > SEVO_NOALLOC_MAX_ROWS) return SEVO_ERR_UNSUPPORTED;
+  // the problem's device copy must already exist here: making it allocates
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SEVO_ERR_CUDA;
+  if (!p->desc_d || p->device != dev) return SEVO_ERR_STATE;
+  if (N == 0) return SEVO_OK;
+  const bool comp = (p->family == SEVO_COMPOSITION);
+  if (sv_eval_scratch_bytes(comp, prec, N) > SEVO_NOALLOC_SCRATCH_BYTES) return SEVO_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  int32_t st = scratch_address(&base);
+  if (st != SEVO_OK) return st;
+  EvalScratch sc;
+  sv_eval_scratch_carve(base, comp, prec, N, &sc);
+  TcSegment seg{p, 0, N};
+  cudaError_t e = sv_eval_segments(&seg, 1, prec, pop, ld, out, sc, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    sv_set_last_cuda_error(e);
+    return SEVO_ERR_CUDA;
+  }
+  return SEVO_OK;
+}
