@@ -28,8 +28,8 @@
  *     default stream); calls that only launch work are asynchronous on that
  *     stream; calls that return results to the host synchronize it;
  *   - FP64 populations are row-major N x D with a leading dimension ld >= D
- *     (in elements); ld * 8 must be a multiple of 16 bytes for the tensor-core
- *     paths (ld even); row pointers must be 16-byte aligned.
+ *     (in elements) and 8-byte aligned; 16-byte aligned rows (ld even) let
+ *     the tensor-core path use vector loads.
  */
 #ifndef SEVO_H
 #define SEVO_H

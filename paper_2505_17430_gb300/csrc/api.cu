@@ -9,24 +9,25 @@
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t sv_eval_scratch_bytes(bool any_comp, int prec, int64_t rows) {
-  size_t b = al256((size_t)rows * 4) + al256(SV_COUNTERS_BYTES);
-  if (prec == SEVO_TF32 || prec == SEVO_BF16X3) b += al256(sv_eval_tc_scratch_bytes(any_comp, prec, rows));
-  return b;
+static size_t tc_bytes(int D, bool any_comp, int prec, int64_t rows) {
+  if (prec != SEVO_TF32 && prec != SEVO_BF16X3) return 0;
+  return D > 128 ? sv_eval_big_scratch_bytes(D, any_comp, prec, rows)
+                 : sv_eval_tc_scratch_bytes(any_comp, prec, rows);
 }
 
-void sv_eval_scratch_carve(void* base, bool any_comp, int prec, int64_t rows, EvalScratch* s) {
+size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
+  return al256((size_t)rows * 4) + al256(SV_COUNTERS_BYTES) + al256(tc_bytes(D, any_comp, prec, rows));
+}
+
+void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
+                           EvalScratch* s) {
   char* c = (char*)base;
   s->list = (int32_t*)c;
   c += al256((size_t)rows * 4);
   s->counters = (int32_t*)c;
   c += al256(SV_COUNTERS_BYTES);
-  s->tc = nullptr;
-  s->tc_bytes = 0;
-  if (prec == SEVO_TF32 || prec == SEVO_BF16X3) {
-    s->tc_bytes = sv_eval_tc_scratch_bytes(any_comp, prec, rows);
-    s->tc = s->tc_bytes ? (void*)c : nullptr;
-  }
+  s->tc_bytes = tc_bytes(D, any_comp, prec, rows);
+  s->tc = s->tc_bytes ? (void*)c : nullptr;
 }
 
 // one pass: mixed evaluation of every segment, then one FP64 re-evaluation
@@ -62,10 +63,16 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
         e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP32, X, ld, sg[k].row0, sg[k].nrows, out, aux, st);
         if (e != cudaSuccess) return e;
       }
-    } else {
+    } else if (sg[0].p->D <= 128) {
       e = sv_eval_tc_segments(sg, n, prec, X, ld, out, s.list, off, s.counters, nonfinite, s.tc,
                               s.tc_bytes, dev_err, st);
       if (e != cudaSuccess) return e;
+    } else {
+      for (int k = 0; k < n; ++k) {
+        e = sv_eval_tc_big(sg[k], prec, X, ld, out, s.list, off[k], s.counters + k, nonfinite,
+                           s.tc, s.tc_bytes, dev_err, st);
+        if (e != cudaSuccess) return e;
+      }
     }
     RefineTable RT;
     RT.nseg = n;
@@ -84,8 +91,6 @@ static int32_t check_eval_args(const sevo_problem* p, const double* pop, int64_t
   if (!p || !pop || !out || N < 0 || D != p->D || ld < D) return SEVO_ERR_ARG;
   if (prec < SEVO_FP64 || prec > SEVO_FP32) return SEVO_ERR_ARG;
   if (N > (int64_t)INT32_MAX) return SEVO_ERR_UNSUPPORTED;
-  if ((prec == SEVO_TF32 || prec == SEVO_BF16X3) && (((uintptr_t)pop & 15) || (ld & 1)))
-    return SEVO_ERR_ARG;
   if (((uintptr_t)pop & 7) || ((uintptr_t)out & 7)) return SEVO_ERR_ARG;
   return sv_problem_ready(p);
 }
@@ -102,11 +107,11 @@ static int32_t evaluate_impl(const sevo_problem* p, const double* pop, int64_t N
   }
   cudaStream_t s = (cudaStream_t)stream;
   const bool comp = (p->family == SEVO_COMPOSITION);
-  size_t bytes = sv_eval_scratch_bytes(comp, prec, N);
+  size_t bytes = sv_eval_scratch_bytes(p->D, comp, prec, N);
   void* base = nullptr;
   SV_CUDA(cudaMallocAsync(&base, bytes, s));
   EvalScratch sc;
-  sv_eval_scratch_carve(base, comp, prec, N, &sc);
+  sv_eval_scratch_carve(base, p->D, comp, prec, N, &sc);
   TcSegment seg{p, 0, N};
   cudaError_t e = sv_eval_segments(&seg, 1, prec, pop, ld, out, sc, s);
   int32_t host_c[SV_MAX_SEG + 4] = {0};

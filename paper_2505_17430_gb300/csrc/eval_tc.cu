@@ -24,6 +24,7 @@
 #include "bodies.cuh"
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
+#include "tc_walk.cuh"
 
 namespace {
 
@@ -61,6 +62,7 @@ struct FusedGeom {
   int a_bytes;     // one A stage (both copies for bf16)
   int b_bytes;     // resident B (both copies for bf16)
   uint32_t idesc;
+  int vec_ok;      // rows 16-byte aligned (X aligned, ld even): vector loads
 };
 
 struct __align__(8) Bars {
@@ -99,91 +101,15 @@ struct JobIter {
 };
 
 // ------------------------------------------------------------ epilogue walk
-// One thread, one row: z_i (i < D) in TMEM columns; groups are contiguous
-// column ranges with a body each.  A 16-column chunk inside one group is
-// handled with a single body dispatch.
-template <int BODY>
-__device__ __forceinline__ void chunk16(const float* v, const float* aux, int col0, int gstart,
-                                        float& zprev, const ProblemDev& P, Acc32& acc) {
-  if (BODY == SEVO_ROSENBROCK) {
-    if (col0 > gstart) term32(SEVO_ROSENBROCK, zprev, 0.f, true, v[0], P, acc);
-#pragma unroll
-    for (int k = 0; k + 1 < 16; ++k) term32(SEVO_ROSENBROCK, v[k], 0.f, true, v[k + 1], P, acc);
-  } else if (BODY == SEVO_ELLIPSOID || BODY == SEVO_GRIEWANK) {
-    float a[16];
-    const float4* a4 = reinterpret_cast<const float4*>(aux + col0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 t = __ldg(a4 + q);
-      a[4 * q] = t.x;
-      a[4 * q + 1] = t.y;
-      a[4 * q + 2] = t.z;
-      a[4 * q + 3] = t.w;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) term32(BODY, v[k], a[k], false, 0.f, P, acc);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) term32(BODY, v[k], 0.f, false, 0.f, P, acc);
-  }
-  zprev = v[15];
-}
-
+// the whole row: every group finalized and summed (FP64)
 __device__ __forceinline__ double walk_row(uint32_t taddr, int D, int c, bool comp,
                                            const ProblemDev& P) {
-  const float* __restrict__ aux32 = P.aux32[c];
-  int g = 0;
-  int gend = P.gstart[1];
-  int body = comp ? P.cbody[c] : P.gbody[0];
-  Acc32 acc;
-  acc32_init(acc);
   double gsum = 0.0;
-  float zprev = 0.f;
-  for (int col0 = 0; col0 < D; col0 += 16) {
-    float v[16];
-    tc::tmem_ld16(taddr + (uint32_t)col0, v);
-    while (col0 >= gend) {  // close groups that ended before this chunk
-      gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
-      ++g;
-      gend = P.gstart[g + 1];
-      body = comp ? P.cbody[c] : P.gbody[g];
-      acc32_init(acc);
-    }
-    if (col0 + 16 <= gend) {
-      const int gs = P.gstart[g];
-      switch (body) {
-        case SEVO_ELLIPSOID: chunk16<SEVO_ELLIPSOID>(v, aux32, col0, gs, zprev, P, acc); break;
-        case SEVO_ROSENBROCK: chunk16<SEVO_ROSENBROCK>(v, aux32, col0, gs, zprev, P, acc); break;
-        case SEVO_RASTRIGIN: chunk16<SEVO_RASTRIGIN>(v, aux32, col0, gs, zprev, P, acc); break;
-        case SEVO_SCHWEFEL: chunk16<SEVO_SCHWEFEL>(v, aux32, col0, gs, zprev, P, acc); break;
-        case SEVO_ACKLEY: chunk16<SEVO_ACKLEY>(v, aux32, col0, gs, zprev, P, acc); break;
-        default: chunk16<SEVO_GRIEWANK>(v, aux32, col0, gs, zprev, P, acc); break;
-      }
-    } else {
-      // chunk crosses a group border or the end of the row: per element
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int i = col0 + k;
-        if (i < D) {
-          while (i == gend) {
-            gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
-            ++g;
-            gend = P.gstart[g + 1];
-            body = comp ? P.cbody[c] : P.gbody[g];
-            acc32_init(acc);
-          }
-          const float z = v[k];
-          if (body == SEVO_ROSENBROCK) {
-            if (i > P.gstart[g]) term32(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
-          } else {
-            term32(body, z, aux32[i], false, 0.f, P, acc);
-          }
-          zprev = z;
-        }
-      }
-    }
-  }
-  gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+  float zf, zl;
+  walk_cols(taddr, 0, D, c, comp, P, zf, zl, [&](int g, const Acc32& acc) {
+    const int body = comp ? P.cbody[c] : P.gbody[g];
+    gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+  });
   return gsum;
 }
 
@@ -330,7 +256,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int pw = warp - NEPI;
     constexpr int RPW = BM / NPROD;  // rows per producer warp
     const int k0 = lane * 4;         // lane owns columns k0..k0+3 (kpad <= 128)
-    const bool full4 = (k0 + 3 < D);
+    const bool full4 = (k0 + 3 < D) && geo.vec_ok;
     JobIter it;
     it.init(&T);
     for (int64_t j = 0; it.valid(); ++j, it.next()) {
@@ -554,7 +480,7 @@ FusedGeom fused_geom(const ProblemDev& h, bool bf16) {
 }  // namespace
 
 // rows of the B box: the whole padded N extent for the fused kernel
-static int b_box_rows(const ProblemDev& h) { return h.D <= 128 ? h.npad : 256; }
+static int b_box_rows(const ProblemDev& h) { return h.D <= 128 ? h.npad : 128; }
 
 int32_t sv_build_tmaps(sevo_problem* p) {
   const ProblemDev& h = p->host_desc;
@@ -587,7 +513,8 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
   const ProblemDev& h0 = segs[0].p->host_desc;
   if (h0.D > 128) return cudaErrorNotSupported;
   const bool bf16 = (prec == SEVO_BF16X3);
-  const FusedGeom g = fused_geom(h0, bf16);
+  FusedGeom g = fused_geom(h0, bf16);
+  g.vec_ok = (((uintptr_t)X & 15) == 0) && ((ld & 1) == 0);
   const size_t smem = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   static bool attr_done[2] = {false, false};
   if (!attr_done[bf16]) {

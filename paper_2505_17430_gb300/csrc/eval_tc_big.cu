@@ -1,0 +1,485 @@
+// eval_tc_big.cu -- tcgen05 evaluation for D > 128, where the rotation GEMM
+// (N x D times D x D, 2 N D^2 flops) is tensor-bound.
+//
+//   1. convert: d = x - o_c once per element (float hi/lo split, integer and
+//      FP32 work), stored as TF32 (or BF16 hi and lo) rows padded to kpad;
+//      for compositions also s_c = |x - o_c|^2 per row;
+//   2. gemm: persistent CTAs over jobs (128-row tile, 128-column chunk of z),
+//      full K per job: one thread issues TMA loads of A and B K-blocks into a
+//      multi-stage shared-memory ring (128B swizzle), one thread issues
+//      tcgen05.mma into a double-buffered TMEM accumulator, four epilogue
+//      warps walk their row's chunk (thread = row = TMEM lane) and store the
+//      per-group FP32 accumulators of the chunk plus its first and last z;
+//   3. combine: per row, the chunk records are merged in column order (the
+//      Rosenbrock pair across a chunk border is added here), the groups are
+//      finished, the FP64 error is written and rows below the refinement
+//      threshold are listed.
+// Splitting z into 128-column chunks gives tiles x chunks independent jobs,
+// enough to fill the GPU even for N = 1024.  Waits are bounded as in the
+// fused kernel.
+#include "kernels.cuh"
+#include "tc_walk.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int NEPI = 4;
+constexpr int WARP_TMA = NEPI, WARP_MMA = NEPI + 1;
+constexpr int NTHREADS = (NEPI + 2) * 32;
+constexpr int KB_BYTES = 128 * 128;  // one 128-row x 128-byte K block (A or B)
+constexpr int REC = 3 * SV_MAXG + 2;  // floats per (row, chunk) record
+constexpr long long WAIT_BUDGET = 4000000000LL;
+
+struct BigGeom {
+  int D, kpad, nkb, nchunks, ntiles, stages, stage_bytes;
+  int64_t N;
+  uint32_t idesc;
+};
+
+struct __align__(8) BigBars {
+  uint64_t full[4], empty[4], t_full[2], t_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ void big_abort(BigBars* b, uint32_t* dev_err) {
+  b->abort = 1;
+  if (dev_err) atomicOr(dev_err, SV_DEVERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- convert
+template <bool BF16>
+__global__ void __launch_bounds__(128)
+    convert_kernel(const ProblemDev* __restrict__ P, int c, const double* __restrict__ X,
+                   int64_t ld, int64_t row0, int64_t N, int D, int kpad, float* __restrict__ A32,
+                   __nv_bfloat16* __restrict__ Ahi, __nv_bfloat16* __restrict__ Alo,
+                   double* __restrict__ s_out) {
+  __shared__ float red[4];
+  const float* __restrict__ oh = P->oh32[c];
+  const float* __restrict__ ol = P->ol32[c];
+  for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
+    const double* xr = X + (row0 + r) * ld;
+    float sq = 0.f;
+    for (int k0 = threadIdx.x * 4; k0 < kpad; k0 += blockDim.x * 4) {
+      float d[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        d[q] = 0.f;
+        if (k < D) {
+          float xh, xl;
+          sv_split_hi_lo(__ldg(xr + k), xh, xl);
+          d[q] = (xh - __ldg(oh + k)) + (xl - __ldg(ol + k));
+          sq += d[q] * d[q];
+        }
+      }
+      if (BF16) {
+        __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          h[q] = __float2bfloat16_rn(d[q]);
+          l[q] = __float2bfloat16_rn(d[q] - __bfloat162float(h[q]));
+        }
+        uint2 hv, lv;
+        hv.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+        hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+        lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+        lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+        *reinterpret_cast<uint2*>(Ahi + r * kpad + k0) = hv;
+        *reinterpret_cast<uint2*>(Alo + r * kpad + k0) = lv;
+      } else {
+        *reinterpret_cast<float4*>(A32 + r * kpad + k0) =
+            make_float4(tc::to_tf32(d[0]), tc::to_tf32(d[1]), tc::to_tf32(d[2]), tc::to_tf32(d[3]));
+      }
+    }
+    if (s_out) {
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+      __syncthreads();
+      if (threadIdx.x == 0) s_out[(row0 + r) * SV_MAXC + c] = (double)(red[0] + red[1] + red[2] + red[3]);
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- gemm
+template <bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_big_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
+                    const ProblemDev* __restrict__ P, const BigGeom geo, int c, bool comp,
+                    float* __restrict__ part, uint32_t* dev_err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ BigBars bars;
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = geo.stages;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&bars.full[s], 1);
+      tc::mbar_init(&bars.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars.t_full[b], 1);
+      tc::mbar_init(&bars.t_empty[b], NEPI);
+    }
+    bars.abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == WARP_MMA) {
+    tc::tmem_alloc(&bars.tmem_base, 2 * BN);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bars.tmem_base;
+  const int njobs_total = geo.ntiles * geo.nchunks;
+  const int KBLK = BF16 ? 64 : 32;  // elements per 128-byte K block
+
+  if (warp == WARP_TMA) {
+    if (lane == 0) {
+      const CUtensorMap* mB = BF16 ? P->tmaphi[c] : P->tmap32[c];
+      const CUtensorMap* mBlo = P->tmaplo[c];
+      uint32_t it = 0;
+      bool ok = true;
+      for (int job = blockIdx.x; job < njobs_total && ok; job += gridDim.x) {
+        const int tile = job / geo.nchunks, nb = job % geo.nchunks;
+        for (int kb = 0; kb < geo.nkb; ++kb, ++it) {
+          const int s = (int)(it % (uint32_t)S);
+          const uint32_t ph = (it / (uint32_t)S) & 1u;
+          if (!tc::mbar_wait(&bars.empty[s], ph ^ 1u, &bars.abort, WAIT_BUDGET)) {
+            big_abort(&bars, dev_err);
+            ok = false;
+            break;
+          }
+          unsigned char* st = base + (size_t)s * geo.stage_bytes;
+          tc::mbar_arrive_expect_tx(&bars.full[s], (uint32_t)geo.stage_bytes);
+          tc::tma_load_2d(st, &mapA, &bars.full[s], kb * KBLK, tile * BM);
+          tc::tma_load_2d(st + KB_BYTES, mB, &bars.full[s], kb * KBLK, nb * BN);
+          if (BF16) {
+            tc::tma_load_2d(st + 2 * KB_BYTES, &mapAlo, &bars.full[s], kb * KBLK, tile * BM);
+            tc::tma_load_2d(st + 3 * KB_BYTES, mBlo, &bars.full[s], kb * KBLK, nb * BN);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == WARP_MMA) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      int jl = 0;
+      bool ok = true;
+      for (int job = blockIdx.x; job < njobs_total && ok; job += gridDim.x, ++jl) {
+        const int a = jl & 1;
+        const uint32_t u = (uint32_t)(jl >> 1);
+        if (!tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
+          big_abort(&bars, dev_err);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(a * BN);
+        for (int kb = 0; kb < geo.nkb; ++kb, ++it) {
+          const int s = (int)(it % (uint32_t)S);
+          const uint32_t ph = (it / (uint32_t)S) & 1u;
+          if (!tc::mbar_wait(&bars.full[s], ph, &bars.abort, WAIT_BUDGET)) {
+            big_abort(&bars, dev_err);
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t aS = tc::smem_u32(base + (size_t)s * geo.stage_bytes);
+          const uint32_t bS = aS + KB_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+            if (BF16) {
+              const uint32_t aLo = aS + 2 * KB_BYTES, bLo = aS + 3 * KB_BYTES;
+              tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bS + ks * 32),
+                          geo.idesc, acc);
+              tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bLo + ks * 32),
+                          geo.idesc, 1u);
+              tc::mma_f16(d_tmem, tc::sdesc_sw128(aLo + ks * 32), tc::sdesc_sw128(bS + ks * 32),
+                          geo.idesc, 1u);
+            } else {
+              tc::mma_tf32(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bS + ks * 32),
+                           geo.idesc, acc);
+            }
+          }
+          tc::mma_commit(&bars.empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&bars.t_full[a]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue: thread = row of the tile = TMEM lane
+    const int r = warp * 32 + lane;
+    int jl = 0;
+    for (int job = blockIdx.x; job < njobs_total; job += gridDim.x, ++jl) {
+      const int tile = job / geo.nchunks, nb = job % geo.nchunks;
+      const int a = jl & 1;
+      const uint32_t u = (uint32_t)(jl >> 1);
+      if (!tc::mbar_wait(&bars.t_full[a], u & 1u, &bars.abort, WAIT_BUDGET)) {
+        big_abort(&bars, dev_err);
+        break;
+      }
+      tc::tc_fence_after();
+      const int c0 = nb * BN, c1 = min(geo.D, c0 + BN);
+      const int64_t row = (int64_t)tile * BM + r;
+      float* rec = part + (row * geo.nchunks + nb) * REC;
+      const bool live = row < geo.N;
+      float zf = 0.f, zl = 0.f;
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN);
+      if (c0 < c1) {
+        walk_cols(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
+          if (live) {
+            rec[3 * g] = acc.a0;
+            rec[3 * g + 1] = acc.a1;
+            rec[3 * g + 2] = acc.a2;
+          }
+        });
+      }
+      if (live) {
+        rec[3 * SV_MAXG] = zf;
+        rec[3 * SV_MAXG + 1] = zl;
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars.t_empty[a]);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == WARP_MMA) {
+    if (bars.abort) {
+      for (int k = 0; k < 1000; ++k) __nanosleep(1000);
+    }
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
+// ---------------------------------------------------------------- combine
+struct ListOutB {
+  int32_t* list;
+  int32_t* count;
+  uint32_t* nonfinite;
+  int64_t list_off;
+};
+
+__device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, int i) {
+  return comp ? 0 : P.gid[c][i];
+}
+
+__global__ void combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D,
+                               int nchunks, const float* __restrict__ part, int64_t row0,
+                               int64_t N, double* __restrict__ out, double* __restrict__ comp_g,
+                               ListOutB lo) {
+  const ProblemDev& P = *Pp;
+  for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < N;
+       lr += (int64_t)gridDim.x * blockDim.x) {
+    Acc32 acc[SV_MAXG];
+    for (int g = 0; g < SV_MAXG; ++g) acc32_init(acc[g]);
+    const float* recs = part + lr * (int64_t)nchunks * REC;
+    float zlast_prev = 0.f;
+    for (int nb = 0; nb < nchunks; ++nb) {
+      const int c0 = nb * BN, c1 = min(D, c0 + BN);
+      if (c0 >= c1) break;
+      const float* rec = recs + (int64_t)nb * REC;
+      const int g0 = group_of(P, c, comp, c0), g1 = group_of(P, c, comp, c1 - 1);
+      for (int g = g0; g <= g1; ++g) {
+        acc[g].a0 += rec[3 * g];
+        acc[g].a1 += rec[3 * g + 1];
+        acc[g].a2 += rec[3 * g + 2];
+      }
+      if (nb > 0) {  // Rosenbrock pair (c0 - 1, c0) inside one group
+        const int gp = group_of(P, c, comp, c0 - 1);
+        const int body = comp ? P.cbody[c] : P.gbody[gp];
+        if (gp == g0 && body == SEVO_ROSENBROCK)
+          term32(SEVO_ROSENBROCK, zlast_prev, 0.f, true, rec[3 * SV_MAXG], P, acc[gp]);
+      }
+      zlast_prev = rec[3 * SV_MAXG + 1];
+    }
+    double gsum = 0.0;
+    const int ng = comp ? 1 : P.ngroups;
+    for (int g = 0; g < ng; ++g) {
+      const int body = comp ? P.cbody[c] : P.gbody[g];
+      const int n = comp ? D : P.gstart[g + 1] - P.gstart[g];
+      gsum += (double)finalize32(body, acc[g], n);
+    }
+    const int64_t row = row0 + lr;
+    if (comp) {
+      comp_g[row * SV_MAXC + c] = gsum;
+      continue;
+    }
+    double err = gsum;
+    if (!isfinite(err)) {
+      err = __longlong_as_double(0x7ff8000000000000ll);
+      if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
+    } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
+      int k = atomicAdd(lo.count, 1);
+      lo.list[lo.list_off + k] = (int32_t)row;
+    }
+    out[row] = err;
+  }
+}
+
+__global__ void compose_big_kernel(const ProblemDev* __restrict__ Pp, const double* comp_g,
+                                   const double* comp_s, int64_t row0, int64_t N, double* out,
+                                   ListOutB lo) {
+  const ProblemDev& P = *Pp;
+  for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < N;
+       lr += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = row0 + lr;
+    double err = compose(P, comp_s + row * SV_MAXC, comp_g + row * SV_MAXC);
+    if (!isfinite(err)) {
+      err = __longlong_as_double(0x7ff8000000000000ll);
+      if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
+    } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
+      int k = atomicAdd(lo.count, 1);
+      lo.list[lo.list_off + k] = (int32_t)row;
+    }
+    out[row] = err;
+  }
+}
+
+typedef CUresult (*EncodeTiledFnB)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool make_a_map(CUtensorMap* m, const void* ptr, bool bf16, int kpad, int64_t rows) {
+  static EncodeTiledFnB fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return false;
+    fn = (EncodeTiledFnB)p;
+  }
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * es};
+  cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 32), (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// scratch of one segment of `rows` rows: converted operand, chunk records,
+// composition staging (per row SV_MAXC slots of g_c and of s_c)
+size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
+  (void)prec;
+  const int kpad = (D + 63) / 64 * 64;
+  const int nchunks = ((D + 127) / 128 * 128) / BN;
+  size_t b = al256b((size_t)rows * kpad * 4) + al256b((size_t)rows * nchunks * REC * 4);
+  if (any_comp) b += al256b((size_t)rows * SV_MAXC * 16);
+  return b;
+}
+
+cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int64_t ld,
+                           double* out, int32_t* list, int64_t list_off, int32_t* count,
+                           uint32_t* nonfinite, void* scratch, size_t scratch_bytes,
+                           uint32_t* dev_err, cudaStream_t st) {
+  const sevo_problem* p = seg.p;
+  const ProblemDev& h = p->host_desc;
+  const int64_t N = seg.nrows;
+  if (N <= 0) return cudaSuccess;
+  const bool bf16 = (prec == SEVO_BF16X3);
+  const bool comp = (p->family == SEVO_COMPOSITION);
+  if (h.npad % BN != 0 || p->tmap_rows != BN) return cudaErrorNotSupported;
+  if (!scratch || scratch_bytes < sv_eval_big_scratch_bytes(h.D, comp, prec, N))
+    return cudaErrorInvalidValue;
+  BigGeom g;
+  g.D = h.D;
+  g.kpad = h.kpad;
+  g.nkb = h.kpad / (bf16 ? 64 : 32);
+  g.nchunks = h.npad / BN;
+  g.ntiles = (int)((N + BM - 1) / BM);
+  g.N = N;
+  g.stage_bytes = (bf16 ? 4 : 2) * KB_BYTES;
+  g.stages = bf16 ? 3 : 4;
+  g.idesc = tc::idesc_make(bf16 ? 1 : 2, BM, BN);
+  // scratch: A (N x kpad fp32, or hi then lo bf16), chunk records, composition
+  char* cp = (char*)scratch;
+  void* Abase = cp;
+  cp += al256b((size_t)N * h.kpad * 4);
+  float* part = (float*)cp;
+  cp += al256b((size_t)N * g.nchunks * REC * 4);
+  // composition staging: g_c in the first N x SV_MAXC doubles, s_c in the
+  // next; both indexed by global row (row0 + local row)
+  double* comp_g = nullptr;
+  double* comp_s = nullptr;
+  if (comp) {
+    double* comp_base = (double*)cp;
+    comp_g = comp_base - seg.row0 * SV_MAXC;
+    comp_s = comp_base + (size_t)N * SV_MAXC - seg.row0 * SV_MAXC;
+  }
+  float* A32 = (float*)Abase;
+  __nv_bfloat16* Ahi = (__nv_bfloat16*)Abase;
+  __nv_bfloat16* Alo = Ahi + (size_t)N * h.kpad;
+  CUtensorMap mA, mAlo;
+  if (bf16) {
+    if (!make_a_map(&mA, Ahi, true, h.kpad, N) || !make_a_map(&mAlo, Alo, true, h.kpad, N))
+      return cudaErrorInvalidValue;
+  } else {
+    if (!make_a_map(&mA, A32, false, h.kpad, N)) return cudaErrorInvalidValue;
+    mAlo = mA;
+  }
+  const size_t smem = (size_t)g.stages * g.stage_bytes + 1024;
+  static bool attr_done[2] = {false, false};
+  if (!attr_done[bf16]) {
+    cudaError_t e = bf16 ? cudaFuncSetAttribute(gemm_big_kernel<true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)(200 * 1024))
+                         : cudaFuncSetAttribute(gemm_big_kernel<false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)(200 * 1024));
+    if (e != cudaSuccess) return e;
+    attr_done[bf16] = true;
+  }
+  const int cvt_grid = (int)std::min<int64_t>(N, (int64_t)sv_num_sms() * 16);
+  const int njobs = g.ntiles * g.nchunks;
+  const int ggrid = std::min(njobs, sv_num_sms());
+  const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 127) / 128, sv_num_sms() * 4));
+  const ListOutB lo{list, count, nonfinite, list_off};
+  cudaError_t e;
+  for (int c = 0; c < h.ncomp; ++c) {
+    if (bf16)
+      convert_kernel<true><<<cvt_grid, 128, 0, st>>>(p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad,
+                                                     nullptr, Ahi, Alo, comp ? comp_s : nullptr);
+    else
+      convert_kernel<false><<<cvt_grid, 128, 0, st>>>(p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad,
+                                                      A32, nullptr, nullptr, comp ? comp_s : nullptr);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (bf16)
+      gemm_big_kernel<true><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
+                                                           dev_err);
+    else
+      gemm_big_kernel<false><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
+                                                            dev_err);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    combine_kernel<<<cgrid, 128, 0, st>>>(p->desc_d, c, comp, h.D, g.nchunks, part, seg.row0, N,
+                                          out, comp_g, lo);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (comp) {
+    compose_big_kernel<<<cgrid, 128, 0, st>>>(p->desc_d, comp_g, comp_s, seg.row0, N, out, lo);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

@@ -555,7 +555,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   bool any_comp = false;
   for (const sevo_problem* q : probs) any_comp |= (q->family == SEVO_COMPOSITION);
   b->any_comp = any_comp;
-  b->eval_bytes = sv_eval_scratch_bytes(any_comp, b->prec, rows);
+  b->eval_bytes = sv_eval_scratch_bytes(b->D, any_comp, b->prec, rows);
   SV_CUDA(cudaMalloc(&b->eval_block, b->eval_bytes));
   return SEVO_OK;
 }
@@ -575,7 +575,7 @@ static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
     segs.push_back(TcSegment{b->run_prob[r0], (int64_t)r0 * b->NP, (int64_t)(r1 - r0) * b->NP});
   }
   EvalScratch sc;
-  sv_eval_scratch_carve(b->eval_block, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
+  sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
   return sv_eval_segments(segs.data(), (int)segs.size(), b->prec, M, b->ld, f, sc, b->stream);
 }
 

@@ -44,8 +44,14 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
                                 int64_t ld, double* out, int32_t* list, const int64_t* list_off,
                                 int32_t* counts, uint32_t* nonfinite, void* scratch,
                                 size_t scratch_bytes, uint32_t* dev_err, cudaStream_t st);
-// composition scratch of the tensor-core pass for `rows` rows
+// composition scratch of the fused tensor-core pass for `rows` rows
 size_t sv_eval_tc_scratch_bytes(bool any_comp, int prec, int64_t rows);
+// tensor-core evaluation of one segment with D > 128 (convert, GEMM, combine)
+cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int64_t ld,
+                           double* out, int32_t* list, int64_t list_off, int32_t* count,
+                           uint32_t* nonfinite, void* scratch, size_t scratch_bytes,
+                           uint32_t* dev_err, cudaStream_t st);
+size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
 // encode the TMA descriptors of a freshly uploaded problem
 int32_t sv_build_tmaps(sevo_problem* p);
 
@@ -58,8 +64,9 @@ struct EvalScratch {
   size_t tc_bytes;
 };
 #define SV_COUNTERS_BYTES ((SV_MAX_SEG + 4) * 4)
-size_t sv_eval_scratch_bytes(bool any_comp, int prec, int64_t rows);
-void sv_eval_scratch_carve(void* base, bool any_comp, int prec, int64_t rows, EvalScratch* s);
+size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
+void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
+                           EvalScratch* s);
 // evaluate segments (same D) into out with refinement; resets counters first
 cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const double* X,
                              int64_t ld, double* out, const EvalScratch& s, cudaStream_t st);

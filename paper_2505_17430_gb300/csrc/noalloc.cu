@@ -38,8 +38,6 @@ extern "C" int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* po
                                          void* stream) {
   if (!p || !pop || !out || N < 0 || D != p->D || ld < D) return SEVO_ERR_ARG;
   if (prec < SEVO_FP64 || prec > SEVO_FP32) return SEVO_ERR_ARG;
-  if ((prec == SEVO_TF32 || prec == SEVO_BF16X3) && (((uintptr_t)pop & 15) || (ld & 1)))
-    return SEVO_ERR_ARG;
   if (((uintptr_t)pop & 7) || ((uintptr_t)out & 7)) return SEVO_ERR_ARG;
   if (N > SEVO_NOALLOC_MAX_ROWS) return SEVO_ERR_UNSUPPORTED;
   // the problem's device copy must already exist here: making it allocates
@@ -48,12 +46,13 @@ extern "C" int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* po
   if (!p->desc_d || p->device != dev) return SEVO_ERR_STATE;
   if (N == 0) return SEVO_OK;
   const bool comp = (p->family == SEVO_COMPOSITION);
-  if (sv_eval_scratch_bytes(comp, prec, N) > SEVO_NOALLOC_SCRATCH_BYTES) return SEVO_ERR_UNSUPPORTED;
+  if (sv_eval_scratch_bytes(p->D, comp, prec, N) > SEVO_NOALLOC_SCRATCH_BYTES)
+    return SEVO_ERR_UNSUPPORTED;
   void* base = nullptr;
   int32_t st = scratch_address(&base);
   if (st != SEVO_OK) return st;
   EvalScratch sc;
-  sv_eval_scratch_carve(base, comp, prec, N, &sc);
+  sv_eval_scratch_carve(base, p->D, comp, prec, N, &sc);
   TcSegment seg{p, 0, N};
   cudaError_t e = sv_eval_segments(&seg, 1, prec, pop, ld, out, sc, (cudaStream_t)stream);
   if (e != cudaSuccess) {

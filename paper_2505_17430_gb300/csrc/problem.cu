@@ -184,7 +184,7 @@ static int32_t upload(sevo_problem* p) {
   h.ncomp = nc;
   h.ngroups = p->ngroups;
   h.kpad = round_up(D, 64);
-  h.npad = (D <= 256) ? round_up(D, 16) : round_up(D, 128);
+  h.npad = (D <= 128) ? round_up(D, 16) : round_up(D, 128);
   h.fstar = p->fstar;
   h.sch_s = schwefel_shift();
   h.sch_c = h.sch_s * std::sin(std::sqrt(h.sch_s));

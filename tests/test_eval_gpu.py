@@ -182,3 +182,38 @@ def test_tensor_core_deterministic(S):
         a = p.evaluate(X, prec=prec).cpu().numpy()
         b = p.evaluate(X, prec=prec).cpu().numpy()
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("D", [129, 257, 1000])
+def test_tensor_core_large_d_matches_oracle(S, prec, fam, D):
+    """Large-D tensor-core path (converted operand, 128-column chunk jobs,
+    chunk records merged per row): 300 rows over three tiles (one ragged),
+    D spanning one, two or eight 128-column chunks with a ragged last chunk
+    (Rosenbrock pairs and hybrid groups across chunk borders)."""
+    seed = 777 + 7 * fam + D
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = np.vstack([inputs.uniform_pop(270, D, seed=seed),
+                   inputs.mixed_scales(q.shift(0), 20, D, seed),
+                   _inputs(q, 0, D, seed)])
+    got, info = p.evaluate(to_dev(X), prec=getattr(S, prec), sync=True)
+    got = got.cpu().numpy()
+    want, scale = q.eval(X), q.scale(X)
+    bound = MIXED_TOL[prec] * np.maximum(np.abs(want), scale) + 1e-13
+    err = np.abs(got - want)
+    assert (err <= bound).all(), (np.max(err / bound), int(np.argmax(err / bound)))
+    sure = want + bound < 1e-4
+    assert (err[sure] <= tol64(want, scale)[sure]).all()
+    assert got[-1] == 0.0
+
+
+def test_tensor_core_d5000_sampled(S):
+    """D = 5000 (40 chunks of 128 columns, K = 5056): 130 rows, TF32."""
+    D = 5000
+    p, q = S.Problem(50, S.RASTRIGIN, D), O.Problem(50, O.RASTRIGIN, D)
+    X = np.vstack([inputs.uniform_pop(129, D, seed=50), q.shift(0)[None, :]])
+    got = p.evaluate(to_dev(X), prec=S.TF32).cpu().numpy()
+    want, scale = q.eval(X), q.scale(X)
+    assert (np.abs(got - want) <= MIXED_TOL["TF32"] * np.maximum(want, scale) + 1e-13).all()
+    assert got[-1] == 0.0
