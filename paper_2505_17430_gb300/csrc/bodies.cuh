@@ -107,12 +107,10 @@ __device__ __forceinline__ void acc32_init(Acc32& a) { a.a0 = a.a1 = a.a2 = 0.f;
 
 // sin(d) - d without cancellation for small |d| (Taylor to d^9)
 __device__ __forceinline__ float sin_minus_x(float d) {
-  float ad = fabsf(d);
-  if (ad < 0.25f) {
-    float d2 = d * d;
-    return d * d2 * (-1.f / 6.f + d2 * (1.f / 120.f + d2 * (-1.f / 5040.f + d2 * (1.f / 362880.f))));
-  }
-  return sinf(d) - d;
+  const float d2 = d * d;
+  const float series =
+      d * d2 * (-1.f / 6.f + d2 * (1.f / 120.f + d2 * (-1.f / 5040.f + d2 * (1.f / 362880.f))));
+  return (fabsf(d) < 0.25f) ? series : (sinf(d) - d);
 }
 
 __device__ __forceinline__ float schwefel_term32(float z, const ProblemDev& P) {
@@ -178,6 +176,83 @@ __device__ __forceinline__ void term32(int body, float z, float aux, bool has_ne
       break;
     }
   }
+}
+
+// Fast variant for the TF32 path (operands carry 2^-11 relative rounding, far
+// above these approximations' error): sin^2(pi z) from the reduced argument
+// z - rint(z) with the hardware sine, hardware sine / fast divide in
+// Schwefel.  Same algebraic forms as term32.
+__device__ __forceinline__ float sin_pi_red(float z) {
+  const float r = z - rintf(z);  // exact for |z| < 2^23; sin^2(pi z) has period 1
+  return __sinf(3.14159265358979f * r);
+}
+
+__device__ __forceinline__ float schwefel_term32f(float z, const ProblemDev& P) {
+  // both forms are computed and one is selected (no divergent branch)
+  const float s = P.sch_s32;
+  const float y = z + s;
+  const float ay = fabsf(y);
+  const float B = P.sch_B32, sB = P.sch_sinB32, cB = P.sch_cosB32;
+  const float spt = fmaxf(s + z, 0.f);
+  const float A = sqrtf(spt);
+  const float apb = A + B;
+  const float d = __fdividef(z, apb);
+  const float h = __sinf(0.5f * d);
+  const float t1 = spt * sB * 2.f * h * h;
+  const float t2 = -cB * spt * sin_minus_x(d);
+  const float t3 = -z * cB * (2.f * A + B) * __fdividef(d, 2.f * apb);
+  const float t4 = -z * P.sch_h032;
+  const float near = t1 + t2 + t3 + t4;
+  const float yc = fminf(ay, 500.f);
+  const float bsgn = (y > 0.f) ? 1.f : -1.f;
+  const float e = fmaxf(ay - 500.f, 0.f);
+  const float far = P.sch_c32 - bsgn * yc * __sinf(sqrtf(yc)) + 1e-4f * e * e;
+  return (y > 0.f && ay <= 500.f) ? near : far;
+}
+
+__device__ __forceinline__ void term32f(int body, float z, float aux, bool has_next, float znext,
+                                        const ProblemDev& P, Acc32& a) {
+  switch (body) {
+    case SEVO_RASTRIGIN: {
+      float sp = sin_pi_red(z);
+      a.a0 += z * z + 20.f * sp * sp;
+      break;
+    }
+    case SEVO_SCHWEFEL:
+      a.a0 += schwefel_term32f(z, P);
+      break;
+    case SEVO_ACKLEY: {
+      float sp = sin_pi_red(z);
+      a.a0 += z * z;
+      a.a1 += sp * sp;
+      break;
+    }
+    case SEVO_GRIEWANK: {
+      // sin^2(x/2) has period pi in x/2: reduce before the hardware sine
+      const float hx = 0.5f * __fdividef(z, aux);
+      const float h = __sinf(hx - 3.14159265358979f * rintf(hx * 0.318309886183791f));
+      float c = 1.f - 2.f * h * h;
+      a.a0 += z * z;
+      if (c > 0.f) {
+        a.a1 += log1pf(-2.f * h * h);
+      } else {
+        a.a1 += __logf(fmaxf(-c, 1e-30f));
+        a.a2 += 1.f;
+      }
+      break;
+    }
+    default:
+      term32(body, z, aux, has_next, znext, P, a);
+  }
+}
+
+template <bool FAST>
+__device__ __forceinline__ void term32t(int body, float z, float aux, bool has_next, float znext,
+                                        const ProblemDev& P, Acc32& a) {
+  if (FAST)
+    term32f(body, z, aux, has_next, znext, P, a);
+  else
+    term32(body, z, aux, has_next, znext, P, a);
 }
 
 __device__ __forceinline__ float finalize32(int body, const Acc32& a, int n) {

@@ -21,6 +21,8 @@
 // Composition components are written per row (g_c, s_c) and combined by a
 // second small kernel.  Every mbarrier wait is bounded; on a timeout the
 // kernel raises an error bit, stops issuing work and still frees its TMEM.
+#include <cstring>
+
 #include "bodies.cuh"
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
@@ -31,7 +33,10 @@ namespace {
 constexpr int BM = 128;
 constexpr int NEPI = 8, NPROD = 8;
 constexpr int WARP_MMA = NEPI + NPROD;
-constexpr int NTHREADS = (NEPI + NPROD + 1) * 32;
+constexpr int WARP_LOAD = NEPI + NPROD + 1;    // TMA loader of FP64 rows (staged mode)
+constexpr int NTHREADS = (NEPI + NPROD + 2) * 32;
+constexpr int XQ = 32;                        // rows per staged quarter-tile
+constexpr int MAX_XB = 4;                     // staged row buffers (ring)
 constexpr long long WAIT_BUDGET = 4000000000LL;  // ~2 s of clock64
 constexpr int TCOLS = 128;                      // TMEM columns per accumulator buffer
 constexpr int A_KB_BYTES = BM * 128;            // one 128-byte-wide K block of A
@@ -63,10 +68,14 @@ struct FusedGeom {
   int b_bytes;     // resident B (both copies for bf16)
   uint32_t idesc;
   int vec_ok;      // rows 16-byte aligned (X aligned, ld even): vector loads
+  int dbox;        // staged mode: columns per staged row (D rounded up to even)
+  int xb_bytes;    // staged mode: bytes of one quarter-tile buffer
+  int nxb;         // staged mode: number of quarter-tile buffers
 };
 
 struct __align__(8) Bars {
   uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], s_full[2];
+  uint64_t x_full[MAX_XB], x_empty[MAX_XB];
   uint64_t b_full, mma_done;
   uint32_t tmem_base;
   int abort;
@@ -102,11 +111,12 @@ struct JobIter {
 
 // ------------------------------------------------------------ epilogue walk
 // the whole row: every group finalized and summed (FP64)
+template <bool FAST>
 __device__ __forceinline__ double walk_row(uint32_t taddr, int D, int c, bool comp,
                                            const ProblemDev& P) {
   double gsum = 0.0;
   float zf, zl;
-  walk_cols(taddr, 0, D, c, comp, P, zf, zl, [&](int g, const Acc32& acc) {
+  walk_cols<FAST>(taddr, 0, D, c, comp, P, zf, zl, [&](int g, const Acc32& acc) {
     const int body = comp ? P.cbody[c] : P.gbody[g];
     gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
   });
@@ -131,19 +141,72 @@ __device__ __forceinline__ void emit(double err, int64_t row, double* out, const
   out[row] = err;
 }
 
+// one producer lane: 4 FP64 values of row r (columns k0..k0+3) -> d = x - o
+// from the float hi/lo split -> TF32 (or BF16 hi/lo) into the 128B-swizzled
+// K-major A tile; for a composition also the row's |d|^2 (warp sum)
 template <bool BF16>
+__device__ __forceinline__ void convert_store(int r, const double (&x)[4], int k0, int D,
+                                              const FusedGeom& geo, const float (&ohv)[4],
+                                              const float (&olv)[4], bool comp, int lane,
+                                              float* sSa, unsigned char* At) {
+  // unconditional: columns past D hold x = 0 and o = 0, so d = 0 there
+  float d[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float xh, xl;
+    sv_split_hi_lo(x[q], xh, xl);
+    d[q] = (xh - ohv[q]) + (xl - olv[q]);
+  }
+  if (comp) {
+    float sq = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
+    if (lane == 0) sSa[r] = sq;
+  }
+  const int sw = r & 7;
+  if (k0 >= geo.kpad) return;
+  if (BF16) {
+    // 64 bf16 per 128-byte K block: k0 -> block k0/64, chunk (k0%64)/8, half (k0%8)/4
+    const int kb = k0 >> 6, ch = (k0 & 63) >> 3, hf = (k0 & 7) >> 2;
+    uint32_t hi2[2], lo2[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      __nv_bfloat16 h0 = __float2bfloat16_rn(d[2 * q]), h1 = __float2bfloat16_rn(d[2 * q + 1]);
+      __nv_bfloat16 l0 = __float2bfloat16_rn(d[2 * q] - __bfloat162float(h0));
+      __nv_bfloat16 l1 = __float2bfloat16_rn(d[2 * q + 1] - __bfloat162float(h1));
+      hi2[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      lo2[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4) + hf * 8;
+    *reinterpret_cast<uint2*>(At + off) = make_uint2(hi2[0], hi2[1]);
+    *reinterpret_cast<uint2*>(At + geo.nkb * A_KB_BYTES + off) = make_uint2(lo2[0], lo2[1]);
+  } else {
+    // 32 tf32 per 128-byte K block: k0 -> block k0/32, chunk (k0%32)/4
+    const int kb = k0 >> 5, ch = (k0 & 31) >> 2;
+    const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4);
+    *reinterpret_cast<float4*>(At + off) =
+        make_float4(tc::to_tf32(d[0]), tc::to_tf32(d[1]), tc::to_tf32(d[2]), tc::to_tf32(d[3]));
+  }
+}
+
+// XTMA: FP64 rows are streamed by TMA (32-row quarter tiles) into a ring of
+// shared-memory buffers and converted from there; the A tile is then single
+// buffered.  Otherwise producers load rows from global memory directly.
+template <bool BF16, bool XTMA>
 __global__ void __launch_bounds__(NTHREADS, 1)
     eval_tc_fused(const __grid_constant__ SegTable T, const FusedGeom geo,
-                  const double* __restrict__ X, int64_t ld, double* __restrict__ out,
-                  double* __restrict__ comp_g, double* __restrict__ comp_s, ListOut lo,
-                  uint32_t* dev_err) {
+                  const __grid_constant__ CUtensorMap mapX, const double* __restrict__ X,
+                  int64_t ld, double* __restrict__ out, double* __restrict__ comp_g,
+                  double* __restrict__ comp_s, ListOut lo, uint32_t* dev_err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ Bars bars;
   __shared__ float sS[2][BM];
 
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA[2] = {base, base + geo.a_bytes};
-  unsigned char* sB = base + 2 * geo.a_bytes;
+  // staged: [A][B][x ring]; direct: [A0][A1][B]
+  unsigned char* sA[2] = {base, XTMA ? base : base + geo.a_bytes};
+  unsigned char* sB = base + (XTMA ? 1 : 2) * geo.a_bytes;
+  unsigned char* sX = sB + geo.b_bytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -153,6 +216,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_init(&bars.t_full[b], 1);
       tc::mbar_init(&bars.t_empty[b], NEPI / 2);
       tc::mbar_init(&bars.s_full[b], NPROD);
+    }
+    for (int b = 0; b < MAX_XB; ++b) {
+      tc::mbar_init(&bars.x_full[b], 1);
+      tc::mbar_init(&bars.x_empty[b], NPROD);
     }
     tc::mbar_init(&bars.b_full, 1);
     tc::mbar_init(&bars.mma_done, 1);
@@ -211,14 +278,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           curP = sg.P;
           cur_c = c;
         }
-        if (!tc::mbar_wait(&bars.a_full[a], u & 1u, &bars.abort, WAIT_BUDGET) ||
+        const int ab = XTMA ? 0 : a;                        // A buffer
+        const uint32_t apar = XTMA ? (uint32_t)(j & 1) : (u & 1u);
+        if (!tc::mbar_wait(&bars.a_full[ab], apar, &bars.abort, WAIT_BUDGET) ||
             !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
           raise_abort(&bars, dev_err);
           break;
         }
         tc::tc_fence_after();
         const uint32_t d_tmem = tmem + (uint32_t)(a * TCOLS);
-        const uint32_t aS = tc::smem_u32(sA[a]);
+        const uint32_t aS = tc::smem_u32(sA[ab]);
         const uint32_t bS = tc::smem_u32(sB);
         if (BF16) {
           const uint32_t a_lo = aS + (uint32_t)(geo.nkb * A_KB_BYTES);
@@ -239,7 +308,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                          ks > 0 ? 1u : 0u);
           }
         }
-        tc::mma_commit(&bars.a_empty[a]);
+        tc::mma_commit(&bars.a_empty[ab]);
         tc::mma_commit(&bars.t_full[a]);
         // if the next job needs another B, track when these MMAs are done
         JobIter nx = it;
@@ -251,7 +320,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp >= NEPI) {
+  } else if (warp == WARP_LOAD) {
+    // ------------------------------------------------------------ row loader
+    if (XTMA && lane == 0) {
+      JobIter it;
+      it.init(&T);
+      uint32_t q = 0;  // quarter-tiles issued
+      bool ok = true;
+      for (int64_t j = 0; it.valid() && ok; ++j, it.next()) {
+        const Seg& sg = it.seg();
+        const int64_t row0 = sg.row0 + (int64_t)it.local_tile() * BM;
+        for (int h = 0; h < BM / XQ; ++h, ++q) {
+          const int b = (int)(q % (uint32_t)geo.nxb);
+          const uint32_t use = q / (uint32_t)geo.nxb;
+          if (!tc::mbar_wait(&bars.x_empty[b], (use & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
+            raise_abort(&bars, dev_err);
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&bars.x_full[b], (uint32_t)geo.xb_bytes);
+          tc::tma_load_2d(sX + (size_t)b * geo.xb_bytes, &mapX, &bars.x_full[b], 0,
+                          (int32_t)(row0 + h * XQ));
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp >= NEPI && warp < WARP_MMA) {
     // ------------------------------------------------------------ producers
     const int pw = warp - NEPI;
     constexpr int RPW = BM / NPROD;  // rows per producer warp
@@ -265,7 +359,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool comp = sg.comp;
       const int a = (int)(j & 1);
       const uint32_t u = (uint32_t)(j >> 1);
-      if (!tc::mbar_wait(&bars.a_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET) ||
+      const int ab = XTMA ? 0 : a;
+      const uint32_t apar = XTMA ? (uint32_t)((j & 1) ^ 1) : ((u & 1u) ^ 1u);
+      if (!tc::mbar_wait(&bars.a_empty[ab], apar, &bars.abort, WAIT_BUDGET) ||
           (comp && !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET))) {
         if (lane == 0) raise_abort(&bars, dev_err);
         break;
@@ -280,7 +376,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         olv[t] = (k < D) ? __ldg(ol + k) : 0.f;
       }
       const int64_t lrow0 = (int64_t)it.local_tile() * BM;
-      unsigned char* At = sA[a];
+      unsigned char* At = sA[ab];
+      if (XTMA) {
+        // quarter-tiles of 32 rows from the staged ring: warp pw converts 4 rows
+        bool okq = true;
+        for (int h = 0; h < BM / XQ; ++h) {
+          const uint32_t qi = (uint32_t)j * (BM / XQ) + (uint32_t)h;
+          const int b = (int)(qi % (uint32_t)geo.nxb);
+          const uint32_t use = qi / (uint32_t)geo.nxb;
+          if (!tc::mbar_wait(&bars.x_full[b], use & 1u, &bars.abort, WAIT_BUDGET)) {
+            if (lane == 0) raise_abort(&bars, dev_err);
+            okq = false;
+            break;
+          }
+          const double* xs = reinterpret_cast<const double*>(sX + (size_t)b * geo.xb_bytes);
+#pragma unroll
+          for (int t = 0; t < XQ / NPROD; ++t) {
+            const int rq = pw * (XQ / NPROD) + t;  // row within the quarter
+            const int r = h * XQ + rq;             // row within the tile
+            double xv[4] = {0.0, 0.0, 0.0, 0.0};
+            if (lrow0 + r < sg.nrows) {
+              const double* xr = xs + rq * geo.dbox;
+              if (k0 + 3 < D) {
+                const double2 p0 = *reinterpret_cast<const double2*>(xr + k0);
+                const double2 p1 = *reinterpret_cast<const double2*>(xr + k0 + 2);
+                xv[0] = p0.x;
+                xv[1] = p0.y;
+                xv[2] = p1.x;
+                xv[3] = p1.y;
+              } else {
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+                  if (k0 + qq < D) xv[qq] = xr[k0 + qq];
+              }
+            }
+            convert_store<BF16>(r, xv, k0, D, geo, ohv, olv, comp, lane, sS[a], At);
+          }
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&bars.x_empty[b]);
+        }
+        if (!okq) break;
+      } else
       for (int rb = 0; rb < RPW; rb += 4) {
         double xv[4][4];
 #pragma unroll
@@ -306,54 +442,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int r = pw * RPW + rb + t;
-          float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (k0 + q < D) {
-              float xh, xl;
-              sv_split_hi_lo(xv[t][q], xh, xl);
-              d[q] = (xh - ohv[q]) + (xl - olv[q]);
-            }
-          }
-          if (comp) {
-            float sq = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
-            if (lane == 0) sS[a][r] = sq;
-          }
-          const int sw = r & 7;
-          if (k0 >= geo.kpad) continue;
-          if (BF16) {
-            // 64 bf16 per 128-byte K block: k0 -> block k0/64, chunk (k0%64)/8, half (k0%8)/4
-            const int kb = k0 >> 6, ch = (k0 & 63) >> 3, hf = (k0 & 7) >> 2;
-            uint32_t hi2[2], lo2[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              __nv_bfloat16 h0 = __float2bfloat16_rn(d[2 * q]), h1 = __float2bfloat16_rn(d[2 * q + 1]);
-              __nv_bfloat16 l0 = __float2bfloat16_rn(d[2 * q] - __bfloat162float(h0));
-              __nv_bfloat16 l1 = __float2bfloat16_rn(d[2 * q + 1] - __bfloat162float(h1));
-              hi2[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-              lo2[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-            const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4) + hf * 8;
-            *reinterpret_cast<uint2*>(At + off) = make_uint2(hi2[0], hi2[1]);
-            *reinterpret_cast<uint2*>(At + geo.nkb * A_KB_BYTES + off) = make_uint2(lo2[0], lo2[1]);
-          } else {
-            // 32 tf32 per 128-byte K block: k0 -> block k0/32, chunk (k0%32)/4
-            const int kb = k0 >> 5, ch = (k0 & 31) >> 2;
-            const int off = kb * A_KB_BYTES + r * 128 + ((ch ^ sw) << 4);
-            *reinterpret_cast<float4*>(At + off) = make_float4(
-                tc::to_tf32(d[0]), tc::to_tf32(d[1]), tc::to_tf32(d[2]), tc::to_tf32(d[3]));
-          }
-        }
+        for (int t = 0; t < 4; ++t)
+          convert_store<BF16>(pw * RPW + rb + t, xv[t], k0, D, geo, ohv, olv, comp, lane, sS[a], At);
       }
       __syncwarp();
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        tc::mbar_arrive(&bars.a_full[a]);
+        tc::mbar_arrive(&bars.a_full[XTMA ? 0 : a]);
         if (comp) tc::mbar_arrive(&bars.s_full[a]);
       }
     }
@@ -379,7 +475,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc::tc_fence_after();
       const float s_c = comp ? sS[g][r] : 0.f;
-      const double gsum = walk_row(taddr, D, c, comp, *sg.P);
+      const double gsum = walk_row<!BF16>(taddr, D, c, comp, *sg.P);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bars.t_empty[g]);
@@ -455,6 +551,21 @@ bool make_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// FP64 rows of X as a 2D tensor (D columns, rows_total rows, pitch ld),
+// box = dbox columns x 32 rows, no swizzle (row-major in shared memory);
+// columns D..dbox-1 and rows past the end read as zeros
+bool make_x_map(CUtensorMap* m, const double* X, int D, int dbox, int64_t rows_total, int64_t ld) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || rows_total <= 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows_total};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  cuuint32_t box[2] = {(cuuint32_t)dbox, (cuuint32_t)XQ};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(X), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 FusedGeom fused_geom(const ProblemDev& h, bool bf16) {
   FusedGeom g;
   g.D = h.D;
@@ -515,17 +626,32 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
   const bool bf16 = (prec == SEVO_BF16X3);
   FusedGeom g = fused_geom(h0, bf16);
   g.vec_ok = (((uintptr_t)X & 15) == 0) && ((ld & 1) == 0);
-  const size_t smem = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[bf16]) {
-    cudaError_t e = bf16 ? cudaFuncSetAttribute(eval_tc_fused<true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)(200 * 1024))
-                         : cudaFuncSetAttribute(eval_tc_fused<false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)(200 * 1024));
+  // staged rows: TMA needs a 16-byte aligned base and row pitch
+  const bool xtma = g.vec_ok;
+  g.dbox = (h0.D + 1) & ~1;
+  g.xb_bytes = XQ * g.dbox * 8;
+  const size_t budget = 220 * 1024;
+  const size_t fixed = (size_t)g.a_bytes + g.b_bytes + 1024;
+  g.nxb = (int)std::min<size_t>(MAX_XB, (budget - fixed) / (size_t)g.xb_bytes);
+  const bool use_xtma = xtma && g.nxb >= 2;
+  const size_t smem = use_xtma ? fixed + (size_t)g.nxb * g.xb_bytes
+                               : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const int lim = 224 * 1024;  // opt-in maximum minus this kernel's static shared memory
+    cudaError_t e = cudaFuncSetAttribute(eval_tc_fused<true, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eval_tc_fused<true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eval_tc_fused<false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eval_tc_fused<false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
-    attr_done[bf16] = true;
+    attr_done = true;
   }
   SegTable T;
   T.nseg = nseg;
@@ -566,12 +692,31 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
   }
   const ListOut lo{list, counts, nonfinite};
   const int grid = std::min(tiles, sv_num_sms());
-  if (bf16)
-    eval_tc_fused<true><<<grid, NTHREADS, smem, st>>>(T, g, X, ld, out, comp_g, comp_s, lo,
-                                                      dev_err);
-  else
-    eval_tc_fused<false><<<grid, NTHREADS, smem, st>>>(T, g, X, ld, out, comp_g, comp_s, lo,
-                                                       dev_err);
+  CUtensorMap mapX;
+  std::memset(&mapX, 0, sizeof(mapX));
+  bool staged = use_xtma;
+  if (staged) {
+    int64_t rows_total = 0;
+    for (int k = 0; k < nseg; ++k)
+      rows_total = std::max<int64_t>(rows_total, segs[k].row0 + segs[k].nrows);
+    staged = make_x_map(&mapX, X, h0.D, g.dbox, rows_total, ld);
+  }
+  if (!staged) {
+    const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
+    if (bf16)
+      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, mapX, X, ld, out,
+                                                                      comp_g, comp_s, lo, dev_err);
+    else
+      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, mapX, X, ld, out,
+                                                                       comp_g, comp_s, lo, dev_err);
+  } else {
+    if (bf16)
+      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, mapX, X, ld, out, comp_g,
+                                                              comp_s, lo, dev_err);
+    else
+      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, mapX, X, ld, out, comp_g,
+                                                               comp_s, lo, dev_err);
+  }
   sv_note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       float zf = 0.f, zl = 0.f;
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN);
       if (c0 < c1) {
-        walk_cols(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
+        walk_cols<!BF16>(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
           if (live) {
             rec[3 * g] = acc.a0;
             rec[3 * g + 1] = acc.a1;

@@ -137,25 +137,24 @@ __host__ __device__ __forceinline__ void sv_split_hi_lo(double x, float& hi, flo
 #endif
   const uint32_t h = (uint32_t)((unsigned long long)b >> 32), l = (uint32_t)b;
   const int e = (int)((h >> 20) & 0x7FF);
-  if (e < 949 || e > 1150) {  // |x| < 2^-74 (or out of the float range: unused)
-    hi = 0.f;
-    lo = 0.f;
-    return;
-  }
+  // branch-free: the bits are formed for every input and replaced by 0 when
+  // |x| < 2^-74 (or beyond the float range, which the callers never pass)
+  const bool ok = (e >= 949) && (e <= 1150);
   const uint32_t sign = h & 0x80000000u;
   const uint32_t hb = sign | ((uint32_t)(e - 896) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
   const uint32_t r = l & 0x1FFFFFFFu;
   const uint32_t sb = (uint32_t)(e - 948) << 23;  // 2^(e - 1075) as float bits
 #ifdef __CUDA_ARCH__
-  hi = __uint_as_float(hb);
-  float v = __uint2float_rn(r) * __uint_as_float(sb);
+  const float hv = __uint_as_float(hb);
+  const float v = __uint2float_rn(r) * __uint_as_float(sb);
 #else
-  __builtin_memcpy(&hi, &hb, 4);
-  float scl;
+  float hv, scl;
+  __builtin_memcpy(&hv, &hb, 4);
   __builtin_memcpy(&scl, &sb, 4);
-  float v = (float)r * scl;
+  const float v = (float)r * scl;
 #endif
-  lo = sign ? -v : v;
+  hi = ok ? hv : 0.f;
+  lo = ok ? (sign ? -v : v) : 0.f;
 }
 
 // status helpers --------------------------------------------------------

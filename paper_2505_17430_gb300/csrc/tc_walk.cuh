@@ -5,13 +5,13 @@
 #include "bodies.cuh"
 #include "tc_ptx.cuh"
 
-template <int BODY>
+template <int BODY, bool FAST>
 __device__ __forceinline__ void chunk16(const float* v, const float* aux, int col0, bool pair0,
                                         float& zprev, const ProblemDev& P, Acc32& acc) {
   if (BODY == SEVO_ROSENBROCK) {
-    if (pair0) term32(SEVO_ROSENBROCK, zprev, 0.f, true, v[0], P, acc);
+    if (pair0) term32t<FAST>(SEVO_ROSENBROCK, zprev, 0.f, true, v[0], P, acc);
 #pragma unroll
-    for (int k = 0; k + 1 < 16; ++k) term32(SEVO_ROSENBROCK, v[k], 0.f, true, v[k + 1], P, acc);
+    for (int k = 0; k + 1 < 16; ++k) term32t<FAST>(SEVO_ROSENBROCK, v[k], 0.f, true, v[k + 1], P, acc);
   } else if (BODY == SEVO_ELLIPSOID || BODY == SEVO_GRIEWANK) {
     float a[16];
     const float4* a4 = reinterpret_cast<const float4*>(aux + col0);
@@ -24,10 +24,10 @@ __device__ __forceinline__ void chunk16(const float* v, const float* aux, int co
       a[4 * q + 3] = t.w;
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) term32(BODY, v[k], a[k], false, 0.f, P, acc);
+    for (int k = 0; k < 16; ++k) term32t<FAST>(BODY, v[k], a[k], false, 0.f, P, acc);
   } else {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) term32(BODY, v[k], 0.f, false, 0.f, P, acc);
+    for (int k = 0; k < 16; ++k) term32t<FAST>(BODY, v[k], 0.f, false, 0.f, P, acc);
   }
   zprev = v[15];
 }
@@ -37,7 +37,7 @@ __device__ __forceinline__ void chunk16(const float* v, const float* aux, int co
 // and inside a group.  close(g, acc) is called for every group the walk
 // leaves and for the group it ends in.  zfirst/zlast receive z_{c0} and
 // z_{c1-1} (used to join Rosenbrock pairs across walks).
-template <class Close>
+template <bool FAST, class Close>
 __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c, bool comp,
                                           const ProblemDev& P, float& zfirst, float& zlast,
                                           Close&& close) {
@@ -63,12 +63,12 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
     if (col0 + 16 <= gend && col0 + 16 <= c1) {
       const bool pair0 = col0 > P.gstart[g] && col0 > c0;
       switch (body) {
-        case SEVO_ELLIPSOID: chunk16<SEVO_ELLIPSOID>(v, aux32, col0, pair0, zprev, P, acc); break;
-        case SEVO_ROSENBROCK: chunk16<SEVO_ROSENBROCK>(v, aux32, col0, pair0, zprev, P, acc); break;
-        case SEVO_RASTRIGIN: chunk16<SEVO_RASTRIGIN>(v, aux32, col0, pair0, zprev, P, acc); break;
-        case SEVO_SCHWEFEL: chunk16<SEVO_SCHWEFEL>(v, aux32, col0, pair0, zprev, P, acc); break;
-        case SEVO_ACKLEY: chunk16<SEVO_ACKLEY>(v, aux32, col0, pair0, zprev, P, acc); break;
-        default: chunk16<SEVO_GRIEWANK>(v, aux32, col0, pair0, zprev, P, acc); break;
+        case SEVO_ELLIPSOID: chunk16<SEVO_ELLIPSOID, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
+        case SEVO_ROSENBROCK: chunk16<SEVO_ROSENBROCK, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
+        case SEVO_RASTRIGIN: chunk16<SEVO_RASTRIGIN, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
+        case SEVO_SCHWEFEL: chunk16<SEVO_SCHWEFEL, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
+        case SEVO_ACKLEY: chunk16<SEVO_ACKLEY, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
+        default: chunk16<SEVO_GRIEWANK, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
       }
       if (col0 + 16 == c1) zlast = v[15];
     } else {
@@ -85,9 +85,9 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
           }
           const float z = v[k];
           if (body == SEVO_ROSENBROCK) {
-            if (i > P.gstart[g] && i > c0) term32(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
+            if (i > P.gstart[g] && i > c0) term32t<FAST>(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
           } else {
-            term32(body, z, aux32[i], false, 0.f, P, acc);
+            term32t<FAST>(body, z, aux32[i], false, 0.f, P, acc);
           }
           zprev = z;
           if (i == c1 - 1) zlast = z;
