@@ -226,7 +226,9 @@ int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
  * update and guide (gbest or ring lbest) refresh. */
 int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter);
 
-/* Synchronize the state's stream and read the run's bookkeeping (host). */
+/* Synchronize the state's stream and read the run's bookkeeping (host).
+ * Returns SEVO_ERR_TIMEOUT if a bounded device wait gave up in any
+ * evaluation since the last call (the results are then unreliable). */
 int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes, int64_t* gens,
                           int64_t* refined);
 

@@ -28,6 +28,7 @@ void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t r
   c += al256(SV_COUNTERS_BYTES);
   s->tc_bytes = tc_bytes(D, any_comp, prec, rows);
   s->tc = s->tc_bytes ? (void*)c : nullptr;
+  s->err = nullptr;
 }
 
 // one pass: mixed evaluation of every segment, then one FP64 re-evaluation
@@ -42,7 +43,7 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
     e = cudaMemsetAsync(s.counters, 0, SV_COUNTERS_BYTES, st);
     if (e != cudaSuccess) return e;
     uint32_t* nonfinite = (uint32_t*)(s.counters + SV_MAX_SEG);
-    uint32_t* dev_err = (uint32_t*)(s.counters + SV_MAX_SEG + 1);
+    uint32_t* dev_err = s.err ? s.err : (uint32_t*)(s.counters + SV_MAX_SEG + 1);
     int64_t off[SV_MAX_SEG];
     int64_t tot = 0;
     for (int k = 0; k < n; ++k) {

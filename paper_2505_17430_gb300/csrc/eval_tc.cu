@@ -462,14 +462,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * TCOLS);
     JobIter it;
     it.init(&T);
+    // s_full[g] completes only on composition jobs of parity g: its phase is
+    // counted separately from t_full[g], which completes on every job
+    uint32_t comp_uses = 0;
     for (int64_t j = 0; it.valid(); ++j, it.next()) {
       if ((int)(j & 1) != g) continue;
       const Seg& sg = it.seg();
       const int c = it.c;
       const bool comp = sg.comp;
       const uint32_t u = (uint32_t)(j >> 1);
+      const uint32_t sp = comp_uses & 1u;
+      if (comp) ++comp_uses;
       if (!tc::mbar_wait(&bars.t_full[g], u & 1u, &bars.abort, WAIT_BUDGET) ||
-          (comp && !tc::mbar_wait(&bars.s_full[g], u & 1u, &bars.abort, WAIT_BUDGET))) {
+          (comp && !tc::mbar_wait(&bars.s_full[g], sp, &bars.abort, WAIT_BUDGET))) {
         raise_abort(&bars, dev_err);
         break;
       }

@@ -202,6 +202,45 @@ __global__ void __launch_bounds__(RANK_ROWS)
   if (rank < k) order[(int64_t)r * NP + rank] = i;
 }
 
+// Larger populations: one CTA per run sorts (key, index) pairs with a
+// bitonic network in shared memory (padded to a power of two with +inf
+// keys), lexicographic order = (fitness, index); the first k indices are the
+// p-best pool, identical to the counting rank.
+constexpr int SORT_THREADS = 512;
+__global__ void __launch_bounds__(SORT_THREADS)
+    de_rank_sort_kernel(const double* __restrict__ fx, int32_t* __restrict__ order, int NP,
+                        int npow2, int k) {
+  extern __shared__ long long sk[];
+  int* si = (int*)(sk + npow2);
+  const int r = blockIdx.x;
+  const double* f = fx + (int64_t)r * NP;
+  for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+    sk[i] = (i < NP) ? fkey(f[i]) : 0x7FFFFFFFFFFFFFFFll;
+    si[i] = (i < NP) ? i : 0x7FFFFFFF;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npow2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < npow2 / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const long long ka = sk[lo], kb = sk[hi];
+        const int ia = si[lo], ib = si[hi];
+        const bool a_gt_b = (ka > kb) || (ka == kb && ia > ib);
+        if (a_gt_b == up) {
+          sk[lo] = kb;
+          sk[hi] = ka;
+          si[lo] = ib;
+          si[hi] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = threadIdx.x; q < k; q += blockDim.x) order[(int64_t)r * NP + q] = si[q];
+}
+
 // ---------------------------------------------------------------- DE select
 // per run: acceptance, best-so-far, archive slots (row order, random slot
 // once full, the last row targeting a slot wins), fitness update.
@@ -510,7 +549,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
                ivec = al256((size_t)rows * 4);
   const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB);
   const bool ctpb = (b->alg == SEVO_DE_CTPB);
-  size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ +
+  size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ + al256(16) /*err*/ +
                  al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
                  al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
   if (de) bytes += mat /*U*/ + vec /*fu*/;
@@ -528,6 +567,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->X = (double*)take(mat);
   b->fx = (double*)take(vec);
   b->best = (double*)take(al256((size_t)b->R * 8));
+  b->err = (uint32_t*)take(al256(16));
   b->seeds = (uint64_t*)take(al256((size_t)b->R * 8));
   b->ctl = (GenCtl*)take(al256(sizeof(GenCtl)));
   b->guide = (int32_t*)take(ivec);
@@ -576,6 +616,7 @@ static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
   }
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
+  sc.err = b->err;
   return sv_eval_segments(segs.data(), (int)segs.size(), b->prec, M, b->ld, f, sc, b->stream);
 }
 
@@ -632,8 +673,15 @@ cudaError_t sv_batch_generation(Batch* b) {
   cudaError_t e;
   if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
     if (b->alg == SEVO_DE_CTPB) {
-      de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
-                       (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
+      if (b->NP <= 512) {
+        de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
+                         (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
+      } else {
+        int np2 = 1;
+        while (np2 < b->NP) np2 <<= 1;
+        de_rank_sort_kernel<<<b->R, SORT_THREADS, (size_t)np2 * 12, st>>>(b->fx, b->order, b->NP,
+                                                                          np2, b->pbest_k);
+      }
       sv_note_launch();
       de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
@@ -678,4 +726,16 @@ cudaError_t sv_batch_guides(Batch* b) {
                                                          b->alg == SEVO_PSO_RING, 0, 0);
                                                          sv_note_launch();
   return cudaGetLastError();
+}
+
+int32_t sv_batch_status(Batch* b) {
+  uint32_t e = 0;
+  SV_CUDA(cudaMemcpyAsync(&e, b->err, 4, cudaMemcpyDeviceToHost, b->stream));
+  SV_CUDA(cudaStreamSynchronize(b->stream));
+  if (e) {
+    SV_CUDA(cudaMemsetAsync(b->err, 0, 4, b->stream));
+    if (e & SV_DEVERR_TIMEOUT) return SEVO_ERR_TIMEOUT;
+    return SEVO_ERR_CUDA;
+  }
+  return SEVO_OK;
 }

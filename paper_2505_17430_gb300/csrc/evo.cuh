@@ -30,6 +30,7 @@ struct Batch {
   int32_t *asize, *guide, *part, *order, *action;
   uint64_t* seeds;
   GenCtl* ctl;
+  uint32_t* err;  // device error bits accumulated over every evaluation
   // evaluation scratch (refine list + counters + tensor-core staging)
   void* eval_block;
   size_t eval_bytes;
@@ -50,4 +51,6 @@ cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count);
 cudaError_t sv_ctl_advance(Batch* b);  // gen += 1, count from gen and budget
 int sv_pbest_k(double p, int NP);
 cudaError_t sv_batch_guides(Batch* b);
+// read and clear the batch's device error bits (synchronizes its stream)
+int32_t sv_batch_status(Batch* b);
 #define SV_MAX_NP 4096

@@ -125,7 +125,12 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(best.data(), b.best, (size_t)b.R * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int32_t dev = (e == cudaSuccess) ? sv_batch_status(&b) : SEVO_OK;
     sv_batch_free(&b);
+    if (dev != SEVO_OK) {
+      status = dev;
+      break;
+    }
     if (e != cudaSuccess) {
       sv_set_last_cuda_error(e);
       status = (e == cudaErrorMemoryAllocation) ? SEVO_ERR_OOM : SEVO_ERR_CUDA;

@@ -62,6 +62,7 @@ struct EvalScratch {
                       // [SV_MAX_SEG + 1] device error bits
   void* tc;           // tensor-core composition staging
   size_t tc_bytes;
+  uint32_t* err;      // persistent device error bits (null: use the counters' word)
 };
 #define SV_COUNTERS_BYTES ((SV_MAX_SEG + 4) * 4)
 size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);

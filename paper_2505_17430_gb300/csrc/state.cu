@@ -84,7 +84,7 @@ extern "C" int32_t sevo_state_best(const sevo_state* s, double* best) {
   SV_CUDA(cudaMemcpyAsync(best, s->b.best, (size_t)s->b.R * 8, cudaMemcpyDeviceToHost,
                           s->b.stream));
   SV_CUDA(cudaStreamSynchronize(s->b.stream));
-  return SEVO_OK;
+  return sv_batch_status(const_cast<Batch*>(&s->b));
 }
 
 extern "C" int32_t sevo_state_destroy(sevo_state* s) {
@@ -125,6 +125,8 @@ extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t*
   double b = 0.0;
   SV_CUDA(cudaMemcpyAsync(&b, s->b.best, 8, cudaMemcpyDeviceToHost, s->b.stream));
   SV_CUDA(cudaStreamSynchronize(s->b.stream));
+  const int32_t dev = sv_batch_status(const_cast<Batch*>(&s->b));
+  if (dev != SEVO_OK) return dev;
   if (best) *best = b;
   if (fes) *fes = s->fes;
   if (gens) *gens = s->gens;

@@ -234,3 +234,48 @@ def test_mixed_precision_runs_reach_oracle_quality(S, prec):
     q = O.Problem(2, O.ELLIPSOID, D)
     ref = [O.run(q, O.make_alg(O.ALG_DE_CTPB, NP, budget), s)["success"] for s in range(1, 9)]
     assert res["success"].sum() >= sum(ref) - 2
+
+
+def test_de_ctpb_large_population_sorted_pbest(S):
+    """NP > 512 uses the bitonic (fitness, index) sort for the p-best pool;
+    trial vectors must still match the oracle bit for bit."""
+    fam, D, NP = S.RASTRIGIN, 10, 600
+    p, q, st = _state(S, fam, D, S.DE_CTPB, NP, 10 ** 7, 21)
+    X = O.init_population(21, NP, D)
+    fx = q.eval(X)
+    fx[::7] = fx[0]  # ties, broken by index
+    A = np.zeros((NP, D))
+    st.set(X=X, fx=fx, A=A[:0], asize=0, fes=NP)
+    assert st.de_step(3) == 0
+    g = st.get()
+    U, part = O.de_ctpb_trials(21, 3, X, fx, A, 0)
+    assert np.array_equal(g["part"], part)
+    assert np.array_equal(g["U"], U)
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+def test_batched_mixed_segments_many_jobs_per_cta(S, prec):
+    """A batch of 48 runs over single, hybrid and composition problems at
+    D=30 with NP=540: the fused tensor-core evaluation has more (tile,
+    component) jobs than CTAs, so one CTA alternates composition and
+    non-composition jobs. Every initial fitness matches the oracle within the
+    mixed tolerance, and no bounded device wait gives up (a timeout would
+    surface as SEVO_ERR_TIMEOUT from sevo_state_best / sevo_state_result)."""
+    D, NP = 30, 540
+    tol = {"TF32": 2e-3, "BF16X3": 1e-4}[prec]
+    keys = [(600 + k, k % 8) for k in range(24)]
+    probs = [S.Problem(s, f, D) for s, f in keys for _ in range(2)]
+    seeds = [9000 + r for r in range(len(probs))]
+    st = S.State(probs, S.alg_params(S.DE_CTPB, NP, 10 ** 9, prec=getattr(S, prec)), seeds)
+    fx = st.get()["fx"]
+    for r, (s, f) in enumerate([k for k in keys for _ in range(2)]):
+        q = O.Problem(s, f, D)
+        X = O.init_population(seeds[r], NP, D)
+        want, scale = q.eval(X), q.scale(X)
+        got = fx[r * NP:(r + 1) * NP]
+        bound = tol * np.maximum(np.abs(want), scale) + 1e-13
+        assert (np.abs(got - want) <= bound).all(), (r, f, np.max(np.abs(got - want) / bound))
+    for g in range(1, 4):
+        assert st.step(g) == 0
+    st.best()
+    assert st.result()["gens"] == 3
