@@ -217,6 +217,81 @@ def e2e_rate(S, torch, states, gen, K):
             "d2h_bytes_per_step": sum(r * 8 for r in rows)}, gen + K
 
 
+# ---------------------------------------------------------------- grid
+GRID_DIMS = (10, 30, 50, 100)
+GRID_RUNS = 51
+
+
+def grid_problems(S_or_O, D, make):
+    """30 seeded problems of dimension D: 10 single-family (the six families
+    cycled), 10 hybrid, 10 composition."""
+    out = []
+    for i in range(10):
+        out.append(make(0xC3000000 + 1000 * D + i, i % 6, D))
+    for i in range(10):
+        out.append(make(0xC3100000 + 1000 * D + i, 6, D))
+    for i in range(10):
+        out.append(make(0xC3200000 + 1000 * D + i, 7, D))
+    return out
+
+
+def grid_algs(S, D, prec):
+    b = 10000 * D
+    return [S.alg_params(1, 18 * D, b, prec=prec),   # DE current-to-pbest/1/bin + archive
+            S.alg_params(2, 40, b, prec=prec),       # PSO gbest
+            S.alg_params(3, 40, b, prec=prec)]       # PSO ring
+
+
+def run_grid_bench(S, dims, prec, runs=GRID_RUNS):
+    res = {"wall_ms": 0.0, "evals": 0, "tasks": 0, "success": {}}
+    names = ("de_ctpb", "pso_gbest", "pso_ring")
+    succ = {n: [0, 0] for n in names}
+    for D in dims:
+        probs = grid_problems(S, D, lambda seed, fam, d: S.Problem(seed, fam, d))
+        algs = grid_algs(S, D, prec)
+        tasks = [(pi, ai, 1 + r + 1000 * pi) for pi in range(len(probs)) for ai in range(3)
+                 for r in range(runs)]
+        r = S.sevo_run_grid(probs, algs, tasks)
+        res["wall_ms"] += r["wall_ms"]
+        res["evals"] += int(r["evals"])
+        res["tasks"] += len(tasks)
+        for (pi, ai, _), ok in zip(tasks, r["success"]):
+            succ[names[ai]][0] += int(ok)
+            succ[names[ai]][1] += 1
+    res["success"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in succ.items()}
+    return res
+
+
+def oracle_grid_sample(dims, frac=0.1):
+    """The oracle's thread pool on 3 problems (single, hybrid, composition)
+    per (algorithm, D) with one run each at frac of the budget; extrapolated
+    to the full grid (30 problems x 51 runs, whole budget) by evaluations."""
+    import oracle as O
+    probs, algs, seeds, full_evals, sample_evals = [], [], [], 0, 0
+    for D in dims:
+        gp = grid_problems(O, D, lambda seed, fam, d: O.Problem(seed, fam, d))
+        for pi in (0, 10, 20):
+            for kind, NP in ((O.ALG_DE_CTPB, 18 * D), (O.ALG_PSO_GBEST, 40),
+                             (O.ALG_PSO_RING, 40)):
+                probs.append(gp[pi])
+                algs.append(O.make_alg(kind, NP, int(frac * 10000 * D)))
+                seeds.append(1 + pi)
+                sample_evals += int(frac * 10000 * D)
+                full_evals += 10 * GRID_RUNS * 10000 * D  # 10 problems of this type x 51 runs
+    t0, c0 = time.perf_counter(), time.process_time()
+    O.run_many(probs, algs, seeds, nthreads=oracle_cores())
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
+    cores = oracle_cores()
+    # CPU seconds scale with evaluations; a full grid keeps every core busy
+    full_cpu = cpu * full_evals / sample_evals
+    return {"sample_wall_s": round(dt, 3), "sample_cpu_s": round(cpu, 3),
+            "sample_evals": sample_evals, "cores": cores,
+            "extrapolated_full_wall_s": round(full_cpu / cores, 1),
+            "sample": f"3 problems (single, hybrid, composition) x 3 algorithms x D in {list(dims)}, "
+                      f"one run each at {frac:g} of the budget, thread pool on all host cores; "
+                      "extrapolated to 30 problems x 51 runs at the full budget by evaluation count"}
+
+
 # ---------------------------------------------------------------- oracle arm
 class OracleStep:
     """The oracle's own operators on a bounded sample of the workload: the
@@ -322,6 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grid", action="store_true", help="skip the run-grid measurement")
     ap.add_argument("--only-steps", action="store_true",
                     help="time the steps only (for launch-list profiling)")
     args = ap.parse_args()
@@ -386,6 +462,25 @@ def main():
     roof = eval_kernel_roofline(S, torch, probs, peaks)
     modes = mode_eval_rates(S, torch, probs)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
+    grid = None
+    if not args.no_grid:
+        g = run_grid_bench(S, GRID_DIMS, S.TF32)
+        g64 = run_grid_bench(S, (10,), S.FP64)
+        g32 = run_grid_bench(S, (10,), S.TF32)
+        og = None if args.no_cpu_baseline else oracle_grid_sample(GRID_DIMS)
+        grid = {"workload": "30 problems (10 single, 10 hybrid, 10 composition) x D in "
+                            "{10,30,50,100} x 51 runs x {DE ctpb/1/bin+archive NP=18D, PSO gbest "
+                            "NP=40, PSO ring NP=40}, budget 10000*D, TF32 + FP64 refinement",
+                "gpu_wall_s": round(g["wall_ms"] / 1e3, 3), "evals": g["evals"],
+                "evals_per_s": round(g["evals"] / (g["wall_ms"] / 1e3), 1),
+                "tasks": g["tasks"], "success_rate_tf32": g["success"],
+                "d10_success_fp64_vs_tf32": {"fp64": g64["success"], "tf32": g32["success"],
+                                             "fp64_wall_s": round(g64["wall_ms"] / 1e3, 3),
+                                             "tf32_wall_s": round(g32["wall_ms"] / 1e3, 3)},
+                "oracle": og}
+        if og:
+            grid["speedup_vs_oracle_extrapolated"] = round(
+                og["extrapolated_full_wall_s"] / (g["wall_ms"] / 1e3), 1)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
@@ -396,7 +491,7 @@ def main():
                        "l2": "working set ~160 MB per step > 129 MB L2 (no flush needed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "fp64_path": fp64, "eval_only_evals_per_s": modes}
+            "clocks": clk, "fp64_path": fp64, "eval_only_evals_per_s": modes, "grid": grid}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
