@@ -7,11 +7,14 @@
 //   2. gemm: persistent CTAs over jobs (128-row tile, 128-column chunk of z),
 //      full K per job: one thread issues TMA loads of A and B K-blocks into a
 //      multi-stage shared-memory ring (128B swizzle), one thread issues
-//      tcgen05.mma into a double-buffered TMEM accumulator, four epilogue
-//      warps walk their row's chunk (thread = row = TMEM lane) and store the
-//      per-group FP32 accumulators of the chunk plus its first and last z;
-//   3. combine: per row, the chunk records are merged in column order (the
-//      Rosenbrock pair across a chunk border is added here), the groups are
+//      tcgen05.mma into one of four TMEM accumulators (the whole 512-column
+//      TMEM, so the MMA runs up to three jobs ahead of the epilogue), sixteen
+//      epilogue warps walk the chunk (four per TMEM lane quarter, 32 columns
+//      each; thread = row = TMEM lane) and store, per 32-column slice, the
+//      per-group FP32 accumulators plus the slice's first and last z, row
+//      index fastest so that a warp's stores are coalesced;
+//   3. combine: per row, the slice records are merged in column order (the
+//      Rosenbrock pair across a slice border is added here), the groups are
 //      finished, the FP64 error is written and rows below the refinement
 //      threshold are listed.
 // Splitting z into 128-column chunks gives tiles x chunks independent jobs,
@@ -23,21 +26,24 @@
 namespace {
 
 constexpr int BM = 128, BN = 128;
-constexpr int NEPI = 4;
+constexpr int NBUF = 4;              // TMEM accumulators of BN columns (512 in all)
+constexpr int WPQ = 4;               // epilogue warps per TMEM lane quarter
+constexpr int NEPI = 4 * WPQ;
+constexpr int SUB = BN / WPQ;        // columns per epilogue warp and per record
 constexpr int WARP_TMA = NEPI, WARP_MMA = NEPI + 1;
 constexpr int NTHREADS = (NEPI + 2) * 32;
 constexpr int KB_BYTES = 128 * 128;  // one 128-row x 128-byte K block (A or B)
-constexpr int REC = 3 * SV_MAXG + 2;  // floats per (row, chunk) record
+constexpr int REC = 3 * SV_MAXG + 2;  // float slots per (row, slice) record
 constexpr long long WAIT_BUDGET = 4000000000LL;
 
 struct BigGeom {
-  int D, kpad, nkb, nchunks, ntiles, stages, stage_bytes;
+  int D, kpad, nkb, nchunks, nsub, ntiles, stages, stage_bytes;
   int64_t N;
   uint32_t idesc;
 };
 
 struct __align__(8) BigBars {
-  uint64_t full[4], empty[4], t_full[2], t_empty[2];
+  uint64_t full[4], empty[4], t_full[NBUF], t_empty[NBUF];
   uint32_t tmem_base;
   int abort;
 };
@@ -48,19 +54,38 @@ __device__ __forceinline__ void big_abort(BigBars* b, uint32_t* dev_err) {
 }
 
 // ---------------------------------------------------------------- convert
+// One warp per row (grid-stride), lane = 4 consecutive columns per step:
+// 16-byte FP64 loads when rows are 16-byte aligned, 16-byte (TF32) or 8-byte
+// (BF16 hi and lo) stores; s_c = |x - o_c|^2 in FP32 by a warp reduction.
+constexpr int CVT_WARPS = 8;
+
 template <bool BF16>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CVT_WARPS * 32)
     convert_kernel(const ProblemDev* __restrict__ P, int c, const double* __restrict__ X,
-                   int64_t ld, int64_t row0, int64_t N, int D, int kpad, float* __restrict__ A32,
-                   __nv_bfloat16* __restrict__ Ahi, __nv_bfloat16* __restrict__ Alo,
-                   double* __restrict__ s_out) {
-  __shared__ float red[4];
+                   int64_t ld, int64_t row0, int64_t N, int D, int kpad, bool vec,
+                   float* __restrict__ A32, __nv_bfloat16* __restrict__ Ahi,
+                   __nv_bfloat16* __restrict__ Alo, double* __restrict__ s_out) {
   const float* __restrict__ oh = P->oh32[c];
   const float* __restrict__ ol = P->ol32[c];
-  for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * CVT_WARPS;
+  for (int64_t r = (int64_t)blockIdx.x * CVT_WARPS + (threadIdx.x >> 5); r < N; r += nw) {
     const double* xr = X + (row0 + r) * ld;
     float sq = 0.f;
-    for (int k0 = threadIdx.x * 4; k0 < kpad; k0 += blockDim.x * 4) {
+    for (int k0 = lane * 4; k0 < kpad; k0 += 128) {
+      double xv[4] = {0.0, 0.0, 0.0, 0.0};
+      if (vec && k0 + 3 < D) {
+        const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
+        const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k0 + 2));
+        xv[0] = p0.x;
+        xv[1] = p0.y;
+        xv[2] = p1.x;
+        xv[3] = p1.y;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (k0 + q < D) xv[q] = __ldg(xr + k0 + q);
+      }
       float d[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -68,7 +93,7 @@ __global__ void __launch_bounds__(128)
         d[q] = 0.f;
         if (k < D) {
           float xh, xl;
-          sv_split_hi_lo(__ldg(xr + k), xh, xl);
+          sv_split_hi_lo(xv[q], xh, xl);
           d[q] = (xh - __ldg(oh + k)) + (xl - __ldg(ol + k));
           sq += d[q] * d[q];
         }
@@ -95,10 +120,7 @@ __global__ void __launch_bounds__(128)
     if (s_out) {
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
-      __syncthreads();
-      if (threadIdx.x == 0) s_out[(row0 + r) * SV_MAXC + c] = (double)(red[0] + red[1] + red[2] + red[3]);
-      __syncthreads();
+      if (lane == 0) s_out[(row0 + r) * SV_MAXC + c] = (double)sq;
     }
   }
 }
@@ -119,7 +141,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_init(&bars.full[s], 1);
       tc::mbar_init(&bars.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       tc::mbar_init(&bars.t_full[b], 1);
       tc::mbar_init(&bars.t_empty[b], NEPI);
     }
@@ -127,7 +149,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc::fence_mbar_init();
   }
   if (warp == WARP_MMA) {
-    tc::tmem_alloc(&bars.tmem_base, 2 * BN);
+    tc::tmem_alloc(&bars.tmem_base, NBUF * BN);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -171,8 +193,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int jl = 0;
       bool ok = true;
       for (int job = blockIdx.x; job < njobs_total && ok; job += gridDim.x, ++jl) {
-        const int a = jl & 1;
-        const uint32_t u = (uint32_t)(jl >> 1);
+        const int a = jl % NBUF;
+        const uint32_t u = (uint32_t)(jl / NBUF);
         if (!tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
           big_abort(&bars, dev_err);
           break;
@@ -214,36 +236,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else {
-    // epilogue: thread = row of the tile = TMEM lane
-    const int r = warp * 32 + lane;
+    // epilogue: warp w reads TMEM lane quarter w % 4 (thread = row of the
+    // tile) and columns [SUB * (w / 4), SUB * (w / 4 + 1)) of the chunk
+    const int r = (warp & 3) * 32 + lane;
+    const int sl = warp >> 2;
+    const int64_t N = geo.N;
     int jl = 0;
     for (int job = blockIdx.x; job < njobs_total; job += gridDim.x, ++jl) {
       const int tile = job / geo.nchunks, nb = job % geo.nchunks;
-      const int a = jl & 1;
-      const uint32_t u = (uint32_t)(jl >> 1);
+      const int a = jl % NBUF;
+      const uint32_t u = (uint32_t)(jl / NBUF);
       if (!tc::mbar_wait(&bars.t_full[a], u & 1u, &bars.abort, WAIT_BUDGET)) {
         big_abort(&bars, dev_err);
         break;
       }
       tc::tc_fence_after();
-      const int c0 = nb * BN, c1 = min(geo.D, c0 + BN);
+      const int sb = nb * WPQ + sl;  // slice index within the row
+      const int c0 = sb * SUB, c1 = min(geo.D, c0 + SUB);
       const int64_t row = (int64_t)tile * BM + r;
-      float* rec = part + (row * geo.nchunks + nb) * REC;
-      const bool live = row < geo.N;
+      float* rec = part + (int64_t)sb * REC * N + row;  // slot k at rec[k * N]
+      const bool live = row < N;
       float zf = 0.f, zl = 0.f;
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN);
+      const uint32_t taddr =
+          tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(a * BN + sl * SUB);
       if (c0 < c1) {
         walk_cols<!BF16>(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
           if (live) {
-            rec[3 * g] = acc.a0;
-            rec[3 * g + 1] = acc.a1;
-            rec[3 * g + 2] = acc.a2;
+            rec[(3 * g) * N] = acc.a0;
+            rec[(3 * g + 1) * N] = acc.a1;
+            rec[(3 * g + 2) * N] = acc.a2;
           }
         });
       }
       if (live) {
-        rec[3 * SV_MAXG] = zf;
-        rec[3 * SV_MAXG + 1] = zl;
+        rec[(3 * SV_MAXG) * N] = zf;
+        rec[(3 * SV_MAXG + 1) * N] = zl;
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -257,7 +284,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int k = 0; k < 1000; ++k) __nanosleep(1000);
     }
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 2 * BN);
+    tc::tmem_dealloc(tmem, NBUF * BN);
   }
 }
 
@@ -273,42 +300,68 @@ __device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, i
   return comp ? 0 : P.gid[c][i];
 }
 
-__global__ void combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D,
-                               int nchunks, const float* __restrict__ part, int64_t row0,
-                               int64_t N, double* __restrict__ out, double* __restrict__ comp_g,
-                               ListOutB lo) {
+// one warp per row: lane l merges slices l, l + 32, ... into per-group
+// accumulators (adding the Rosenbrock pair across a slice border from the
+// previous slice's last z), then the groups are summed across the warp
+constexpr int CMB_WARPS = 4;
+
+__global__ void __launch_bounds__(CMB_WARPS * 32)
+    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub,
+                   const float* __restrict__ part, int64_t row0, int64_t N,
+                   double* __restrict__ out, double* __restrict__ comp_g, ListOutB lo) {
   const ProblemDev& P = *Pp;
-  for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < N;
-       lr += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int ng = comp ? 1 : P.ngroups;
+  const int64_t nw = (int64_t)gridDim.x * CMB_WARPS;
+  for (int64_t lr = (int64_t)blockIdx.x * CMB_WARPS + (threadIdx.x >> 5); lr < N; lr += nw) {
     Acc32 acc[SV_MAXG];
+#pragma unroll
     for (int g = 0; g < SV_MAXG; ++g) acc32_init(acc[g]);
-    const float* recs = part + lr * (int64_t)nchunks * REC;
-    float zlast_prev = 0.f;
-    for (int nb = 0; nb < nchunks; ++nb) {
-      const int c0 = nb * BN, c1 = min(D, c0 + BN);
+    for (int sb = lane; sb < nsub; sb += 32) {
+      const int c0 = sb * SUB, c1 = min(D, c0 + SUB);
       if (c0 >= c1) break;
-      const float* rec = recs + (int64_t)nb * REC;
+      const float* rec = part + (int64_t)sb * REC * N + lr;  // slot k at rec[k * N]
       const int g0 = group_of(P, c, comp, c0), g1 = group_of(P, c, comp, c1 - 1);
-      for (int g = g0; g <= g1; ++g) {
-        acc[g].a0 += rec[3 * g];
-        acc[g].a1 += rec[3 * g + 1];
-        acc[g].a2 += rec[3 * g + 2];
+#pragma unroll
+      for (int g = 0; g < SV_MAXG; ++g) {
+        if (g >= g0 && g <= g1) {
+          acc[g].a0 += rec[(3 * g) * N];
+          acc[g].a1 += rec[(3 * g + 1) * N];
+          acc[g].a2 += rec[(3 * g + 2) * N];
+        }
       }
-      if (nb > 0) {  // Rosenbrock pair (c0 - 1, c0) inside one group
+      if (sb > 0) {  // Rosenbrock pair (c0 - 1, c0) inside one group
         const int gp = group_of(P, c, comp, c0 - 1);
         const int body = comp ? P.cbody[c] : P.gbody[gp];
-        if (gp == g0 && body == SEVO_ROSENBROCK)
-          term32(SEVO_ROSENBROCK, zlast_prev, 0.f, true, rec[3 * SV_MAXG], P, acc[gp]);
+        if (gp == g0 && body == SEVO_ROSENBROCK) {
+          const float zprev = part[((int64_t)(sb - 1) * REC + 3 * SV_MAXG + 1) * N + lr];
+#pragma unroll
+          for (int g = 0; g < SV_MAXG; ++g)
+            if (g == gp) term32(SEVO_ROSENBROCK, zprev, 0.f, true, rec[(3 * SV_MAXG) * N], P, acc[g]);
+        }
       }
-      zlast_prev = rec[3 * SV_MAXG + 1];
     }
     double gsum = 0.0;
-    const int ng = comp ? 1 : P.ngroups;
-    for (int g = 0; g < ng; ++g) {
-      const int body = comp ? P.cbody[c] : P.gbody[g];
-      const int n = comp ? D : P.gstart[g + 1] - P.gstart[g];
-      gsum += (double)finalize32(body, acc[g], n);
+#pragma unroll
+    for (int g = 0; g < SV_MAXG; ++g) {
+      if (g < ng) {
+        float a0 = acc[g].a0, a1 = acc[g].a1, a2 = acc[g].a2;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+          a0 += __shfl_xor_sync(0xffffffffu, a0, m);
+          a1 += __shfl_xor_sync(0xffffffffu, a1, m);
+          a2 += __shfl_xor_sync(0xffffffffu, a2, m);
+        }
+        Acc32 t;
+        t.a0 = a0;
+        t.a1 = a1;
+        t.a2 = a2;
+        const int body = comp ? P.cbody[c] : P.gbody[g];
+        const int n = comp ? D : P.gstart[g + 1] - P.gstart[g];
+        gsum += (double)finalize32(body, t, n);
+      }
     }
+    if (lane != 0) continue;
     const int64_t row = row0 + lr;
     if (comp) {
       comp_g[row * SV_MAXC + c] = gsum;
@@ -381,8 +434,8 @@ size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
   (void)prec;
   const int kpad = (D + 63) / 64 * 64;
-  const int nchunks = ((D + 127) / 128 * 128) / BN;
-  size_t b = al256b((size_t)rows * kpad * 4) + al256b((size_t)rows * nchunks * REC * 4);
+  const int nsub = ((D + 127) / 128 * 128) / SUB;
+  size_t b = al256b((size_t)rows * kpad * 4) + al256b((size_t)rows * nsub * REC * 4);
   if (any_comp) b += al256b((size_t)rows * SV_MAXC * 16);
   return b;
 }
@@ -405,6 +458,7 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   g.kpad = h.kpad;
   g.nkb = h.kpad / (bf16 ? 64 : 32);
   g.nchunks = h.npad / BN;
+  g.nsub = h.npad / SUB;
   g.ntiles = (int)((N + BM - 1) / BM);
   g.N = N;
   g.stage_bytes = (bf16 ? 4 : 2) * KB_BYTES;
@@ -415,7 +469,7 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   void* Abase = cp;
   cp += al256b((size_t)N * h.kpad * 4);
   float* part = (float*)cp;
-  cp += al256b((size_t)N * g.nchunks * REC * 4);
+  cp += al256b((size_t)N * g.nsub * REC * 4);
   // composition staging: g_c in the first N x SV_MAXC doubles, s_c in the
   // next; both indexed by global row (row0 + local row)
   double* comp_g = nullptr;
@@ -448,19 +502,25 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     if (e != cudaSuccess) return e;
     attr_done[bf16] = true;
   }
-  const int cvt_grid = (int)std::min<int64_t>(N, (int64_t)sv_num_sms() * 16);
+  const int cvt_grid =
+      (int)std::min<int64_t>((N + CVT_WARPS - 1) / CVT_WARPS, (int64_t)sv_num_sms() * 8);
+  const bool vec = ((uintptr_t)X % 16 == 0) && (ld % 2 == 0);
   const int njobs = g.ntiles * g.nchunks;
   const int ggrid = std::min(njobs, sv_num_sms());
   const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 127) / 128, sv_num_sms() * 4));
+  const int mgrid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((N + CMB_WARPS - 1) / CMB_WARPS, (int64_t)sv_num_sms() * 16));
   const ListOutB lo{list, count, nonfinite, list_off};
   cudaError_t e;
   for (int c = 0; c < h.ncomp; ++c) {
     if (bf16)
-      convert_kernel<true><<<cvt_grid, 128, 0, st>>>(p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad,
-                                                     nullptr, Ahi, Alo, comp ? comp_s : nullptr);
+      convert_kernel<true><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
+          p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, nullptr, Ahi, Alo,
+          comp ? comp_s : nullptr);
     else
-      convert_kernel<false><<<cvt_grid, 128, 0, st>>>(p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad,
-                                                      A32, nullptr, nullptr, comp ? comp_s : nullptr);
+      convert_kernel<false><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
+          p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, A32, nullptr, nullptr,
+          comp ? comp_s : nullptr);
     sv_note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (bf16)
@@ -471,8 +531,8 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
                                                             dev_err);
     sv_note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    combine_kernel<<<cgrid, 128, 0, st>>>(p->desc_d, c, comp, h.D, g.nchunks, part, seg.row0, N,
-                                          out, comp_g, lo);
+    combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, part,
+                                                     seg.row0, N, out, comp_g, lo);
     sv_note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
