@@ -107,8 +107,21 @@ def make_states(S, prec, seed0, torch):
     return probs, states
 
 
+RESTART_EVERY = 25
+
+
 def run_steps(states, first_gen, n):
+    """Generations first_gen .. first_gen + n - 1 of every state.  Every
+    RESTART_EVERY generations each run restarts from a fresh uniform
+    population (sevo_state_restart, new seeds; its work is inside the timed
+    region, its evaluations are not counted), so the timed generations stay
+    in the early phase the microbench describes (X ~ U[-100, 100]) instead
+    of drifting into the refinement-heavy end of converged runs, which the
+    run-grid measurement covers."""
     for g in range(first_gen, first_gen + n):
+        if g % RESTART_EVERY == 0:
+            for k, st in enumerate(states):
+                st.restart([(g * 7919 + 1000 * k + r) & 0xFFFFFFFF for r in range(st.R)])
         for st in states:
             rc = st.step(g)
             if rc != 0:
@@ -127,44 +140,77 @@ def time_steps(torch, states, gen, K):
     return e0.elapsed_time(e1), gen
 
 
-def eval_kernel_roofline(S, torch, probs, peaks):
-    """Dominant kernel: the fused tcgen05 evaluation.  One launch over a
-    population of 73,728 rows (the step's row count) of one problem; the
-    algorithmic bytes are the FP64 rows read (D * 8) plus the FP64 result
-    written (8) per row."""
-    rows = len(ALGS) * FAMILIES * NP
-    X = torch.empty((rows, D), dtype=torch.float64, device="cuda").uniform_(-100, 100)
-    out = torch.empty(rows, dtype=torch.float64, device="cuda")
-    p = probs[2]
-    for _ in range(5):
-        p.evaluate(X, out, prec=S.TF32)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 50
+def _source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2505_17430_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name, files):
+    """DRAM bytes per row of a kernel from its committed ncu summary: the
+    summary's 'traffic_bytes_per_row' and 'source_hash' lines; None if the
+    kernel's sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    per_row = src = None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_row:"):
+            per_row = float(line.split(":", 1)[1])
+        elif line.startswith("source_hash:"):
+            src = line.split(":", 1)[1].strip()
+    if per_row is None or src != _source_hash(files):
+        return None
+    return per_row
+
+
+FUSED_SOURCES = ("eval_tc.cu", "tc_walk.cuh", "bodies.cuh", "tc_ptx.cuh")
+
+
+def traced_step_kernels(S, torch, states, gen, K):
+    """Per-kernel device time from a traced repeat of the timed steps (CUDA
+    events recorded on the launching stream around every launch)."""
+    S.trace_enable(True)
+    gen = run_steps(states, gen, K)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        p.evaluate(X, out, prec=S.TF32)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    algo_bytes = rows * (D * 8 + 8)
-    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    t = S.trace_read()
+    S.trace_enable(False)
+    return {k: v for k, v in t.items() if v[0] > 0}, gen
+
+
+def rooflines(trace, states, peaks):
+    """Dominant kernel (fused tcgen05 evaluation) and the streaming DE/PSO
+    kernels against the measured HBM copy bandwidth."""
     peak = peaks.get("hbm_gbs")
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "eval_tc_fused_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            t = json.load(open(tpath))
-            if t.get("rows") and t.get("bytes"):
-                traffic = t["bytes"] / t["rows"] * rows
-        except Exception:
-            traffic = None
-    return {"kernel": "eval_tc_fused<tf32>", "bound": "hbm", "achieved": round(achieved, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if peak else None,
-            "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
-            "launch_ms": round(ms, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
-            if peak else "fallback"}
+    src = "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"
+    rows = FAMILIES * NP  # rows per launch: one state's six populations
+    total_ms = sum(ms for _, ms in trace.values())
+
+    def entry(kind, bytes_per_row, bound="hbm"):
+        n, ms = trace.get(kind, (0, 0.0))
+        if not n:
+            return None
+        per = ms / n
+        algo = rows * bytes_per_row
+        ach = algo / (per * 1e-3) / 1e9
+        return {"kernel": kind, "bound": bound, "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4) if peak else None,
+                "algorithmic_bytes_per_launch": algo, "launch_ms": round(per, 4),
+                "launches": n, "share_of_step": round(ms / total_ms, 4), "peak_source": src}
+
+    main = entry("eval_tc_fused", D * 8 + 8)
+    per_row = profiled_traffic("eval_tc_fused_tf32_d100.md", FUSED_SOURCES)
+    main["traffic"] = round(per_row * rows) if per_row else None
+    # DE trial: target + three donors read, trial written (FP64 rows) + 16 B
+    # of partner indices; PSO move: x, v, pbest read, x, v written (the guide
+    # row is one per run or neighbourhood and is served from L2)
+    stream = {k: entry(k, b) for k, b in (("de_trial", 5 * 8 * D + 16), ("pso_move", 5 * 8 * D))}
+    shares = {k: {"launches": n, "ms": round(ms, 3), "share": round(ms / total_ms, 4)}
+              for k, (n, ms) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+    return main, stream, shares
 
 
 def mode_eval_rates(S, torch, probs):
@@ -187,6 +233,78 @@ def mode_eval_rates(S, torch, probs):
         dt = (time.perf_counter() - t0) / reps
         res[name] = round(rows * len(probs) / dt, 1)
     return res
+
+
+def large_d_rates(S, torch, peaks):
+    """Mixed precision at large D (N = 1024 rows, D in {1000, 5000}; and
+    16,384 rows at D = 1000 to fill the GPU): evaluation rate per mode on a
+    shifted-rotated Rastrigin, a hybrid and a composition instance, against
+    the FP64 GPU path; the rotation GEMM's own tensor rate from traced launch
+    times (2 N D^2 flops per component; BF16X3 counts its three bf16
+    products against the bf16 peak, TF32 is held against the bf16 peak x
+    1.1 / 2.25, the nominal dense TF32 : BF16 ratio)."""
+    bf16 = peaks.get("bf16_tflops")
+    res = []
+    for Dl, N in ((1000, 1024), (5000, 1024), (1000, 16384)):
+        X = torch.empty((N, Dl), dtype=torch.float64, device="cuda").uniform_(-100, 100)
+        out = torch.empty(N, dtype=torch.float64, device="cuda")
+        fams = (2, 6, 7) if N == 1024 else (2,)
+        for fam in fams:
+            p = S.Problem(0x5EB10000 + 16 * fam + Dl, fam, Dl)
+            row = {"D": Dl, "N": N, "family": ["ellipsoid", "rosenbrock", "rastrigin", "schwefel",
+                                               "ackley", "griewank", "hybrid", "composition"][fam],
+                   "components": p.ncomp}
+            for name, prec in (("tf32", S.TF32), ("bf16x3", S.BF16X3), ("fp64", S.FP64)):
+                if prec == S.FP64 and (Dl > 1000 or fam == 7 or N > 1024):
+                    continue
+                reps = 3 if prec == S.FP64 else 10
+                p.evaluate(X, out, prec=prec)
+                torch.cuda.synchronize()
+                S.trace_enable(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    p.evaluate(X, out, prec=prec)
+                e1.record()
+                torch.cuda.synchronize()
+                t = S.trace_read()
+                S.trace_enable(False)
+                ms = e0.elapsed_time(e1) / reps
+                row[name] = {"evals_per_s": round(N / (ms * 1e-3), 1), "ms_per_call": round(ms, 4)}
+                n, gms = t.get("gemm_big", (0, 0.0))
+                if n and prec != S.FP64:
+                    fl = 2.0 * N * Dl * Dl  # per launch (one component)
+                    tf = fl / (gms / n * 1e-3) / 1e12
+                    pk = (bf16 * 1.1 / 2.25) if prec == S.TF32 else bf16 / 3.0
+                    row[name]["gemm_tflops"] = round(tf, 1)
+                    row[name]["gemm_frac_of_tensor_peak"] = round(tf / pk, 4) if bf16 else None
+                    row[name]["gemm_share_of_call"] = round(gms / reps / ms, 3)
+            res.append(row)
+        del X, out
+    return res
+
+
+def c0_single_run(S):
+    """The smallest configuration: DE/rand/1/bin, NP = 50, D = 10, FP64, one
+    run of 1e5 evaluations on shifted-rotated Rastrigin, seed 1 -- GPU run
+    through sevo_run_grid (graph-captured generations) and the oracle's own
+    run on one host core."""
+    import oracle as O
+    p = S.Problem(0x5EB00002, 2, 10)
+    a = S.alg_params(S.DE_RAND1, 50, 100000)
+    S.sevo_run_grid([p], [a], [(0, 0, 1)])  # warm-up (instance upload, graph build)
+    t0 = time.perf_counter()
+    r = S.sevo_run_grid([p], [a], [(0, 0, 1)])
+    wall = time.perf_counter() - t0
+    q = O.Problem(0x5EB00002, 2, 10)
+    t0 = time.perf_counter()
+    ro = O.run(q, O.make_alg(O.ALG_DE_RAND1, 50, 100000), 1)
+    owall = time.perf_counter() - t0
+    return {"workload": "DE/rand/1/bin NP=50 D=10 F=0.5 CR=0.9 FP64, 1e5 evals, shifted-rotated "
+                        "Rastrigin, seed 1",
+            "gpu_wall_s": round(wall, 4), "gpu_device_ms": round(r["wall_ms"], 3),
+            "gpu_best": r["best"][0], "oracle_wall_s": round(owall, 4), "oracle_best": ro["best"],
+            "oracle_cores": 1, "gens": int(r["gens"][0])}
 
 
 def e2e_rate(S, torch, states, gen, K):
@@ -363,7 +481,9 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    npop = NP
+    # each step is the workload's generation on a population sample sized so
+    # that the whole run takes about a minute on the host cores
+    npop = max(64, min(NP, int(NP * 24 / max(args.steps + args.warmup, 1))))
     o = OracleStep(npop)
     for _ in range(args.warmup):
         o.step()
@@ -393,11 +513,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grid", action="store_true", help="skip the run-grid measurement")
+    ap.add_argument("--no-large-d", action="store_true", help="skip the D=1000/5000 rates")
     ap.add_argument("--only-steps", action="store_true",
                     help="time the steps only (for launch-list profiling)")
     args = ap.parse_args()
@@ -458,9 +579,12 @@ def main():
     fp64 = {"value": round(evals_per_step / (ms64 / 2 * 1e-3), 1),
             "ms_per_step": round(ms64 / 2, 3)}
     del st64
-    e2e, gen = e2e_rate(S, torch, states, gen, max(3, args.steps // 4))
-    roof = eval_kernel_roofline(S, torch, probs, peaks)
+    traced, gen = traced_step_kernels(S, torch, states, gen, min(args.steps, 200))
+    roof, stream_roof, shares = rooflines(traced, states, peaks)
+    e2e, gen = e2e_rate(S, torch, states, gen, max(3, min(args.steps // 4, 400)))
     modes = mode_eval_rates(S, torch, probs)
+    large = None if args.no_large_d else large_d_rates(S, torch, peaks)
+    c0 = c0_single_run(S)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     grid = None
     if not args.no_grid:
@@ -489,9 +613,14 @@ def main():
                        "algorithms": [a for a, _ in ALGS], "evals_per_step": evals_per_step,
                        "prec": "tf32 rotation, fp32 bodies, fp64 shift/refine/positions",
                        "l2": "working set ~160 MB per step > 129 MB L2 (no flush needed)",
+                       "kernel_times": "per-kernel CUDA-event times from a traced repeat of "
+                                       "the timed steps (events on the launching stream)",
+                       "restart_every": RESTART_EVERY,
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "fp64_path": fp64, "eval_only_evals_per_s": modes, "grid": grid}
+            "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
+            "kernel_shares": shares, "eval_only_evals_per_s": modes, "large_d": large,
+            "c0_single_run": c0, "grid": grid}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

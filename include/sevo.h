@@ -57,6 +57,9 @@ int32_t sevo_version(void);
  * (launch accounting for benchmarks; graph replays count the kernels of
  * every replayed generation) */
 int64_t sevo_kernel_launches(void);
+/* name of the CUDA error behind the calling thread's most recent
+ * SEVO_ERR_CUDA ("" if none); static storage */
+const char* sevo_last_cuda_error(void);
 
 /* ---- problem families and precision modes ----------------------------- */
 enum sevo_family {
@@ -200,6 +203,15 @@ typedef struct sevo_state sevo_state; /* opaque, library-owned */
 int32_t sevo_state_create(const sevo_problem* p, const sevo_alg_params* a, uint64_t seed,
                           void* stream, sevo_state** out);
 int32_t sevo_state_destroy(sevo_state* s);
+/* Restart every run of the state from a fresh initial population drawn with
+ * seeds[0..R) (R = the runs given at creation): the state becomes what
+ * sevo_state_create / _create_batch would have made with these seeds and
+ * the same problems and parameters (population, fitness, archive emptied,
+ * velocities zeroed, personal bests, guides, best-so-far, evaluation and
+ * generation counts), without reallocating.  A restart strategy for the
+ * caller's outer loop; the paper's algorithms themselves never restart.
+ * Enqueued on the state's stream. */
+int32_t sevo_state_restart(sevo_state* s, const uint64_t* seeds);
 
 /* Batched state: R independent runs of the same algorithm in one state,
  * run r on problems[r] (all of one dimension D) with Philox key seeds[r].
@@ -283,6 +295,41 @@ typedef struct {          /* caller-allocated host arrays, ntasks entries each *
  * all their runs, generations captured into CUDA graphs.  Results equal the
  * single-run state API's for the same (problem, alg, seed).  Synchronous. */
 int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, void* stream);
+
+/* ---- kernel tracing (library infrastructure; the paper has no counterpart)
+ * While tracing is on, every kernel this library launches on a stream that is
+ * not being captured into a graph is bracketed by two CUDA events recorded on
+ * that same stream, so the device time of each launch is measured where it
+ * ran.  Launches made during graph capture (sevo_run_grid) are not traced.
+ * Kinds are fixed; sevo_trace_name gives each one's name. */
+enum sevo_trace_kind {
+  SEVO_TK_EVAL_TC_FUSED = 0, /* tensor-core evaluation, D <= 128 (fused)     */
+  SEVO_TK_EVAL_CC,           /* CUDA-core evaluation (FP64 or FP32 path)      */
+  SEVO_TK_REFINE,            /* FP64 re-evaluation of listed rows             */
+  SEVO_TK_COMPOSE,           /* composition weighting of component values     */
+  SEVO_TK_CONVERT,           /* D > 128: x - o to TF32 / BF16 operand         */
+  SEVO_TK_GEMM_BIG,          /* D > 128: rotation GEMM + fused bodies         */
+  SEVO_TK_COMBINE,           /* D > 128: merge of column-slice records        */
+  SEVO_TK_INIT,              /* initial population                             */
+  SEVO_TK_DE_TRIAL,          /* DE mutation + crossover + repair               */
+  SEVO_TK_DE_RANK,           /* p-best ranking for current-to-pbest           */
+  SEVO_TK_DE_SELECT,         /* DE selection decisions + archive slots        */
+  SEVO_TK_DE_APPLY,          /* DE row copies (population, archive)           */
+  SEVO_TK_PSO_MOVE,          /* PSO velocity + position update                */
+  SEVO_TK_PSO_UPDATE,        /* PSO personal/neighbourhood best               */
+  SEVO_TK_PSO_COPY,          /* PSO personal-best row copies                  */
+  SEVO_TK_CONTROL,           /* generation counters, fills                     */
+  SEVO_TRACE_KINDS
+};
+/* on != 0: clear the accumulators and start tracing; on == 0: stop (the
+ * accumulated figures stay readable).  Host-side; cheap when off. */
+int32_t sevo_trace_enable(int32_t on);
+/* Wait for every traced launch to finish and add its event-measured time to
+ * the per-kind totals; counts and ms are caller arrays of SEVO_TRACE_KINDS
+ * entries (either may be NULL). */
+int32_t sevo_trace_read(int64_t* counts, double* ms);
+/* static name of a kind ("" if out of range) */
+const char* sevo_trace_name(int32_t kind);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,7 @@ FP64, TF32, BF16X3, FP32 = 0, 1, 2, 3
 PREC_NAMES = {FP64: "fp64", TF32: "tf32", BF16X3: "bf16x3", FP32: "fp32"}
 DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING = 0, 1, 2, 3
 OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED, ERR_STATE = range(-1, -8, -1)
 REFINE_THRESHOLD = 1e-4
 SUCCESS_THRESHOLD = 1e-8
 
@@ -65,6 +66,7 @@ SIGNATURES = {
     "sevo_strerror": (C.c_char_p, [C.c_int32]),
     "sevo_version": (C.c_int32, []),
     "sevo_kernel_launches": (C.c_int64, []),
+    "sevo_last_cuda_error": (C.c_char_p, []),
     "sevo_state_create_batch": (C.c_int32, [C.POINTER(_vp), C.c_int32, C.POINTER(AlgParams),
                                             C.POINTER(C.c_uint64), _vp, C.POINTER(_vp)]),
     "sevo_state_best": (C.c_int32, [_vp, _dp]),
@@ -82,6 +84,7 @@ SIGNATURES = {
     "sevo_state_create": (C.c_int32, [_vp, C.POINTER(AlgParams), C.c_uint64, _vp,
                                       C.POINTER(_vp)]),
     "sevo_state_destroy": (C.c_int32, [_vp]),
+    "sevo_state_restart": (C.c_int32, [_vp, C.POINTER(C.c_uint64)]),
     "sevo_de_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_pso_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_state_result": (C.c_int32, [_vp, _dp, _i64p, _i64p, _i64p]),
@@ -90,7 +93,11 @@ SIGNATURES = {
     "sevo_state_save": (C.c_int32, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "sevo_state_load": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "sevo_run_grid": (C.c_int32, [C.POINTER(Grid), C.POINTER(GridResult), _vp]),
+    "sevo_trace_enable": (C.c_int32, [C.c_int32]),
+    "sevo_trace_read": (C.c_int32, [_i64p, _dp]),
+    "sevo_trace_name": (C.c_char_p, [C.c_int32]),
 }
+SEVO_TRACE_KINDS = 16
 
 _LIB = None
 
@@ -123,6 +130,9 @@ def lib():
 
 def check(status, what=""):
     if status != OK:
+        if status == ERR_CUDA:
+            cuda = _lib().sevo_last_cuda_error().decode()
+            what = f"{what} ({cuda})" if cuda else what
         raise SevoError(status, what)
     return status
 
@@ -255,6 +265,14 @@ class State:
             _LIB.sevo_state_destroy(h)
             self.h = None
 
+    def restart(self, seeds):
+        """Fresh initial populations for every run (seeds: one per run)."""
+        seeds = [seeds] if isinstance(seeds, int) else list(seeds)
+        if len(seeds) != self.R:
+            raise ValueError("one seed per run")
+        sd = (C.c_uint64 * self.R)(*[int(x) for x in seeds])
+        check(_lib().sevo_state_restart(self.h, sd), "sevo_state_restart")
+
     def de_step(self, counter):
         return _lib().sevo_de_step(self.h, counter)
 
@@ -328,3 +346,17 @@ def sevo_run_grid(problems, algs, tasks, gens_per_graph=0, stream=None):
     check(_lib().sevo_run_grid(C.byref(g), C.byref(r), _stream_ptr(stream)), "sevo_run_grid")
     return {"best": best, "fes": fes, "gens": gens, "success": succ.astype(bool),
             "wall_ms": r.wall_ms, "evals": r.evals}
+
+
+def trace_enable(on=True):
+    """Start (clearing the totals) or stop per-kernel event tracing."""
+    check(_lib().sevo_trace_enable(1 if on else 0), "sevo_trace_enable")
+
+
+def trace_read():
+    """{kernel kind: (launches, device ms)} of the traced launches so far."""
+    counts = (C.c_int64 * SEVO_TRACE_KINDS)()
+    ms = (C.c_double * SEVO_TRACE_KINDS)()
+    check(_lib().sevo_trace_read(counts, ms), "sevo_trace_read")
+    return {_lib().sevo_trace_name(k).decode(): (counts[k], ms[k])
+            for k in range(SEVO_TRACE_KINDS)}

@@ -298,13 +298,14 @@ cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t 
   int64_t tiles = (N + TR - 1) / TR;
   int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 8);
   RefineTable none{};
+  const int tk = sv_trace_begin(SEVO_TK_EVAL_CC, st);
   if (prec == SEVO_FP64)
     eval_cc_kernel<double, false><<<(unsigned)grid, NT, 0, st>>>(Pd, none, X, ld, row0, N, nullptr,
                                                                   nullptr, out, aux);
   else
     eval_cc_kernel<float, false><<<(unsigned)grid, NT, 0, st>>>(Pd, none, X, ld, row0, N, nullptr,
                                                                  nullptr, out, aux);
-  sv_note_launch();
+  sv_trace_end(tk, st);
   return cudaGetLastError();
 }
 
@@ -316,8 +317,9 @@ cudaError_t sv_eval_refine(const RefineTable& T, const double* X, int64_t ld, in
   int64_t tiles = (max_rows + TR - 1) / TR + T.nseg;
   int64_t grid = std::min<int64_t>(tiles, (int64_t)sv_num_sms() * 2);
   EvalAux none{};
+  const int tk = sv_trace_begin(SEVO_TK_REFINE, st);
   eval_cc_kernel<double, true><<<(unsigned)grid, NT, 0, st>>>(nullptr, T, X, ld, 0, 0, list,
                                                                counts, out, none);
-  sv_note_launch();
+  sv_trace_end(tk, st);
   return cudaGetLastError();
 }

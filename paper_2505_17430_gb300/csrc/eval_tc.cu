@@ -706,6 +706,7 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
       rows_total = std::max<int64_t>(rows_total, segs[k].row0 + segs[k].nrows);
     staged = make_x_map(&mapX, X, h0.D, g.dbox, rows_total, ld);
   }
+  const int tk = sv_trace_begin(SEVO_TK_EVAL_TC_FUSED, st);
   if (!staged) {
     const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
     if (bf16)
@@ -722,13 +723,14 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
       eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, mapX, X, ld, out, comp_g,
                                                                comp_s, lo, dev_err);
   }
-  sv_note_launch();
+  sv_trace_end(tk, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (any_comp) {
     const int cgrid = std::max(1, std::min(sv_num_sms() * 4, (int)((row_hi - row_lo + 255) / 256)));
+    const int tkc = sv_trace_begin(SEVO_TK_COMPOSE, st);
     compose_rows_kernel<<<cgrid, 256, 0, st>>>(T, comp_g, comp_s, out, lo);
-    sv_note_launch();
+    sv_trace_end(tkc, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

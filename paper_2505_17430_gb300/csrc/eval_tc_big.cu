@@ -513,6 +513,7 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   const ListOutB lo{list, count, nonfinite, list_off};
   cudaError_t e;
   for (int c = 0; c < h.ncomp; ++c) {
+    int tk = sv_trace_begin(SEVO_TK_CONVERT, st);
     if (bf16)
       convert_kernel<true><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
           p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, nullptr, Ahi, Alo,
@@ -521,24 +522,27 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
       convert_kernel<false><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
           p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, A32, nullptr, nullptr,
           comp ? comp_s : nullptr);
-    sv_note_launch();
+    sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tk = sv_trace_begin(SEVO_TK_GEMM_BIG, st);
     if (bf16)
       gemm_big_kernel<true><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
                                                            dev_err);
     else
       gemm_big_kernel<false><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
                                                             dev_err);
-    sv_note_launch();
+    sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tk = sv_trace_begin(SEVO_TK_COMBINE, st);
     combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, part,
                                                      seg.row0, N, out, comp_g, lo);
-    sv_note_launch();
+    sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (comp) {
+    const int tk = sv_trace_begin(SEVO_TK_COMPOSE, st);
     compose_big_kernel<<<cgrid, 128, 0, st>>>(p->desc_d, comp_g, comp_s, seg.row0, N, out, lo);
-    sv_note_launch();
+    sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -45,6 +45,58 @@ __device__ __forceinline__ long long fkey(double f) {
 
 __device__ __forceinline__ double dmin_pos(double a, double b) { return (b < a) ? b : a; }
 
+// IEEE x < y and x > y against a finite bound, decided on the bit patterns
+// with integer instructions (GB300's FP64 pipe is the scarce unit in the
+// generation kernels): -0.0 and +0.0 get the same key, NaN compares false.
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFll) : b;
+}
+__device__ __forceinline__ bool not_nan(double x) {
+  return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) <= 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool lt_key(double x, long long ky) {
+  return not_nan(x) && ord_key(x) < ky;
+}
+__device__ __forceinline__ bool gt_key(double x, long long ky) {
+  return not_nan(x) && ord_key(x) > ky;
+}
+
+// v * 0.5, exactly as IEEE multiplication rounds it, with integer
+// instructions: a normal result only loses one from the exponent; when the
+// result is subnormal the significand shifts right once with round to nearest
+// even; zeros, infinities and NaN are returned unchanged (all exact halves).
+__device__ __forceinline__ double half_exact(double v) {
+  const long long b = __double_as_longlong(v);
+  const long long sign = b & (long long)0x8000000000000000ull;
+  const long long mag = b & 0x7FFFFFFFFFFFFFFFll;
+  const int e = (int)(mag >> 52);
+  if (e > 1 && e < 0x7FF) return __longlong_as_double(b - (1ll << 52));
+  if (e == 0x7FF || mag == 0) return v;
+  // e == 1 or subnormal: the significand with its implicit bit, halved
+  const long long s = mag;  // for e == 1 the exponent bit is the implicit 1
+  long long h = s >> 1;
+  if ((s & 1) && (h & 1)) ++h;  // tie: round to even
+  return __longlong_as_double(sign | h);
+}
+
+// four consecutive coordinates j0..j0+3 of a row (16-byte loads when the
+// quad is whole: rows start 16-byte aligned and j0 is a multiple of 4)
+__device__ __forceinline__ void load_quad(const double* __restrict__ row, int j0, int D,
+                                          double (&v)[4]) {
+  if (j0 + 3 < D) {
+    const double2 a = *reinterpret_cast<const double2*>(row + j0);
+    const double2 b = *reinterpret_cast<const double2*>(row + j0 + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (j0 + q < D) ? row[j0 + q] : 0.0;
+  }
+}
+
 // ---------------------------------------------------------------- control
 __global__ void ctl_set_kernel(GenCtl* ctl, unsigned long long gen, int count) {
   ctl->gen = gen;
@@ -155,20 +207,33 @@ __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict
     const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
     double* ui = U + ((int64_t)r * NP + i) * ld;
     const int j0 = jq * 4;
+    double xv[4], v1[4], v2[4], v3[4];
+    load_quad(xi, j0, D, xv);
+    load_quad(d1, j0, D, v1);
+    load_quad(d2, j0, D, v2);
+    load_quad(d3, j0, D, v3);
+    const long long lbk = ord_key(lb), ubk = ord_key(ub);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + q;
       if (j >= D) break;
-      const double x = xi[j];
+      const double x = xv[q];
       double u = x;
       if ((unsigned long long)cws[q] < cr_thr || j == jr) {
         if (ALG == SEVO_DE_RAND1)
-          u = __fma_rn(F, __dsub_rn(d2[j], d3[j]), d1[j]);
+          u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), v1[q]);
         else
-          u = __fma_rn(F, __dsub_rn(d2[j], d3[j]), __fma_rn(F, __dsub_rn(d1[j], x), x));
+          u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), __fma_rn(F, __dsub_rn(v1[q], x), x));
       }
-      if (u < lb) u = __dmul_rn(__dadd_rn(lb, x), 0.5);
-      if (u > ub) u = __dmul_rn(__dadd_rn(ub, x), 0.5);
+      // repair: if u < lb then u = (lb + x) / 2; then if u > ub, u = (ub + x) / 2.
+      // With the parent inside the bounds at most one of them applies, so one
+      // FP64 add with the bound chosen by a select; the second check only
+      // fires for parents outside the bounds (populations set by the caller)
+      const bool lo = lt_key(u, lbk), hi = gt_key(u, ubk);
+      if (lo || hi) {
+        u = half_exact(__dadd_rn(lo ? lb : ub, x));
+        if (lo && gt_key(u, ubk)) u = half_exact(__dadd_rn(ub, x));
+      }
       ui[j] = u;
     }
   }
@@ -202,43 +267,118 @@ __global__ void __launch_bounds__(RANK_ROWS)
   if (rank < k) order[(int64_t)r * NP + rank] = i;
 }
 
-// Larger populations: one CTA per run sorts (key, index) pairs with a
-// bitonic network in shared memory (padded to a power of two with +inf
-// keys), lexicographic order = (fitness, index); the first k indices are the
-// p-best pool, identical to the counting rank.
-constexpr int SORT_THREADS = 512;
-__global__ void __launch_bounds__(SORT_THREADS)
-    de_rank_sort_kernel(const double* __restrict__ fx, int32_t* __restrict__ order, int NP,
-                        int npow2, int k) {
-  extern __shared__ long long sk[];
-  int* si = (int*)(sk + npow2);
-  const int r = blockIdx.x;
+// Larger populations: one CTA per run finds the k-th smallest key by an
+// MSB-first radix select (8-bit digits, shared-memory histograms), gathers
+// the rows whose key is at most that threshold (the k best plus any rows
+// tied with the k-th) and sorts only those by (key, index) with a bitonic
+// network; the first k indices are the p-best pool, identical to the
+// counting rank.
+constexpr int RSEL_THREADS = 512;
+
+__host__ __device__ inline int pow2_at_least(int n) {
+  int m = 1;
+  while (m < n) m <<= 1;
+  return m;
+}
+__host__ __device__ inline size_t rsel_smem_bytes(int NP) {
+  return (size_t)NP * 8 + (size_t)pow2_at_least(NP) * 12 + 16;
+}
+
+__global__ void __launch_bounds__(RSEL_THREADS)
+    de_rank_select_kernel(const double* __restrict__ fx, int32_t* __restrict__ order, int NP,
+                          int npow2, int k) {
+  extern __shared__ __align__(16) unsigned char rs_sm[];
+  unsigned long long* uk = reinterpret_cast<unsigned long long*>(rs_sm);  // NP keys
+  unsigned long long* ck = uk + NP;                                       // candidates
+  int* ci = reinterpret_cast<int*>(ck + npow2);
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_rem, s_ncand;
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   const double* f = fx + (int64_t)r * NP;
-  for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-    sk[i] = (i < NP) ? fkey(f[i]) : 0x7FFFFFFFFFFFFFFFll;
-    si[i] = (i < NP) ? i : 0x7FFFFFFF;
+  for (int i = tid; i < NP; i += blockDim.x)
+    uk[i] = (unsigned long long)fkey(f[i]) ^ 0x8000000000000000ull;  // unsigned order
+  if (tid == 0) s_ncand = 0;
+  unsigned long long prefix = 0ull, pmask = 0ull;
+  int rem = k;  // rank (1-based) of the wanted key among the keys matching prefix
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    for (int i = tid; i < NP; i += blockDim.x) {
+      const unsigned long long v = uk[i];
+      if ((v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7
+      unsigned c[8], sum = 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = hist[lane * 8 + q];
+        sum += c[q];
+      }
+      unsigned incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned excl = incl - sum;
+      if (excl < (unsigned)rem && (unsigned)rem <= incl) {
+        unsigned acc = excl;
+        int b = lane * 8 + 7;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (acc + c[q] >= (unsigned)rem) {
+            b = lane * 8 + q;
+            break;
+          }
+          acc += c[q];
+        }
+        s_prefix = prefix | ((unsigned long long)b << shift);
+        s_rem = rem - (int)acc;
+      }
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    rem = s_rem;
+    pmask |= 255ull << shift;
+  }
+  // prefix is now the k-th smallest key: gather every key <= it
+  for (int i = tid; i < NP; i += blockDim.x) {
+    const unsigned long long v = uk[i];
+    if (v <= prefix) {
+      const int slot = atomicAdd(&s_ncand, 1);
+      ck[slot] = v;
+      ci[slot] = i;
+    }
   }
   __syncthreads();
-  for (int size = 2; size <= npow2; size <<= 1) {
+  const int n = s_ncand;  // >= k
+  const int m = pow2_at_least(n);
+  for (int i = n + tid; i < m; i += blockDim.x) {
+    ck[i] = ~0ull;
+    ci[i] = 0x7FFFFFFF;
+  }
+  __syncthreads();
+  for (int size = 2; size <= m; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < npow2 / 2; t += blockDim.x) {
+      for (int t = tid; t < m / 2; t += blockDim.x) {
         const int lo = 2 * t - (t & (stride - 1));
         const int hi = lo + stride;
         const bool up = ((lo & size) == 0);
-        const long long ka = sk[lo], kb = sk[hi];
-        const int ia = si[lo], ib = si[hi];
+        const unsigned long long ka = ck[lo], kb = ck[hi];
+        const int ia = ci[lo], ib = ci[hi];
         const bool a_gt_b = (ka > kb) || (ka == kb && ia > ib);
         if (a_gt_b == up) {
-          sk[lo] = kb;
-          sk[hi] = ka;
-          si[lo] = ib;
-          si[hi] = ia;
+          ck[lo] = kb;
+          ck[hi] = ka;
+          ci[lo] = ib;
+          ci[hi] = ia;
         }
       }
       __syncthreads();
     }
   }
-  for (int q = threadIdx.x; q < k; q += blockDim.x) order[(int64_t)r * NP + q] = si[q];
+  for (int q = tid; q < k; q += blockDim.x) order[(int64_t)r * NP + q] = ci[q];
 }
 
 // ---------------------------------------------------------------- DE select
@@ -261,12 +401,24 @@ __device__ __forceinline__ void block_min_update(double v, double* best_r) {
   __syncthreads();
 }
 
+// One CTA per run stages the run's current and trial fitness in shared
+// memory with coalesced loads; acceptance flags, the row-order scan and the
+// slot resolution then run on shared memory.
+__host__ __device__ constexpr size_t sel_smem_bytes(int NP) {
+  return (size_t)NP * (8 + 8 + 4 + 4 + 1) + 16;
+}
+
 __global__ void __launch_bounds__(SEL_THREADS)
     de_select_kernel(double* __restrict__ fx, const double* __restrict__ fu,
                      int32_t* __restrict__ asize, int32_t* __restrict__ action,
                      double* __restrict__ best, const uint64_t* __restrict__ seeds,
                      const GenCtl* __restrict__ ctl, int NP, int use_archive) {
-  extern __shared__ int owner[];
+  extern __shared__ __align__(16) unsigned char sel_sm[];
+  double* sf = reinterpret_cast<double*>(sel_sm);  // current fitness
+  double* sg = sf + NP;                             // trial fitness
+  int* owner = reinterpret_cast<int*>(sg + NP);     // archive slot -> last row
+  int* sact = owner + NP;                           // action per row
+  unsigned char* sacc = reinterpret_cast<unsigned char*>(sact + NP);  // accepted
   __shared__ int wsum[SEL_THREADS / 32];
   const int r = blockIdx.x, tid = threadIdx.x;
   const int count = ctl->count;
@@ -274,16 +426,23 @@ __global__ void __launch_bounds__(SEL_THREADS)
   double* f = fx + (int64_t)r * NP;
   const double* g = fu + (int64_t)r * NP;
   int32_t* act = action + (int64_t)r * NP;
+  for (int i = tid; i < NP; i += blockDim.x) {
+    sf[i] = f[i];
+    sg[i] = g[i];
+    owner[i] = -1;
+  }
+  __syncthreads();
   // best-so-far over the rows that count toward the budget
   double m = INFINITY;
-  for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, g[i]);
+  for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, sg[i]);
   block_min_update(m, best + r);
+  for (int i = tid; i < NP; i += blockDim.x) sacc[i] = (sg[i] <= sf[i]) ? 1 : 0;
+  __syncthreads();
   // contiguous chunk of rows per thread, so the scan follows row order
   const int per = (NP + blockDim.x - 1) / blockDim.x;
   const int i0 = min(NP, tid * per), i1 = min(NP, i0 + per);
   int cnt = 0;
-  for (int i = i0; i < i1; ++i) cnt += (g[i] <= f[i]);
-  // block exclusive scan of cnt
+  for (int i = i0; i < i1; ++i) cnt += sacc[i];
   const int warp = tid >> 5, lane = tid & 31;
   int incl = cnt;
   for (int o = 1; o < 32; o <<= 1) {
@@ -291,7 +450,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
     if (lane >= o) incl += v;
   }
   if (lane == 31) wsum[warp] = incl;
-  for (int i = tid; i < NP; i += blockDim.x) owner[i] = -1;
   __syncthreads();
   int woff = 0;
   for (int w = 0; w < warp; ++w) woff += wsum[w];
@@ -300,9 +458,8 @@ __global__ void __launch_bounds__(SEL_THREADS)
   int k = woff + incl - cnt;
   const int as0 = use_archive ? asize[r] : 0;  // rand/1 has no archive (asize null)
   for (int i = i0; i < i1; ++i) {
-    const bool acc = g[i] <= f[i];
     int a = -2;
-    if (acc) {
+    if (sacc[i]) {
       a = -1;
       if (use_archive) {
         int slot;
@@ -317,13 +474,14 @@ __global__ void __launch_bounds__(SEL_THREADS)
       }
       ++k;
     }
-    act[i] = a;
+    sact[i] = a;
   }
   __syncthreads();
-  for (int i = i0; i < i1; ++i) {
-    int a = act[i];
-    if (a >= 0 && owner[a] != i) act[i] = -1;  // a later row overwrote this slot
-    if (a != -2) f[i] = g[i];
+  for (int i = tid; i < NP; i += blockDim.x) {
+    int a = sact[i];
+    if (a >= 0 && owner[a] != i) a = -1;  // a later row overwrote this slot
+    act[i] = a;
+    if (a != -2) f[i] = sg[i];
   }
   if (tid == 0 && use_archive) asize[r] = min(NP, as0 + nacc_total);
 }
@@ -377,11 +535,11 @@ __global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
     const double gj = P[((int64_t)r * NP + gi) * ld + j];
     double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
     double xn = __dadd_rn(x, v);
-    if (xn < lb) {
+    if (lt_key(xn, ord_key(lb))) {
       xn = lb;
       v = 0.0;
     }
-    if (xn > ub) {
+    if (gt_key(xn, ord_key(ub))) {
       xn = ub;
       v = 0.0;
     }
@@ -409,17 +567,24 @@ __global__ void __launch_bounds__(SEL_THREADS)
     for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, f[i]);
     block_min_update(m, best + r);
   }
+  extern __shared__ double sp[];  // the run's personal-best fitness
   for (int i = tid; i < NP; i += blockDim.x) {
-    const bool up = f[i] < p[i];
+    const double fi = f[i];
+    double pi = p[i];
+    const bool up = fi < pi;
     fl[i] = up;
-    if (up) p[i] = f[i];
+    if (up) {
+      p[i] = fi;
+      pi = fi;
+    }
+    sp[i] = pi;
   }
   __syncthreads();
   if (topology == 0) {
     long long kb = 0x7FFFFFFFFFFFFFFFll;
     int ib = 0x7FFFFFFF;
     for (int i = tid; i < NP; i += blockDim.x) {
-      const long long k = fkey(p[i]);
+      const long long k = fkey(sp[i]);
       if (k < kb || (k == kb && i < ib)) {
         kb = k;
         ib = i;
@@ -461,7 +626,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
           }
       int b = nb[0];
       for (int t = 1; t < 3; ++t)
-        if (p[nb[t]] < p[b]) b = nb[t];
+        if (sp[nb[t]] < sp[b]) b = nb[t];
       gd[i] = b;
     }
   }
@@ -556,6 +721,12 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   if (ctpb) bytes += mat /*A*/ + al256((size_t)b->R * 4) /*asize*/ + ivec /*order*/;
   if (!de) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
   b->block_bytes = bytes;
+  if (ctpb && rsel_smem_bytes(b->NP) > 48 * 1024)
+    SV_CUDA(cudaFuncSetAttribute(de_rank_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rsel_smem_bytes(SV_MAX_NP)));
+  if (de && sel_smem_bytes(b->NP) > 48 * 1024)
+    SV_CUDA(cudaFuncSetAttribute(de_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sel_smem_bytes(SV_MAX_NP)));
   SV_CUDA(cudaMalloc(&b->block, bytes));
   SV_CUDA(cudaMemsetAsync(b->block, 0, bytes, st));
   char* c = (char*)b->block;
@@ -621,14 +792,16 @@ static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
 }
 
 cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count) {
+  const int tk1 = sv_trace_begin(SEVO_TK_CONTROL, b->stream);
   ctl_set_kernel<<<1, 1, 0, b->stream>>>(b->ctl, gen, count);
-  sv_note_launch();
+  sv_trace_end(tk1, b->stream);
   return cudaGetLastError();
 }
 
 cudaError_t sv_ctl_advance(Batch* b) {
+  const int tk2 = sv_trace_begin(SEVO_TK_CONTROL, b->stream);
   ctl_advance_kernel<<<1, 1, 0, b->stream>>>(b->ctl, b->NP, (long long)b->budget);
-  sv_note_launch();
+  sv_trace_end(tk2, b->stream);
   return cudaGetLastError();
 }
 
@@ -636,13 +809,15 @@ cudaError_t sv_batch_init(Batch* b) {
   cudaStream_t st = b->stream;
   const int64_t rows = (int64_t)b->R * b->NP;
   const int T = 256;
+  const int tk3 = sv_trace_begin(SEVO_TK_INIT, st);
   init_pop_kernel<<<grid_for(rows * ((b->D + 1) / 2), T), T, 0, st>>>(b->X, b->seeds, b->R, b->NP,
                                                                      b->D, b->ld, b->lb, b->ub);
-                                                                     sv_note_launch();
+  sv_trace_end(tk3, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int tk4 = sv_trace_begin(SEVO_TK_CONTROL, st);
   fill_kernel<<<grid_for(b->R, T), T, 0, st>>>(b->best, b->R, INFINITY);
-  sv_note_launch();
+  sv_trace_end(tk4, st);
   const int count0 = (int)std::min<int64_t>(b->budget, b->NP);
   if ((e = sv_ctl_set(b, 0ull, count0)) != cudaSuccess) return e;
   if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
@@ -650,17 +825,20 @@ cudaError_t sv_batch_init(Batch* b) {
     // best-so-far of the initial population (the select kernel's min part
     // with no trials: fu == fx, every row "accepted" onto itself is avoided
     // by using the PSO-style per-run reducer on fx)
-    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fx, b->action, b->guide, b->best,
+    const int tk5 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fx, b->action, b->guide, b->best,
                                                     b->ctl, b->NP, 0, 1, 1);
-                                                    sv_note_launch();
+    sv_trace_end(tk5, st);
   } else {
     const size_t m = (size_t)rows * b->ld * 8;
     if ((e = cudaMemcpyAsync(b->P, b->X, m, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    const int tk6 = sv_trace_begin(SEVO_TK_CONTROL, st);
     fill_kernel<<<grid_for(rows, T), T, 0, st>>>(b->fp, rows, INFINITY);
-    sv_note_launch();
-    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
+    sv_trace_end(tk6, st);
+    const int tk7 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
                                                     b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
-                                                    sv_note_launch();
+    sv_trace_end(tk7, st);
   }
   return cudaGetLastError();
 }
@@ -673,58 +851,67 @@ cudaError_t sv_batch_generation(Batch* b) {
   cudaError_t e;
   if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
     if (b->alg == SEVO_DE_CTPB) {
+      const int tk_rank = sv_trace_begin(SEVO_TK_DE_RANK, st);
+      // counting rank (O(NP^2) per run, parallel over row blocks) for small
+      // populations; radix select + sort of the candidates above that
       if (b->NP <= 512) {
         de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
                          (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
       } else {
-        int np2 = 1;
-        while (np2 < b->NP) np2 <<= 1;
-        de_rank_sort_kernel<<<b->R, SORT_THREADS, (size_t)np2 * 12, st>>>(b->fx, b->order, b->NP,
-                                                                          np2, b->pbest_k);
+        de_rank_select_kernel<<<b->R, RSEL_THREADS, rsel_smem_bytes(b->NP), st>>>(
+            b->fx, b->order, b->NP, pow2_at_least(b->NP), b->pbest_k);
       }
-      sv_note_launch();
+      sv_trace_end(tk_rank, st);
+      const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
       de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
           b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k);
-          sv_note_launch();
+      sv_trace_end(tk8, st);
     } else {
+      const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
       de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
           b->ld, b->F, b->cr_thr, b->lb, b->ub, 0);
-          sv_note_launch();
+      sv_trace_end(tk9, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
-    de_select_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 4, st>>>(
+    const int tk10 = sv_trace_begin(SEVO_TK_DE_SELECT, st);
+    de_select_kernel<<<b->R, SEL_THREADS, sel_smem_bytes(b->NP), st>>>(
         b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
         b->alg == SEVO_DE_CTPB);
-        sv_note_launch();
+    sv_trace_end(tk10, st);
+    const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
     de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
                                                          b->D, b->ld);
-                                                         sv_note_launch();
+    sv_trace_end(tk11, st);
   } else {
+    const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
     pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
                                                            b->ctl, b->R, b->NP, b->D, b->ld, b->w,
                                                            b->c1, b->c2, b->lb, b->ub);
-                                                           sv_note_launch();
+    sv_trace_end(tk12, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
-    pso_update_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
+    const int tk13 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
                                                     b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
-                                                    sv_note_launch();
+    sv_trace_end(tk13, st);
+    const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
     pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
                                                          b->D, b->ld);
-                                                         sv_note_launch();
+    sv_trace_end(tk14, st);
   }
   return cudaGetLastError();
 }
 
 // guides only (after the host overwrote pbest fitness)
 cudaError_t sv_batch_guides(Batch* b) {
-  pso_update_kernel<<<b->R, SEL_THREADS, 0, b->stream>>>(b->fp, b->fp, b->action, b->guide,
+  const int tk15 = sv_trace_begin(SEVO_TK_PSO_UPDATE, b->stream);
+  pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, b->stream>>>(b->fp, b->fp, b->action, b->guide,
                                                          b->best, b->ctl, b->NP,
                                                          b->alg == SEVO_PSO_RING, 0, 0);
-                                                         sv_note_launch();
+  sv_trace_end(tk15, b->stream);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,9 @@
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void sv_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+extern "C" const char* sevo_last_cuda_error(void) {
+  return g_last_cuda == cudaSuccess ? "" : cudaGetErrorString(g_last_cuda);
+}
 
 extern "C" const char* sevo_strerror(int32_t s) {
   switch (s) {

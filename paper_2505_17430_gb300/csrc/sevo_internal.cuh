@@ -170,6 +170,11 @@ __host__ __device__ __forceinline__ void sv_split_hi_lo(double x, float& hi, flo
 void sv_set_last_cuda_error(cudaError_t e);
 // kernel launch accounting (see sevo_kernel_launches)
 void sv_note_launch(int64_t n = 1);
+// kernel tracing: a token from sv_trace_begin (before the launch; -1 when
+// tracing is off or the stream is capturing) is closed by sv_trace_end
+// (after the launch), which also counts the launch
+int sv_trace_begin(int kind, cudaStream_t st);
+void sv_trace_end(int token, cudaStream_t st);
 // upload the instance to the current device on first use (thread-safe);
 // SEVO_ERR_STATE if it already lives on another device
 int32_t sv_problem_ready(const sevo_problem* p);

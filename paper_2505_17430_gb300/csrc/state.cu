@@ -73,6 +73,25 @@ extern "C" int32_t sevo_state_create(const sevo_problem* p, const sevo_alg_param
   return create_impl(&p, 1, a, &seed, stream, out);
 }
 
+extern "C" int32_t sevo_state_restart(sevo_state* s, const uint64_t* seeds) {
+  if (!s || !seeds) return SEVO_ERR_ARG;
+  Batch& b = s->b;
+  const int64_t rows = (int64_t)b.R * b.NP;
+  cudaError_t e = cudaMemcpyAsync(b.seeds, seeds, (size_t)b.R * 8, cudaMemcpyHostToDevice, b.stream);
+  if (e == cudaSuccess && b.asize) e = cudaMemsetAsync(b.asize, 0, (size_t)b.R * 4, b.stream);
+  if (e == cudaSuccess && b.V)
+    e = cudaMemsetAsync(b.V, 0, (size_t)rows * b.ld * 8, b.stream);
+  if (e == cudaSuccess) e = sv_batch_init(&b);
+  if (e != cudaSuccess) {
+    sv_set_last_cuda_error(e);
+    return SEVO_ERR_CUDA;
+  }
+  s->seed = seeds[0];
+  s->fes = std::min<int64_t>(s->params.budget, s->params.NP);
+  s->gens = 0;
+  return SEVO_OK;
+}
+
 extern "C" int32_t sevo_state_create_batch(const sevo_problem* const* problems, int32_t R,
                                            const sevo_alg_params* a, const uint64_t* seeds,
                                            void* stream, sevo_state** out) {

@@ -236,10 +236,12 @@ def test_mixed_precision_runs_reach_oracle_quality(S, prec):
     assert res["success"].sum() >= sum(ref) - 2
 
 
-def test_de_ctpb_large_population_sorted_pbest(S):
-    """NP > 512 uses the bitonic (fitness, index) sort for the p-best pool;
-    trial vectors must still match the oracle bit for bit."""
-    fam, D, NP = S.RASTRIGIN, 10, 600
+@pytest.mark.parametrize("NP", [600, 1800, 4096])
+def test_de_ctpb_large_population_sorted_pbest(S, NP):
+    """NP > 512 ranks by radix select of the k-th key plus a sort of the
+    candidates (ties by index); trial vectors must still match the oracle
+    bit for bit."""
+    fam, D = S.RASTRIGIN, 10
     p, q, st = _state(S, fam, D, S.DE_CTPB, NP, 10 ** 7, 21)
     X = O.init_population(21, NP, D)
     fx = q.eval(X)
@@ -279,3 +281,48 @@ def test_batched_mixed_segments_many_jobs_per_cta(S, prec):
         assert st.step(g) == 0
     st.best()
     assert st.result()["gens"] == 3
+
+
+def test_kernel_trace_counts_and_times(S):
+    """Tracing brackets every launch outside graph capture with events on its
+    stream: one DE/ctpb step traces rank, trial, evaluation, select and apply
+    launches with positive device time; a run grid (graph-captured
+    generations) adds no captured launch to the totals."""
+    D, NP = 30, 64
+    p = S.Problem(77, S.RASTRIGIN, D)
+    st = S.State(p, S.alg_params(S.DE_CTPB, NP, 10 ** 6, prec=S.TF32), 5)
+    S.trace_enable(True)
+    assert st.de_step(1) == 0
+    t = S.trace_read()
+    for k in ("de_rank", "de_trial", "eval_tc_fused", "de_select", "de_apply"):
+        assert t[k][0] == 1 and t[k][1] > 0.0, (k, t[k])
+    S.trace_enable(True)
+    S.sevo_run_grid([p], [S.alg_params(S.PSO_RING, 20, 20 * 40)], [(0, 0, 3)], gens_per_graph=8)
+    t = S.trace_read()
+    S.trace_enable(False)
+    assert t["pso_move"][0] < 39  # most generations ran inside graphs
+    assert t["init"][0] == 1
+
+
+@pytest.mark.parametrize("alg", [1, 3])
+def test_restart_equals_fresh_state(S, alg):
+    """sevo_state_restart(seeds) leaves a (batched) state bit-identical to a
+    state freshly created with those seeds, and both step identically."""
+    D, NP = 13, 40
+    probs = [S.Problem(300 + k, fam, D) for k, fam in enumerate((2, 6, 7))]
+    a = S.alg_params(alg, NP, 10 ** 6)
+    st = S.State(probs, a, [1, 2, 3])
+    for g in range(1, 6):
+        assert st.step(g) == 0
+    st.restart([11, 12, 13])
+    fresh = S.State(probs, a, [11, 12, 13])
+    for g in range(0, 3):
+        if g:
+            assert st.step(g) == 0 and fresh.step(g) == 0
+        ga, gb = st.get(), fresh.get()
+        # partner indices are written by each generation's trial kernel
+        for k in ("X", "fx", "A", "V", "P", "fp") + (("part",) if g else ()):
+            assert np.array_equal(ga[k], gb[k]), (g, k)
+        assert ga["asize"] == gb["asize"]
+        assert st.result() == fresh.result()
+        assert np.array_equal(st.best(), fresh.best())

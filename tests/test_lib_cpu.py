@@ -90,3 +90,36 @@ def test_large_rotation_orthogonal():
     p = S.Problem(1, S.ELLIPSOID, 500)
     M = p.export()["M"]
     assert np.abs(M.T @ M - np.eye(500)).max() < 1e-13
+
+
+def test_trace_kinds_match_header_and_read_without_gpu():
+    """The tracing kinds enumerated in the header match the binding's count,
+    every kind has a distinct name, and enabling / reading with nothing
+    traced touches no device."""
+    txt = open(os.path.join(ROOT, "include", "sevo.h")).read()
+    body = txt[txt.index("enum sevo_trace_kind"):txt.index("SEVO_TRACE_KINDS")]
+    kinds = re.findall(r"\b(SEVO_TK_[A-Z_]+)", body)
+    assert len(kinds) == S.SEVO_TRACE_KINDS
+    lib = S.lib()
+    names = [lib.sevo_trace_name(k).decode() for k in range(S.SEVO_TRACE_KINDS)]
+    assert all(names) and len(set(names)) == len(names)
+    assert lib.sevo_trace_name(S.SEVO_TRACE_KINDS) == b""
+    assert lib.sevo_trace_name(-1) == b""
+    S.trace_enable(True)
+    t = S.trace_read()
+    S.trace_enable(False)
+    assert set(t) == set(names) and all(v == (0, 0.0) for v in t.values())
+
+
+def test_last_cuda_error_empty_before_any_failure():
+    assert S.lib().sevo_last_cuda_error() == b""
+
+
+def test_status_constants_match_header():
+    txt = open(os.path.join(ROOT, "include", "sevo.h")).read()
+    for name in ("ARG", "CUDA", "OOM", "TIMEOUT", "NAN", "UNSUPPORTED", "STATE"):
+        m = re.search(r"#define SEVO_ERR_%s\s+(-?\d+)" % name, txt)
+        assert m and int(m.group(1)) == getattr(S, "ERR_" + name), name
+    with pytest.raises(S.SevoError) as ei:
+        S.check(S.ERR_ARG, "probe")
+    assert ei.value.status == S.ERR_ARG
