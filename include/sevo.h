@@ -296,6 +296,21 @@ typedef struct {          /* caller-allocated host arrays, ntasks entries each *
  * single-run state API's for the same (problem, alg, seed).  Synchronous. */
 int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, void* stream);
 
+/* ---- execution policy (library infrastructure; the paper has no counterpart)
+ * Process-wide switches, read when a state or a grid bucket is created. */
+enum sevo_policy {
+  /* 1: runs with D <= 32 and NP <= 512 advance in one CTA per run, whole
+   * generations per launch, evaluated by CUDA cores (FP64, or FP32 with the
+   * operand rounding of the requested mode and FP64 refinement); 0 (default):
+   * such runs use the batched kernels like every other run (faster on this
+   * part for run grids: one SM's FP64 rate bounds a run-per-CTA generation) */
+  SEVO_POLICY_SMALL_RUNS = 0
+};
+/* SEVO_ERR_ARG for an unknown key or value */
+int32_t sevo_set_policy(int32_t key, int64_t value);
+/* current value, or -1 for an unknown key */
+int64_t sevo_get_policy(int32_t key);
+
 /* ---- kernel tracing (library infrastructure; the paper has no counterpart)
  * While tracing is on, every kernel this library launches on a stream that is
  * not being captured into a graph is bracketed by two CUDA events recorded on
@@ -319,6 +334,7 @@ enum sevo_trace_kind {
   SEVO_TK_PSO_UPDATE,        /* PSO personal/neighbourhood best               */
   SEVO_TK_PSO_COPY,          /* PSO personal-best row copies                  */
   SEVO_TK_CONTROL,           /* generation counters, fills                     */
+  SEVO_TK_SMALL_RUN,         /* run-per-CTA generations of small runs          */
   SEVO_TRACE_KINDS
 };
 /* on != 0: clear the accumulators and start tracing; on == 0: stop (the

@@ -93,11 +93,14 @@ SIGNATURES = {
     "sevo_state_save": (C.c_int32, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "sevo_state_load": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "sevo_run_grid": (C.c_int32, [C.POINTER(Grid), C.POINTER(GridResult), _vp]),
+    "sevo_set_policy": (C.c_int32, [C.c_int32, C.c_int64]),
+    "sevo_get_policy": (C.c_int64, [C.c_int32]),
     "sevo_trace_enable": (C.c_int32, [C.c_int32]),
     "sevo_trace_read": (C.c_int32, [_i64p, _dp]),
     "sevo_trace_name": (C.c_char_p, [C.c_int32]),
 }
-SEVO_TRACE_KINDS = 16
+SEVO_TRACE_KINDS = 17
+POLICY_SMALL_RUNS = 0
 
 _LIB = None
 

@@ -29,6 +29,7 @@ void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t r
   s->tc_bytes = tc_bytes(D, any_comp, prec, rows);
   s->tc = s->tc_bytes ? (void*)c : nullptr;
   s->err = nullptr;
+  s->refined = nullptr;
 }
 
 // one pass: mixed evaluation of every segment, then one FP64 re-evaluation
@@ -77,6 +78,7 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
     }
     RefineTable RT;
     RT.nseg = n;
+    RT.total = s.refined;
     for (int k = 0; k < n; ++k) {
       RT.P[k] = sg[k].p->desc_d;
       RT.list_off[k] = off[k];

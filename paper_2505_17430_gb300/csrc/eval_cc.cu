@@ -132,8 +132,13 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
   if (LIST) {
     if (tid == 0) {
       cumS[0] = 0;
-      for (int q = 0; q < RT.nseg; ++q) cumS[q + 1] = cumS[q] + (counts[q] + TR - 1) / TR;
+      unsigned long long listed = 0;
+      for (int q = 0; q < RT.nseg; ++q) {
+        cumS[q + 1] = cumS[q] + (counts[q] + TR - 1) / TR;
+        listed += (unsigned long long)counts[q];
+      }
       curSeg = -1;
+      if (blockIdx.x == 0 && RT.total && listed) atomicAdd(RT.total, listed);
     }
     __syncthreads();
     total_tiles = cumS[RT.nseg];

@@ -18,11 +18,14 @@
 // beyond the stated fma), so trial vectors equal the oracle's bit for bit.
 // Streaming kernels move 4 consecutive coordinates per thread (one Philox
 // call covers the four crossover words).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "bodies.cuh"
 #include "evo.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -111,16 +114,57 @@ __global__ void ctl_advance_kernel(GenCtl* ctl, int NP, long long budget) {
   ctl->count = (int)(c < 0 ? 0 : (c > NP ? NP : c));
 }
 
+// ---------------------------------------------------------------- indexing
+// n / d for 0 <= n < 2^31 by multiply-high (Granlund and Montgomery's
+// round-up method): q = (umulhi(n, m) + n) >> l with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, instead of a 64-bit division per thread.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return FastDiv{d, (uint32_t)m, l};
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return (__umulhi(n, f.m) + n) >> f.l;
+}
+// t = (hi * nmid + mid) * nlo + lo; row = hi * nmid + mid
+struct Split3 {
+  int lo, mid, hi;
+  int64_t row;
+};
+__device__ __forceinline__ Split3 split3(int64_t t, bool fast, const FastDiv& flo,
+                                         const FastDiv& fmid) {
+  Split3 s;
+  if (fast) {
+    const uint32_t u = (uint32_t)t, q = fdiv(u, flo), q2 = fdiv(q, fmid);
+    s.lo = (int)(u - q * flo.d);
+    s.mid = (int)(q - q2 * fmid.d);
+    s.hi = (int)q2;
+    s.row = (int64_t)q;
+  } else {
+    const int64_t q = t / flo.d, q2 = q / fmid.d;
+    s.lo = (int)(t - q * flo.d);
+    s.mid = (int)(q - q2 * fmid.d);
+    s.hi = (int)q2;
+    s.row = q;
+  }
+  return s;
+}
+
 // ---------------------------------------------------------------- init
 __global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restrict__ seeds, int R,
-                                int NP, int D, int ld, double lb, double ub) {
+                                int NP, int D, int ld, double lb, double ub, FastDiv fpair,
+                                FastDiv fnp) {
   const int64_t total = (int64_t)R * NP * ((D + 1) / 2);
+  const bool fast = total < (1ll << 31);
   const double span = __dsub_rn(ub, lb);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int jp = (int)(t % ((D + 1) / 2));
-    const int64_t ri = t / ((D + 1) / 2);
-    const int i = (int)(ri % NP), r = (int)(ri / NP);
+    const Split3 sp = split3(t, fast, fpair, fnp);
+    const int jp = sp.lo, i = sp.mid, r = sp.hi;
     const uint4 w = sv_draw(seeds[r], (uint32_t)jp, (uint32_t)i, 0u, SV_P_INIT);
     double* xr = X + ((int64_t)r * NP + i) * ld;
     const int j = 2 * jp;
@@ -130,112 +174,126 @@ __global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restri
 }
 
 // ---------------------------------------------------------------- DE trials
+// one quad (coordinates 4 jq .. 4 jq + 3) of run r's trial row i
+template <int ALG>
+__device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, double* __restrict__ U,
+                                              const double* __restrict__ A,
+                                              const int32_t* __restrict__ asize,
+                                              const int32_t* __restrict__ order,
+                                              int32_t* __restrict__ part,
+                                              const uint64_t* __restrict__ seeds, int NP, int D,
+                                              int ld, double F, unsigned long long cr_thr,
+                                              double lb, double ub, int pk,
+                                              unsigned long long gen, int r, int i, int jq) {
+  const uint64_t seed = seeds[r];
+  const uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_PART);
+  const double* Xr = X + (int64_t)r * NP * ld;
+  const double* xi = Xr + (int64_t)i * ld;
+  const double *d1, *d2, *d3;
+  int p0, p1, p2, jr;
+  if (ALG == SEVO_DE_RAND1) {
+    int a = (int)sv_below(w.x, (uint32_t)(NP - 1));
+    if (a >= i) ++a;
+    const int lo = min(i, a), hi = max(i, a);
+    int b = (int)sv_below(w.y, (uint32_t)(NP - 2));
+    if (b >= lo) ++b;
+    if (b >= hi) ++b;
+    int e0 = lo, e1 = hi, e2 = b;  // sort {i, a, b}
+    if (e2 < e1) {
+      int tt = e1;
+      e1 = e2;
+      e2 = tt;
+    }
+    if (e1 < e0) {
+      int tt = e0;
+      e0 = e1;
+      e1 = tt;
+    }
+    int c = (int)sv_below(w.z, (uint32_t)(NP - 3));
+    if (c >= e0) ++c;
+    if (c >= e1) ++c;
+    if (c >= e2) ++c;
+    p0 = a;
+    p1 = b;
+    p2 = c;
+    d1 = Xr + (int64_t)a * ld;
+    d2 = Xr + (int64_t)b * ld;
+    d3 = Xr + (int64_t)c * ld;
+  } else {
+    const int as = asize[r];
+    const int pb = order[(int64_t)r * NP + (int)sv_below(w.x, (uint32_t)pk)];
+    int r1 = (int)sv_below(w.y, (uint32_t)(NP - 1));
+    if (r1 >= i) ++r1;
+    const int lo = min(i, r1), hi = max(i, r1);
+    int r2 = (int)sv_below(w.z, (uint32_t)(NP + as - 2));
+    if (r2 >= lo) ++r2;
+    if (r2 >= hi) ++r2;
+    p0 = pb;
+    p1 = r1;
+    p2 = r2;
+    d1 = Xr + (int64_t)pb * ld;
+    d2 = Xr + (int64_t)r1 * ld;
+    d3 = (r2 < NP) ? Xr + (int64_t)r2 * ld : A + ((int64_t)r * NP + (r2 - NP)) * ld;
+  }
+  jr = (int)sv_below(w.w, (uint32_t)D);
+  if (jq == 0 && part) {
+    int32_t* pp = part + ((int64_t)r * NP + i) * 4;
+    pp[0] = p0;
+    pp[1] = p1;
+    pp[2] = p2;
+    pp[3] = jr;
+  }
+  const uint4 cw = sv_draw(seed, (uint32_t)jq, (uint32_t)i, (uint32_t)gen, SV_P_CROSS);
+  const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
+  double* ui = U + ((int64_t)r * NP + i) * ld;
+  const int j0 = jq * 4;
+  double xv[4], v1[4], v2[4], v3[4];
+  load_quad(xi, j0, D, xv);
+  load_quad(d1, j0, D, v1);
+  load_quad(d2, j0, D, v2);
+  load_quad(d3, j0, D, v3);
+  const long long lbk = ord_key(lb), ubk = ord_key(ub);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = j0 + q;
+    if (j >= D) break;
+    const double x = xv[q];
+    double u = x;
+    if ((unsigned long long)cws[q] < cr_thr || j == jr) {
+      if (ALG == SEVO_DE_RAND1)
+        u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), v1[q]);
+      else
+        u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), __fma_rn(F, __dsub_rn(v1[q], x), x));
+    }
+    // repair: if u < lb then u = (lb + x) / 2; then if u > ub, u = (ub + x) / 2.
+    // With the parent inside the bounds at most one of them applies, so one
+    // FP64 add with the bound chosen by a select; the second check only
+    // fires for parents outside the bounds (populations set by the caller)
+    const bool lo = lt_key(u, lbk), hi = gt_key(u, ubk);
+    if (lo || hi) {
+      u = half_exact(__dadd_rn(lo ? lb : ub, x));
+      if (lo && gt_key(u, ubk)) u = half_exact(__dadd_rn(ub, x));
+    }
+    ui[j] = u;
+  }
+}
+
 template <int ALG>
 __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict__ U,
                                 const double* __restrict__ A, const int32_t* __restrict__ asize,
                                 const int32_t* __restrict__ order, int32_t* __restrict__ part,
                                 const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
                                 int R, int NP, int D, int ld, double F, unsigned long long cr_thr,
-                                double lb, double ub, int pk) {
+                                double lb, double ub, int pk, FastDiv fq, FastDiv fnp) {
   const int nq = (D + 3) >> 2;
   const int64_t total = (int64_t)R * NP * nq;
+  const bool fast = total < (1ll << 31);
   const unsigned long long gen = ctl->gen;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int jq = (int)(t % nq);
-    const int64_t ri = t / nq;
-    const int i = (int)(ri % NP), r = (int)(ri / NP);
-    const uint64_t seed = seeds[r];
-    const uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_PART);
-    const double* Xr = X + (int64_t)r * NP * ld;
-    const double* xi = Xr + (int64_t)i * ld;
-    const double *d1, *d2, *d3;
-    int p0, p1, p2, jr;
-    if (ALG == SEVO_DE_RAND1) {
-      int a = (int)sv_below(w.x, (uint32_t)(NP - 1));
-      if (a >= i) ++a;
-      const int lo = min(i, a), hi = max(i, a);
-      int b = (int)sv_below(w.y, (uint32_t)(NP - 2));
-      if (b >= lo) ++b;
-      if (b >= hi) ++b;
-      int e0 = lo, e1 = hi, e2 = b;  // sort {i, a, b}
-      if (e2 < e1) {
-        int tt = e1;
-        e1 = e2;
-        e2 = tt;
-      }
-      if (e1 < e0) {
-        int tt = e0;
-        e0 = e1;
-        e1 = tt;
-      }
-      int c = (int)sv_below(w.z, (uint32_t)(NP - 3));
-      if (c >= e0) ++c;
-      if (c >= e1) ++c;
-      if (c >= e2) ++c;
-      p0 = a;
-      p1 = b;
-      p2 = c;
-      d1 = Xr + (int64_t)a * ld;
-      d2 = Xr + (int64_t)b * ld;
-      d3 = Xr + (int64_t)c * ld;
-    } else {
-      const int as = asize[r];
-      const int pb = order[(int64_t)r * NP + (int)sv_below(w.x, (uint32_t)pk)];
-      int r1 = (int)sv_below(w.y, (uint32_t)(NP - 1));
-      if (r1 >= i) ++r1;
-      const int lo = min(i, r1), hi = max(i, r1);
-      int r2 = (int)sv_below(w.z, (uint32_t)(NP + as - 2));
-      if (r2 >= lo) ++r2;
-      if (r2 >= hi) ++r2;
-      p0 = pb;
-      p1 = r1;
-      p2 = r2;
-      d1 = Xr + (int64_t)pb * ld;
-      d2 = Xr + (int64_t)r1 * ld;
-      d3 = (r2 < NP) ? Xr + (int64_t)r2 * ld : A + ((int64_t)r * NP + (r2 - NP)) * ld;
-    }
-    jr = (int)sv_below(w.w, (uint32_t)D);
-    if (jq == 0 && part) {
-      int32_t* pp = part + ((int64_t)r * NP + i) * 4;
-      pp[0] = p0;
-      pp[1] = p1;
-      pp[2] = p2;
-      pp[3] = jr;
-    }
-    const uint4 cw = sv_draw(seed, (uint32_t)jq, (uint32_t)i, (uint32_t)gen, SV_P_CROSS);
-    const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
-    double* ui = U + ((int64_t)r * NP + i) * ld;
-    const int j0 = jq * 4;
-    double xv[4], v1[4], v2[4], v3[4];
-    load_quad(xi, j0, D, xv);
-    load_quad(d1, j0, D, v1);
-    load_quad(d2, j0, D, v2);
-    load_quad(d3, j0, D, v3);
-    const long long lbk = ord_key(lb), ubk = ord_key(ub);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = j0 + q;
-      if (j >= D) break;
-      const double x = xv[q];
-      double u = x;
-      if ((unsigned long long)cws[q] < cr_thr || j == jr) {
-        if (ALG == SEVO_DE_RAND1)
-          u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), v1[q]);
-        else
-          u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), __fma_rn(F, __dsub_rn(v1[q], x), x));
-      }
-      // repair: if u < lb then u = (lb + x) / 2; then if u > ub, u = (ub + x) / 2.
-      // With the parent inside the bounds at most one of them applies, so one
-      // FP64 add with the bound chosen by a select; the second check only
-      // fires for parents outside the bounds (populations set by the caller)
-      const bool lo = lt_key(u, lbk), hi = gt_key(u, ubk);
-      if (lo || hi) {
-        u = half_exact(__dadd_rn(lo ? lb : ub, x));
-        if (lo && gt_key(u, ubk)) u = half_exact(__dadd_rn(ub, x));
-      }
-      ui[j] = u;
-    }
+    const Split3 sp = split3(t, fast, fq, fnp);
+    de_trial_elem<ALG>(X, U, A, asize, order, part, seeds, NP, D, ld, F, cr_thr, lb, ub, pk, gen,
+                       sp.hi, sp.mid, sp.lo);
   }
 }
 
@@ -265,6 +323,21 @@ __global__ void __launch_bounds__(RANK_ROWS)
   }
   for (; j < NP; ++j) rank += (keys[j] < ki) || (keys[j] == ki && j < i);
   if (rank < k) order[(int64_t)r * NP + rank] = i;
+}
+
+// the same ranking for run r by one block (keys: NP entries of shared memory)
+__device__ __forceinline__ void rank_run_block(const double* __restrict__ f,
+                                               int32_t* __restrict__ order_r, int NP, int k,
+                                               long long* keys) {
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) keys[i] = fkey(f[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+    const long long ki = keys[i];
+    int rank = 0;
+    for (int j = 0; j < NP; ++j) rank += (keys[j] < ki) || (keys[j] == ki && j < i);
+    if (rank < k) order_r[rank] = i;
+  }
+  __syncthreads();
 }
 
 // Larger populations: one CTA per run finds the k-th smallest key by an
@@ -408,21 +481,21 @@ __host__ __device__ constexpr size_t sel_smem_bytes(int NP) {
   return (size_t)NP * (8 + 8 + 4 + 4 + 1) + 16;
 }
 
-__global__ void __launch_bounds__(SEL_THREADS)
-    de_select_kernel(double* __restrict__ fx, const double* __restrict__ fu,
-                     int32_t* __restrict__ asize, int32_t* __restrict__ action,
-                     double* __restrict__ best, const uint64_t* __restrict__ seeds,
-                     const GenCtl* __restrict__ ctl, int NP, int use_archive) {
-  extern __shared__ __align__(16) unsigned char sel_sm[];
+// run r by the whole block; sel_sm: sel_smem_bytes(NP) of shared memory
+__device__ __forceinline__ void de_select_run(double* __restrict__ fx, const double* __restrict__ fu,
+                                              int32_t* __restrict__ asize,
+                                              int32_t* __restrict__ action,
+                                              double* __restrict__ best,
+                                              const uint64_t* __restrict__ seeds, int count,
+                                              unsigned long long gen, int NP, int use_archive,
+                                              int r, unsigned char* sel_sm) {
   double* sf = reinterpret_cast<double*>(sel_sm);  // current fitness
   double* sg = sf + NP;                             // trial fitness
   int* owner = reinterpret_cast<int*>(sg + NP);     // archive slot -> last row
   int* sact = owner + NP;                           // action per row
   unsigned char* sacc = reinterpret_cast<unsigned char*>(sact + NP);  // accepted
   __shared__ int wsum[SEL_THREADS / 32];
-  const int r = blockIdx.x, tid = threadIdx.x;
-  const int count = ctl->count;
-  const unsigned long long gen = ctl->gen;
+  const int tid = threadIdx.x;
   double* f = fx + (int64_t)r * NP;
   const double* g = fu + (int64_t)r * NP;
   int32_t* act = action + (int64_t)r * NP;
@@ -484,21 +557,27 @@ __global__ void __launch_bounds__(SEL_THREADS)
     if (a != -2) f[i] = sg[i];
   }
   if (tid == 0 && use_archive) asize[r] = min(NP, as0 + nacc_total);
+  __syncthreads();
 }
 
-// accepted rows: archive <- old x (if slot), x <- u
-__global__ void de_apply_kernel(double* __restrict__ X, const double* __restrict__ U,
-                                double* __restrict__ A, const int32_t* __restrict__ action, int R,
-                                int NP, int D, int ld) {
-  const int nq = (D + 3) >> 2;
-  const int64_t total = (int64_t)R * NP * nq;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int jq = (int)(t % nq);
-    const int64_t ri = t / nq;
+__global__ void __launch_bounds__(SEL_THREADS)
+    de_select_kernel(double* __restrict__ fx, const double* __restrict__ fu,
+                     int32_t* __restrict__ asize, int32_t* __restrict__ action,
+                     double* __restrict__ best, const uint64_t* __restrict__ seeds,
+                     const GenCtl* __restrict__ ctl, int NP, int use_archive) {
+  extern __shared__ __align__(16) unsigned char sel_sm[];
+  de_select_run(fx, fu, asize, action, best, seeds, ctl->count, ctl->gen, NP, use_archive,
+                blockIdx.x, sel_sm);
+}
+
+// accepted row ri (run r): archive <- old x (if slot), x <- u; one quad
+__device__ __forceinline__ void de_apply_elem(double* __restrict__ X, const double* __restrict__ U,
+                                              double* __restrict__ A,
+                                              const int32_t* __restrict__ action, int NP, int D,
+                                              int ld, int r, int64_t ri, int jq) {
+  {
     const int a = action[ri];
-    if (a == -2) continue;
-    const int r = (int)(ri / NP);
+    if (a == -2) return;
     double* xi = X + ri * ld;
     const double* ui = U + ri * ld;
     double* as = (a >= 0) ? A + ((int64_t)r * NP + a) * ld : nullptr;
@@ -513,19 +592,32 @@ __global__ void de_apply_kernel(double* __restrict__ X, const double* __restrict
   }
 }
 
-// ---------------------------------------------------------------- PSO
-__global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
-                                const double* __restrict__ P, const int32_t* __restrict__ guide,
-                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
-                                int R, int NP, int D, int ld, double w, double c1, double c2,
-                                double lb, double ub) {
-  const int64_t total = (int64_t)R * NP * D;
-  const unsigned long long gen = ctl->gen;
+// accepted rows: archive <- old x (if slot), x <- u
+__global__ void de_apply_kernel(double* __restrict__ X, const double* __restrict__ U,
+                                double* __restrict__ A, const int32_t* __restrict__ action, int R,
+                                int NP, int D, int ld, FastDiv fq, FastDiv fnp) {
+  const int nq = (D + 3) >> 2;
+  const int64_t total = (int64_t)R * NP * nq;
+  const bool fast = total < (1ll << 31);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t % D);
-    const int64_t ri = t / D;
-    const int i = (int)(ri % NP), r = (int)(ri / NP);
+    const Split3 sp = split3(t, fast, fq, fnp);
+    const int jq = sp.lo;
+    const int64_t ri = sp.row;
+    de_apply_elem(X, U, A, action, NP, D, ld, sp.hi, ri, jq);
+  }
+}
+
+// ---------------------------------------------------------------- PSO
+// coordinate j of run r's particle i (row ri = r * NP + i)
+__device__ __forceinline__ void pso_move_elem(double* __restrict__ X, double* __restrict__ V,
+                                              const double* __restrict__ P,
+                                              const int32_t* __restrict__ guide,
+                                              const uint64_t* __restrict__ seeds,
+                                              unsigned long long gen, int NP, int ld, double w,
+                                              double c1, double c2, double lb, double ub, int r,
+                                              int i, int j, int64_t ri) {
+  {
     const uint4 rw = sv_draw(seeds[r], (uint32_t)j, (uint32_t)i, (uint32_t)gen, SV_P_PSO);
     const double r1 = u53_int(rw.x, rw.y), r2 = u53_int(rw.z, rw.w);
     const double a = __dmul_rn(c1, r1), b = __dmul_rn(c2, r2);
@@ -548,16 +640,32 @@ __global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
   }
 }
 
-// per run: strict pbest update flags, best-so-far, guides (gbest / ring)
-__global__ void __launch_bounds__(SEL_THREADS)
-    pso_update_kernel(const double* __restrict__ fx, double* __restrict__ fp,
-                      int32_t* __restrict__ flag, int32_t* __restrict__ guide,
-                      double* __restrict__ best, const GenCtl* __restrict__ ctl, int NP,
-                      int topology, int use_count, int update_best) {
+__global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
+                                const double* __restrict__ P, const int32_t* __restrict__ guide,
+                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
+                                int R, int NP, int D, int ld, double w, double c1, double c2,
+                                double lb, double ub, FastDiv fd, FastDiv fnp) {
+  const int64_t total = (int64_t)R * NP * D;
+  const bool fast = total < (1ll << 31);
+  const unsigned long long gen = ctl->gen;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Split3 sp = split3(t, fast, fd, fnp);
+    pso_move_elem(X, V, P, guide, seeds, gen, NP, ld, w, c1, c2, lb, ub, sp.hi, sp.mid, sp.lo,
+                  sp.row);
+  }
+}
+
+// run r by the whole block: strict pbest update flags, best-so-far, guides
+// (gbest / ring); sp: NP doubles of shared memory
+__device__ __forceinline__ void pso_update_run(const double* __restrict__ fx,
+                                               double* __restrict__ fp, int32_t* __restrict__ flag,
+                                               int32_t* __restrict__ guide,
+                                               double* __restrict__ best, int count, int NP,
+                                               int topology, int update_best, int r, double* sp) {
   __shared__ long long kbest[SEL_THREADS / 32];
   __shared__ int ibest[SEL_THREADS / 32];
-  const int r = blockIdx.x, tid = threadIdx.x;
-  const int count = use_count ? ctl->count : NP;
+  const int tid = threadIdx.x;
   const double* f = fx + (int64_t)r * NP;
   double* p = fp + (int64_t)r * NP;
   int32_t* fl = flag + (int64_t)r * NP;
@@ -567,7 +675,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
     for (int i = tid; i < count; i += blockDim.x) m = dmin_pos(m, f[i]);
     block_min_update(m, best + r);
   }
-  extern __shared__ double sp[];  // the run's personal-best fitness
   for (int i = tid; i < NP; i += blockDim.x) {
     const double fi = f[i];
     double pi = p[i];
@@ -630,24 +737,43 @@ __global__ void __launch_bounds__(SEL_THREADS)
       gd[i] = b;
     }
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+    pso_update_kernel(const double* __restrict__ fx, double* __restrict__ fp,
+                      int32_t* __restrict__ flag, int32_t* __restrict__ guide,
+                      double* __restrict__ best, const GenCtl* __restrict__ ctl, int NP,
+                      int topology, int use_count, int update_best) {
+  extern __shared__ double sp_sm[];  // the run's personal-best fitness
+  pso_update_run(fx, fp, flag, guide, best, use_count ? ctl->count : NP, NP, topology,
+                 update_best, blockIdx.x, sp_sm);
+}
+
+// improved row ri: pbest <- x, one quad
+__device__ __forceinline__ void pso_copy_elem(double* __restrict__ P, const double* __restrict__ X,
+                                              const int32_t* __restrict__ flag, int D, int ld,
+                                              int64_t ri, int jq) {
+  if (!flag[ri]) return;
+  const int j0 = jq * 4;
+  double* pi = P + ri * ld;
+  const double* xi = X + ri * ld;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (j0 + q < D) pi[j0 + q] = xi[j0 + q];
 }
 
 // improved rows: pbest <- x
 __global__ void pso_copy_kernel(double* __restrict__ P, const double* __restrict__ X,
-                                const int32_t* __restrict__ flag, int R, int NP, int D, int ld) {
+                                const int32_t* __restrict__ flag, int R, int NP, int D, int ld,
+                                FastDiv fq, FastDiv fnp) {
   const int nq = (D + 3) >> 2;
   const int64_t total = (int64_t)R * NP * nq;
+  const bool fast = total < (1ll << 31);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int jq = (int)(t % nq);
-    const int64_t ri = t / nq;
-    if (!flag[ri]) continue;
-    const int j0 = jq * 4;
-    double* pi = P + ri * ld;
-    const double* xi = X + ri * ld;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (j0 + q < D) pi[j0 + q] = xi[j0 + q];
+    const Split3 sp = split3(t, fast, fq, fnp);
+    pso_copy_elem(P, X, flag, D, ld, sp.row, sp.lo);
   }
 }
 
@@ -655,6 +781,318 @@ __global__ void fill_kernel(double* __restrict__ a, int64_t n, double v) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)
     a[t] = v;
+}
+
+// ---------------------------------------------------------------- small runs
+// One CTA per run carries whole generations of a small run (D <= 32,
+// NP <= 512): launched with G > 1 it runs G consecutive generations without
+// returning to the host.  The operators are the batched kernels' device
+// functions above (same draws, same arithmetic); the evaluation is a warp
+// per row on CUDA cores -- FP64, or FP32 with the operand rounding of the
+// requested mode (TF32, BF16 hi/lo products, plain FP32) and FP64
+// refinement below the threshold -- so one evaluator serves a run throughout.
+constexpr int SRK_THREADS = 256;
+constexpr int SRK_MAX_D = 32, SRK_MAX_NP = 512;
+
+struct SrkArgs {
+  double *X, *fx, *U, *fu, *A, *V, *P, *fp, *best;
+  int32_t *asize, *guide, *part, *order, *action;
+  const uint64_t* seeds;
+  const ProblemDev* const* rp;
+  const GenCtl* ctl;
+  unsigned long long* refined;
+  int NP, D, ld, pk, topology;
+  double F, lb, ub, w, c1, c2;
+  unsigned long long cr_thr;
+  long long budget;
+};
+
+__host__ __device__ inline size_t srk_smem_bytes(int NP) {
+  const size_t a = sel_smem_bytes(NP), b = (size_t)NP * 8;
+  return a > b ? a : b;
+}
+
+__device__ __forceinline__ void warp_sum64(int body, Acc64& a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const double b0 = __shfl_xor_sync(0xffffffffu, a.a0, m);
+    const double b1 = __shfl_xor_sync(0xffffffffu, a.a1, m);
+    const double b2 = __shfl_xor_sync(0xffffffffu, a.a2, m);
+    a.a0 += b0;
+    a.a1 = slot1_is_product64(body) ? a.a1 * b1 : a.a1 + b1;
+    a.a2 += b2;
+  }
+}
+
+__device__ __forceinline__ void warp_sum32(Acc32& a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    a.a0 += __shfl_xor_sync(0xffffffffu, a.a0, m);
+    a.a1 += __shfl_xor_sync(0xffffffffu, a.a1, m);
+    a.a2 += __shfl_xor_sync(0xffffffffu, a.a2, m);
+  }
+}
+
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// FP64 error of row x by one warp: lane = coordinate (D <= 32)
+__device__ double srk_eval64(const ProblemDev& P, const double* __restrict__ x, int lane) {
+  const int D = P.D;
+  const bool comp = (P.family == SEVO_COMPOSITION);
+  const double xj = (lane < D) ? x[lane] : 0.0;
+  double gv[SV_MAXC], sv[SV_MAXC];
+  double total = 0.0;
+  for (int c = 0; c < P.ncomp; ++c) {
+    const double dj = (lane < D) ? __dsub_rn(xj, P.o[c][lane]) : 0.0;
+    const double* __restrict__ MT = P.MT64[c];
+    double z = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double dd = __shfl_sync(0xffffffffu, dj, j);
+      if (lane < D) z = __fma_rn(MT[(size_t)j * D + lane], dd, z);
+    }
+    const int gi = comp ? 0 : ((lane < D) ? P.gid[c][lane] : -1);
+    const double zn = __shfl_down_sync(0xffffffffu, z, 1);
+    const int gn = __shfl_down_sync(0xffffffffu, gi, 1);
+    const int ng = comp ? 1 : P.ngroups;
+    double gc = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const int body = comp ? P.cbody[c] : P.gbody[g];
+      Acc64 a;
+      acc64_init(body, a);
+      if (lane < D && gi == g)
+        term64(body, z, P.aux64[c][lane], lane + 1 < D && gn == g, zn, P, a);
+      warp_sum64(body, a);
+      gc += finalize64(body, a, P.gstart[g + 1] - P.gstart[g]);
+    }
+    if (comp) {
+      gv[c] = gc;
+      sv[c] = warp_sumd(dj * dj);
+    } else {
+      total = gc;
+    }
+  }
+  const double err = comp ? compose(P, sv, gv) : total;
+  return isfinite(err) ? err : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// mixed-precision error of row x by one warp; rows below the refinement
+// threshold are re-evaluated by srk_eval64 (*refined = true)
+template <int PREC>
+__device__ double srk_eval32(const ProblemDev& P, const double* __restrict__ x, int lane,
+                             bool* refined) {
+  const int D = P.D;
+  const bool comp = (P.family == SEVO_COMPOSITION);
+  float xh = 0.f, xl = 0.f;
+  if (lane < D) sv_split_hi_lo(x[lane], xh, xl);
+  double gv[SV_MAXC], sv[SV_MAXC];
+  double total = 0.0;
+  for (int c = 0; c < P.ncomp; ++c) {
+    const float d = (lane < D) ? (xh - P.oh32[c][lane]) + (xl - P.ol32[c][lane]) : 0.f;
+    float z = 0.f;
+    if (PREC == SEVO_FP32) {
+      const float* __restrict__ MT = P.MT32[c];
+      for (int j = 0; j < D; ++j) {
+        const float dd = __shfl_sync(0xffffffffu, d, j);
+        if (lane < D) z = fmaf(MT[(size_t)j * D + lane], dd, z);
+      }
+    } else if (PREC == SEVO_TF32) {
+      const float dt = tc::to_tf32(d);
+      const float* __restrict__ Mr = P.M32[c] + (size_t)lane * P.kpad;
+      for (int j = 0; j < D; ++j) {
+        const float dd = __shfl_sync(0xffffffffu, dt, j);
+        if (lane < D) z = fmaf(Mr[j], dd, z);
+      }
+    } else {  // BF16X3: hi*hi + hi*lo + lo*hi, products exact in FP32
+      const __nv_bfloat16 h = __float2bfloat16_rn(d);
+      const float dh = __bfloat162float(h);
+      const float dl = __bfloat162float(__float2bfloat16_rn(d - dh));
+      const __nv_bfloat16* __restrict__ Mh = P.Mhi[c] + (size_t)lane * P.kpad;
+      const __nv_bfloat16* __restrict__ Ml = P.Mlo[c] + (size_t)lane * P.kpad;
+      for (int j = 0; j < D; ++j) {
+        const float hj = __shfl_sync(0xffffffffu, dh, j), lj = __shfl_sync(0xffffffffu, dl, j);
+        if (lane < D) {
+          const float mh = __bfloat162float(Mh[j]), ml = __bfloat162float(Ml[j]);
+          z = fmaf(mh, hj, z);
+          z = fmaf(mh, lj, z);
+          z = fmaf(ml, hj, z);
+        }
+      }
+    }
+    const int gi = comp ? 0 : ((lane < D) ? P.gid[c][lane] : -1);
+    const float zn = __shfl_down_sync(0xffffffffu, z, 1);
+    const int gn = __shfl_down_sync(0xffffffffu, gi, 1);
+    const int ng = comp ? 1 : P.ngroups;
+    double gc = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const int body = comp ? P.cbody[c] : P.gbody[g];
+      Acc32 a;
+      acc32_init(a);
+      if (lane < D && gi == g)
+        term32t<PREC == SEVO_TF32>(body, z, P.aux32[c][lane], lane + 1 < D && gn == g, zn, P, a);
+      warp_sum32(a);
+      gc += (double)finalize32(body, a, P.gstart[g + 1] - P.gstart[g]);
+    }
+    if (comp) {
+      gv[c] = gc;
+      sv[c] = warp_sumd((double)(d * d));
+    } else {
+      total = gc;
+    }
+  }
+  double err = comp ? compose(P, sv, gv) : total;
+  if (!isfinite(err)) return __longlong_as_double(0x7ff8000000000000ll);
+  if (err < SEVO_REFINE_THRESHOLD) {
+    err = srk_eval64(P, x, lane);
+    *refined = true;
+  }
+  return err;
+}
+
+template <int PREC>
+__device__ __forceinline__ double srk_eval(const ProblemDev& P, const double* x, int lane,
+                                           bool* refined) {
+  if (PREC == SEVO_FP64) return srk_eval64(P, x, lane);
+  return srk_eval32<PREC>(P, x, lane, refined);
+}
+
+// advance = 0: one generation with the counter and count of ctl;
+// advance = 1: G generations gen0 + 1 .. gen0 + G (gen0 = ctl->gen), each
+// with the evaluation count ctl_advance_kernel would give it
+template <int ALG, int PREC>
+__global__ void __launch_bounds__(SRK_THREADS)
+    srk_kernel(const SrkArgs a, int G, int advance) {
+  extern __shared__ __align__(16) unsigned char srk_sm[];
+  __shared__ ProblemDev P;
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  const int nwarp = blockDim.x >> 5, warp = tid >> 5;
+  {  // the run's problem descriptor, with the Schwefel constant computed by
+     // the device sin as in the FP64 bodies (term exactly 0 at the optimum)
+    const int* src = reinterpret_cast<const int*>(a.rp[r]);
+    int* dst = reinterpret_cast<int*>(&P);
+    for (int q = tid; q < (int)(sizeof(ProblemDev) / 4); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    if (tid == 0) P.sch_c = __dmul_rn(P.sch_s, sin(sqrt(P.sch_s)));
+    __syncthreads();
+  }
+  const int NP = a.NP, D = a.D, nq = (D + 3) >> 2;
+  const int64_t r0 = (int64_t)r * NP;
+  unsigned long long gen = a.ctl->gen;
+  int count = a.ctl->count;
+  unsigned long long nref = 0;
+  for (int k = 0; k < G; ++k) {
+    if (advance) {
+      ++gen;
+      const long long c = a.budget - ((long long)NP + (long long)(gen - 1) * NP);
+      count = (int)(c < 0 ? 0 : (c > NP ? NP : c));
+    }
+    if (ALG == SEVO_DE_RAND1 || ALG == SEVO_DE_CTPB) {
+      if (ALG == SEVO_DE_CTPB)
+        rank_run_block(a.fx + r0, a.order + r0, NP, a.pk, reinterpret_cast<long long*>(srk_sm));
+      for (int t = tid; t < NP * nq; t += blockDim.x) {
+        const int i = t / nq;
+        de_trial_elem<ALG>(a.X, a.U, a.A, a.asize, a.order, a.part, a.seeds, NP, D, a.ld, a.F,
+                           a.cr_thr, a.lb, a.ub, a.pk, gen, r, i, t - i * nq);
+      }
+      __syncthreads();
+      for (int i = warp; i < NP; i += nwarp) {
+        bool ref = false;
+        const double e = srk_eval<PREC>(P, a.U + (r0 + i) * a.ld, lane, &ref);
+        if (lane == 0) {
+          a.fu[r0 + i] = e;
+          nref += ref;
+        }
+      }
+      __syncthreads();
+      de_select_run(a.fx, a.fu, a.asize, a.action, a.best, a.seeds, count, gen, NP,
+                    ALG == SEVO_DE_CTPB, r, srk_sm);
+      for (int t = tid; t < NP * nq; t += blockDim.x) {
+        const int i = t / nq;
+        de_apply_elem(a.X, a.U, a.A, a.action, NP, D, a.ld, r, r0 + i, t - i * nq);
+      }
+      __syncthreads();
+    } else {
+      for (int t = tid; t < NP * D; t += blockDim.x) {
+        const int i = t / D;
+        pso_move_elem(a.X, a.V, a.P, a.guide, a.seeds, gen, NP, a.ld, a.w, a.c1, a.c2, a.lb, a.ub,
+                      r, i, t - i * D, r0 + i);
+      }
+      __syncthreads();
+      for (int i = warp; i < NP; i += nwarp) {
+        bool ref = false;
+        const double e = srk_eval<PREC>(P, a.X + (r0 + i) * a.ld, lane, &ref);
+        if (lane == 0) {
+          a.fx[r0 + i] = e;
+          nref += ref;
+        }
+      }
+      __syncthreads();
+      pso_update_run(a.fx, a.fp, a.action, a.guide, a.best, count, NP, a.topology, 1, r,
+                     reinterpret_cast<double*>(srk_sm));
+      for (int t = tid; t < NP * nq; t += blockDim.x) {
+        const int i = t / nq;
+        pso_copy_elem(a.P, a.X, a.action, D, a.ld, r0 + i, t - i * nq);
+      }
+      __syncthreads();
+    }
+  }
+  if (PREC != SEVO_FP64 && lane == 0 && nref) atomicAdd(a.refined, nref);
+}
+
+template <int ALG>
+cudaError_t srk_launch_prec(const Batch* b, const SrkArgs& a, int G, int advance) {
+  const size_t sm = srk_smem_bytes(b->NP);
+  switch (b->prec) {
+    case SEVO_FP64: srk_kernel<ALG, SEVO_FP64><<<b->R, SRK_THREADS, sm, b->stream>>>(a, G, advance); break;
+    case SEVO_TF32: srk_kernel<ALG, SEVO_TF32><<<b->R, SRK_THREADS, sm, b->stream>>>(a, G, advance); break;
+    case SEVO_BF16X3: srk_kernel<ALG, SEVO_BF16X3><<<b->R, SRK_THREADS, sm, b->stream>>>(a, G, advance); break;
+    default: srk_kernel<ALG, SEVO_FP32><<<b->R, SRK_THREADS, sm, b->stream>>>(a, G, advance); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t srk_launch(const Batch* b, int G, int advance) {
+  SrkArgs a;
+  a.X = b->X;
+  a.fx = b->fx;
+  a.U = b->U;
+  a.fu = b->fu;
+  a.A = b->A;
+  a.V = b->V;
+  a.P = b->P;
+  a.fp = b->fp;
+  a.best = b->best;
+  a.asize = b->asize;
+  a.guide = b->guide;
+  a.part = b->part;
+  a.order = b->order;
+  a.action = b->action;
+  a.seeds = b->seeds;
+  a.rp = b->rp;
+  a.ctl = b->ctl;
+  a.refined = b->refined;
+  a.NP = b->NP;
+  a.D = b->D;
+  a.ld = b->ld;
+  a.pk = b->pbest_k;
+  a.topology = (b->alg == SEVO_PSO_RING) ? 1 : 0;
+  a.F = b->F;
+  a.lb = b->lb;
+  a.ub = b->ub;
+  a.w = b->w;
+  a.c1 = b->c1;
+  a.c2 = b->c2;
+  a.cr_thr = b->cr_thr;
+  a.budget = (long long)b->budget;
+  switch (b->alg) {
+    case SEVO_DE_RAND1: return srk_launch_prec<SEVO_DE_RAND1>(b, a, G, advance);
+    case SEVO_DE_CTPB: return srk_launch_prec<SEVO_DE_CTPB>(b, a, G, advance);
+    case SEVO_PSO_GBEST: return srk_launch_prec<SEVO_PSO_GBEST>(b, a, G, advance);
+    default: return srk_launch_prec<SEVO_PSO_RING>(b, a, G, advance);
+  }
 }
 
 unsigned grid_for(int64_t work, int threads) {
@@ -668,6 +1106,18 @@ unsigned grid_for(int64_t work, int threads) {
 }  // namespace
 
 // ====================================================================== host
+static std::atomic<int> g_policy_small_runs{0};
+
+extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
+  if (key != SEVO_POLICY_SMALL_RUNS || (value != 0 && value != 1)) return SEVO_ERR_ARG;
+  g_policy_small_runs.store((int)value);
+  return SEVO_OK;
+}
+
+extern "C" int64_t sevo_get_policy(int32_t key) {
+  return key == SEVO_POLICY_SMALL_RUNS ? g_policy_small_runs.load() : -1;
+}
+
 int sv_pbest_k(double p, int NP) {
   int k = (int)std::ceil(p * (double)NP - 1e-9);
   if (k < 1) k = 1;
@@ -704,6 +1154,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->cr_thr = (unsigned long long)t;
   }
   b->pbest_k = sv_pbest_k(a->p, a->NP);
+  b->small = g_policy_small_runs.load() != 0 && b->D <= SRK_MAX_D && b->NP <= SRK_MAX_NP;
   b->run_prob = probs;
   b->seg_begin.clear();
   for (int r = 0; r < b->R; ++r)
@@ -715,6 +1166,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB);
   const bool ctpb = (b->alg == SEVO_DE_CTPB);
   size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ + al256(16) /*err*/ +
+                 al256(8) /*refined*/ + al256((size_t)b->R * 8) /*rp*/ +
                  al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
                  al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
   if (de) bytes += mat /*U*/ + vec /*fu*/;
@@ -739,6 +1191,8 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->fx = (double*)take(vec);
   b->best = (double*)take(al256((size_t)b->R * 8));
   b->err = (uint32_t*)take(al256(16));
+  b->refined = (unsigned long long*)take(al256(8));
+  b->rp = (const ProblemDev**)take(al256((size_t)b->R * 8));
   b->seeds = (uint64_t*)take(al256((size_t)b->R * 8));
   b->ctl = (GenCtl*)take(al256(sizeof(GenCtl)));
   b->guide = (int32_t*)take(ivec);
@@ -761,6 +1215,11 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->fp = (double*)take(vec);
   }
   SV_CUDA(cudaMemcpyAsync(b->seeds, seeds.data(), (size_t)b->R * 8, cudaMemcpyHostToDevice, st));
+  {
+    std::vector<const ProblemDev*> rp(b->R);
+    for (int r = 0; r < b->R; ++r) rp[r] = probs[r]->desc_d;
+    SV_CUDA(cudaMemcpyAsync(b->rp, rp.data(), (size_t)b->R * 8, cudaMemcpyHostToDevice, st));
+  }
   // evaluation scratch for all rows (refine sub-lists per segment and the
   // tensor-core composition staging)
   bool any_comp = false;
@@ -788,6 +1247,7 @@ static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
   sc.err = b->err;
+  sc.refined = b->refined;
   return sv_eval_segments(segs.data(), (int)segs.size(), b->prec, M, b->ld, f, sc, b->stream);
 }
 
@@ -811,7 +1271,9 @@ cudaError_t sv_batch_init(Batch* b) {
   const int T = 256;
   const int tk3 = sv_trace_begin(SEVO_TK_INIT, st);
   init_pop_kernel<<<grid_for(rows * ((b->D + 1) / 2), T), T, 0, st>>>(b->X, b->seeds, b->R, b->NP,
-                                                                     b->D, b->ld, b->lb, b->ub);
+                                                                     b->D, b->ld, b->lb, b->ub,
+                                                                     make_fastdiv((b->D + 1) / 2),
+                                                                     make_fastdiv(b->NP));
   sv_trace_end(tk3, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -843,8 +1305,32 @@ cudaError_t sv_batch_init(Batch* b) {
   return cudaGetLastError();
 }
 
+cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens) {
+  const int64_t chunk = 1 << 16;  // generations per launch
+  cudaError_t e = cudaSuccess;
+  for (int64_t done = 0; done < gens && e == cudaSuccess;) {
+    const int G = (int)std::min<int64_t>(chunk, gens - done);
+    const int tk = sv_trace_begin(SEVO_TK_SMALL_RUN, b->stream);
+    e = srk_launch(b, G, 1);
+    sv_trace_end(tk, b->stream);
+    done += G;
+    if (e != cudaSuccess) break;
+    // the counter and count of the last generation run, as ctl_advance leaves them
+    const unsigned long long g = gen0 + (unsigned long long)done;
+    const long long c = (long long)b->budget - ((long long)b->NP + (long long)(g - 1) * b->NP);
+    e = sv_ctl_set(b, g, (int)(c < 0 ? 0 : (c > b->NP ? b->NP : c)));
+  }
+  return e;
+}
+
 cudaError_t sv_batch_generation(Batch* b) {
   cudaStream_t st = b->stream;
+  if (b->small) {
+    const int tk = sv_trace_begin(SEVO_TK_SMALL_RUN, st);
+    const cudaError_t es = srk_launch(b, 1, 0);
+    sv_trace_end(tk, st);
+    return es;
+  }
   const int64_t rows = (int64_t)b->R * b->NP;
   const int nq = (b->D + 3) >> 2;
   const int T = 256;
@@ -865,13 +1351,14 @@ cudaError_t sv_batch_generation(Batch* b) {
       const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
       de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k);
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
+          make_fastdiv(b->NP));
       sv_trace_end(tk8, st);
     } else {
       const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
       de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0);
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP));
       sv_trace_end(tk9, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -883,13 +1370,15 @@ cudaError_t sv_batch_generation(Batch* b) {
     sv_trace_end(tk10, st);
     const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
     de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
-                                                         b->D, b->ld);
+                                                         b->D, b->ld, make_fastdiv(nq),
+                                                         make_fastdiv(b->NP));
     sv_trace_end(tk11, st);
   } else {
     const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
     pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
                                                            b->ctl, b->R, b->NP, b->D, b->ld, b->w,
-                                                           b->c1, b->c2, b->lb, b->ub);
+                                                           b->c1, b->c2, b->lb, b->ub,
+                                                           make_fastdiv(b->D), make_fastdiv(b->NP));
     sv_trace_end(tk12, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
@@ -899,7 +1388,8 @@ cudaError_t sv_batch_generation(Batch* b) {
     sv_trace_end(tk13, st);
     const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
     pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
-                                                         b->D, b->ld);
+                                                         b->D, b->ld, make_fastdiv(nq),
+                                                         make_fastdiv(b->NP));
     sv_trace_end(tk14, st);
   }
   return cudaGetLastError();

@@ -31,12 +31,15 @@ struct Batch {
   uint64_t* seeds;
   GenCtl* ctl;
   uint32_t* err;  // device error bits accumulated over every evaluation
+  unsigned long long* refined;  // rows re-evaluated in FP64, all generations
+  const ProblemDev** rp;        // per-run problem descriptors (device)
+  bool small;                   // generations run by the run-per-CTA kernel
   // evaluation scratch (refine list + counters + tensor-core staging)
   void* eval_block;
   size_t eval_bytes;
   bool any_comp;
   cudaStream_t stream;
-  int64_t refined_host;  // running count read back on result queries
+  int64_t refined_host;  // unused (the device counter `refined` is read instead)
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
@@ -47,6 +50,9 @@ void sv_batch_free(Batch* b);
 cudaError_t sv_batch_init(Batch* b);
 // one generation; gen/count read from b->ctl (set by the caller's launch)
 cudaError_t sv_batch_generation(Batch* b);
+// small batches (b->small): generations gen0 + 1 .. gen0 + gens in run-per-CTA
+// launches; leaves ctl at generation gen0 + gens
+cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens);
 cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count);
 cudaError_t sv_ctl_advance(Batch* b);  // gen += 1, count from gen and budget
 int sv_pbest_k(double p, int NP);

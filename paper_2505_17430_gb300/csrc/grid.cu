@@ -108,7 +108,11 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
     int G = grid->gens_per_graph > 0 ? grid->gens_per_graph : 32;
     if (G > gens) G = (int)std::max<int64_t>(gens, 1);
     int64_t done = 0;
-    if (e == cudaSuccess && gens >= G && G > 0) {
+    if (e == cudaSuccess && b.small) {  // run-per-CTA launches, no graph needed
+      e = sv_batch_run_small(&b, 0ull, gens);
+      done = gens;
+    }
+    if (e == cudaSuccess && !b.small && gens >= G && G > 0) {
       GraphExec ge;
       int64_t nk = 0;
       e = capture(&b, G, &ge, &nk);

@@ -27,6 +27,7 @@ struct RefineTable {
   int nseg;
   const ProblemDev* P[SV_MAX_SEG];
   int64_t list_off[SV_MAX_SEG];
+  unsigned long long* total;  // running count of refined rows (null: none)
 };
 
 int sv_num_sms();
@@ -63,6 +64,7 @@ struct EvalScratch {
   void* tc;           // tensor-core composition staging
   size_t tc_bytes;
   uint32_t* err;      // persistent device error bits (null: use the counters' word)
+  unsigned long long* refined;  // running count of refined rows (null: none)
 };
 #define SV_COUNTERS_BYTES ((SV_MAX_SEG + 4) * 4)
 size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);

@@ -79,6 +79,7 @@ extern "C" int32_t sevo_state_restart(sevo_state* s, const uint64_t* seeds) {
   const int64_t rows = (int64_t)b.R * b.NP;
   cudaError_t e = cudaMemcpyAsync(b.seeds, seeds, (size_t)b.R * 8, cudaMemcpyHostToDevice, b.stream);
   if (e == cudaSuccess && b.asize) e = cudaMemsetAsync(b.asize, 0, (size_t)b.R * 4, b.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.refined, 0, 8, b.stream);
   if (e == cudaSuccess && b.V)
     e = cudaMemsetAsync(b.V, 0, (size_t)rows * b.ld * 8, b.stream);
   if (e == cudaSuccess) e = sv_batch_init(&b);
@@ -149,7 +150,12 @@ extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t*
   if (best) *best = b;
   if (fes) *fes = s->fes;
   if (gens) *gens = s->gens;
-  if (refined) *refined = s->b.refined_host;
+  if (refined) {
+    unsigned long long n = 0;
+    SV_CUDA(cudaMemcpyAsync(&n, s->b.refined, 8, cudaMemcpyDeviceToHost, s->b.stream));
+    SV_CUDA(cudaStreamSynchronize(s->b.stream));
+    *refined = (int64_t)n;
+  }
   return SEVO_OK;
 }
 

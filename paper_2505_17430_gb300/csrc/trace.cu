@@ -25,7 +25,7 @@ double g_ms[SEVO_TRACE_KINDS];
 const char* const k_names[SEVO_TRACE_KINDS] = {
     "eval_tc_fused", "eval_cc", "refine", "compose", "convert", "gemm_big", "combine", "init",
     "de_trial", "de_rank", "de_select", "de_apply", "pso_move", "pso_update", "pso_copy",
-    "control"};
+    "control", "small_run"};
 
 cudaEvent_t take_event(int dev) {
   for (size_t i = 0; i < g_pool.size(); ++i) {

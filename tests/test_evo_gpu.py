@@ -22,6 +22,17 @@ def S():
     return S
 
 
+@pytest.fixture(params=[1, 0], ids=["small_runs", "batched"])
+def policy(S, request):
+    """Run the test with runs of D <= 32, NP <= 512 advanced by the
+    run-per-CTA kernel (1) and by the batched kernels (0)."""
+    lib = S.lib()
+    old = lib.sevo_get_policy(S.POLICY_SMALL_RUNS)
+    S.check(lib.sevo_set_policy(S.POLICY_SMALL_RUNS, request.param), "sevo_set_policy")
+    yield request.param
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, old)
+
+
 def _state(S, fam, D, alg, NP, budget, seed, prec=None, pseed=None):
     prec = S.FP64 if prec is None else prec
     p = S.Problem(pseed if pseed is not None else 100 + fam, fam, D)
@@ -31,7 +42,7 @@ def _state(S, fam, D, alg, NP, budget, seed, prec=None, pseed=None):
 
 
 @pytest.mark.parametrize("alg", [0, 1, 2, 3])
-def test_initial_population_bit_exact(S, alg):
+def test_initial_population_bit_exact(S, policy, alg):
     NP, D = 40, 13
     p, q, st = _state(S, S.RASTRIGIN, D, alg, NP, 10000, 77)
     g = st.get()
@@ -48,7 +59,7 @@ def _decided(fa, fb, tol):
 
 @pytest.mark.parametrize("fam,D,NP", [(S_, D_, N_) for S_, D_, N_ in
                                       [(2, 10, 50), (6, 30, 37), (7, 17, 64), (1, 100, 24)]])
-def test_de_rand1_lockstep(S, fam, D, NP):
+def test_de_rand1_lockstep(S, policy, fam, D, NP):
     p, q, st = _state(S, fam, D, S.DE_RAND1, NP, 10 ** 6, 5)
     X = O.init_population(5, NP, D)
     fx = q.eval(X)
@@ -71,7 +82,7 @@ def test_de_rand1_lockstep(S, fam, D, NP):
         X, fx = X2, fx2
 
 
-def test_de_ctpb_archive_lockstep(S):
+def test_de_ctpb_archive_lockstep(S, policy):
     fam, D, NP = S.ACKLEY, 20, 60
     p, q, st = _state(S, fam, D, S.DE_CTPB, NP, 10 ** 6, 9)
     X = O.init_population(9, NP, D)
@@ -98,7 +109,7 @@ def test_de_ctpb_archive_lockstep(S):
 
 
 @pytest.mark.parametrize("alg", [2, 3])
-def test_pso_lockstep(S, alg):
+def test_pso_lockstep(S, policy, alg):
     fam, D, NP = S.GRIEWANK, 25, 40
     p, q, st = _state(S, fam, D, alg, NP, 10 ** 6, 13)
     X = O.init_population(13, NP, D)
@@ -124,7 +135,7 @@ def test_pso_lockstep(S, alg):
         X, V, P, fp = X2, V2, P2, fp2
 
 
-def test_c0_full_run_lockstep(S):
+def test_c0_full_run_lockstep(S, policy):
     """configs[0]: DE/rand/1/bin, NP=50, D=10, F=.5, CR=.9, FP64, budget 1e5
     on shifted-rotated Rastrigin; every one of the 1999 generations is
     compared in lock step (re-synchronised from the oracle each time)."""
@@ -156,7 +167,7 @@ def test_c0_full_run_lockstep(S):
     print("undecided selections:", mism, "of", 1999 * NP)
 
 
-def test_full_run_matches_oracle_fp64(S):
+def test_full_run_matches_oracle_fp64(S, policy):
     """A whole run on the FP64 path (no re-sync) ends at the oracle's best
     error: the trajectories agree unless a near-tie flips a decision."""
     NP, D, budget, seed = 30, 10, 6000, 3
@@ -173,7 +184,7 @@ def test_full_run_matches_oracle_fp64(S):
         assert r["best"] == pytest.approx(ref["best"], rel=1e-9, abs=1e-12), alg
 
 
-def test_budget_and_bad_calls(S):
+def test_budget_and_bad_calls(S, policy):
     p = S.Problem(1, S.SCHWEFEL, 10)
     st = S.State(p, S.alg_params(S.PSO_GBEST, 40, 100), 1)
     assert st.de_step(1) == -7          # wrong algorithm kind
@@ -183,7 +194,7 @@ def test_budget_and_bad_calls(S):
     assert st.pso_step(3) == -7         # budget spent
 
 
-def test_save_load_resume_bit_identical(S):
+def test_save_load_resume_bit_identical(S, policy):
     p = S.Problem(4, S.HYBRID, 20)
     for alg in (1, 3):
         a = S.State(p, S.alg_params(alg, 32, 10 ** 6), 8)
@@ -202,7 +213,7 @@ def test_save_load_resume_bit_identical(S):
         assert a.result()["best"] == b.result()["best"]
 
 
-def test_grid_equals_single_runs(S):
+def test_grid_equals_single_runs(S, policy):
     """sevo_run_grid (batched runs, graph-captured generations) gives the
     same results as driving each run alone through the state API."""
     D = 10
@@ -223,7 +234,7 @@ def test_grid_equals_single_runs(S):
 
 
 @pytest.mark.parametrize("prec", ["TF32", "BF16X3", "FP32"])
-def test_mixed_precision_runs_reach_oracle_quality(S, prec):
+def test_mixed_precision_runs_reach_oracle_quality(S, policy, prec):
     """Mixed-precision runs (FP64 refinement below 1e-4): DE/ctpb on the
     unimodal shifted-rotated ellipsoid at D=10 reaches the 1e-8 success
     threshold like the oracle does."""
@@ -290,14 +301,26 @@ def test_kernel_trace_counts_and_times(S):
     generations) adds no captured launch to the totals."""
     D, NP = 30, 64
     p = S.Problem(77, S.RASTRIGIN, D)
+    lib = S.lib()
+    old_policy = lib.sevo_get_policy(S.POLICY_SMALL_RUNS)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 0)
     st = S.State(p, S.alg_params(S.DE_CTPB, NP, 10 ** 6, prec=S.TF32), 5)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 1)
+    small = S.State(p, S.alg_params(S.DE_CTPB, NP, 10 ** 6, prec=S.TF32), 5)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, old_policy)
+    S.trace_enable(True)
+    assert small.de_step(1) == 0
+    t = S.trace_read()
+    assert t["small_run"][0] == 1 and t["small_run"][1] > 0.0 and t["de_trial"][0] == 0
     S.trace_enable(True)
     assert st.de_step(1) == 0
     t = S.trace_read()
     for k in ("de_rank", "de_trial", "eval_tc_fused", "de_select", "de_apply"):
         assert t[k][0] == 1 and t[k][1] > 0.0, (k, t[k])
     S.trace_enable(True)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 0)
     S.sevo_run_grid([p], [S.alg_params(S.PSO_RING, 20, 20 * 40)], [(0, 0, 3)], gens_per_graph=8)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, old_policy)
     t = S.trace_read()
     S.trace_enable(False)
     assert t["pso_move"][0] < 39  # most generations ran inside graphs
@@ -305,7 +328,7 @@ def test_kernel_trace_counts_and_times(S):
 
 
 @pytest.mark.parametrize("alg", [1, 3])
-def test_restart_equals_fresh_state(S, alg):
+def test_restart_equals_fresh_state(S, policy, alg):
     """sevo_state_restart(seeds) leaves a (batched) state bit-identical to a
     state freshly created with those seeds, and both step identically."""
     D, NP = 13, 40
@@ -326,3 +349,42 @@ def test_restart_equals_fresh_state(S, alg):
         assert ga["asize"] == gb["asize"]
         assert st.result() == fresh.result()
         assert np.array_equal(st.best(), fresh.best())
+
+
+def test_small_runs_grid_single_launch_and_refined_count(S):
+    """With the run-per-CTA policy a grid bucket of small runs advances all
+    its generations in one launch; mixed-precision runs report how many rows
+    were re-evaluated in FP64 (nonzero once a run gets below 1e-4)."""
+    D, NP, budget = 10, 50, 150000
+    p = S.Problem(2, S.ELLIPSOID, D)
+    a = S.alg_params(S.DE_CTPB, NP, budget, prec=S.TF32)
+    lib = S.lib()
+    old = lib.sevo_get_policy(S.POLICY_SMALL_RUNS)
+    lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 1)
+    try:
+        S.trace_enable(True)
+        res = S.sevo_run_grid([p], [a], [(0, 0, s) for s in range(1, 5)])
+        t = S.trace_read()
+        S.trace_enable(False)
+        assert t["small_run"][0] == 1 and t.get("de_trial", (0, 0))[0] == 0
+        assert res["gens"][0] == (budget - NP + NP - 1) // NP
+        done = [k for k in range(4) if res["best"][k] < 1e-4]
+        assert done, res["best"]  # some run reached the refinement range
+        seed = 1 + done[0]
+        st = S.State(p, a, seed)
+        g = 0
+        while st.result()["fes"] < budget:
+            g += 1
+            st.step(g)
+        r = st.result()
+        assert r["best"] == res["best"][done[0]]
+        assert r["refined"] > 0
+    finally:
+        lib.sevo_set_policy(S.POLICY_SMALL_RUNS, old)
+
+
+def test_policy_arguments(S):
+    lib = S.lib()
+    assert lib.sevo_set_policy(99, 1) == S.ERR_ARG
+    assert lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 7) == S.ERR_ARG
+    assert lib.sevo_get_policy(99) == -1
