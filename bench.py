@@ -284,6 +284,29 @@ def large_d_rates(S, torch, peaks):
     return res
 
 
+def c4_sample(S):
+    """Bounded sample of the large-scale grid (D = 1000; PSO NP = 1000 and DE
+    current-to-pbest NP = 200 on hybrid and composition instances, 3e6
+    evaluations per run in full): 2 hybrid + 2 composition instances x 2 runs
+    x both algorithms at a budget of 2e4, mixed (TF32 + FP64 refinement)
+    against the FP64 GPU path through sevo_run_grid."""
+    import numpy as np
+    Dl, budget = 1000, 20000
+    probs = [S.Problem(0xC4000000 + k, 6 if k < 2 else 7, Dl) for k in range(4)]
+    out = {"workload": "2 hybrid + 2 composition instances x 2 runs x {PSO NP=1000, DE ctpb NP=200}, "
+                       "D=1000, budget 2e4 (of 3e6)", "evals": None}
+    for name, prec in (("tf32", S.TF32), ("fp64", S.FP64)):
+        algs = [S.alg_params(2, 1000, budget, prec=prec), S.alg_params(1, 200, budget, prec=prec)]
+        tasks = [(pi, ai, 1 + r) for pi in range(4) for ai in range(2) for r in range(2)]
+        r = S.sevo_run_grid(probs, algs, tasks)
+        out["evals"] = int(r["evals"])
+        out[name] = {"wall_s": round(r["wall_ms"] / 1e3, 3),
+                     "evals_per_s": round(r["evals"] / (r["wall_ms"] / 1e3), 1),
+                     "median_final_error": float(np.median(r["best"]))}
+    out["tf32_speedup"] = round(out["fp64"]["wall_s"] / out["tf32"]["wall_s"], 1)
+    return out
+
+
 def c0_single_run(S):
     """The smallest configuration: DE/rand/1/bin, NP = 50, D = 10, FP64, one
     run of 1e5 evaluations on shifted-rotated Rastrigin, seed 1 -- GPU run
@@ -509,6 +532,24 @@ def run_reference(args):
     return 0
 
 
+def eval_only(spec):
+    """Three evaluation calls of ROWS x D rows ~ U[-100, 100] (a small fixed
+    workload for profiler captures of one evaluation kernel)."""
+    import torch
+    import paper_2505_17430_gb300 as S
+    rows, Dv, prec, fam = int(spec[0]), int(spec[1]), spec[2].upper(), int(spec[3])
+    S.build()
+    X = torch.empty((rows, Dv), dtype=torch.float64, device="cuda").uniform_(-100, 100)
+    out = torch.empty(rows, dtype=torch.float64, device="cuda")
+    p = S.Problem(0x5EB00000 + fam, fam, Dv)
+    for _ in range(3):
+        p.evaluate(X, out, prec=getattr(S, prec))
+    torch.cuda.synchronize()
+    print(json.dumps({"eval_only": True, "rows": rows, "D": Dv, "prec": prec, "family": fam,
+                      "checksum": float(out.sum())}))
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -519,12 +560,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grid", action="store_true", help="skip the run-grid measurement")
     ap.add_argument("--no-large-d", action="store_true", help="skip the D=1000/5000 rates")
+    ap.add_argument("--eval-only", nargs=4, metavar=("ROWS", "D", "PREC", "FAMILY"),
+                    help="evaluate ROWS x D uniform rows three times with one mode "
+                         "(tf32|bf16x3|fp32|fp64) on one family (0-7); for profiling")
     ap.add_argument("--only-steps", action="store_true",
                     help="time the steps only (for launch-list profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.eval_only:
+        return eval_only(args.eval_only)
 
     import torch
     import paper_2505_17430_gb300 as S
@@ -584,6 +630,7 @@ def main():
     e2e, gen = e2e_rate(S, torch, states, gen, max(3, min(args.steps // 4, 400)))
     modes = mode_eval_rates(S, torch, probs)
     large = None if args.no_large_d else large_d_rates(S, torch, peaks)
+    c4 = None if args.no_large_d else c4_sample(S)
     c0 = c0_single_run(S)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     grid = None
@@ -620,6 +667,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
             "kernel_shares": shares, "eval_only_evals_per_s": modes, "large_d": large,
+            "c4_sample": c4,
             "c0_single_run": c0, "grid": grid}
     print(json.dumps(line), flush=True)
     if dist:
