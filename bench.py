@@ -97,12 +97,19 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 def make_states(S, prec, seed0, torch):
+    """One batched state per algorithm, each on its own CUDA stream: the three
+    algorithms' runs are independent, so their generations overlap on the
+    GPU (the fused evaluation of one state leaves issue slots that another
+    state's DE/PSO kernels use)."""
     probs = [S.Problem(0x5EB00000 + f, f, D) for f in range(FAMILIES)]
     states = []
     for k, (name, alg) in enumerate(ALGS):
         params = S.alg_params(alg, NP, 10 ** 12, prec=prec)
         seeds = [seed0 + 1000 * k + f for f in range(FAMILIES)]
-        states.append(S.State(probs, params, seeds))
+        stream = torch.cuda.Stream()
+        st = S.State(probs, params, seeds, stream=stream)
+        st.torch_stream = stream  # keep the stream alive with its state
+        states.append(st)
     torch.cuda.synchronize()
     return probs, states
 
@@ -110,7 +117,7 @@ def make_states(S, prec, seed0, torch):
 RESTART_EVERY = 25
 
 
-def run_steps(states, first_gen, n):
+def run_steps(states, first_gen, n, serial=False):
     """Generations first_gen .. first_gen + n - 1 of every state.  Every
     RESTART_EVERY generations each run restarts from a fresh uniform
     population (sevo_state_restart, new seeds; its work is inside the timed
@@ -118,23 +125,38 @@ def run_steps(states, first_gen, n):
     in the early phase the microbench describes (X ~ U[-100, 100]) instead
     of drifting into the refinement-heavy end of converged runs, which the
     run-grid measurement covers."""
+    import torch
+    prev = None
     for g in range(first_gen, first_gen + n):
         if g % RESTART_EVERY == 0:
             for k, st in enumerate(states):
                 st.restart([(g * 7919 + 1000 * k + r) & 0xFFFFFFFF for r in range(st.R)])
         for st in states:
+            if serial and prev is not None:  # one state at a time: chain the streams
+                st.torch_stream.wait_event(prev)
             rc = st.step(g)
             if rc != 0:
                 raise RuntimeError(f"step failed: {rc}")
+            if serial:
+                prev = torch.cuda.Event()
+                prev.record(st.torch_stream)
     return first_gen + n
 
 
 def time_steps(torch, states, gen, K):
+    """K steps between two events on the current stream: the states' streams
+    start after the first event and the second waits for all of them."""
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
+    for st in states:
+        st.torch_stream.wait_event(e0)
     gen = run_steps(states, gen, K)
+    for st in states:
+        done = torch.cuda.Event()
+        done.record(st.torch_stream)
+        stream.wait_event(done)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), gen
@@ -170,11 +192,12 @@ def profiled_traffic(name, files):
 FUSED_SOURCES = ("eval_tc.cu", "tc_walk.cuh", "bodies.cuh", "tc_ptx.cuh")
 
 
-def traced_step_kernels(S, torch, states, gen, K):
+def traced_step_kernels(S, torch, states, gen, K, serial=False):
     """Per-kernel device time from a traced repeat of the timed steps (CUDA
-    events recorded on the launching stream around every launch)."""
+    events recorded on the launching stream around every launch); serial:
+    the states' streams chained so that no two kernels overlap."""
     S.trace_enable(True)
-    gen = run_steps(states, gen, K)
+    gen = run_steps(states, gen, K, serial=serial)
     torch.cuda.synchronize()
     t = S.trace_read()
     S.trace_enable(False)
@@ -627,6 +650,12 @@ def main():
     del st64
     traced, gen = traced_step_kernels(S, torch, states, gen, min(args.steps, 200))
     roof, stream_roof, shares = rooflines(traced, states, peaks)
+    traced1, gen = traced_step_kernels(S, torch, states, gen, min(args.steps, 200), serial=True)
+    roof1, stream1, shares1 = rooflines(traced1, states, peaks)
+    roof["alone"] = {k: roof1[k] for k in ("achieved", "frac", "launch_ms")}
+    for k in stream_roof:
+        if stream_roof[k] and stream1.get(k):
+            stream_roof[k]["alone"] = {q: stream1[k][q] for q in ("achieved", "frac", "launch_ms")}
     e2e, gen = e2e_rate(S, torch, states, gen, max(3, min(args.steps // 4, 400)))
     modes = mode_eval_rates(S, torch, probs)
     large = None if args.no_large_d else large_d_rates(S, torch, peaks)
@@ -661,8 +690,12 @@ def main():
                        "prec": "tf32 rotation, fp32 bodies, fp64 shift/refine/positions",
                        "l2": "working set ~160 MB per step > 129 MB L2 (no flush needed)",
                        "kernel_times": "per-kernel CUDA-event times from a traced repeat of "
-                                       "the timed steps (events on the launching stream)",
+                                       "the timed steps (events on the launching stream); "
+                                       "'alone': a second repeat with the states' streams "
+                                       "chained, so no two kernels overlap",
                        "restart_every": RESTART_EVERY,
+                       "streams": "one CUDA stream per algorithm's state; the timed region is "
+                                  "forked from and joined to one stream by events",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
