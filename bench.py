@@ -354,12 +354,15 @@ def c0_single_run(S):
 
 
 def e2e_rate(S, torch, states, gen, K):
-    """Same step through the C ABI with host buffers: pinned host X of all
-    runs copied in, one step, fitness copied out; copies inside the timing."""
-    import numpy as np
+    """Same step through the C ABI with host buffers: every step each state's
+    population is copied in from pinned host memory, the generation runs and
+    the fitness of all its rows is copied out to pinned host memory; the
+    three states' copies and generations are enqueued on their own streams
+    (sevo_state_set_async / sevo_state_get_async) and the step ends when all
+    results are on the host.  Copies are inside the timing."""
     rows = [st.R * NP for st in states]
     hostX = [torch.empty((r, D), dtype=torch.float64).pin_memory() for r in rows]
-    hostF = [np.zeros(r) for r in rows]
+    hostF = [torch.empty(r, dtype=torch.float64).pin_memory() for r in rows]
     for st, hx in zip(states, hostX):
         hx.copy_(torch.from_numpy(st.get()["X"]))
     lib = S.lib()
@@ -369,16 +372,21 @@ def e2e_rate(S, torch, states, gen, K):
     t0 = time.perf_counter()
     for g in range(gen, gen + K):
         for st, hx, hf in zip(states, hostX, hostF):
-            S.check(lib.sevo_state_set(st.h, C.cast(C.c_void_p(hx.data_ptr()), dp), None, None, 0,
-                                       None, None, None, -1), "sevo_state_set")
+            S.check(lib.sevo_state_set_async(st.h, C.cast(C.c_void_p(hx.data_ptr()), dp), None,
+                                             None, 0, None, None, None, -1), "sevo_state_set_async")
             S.check(st.step(g), "step")
-            S.check(lib.sevo_state_get(st.h, None, hf.ctypes.data_as(dp), None, None, None, None,
-                                       None, None, None, None), "sevo_state_get")
+            S.check(lib.sevo_state_get_async(st.h, None, C.cast(C.c_void_p(hf.data_ptr()), dp),
+                                             None, None, None, None, None, None),
+                    "sevo_state_get_async")
+        for st in states:
+            st.torch_stream.synchronize()
     dt = (time.perf_counter() - t0) / K
     evals = sum(rows)
     return {"value": round(evals / dt, 1), "unit": "evals/s",
             "h2d_bytes_per_step": sum(r * D * 8 for r in rows),
-            "d2h_bytes_per_step": sum(r * 8 for r in rows)}, gen + K
+            "d2h_bytes_per_step": sum(r * 8 for r in rows),
+            "path": "sevo_state_set_async (pinned X in) + step + sevo_state_get_async (pinned "
+                    "fitness out) per state on its own stream, host waits for every step"}, gen + K
 
 
 # ---------------------------------------------------------------- grid

@@ -257,6 +257,18 @@ int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A, in
 int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx, const double* A,
                        int32_t asize, const double* V, const double* P, const double* fp,
                        int64_t fes);
+/* The same two transfers without waiting: enqueued on the state's stream
+ * (after any work already there) and returning at once.  The caller owns the
+ * host arrays until the stream has passed this point (set: unchanged; get:
+ * not yet valid) -- synchronize the stream (or an event recorded after the
+ * call) first.  Page-locked (pinned) host arrays let the copies overlap other
+ * work; pageable ones are staged.  sevo_state_get_async has no asize or part
+ * outputs. */
+int32_t sevo_state_set_async(sevo_state* s, const double* X, const double* fx, const double* A,
+                             int32_t asize, const double* V, const double* P, const double* fp,
+                             int64_t fes);
+int32_t sevo_state_get_async(const sevo_state* s, double* X, double* fx, double* A, double* V,
+                             double* P, double* fp, double* U, double* fu);
 /* Serialize the whole state (arrays + counters) into buf; *size in: buffer
  * capacity, out: bytes needed/written.  buf == NULL queries the size.
  * Because every draw is counter-based, load + the same counters resumes the

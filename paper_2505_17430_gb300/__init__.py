@@ -90,6 +90,9 @@ SIGNATURES = {
     "sevo_state_result": (C.c_int32, [_vp, _dp, _i64p, _i64p, _i64p]),
     "sevo_state_get": (C.c_int32, [_vp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _ip]),
     "sevo_state_set": (C.c_int32, [_vp, _dp, _dp, _dp, C.c_int32, _dp, _dp, _dp, C.c_int64]),
+    "sevo_state_set_async": (C.c_int32, [_vp, _dp, _dp, _dp, C.c_int32, _dp, _dp, _dp,
+                                         C.c_int64]),
+    "sevo_state_get_async": (C.c_int32, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
     "sevo_state_save": (C.c_int32, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "sevo_state_load": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "sevo_run_grid": (C.c_int32, [C.POINTER(Grid), C.POINTER(GridResult), _vp]),

@@ -160,13 +160,21 @@ extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t*
 }
 
 // copy a row-major NP x D host matrix to/from the ld-strided device matrix
+// host rows are dense (D doubles); device rows have pitch ld (D rounded up to
+// even): one plain copy when they coincide, a pitched copy otherwise
 static cudaError_t put(double* dst, const double* src, const Batch& b) {
-  return cudaMemcpy2DAsync(dst, (size_t)b.ld * 8, src, (size_t)b.D * 8, (size_t)b.D * 8,
-                           (size_t)b.R * b.NP, cudaMemcpyHostToDevice, b.stream);
+  const size_t rows = (size_t)b.R * b.NP;
+  if (b.ld == b.D)
+    return cudaMemcpyAsync(dst, src, rows * b.D * 8, cudaMemcpyHostToDevice, b.stream);
+  return cudaMemcpy2DAsync(dst, (size_t)b.ld * 8, src, (size_t)b.D * 8, (size_t)b.D * 8, rows,
+                           cudaMemcpyHostToDevice, b.stream);
 }
 static cudaError_t get(double* dst, const double* src, const Batch& b) {
-  return cudaMemcpy2DAsync(dst, (size_t)b.D * 8, src, (size_t)b.ld * 8, (size_t)b.D * 8,
-                           (size_t)b.R * b.NP, cudaMemcpyDeviceToHost, b.stream);
+  const size_t rows = (size_t)b.R * b.NP;
+  if (b.ld == b.D)
+    return cudaMemcpyAsync(dst, src, rows * b.D * 8, cudaMemcpyDeviceToHost, b.stream);
+  return cudaMemcpy2DAsync(dst, (size_t)b.D * 8, src, (size_t)b.ld * 8, (size_t)b.D * 8, rows,
+                           cudaMemcpyDeviceToHost, b.stream);
 }
 
 extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A,
@@ -203,9 +211,9 @@ extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, do
   return SEVO_OK;
 }
 
-extern "C" int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx,
-                                  const double* A, int32_t asize, const double* V,
-                                  const double* P, const double* fp, int64_t fes) {
+static int32_t set_impl(sevo_state* s, const double* X, const double* fx, const double* A,
+                        int32_t asize, const double* V, const double* P, const double* fp,
+                        int64_t fes, bool wait) {
   if (!s) return SEVO_ERR_ARG;
   Batch& b = s->b;
   const size_t vb = (size_t)b.R * b.NP * 8;
@@ -213,6 +221,7 @@ extern "C" int32_t sevo_state_set(sevo_state* s, const double* X, const double* 
   if (X) SV_CUDA(put(b.X, X, b));
   if (fx) SV_CUDA(cudaMemcpyAsync(b.fx, fx, vb, cudaMemcpyHostToDevice, b.stream));
   if (A && b.A) SV_CUDA(put(b.A, A, b));
+  // (a copy from pageable host memory returns once the source has been read)
   if (b.asize && A) SV_CUDA(cudaMemcpyAsync(b.asize, &asize, 4, cudaMemcpyHostToDevice, b.stream));
   if (V && b.V) SV_CUDA(put(b.V, V, b));
   if (P && b.P) SV_CUDA(put(b.P, P, b));
@@ -225,7 +234,36 @@ extern "C" int32_t sevo_state_set(sevo_state* s, const double* X, const double* 
     }
   }
   if (fes >= 0) s->fes = fes;
-  SV_CUDA(cudaStreamSynchronize(b.stream));
+  if (wait) SV_CUDA(cudaStreamSynchronize(b.stream));
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx,
+                                  const double* A, int32_t asize, const double* V,
+                                  const double* P, const double* fp, int64_t fes) {
+  return set_impl(s, X, fx, A, asize, V, P, fp, fes, true);
+}
+
+extern "C" int32_t sevo_state_set_async(sevo_state* s, const double* X, const double* fx,
+                                        const double* A, int32_t asize, const double* V,
+                                        const double* P, const double* fp, int64_t fes) {
+  return set_impl(s, X, fx, A, asize, V, P, fp, fes, false);
+}
+
+extern "C" int32_t sevo_state_get_async(const sevo_state* s, double* X, double* fx, double* A,
+                                        double* V, double* P, double* fp, double* U,
+                                        double* fu) {
+  if (!s) return SEVO_ERR_ARG;
+  const Batch& b = s->b;
+  const size_t vb = (size_t)b.R * b.NP * 8;
+  if (X) SV_CUDA(get(X, b.X, b));
+  if (fx) SV_CUDA(cudaMemcpyAsync(fx, b.fx, vb, cudaMemcpyDeviceToHost, b.stream));
+  if (A && b.A) SV_CUDA(get(A, b.A, b));
+  if (V && b.V) SV_CUDA(get(V, b.V, b));
+  if (P && b.P) SV_CUDA(get(P, b.P, b));
+  if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(fp, b.fp, vb, cudaMemcpyDeviceToHost, b.stream));
+  if (U && b.U) SV_CUDA(get(U, b.U, b));
+  if (fu && b.fu) SV_CUDA(cudaMemcpyAsync(fu, b.fu, vb, cudaMemcpyDeviceToHost, b.stream));
   return SEVO_OK;
 }
 

@@ -388,3 +388,31 @@ def test_policy_arguments(S):
     assert lib.sevo_set_policy(99, 1) == S.ERR_ARG
     assert lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 7) == S.ERR_ARG
     assert lib.sevo_get_policy(99) == -1
+
+
+def test_async_set_get_match_sync(S):
+    """sevo_state_set_async / sevo_state_get_async move the same data as the
+    synchronous calls once the state's stream has passed them."""
+    import ctypes as C
+    import torch
+    D, NP = 24, 32
+    p = S.Problem(41, S.ACKLEY, D)
+    stream = torch.cuda.Stream()
+    st = S.State([p, p], S.alg_params(S.PSO_RING, NP, 10 ** 6), [3, 4], stream=stream)
+    X = torch.from_numpy(O.init_population(99, 2 * NP, D)).pin_memory()
+    fx = torch.empty(2 * NP, dtype=torch.float64).pin_memory()
+    V = torch.empty((2 * NP, D), dtype=torch.float64).pin_memory()
+    dp = C.POINTER(C.c_double)
+    ptr = lambda t: C.cast(C.c_void_p(t.data_ptr()), dp)  # noqa: E731
+    lib = S.lib()
+    assert lib.sevo_state_set_async(st.h, ptr(X), None, None, 0, None, None, None, -1) == 0
+    assert st.step(1) == 0
+    assert lib.sevo_state_get_async(st.h, None, ptr(fx), None, ptr(V), None, None, None, None) == 0
+    stream.synchronize()
+    g = st.get()
+    assert np.array_equal(fx.numpy(), g["fx"]) and np.array_equal(V.numpy(), g["V"])
+    ref = S.State([p, p], S.alg_params(S.PSO_RING, NP, 10 ** 6), [3, 4])
+    ref.set(X=X.numpy())
+    assert ref.step(1) == 0
+    r = ref.get()
+    assert np.array_equal(r["fx"], g["fx"]) and np.array_equal(r["X"], g["X"])
