@@ -25,11 +25,18 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128;
-constexpr int NBUF = 4;              // TMEM accumulators of BN columns (512 in all)
+constexpr int BM = 128;
 constexpr int WPQ = 4;               // epilogue warps per TMEM lane quarter
 constexpr int NEPI = 4 * WPQ;
-constexpr int SUB = BN / WPQ;        // columns per epilogue warp and per record
+constexpr int SUB_MIN = 128 / WPQ;   // narrowest record slice (N tile 128): sizes the scratch
+constexpr int MAX_NBUF = 4;
+// N tile of one job (128 or 256 columns of z): NBUF TMEM accumulators of BN
+// columns fill the 512-column TMEM; an epilogue warp walks SUB columns; the
+// B operand of a stage is NB boxes of 128 rotation rows
+template <int BN>
+struct Tile {
+  static constexpr int NBUF = 512 / BN, SUB = BN / WPQ, NB = BN / 128;
+};
 constexpr int WARP_TMA = NEPI, WARP_MMA = NEPI + 1;
 constexpr int NTHREADS = (NEPI + 2) * 32;
 constexpr int KB_BYTES = 128 * 128;  // one 128-row x 128-byte K block (A or B)
@@ -43,7 +50,7 @@ struct BigGeom {
 };
 
 struct __align__(8) BigBars {
-  uint64_t full[4], empty[4], t_full[NBUF], t_empty[NBUF];
+  uint64_t full[4], empty[4], t_full[MAX_NBUF], t_empty[MAX_NBUF];
   uint32_t tmem_base;
   int abort;
 };
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(CVT_WARPS * 32)
 }
 
 // ---------------------------------------------------------------- gemm
-template <bool BF16>
+template <bool BF16, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_big_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
                     const ProblemDev* __restrict__ P, const BigGeom geo, int c, bool comp,
@@ -136,6 +143,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = geo.stages;
+  constexpr int NBUF = Tile<BN>::NBUF, SUB = Tile<BN>::SUB, NB = Tile<BN>::NB;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&bars.full[s], 1);
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc::fence_mbar_init();
   }
   if (warp == WARP_MMA) {
-    tc::tmem_alloc(&bars.tmem_base, NBUF * BN);
+    tc::tmem_alloc(&bars.tmem_base, 512);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -177,11 +185,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           unsigned char* st = base + (size_t)s * geo.stage_bytes;
           tc::mbar_arrive_expect_tx(&bars.full[s], (uint32_t)geo.stage_bytes);
+          // stage: [A][B x NB] (+ [A_lo][B_lo x NB] for BF16); B boxes past
+          // the padded rotation read zeros
           tc::tma_load_2d(st, &mapA, &bars.full[s], kb * KBLK, tile * BM);
-          tc::tma_load_2d(st + KB_BYTES, mB, &bars.full[s], kb * KBLK, nb * BN);
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            tc::tma_load_2d(st + (1 + q) * KB_BYTES, mB, &bars.full[s], kb * KBLK, nb * BN + q * 128);
           if (BF16) {
-            tc::tma_load_2d(st + 2 * KB_BYTES, &mapAlo, &bars.full[s], kb * KBLK, tile * BM);
-            tc::tma_load_2d(st + 3 * KB_BYTES, mBlo, &bars.full[s], kb * KBLK, nb * BN);
+            tc::tma_load_2d(st + (1 + NB) * KB_BYTES, &mapAlo, &bars.full[s], kb * KBLK, tile * BM);
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+              tc::tma_load_2d(st + (2 + NB + q) * KB_BYTES, mBlo, &bars.full[s], kb * KBLK,
+                              nb * BN + q * 128);
           }
         }
       }
@@ -216,7 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int ks = 0; ks < 4; ++ks) {
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (BF16) {
-              const uint32_t aLo = aS + 2 * KB_BYTES, bLo = aS + 3 * KB_BYTES;
+              const uint32_t aLo = aS + (1 + NB) * KB_BYTES, bLo = aS + (2 + NB) * KB_BYTES;
               tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bS + ks * 32),
                           geo.idesc, acc);
               tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bLo + ks * 32),
@@ -284,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int k = 0; k < 1000; ++k) __nanosleep(1000);
     }
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, NBUF * BN);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -306,7 +321,7 @@ __device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, i
 constexpr int CMB_WARPS = 4;
 
 __global__ void __launch_bounds__(CMB_WARPS * 32)
-    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub,
+    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub, int SUB,
                    const float* __restrict__ part, int64_t row0, int64_t N,
                    double* __restrict__ out, double* __restrict__ comp_g, ListOutB lo) {
   const ProblemDev& P = *Pp;
@@ -434,7 +449,7 @@ size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
   (void)prec;
   const int kpad = (D + 63) / 64 * 64;
-  const int nsub = ((D + 127) / 128 * 128) / SUB;
+  const int nsub = ((D + 127) / 128 * 128) / SUB_MIN;
   size_t b = al256b((size_t)rows * kpad * 4) + al256b((size_t)rows * nsub * REC * 4);
   if (any_comp) b += al256b((size_t)rows * SV_MAXC * 16);
   return b;
@@ -450,19 +465,28 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   if (N <= 0) return cudaSuccess;
   const bool bf16 = (prec == SEVO_BF16X3);
   const bool comp = (p->family == SEVO_COMPOSITION);
-  if (h.npad % BN != 0 || p->tmap_rows != BN) return cudaErrorNotSupported;
+  if (h.npad % 128 != 0 || p->tmap_rows != 128) return cudaErrorNotSupported;
   if (!scratch || scratch_bytes < sv_eval_big_scratch_bytes(h.D, comp, prec, N))
     return cudaErrorInvalidValue;
   BigGeom g;
   g.D = h.D;
   g.kpad = h.kpad;
   g.nkb = h.kpad / (bf16 ? 64 : 32);
-  g.nchunks = h.npad / BN;
-  g.nsub = h.npad / SUB;
+  // N tile: 256 columns (3/4 of the operand bytes per flop of a 128-column
+  // tile) when the jobs still fill every SM -- once for TF32 (4 stages of 48
+  // KB), twice for BF16X3, whose 96 KB stages leave room for only two and
+  // whose last partial wave then costs more (measured at D = 5000 x 1,024
+  // rows: 172 us with 256-column tiles, 153 us with 128)
+  const int64_t tiles = (N + BM - 1) / BM;
+  const int64_t jobs256 = tiles * ((h.npad + 255) / 256);
+  const int BN = (jobs256 >= (int64_t)sv_num_sms() * (bf16 ? 2 : 1)) ? 256 : 128;
+  const int NB = BN / 128;
+  g.nchunks = (h.npad + BN - 1) / BN;
+  g.nsub = g.nchunks * WPQ;
   g.ntiles = (int)((N + BM - 1) / BM);
   g.N = N;
-  g.stage_bytes = (bf16 ? 4 : 2) * KB_BYTES;
-  g.stages = bf16 ? 3 : 4;
+  g.stage_bytes = (bf16 ? 2 : 1) * (1 + NB) * KB_BYTES;
+  g.stages = bf16 ? (BN == 256 ? 2 : 3) : 4;  // at most 192 KB of stages
   g.idesc = tc::idesc_make(bf16 ? 1 : 2, BM, BN);
   // scratch: A (N x kpad fp32, or hi then lo bf16), chunk records, composition
   char* cp = (char*)scratch;
@@ -491,16 +515,16 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     mAlo = mA;
   }
   const size_t smem = (size_t)g.stages * g.stage_bytes + 1024;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[bf16]) {
-    cudaError_t e = bf16 ? cudaFuncSetAttribute(gemm_big_kernel<true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)(200 * 1024))
-                         : cudaFuncSetAttribute(gemm_big_kernel<false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)(200 * 1024));
+  static bool attr_done = false;
+  if (!attr_done) {
+    const int lim = 200 * 1024;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(gemm_big_kernel<true, 128>, a, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<true, 256>, a, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 128>, a, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 256>, a, lim);
     if (e != cudaSuccess) return e;
-    attr_done[bf16] = true;
+    attr_done = true;
   }
   const int cvt_grid =
       (int)std::min<int64_t>((N + CVT_WARPS - 1) / CVT_WARPS, (int64_t)sv_num_sms() * 8);
@@ -525,17 +549,23 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tk = sv_trace_begin(SEVO_TK_GEMM_BIG, st);
-    if (bf16)
-      gemm_big_kernel<true><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
-                                                           dev_err);
+    if (bf16 && BN == 256)
+      gemm_big_kernel<true, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
+                                                                part, dev_err);
+    else if (bf16)
+      gemm_big_kernel<true, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
+                                                                part, dev_err);
+    else if (BN == 256)
+      gemm_big_kernel<false, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
+                                                                 part, dev_err);
     else
-      gemm_big_kernel<false><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp, part,
-                                                            dev_err);
+      gemm_big_kernel<false, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
+                                                                 part, dev_err);
     sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tk = sv_trace_begin(SEVO_TK_COMBINE, st);
-    combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, part,
-                                                     seg.row0, N, out, comp_g, lo);
+    combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, BN / WPQ,
+                                                     part, seg.row0, N, out, comp_g, lo);
     sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -217,3 +217,29 @@ def test_tensor_core_d5000_sampled(S):
     want, scale = q.eval(X), q.scale(X)
     assert (np.abs(got - want) <= MIXED_TOL["TF32"] * np.maximum(want, scale) + 1e-13).all()
     assert got[-1] == 0.0
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("D,N", [(300, 10200), (1000, 4990)])
+def test_tensor_core_large_d_wide_tiles_sampled(S, prec, fam, D, N):
+    """Enough rows that the large-D GEMM uses 256-column N tiles (two TMEM
+    accumulators, 64-column epilogue slices; at D = 300 the second tile is
+    half past the padded rotation): sampled rows, the near-optimum probes and
+    the ragged last row tile checked against the oracle."""
+    seed = 901 + 11 * fam + D
+    p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
+    X = inputs.uniform_pop(N, D, seed=seed)
+    probes = np.vstack([inputs.mixed_scales(q.shift(0), 20, D, seed), _inputs(q, 0, D, seed)])
+    X[N - len(probes):] = probes
+    got = p.evaluate(to_dev(X), prec=getattr(S, prec)).cpu().numpy()
+    rows = np.random.default_rng(seed).choice(N - 128, 160, replace=False)
+    rows = np.concatenate([rows, np.arange(N - 128, N)])
+    want, scale = q.eval(X[rows]), q.scale(X[rows])
+    bound = MIXED_TOL[prec] * np.maximum(np.abs(want), scale) + 1e-13
+    err = np.abs(got[rows] - want)
+    assert (err <= bound).all(), (np.max(err / bound), int(rows[np.argmax(err / bound)]))
+    sure = want + bound < 1e-4
+    assert (err[sure] <= tol64(want, scale)[sure]).all()
+    assert got[-1] == 0.0
+    assert np.isfinite(got).all()
