@@ -86,6 +86,12 @@ def lib():
                                               C.c_double, C.c_double, dp, ip]),
                 "orc_de_select": (C.c_int, [C.c_uint64, C.c_uint64, dp, dp, dp, dp, C.c_int,
                                             C.c_int, dp, ip, u8p]),
+                "orc_shade_params": (None, [C.c_uint64, C.c_uint64, C.c_int, C.c_int, dp, dp,
+                                            dp, dp, ip]),
+                "orc_shade_kmax": (C.c_int, [C.c_int]),
+                "orc_shade_trials": (None, [C.c_uint64, C.c_uint64, dp, dp, C.c_int, C.c_int,
+                                            dp, dp, ip, C.c_double, C.c_double, dp, ip]),
+                "orc_shade_update": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, ip]),
                 "orc_pso_guides": (None, [dp, C.c_int, C.c_int, ip]),
                 "orc_pso_move": (None, [C.c_uint64, C.c_uint64, dp, dp, dp, ip, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
@@ -251,6 +257,48 @@ def de_ctpb_trials(seed, gen, X, fx, A, asize, F=0.5, CR=0.9, p=0.11, lb=-100.0,
     return U, part
 
 
+SHADE_H = 100
+
+
+def shade_memory():
+    """Initial SHADE memory: (M_F, M_CR, k) with every slot 0.5."""
+    return np.full(SHADE_H, 0.5), np.full(SHADE_H, 0.5), 0
+
+
+def shade_params(seed, gen, NP, MF, MCR):
+    """Per-individual (F, CR, pbest pool size) drawn from the memory."""
+    F, CR = np.zeros(NP), np.zeros(NP)
+    kpb = np.zeros(NP, np.int32)
+    MF, MCR = f64(MF), f64(MCR)
+    lib().orc_shade_params(seed, gen, NP, len(MF), _dp(MF), _dp(MCR), _dp(F), _dp(CR), _ip(kpb))
+    return F, CR, kpb
+
+
+def shade_kmax(NP):
+    return lib().orc_shade_kmax(NP)
+
+
+def shade_trials(seed, gen, X, fx, F, CR, kpb, lb=-100.0, ub=100.0):
+    X, fx, F, CR = f64(X), f64(fx), f64(F), f64(CR)
+    kpb = np.ascontiguousarray(kpb, np.int32)
+    NP, D = X.shape
+    U = np.zeros_like(X)
+    part = np.zeros((NP, 4), np.int32)
+    lib().orc_shade_trials(seed, gen, _dp(X), _dp(fx), NP, D, _dp(F), _dp(CR), _ip(kpb), lb, ub,
+                           _dp(U), _ip(part))
+    return U, part
+
+
+def shade_update(fx, fu, F, CR, MF, MCR, k):
+    """Memory after one generation: returns (M_F', M_CR', k', improvements)."""
+    fx, fu, F, CR = f64(fx), f64(fu), f64(F), f64(CR)
+    MF, MCR = f64(MF).copy(), f64(MCR).copy()
+    kk = C.c_int(k)
+    n = lib().orc_shade_update(len(fx), len(MF), _dp(fx), _dp(fu), _dp(F), _dp(CR), _dp(MF),
+                               _dp(MCR), C.byref(kk))
+    return MF, MCR, kk.value, n
+
+
 def de_select(seed, gen, X, fx, U, fu, A=None, asize=0):
     """Returns (X', fx', A', asize', accepted flags); inputs are not modified."""
     X, fx, U, fu = f64(X).copy(), f64(fx).copy(), f64(U), f64(fu)
@@ -292,7 +340,7 @@ def pso_update(X, fx, P, fp):
     return P, fp, n
 
 
-ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING = 0, 1, 2, 3
+ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING, ALG_DE_SHADE = 0, 1, 2, 3, 4
 
 
 def make_alg(alg, NP, budget, F=0.5, CR=0.9, p=0.11, w=0.7298, c1=1.49618, c2=1.49618,

@@ -752,6 +752,101 @@ void orc_de_ctpb_trials(uint64_t seed, uint64_t gen, const double* X,
   free(order);
 }
 
+/* ---------------------------------------------------------------- SHADE */
+void orc_shade_params(uint64_t seed, uint64_t gen, int NP, int H, const double* MF,
+                      const double* MCR, double* F, double* CR, int32_t* kpb) {
+  uint32_t w[4];
+  const double pmin = 2.0 / (double)NP;
+  for (int i = 0; i < NP; ++i) {
+    draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_SHADE, 0, w);
+    const int r = (int)orc_below(w[0], (uint32_t)H);
+    const double p = pmin + (0.2 - pmin) * orc_u53(w[1], w[2]);
+    int k = (int)floor(p * (double)NP + 0.5);
+    if (k < 1) k = 1;
+    if (k > NP) k = NP;
+    kpb[i] = k;
+    draw(seed, 1, (uint32_t)i, (uint32_t)gen, ORC_P_SHADE, 0, w);
+    const double u1 = orc_u53(w[0], w[1]), u2 = orc_u53(w[2], w[3]);
+    double cr = MCR[r] + 0.1 * (sqrt(-2.0 * log(1.0 - u1)) * cos(2.0 * ORC_PI * u2));
+    if (cr < 0.0) cr = 0.0;
+    if (cr > 1.0) cr = 1.0;
+    CR[i] = cr;
+    double f = MF[r];
+    for (int t = 0; t < 64; ++t) {
+      draw(seed, (uint32_t)(2 + t), (uint32_t)i, (uint32_t)gen, ORC_P_SHADE, 0, w);
+      const double c = MF[r] + 0.1 * tan(ORC_PI * (orc_u53(w[0], w[1]) - 0.5));
+      if (c > 0.0) {
+        f = c;
+        break;
+      }
+    }
+    F[i] = f > 1.0 ? 1.0 : f;
+  }
+}
+
+int orc_shade_kmax(int NP) {
+  const double p = (2.0 / (double)NP > 0.2) ? 2.0 / (double)NP : 0.2;
+  int k = (int)floor(p * (double)NP + 0.5);
+  if (k < 1) k = 1;
+  if (k > NP) k = NP;
+  return k;
+}
+
+void orc_shade_trials(uint64_t seed, uint64_t gen, const double* X, const double* fx,
+                      int NP, int D, const double* F, const double* CR,
+                      const int32_t* kpb, double lb, double ub, double* U, int32_t* part) {
+  uint32_t w[4];
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * NP);
+  orc_rank(fx, NP, order);
+  double* v = (double*)malloc(sizeof(double) * D);
+  for (int i = 0; i < NP; ++i) {
+    draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_PART, 0, w);
+    const int pb = order[orc_below(w[0], (uint32_t)kpb[i])];
+    int ex[2] = {i, 0};
+    const int r1 = skip_sorted((int)orc_below(w[1], (uint32_t)(NP - 1)), ex, 1);
+    ex[1] = r1;
+    sort_small(ex, 2);
+    const int r2 = skip_sorted((int)orc_below(w[2], (uint32_t)(NP - 2)), ex, 2);
+    const int jr = (int)orc_below(w[3], (uint32_t)D);
+    const double* xi = X + (size_t)i * D;
+    const double* xp = X + (size_t)pb * D;
+    const double* x1 = X + (size_t)r1 * D;
+    const double* x2 = X + (size_t)r2 * D;
+    for (int j = 0; j < D; ++j)
+      v[j] = fma(F[i], x1[j] - x2[j], fma(F[i], xp[j] - xi[j], xi[j]));
+    cross_repair(seed, gen, i, D, CR[i], jr, v, xi, lb, ub, U + (size_t)i * D);
+    if (part) {
+      part[4 * i + 0] = pb;
+      part[4 * i + 1] = r1;
+      part[4 * i + 2] = r2;
+      part[4 * i + 3] = jr;
+    }
+  }
+  free(v);
+  free(order);
+}
+
+int orc_shade_update(int NP, int H, const double* fx, const double* fu, const double* F,
+                     const double* CR, double* MF, double* MCR, int* k) {
+  double sw = 0.0, swf = 0.0, swf2 = 0.0, swcr = 0.0;
+  int n = 0;
+  for (int i = 0; i < NP; ++i) {
+    if (!(fu[i] < fx[i])) continue;
+    const double d = fx[i] - fu[i];
+    sw += d;
+    swf += d * F[i];
+    swf2 += d * F[i] * F[i];
+    swcr += d * CR[i];
+    ++n;
+  }
+  if (n > 0 && sw > 0.0 && swf > 0.0) {
+    MF[*k] = swf2 / swf;
+    MCR[*k] = swcr / sw;
+    *k = (*k + 1) % H;
+  }
+  return n;
+}
+
 int orc_de_select(uint64_t seed, uint64_t gen, double* X, double* fx,
                   const double* U, const double* fu, int NP, int D, double* A,
                   int* asize, uint8_t* acc) {
@@ -876,7 +971,17 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
   }
   int64_t gen = 0;
   if (a->alg == 1) A = (double*)malloc(sizeof(double) * n);
-  if (a->alg >= 2) {
+  double MF[ORC_SHADE_H], MCR[ORC_SHADE_H];
+  int mk = 0;
+  double *Fi = NULL, *CRi = NULL;
+  int32_t* kpb = NULL;
+  if (a->alg == 4) {
+    for (int h = 0; h < ORC_SHADE_H; ++h) MF[h] = MCR[h] = 0.5;
+    Fi = (double*)malloc(sizeof(double) * NP);
+    CRi = (double*)malloc(sizeof(double) * NP);
+    kpb = (int32_t*)malloc(sizeof(int32_t) * NP);
+  }
+  if (a->alg == 2 || a->alg == 3) {
     V = (double*)calloc(n, sizeof(double));
     P = (double*)malloc(sizeof(double) * n);
     fp = (double*)malloc(sizeof(double) * NP);
@@ -889,7 +994,15 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
     ++gen;
     cnt = a->budget - fes;
     if (cnt > NP) cnt = NP;
-    if (a->alg <= 1) {
+    if (a->alg == 4) {
+      orc_shade_params(seed, (uint64_t)gen, NP, ORC_SHADE_H, MF, MCR, Fi, CRi, kpb);
+      orc_shade_trials(seed, (uint64_t)gen, X, fx, NP, D, Fi, CRi, kpb, a->lb, a->ub, U, NULL);
+      for (int i = 0; i < NP; ++i) fu[i] = orc_eval(p, U + (size_t)i * D);
+      double b = min_first(fu, (int)cnt);
+      if (b < best) best = b;
+      orc_shade_update(NP, ORC_SHADE_H, fx, fu, Fi, CRi, MF, MCR, &mk);
+      orc_de_select(seed, (uint64_t)gen, X, fx, U, fu, NP, D, NULL, NULL, NULL);
+    } else if (a->alg <= 1) {
       if (a->alg == 0)
         orc_de_rand1_trials(seed, (uint64_t)gen, X, NP, D, a->F, a->CR, a->lb, a->ub, U, NULL);
       else
@@ -928,6 +1041,9 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
   free(V);
   free(P);
   free(fp);
+  free(Fi);
+  free(CRi);
+  free(kpb);
   free(guide);
 }
 

@@ -47,6 +47,7 @@ enum {
 /* ---- Philox purposes (high byte of counter word 3) */
 enum {
   ORC_P_INIT = 1, ORC_P_PART = 2, ORC_P_CROSS = 3, ORC_P_ARCH = 4, ORC_P_PSO = 5,
+  ORC_P_SHADE = 6,
   ORC_P_SHIFT = 16, ORC_P_ROT = 17, ORC_P_PERM = 18, ORC_P_HYB = 19, ORC_P_COMP = 20
 };
 
@@ -109,6 +110,34 @@ void orc_de_ctpb_trials(uint64_t seed, uint64_t gen, const double* X,
 int orc_de_select(uint64_t seed, uint64_t gen, double* X, double* fx,
                   const double* U, const double* fu, int NP, int D, double* A,
                   int* asize, uint8_t* acc);
+/* ---- SHADE (Sec. 2.2, Listing 1: shade_parameter with current-to-pbest/1,
+ * binomial crossover, midpoint repair, no external archive; success-history
+ * adaptation as in the SHADE reference [14] of the paper).  Memory of H slots
+ * (M_F, M_CR), initialised to 0.5, write position k. */
+#define ORC_SHADE_H 100
+/* per individual i (Philox purpose SHADE, counter (sub, i, gen)):
+ *   sub 0: r = below(w0, H); p = pmin + (0.2 - pmin) u53(w1, w2), pmin = 2/NP;
+ *          pool k_i = floor(p NP + 1/2) clamped to [1, NP] (the top p NP
+ *          members, rounded: 2 .. 0.2 NP)
+ *   sub 1: CR = M_CR[r] + 0.1 sqrt(-2 ln(1 - u53(w0,w1))) cos(2 pi u53(w2,w3)),
+ *          clipped to [0, 1]
+ *   sub 2 + t, t < 64: F = M_F[r] + 0.1 tan(pi (u53(w0,w1) - 0.5)) until F > 0
+ *          (all 64 failing: F = M_F[r]); F > 1 -> 1 */
+void orc_shade_params(uint64_t seed, uint64_t gen, int NP, int H, const double* MF,
+                      const double* MCR, double* F, double* CR, int32_t* kpb);
+/* largest pool any individual can draw: floor(max(0.2, 2/NP) NP + 1/2) */
+int orc_shade_kmax(int NP);
+/* current-to-pbest/1/bin without archive with per-individual F, CR, pool */
+void orc_shade_trials(uint64_t seed, uint64_t gen, const double* X, const double* fx,
+                      int NP, int D, const double* F, const double* CR,
+                      const int32_t* kpb, double lb, double ub, double* U, int32_t* part);
+/* memory update from the strict improvements fu < fx (fx before selection),
+ * weights proportional to fx - fu: M_F[k] = sum w F^2 / sum w F (Lehmer),
+ * M_CR[k] = sum w CR / sum w; k = (k + 1) mod H; nothing if no improvement.
+ * Sums in row order.  Returns the number of improvements. */
+int orc_shade_update(int NP, int H, const double* fx, const double* fu, const double* F,
+                     const double* CR, double* MF, double* MCR, int* k);
+
 /* PSO guide index per particle from pbest fitness: topology 0 = global,
  * 1 = ring {i-1,i,i+1} */
 void orc_pso_guides(const double* fp, int NP, int topology, int32_t* guide);
@@ -122,7 +151,8 @@ int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
 
 /* ---- whole runs ------------------------------------------------------- */
 typedef struct {
-  int alg;          /* 0 DE rand/1/bin, 1 DE ctpb/1/bin+archive, 2 PSO gbest, 3 PSO ring */
+  int alg;          /* 0 DE rand/1/bin, 1 DE ctpb/1/bin+archive, 2 PSO gbest, 3 PSO ring,
+                       4 SHADE (F, CR, p unused) */
   int NP;
   double F, CR, p;  /* DE */
   double w, c1, c2; /* PSO */

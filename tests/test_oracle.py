@@ -474,3 +474,96 @@ def test_run_many_equals_run():
     for pr, al, sd, m in zip(probs, algs, seeds, many):
         one = O.run(pr, al, sd)
         assert one["best"] == m["best"] and one["fes"] == m["fes"]
+
+
+# ---------------------------------------------------------------- SHADE
+def _shade_samples(MF, MCR, NP=50, gens=200, seed=3):
+    F, CR, K = [], [], []
+    for g in range(1, gens + 1):
+        f, c, k = O.shade_params(seed, g, NP, MF, MCR)
+        F.append(f)
+        CR.append(c)
+        K.append(k)
+    return np.concatenate(F), np.concatenate(CR), np.concatenate(K)
+
+
+@pytest.mark.parametrize("loc", [0.3, 0.5, 0.7])
+def test_shade_F_is_cauchy_resampled_positive_and_capped(loc):
+    """F ~ Cauchy(M_F, 0.1) redrawn until > 0, capped at 1: the empirical
+    median and the mass at F = 1 match the closed forms of that conditional
+    Cauchy law (CDF G(x) = 1/2 + atan((x - loc)/0.1)/pi)."""
+    H = O.SHADE_H
+    F, _, _ = _shade_samples(np.full(H, loc), np.full(H, 0.5))
+    assert (F > 0).all() and (F <= 1).all()
+    G = lambda x: 0.5 + np.arctan((x - loc) / 0.1) / np.pi  # noqa: E731
+    g0 = G(0.0)
+    med = loc + 0.1 * np.tan(np.pi * (g0 + 0.5 * (1 - g0) - 0.5))
+    assert abs(np.median(F) - med) < 0.006, (np.median(F), med)
+    p_one = (1 - G(1.0)) / (1 - g0)
+    assert abs(np.mean(F == 1.0) - p_one) < 0.01, (np.mean(F == 1.0), p_one)
+
+
+def test_shade_CR_is_clipped_normal():
+    """CR ~ N(M_CR, 0.1) clipped to [0, 1]: mean and spread at 0.5, and the
+    mass at 1 for M_CR = 0.95 equals 1 - Phi(0.5)."""
+    H = O.SHADE_H
+    _, CR, _ = _shade_samples(np.full(H, 0.5), np.full(H, 0.5))
+    assert abs(CR.mean() - 0.5) < 0.005 and abs(CR.std() - 0.1) < 0.005
+    _, CR, _ = _shade_samples(np.full(H, 0.5), np.full(H, 0.95))
+    from math import erf, sqrt
+    p1 = 1 - 0.5 * (1 + erf(0.5 / sqrt(2)))
+    assert abs(np.mean(CR == 1.0) - p1) < 0.015 and (CR >= 0).all() and (CR <= 1).all()
+
+
+def test_shade_memory_slot_uniform_and_pool_range():
+    """The memory slot is uniform over the H slots (mean of CR over slots
+    holding M_CR[h] = h / H), and the pbest pool k = ceil(p NP) with
+    p ~ U[2/NP, 0.2] spans 2 .. ceil(0.2 NP)."""
+    H = O.SHADE_H
+    _, CR, K = _shade_samples(np.full(H, 0.5), np.arange(H) / H, NP=100, gens=300)
+    assert abs(CR.mean() - np.mean(np.clip(np.arange(H) / H, 0, 1))) < 0.01
+    assert K.min() == 2 and K.max() == 20 and O.shade_kmax(100) == 20
+    assert O.shade_kmax(8) == 2  # 2/NP > 0.2 for NP < 10
+
+
+def test_shade_memory_update_closed_form():
+    """Weights proportional to the improvement fx - fu over strict
+    improvements: M_F[k] = sum w F^2 / sum w F, M_CR[k] = sum w CR / sum w,
+    then k advances (mod H); ties and non-improvements are ignored."""
+    H = O.SHADE_H
+    MF, MCR, k = O.shade_memory()
+    fx = np.array([10.0, 10.0, 10.0, 5.0, 7.0, 3.0])
+    fu = np.array([9.0, 8.0, 7.0, 5.0, 8.0, 3.0])  # improvements 1, 2, 3; a tie; worse; a tie
+    F = np.array([0.5, 0.6, 0.7, 0.9, 0.9, 0.9])
+    CR = np.array([0.1, 0.2, 0.3, 0.9, 0.9, 0.9])
+    MF2, MCR2, k2, n = O.shade_update(fx, fu, F, CR, MF, MCR, 7 % H)
+    assert n == 3 and k2 == 8
+    assert MF2[7] == pytest.approx((0.25 + 2 * 0.36 + 3 * 0.49) / (0.5 + 2 * 0.6 + 3 * 0.7), rel=1e-15)
+    assert MCR2[7] == pytest.approx((0.1 + 2 * 0.2 + 3 * 0.3) / 6, rel=1e-15)
+    assert np.array_equal(np.delete(MF2, 7), np.delete(MF, 7))
+    MF3, MCR3, k3, n = O.shade_update(fx, fx, F, CR, MF2, MCR2, H - 1)  # no improvement
+    assert n == 0 and k3 == H - 1 and np.array_equal(MF3, MF2)
+    _, _, k4, _ = O.shade_update(fx, fu, F, CR, MF2, MCR2, H - 1)  # wraps
+    assert k4 == 0
+
+
+def test_shade_trials_reduce_to_current_to_pbest_without_archive():
+    """With F, CR and the pool size equal for every individual, the SHADE
+    trial is the (pinned) current-to-pbest/1/bin trial with an empty
+    archive."""
+    NP, D = 40, 13
+    X = O.init_population(11, NP, D)
+    fx = O.Problem(5, O.RASTRIGIN, D).eval(X)
+    k = O.pbest_k(0.11, NP)
+    F, CR, kpb = np.full(NP, 0.5), np.full(NP, 0.9), np.full(NP, k, np.int32)
+    U, part = O.shade_trials(11, 4, X, fx, F, CR, kpb)
+    U2, part2 = O.de_ctpb_trials(11, 4, X, fx, np.zeros((1, D)), 0, F=0.5, CR=0.9, p=0.11)
+    assert np.array_equal(U, U2) and np.array_equal(part, part2)
+
+
+def test_shade_control_run_reaches_success():
+    """Control: SHADE on the shifted-rotated ellipsoid (D = 10, NP = 50,
+    6e4 evaluations) reaches the 1e-8 success threshold."""
+    q = O.Problem(3, O.ELLIPSOID, 10)
+    r = O.run(q, O.make_alg(O.ALG_DE_SHADE, 50, 60000), 1)
+    assert r["success"] and r["fes"] == 60000
