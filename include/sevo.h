@@ -181,8 +181,18 @@ enum sevo_alg {
   SEVO_DE_RAND1 = 0,     /* DE/rand/1/bin                                  */
   SEVO_DE_CTPB = 1,      /* DE/current-to-pbest/1/bin + external archive   */
   SEVO_PSO_GBEST = 2,    /* inertia-weight PSO, global topology            */
-  SEVO_PSO_RING = 3      /* inertia-weight PSO, ring {i-1,i,i+1} topology  */
+  SEVO_PSO_RING = 3,     /* inertia-weight PSO, ring {i-1,i,i+1} topology  */
+  /* SHADE (Sec. 2.2, Listing 1's shade_parameter with current-to-pbest/1,
+   * binomial crossover and midpoint repair, no external archive): every
+   * generation each individual draws its own F (Cauchy around a memory slot's
+   * M_F, scale 0.1, redrawn while <= 0, capped at 1), CR (normal around
+   * M_CR, sd 0.1, clipped to [0, 1]) and pbest pool (the top round(p NP),
+   * p ~ U[2/NP, 0.2]); after selection the strict improvements update one
+   * slot (weighted Lehmer mean of F, weighted mean of CR, weights fx - fu).
+   * The F, CR and p fields of sevo_alg_params are not used. */
+  SEVO_DE_SHADE = 4
 };
+#define SEVO_SHADE_H 100   /* success-history memory slots per run */
 
 typedef struct {
   int32_t alg;        /* enum sevo_alg                                   */
@@ -252,6 +262,14 @@ int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes, int64
  * Arrays are NP x D row-major (ld = D). Synchronizes. */
 int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A, int32_t* asize,
                        double* V, double* P, double* fp, double* U, double* fu, int32_t* part);
+/* SHADE runs only (SEVO_ERR_ARG otherwise).  get: the memory (M_F, M_CR: R x
+ * SEVO_SHADE_H, slot-major per run; k: R write positions) and the last
+ * generation's per-row F, CR and pbest pool sizes (R x NP); any pointer may be
+ * NULL; synchronizes.  set: overwrite the memory (NULL = leave as is). */
+int32_t sevo_state_get_shade(const sevo_state* s, double* MF, double* MCR, int32_t* k, double* F,
+                             double* CR, int32_t* kpb);
+int32_t sevo_state_set_shade(sevo_state* s, const double* MF, const double* MCR,
+                             const int32_t* k);
 /* Overwrite the state arrays from host copies (NULL = leave as is); fes is
  * set to `fes` (>= 0) and guides are recomputed for PSO. */
 int32_t sevo_state_set(sevo_state* s, const double* X, const double* fx, const double* A,

@@ -22,7 +22,8 @@ FAMILY_NAMES = ["ellipsoid", "rosenbrock", "rastrigin", "schwefel", "ackley", "g
                 "hybrid", "composition"]
 FP64, TF32, BF16X3, FP32 = 0, 1, 2, 3
 PREC_NAMES = {FP64: "fp64", TF32: "tf32", BF16X3: "bf16x3", FP32: "fp32"}
-DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING = 0, 1, 2, 3
+DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING, DE_SHADE = 0, 1, 2, 3, 4
+SHADE_H = 100
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED, ERR_STATE = range(-1, -8, -1)
 REFINE_THRESHOLD = 1e-4
@@ -85,6 +86,8 @@ SIGNATURES = {
                                       C.POINTER(_vp)]),
     "sevo_state_destroy": (C.c_int32, [_vp]),
     "sevo_state_restart": (C.c_int32, [_vp, C.POINTER(C.c_uint64)]),
+    "sevo_state_get_shade": (C.c_int32, [_vp, _dp, _dp, _ip, _dp, _dp, _ip]),
+    "sevo_state_set_shade": (C.c_int32, [_vp, _dp, _dp, _ip]),
     "sevo_de_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_pso_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_state_result": (C.c_int32, [_vp, _dp, _i64p, _i64p, _i64p]),
@@ -270,6 +273,24 @@ class State:
         if h and _LIB is not None:
             _LIB.sevo_state_destroy(h)
             self.h = None
+
+    def get_shade(self):
+        """SHADE memory and the last generation's per-row parameters."""
+        import numpy as np
+        R, NP = self.R, self.params.NP
+        MF, MCR = np.zeros((R, SHADE_H)), np.zeros((R, SHADE_H))
+        k = np.zeros(R, np.int32)
+        F, CR, kpb = np.zeros(R * NP), np.zeros(R * NP), np.zeros(R * NP, np.int32)
+        check(_lib().sevo_state_get_shade(self.h, _np_dp(MF), _np_dp(MCR), _np_ip(k), _np_dp(F),
+                                          _np_dp(CR), _np_ip(kpb)), "sevo_state_get_shade")
+        return {"MF": MF, "MCR": MCR, "k": k, "F": F, "CR": CR, "kpb": kpb}
+
+    def set_shade(self, MF=None, MCR=None, k=None):
+        import numpy as np
+        c = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        kk = None if k is None else np.ascontiguousarray(np.atleast_1d(k), dtype=np.int32)
+        check(_lib().sevo_state_set_shade(self.h, _np_dp(c(MF)), _np_dp(c(MCR)), _np_ip(kk)),
+              "sevo_state_set_shade")
 
     def restart(self, seeds):
         """Fresh initial populations for every run (seeds: one per run)."""

@@ -184,7 +184,17 @@ __device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, doub
                                               const uint64_t* __restrict__ seeds, int NP, int D,
                                               int ld, double F, unsigned long long cr_thr,
                                               double lb, double ub, int pk,
-                                              unsigned long long gen, int r, int i, int jq) {
+                                              unsigned long long gen, int r, int i, int jq,
+                                              const double* __restrict__ Fi = nullptr,
+                                              const double* __restrict__ CRi = nullptr,
+                                              const int32_t* __restrict__ kpb = nullptr) {
+  // SHADE: this row's F, crossover threshold and pbest pool
+  if (ALG == SEVO_DE_SHADE) {
+    const int64_t row = (int64_t)r * NP + i;
+    F = Fi[row];
+    cr_thr = (unsigned long long)ceil(__dmul_rn(CRi[row], 4294967296.0));
+    pk = kpb[row];
+  }
   const uint64_t seed = seeds[r];
   const uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_PART);
   const double* Xr = X + (int64_t)r * NP * ld;
@@ -220,7 +230,7 @@ __device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, doub
     d2 = Xr + (int64_t)b * ld;
     d3 = Xr + (int64_t)c * ld;
   } else {
-    const int as = asize[r];
+    const int as = (ALG == SEVO_DE_CTPB) ? asize[r] : 0;  // SHADE: no archive
     const int pb = order[(int64_t)r * NP + (int)sv_below(w.x, (uint32_t)pk)];
     int r1 = (int)sv_below(w.y, (uint32_t)(NP - 1));
     if (r1 >= i) ++r1;
@@ -284,7 +294,9 @@ __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict
                                 const int32_t* __restrict__ order, int32_t* __restrict__ part,
                                 const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
                                 int R, int NP, int D, int ld, double F, unsigned long long cr_thr,
-                                double lb, double ub, int pk, FastDiv fq, FastDiv fnp) {
+                                double lb, double ub, int pk, FastDiv fq, FastDiv fnp,
+                                const double* __restrict__ Fi, const double* __restrict__ CRi,
+                                const int32_t* __restrict__ kpb) {
   const int nq = (D + 3) >> 2;
   const int64_t total = (int64_t)R * NP * nq;
   const bool fast = total < (1ll << 31);
@@ -293,7 +305,53 @@ __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fq, fnp);
     de_trial_elem<ALG>(X, U, A, asize, order, part, seeds, NP, D, ld, F, cr_thr, lb, ub, pk, gen,
-                       sp.hi, sp.mid, sp.lo);
+                       sp.hi, sp.mid, sp.lo, Fi, CRi, kpb);
+  }
+}
+
+// ---------------------------------------------------------------- SHADE
+// per row: memory slot, pbest pool, CR (normal, clipped), F (Cauchy, redrawn
+// while <= 0, capped at 1) from the run's memory; the arithmetic is written
+// with explicit roundings (no contraction) in the order of the definition
+constexpr double SV_PI = 3.14159265358979323846;
+
+__global__ void shade_param_kernel(const double* __restrict__ MF, const double* __restrict__ MCR,
+                                   const uint64_t* __restrict__ seeds,
+                                   const GenCtl* __restrict__ ctl, int R, int NP, int H,
+                                   double* __restrict__ Fi, double* __restrict__ CRi,
+                                   int32_t* __restrict__ kpb) {
+  const int64_t rows = (int64_t)R * NP;
+  const unsigned long long gen = ctl->gen;
+  const double pmin = 2.0 / (double)NP;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / NP), i = (int)(t - (int64_t)r * NP);
+    const uint64_t seed = seeds[r];
+    uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_SHADE);
+    const int h = (int)sv_below(w.x, (uint32_t)H);
+    const double p = __dadd_rn(pmin, __dmul_rn(__dsub_rn(0.2, pmin), u53_int(w.y, w.z)));
+    int k = (int)floor(__dadd_rn(__dmul_rn(p, (double)NP), 0.5));
+    k = k < 1 ? 1 : (k > NP ? NP : k);
+    kpb[t] = k;
+    const double mcr = MCR[(int64_t)r * H + h], mf = MF[(int64_t)r * H + h];
+    w = sv_draw(seed, 1u, (uint32_t)i, (uint32_t)gen, SV_P_SHADE);
+    const double u1 = u53_int(w.x, w.y), u2 = u53_int(w.z, w.w);
+    const double z = __dmul_rn(sqrt(__dmul_rn(-2.0, log(__dsub_rn(1.0, u1)))),
+                               cos(__dmul_rn(2.0 * SV_PI, u2)));
+    double cr = __dadd_rn(mcr, __dmul_rn(0.1, z));
+    cr = cr < 0.0 ? 0.0 : (cr > 1.0 ? 1.0 : cr);
+    CRi[t] = cr;
+    double f = mf;
+    for (int a = 0; a < 64; ++a) {
+      w = sv_draw(seed, 2u + (uint32_t)a, (uint32_t)i, (uint32_t)gen, SV_P_SHADE);
+      const double c =
+          __dadd_rn(mf, __dmul_rn(0.1, tan(__dmul_rn(SV_PI, __dsub_rn(u53_int(w.x, w.y), 0.5)))));
+      if (c > 0.0) {
+        f = c;
+        break;
+      }
+    }
+    Fi[t] = f > 1.0 ? 1.0 : f;
   }
 }
 
@@ -488,7 +546,12 @@ __device__ __forceinline__ void de_select_run(double* __restrict__ fx, const dou
                                               double* __restrict__ best,
                                               const uint64_t* __restrict__ seeds, int count,
                                               unsigned long long gen, int NP, int use_archive,
-                                              int r, unsigned char* sel_sm) {
+                                              int r, unsigned char* sel_sm,
+                                              const double* __restrict__ Fi = nullptr,
+                                              const double* __restrict__ CRi = nullptr,
+                                              double* __restrict__ MF = nullptr,
+                                              double* __restrict__ MCR = nullptr,
+                                              int32_t* __restrict__ mk = nullptr, int H = 0) {
   double* sf = reinterpret_cast<double*>(sel_sm);  // current fitness
   double* sg = sf + NP;                             // trial fitness
   int* owner = reinterpret_cast<int*>(sg + NP);     // archive slot -> last row
@@ -529,6 +592,47 @@ __device__ __forceinline__ void de_select_run(double* __restrict__ fx, const dou
   int nacc_total = 0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nacc_total += wsum[w];
   int k = woff + incl - cnt;
+  if (MF) {  // SHADE: the strict improvements update memory slot mk[r]
+    __shared__ double ssum[SEL_THREADS / 32][4];
+    double sw = 0.0, swf = 0.0, swf2 = 0.0, swcr = 0.0;
+    for (int i = i0; i < i1; ++i) {
+      if (!(sg[i] < sf[i])) continue;
+      const int64_t row = (int64_t)r * NP + i;
+      const double d = __dsub_rn(sf[i], sg[i]), F = Fi[row];
+      sw = __dadd_rn(sw, d);
+      swf = __dadd_rn(swf, __dmul_rn(d, F));
+      swf2 = __dadd_rn(swf2, __dmul_rn(__dmul_rn(d, F), F));
+      swcr = __dadd_rn(swcr, __dmul_rn(d, CRi[row]));
+    }
+    for (int o = 16; o >= 1; o >>= 1) {  // fixed-order tree: deterministic sums
+      sw += __shfl_down_sync(0xffffffffu, sw, o);
+      swf += __shfl_down_sync(0xffffffffu, swf, o);
+      swf2 += __shfl_down_sync(0xffffffffu, swf2, o);
+      swcr += __shfl_down_sync(0xffffffffu, swcr, o);
+    }
+    if (lane == 0) {
+      ssum[warp][0] = sw;
+      ssum[warp][1] = swf;
+      ssum[warp][2] = swf2;
+      ssum[warp][3] = swcr;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0, c = 0.0, e = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        a += ssum[q][0];
+        b += ssum[q][1];
+        c += ssum[q][2];
+        e += ssum[q][3];
+      }
+      if (a > 0.0 && b > 0.0) {
+        const int slot = mk[r];
+        MF[(int64_t)r * H + slot] = c / b;
+        MCR[(int64_t)r * H + slot] = e / a;
+        mk[r] = (slot + 1) % H;
+      }
+    }
+  }
   const int as0 = use_archive ? asize[r] : 0;  // rand/1 has no archive (asize null)
   for (int i = i0; i < i1; ++i) {
     int a = -2;
@@ -564,10 +668,13 @@ __global__ void __launch_bounds__(SEL_THREADS)
     de_select_kernel(double* __restrict__ fx, const double* __restrict__ fu,
                      int32_t* __restrict__ asize, int32_t* __restrict__ action,
                      double* __restrict__ best, const uint64_t* __restrict__ seeds,
-                     const GenCtl* __restrict__ ctl, int NP, int use_archive) {
+                     const GenCtl* __restrict__ ctl, int NP, int use_archive,
+                     const double* __restrict__ Fi, const double* __restrict__ CRi,
+                     double* __restrict__ MF, double* __restrict__ MCR, int32_t* __restrict__ mk,
+                     int H) {
   extern __shared__ __align__(16) unsigned char sel_sm[];
   de_select_run(fx, fu, asize, action, best, seeds, ctl->count, ctl->gen, NP, use_archive,
-                blockIdx.x, sel_sm);
+                blockIdx.x, sel_sm, Fi, CRi, MF, MCR, mk, H);
 }
 
 // accepted row ri (run r): archive <- old x (if slot), x <- u; one quad
@@ -1154,7 +1261,12 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->cr_thr = (unsigned long long)t;
   }
   b->pbest_k = sv_pbest_k(a->p, a->NP);
-  b->small = g_policy_small_runs.load() != 0 && b->D <= SRK_MAX_D && b->NP <= SRK_MAX_NP;
+  if (b->alg == SEVO_DE_SHADE) {  // largest pool: round(max(0.2, 2/NP) NP)
+    const double pm = std::max(0.2, 2.0 / (double)a->NP);
+    b->pbest_k = std::min(a->NP, std::max(1, (int)std::floor(pm * (double)a->NP + 0.5)));
+  }
+  b->small = g_policy_small_runs.load() != 0 && b->D <= SRK_MAX_D && b->NP <= SRK_MAX_NP &&
+             b->alg != SEVO_DE_SHADE;
   b->run_prob = probs;
   b->seg_begin.clear();
   for (int r = 0; r < b->R; ++r)
@@ -1163,14 +1275,17 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   const int64_t rows = (int64_t)b->R * b->NP;
   const size_t mat = al256((size_t)rows * b->ld * 8), vec = al256((size_t)rows * 8),
                ivec = al256((size_t)rows * 4);
-  const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB);
-  const bool ctpb = (b->alg == SEVO_DE_CTPB);
+  const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE);
+  const bool ctpb = (b->alg == SEVO_DE_CTPB), shade = (b->alg == SEVO_DE_SHADE);
   size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ + al256(16) /*err*/ +
                  al256(8) /*refined*/ + al256((size_t)b->R * 8) /*rp*/ +
                  al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
                  al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
   if (de) bytes += mat /*U*/ + vec /*fu*/;
   if (ctpb) bytes += mat /*A*/ + al256((size_t)b->R * 4) /*asize*/ + ivec /*order*/;
+  if (shade)
+    bytes += ivec /*order*/ + 2 * al256((size_t)b->R * SEVO_SHADE_H * 8) /*MF, MCR*/ +
+             al256((size_t)b->R * 4) /*mk*/ + 2 * vec /*Fi, CRi*/ + ivec /*kpb*/;
   if (!de) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
   b->block_bytes = bytes;
   if (ctpb && rsel_smem_bytes(b->NP) > 48 * 1024)
@@ -1208,6 +1323,17 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->A = (double*)take(mat);
     b->asize = (int32_t*)take(al256((size_t)b->R * 4));
     b->order = (int32_t*)take(ivec);
+  }
+  b->MF = b->MCR = b->Fi = b->CRi = nullptr;
+  b->mk = b->kpb = nullptr;
+  if (shade) {
+    b->order = (int32_t*)take(ivec);
+    b->MF = (double*)take(al256((size_t)b->R * SEVO_SHADE_H * 8));
+    b->MCR = (double*)take(al256((size_t)b->R * SEVO_SHADE_H * 8));
+    b->mk = (int32_t*)take(al256((size_t)b->R * 4));
+    b->Fi = (double*)take(vec);
+    b->CRi = (double*)take(vec);
+    b->kpb = (int32_t*)take(ivec);
   }
   if (!de) {
     b->V = (double*)take(mat);
@@ -1280,10 +1406,19 @@ cudaError_t sv_batch_init(Batch* b) {
   const int tk4 = sv_trace_begin(SEVO_TK_CONTROL, st);
   fill_kernel<<<grid_for(b->R, T), T, 0, st>>>(b->best, b->R, INFINITY);
   sv_trace_end(tk4, st);
+  if (b->alg == SEVO_DE_SHADE) {  // memory: every slot 0.5, write position 0
+    const int64_t hm = (int64_t)b->R * SEVO_SHADE_H;
+    const int tkm = sv_trace_begin(SEVO_TK_CONTROL, st);
+    fill_kernel<<<grid_for(hm, T), T, 0, st>>>(b->MF, hm, 0.5);
+    fill_kernel<<<grid_for(hm, T), T, 0, st>>>(b->MCR, hm, 0.5);
+    sv_trace_end(tkm, st);
+    sv_note_launch();
+    if ((e = cudaMemsetAsync(b->mk, 0, (size_t)b->R * 4, st)) != cudaSuccess) return e;
+  }
   const int count0 = (int)std::min<int64_t>(b->budget, b->NP);
   if ((e = sv_ctl_set(b, 0ull, count0)) != cudaSuccess) return e;
   if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
-  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
+  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
     // best-so-far of the initial population (the select kernel's min part
     // with no trials: fu == fx, every row "accepted" onto itself is avoided
     // by using the PSO-style per-run reducer on fx)
@@ -1335,8 +1470,15 @@ cudaError_t sv_batch_generation(Batch* b) {
   const int nq = (b->D + 3) >> 2;
   const int T = 256;
   cudaError_t e;
-  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB) {
-    if (b->alg == SEVO_DE_CTPB) {
+  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
+    if (b->alg == SEVO_DE_SHADE) {
+      const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
+      shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl, b->R,
+                                                          b->NP, SEVO_SHADE_H, b->Fi, b->CRi,
+                                                          b->kpb);
+      sv_trace_end(tks, st);
+    }
+    if (b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
       const int tk_rank = sv_trace_begin(SEVO_TK_DE_RANK, st);
       // counting rank (O(NP^2) per run, parallel over row blocks) for small
       // populations; radix select + sort of the candidates above that
@@ -1349,16 +1491,23 @@ cudaError_t sv_batch_generation(Batch* b) {
       }
       sv_trace_end(tk_rank, st);
       const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-      de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
-          b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
-          make_fastdiv(b->NP));
+      if (b->alg == SEVO_DE_SHADE)
+        de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
+            b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+            b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
+            b->Fi, b->CRi, b->kpb);
+      else
+        de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
+            b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+            b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
+            make_fastdiv(b->NP), nullptr, nullptr, nullptr);
       sv_trace_end(tk8, st);
     } else {
       const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
       de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
           b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP));
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
+          nullptr, nullptr, nullptr);
       sv_trace_end(tk9, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1366,7 +1515,7 @@ cudaError_t sv_batch_generation(Batch* b) {
     const int tk10 = sv_trace_begin(SEVO_TK_DE_SELECT, st);
     de_select_kernel<<<b->R, SEL_THREADS, sel_smem_bytes(b->NP), st>>>(
         b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
-        b->alg == SEVO_DE_CTPB);
+        b->alg == SEVO_DE_CTPB, b->Fi, b->CRi, b->MF, b->MCR, b->mk, SEVO_SHADE_H);
     sv_trace_end(tk10, st);
     const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
     de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,

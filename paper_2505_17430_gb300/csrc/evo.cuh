@@ -28,6 +28,8 @@ struct Batch {
   size_t block_bytes;
   double *X, *fx, *U, *fu, *A, *V, *P, *fp, *best;
   int32_t *asize, *guide, *part, *order, *action;
+  double *MF, *MCR, *Fi, *CRi;  // SHADE memory (R x SEVO_SHADE_H) and per-row F, CR
+  int32_t *mk, *kpb;            // SHADE write positions (R) and per-row pbest pools
   uint64_t* seeds;
   GenCtl* ctl;
   uint32_t* err;  // device error bits accumulated over every evaluation

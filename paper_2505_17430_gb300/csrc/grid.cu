@@ -61,8 +61,8 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
   }
   for (int a = 0; a < grid->nalgs; ++a) {
     const sevo_alg_params& p = grid->algs[a];
-    const bool de = (p.alg == SEVO_DE_RAND1 || p.alg == SEVO_DE_CTPB);
-    if (p.alg < 0 || p.alg > SEVO_PSO_RING || p.NP > SV_MAX_NP || p.budget < 1 ||
+    const bool de = (p.alg == SEVO_DE_RAND1 || p.alg == SEVO_DE_CTPB || p.alg == SEVO_DE_SHADE);
+    if (p.alg < 0 || p.alg > SEVO_DE_SHADE || p.NP > SV_MAX_NP || p.budget < 1 ||
         (de && p.NP < 4) || (!de && p.NP < 2) || !(p.lb < p.ub) || p.prec < 0 || p.prec > 3)
       return SEVO_ERR_ARG;
   }

@@ -14,11 +14,13 @@ struct sevo_state {
   int64_t fes, gens;
 };
 
-static bool is_de(int alg) { return alg == SEVO_DE_RAND1 || alg == SEVO_DE_CTPB; }
+static bool is_de(int alg) {
+  return alg == SEVO_DE_RAND1 || alg == SEVO_DE_CTPB || alg == SEVO_DE_SHADE;
+}
 
 static int32_t check_params(const sevo_problem* p, const sevo_alg_params* a) {
   if (!p || !a) return SEVO_ERR_ARG;
-  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_PSO_RING) return SEVO_ERR_ARG;
+  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_DE_SHADE) return SEVO_ERR_ARG;
   if (a->prec < SEVO_FP64 || a->prec > SEVO_FP32) return SEVO_ERR_ARG;
   if (a->NP > SV_MAX_NP || a->budget < 1) return SEVO_ERR_ARG;
   if (is_de(a->alg) && a->NP < 4) return SEVO_ERR_ARG;
@@ -267,6 +269,36 @@ extern "C" int32_t sevo_state_get_async(const sevo_state* s, double* X, double* 
   return SEVO_OK;
 }
 
+extern "C" int32_t sevo_state_get_shade(const sevo_state* s, double* MF, double* MCR, int32_t* k,
+                                        double* F, double* CR, int32_t* kpb) {
+  if (!s || s->params.alg != SEVO_DE_SHADE) return SEVO_ERR_ARG;
+  const Batch& b = s->b;
+  const size_t hm = (size_t)b.R * SEVO_SHADE_H * 8, rows = (size_t)b.R * b.NP;
+  if (MF) SV_CUDA(cudaMemcpyAsync(MF, b.MF, hm, cudaMemcpyDeviceToHost, b.stream));
+  if (MCR) SV_CUDA(cudaMemcpyAsync(MCR, b.MCR, hm, cudaMemcpyDeviceToHost, b.stream));
+  if (k) SV_CUDA(cudaMemcpyAsync(k, b.mk, (size_t)b.R * 4, cudaMemcpyDeviceToHost, b.stream));
+  if (F) SV_CUDA(cudaMemcpyAsync(F, b.Fi, rows * 8, cudaMemcpyDeviceToHost, b.stream));
+  if (CR) SV_CUDA(cudaMemcpyAsync(CR, b.CRi, rows * 8, cudaMemcpyDeviceToHost, b.stream));
+  if (kpb) SV_CUDA(cudaMemcpyAsync(kpb, b.kpb, rows * 4, cudaMemcpyDeviceToHost, b.stream));
+  SV_CUDA(cudaStreamSynchronize(b.stream));
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_set_shade(sevo_state* s, const double* MF, const double* MCR,
+                                        const int32_t* k) {
+  if (!s || s->params.alg != SEVO_DE_SHADE) return SEVO_ERR_ARG;
+  const Batch& b = s->b;
+  if (k)
+    for (int r = 0; r < b.R; ++r)
+      if (k[r] < 0 || k[r] >= SEVO_SHADE_H) return SEVO_ERR_ARG;
+  const size_t hm = (size_t)b.R * SEVO_SHADE_H * 8;
+  if (MF) SV_CUDA(cudaMemcpyAsync(b.MF, MF, hm, cudaMemcpyHostToDevice, b.stream));
+  if (MCR) SV_CUDA(cudaMemcpyAsync(b.MCR, MCR, hm, cudaMemcpyHostToDevice, b.stream));
+  if (k) SV_CUDA(cudaMemcpyAsync(b.mk, k, (size_t)b.R * 4, cudaMemcpyHostToDevice, b.stream));
+  SV_CUDA(cudaStreamSynchronize(b.stream));
+  return SEVO_OK;
+}
+
 // ---- save / load: header + arrays, every array the run's next generation
 // reads (counter-based draws make a resumed run bit-identical)
 struct SaveHeader {
@@ -283,6 +315,7 @@ static size_t save_bytes(const sevo_state* s) {
   size_t n = sizeof(SaveHeader) + m + v;  // X, fx
   if (s->params.alg == SEVO_DE_CTPB) n += m;        // A
   if (!is_de(s->params.alg)) n += 2 * m + v;        // V, P, fp
+  if (s->params.alg == SEVO_DE_SHADE) n += 2 * SEVO_SHADE_H * 8 + 8;  // M_F, M_CR, k
   return n;
 }
 
@@ -309,6 +342,14 @@ extern "C" int32_t sevo_state_save(const sevo_state* s, void* buf, size_t* size)
                               is_de(s->params.alg) ? nullptr : (double*)(c + 3 * m + v), nullptr,
                               nullptr, nullptr);
   if (st != SEVO_OK) return st;
+  if (s->params.alg == SEVO_DE_SHADE) {  // memory after the population arrays
+    char* q = c + m + v;
+    int32_t k = 0;
+    st = sevo_state_get_shade(s, (double*)q, (double*)(q + SEVO_SHADE_H * 8), &k, nullptr,
+                              nullptr, nullptr);
+    if (st != SEVO_OK) return st;
+    std::memcpy(q + 2 * SEVO_SHADE_H * 8, &k, 4);
+  }
   h.asize = as;
   SV_CUDA(cudaMemcpy(&h.best, b.best, 8, cudaMemcpyDeviceToHost));
   std::memcpy(buf, &h, sizeof(h));
@@ -333,6 +374,13 @@ extern "C" int32_t sevo_state_load(sevo_state* s, const void* buf, size_t size) 
                               de ? nullptr : (const double*)(c + 2 * m + v),
                               de ? nullptr : (const double*)(c + 3 * m + v), h.fes);
   if (st != SEVO_OK) return st;
+  if (s->params.alg == SEVO_DE_SHADE) {
+    const char* q = c + m + v;
+    int32_t k = 0;
+    std::memcpy(&k, q + 2 * SEVO_SHADE_H * 8, 4);
+    st = sevo_state_set_shade(s, (const double*)q, (const double*)(q + SEVO_SHADE_H * 8), &k);
+    if (st != SEVO_OK) return st;
+  }
   SV_CUDA(cudaMemcpy(s->b.best, &h.best, 8, cudaMemcpyHostToDevice));
   SV_CUDA(cudaMemcpy(s->b.seeds, &h.seed, 8, cudaMemcpyHostToDevice));
   s->gens = h.gens;

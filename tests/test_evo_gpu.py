@@ -416,3 +416,96 @@ def test_async_set_get_match_sync(S):
     assert ref.step(1) == 0
     r = ref.get()
     assert np.array_equal(r["fx"], g["fx"]) and np.array_equal(r["X"], g["X"])
+
+
+# ---------------------------------------------------------------- SHADE
+def _shade_state(S, fam=2, D=13, NP=64, seed=17, prec=None):
+    p = S.Problem(400 + fam, fam, D)
+    q = O.Problem(400 + fam, fam, D)
+    st = S.State(p, S.alg_params(S.DE_SHADE, NP, 10 ** 6, prec=S.FP64 if prec is None else prec),
+                 seed)
+    return p, q, st
+
+
+def test_shade_params_match_oracle(S):
+    """Per-row F, CR and pbest pool drawn on the GPU from a given memory
+    equal the oracle's draws (pool exactly; F and CR to 1e-13, the two sides'
+    log, cos and tan may differ in the last place)."""
+    NP, seed = 64, 17
+    p, q, st = _shade_state(S, NP=NP, seed=seed)
+    rng = np.random.default_rng(5)
+    MF, MCR = rng.uniform(0.05, 0.95, S.SHADE_H), rng.uniform(0.0, 1.0, S.SHADE_H)
+    st.set_shade(MF, MCR, 17)
+    assert st.de_step(3) == 0
+    sh = st.get_shade()
+    F, CR, kpb = O.shade_params(seed, 3, NP, MF, MCR)
+    assert np.array_equal(sh["kpb"], kpb)
+    assert np.allclose(sh["F"], F, rtol=1e-13, atol=0) and np.allclose(sh["CR"], CR, rtol=1e-13, atol=1e-15)
+    assert (sh["F"] > 0).all() and (sh["F"] <= 1).all() and (sh["CR"] >= 0).all() and (sh["CR"] <= 1).all()
+
+
+@pytest.mark.parametrize("fam,D,NP", [(2, 13, 64), (6, 30, 40), (1, 100, 600)])
+def test_shade_lockstep(S, fam, D, NP):
+    """Five generations in lock step with the oracle: given the GPU's
+    parameters, trial vectors and partners are bit-identical to the oracle's,
+    fitness within the FP64 tolerance, selection identical, and the memory
+    update equal to the oracle's within 1e-13 (sums in another order)."""
+    seed = 23
+    p, q, st = _shade_state(S, fam=fam, D=D, NP=NP, seed=seed)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    MF, MCR, k = O.shade_memory()
+    for gen in range(1, 6):
+        st.set(X=X, fx=fx, fes=NP)
+        st.set_shade(MF, MCR, k)
+        assert st.de_step(gen) == 0
+        g, sh = st.get(), st.get_shade()
+        Fo, CRo, kpbo = O.shade_params(seed, gen, NP, MF, MCR)
+        assert np.array_equal(sh["kpb"], kpbo)
+        assert np.allclose(sh["F"], Fo, rtol=1e-13, atol=0)
+        U, part = O.shade_trials(seed, gen, X, fx, sh["F"], sh["CR"], sh["kpb"])
+        assert np.array_equal(g["part"], part)
+        assert np.array_equal(g["U"], U)
+        fu = q.eval(U)
+        assert (np.abs(g["fu"] - fu) <= tol64(fu, q.scale(U))).all()
+        MFo, MCRo, ko, n = O.shade_update(fx, g["fu"], sh["F"], sh["CR"], MF, MCR, k)
+        assert int(sh["k"][0]) == ko
+        assert np.allclose(sh["MF"][0], MFo, rtol=1e-13, atol=0)
+        assert np.allclose(sh["MCR"][0], MCRo, rtol=1e-13, atol=1e-16)
+        X2, fx2, _, _, _ = O.de_select(seed, gen, X, fx, U, g["fu"])
+        assert np.array_equal(g["X"], X2) and np.array_equal(g["fx"], fx2)
+        X, fx, MF, MCR, k = X2, fx2, sh["MF"][0], sh["MCR"][0], int(sh["k"][0])
+
+
+def test_shade_full_run_and_grid(S):
+    """SHADE on the shifted-rotated ellipsoid (D = 10, NP = 50, 6e4
+    evaluations, FP64) reaches the 1e-8 success threshold like the oracle's
+    control run; a grid of SHADE runs equals the same runs driven alone."""
+    D, NP, budget = 10, 50, 60000
+    p = S.Problem(3, S.ELLIPSOID, D)
+    a = S.alg_params(S.DE_SHADE, NP, budget)
+    res = S.sevo_run_grid([p], [a], [(0, 0, s) for s in (1, 2, 3)])
+    assert res["success"].all(), res["best"]
+    st = S.State(p, a, 2)
+    g = 0
+    while st.result()["fes"] < budget:
+        g += 1
+        st.de_step(g)
+    assert st.result()["best"] == res["best"][1]
+
+
+def test_shade_save_load_resume_bit_identical(S):
+    p, q, a = _shade_state(S, NP=40, seed=8)
+    for g in range(1, 6):
+        a.de_step(g)
+    blob = a.save()
+    p2, q2, b = _shade_state(S, NP=40, seed=99)
+    b.load(blob)
+    for g in range(6, 11):
+        a.de_step(g)
+        b.de_step(g)
+    ga, gb = a.get(), b.get()
+    assert np.array_equal(ga["X"], gb["X"]) and np.array_equal(ga["fx"], gb["fx"])
+    sa, sb = a.get_shade(), b.get_shade()
+    assert np.array_equal(sa["MF"], sb["MF"]) and np.array_equal(sa["k"], sb["k"])
+    assert a.result()["best"] == b.result()["best"]
