@@ -21,6 +21,7 @@ LIB = os.path.join(BUILD, "liboracle.so")
 SRC = [os.path.join(HERE, "sevo_oracle.c")]
 
 ELLIPSOID, ROSENBROCK, RASTRIGIN, SCHWEFEL, ACKLEY, GRIEWANK, HYBRID, COMPOSITION = range(8)
+COMP_HYBRID = 8  # composition whose components are hybrids
 P_INIT, P_PART, P_CROSS, P_ARCH, P_PSO = 1, 2, 3, 4, 5
 
 _lock = threading.Lock()
@@ -69,6 +70,7 @@ def lib():
                 "orc_problem_get": (C.c_int, [vp, C.c_int, dp, dp]),
                 "orc_problem_hybrid": (C.c_int, [vp, ip, ip, ip]),
                 "orc_problem_comp": (C.c_int, [vp, ip, dp, dp, dp]),
+                "orc_problem_comp_hybrid": (C.c_int, [vp, C.c_int, ip, ip, ip]),
                 "orc_eval": (C.c_double, [vp, dp]),
                 "orc_eval_batch": (None, [vp, dp, C.c_int64, C.c_int64, dp]),
                 "orc_eval_scale": (C.c_double, [vp, dp]),
@@ -167,7 +169,7 @@ class Problem:
 
     @property
     def ncomp(self):
-        return self.K if self.family == COMPOSITION else 1
+        return self.K if self.family in (COMPOSITION, COMP_HYBRID) else 1
 
     def shift(self, comp=0):
         o = np.zeros(self.D)
@@ -185,6 +187,14 @@ class Problem:
         gb = np.zeros(self.K, np.int32)
         assert lib().orc_problem_hybrid(self.h, _ip(perm), _ip(gs), _ip(gb)) == 0
         return perm, gs, gb
+
+    def comp_hybrid(self, c):
+        """Component c of a composition of hybrids: (perm, group sizes, bodies)."""
+        perm = np.zeros(self.D, np.int32)
+        gs, gb = np.zeros(8, np.int32), np.zeros(8, np.int32)
+        K = lib().orc_problem_comp_hybrid(self.h, c, _ip(perm), _ip(gs), _ip(gb))
+        assert K > 0
+        return perm, gs[:K], gb[:K]
 
     def comp(self):
         n = self.K

@@ -243,6 +243,10 @@ struct orc_problem {
   double* sigma;        /* composition */
   double* lambda;
   double* bias;
+  int* cK;              /* composition of hybrids: groups per component (Nc) */
+  int* cgsize;          /* Nc x 8 group sizes */
+  int* cgbody;          /* Nc x 8 group bodies */
+  int* cperm;           /* Nc x D permutations */
 };
 
 static void gen_shift(uint64_t seed, int D, int comp, double* o) {
@@ -347,16 +351,45 @@ static void gen_rotation(uint64_t seed, int D, int comp, double* M) {
 }
 
 /* Fisher-Yates over Philox: for i = D-1..1 swap perm[i] with perm[below(i+1)] */
-static void gen_perm(uint64_t seed, int D, int* perm) {
+static void gen_perm_salt(uint64_t seed, int D, uint32_t salt, int* perm) {
   uint32_t w[4];
   for (int i = 0; i < D; ++i) perm[i] = i;
   for (int i = D - 1; i >= 1; --i) {
-    draw(seed, (uint32_t)i, 0, (uint32_t)D, ORC_P_PERM, 0, w);
+    draw(seed, (uint32_t)i, 0, (uint32_t)D, ORC_P_PERM, salt, w);
     int j = (int)orc_below(w[0], (uint32_t)(i + 1));
     int t = perm[i];
     perm[i] = perm[j];
     perm[j] = t;
   }
+}
+
+static void gen_perm(uint64_t seed, int D, int* perm) { gen_perm_salt(seed, D, 0, perm); }
+
+/* hybrid structure from the HYB draws with salt: K in 3..5 groups, fractions
+ * 0.1 + (1 - 0.1 K) E_k / sum E (E ~ Exp(1)), bodies among the six, sizes
+ * floor(frac D) with the last group taking the remainder */
+static int gen_hybrid_groups(uint64_t seed, int D, uint32_t salt, int* gsize, int* gbody) {
+  uint32_t w[4];
+  draw(seed, 0, 0, (uint32_t)D, ORC_P_HYB, salt, w);
+  const int K = 3 + (int)orc_below(w[0], 3);
+  double E[8], sumE = 0.0;
+  for (int k = 0; k < K; ++k) {
+    draw(seed, (uint32_t)(1 + k), 0, (uint32_t)D, ORC_P_HYB, salt, w);
+    E[k] = -log(1.0 - orc_u53(w[0], w[1]));
+    gbody[k] = (int)orc_below(w[2], 6);
+    sumE += E[k];
+  }
+  int used = 0;
+  for (int k = 0; k < K; ++k) {
+    const double frac = 0.1 + (1.0 - 0.1 * (double)K) * E[k] / sumE;
+    if (k < K - 1) {
+      gsize[k] = (int)floor(frac * (double)D);
+      used += gsize[k];
+    } else {
+      gsize[k] = D - used;
+    }
+  }
+  return K;
 }
 
 static orc_problem* alloc_problem(int family, int D, int K, int ncomp) {
@@ -409,8 +442,33 @@ orc_problem* orc_hybrid_create(uint64_t seed, int D, int K, const double* frac,
 }
 
 orc_problem* orc_problem_create(uint64_t seed, int family, int D) {
-  if (D < 1 || family < 0 || family > ORC_COMPOSITION) return NULL;
+  if (D < 1 || family < 0 || family > ORC_COMP_HYBRID) return NULL;
   uint32_t w[4];
+  if (family == ORC_COMP_HYBRID) {
+    draw(seed, 0, 0, (uint32_t)D, ORC_P_COMP, 0, w);
+    const int Nc = 3 + (int)orc_below(w[0], 3);
+    orc_problem* p = alloc_problem(ORC_COMP_HYBRID, D, Nc, Nc);
+    p->sigma = (double*)calloc((size_t)Nc, sizeof(double));
+    p->lambda = (double*)calloc((size_t)Nc, sizeof(double));
+    p->bias = (double*)calloc((size_t)Nc, sizeof(double));
+    p->cK = (int*)calloc((size_t)Nc, sizeof(int));
+    p->cgsize = (int*)calloc((size_t)Nc * 8, sizeof(int));
+    p->cgbody = (int*)calloc((size_t)Nc * 8, sizeof(int));
+    p->cperm = (int*)calloc((size_t)Nc * D, sizeof(int));
+    for (int c = 0; c < Nc; ++c) {
+      draw(seed, (uint32_t)(1 + c), 0, (uint32_t)D, ORC_P_COMP, 0, w);
+      p->sigma[c] = 10.0 * (double)(1 + orc_below(w[0], 6));
+      p->lambda[c] = pow(10.0, -6.0 + 6.0 * orc_u53(w[1], w[2]));
+      p->bias[c] = 100.0 * (double)c;
+      gen_shift(seed, D, c, p->o + (size_t)c * D);
+      gen_rotation(seed, D, c, p->M + (size_t)c * D * D);
+      p->cK[c] = gen_hybrid_groups(seed, D, (uint32_t)(1 + c), p->cgsize + 8 * c,
+                                   p->cgbody + 8 * c);
+      gen_perm_salt(seed, D, (uint32_t)(1 + c), p->cperm + (size_t)c * D);
+      permute_rows(p->M + (size_t)c * D * D, p->cperm + (size_t)c * D, D);
+    }
+    return p;
+  }
   if (family <= ORC_GRIEWANK) {
     orc_problem* p = alloc_problem(family, D, 1, 1);
     gen_shift(seed, D, 0, p->o);
@@ -463,6 +521,10 @@ void orc_problem_destroy(orc_problem* p) {
   free(p->sigma);
   free(p->lambda);
   free(p->bias);
+  free(p->cK);
+  free(p->cgsize);
+  free(p->cgbody);
+  free(p->cperm);
   free(p);
 }
 
@@ -474,7 +536,7 @@ void orc_problem_info(const orc_problem* p, int info[3], double* fstar) {
 }
 
 int orc_problem_get(const orc_problem* p, int comp, double* o, double* M) {
-  int nc = (p->family == ORC_COMPOSITION) ? p->K : 1;
+  int nc = (p->family == ORC_COMPOSITION || p->family == ORC_COMP_HYBRID) ? p->K : 1;
   if (comp < 0 || comp >= nc) return -1;
   size_t D = (size_t)p->D;
   if (o) memcpy(o, p->o + comp * D, sizeof(double) * D);
@@ -490,11 +552,19 @@ int orc_problem_hybrid(const orc_problem* p, int* perm, int* gsize, int* gbody) 
   return 0;
 }
 
+int orc_problem_comp_hybrid(const orc_problem* p, int c, int* perm, int* gsize, int* gbody) {
+  if (p->family != ORC_COMP_HYBRID || c < 0 || c >= p->K) return -1;
+  if (perm) memcpy(perm, p->cperm + (size_t)c * p->D, sizeof(int) * p->D);
+  if (gsize) memcpy(gsize, p->cgsize + 8 * c, sizeof(int) * p->cK[c]);
+  if (gbody) memcpy(gbody, p->cgbody + 8 * c, sizeof(int) * p->cK[c]);
+  return p->cK[c];
+}
+
 int orc_problem_comp(const orc_problem* p, int* body, double* sigma,
                      double* lambda, double* bias) {
-  if (p->family != ORC_COMPOSITION) return -1;
+  if (p->family != ORC_COMPOSITION && p->family != ORC_COMP_HYBRID) return -1;
   int n = p->K;
-  if (body) memcpy(body, p->gbody, sizeof(int) * n);
+  if (body && p->gbody) memcpy(body, p->gbody, sizeof(int) * n);
   if (sigma) memcpy(sigma, p->sigma, sizeof(double) * n);
   if (lambda) memcpy(lambda, p->lambda, sizeof(double) * n);
   if (bias) memcpy(bias, p->bias, sizeof(double) * n);
@@ -568,10 +638,22 @@ static double eval_impl(const orc_problem* p, const double* x, double* scale) {
       }
       sc[c] = s;
       orc_transform(p, c, x, z);
-      gc[c] = body_impl(p->gbody[c], z, D, &Sc[c]);
-      if (za) {
-        transform_abs(p, c, x, za);
-        Sc[c] += body_sens(p->gbody[c], z, za, D);
+      if (za) transform_abs(p, c, x, za);
+      if (p->family == ORC_COMP_HYBRID) {  /* component c is a hybrid */
+        gc[c] = 0.0;
+        Sc[c] = 0.0;
+        int start = 0;
+        for (int k = 0; k < p->cK[c]; ++k) {
+          const int b = p->cgbody[8 * c + k], n = p->cgsize[8 * c + k];
+          double sk = 0.0;
+          gc[c] += body_impl(b, z + start, n, &sk);
+          Sc[c] += sk;
+          if (za) Sc[c] += body_sens(b, z + start, za + start, n);
+          start += n;
+        }
+      } else {
+        gc[c] = body_impl(p->gbody[c], z, D, &Sc[c]);
+        if (za) Sc[c] += body_sens(p->gbody[c], z, za, D);
       }
       if (s == 0.0 && exact < 0) exact = c;
     }

@@ -41,7 +41,12 @@ extern "C" {
 /* ---- families (same numbering as the public C ABI; written independently) */
 enum {
   ORC_ELLIPSOID = 0, ORC_ROSENBROCK = 1, ORC_RASTRIGIN = 2, ORC_SCHWEFEL = 3,
-  ORC_ACKLEY = 4, ORC_GRIEWANK = 5, ORC_HYBRID = 6, ORC_COMPOSITION = 7
+  ORC_ACKLEY = 4, ORC_GRIEWANK = 5, ORC_HYBRID = 6, ORC_COMPOSITION = 7,
+  /* composition whose components are hybrid functions (the CEC-style
+   * composition of hybrid components): Nc in 3..5 components, each with the
+   * composition's sigma, lambda, bias, shift and rotation, and its own hybrid
+   * groups, bodies and permutation (drawn as a hybrid's, salt 1 + c) */
+  ORC_COMP_HYBRID = 8
 };
 
 /* ---- Philox purposes (high byte of counter word 3) */
@@ -73,6 +78,9 @@ int orc_problem_get(const orc_problem* p, int comp, double* o, double* M);
 int orc_problem_hybrid(const orc_problem* p, int* perm, int* gsize, int* gbody);
 int orc_problem_comp(const orc_problem* p, int* body, double* sigma,
                      double* lambda, double* bias);
+/* composition of hybrids: component c's permutation (D), group sizes and
+ * bodies (up to 8 each); returns the component's group count, -1 if none */
+int orc_problem_comp_hybrid(const orc_problem* p, int c, int* perm, int* gsize, int* gbody);
 
 /* ---- evaluation: returns the error f(x) - f* (bias-free) -------------- */
 double orc_eval(const orc_problem* p, const double* x);

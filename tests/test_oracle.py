@@ -567,3 +567,77 @@ def test_shade_control_run_reaches_success():
     q = O.Problem(3, O.ELLIPSOID, 10)
     r = O.run(q, O.make_alg(O.ALG_DE_SHADE, 50, 60000), 1)
     assert r["success"] and r["fes"] == 60000
+
+
+# ---------------------------------------------------------------- composition of hybrids
+@pytest.mark.parametrize("D", [10, 37])
+def test_comp_hybrid_structure_and_optima(D):
+    """Each component carries a valid hybrid structure (a permutation, group
+    sizes summing to D, bodies among the six); F(o_c) equals bias_c exactly
+    and F >= 0 elsewhere (every component is a non-negative hybrid)."""
+    q = O.Problem(0xF1 + D, O.COMP_HYBRID, D)
+    assert 3 <= q.K <= 5 and q.ncomp == q.K
+    _, sig, lam, bias = q.comp()
+    for c in range(q.K):
+        perm, gs, gb = q.comp_hybrid(c)
+        assert sorted(perm) == list(range(D))
+        assert gs.sum() == D and (gs >= 0).all() and 3 <= len(gs) <= 5
+        assert ((gb >= 0) & (gb <= 5)).all()
+        assert q.eval(q.shift(c)[None, :])[0] == bias[c]
+    X = np.random.default_rng(D).uniform(-100, 100, (50, D))
+    assert (q.eval(X) >= 0).all()
+
+
+def test_comp_hybrid_component_reduces_to_its_hybrid():
+    """Approaching o_c along a ray x = o_c + r u, the residual
+    R(r) = F(x) - bias_c - lambda_c g_c(x) vanishes linearly in r (the other
+    weights decay as sqrt(s_c)), with g_c assembled here from the pinned
+    bodies over component c's permuted groups of z = M'_c (x - o_c).  A wrong
+    group partition, body, permutation or lambda leaves R(r)/r non-constant."""
+    D = 24
+    q = O.Problem(0xF1F1, O.COMP_HYBRID, D)
+    _, sig, lam, bias = q.comp()
+    u = np.random.default_rng(2).standard_normal(D)
+    u /= np.linalg.norm(u)
+    for c in range(q.K):
+        _, gs, gb = q.comp_hybrid(c)
+        ratios = []
+        for r in (1e-5, 1e-6, 1e-7):
+            x = q.shift(c) + r * u
+            z = q.rotation(c) @ (x - q.shift(c))
+            g, start = 0.0, 0
+            for n, b in zip(gs, gb):
+                g += O.body(int(b), z[start:start + n]) if n > 0 else 0.0
+                start += n
+            R = q.eval(x[None, :])[0] - bias[c] - lam[c] * g
+            ratios.append(R / r)
+        assert abs(ratios[1] - ratios[0]) <= 1e-3 * abs(ratios[1]), (c, ratios)
+        assert abs(ratios[2] - ratios[1]) <= 1e-3 * abs(ratios[2]), (c, ratios)
+
+
+def test_comp_hybrid_value_assembled_from_pinned_parts():
+    """At generic points, F equals the composition (weights as pinned for the
+    plain composition family) of component values assembled here from the
+    exported rotation and shift, the pinned bodies and each component's group
+    partition: checks the per-component hybrid assembly, where an error would
+    change g_c by O(1)."""
+    D = 16
+    q = O.Problem(0xF1F2, O.COMP_HYBRID, D)
+    _, sig, lam, bias = q.comp()
+    X = np.vstack([np.random.default_rng(4).uniform(-100, 100, (6, D)),
+                   q.shift(1) + 3.0 * np.random.default_rng(5).standard_normal((4, D))])
+    for x in X:
+        g, s = np.zeros(q.K), np.zeros(q.K)
+        for c in range(q.K):
+            d = x - q.shift(c)
+            s[c] = d @ d
+            z = q.rotation(c) @ d
+            _, gs, gb = q.comp_hybrid(c)
+            start = 0
+            for n, b in zip(gs, gb):
+                g[c] += O.body(int(b), z[start:start + n]) if n > 0 else 0.0
+                start += n
+        w = (1.0 / np.sqrt(s)) * np.exp(-s / (2.0 * D * sig * sig))
+        om = w / w.sum() if w.sum() > 0 else np.full(q.K, 1.0 / q.K)
+        want = float(om @ (lam * g + bias))
+        assert q.eval(x[None, :])[0] == pytest.approx(want, rel=1e-10)
