@@ -70,7 +70,12 @@ enum sevo_family {
   SEVO_ACKLEY = 4,      /* 20 - 20 e^{-0.2 rms(z)} + e - e^{mean cos 2 pi z}  */
   SEVO_GRIEWANK = 5,    /* sum z^2/4000 + 1 - prod cos(z_i/sqrt i)            */
   SEVO_HYBRID = 6,      /* permuted z split into 3..5 groups, a body each     */
-  SEVO_COMPOSITION = 7  /* 3..10 shifted-rotated components, distance weights */
+  SEVO_COMPOSITION = 7,  /* 3..10 shifted-rotated components, distance weights */
+  /* composition whose 3..5 components are hybrid functions (the CEC-style
+   * composition of hybrid components): each component has the composition's
+   * sigma, lambda, bias, shift and rotation and its own hybrid groups, bodies
+   * and permutation (drawn as a hybrid's with salt 1 + c) */
+  SEVO_COMP_HYBRID = 8
 };
 
 enum sevo_prec {
@@ -121,7 +126,9 @@ int32_t sevo_problem_info(const sevo_problem* p, int32_t* family, int32_t* D,
 
 /* Copy instance data to host buffers (any may be NULL): component `comp`'s
  * shift o (D) and rotation M (D*D row-major, hybrid: permuted M'); hybrid
- * perm (D), gsize and gbody (K); composition body, sigma, lambda, bias (Nc). */
+ * perm (D), gsize and gbody (K); composition body, sigma, lambda, bias (Nc);
+ * composition of hybrids: component `comp`'s perm (D), gsize and gbody (its
+ * groups, at most 8) and sigma, lambda, bias (Nc). */
 int32_t sevo_problem_export(const sevo_problem* p, int32_t comp, double* o, double* M,
                             int32_t* perm, int32_t* gsize, int32_t* gbody, double* sigma,
                             double* lambda, double* bias);

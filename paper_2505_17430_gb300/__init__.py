@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsevo.so")
 
 ELLIPSOID, ROSENBROCK, RASTRIGIN, SCHWEFEL, ACKLEY, GRIEWANK, HYBRID, COMPOSITION = range(8)
+COMP_HYBRID = 8  # composition whose components are hybrid functions
 FAMILY_NAMES = ["ellipsoid", "rosenbrock", "rastrigin", "schwefel", "ackley", "griewank",
                 "hybrid", "composition"]
 FP64, TF32, BF16X3, FP32 = 0, 1, 2, 3
@@ -190,13 +191,14 @@ class Problem:
 
     @property
     def ncomp(self):
-        return self.K if self.family == COMPOSITION else 1
+        return self.K if self.family in (COMPOSITION, COMP_HYBRID) else 1
 
     def export(self, comp=0):
         import numpy as np
         D, K = self.D, max(self.K, 1)
         o, M = np.zeros(D), np.zeros((D, D))
-        perm, gs, gb = np.zeros(D, np.int32), np.zeros(K, np.int32), np.zeros(K, np.int32)
+        G = max(K, 8)  # groups of a hybrid component can exceed the component count
+        perm, gs, gb = np.zeros(D, np.int32), np.zeros(G, np.int32), np.zeros(G, np.int32)
         sg, lam, bias = np.zeros(K), np.zeros(K), np.zeros(K)
         check(_lib().sevo_problem_export(self.h, comp, _np_dp(o), _np_dp(M), _np_ip(perm),
                                          _np_ip(gs), _np_ip(gb), _np_dp(sg), _np_dp(lam),

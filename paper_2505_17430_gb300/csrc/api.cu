@@ -109,7 +109,7 @@ static int32_t evaluate_impl(const sevo_problem* p, const double* pop, int64_t N
     return SEVO_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const bool comp = (p->family == SEVO_COMPOSITION);
+  const bool comp = sv_weighted_family(p->family);
   size_t bytes = sv_eval_scratch_bytes(p->D, comp, prec, N);
   void* base = nullptr;
   SV_CUDA(cudaMallocAsync(&base, bytes, s));

@@ -173,14 +173,14 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
       const double* __restrict__ o = P.o[c];
       const T* __restrict__ MT = mt_ptr<T>(P, c);
       const int32_t* __restrict__ gid = P.gid[c];
-      const int ng = P.ngroups;
+      const int ng = P.ngc[c];
       if (tid < TR * SV_MAXG) {
         int r = tid / SV_MAXG, g = tid % SV_MAXG;
-        int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+        int body = P.gbody[c][g];
         acc_init(body, tot[r][g]);
       }
       // composition distance s_c = |x - o_c|^2 in FP64 (warp r, row r)
-      if (P.family == SEVO_COMPOSITION) {
+      if (P.weighted) {
         int64_t row = rowS[warp];
         double s = 0.0;
         if (row >= 0)
@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
           const int c0 = ic * CH, c1 = min(D, c0 + CH);
           if (ic > 0 && lane == 0) {  // Rosenbrock pair across the chunk border
             const int ip = c0 - 1, g = gid[ip];
-            const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
-            if (body == SEVO_ROSENBROCK && ip + 1 < P.gstart[g + 1]) {
+            const int body = P.gbody[c][g];
+            if (body == SEVO_ROSENBROCK && ip + 1 < P.gstart[c][g + 1]) {
               Acc a;
               acc_init(body, a);
               term(body, prevz[r], T(0), true, zS[r][0], P, a);
@@ -237,14 +237,14 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
             }
           }
           for (int g = 0; g < ng; ++g) {
-            const int lo = max(c0, P.gstart[g]), hi = min(c1, P.gstart[g + 1]);
+            const int lo = max(c0, P.gstart[c][g]), hi = min(c1, P.gstart[c][g + 1]);
             if (lo >= hi) continue;
-            const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
+            const int body = P.gbody[c][g];
             Acc a;
             acc_init(body, a);
             for (int e = lo + lane; e < hi; e += 32) {
               const T z = zS[r][e - c0];
-              const bool hn = (e + 1 < P.gstart[g + 1]);
+              const bool hn = (e + 1 < P.gstart[c][g + 1]);
               // a Rosenbrock pair that straddles the chunk border is added
               // when the next chunk is in shared memory
               if (body == SEVO_ROSENBROCK && hn && e + 1 >= c1) continue;
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
       if (lane == 0 && rowS[warp] >= 0) {
         double gsum = 0.0;
         for (int g = 0; g < ng; ++g) {
-          const int body = (P.family == SEVO_COMPOSITION) ? P.cbody[c] : P.gbody[g];
-          gsum += finalize(body, tot[warp][g], P.gstart[g + 1] - P.gstart[g]);
+          const int body = P.gbody[c][g];
+          gsum += finalize(body, tot[warp][g], P.gstart[c][g + 1] - P.gstart[c][g]);
         }
         gS[warp][c] = gsum;
       }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
     }
     if (lane == 0 && rowS[warp] >= 0) {
       const int64_t row = rowS[warp];
-      double err = (P.family == SEVO_COMPOSITION) ? compose(P, sS[warp], gS[warp]) : gS[warp][0];
+      double err = (P.weighted) ? compose(P, sS[warp], gS[warp]) : gS[warp][0];
       if (!isfinite(err)) {
         err = __longlong_as_double(0x7ff8000000000000ll);
         if (aux.nonfinite) atomicAdd(aux.nonfinite, 1u);

@@ -117,8 +117,8 @@ __device__ __forceinline__ double walk_row(uint32_t taddr, int D, int c, bool co
   double gsum = 0.0;
   float zf, zl;
   walk_cols<FAST>(taddr, 0, D, c, comp, P, zf, zl, [&](int g, const Acc32& acc) {
-    const int body = comp ? P.cbody[c] : P.gbody[g];
-    gsum += (double)finalize32(body, acc, P.gstart[g + 1] - P.gstart[g]);
+    const int body = P.gbody[c][g];
+    gsum += (double)finalize32(body, acc, P.gstart[c][g + 1] - P.gstart[c][g]);
   });
   return gsum;
 }
@@ -672,7 +672,7 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
     d.list_off = list_off ? list_off[k] : 0;
     d.nrows = (int32_t)s.nrows;
     d.tile0 = tiles;
-    d.comp = (s.p->family == SEVO_COMPOSITION);
+    d.comp = sv_weighted_family(s.p->family);
     d.ncomp = s.p->ncomp;
     d.sidx = k;
     d.pad = 0;

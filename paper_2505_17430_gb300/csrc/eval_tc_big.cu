@@ -312,7 +312,8 @@ struct ListOutB {
 };
 
 __device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, int i) {
-  return comp ? 0 : P.gid[c][i];
+  (void)comp;
+  return P.gid[c][i];
 }
 
 // one warp per row: lane l merges slices l, l + 32, ... into per-group
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(CMB_WARPS * 32)
                    double* __restrict__ out, double* __restrict__ comp_g, ListOutB lo) {
   const ProblemDev& P = *Pp;
   const int lane = threadIdx.x & 31;
-  const int ng = comp ? 1 : P.ngroups;
+  const int ng = P.ngc[c];
   const int64_t nw = (int64_t)gridDim.x * CMB_WARPS;
   for (int64_t lr = (int64_t)blockIdx.x * CMB_WARPS + (threadIdx.x >> 5); lr < N; lr += nw) {
     Acc32 acc[SV_MAXG];
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(CMB_WARPS * 32)
       }
       if (sb > 0) {  // Rosenbrock pair (c0 - 1, c0) inside one group
         const int gp = group_of(P, c, comp, c0 - 1);
-        const int body = comp ? P.cbody[c] : P.gbody[gp];
+        const int body = P.gbody[c][gp];
         if (gp == g0 && body == SEVO_ROSENBROCK) {
           const float zprev = part[((int64_t)(sb - 1) * REC + 3 * SV_MAXG + 1) * N + lr];
 #pragma unroll
@@ -371,8 +372,8 @@ __global__ void __launch_bounds__(CMB_WARPS * 32)
         t.a0 = a0;
         t.a1 = a1;
         t.a2 = a2;
-        const int body = comp ? P.cbody[c] : P.gbody[g];
-        const int n = comp ? D : P.gstart[g + 1] - P.gstart[g];
+        const int body = P.gbody[c][g];
+        const int n = P.gstart[c][g + 1] - P.gstart[c][g];
         gsum += (double)finalize32(body, t, n);
       }
     }
@@ -464,7 +465,7 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   const int64_t N = seg.nrows;
   if (N <= 0) return cudaSuccess;
   const bool bf16 = (prec == SEVO_BF16X3);
-  const bool comp = (p->family == SEVO_COMPOSITION);
+  const bool comp = sv_weighted_family(p->family);
   if (h.npad % 128 != 0 || p->tmap_rows != 128) return cudaErrorNotSupported;
   if (!scratch || scratch_bytes < sv_eval_big_scratch_bytes(h.D, comp, prec, N))
     return cudaErrorInvalidValue;

@@ -949,7 +949,7 @@ __device__ __forceinline__ double warp_sumd(double v) {
 // FP64 error of row x by one warp: lane = coordinate (D <= 32)
 __device__ double srk_eval64(const ProblemDev& P, const double* __restrict__ x, int lane) {
   const int D = P.D;
-  const bool comp = (P.family == SEVO_COMPOSITION);
+  const bool comp = (P.weighted);
   const double xj = (lane < D) ? x[lane] : 0.0;
   double gv[SV_MAXC], sv[SV_MAXC];
   double total = 0.0;
@@ -961,19 +961,19 @@ __device__ double srk_eval64(const ProblemDev& P, const double* __restrict__ x, 
       const double dd = __shfl_sync(0xffffffffu, dj, j);
       if (lane < D) z = __fma_rn(MT[(size_t)j * D + lane], dd, z);
     }
-    const int gi = comp ? 0 : ((lane < D) ? P.gid[c][lane] : -1);
+    const int gi = (lane < D) ? P.gid[c][lane] : -1;
     const double zn = __shfl_down_sync(0xffffffffu, z, 1);
     const int gn = __shfl_down_sync(0xffffffffu, gi, 1);
-    const int ng = comp ? 1 : P.ngroups;
+    const int ng = P.ngc[c];
     double gc = 0.0;
     for (int g = 0; g < ng; ++g) {
-      const int body = comp ? P.cbody[c] : P.gbody[g];
+      const int body = P.gbody[c][g];
       Acc64 a;
       acc64_init(body, a);
       if (lane < D && gi == g)
         term64(body, z, P.aux64[c][lane], lane + 1 < D && gn == g, zn, P, a);
       warp_sum64(body, a);
-      gc += finalize64(body, a, P.gstart[g + 1] - P.gstart[g]);
+      gc += finalize64(body, a, P.gstart[c][g + 1] - P.gstart[c][g]);
     }
     if (comp) {
       gv[c] = gc;
@@ -992,7 +992,7 @@ template <int PREC>
 __device__ double srk_eval32(const ProblemDev& P, const double* __restrict__ x, int lane,
                              bool* refined) {
   const int D = P.D;
-  const bool comp = (P.family == SEVO_COMPOSITION);
+  const bool comp = (P.weighted);
   float xh = 0.f, xl = 0.f;
   if (lane < D) sv_split_hi_lo(x[lane], xh, xl);
   double gv[SV_MAXC], sv[SV_MAXC];
@@ -1029,19 +1029,19 @@ __device__ double srk_eval32(const ProblemDev& P, const double* __restrict__ x, 
         }
       }
     }
-    const int gi = comp ? 0 : ((lane < D) ? P.gid[c][lane] : -1);
+    const int gi = (lane < D) ? P.gid[c][lane] : -1;
     const float zn = __shfl_down_sync(0xffffffffu, z, 1);
     const int gn = __shfl_down_sync(0xffffffffu, gi, 1);
-    const int ng = comp ? 1 : P.ngroups;
+    const int ng = P.ngc[c];
     double gc = 0.0;
     for (int g = 0; g < ng; ++g) {
-      const int body = comp ? P.cbody[c] : P.gbody[g];
+      const int body = P.gbody[c][g];
       Acc32 a;
       acc32_init(a);
       if (lane < D && gi == g)
         term32t<PREC == SEVO_TF32>(body, z, P.aux32[c][lane], lane + 1 < D && gn == g, zn, P, a);
       warp_sum32(a);
-      gc += (double)finalize32(body, a, P.gstart[g + 1] - P.gstart[g]);
+      gc += (double)finalize32(body, a, P.gstart[c][g + 1] - P.gstart[c][g]);
     }
     if (comp) {
       gv[c] = gc;
@@ -1349,7 +1349,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   // evaluation scratch for all rows (refine sub-lists per segment and the
   // tensor-core composition staging)
   bool any_comp = false;
-  for (const sevo_problem* q : probs) any_comp |= (q->family == SEVO_COMPOSITION);
+  for (const sevo_problem* q : probs) any_comp |= sv_weighted_family(q->family);
   b->any_comp = any_comp;
   b->eval_bytes = sv_eval_scratch_bytes(b->D, any_comp, b->prec, rows);
   SV_CUDA(cudaMalloc(&b->eval_block, b->eval_bytes));

@@ -45,7 +45,7 @@ extern "C" int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* po
   if (cudaGetDevice(&dev) != cudaSuccess) return SEVO_ERR_CUDA;
   if (!p->desc_d || p->device != dev) return SEVO_ERR_STATE;
   if (N == 0) return SEVO_OK;
-  const bool comp = (p->family == SEVO_COMPOSITION);
+  const bool comp = sv_weighted_family(p->family);
   if (sv_eval_scratch_bytes(p->D, comp, prec, N) > SEVO_NOALLOC_SCRATCH_BYTES)
     return SEVO_ERR_UNSUPPORTED;
   void* base = nullptr;

@@ -137,10 +137,10 @@ void gen_rotation(uint64_t seed, int D, int comp, double* M) {
     for (int k = 0; k < D; ++k) M[(size_t)r * D + k] = Qc[(size_t)k * D + r];
 }
 
-void gen_perm(uint64_t seed, int D, int32_t* perm) {
+void gen_perm(uint64_t seed, int D, int32_t* perm, uint32_t salt = 0) {
   for (int i = 0; i < D; ++i) perm[i] = i;
   for (int i = D - 1; i >= 1; --i) {
-    uint4 w = sv_draw(seed, (uint32_t)i, 0u, (uint32_t)D, SV_P_PERM);
+    uint4 w = sv_draw(seed, (uint32_t)i, 0u, (uint32_t)D, SV_P_PERM, salt);
     int j = (int)sv_below(w.x, (uint32_t)(i + 1));
     int32_t t = perm[i];
     perm[i] = perm[j];
@@ -185,7 +185,7 @@ static int32_t upload(sevo_problem* p) {
   h.family = p->family;
   h.D = D;
   h.ncomp = nc;
-  h.ngroups = p->ngroups;
+  h.weighted = (p->family == SEVO_COMPOSITION || p->family == SEVO_COMP_HYBRID) ? 1 : 0;
   h.kpad = round_up(D, 64);
   h.npad = (D <= 128) ? round_up(D, 16) : round_up(D, 128);
   h.fstar = p->fstar;
@@ -200,21 +200,32 @@ static int32_t upload(sevo_problem* p) {
     h.sch_h032 = (float)(std::sin(B) + 0.5 * B * std::cos(B));
     h.sch_c32 = (float)h.sch_c;
   }
-  // groups
-  if (p->family == SEVO_HYBRID) {
-    h.gstart[0] = 0;
-    for (int g = 0; g < p->ngroups; ++g) {
-      h.gstart[g + 1] = h.gstart[g] + p->gsize[g];
-      h.gbody[g] = p->gbody[g];
+  // groups of every component
+  for (int c = 0; c < nc; ++c) {
+    int ng = 1;
+    const int32_t *gs = nullptr, *gb = nullptr;
+    int32_t one_size = D, one_body = p->family;
+    if (p->family == SEVO_HYBRID) {
+      ng = p->ngroups;
+      gs = p->gsize;
+      gb = p->gbody;
+    } else if (p->family == SEVO_COMP_HYBRID) {
+      ng = p->cK[c];
+      gs = p->cgsize[c];
+      gb = p->cgbody[c];
+    } else {
+      if (p->family == SEVO_COMPOSITION) one_body = p->cbody[c];
+      gs = &one_size;
+      gb = &one_body;
     }
-  } else {
-    h.ngroups = 1;
-    h.gstart[0] = 0;
-    h.gstart[1] = D;
-    h.gbody[0] = p->family;
+    h.ngc[c] = ng;
+    h.gstart[c][0] = 0;
+    for (int g = 0; g < ng; ++g) {
+      h.gstart[c][g + 1] = h.gstart[c][g] + gs[g];
+      h.gbody[c][g] = gb[g];
+    }
   }
   for (int c = 0; c < nc; ++c) {
-    h.cbody[c] = (p->family == SEVO_COMPOSITION) ? p->cbody[c] : -1;
     h.sigma[c] = p->sigma[c];
     h.lambda[c] = p->lambda[c];
     h.bias[c] = p->bias[c];
@@ -263,9 +274,9 @@ static int32_t upload(sevo_problem* p) {
     double* a64 = (double*)&blob[oa64];
     float* a32 = (float*)&blob[oa32];
     int32_t* gid = (int32_t*)&blob[ogid];
-    for (int g = 0; g < h.ngroups; ++g) {
-      int b = (p->family == SEVO_COMPOSITION) ? p->cbody[c] : h.gbody[g];
-      int s = h.gstart[g], e = h.gstart[g + 1], n = e - s;
+    for (int g = 0; g < h.ngc[c]; ++g) {
+      int b = h.gbody[c][g];
+      int s = h.gstart[c][g], e = h.gstart[c][g + 1], n = e - s;
       for (int i = s; i < e; ++i) {
         int pos = i - s + 1;  // 1-based position in the group
         double v = 0.0;
@@ -410,11 +421,64 @@ extern "C" int32_t sevo_hybrid_create(uint64_t seed, int32_t D, int32_t K, const
   return make_hybrid(seed, D, K, frac, bodies, out);
 }
 
+// hybrid groups drawn with salt (as for the hybrid family, whose salt is 0):
+// K in 3..5, fractions 0.1 + (1 - 0.1 K) E_k / sum E (E ~ Exp(1)), bodies
+// among the six, sizes floor(frac D) with the last group the remainder
+static int hybrid_groups(uint64_t seed, int D, uint32_t salt, int32_t* gsize, int32_t* gbody) {
+  uint4 w = sv_draw(seed, 0u, 0u, (uint32_t)D, SV_P_HYB, salt);
+  const int K = 3 + (int)sv_below(w.x, 3u);
+  double E[8], sumE = 0.0;
+  for (int k = 0; k < K; ++k) {
+    uint4 v = sv_draw(seed, (uint32_t)(1 + k), 0u, (uint32_t)D, SV_P_HYB, salt);
+    E[k] = -std::log(1.0 - sv_u53(v.x, v.y));
+    gbody[k] = (int32_t)sv_below(v.z, 6u);
+    sumE += E[k];
+  }
+  int used = 0;
+  for (int k = 0; k < K; ++k) {
+    const double frac = 0.1 + (1.0 - 0.1 * (double)K) * E[k] / sumE;
+    if (k < K - 1) {
+      gsize[k] = (int32_t)std::floor(frac * (double)D);
+      used += gsize[k];
+    } else {
+      gsize[k] = D - used;
+    }
+  }
+  return K;
+}
+
 extern "C" int32_t sevo_problem_create(uint64_t seed, int32_t family, int32_t D,
                                        sevo_problem** out) {
-  if (!out || D < 2 || D > SEVO_MAX_D || family < 0 || family > SEVO_COMPOSITION)
+  if (!out || D < 2 || D > SEVO_MAX_D || family < 0 || family > SEVO_COMP_HYBRID)
     return SEVO_ERR_ARG;
   *out = nullptr;
+  if (family == SEVO_COMP_HYBRID) {
+    uint4 w = sv_draw(seed, 0u, 0u, (uint32_t)D, SV_P_COMP);
+    const int Nc = 3 + (int)sv_below(w.x, 3u);
+    sevo_problem* p = alloc_problem(SEVO_COMP_HYBRID, D, Nc);
+    if (!p) return SEVO_ERR_OOM;
+    p->perm_h = (int32_t*)std::calloc((size_t)Nc * D, sizeof(int32_t));
+    if (!p->perm_h) {
+      free_problem(p);
+      return SEVO_ERR_OOM;
+    }
+    std::vector<double> M((size_t)D * D);
+    for (int c = 0; c < Nc; ++c) {
+      uint4 v = sv_draw(seed, (uint32_t)(1 + c), 0u, (uint32_t)D, SV_P_COMP);
+      p->sigma[c] = 10.0 * (double)(1 + sv_below(v.x, 6u));
+      p->lambda[c] = std::pow(10.0, -6.0 + 6.0 * sv_u53(v.y, v.z));
+      p->bias[c] = 100.0 * (double)c;
+      gen_shift(seed, D, c, p->o_h + (size_t)c * D);
+      gen_rotation(seed, D, c, M.data());
+      p->cK[c] = hybrid_groups(seed, D, (uint32_t)(1 + c), p->cgsize[c], p->cgbody[c]);
+      int32_t* perm = p->perm_h + (size_t)c * D;
+      gen_perm(seed, D, perm, (uint32_t)(1 + c));
+      for (int t = 0; t < D; ++t)
+        std::memcpy(p->M_h + (size_t)c * D * D + (size_t)t * D, M.data() + (size_t)perm[t] * D,
+                    sizeof(double) * D);
+    }
+    return finish(p, out);
+  }
   if (family <= SEVO_GRIEWANK) {
     sevo_problem* p = alloc_problem(family, D, 1);
     if (!p) return SEVO_ERR_OOM;
@@ -463,7 +527,7 @@ extern "C" int32_t sevo_problem_info(const sevo_problem* p, int32_t* family, int
   if (!p) return SEVO_ERR_ARG;
   if (family) *family = p->family;
   if (D) *D = p->D;
-  if (ncomp) *ncomp = (p->family == SEVO_HYBRID) ? p->ngroups : p->ncomp;
+  if (ncomp) *ncomp = (p->family == SEVO_HYBRID) ? p->ngroups : p->ncomp;  // groups or components
   if (fstar) *fstar = p->fstar;
   return SEVO_OK;
 }
@@ -480,8 +544,13 @@ extern "C" int32_t sevo_problem_export(const sevo_problem* p, int32_t comp, doub
     if (gsize) std::memcpy(gsize, p->gsize, p->ngroups * 4);
     if (gbody) std::memcpy(gbody, p->gbody, p->ngroups * 4);
   }
-  if (p->family == SEVO_COMPOSITION) {
-    if (gbody) std::memcpy(gbody, p->cbody, p->ncomp * 4);
+  if (p->family == SEVO_COMP_HYBRID) {  // component comp's hybrid structure
+    if (perm) std::memcpy(perm, p->perm_h + comp * D, D * 4);
+    if (gsize) std::memcpy(gsize, p->cgsize[comp], p->cK[comp] * 4);
+    if (gbody) std::memcpy(gbody, p->cgbody[comp], p->cK[comp] * 4);
+  }
+  if (p->family == SEVO_COMPOSITION || p->family == SEVO_COMP_HYBRID) {
+    if (gbody && p->family == SEVO_COMPOSITION) std::memcpy(gbody, p->cbody, p->ncomp * 4);
     if (sigma) std::memcpy(sigma, p->sigma, p->ncomp * 8);
     if (lambda) std::memcpy(lambda, p->lambda, p->ncomp * 8);
     if (bias) std::memcpy(bias, p->bias, p->ncomp * 8);

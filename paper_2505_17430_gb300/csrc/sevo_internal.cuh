@@ -70,10 +70,13 @@ __host__ __device__ __forceinline__ uint32_t sv_below(uint32_t w, uint32_t n) {
 // ---------------------------------------------------------------------------
 // Device-resident instance descriptor.  A single-family instance is one
 // component with one group; a hybrid is one component with K groups; a
-// composition is Nc components of one group each.
+// composition is Nc components of one group each; a composition of hybrids is
+// Nc components of K_c groups each.  Groups are contiguous ranges of the
+// (permuted) output coordinates of their component.
 // ---------------------------------------------------------------------------
 struct ProblemDev {
-  int32_t family, D, ncomp, ngroups;
+  int32_t family, D, ncomp;
+  int32_t weighted;  // composition kinds: component values are weighted (compose)
   int32_t kpad;   // K (input) extent padded for the tensor-core operands
   int32_t npad;   // N (output) extent padded for the tensor-core operands
   double fstar;
@@ -93,9 +96,9 @@ struct ProblemDev {
   const CUtensorMap* tmaplo[SV_MAXC];
   const float* oh32[SV_MAXC];           // D: o split as oh + ol (see sv_split_hi_lo)
   const float* ol32[SV_MAXC];
-  int32_t gstart[SV_MAXG + 1];          // group ranges [gstart[g], gstart[g+1])
-  int32_t gbody[SV_MAXG];
-  int32_t cbody[SV_MAXC];
+  int32_t ngc[SV_MAXC];                 // groups of component c
+  int32_t gstart[SV_MAXC][SV_MAXG + 1]; // component c's group ranges
+  int32_t gbody[SV_MAXC][SV_MAXG];      // component c's group bodies
   double sigma[SV_MAXC], lambda[SV_MAXC], bias[SV_MAXC];
 };
 
@@ -105,9 +108,11 @@ struct sevo_problem {
   // host copies
   double* o_h;      // ncomp x D
   double* M_h;      // ncomp x D x D (row-major; hybrid rows permuted)
-  int32_t* perm_h;  // D (hybrid)
-  int32_t gsize[SV_MAXG], gbody[SV_MAXG];
-  int32_t cbody[SV_MAXC];
+  int32_t* perm_h;  // D (hybrid), ncomp x D (composition of hybrids)
+  int32_t gsize[SV_MAXG], gbody[SV_MAXG];   // hybrid groups
+  int32_t cbody[SV_MAXC];                    // composition component bodies
+  int32_t cK[SV_MAXC];                       // composition of hybrids: groups,
+  int32_t cgsize[SV_MAXC][SV_MAXG], cgbody[SV_MAXC][SV_MAXG];  // sizes, bodies
   double sigma[SV_MAXC], lambda[SV_MAXC], bias[SV_MAXC];
   // device
   ProblemDev host_desc;   // descriptor with device pointers (host copy)
@@ -178,6 +183,8 @@ void sv_trace_end(int token, cudaStream_t st);
 // upload the instance to the current device on first use (thread-safe);
 // SEVO_ERR_STATE if it already lives on another device
 int32_t sv_problem_ready(const sevo_problem* p);
+// composition kinds: the row error is a distance-weighted sum of components
+inline bool sv_weighted_family(int f) { return f == SEVO_COMPOSITION || f == SEVO_COMP_HYBRID; }
 
 // error flags set by device code (bitmask in a device word)
 enum : uint32_t { SV_DEVERR_TIMEOUT = 1u, SV_DEVERR_BOUNDS = 2u, SV_DEVERR_NAN = 4u };

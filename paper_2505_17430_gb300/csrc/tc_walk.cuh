@@ -41,10 +41,11 @@ template <bool FAST, class Close>
 __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c, bool comp,
                                           const ProblemDev& P, float& zfirst, float& zlast,
                                           Close&& close) {
+  (void)comp;  // groups are per component for every family
   const float* __restrict__ aux32 = P.aux32[c];
-  int g = comp ? 0 : P.gid[c][c0];
-  int gend = P.gstart[g + 1];
-  int body = comp ? P.cbody[c] : P.gbody[g];
+  int g = P.gid[c][c0];
+  int gend = P.gstart[c][g + 1];
+  int body = P.gbody[c][g];
   Acc32 acc;
   acc32_init(acc);
   float zprev = 0.f;
@@ -56,12 +57,12 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
     while (col0 >= gend) {  // close groups that ended before this chunk
       close(g, acc);
       ++g;
-      gend = P.gstart[g + 1];
-      body = comp ? P.cbody[c] : P.gbody[g];
+      gend = P.gstart[c][g + 1];
+      body = P.gbody[c][g];
       acc32_init(acc);
     }
     if (col0 + 16 <= gend && col0 + 16 <= c1) {
-      const bool pair0 = col0 > P.gstart[g] && col0 > c0;
+      const bool pair0 = col0 > P.gstart[c][g] && col0 > c0;
       switch (body) {
         case SEVO_ELLIPSOID: chunk16<SEVO_ELLIPSOID, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
         case SEVO_ROSENBROCK: chunk16<SEVO_ROSENBROCK, FAST>(v, aux32, col0, pair0, zprev, P, acc); break;
@@ -79,13 +80,13 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
           while (i == gend) {
             close(g, acc);
             ++g;
-            gend = P.gstart[g + 1];
-            body = comp ? P.cbody[c] : P.gbody[g];
+            gend = P.gstart[c][g + 1];
+            body = P.gbody[c][g];
             acc32_init(acc);
           }
           const float z = v[k];
           if (body == SEVO_ROSENBROCK) {
-            if (i > P.gstart[g] && i > c0) term32t<FAST>(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
+            if (i > P.gstart[c][g] && i > c0) term32t<FAST>(SEVO_ROSENBROCK, zprev, 0.f, true, z, P, acc);
           } else {
             term32t<FAST>(body, z, aux32[i], false, 0.f, P, acc);
           }

@@ -8,7 +8,7 @@ from tests.gpu_util import to_dev, tol64
 
 pytestmark = pytest.mark.gpu
 
-FAMS = list(range(8))
+FAMS = list(range(9))  # the six bodies, hybrid, composition, composition of hybrids
 
 
 @pytest.fixture(scope="module")

@@ -276,7 +276,7 @@ def test_batched_mixed_segments_many_jobs_per_cta(S, prec):
     surface as SEVO_ERR_TIMEOUT from sevo_state_best / sevo_state_result)."""
     D, NP = 30, 540
     tol = {"TF32": 2e-3, "BF16X3": 1e-4}[prec]
-    keys = [(600 + k, k % 8) for k in range(24)]
+    keys = [(600 + k, k % 9) for k in range(27)]
     probs = [S.Problem(s, f, D) for s, f in keys for _ in range(2)]
     seeds = [9000 + r for r in range(len(probs))]
     st = S.State(probs, S.alg_params(S.DE_CTPB, NP, 10 ** 9, prec=getattr(S, prec)), seeds)

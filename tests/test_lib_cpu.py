@@ -123,3 +123,24 @@ def test_status_constants_match_header():
     with pytest.raises(S.SevoError) as ei:
         S.check(S.ERR_ARG, "probe")
     assert ei.value.status == S.ERR_ARG
+
+
+@pytest.mark.parametrize("D", [11, 40])
+def test_comp_hybrid_generation_matches_oracle(D):
+    """The library's host-side generation of a composition of hybrids draws
+    the same instance as the oracle: per component the shift, the permuted
+    rotation (to round-off: the two sides' QR differ), the permutation, the
+    group sizes and bodies, and sigma, lambda, bias."""
+    seed = 0xC0FFEE + D
+    p, q = S.Problem(seed, S.COMP_HYBRID, D), O.Problem(seed, O.COMP_HYBRID, D)
+    assert p.K == q.K
+    _, sig, lam, bias = q.comp()
+    for c in range(q.K):
+        e = p.export(c)
+        perm, gs, gb = q.comp_hybrid(c)
+        assert np.array_equal(e["o"], q.shift(c))
+        assert np.abs(e["M"] - q.rotation(c)).max() < 1e-12
+        assert np.array_equal(e["perm"], perm)
+        assert np.array_equal(e["gsize"][:len(gs)], gs) and np.array_equal(e["gbody"][:len(gb)], gb)
+        assert np.array_equal(e["sigma"], sig) and np.array_equal(e["lambda"], lam)
+        assert np.array_equal(e["bias"], bias)
