@@ -94,6 +94,8 @@ def lib():
                 "orc_shade_trials": (None, [C.c_uint64, C.c_uint64, dp, dp, C.c_int, C.c_int,
                                             dp, dp, ip, C.c_double, C.c_double, dp, ip]),
                 "orc_shade_update": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, ip]),
+                "orc_cso_generation": (None, [C.c_uint64, C.c_uint64, dp, dp, dp, C.c_int,
+                                              C.c_int, C.c_double, C.c_double, C.c_double, ip]),
                 "orc_pso_guides": (None, [dp, C.c_int, C.c_int, ip]),
                 "orc_pso_move": (None, [C.c_uint64, C.c_uint64, dp, dp, dp, ip, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
@@ -309,6 +311,16 @@ def shade_update(fx, fu, F, CR, MF, MCR, k):
     return MF, MCR, kk.value, n
 
 
+def cso_generation(seed, gen, X, V, fx, phi=0.1, lb=-100.0, ub=100.0):
+    """One CSO generation: returns (X', V', pair) with pair[2k], pair[2k + 1]
+    the winner and loser of pair k; the caller evaluates the losers."""
+    X, V, fx = f64(X).copy(), f64(V).copy(), f64(fx)
+    NP, D = X.shape
+    pair = np.zeros(NP, np.int32)
+    lib().orc_cso_generation(seed, gen, _dp(X), _dp(V), _dp(fx), NP, D, phi, lb, ub, _ip(pair))
+    return X, V, pair
+
+
 def de_select(seed, gen, X, fx, U, fu, A=None, asize=0):
     """Returns (X', fx', A', asize', accepted flags); inputs are not modified."""
     X, fx, U, fu = f64(X).copy(), f64(fx).copy(), f64(U), f64(fu)
@@ -350,7 +362,7 @@ def pso_update(X, fx, P, fp):
     return P, fp, n
 
 
-ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING, ALG_DE_SHADE = 0, 1, 2, 3, 4
+ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING, ALG_DE_SHADE, ALG_CSO = 0, 1, 2, 3, 4, 5
 
 
 def make_alg(alg, NP, budget, F=0.5, CR=0.9, p=0.11, w=0.7298, c1=1.49618, c2=1.49618,

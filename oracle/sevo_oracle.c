@@ -1002,6 +1002,58 @@ void orc_pso_move(uint64_t seed, uint64_t gen, double* X, double* V,
   }
 }
 
+/* ---------------------------------------------------------------- CSO */
+void orc_cso_generation(uint64_t seed, uint64_t gen, double* X, double* V, const double* fx,
+                        int NP, int D, double phi, double lb, double ub, int32_t* pair) {
+  uint32_t w[4];
+  /* pairing: indices sorted by (key, index) */
+  uint32_t* key = (uint32_t*)malloc(sizeof(uint32_t) * NP);
+  int32_t* ord = (int32_t*)malloc(sizeof(int32_t) * NP);
+  for (int i = 0; i < NP; ++i) {
+    draw(seed, 0, (uint32_t)i, (uint32_t)gen, ORC_P_CSO, 0, w);
+    key[i] = w[0];
+    ord[i] = i;
+  }
+  for (int i = 1; i < NP; ++i) { /* insertion sort, stable in the index */
+    int32_t cur = ord[i];
+    int j = i;
+    while (j > 0 && key[ord[j - 1]] > key[cur]) {
+      ord[j] = ord[j - 1];
+      --j;
+    }
+    ord[j] = cur;
+  }
+  /* mean position before the update */
+  double* xbar = (double*)calloc((size_t)D, sizeof(double));
+  for (int i = 0; i < NP; ++i)
+    for (int j = 0; j < D; ++j) xbar[j] += X[(size_t)i * D + j];
+  for (int j = 0; j < D; ++j) xbar[j] /= (double)NP;
+  for (int k = 0; k < NP / 2; ++k) {
+    const int a = ord[2 * k], b = ord[2 * k + 1];
+    const int win = (fx[a] <= fx[b]) ? a : b, los = (win == a) ? b : a;
+    pair[2 * k] = win;
+    pair[2 * k + 1] = los;
+    double* xl = X + (size_t)los * D;
+    double* vl = V + (size_t)los * D;
+    const double* xw = X + (size_t)win * D;
+    for (int j = 0; j < D; ++j) {
+      draw(seed, (uint32_t)(1 + 2 * j), (uint32_t)los, (uint32_t)gen, ORC_P_CSO, 0, w);
+      const double R1 = orc_u53(w[0], w[1]), R2 = orc_u53(w[2], w[3]);
+      draw(seed, (uint32_t)(2 + 2 * j), (uint32_t)los, (uint32_t)gen, ORC_P_CSO, 0, w);
+      const double R3 = orc_u53(w[0], w[1]);
+      const double v = fma(R1, vl[j], fma(R2, xw[j] - xl[j], (phi * R3) * (xbar[j] - xl[j])));
+      double x = xl[j] + v;
+      if (x < lb) x = lb;
+      if (x > ub) x = ub;
+      vl[j] = v;
+      xl[j] = x;
+    }
+  }
+  free(xbar);
+  free(ord);
+  free(key);
+}
+
 int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
                    int NP, int D) {
   int n = 0;
@@ -1063,6 +1115,11 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
     CRi = (double*)malloc(sizeof(double) * NP);
     kpb = (int32_t*)malloc(sizeof(int32_t) * NP);
   }
+  int32_t* pair = NULL;
+  if (a->alg == 5) {
+    V = (double*)calloc(n, sizeof(double));
+    pair = (int32_t*)malloc(sizeof(int32_t) * NP);
+  }
   if (a->alg == 2 || a->alg == 3) {
     V = (double*)calloc(n, sizeof(double));
     P = (double*)malloc(sizeof(double) * n);
@@ -1076,7 +1133,16 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
     ++gen;
     cnt = a->budget - fes;
     if (cnt > NP) cnt = NP;
-    if (a->alg == 4) {
+    if (a->alg == 5) {  /* CSO: NP/2 evaluations per generation */
+      cnt = a->budget - fes;
+      if (cnt > NP / 2) cnt = NP / 2;
+      orc_cso_generation(seed, (uint64_t)gen, X, V, fx, NP, D, a->w, a->lb, a->ub, pair);
+      for (int k = 0; k < NP / 2; ++k) {
+        const int l = pair[2 * k + 1];
+        fx[l] = orc_eval(p, X + (size_t)l * D);
+        if (k < cnt && fx[l] < best) best = fx[l];
+      }
+    } else if (a->alg == 4) {
       orc_shade_params(seed, (uint64_t)gen, NP, ORC_SHADE_H, MF, MCR, Fi, CRi, kpb);
       orc_shade_trials(seed, (uint64_t)gen, X, fx, NP, D, Fi, CRi, kpb, a->lb, a->ub, U, NULL);
       for (int i = 0; i < NP; ++i) fu[i] = orc_eval(p, U + (size_t)i * D);
@@ -1126,6 +1192,7 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
   free(Fi);
   free(CRi);
   free(kpb);
+  free(pair);
   free(guide);
 }
 

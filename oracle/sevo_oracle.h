@@ -52,7 +52,7 @@ enum {
 /* ---- Philox purposes (high byte of counter word 3) */
 enum {
   ORC_P_INIT = 1, ORC_P_PART = 2, ORC_P_CROSS = 3, ORC_P_ARCH = 4, ORC_P_PSO = 5,
-  ORC_P_SHADE = 6,
+  ORC_P_SHADE = 6, ORC_P_CSO = 7,
   ORC_P_SHIFT = 16, ORC_P_ROT = 17, ORC_P_PERM = 18, ORC_P_HYB = 19, ORC_P_COMP = 20
 };
 
@@ -146,6 +146,21 @@ void orc_shade_trials(uint64_t seed, uint64_t gen, const double* X, const double
 int orc_shade_update(int NP, int H, const double* fx, const double* fu, const double* F,
                      const double* CR, double* MF, double* MCR, int* k);
 
+/* ---- CSO (the competitive swarm optimizer of Sec. 3.3, its reference [16]).
+ * One generation of a swarm of NP (even) particles: the pairing is the
+ * indices sorted by a Philox key (purpose CSO, counter (0, i, gen), word 0;
+ * ties by index) taken two by two; in each pair (a, b) the lower fitness wins
+ * (ties: a); the loser l learns:
+ *   v_l = fma(R1, v_l, fma(R2, x_w - x_l, (phi R3) (xbar - x_l)))
+ *   x_l = x_l + v_l, clamped to [lb, ub] (v_l kept)
+ * with R1, R2 = u53 pairs of the draw (purpose CSO, counter (1 + 2 j, l, gen))
+ * and R3 the first u53 pair of (2 + 2 j, l, gen); xbar is the swarm's mean
+ * position before the update (rows summed in index order, divided by NP).
+ * pair (2 NP/2 entries): winner and loser of pair k at [2k], [2k + 1].  The
+ * caller evaluates the NP/2 losers. */
+void orc_cso_generation(uint64_t seed, uint64_t gen, double* X, double* V, const double* fx,
+                        int NP, int D, double phi, double lb, double ub, int32_t* pair);
+
 /* PSO guide index per particle from pbest fitness: topology 0 = global,
  * 1 = ring {i-1,i,i+1} */
 void orc_pso_guides(const double* fp, int NP, int topology, int32_t* guide);
@@ -160,7 +175,7 @@ int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
 /* ---- whole runs ------------------------------------------------------- */
 typedef struct {
   int alg;          /* 0 DE rand/1/bin, 1 DE ctpb/1/bin+archive, 2 PSO gbest, 3 PSO ring,
-                       4 SHADE (F, CR, p unused) */
+                       4 SHADE (F, CR, p unused), 5 CSO (phi in w) */
   int NP;
   double F, CR, p;  /* DE */
   double w, c1, c2; /* PSO */

@@ -641,3 +641,74 @@ def test_comp_hybrid_value_assembled_from_pinned_parts():
         om = w / w.sum() if w.sum() > 0 else np.full(q.K, 1.0 / q.K)
         want = float(om @ (lam * g + bias))
         assert q.eval(x[None, :])[0] == pytest.approx(want, rel=1e-10)
+
+
+# ---------------------------------------------------------------- CSO
+def _cso_keys(seed, gen, NP):
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    return [O.philox((0, i, gen, (7 << 24)), key)[0] for i in range(NP)]
+
+
+def test_cso_pairing_winners_and_unchanged_winners():
+    """The pairs are the indices sorted by their Philox key (ties by index,
+    counter (0, i, gen, CSO << 24), the KAT-pinned generator) taken two by
+    two; the winner of each pair has the lower fitness (ties: the first) and
+    passes unchanged; every particle appears exactly once."""
+    NP, D, seed, gen = 40, 7, 0x1234_5678_9AB, 5
+    X = O.init_population(seed, NP, D)
+    fx = O.Problem(3, O.RASTRIGIN, D).eval(X)
+    fx[3] = fx[11]  # a tie somewhere
+    V = np.random.default_rng(1).uniform(-1, 1, (NP, D))
+    X2, V2, pair = O.cso_generation(seed, gen, X, V, fx)
+    keys = _cso_keys(seed, gen, NP)
+    order = sorted(range(NP), key=lambda i: (keys[i], i))
+    assert sorted(pair.tolist()) == list(range(NP))
+    for k in range(NP // 2):
+        a, b = order[2 * k], order[2 * k + 1]
+        w, l = pair[2 * k], pair[2 * k + 1]
+        assert {w, l} == {a, b}
+        assert w == (a if fx[a] <= fx[b] else b)
+        assert np.array_equal(X2[w], X[w]) and np.array_equal(V2[w], V[w])
+        assert not np.array_equal(X2[l], X[l])
+
+
+def test_cso_loser_update_formula():
+    """Loser l: v' = R1 v + R2 (x_w - x_l) + phi R3 (xbar - x_l) with R1, R2
+    from draw (1 + 2j, l, gen) and R3 from (2 + 2j, l, gen), xbar the mean
+    position before the update, x' = x + v' clamped: recomputed here from
+    the pinned generator to 1e-14 (the oracle fuses the multiply-adds)."""
+    NP, D, seed, gen, phi = 12, 5, 77, 3, 0.1
+    X = O.init_population(seed, NP, D) * 0.5
+    fx = O.Problem(4, O.ELLIPSOID, D).eval(X)
+    V = np.random.default_rng(2).uniform(-3, 3, (NP, D))
+    X2, V2, pair = O.cso_generation(seed, gen, X, V, fx, phi=phi)
+    xbar = X.mean(axis=0)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for k in range(NP // 2):
+        w, l = pair[2 * k], pair[2 * k + 1]
+        for j in range(D):
+            r = O.philox((1 + 2 * j, l, gen, 7 << 24), key)
+            R1, R2 = O.u53(r[0], r[1]), O.u53(r[2], r[3])
+            r3 = O.philox((2 + 2 * j, l, gen, 7 << 24), key)
+            R3 = O.u53(r3[0], r3[1])
+            v = R1 * V[l, j] + R2 * (X[w, j] - X[l, j]) + phi * R3 * (xbar[j] - X[l, j])
+            assert V2[l, j] == pytest.approx(v, rel=1e-13, abs=1e-12)
+            assert X2[l, j] == pytest.approx(min(100.0, max(-100.0, X[l, j] + v)), rel=1e-13, abs=1e-12)
+
+
+def test_cso_collapsed_swarm_is_stationary():
+    """All particles at one point (dyadic coordinates, so the mean is exact)
+    with zero velocity: x_w - x_l = 0 and xbar - x_l = 0, so nothing moves."""
+    NP, D = 20, 6
+    X = np.tile([-3.0, -1.5, -0.25, 0.5, 1.75, 3.0], (NP, 1))  # dyadic: exact mean
+    fx = O.Problem(1, O.GRIEWANK, D).eval(X)
+    X2, V2, _ = O.cso_generation(9, 1, X, np.zeros((NP, D)), fx)
+    assert np.array_equal(X2, X) and not V2.any()
+
+
+def test_cso_control_run_reaches_success():
+    """Control: CSO (NP = 100, phi = 0.1) on the shifted-rotated Griewank at
+    D = 30 reaches 1e-8 within 3e5 evaluations, NP/2 counted per generation."""
+    q = O.Problem(3, O.GRIEWANK, 30)
+    r = O.run(q, O.make_alg(O.ALG_CSO, 100, 300000, w=0.1), 1)
+    assert r["success"] and r["fes"] == 300000 and r["gens"] == (300000 - 100) // 50
