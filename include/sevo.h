@@ -197,7 +197,14 @@ enum sevo_alg {
    * p ~ U[2/NP, 0.2]); after selection the strict improvements update one
    * slot (weighted Lehmer mean of F, weighted mean of CR, weights fx - fu).
    * The F, CR and p fields of sevo_alg_params are not used. */
-  SEVO_DE_SHADE = 4
+  SEVO_DE_SHADE = 4,
+  /* CSO, the competitive swarm optimizer of Sec. 3.3 (its reference [16]):
+   * each generation the swarm (NP even) is paired at random (indices sorted
+   * by a Philox key); in each pair the loser learns from the winner and from
+   * the swarm's mean position, v = R1 v + R2 (x_w - x_l) + phi R3 (xbar - x_l),
+   * x = x + v clamped to the bounds, and only the NP/2 losers are evaluated.
+   * phi is the `w` field of sevo_alg_params; driven by sevo_pso_step. */
+  SEVO_CSO = 5
 };
 #define SEVO_SHADE_H 100   /* success-history memory slots per run */
 

@@ -23,7 +23,7 @@ FAMILY_NAMES = ["ellipsoid", "rosenbrock", "rastrigin", "schwefel", "ackley", "g
                 "hybrid", "composition"]
 FP64, TF32, BF16X3, FP32 = 0, 1, 2, 3
 PREC_NAMES = {FP64: "fp64", TF32: "tf32", BF16X3: "bf16x3", FP32: "fp32"}
-DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING, DE_SHADE = 0, 1, 2, 3, 4
+DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING, DE_SHADE, CSO = 0, 1, 2, 3, 4, 5
 SHADE_H = 100
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED, ERR_STATE = range(-1, -8, -1)
@@ -309,7 +309,7 @@ class State:
         return _lib().sevo_pso_step(self.h, counter)
 
     def step(self, counter):
-        if self.params.alg in (DE_RAND1, DE_CTPB):
+        if self.params.alg in (DE_RAND1, DE_CTPB, DE_SHADE):
             return self.de_step(counter)
         return self.pso_step(counter)
 

@@ -106,12 +106,12 @@ __global__ void ctl_set_kernel(GenCtl* ctl, unsigned long long gen, int count) {
   ctl->count = count;
 }
 
-__global__ void ctl_advance_kernel(GenCtl* ctl, int NP, long long budget) {
+__global__ void ctl_advance_kernel(GenCtl* ctl, int NP, long long budget, int per_gen) {
   unsigned long long g = ctl->gen + 1;
   ctl->gen = g;
-  long long before = (long long)NP + (long long)(g - 1) * NP;
+  long long before = (long long)NP + (long long)(g - 1) * per_gen;
   long long c = budget - before;
-  ctl->count = (int)(c < 0 ? 0 : (c > NP ? NP : c));
+  ctl->count = (int)(c < 0 ? 0 : (c > per_gen ? per_gen : c));
 }
 
 // ---------------------------------------------------------------- indexing
@@ -715,6 +715,121 @@ __global__ void de_apply_kernel(double* __restrict__ X, const double* __restrict
   }
 }
 
+// ---------------------------------------------------------------- CSO
+// pairing: one CTA per run sorts (Philox key, index) ascending with a bitonic
+// network in shared memory (padded with keys past every real one) and takes
+// the sorted indices two by two; the lower fitness wins (ties: the first)
+constexpr int CSO_THREADS = 512;
+
+__global__ void __launch_bounds__(CSO_THREADS)
+    cso_pair_kernel(const double* __restrict__ fx, int32_t* __restrict__ pair,
+                    const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl, int NP,
+                    int npow2) {
+  extern __shared__ __align__(16) unsigned char cs_sm[];
+  uint32_t* key = reinterpret_cast<uint32_t*>(cs_sm);
+  int32_t* idx = reinterpret_cast<int32_t*>(key + npow2);
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const unsigned long long gen = ctl->gen;
+  for (int i = tid; i < npow2; i += blockDim.x) {
+    key[i] = (i < NP) ? sv_draw(seeds[r], 0u, (uint32_t)i, (uint32_t)gen, SV_P_CSO).x : 0xFFFFFFFFu;
+    idx[i] = (i < NP) ? i : 0x7FFFFFFF;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npow2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = tid; t < npow2 / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const uint32_t ka = key[lo], kb = key[hi];
+        const int ia = idx[lo], ib = idx[hi];
+        const bool a_gt_b = (ka > kb) || (ka == kb && ia > ib);
+        if (a_gt_b == up) {
+          key[lo] = kb;
+          key[hi] = ka;
+          idx[lo] = ib;
+          idx[hi] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const double* f = fx + (int64_t)r * NP;
+  for (int k = tid; k < NP / 2; k += blockDim.x) {
+    const int a = idx[2 * k], b = idx[2 * k + 1];
+    const int w = (f[a] <= f[b]) ? a : b;
+    pair[(int64_t)r * NP + 2 * k] = w;
+    pair[(int64_t)r * NP + 2 * k + 1] = (w == a) ? b : a;
+  }
+}
+
+// the swarm's mean position: one thread per (run, coordinate), rows summed
+// in index order (the order of the definition), then divided by NP
+__global__ void cso_mean_kernel(const double* __restrict__ X, double* __restrict__ xbar, int R,
+                                int NP, int D, int ld) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= D) return;
+  for (int r = blockIdx.y; r < R; r += gridDim.y) {
+    const double* Xr = X + (int64_t)r * NP * ld + j;
+    double s = 0.0;
+    for (int i = 0; i < NP; ++i) s = __dadd_rn(s, Xr[(int64_t)i * ld]);
+    xbar[(int64_t)r * ld + j] = __ddiv_rn(s, (double)NP);
+  }
+}
+
+// the loser of pair k, coordinate j: velocity and position update (the
+// multiply-adds fused as in the definition); the new position is also written
+// to row k of the run's block of U (the rows to evaluate)
+__global__ void cso_update_kernel(double* __restrict__ X, double* __restrict__ V,
+                                  double* __restrict__ U, const int32_t* __restrict__ pair,
+                                  const double* __restrict__ xbar,
+                                  const uint64_t* __restrict__ seeds,
+                                  const GenCtl* __restrict__ ctl, int R, int NP, int D, int ld,
+                                  double phi, double lb, double ub, FastDiv fd, FastDiv fhalf) {
+  const int half = NP / 2;
+  const int64_t total = (int64_t)R * half * D;
+  const bool fast = total < (1ll << 31);
+  const unsigned long long gen = ctl->gen;
+  const long long lbk = ord_key(lb), ubk = ord_key(ub);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Split3 sp = split3(t, fast, fd, fhalf);
+    const int j = sp.lo, k = sp.mid, r = sp.hi;
+    const int64_t r0 = (int64_t)r * NP;
+    const int w = pair[r0 + 2 * k], l = pair[r0 + 2 * k + 1];
+    const uint64_t seed = seeds[r];
+    const uint4 a = sv_draw(seed, (uint32_t)(1 + 2 * j), (uint32_t)l, (uint32_t)gen, SV_P_CSO);
+    const uint4 b = sv_draw(seed, (uint32_t)(2 + 2 * j), (uint32_t)l, (uint32_t)gen, SV_P_CSO);
+    const double R1 = u53_int(a.x, a.y), R2 = u53_int(a.z, a.w), R3 = u53_int(b.x, b.y);
+    const int64_t el = (r0 + l) * ld + j;
+    const double xl = X[el], xw = X[(r0 + w) * ld + j];
+    const double v =
+        __fma_rn(R1, V[el],
+                 __fma_rn(R2, __dsub_rn(xw, xl),
+                          __dmul_rn(__dmul_rn(phi, R3), __dsub_rn(xbar[(int64_t)r * ld + j], xl))));
+    double x = __dadd_rn(xl, v);
+    if (lt_key(x, lbk)) x = lb;
+    if (gt_key(x, ubk)) x = ub;
+    V[el] = v;
+    X[el] = x;
+    U[((int64_t)r * half + k) * ld + j] = x;
+  }
+}
+
+// losers' fitness into fx; best-so-far over the first `count` losers
+__global__ void __launch_bounds__(SEL_THREADS)
+    cso_scatter_kernel(double* __restrict__ fx, const double* __restrict__ fu,
+                       const int32_t* __restrict__ pair, double* __restrict__ best,
+                       const GenCtl* __restrict__ ctl, int NP) {
+  const int r = blockIdx.x, half = NP / 2, count = ctl->count;
+  double m = INFINITY;
+  for (int k = threadIdx.x; k < half; k += blockDim.x) {
+    const double v = fu[(int64_t)r * half + k];
+    fx[(int64_t)r * NP + pair[(int64_t)r * NP + 2 * k + 1]] = v;
+    if (k < count) m = dmin_pos(m, v);
+  }
+  block_min_update(m, best + r);
+}
+
 // ---------------------------------------------------------------- PSO
 // coordinate j of run r's particle i (row ri = r * NP + i)
 __device__ __forceinline__ void pso_move_elem(double* __restrict__ X, double* __restrict__ V,
@@ -1266,7 +1381,8 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->pbest_k = std::min(a->NP, std::max(1, (int)std::floor(pm * (double)a->NP + 0.5)));
   }
   b->small = g_policy_small_runs.load() != 0 && b->D <= SRK_MAX_D && b->NP <= SRK_MAX_NP &&
-             b->alg != SEVO_DE_SHADE;
+             b->alg != SEVO_DE_SHADE && b->alg != SEVO_CSO;
+  b->per_gen = (b->alg == SEVO_CSO) ? b->NP / 2 : b->NP;
   b->run_prob = probs;
   b->seg_begin.clear();
   for (int r = 0; r < b->R; ++r)
@@ -1281,12 +1397,14 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
                  al256(8) /*refined*/ + al256((size_t)b->R * 8) /*rp*/ +
                  al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
                  al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
-  if (de) bytes += mat /*U*/ + vec /*fu*/;
+  const bool cso = (b->alg == SEVO_CSO), pso = !de && !cso;
+  if (de || cso) bytes += mat /*U*/ + vec /*fu*/;
+  if (cso) bytes += mat /*V*/ + ivec /*pair*/ + al256((size_t)b->R * b->ld * 8) /*xbar*/;
   if (ctpb) bytes += mat /*A*/ + al256((size_t)b->R * 4) /*asize*/ + ivec /*order*/;
   if (shade)
     bytes += ivec /*order*/ + 2 * al256((size_t)b->R * SEVO_SHADE_H * 8) /*MF, MCR*/ +
              al256((size_t)b->R * 4) /*mk*/ + 2 * vec /*Fi, CRi*/ + ivec /*kpb*/;
-  if (!de) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
+  if (pso) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
   b->block_bytes = bytes;
   if (ctpb && rsel_smem_bytes(b->NP) > 48 * 1024)
     SV_CUDA(cudaFuncSetAttribute(de_rank_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1315,9 +1433,15 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->action = (int32_t*)take(ivec);
   b->U = b->fu = b->A = b->V = b->P = b->fp = nullptr;
   b->asize = b->order = nullptr;
-  if (de) {
+  b->xbar = nullptr;
+  if (de || cso) {
     b->U = (double*)take(mat);
     b->fu = (double*)take(vec);
+  }
+  if (cso) {
+    b->V = (double*)take(mat);
+    b->order = (int32_t*)take(ivec);  // the pairing: winner, loser of pair k at 2k, 2k + 1
+    b->xbar = (double*)take(al256((size_t)b->R * b->ld * 8));
   }
   if (ctpb) {
     b->A = (double*)take(mat);
@@ -1335,7 +1459,7 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->CRi = (double*)take(vec);
     b->kpb = (int32_t*)take(ivec);
   }
-  if (!de) {
+  if (pso) {
     b->V = (double*)take(mat);
     b->P = (double*)take(mat);
     b->fp = (double*)take(vec);
@@ -1364,11 +1488,13 @@ void sv_batch_free(Batch* b) {
 
 // evaluate every row of `M` (X or U) into `f`: one pass over the batch's
 // problem segments (runs sharing a problem)
-static cudaError_t eval_rows(Batch* b, const double* M, double* f) {
+// evaluate `rpr` rows per run of M (runs in blocks of rpr rows) into f
+static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1) {
+  if (rpr < 0) rpr = b->NP;
   std::vector<TcSegment> segs;
   for (size_t s = 0; s + 1 < b->seg_begin.size(); ++s) {
     const int r0 = b->seg_begin[s], r1 = b->seg_begin[s + 1];
-    segs.push_back(TcSegment{b->run_prob[r0], (int64_t)r0 * b->NP, (int64_t)(r1 - r0) * b->NP});
+    segs.push_back(TcSegment{b->run_prob[r0], (int64_t)r0 * rpr, (int64_t)(r1 - r0) * rpr});
   }
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
@@ -1386,7 +1512,7 @@ cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count) {
 
 cudaError_t sv_ctl_advance(Batch* b) {
   const int tk2 = sv_trace_begin(SEVO_TK_CONTROL, b->stream);
-  ctl_advance_kernel<<<1, 1, 0, b->stream>>>(b->ctl, b->NP, (long long)b->budget);
+  ctl_advance_kernel<<<1, 1, 0, b->stream>>>(b->ctl, b->NP, (long long)b->budget, b->per_gen);
   sv_trace_end(tk2, b->stream);
   return cudaGetLastError();
 }
@@ -1418,7 +1544,8 @@ cudaError_t sv_batch_init(Batch* b) {
   const int count0 = (int)std::min<int64_t>(b->budget, b->NP);
   if ((e = sv_ctl_set(b, 0ull, count0)) != cudaSuccess) return e;
   if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
-  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
+  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE ||
+      b->alg == SEVO_CSO) {
     // best-so-far of the initial population (the select kernel's min part
     // with no trials: fu == fx, every row "accepted" onto itself is avoided
     // by using the PSO-style per-run reducer on fx)
@@ -1522,6 +1649,27 @@ cudaError_t sv_batch_generation(Batch* b) {
                                                          b->D, b->ld, make_fastdiv(nq),
                                                          make_fastdiv(b->NP));
     sv_trace_end(tk11, st);
+  } else if (b->alg == SEVO_CSO) {
+    const int half = b->NP / 2;
+    const int np2 = pow2_at_least(b->NP);
+    const int tkp = sv_trace_begin(SEVO_TK_DE_RANK, st);
+    cso_pair_kernel<<<b->R, CSO_THREADS, (size_t)np2 * 8, st>>>(b->fx, b->order, b->seeds, b->ctl,
+                                                                b->NP, np2);
+    sv_trace_end(tkp, st);
+    const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
+    cso_mean_kernel<<<dim3((b->D + 127) / 128, std::min(b->R, 65535)), 128, 0, st>>>(
+        b->X, b->xbar, b->R, b->NP, b->D, b->ld);
+    cso_update_kernel<<<grid_for((int64_t)b->R * half * b->D, T), T, 0, st>>>(
+        b->X, b->V, b->U, b->order, b->xbar, b->seeds, b->ctl, b->R, b->NP, b->D, b->ld, b->w,
+        b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(half));
+    sv_trace_end(tkm, st);
+    sv_note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = eval_rows(b, b->U, b->fu, half)) != cudaSuccess) return e;
+    const int tks = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+    cso_scatter_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fu, b->order, b->best, b->ctl,
+                                                     b->NP);
+    sv_trace_end(tks, st);
   } else {
     const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
     pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,

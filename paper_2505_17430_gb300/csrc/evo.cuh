@@ -15,6 +15,7 @@ struct GenCtl {
 
 struct Batch {
   int alg, D, NP, R, ld;  // R runs of NP rows each, row stride ld (even)
+  int per_gen;            // evaluations counted per generation (CSO: NP / 2)
   double F, CR, p, w, c1, c2, lb, ub;
   unsigned long long cr_thr;  // crossover test: word < cr_thr  <=>  word * 2^-32 < CR
   int pbest_k;
@@ -28,6 +29,7 @@ struct Batch {
   size_t block_bytes;
   double *X, *fx, *U, *fu, *A, *V, *P, *fp, *best;
   int32_t *asize, *guide, *part, *order, *action;
+  double* xbar;                  // CSO: the swarm's mean position per run (R x ld)
   double *MF, *MCR, *Fi, *CRi;  // SHADE memory (R x SEVO_SHADE_H) and per-row F, CR
   int32_t *mk, *kpb;            // SHADE write positions (R) and per-row pbest pools
   uint64_t* seeds;

@@ -62,7 +62,8 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
   for (int a = 0; a < grid->nalgs; ++a) {
     const sevo_alg_params& p = grid->algs[a];
     const bool de = (p.alg == SEVO_DE_RAND1 || p.alg == SEVO_DE_CTPB || p.alg == SEVO_DE_SHADE);
-    if (p.alg < 0 || p.alg > SEVO_DE_SHADE || p.NP > SV_MAX_NP || p.budget < 1 ||
+    if (p.alg == SEVO_CSO && (p.NP < 2 || (p.NP & 1))) return SEVO_ERR_ARG;
+    if (p.alg < 0 || p.alg > SEVO_CSO || p.NP > SV_MAX_NP || p.budget < 1 ||
         (de && p.NP < 4) || (!de && p.NP < 2) || !(p.lb < p.ub) || p.prec < 0 || p.prec > 3)
       return SEVO_ERR_ARG;
   }
@@ -104,7 +105,8 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
     }
     cudaError_t e = sv_batch_init(&b);
     const int64_t NP = a.NP;
-    const int64_t gens = (a.budget > NP) ? (a.budget - NP + NP - 1) / NP : 0;
+    const int64_t PG = b.per_gen;  // evaluations counted per generation
+    const int64_t gens = (a.budget > NP) ? (a.budget - NP + PG - 1) / PG : 0;
     int G = grid->gens_per_graph > 0 ? grid->gens_per_graph : 32;
     if (G > gens) G = (int)std::max<int64_t>(gens, 1);
     int64_t done = 0;
@@ -140,7 +142,7 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
       status = (e == cudaErrorMemoryAllocation) ? SEVO_ERR_OOM : SEVO_ERR_CUDA;
       break;
     }
-    const int64_t fes = std::min<int64_t>(a.budget, NP + gens * NP);
+    const int64_t fes = std::min<int64_t>(a.budget, NP + gens * PG);
     for (size_t q = 0; q < tasks.size(); ++q) {
       const int t = tasks[q];
       res->best[t] = best[q];
@@ -148,7 +150,7 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
       res->gens[t] = gens;
       res->success[t] = best[q] <= SEVO_SUCCESS_THRESHOLD;
     }
-    evals += (int64_t)tasks.size() * NP * (gens + 1);
+    evals += (int64_t)tasks.size() * (NP + gens * PG);
   }
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);

@@ -14,7 +14,7 @@
 // Philox purposes: high byte of counter word 3 (the low 24 bits carry a salt,
 // the component index for instance data).
 enum : uint32_t {
-  SV_P_INIT = 1, SV_P_PART = 2, SV_P_CROSS = 3, SV_P_ARCH = 4, SV_P_PSO = 5, SV_P_SHADE = 6,
+  SV_P_INIT = 1, SV_P_PART = 2, SV_P_CROSS = 3, SV_P_ARCH = 4, SV_P_PSO = 5, SV_P_SHADE = 6, SV_P_CSO = 7,
   SV_P_SHIFT = 16, SV_P_ROT = 17, SV_P_PERM = 18, SV_P_HYB = 19, SV_P_COMP = 20
 };
 

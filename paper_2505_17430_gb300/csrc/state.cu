@@ -20,7 +20,8 @@ static bool is_de(int alg) {
 
 static int32_t check_params(const sevo_problem* p, const sevo_alg_params* a) {
   if (!p || !a) return SEVO_ERR_ARG;
-  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_DE_SHADE) return SEVO_ERR_ARG;
+  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_CSO) return SEVO_ERR_ARG;
+  if (a->alg == SEVO_CSO && (a->NP < 2 || (a->NP & 1))) return SEVO_ERR_ARG;
   if (a->prec < SEVO_FP64 || a->prec > SEVO_FP32) return SEVO_ERR_ARG;
   if (a->NP > SV_MAX_NP || a->budget < 1) return SEVO_ERR_ARG;
   if (is_de(a->alg) && a->NP < 4) return SEVO_ERR_ARG;
@@ -121,7 +122,7 @@ static int32_t step(sevo_state* s, uint64_t counter, bool want_de) {
   if (!s) return SEVO_ERR_ARG;
   if (is_de(s->params.alg) != want_de) return SEVO_ERR_STATE;
   if (s->fes >= s->params.budget) return SEVO_ERR_STATE;
-  const int count = (int)std::min<int64_t>(s->params.NP, s->params.budget - s->fes);
+  const int count = (int)std::min<int64_t>(s->b.per_gen, s->params.budget - s->fes);
   cudaError_t e = sv_ctl_set(&s->b, (unsigned long long)counter, count);
   if (e == cudaSuccess) e = sv_batch_generation(&s->b);
   if (e != cudaSuccess) {
@@ -196,7 +197,15 @@ extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, do
   if (U && b.U) SV_CUDA(get(U, b.U, b));
   if (fu && b.fu) SV_CUDA(cudaMemcpyAsync(fu, b.fu, vb, cudaMemcpyDeviceToHost, b.stream));
   if (part) {
-    if (is_de(s->params.alg)) {
+    if (s->params.alg == SEVO_CSO) {  // the pairing: part[4i] = pair entry i
+      std::vector<int32_t> g(rows);
+      SV_CUDA(cudaMemcpyAsync(g.data(), b.order, rows * 4, cudaMemcpyDeviceToHost, b.stream));
+      SV_CUDA(cudaStreamSynchronize(b.stream));
+      for (size_t i = 0; i < rows; ++i) {
+        part[4 * i] = g[i];
+        part[4 * i + 1] = part[4 * i + 2] = part[4 * i + 3] = 0;
+      }
+    } else if (is_de(s->params.alg)) {
       SV_CUDA(cudaMemcpyAsync(part, b.part, rows * 16, cudaMemcpyDeviceToHost, b.stream));
     } else {
       std::vector<int32_t> g(rows);
@@ -228,7 +237,7 @@ static int32_t set_impl(sevo_state* s, const double* X, const double* fx, const 
   if (V && b.V) SV_CUDA(put(b.V, V, b));
   if (P && b.P) SV_CUDA(put(b.P, P, b));
   if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(b.fp, fp, vb, cudaMemcpyHostToDevice, b.stream));
-  if (!is_de(s->params.alg) && fp) {
+  if (!is_de(s->params.alg) && fp && b.fp) {  // PSO guides from the new pbest fitness
     cudaError_t e = sv_batch_guides(&b);
     if (e != cudaSuccess) {
       sv_set_last_cuda_error(e);
@@ -314,7 +323,8 @@ static size_t save_bytes(const sevo_state* s) {
   const size_t m = (size_t)s->b.R * s->b.NP * s->b.D * 8, v = (size_t)s->b.R * s->b.NP * 8;
   size_t n = sizeof(SaveHeader) + m + v;  // X, fx
   if (s->params.alg == SEVO_DE_CTPB) n += m;        // A
-  if (!is_de(s->params.alg)) n += 2 * m + v;        // V, P, fp
+  if (s->params.alg == SEVO_CSO) n += m;             // V
+  else if (!is_de(s->params.alg)) n += 2 * m + v;   // V, P, fp
   if (s->params.alg == SEVO_DE_SHADE) n += 2 * SEVO_SHADE_H * 8 + 8;  // M_F, M_CR, k
   return n;
 }

@@ -509,3 +509,69 @@ def test_shade_save_load_resume_bit_identical(S):
     sa, sb = a.get_shade(), b.get_shade()
     assert np.array_equal(sa["MF"], sb["MF"]) and np.array_equal(sa["k"], sb["k"])
     assert a.result()["best"] == b.result()["best"]
+
+
+# ---------------------------------------------------------------- CSO
+@pytest.mark.parametrize("fam,D,NP", [(5, 13, 40), (7, 30, 64), (2, 200, 64)])
+def test_cso_lockstep(S, fam, D, NP):
+    """Five CSO generations in lock step with the oracle: the pairing and the
+    winners / losers exactly, the losers' positions and velocities bit for
+    bit (same fused multiply-adds, same index-order mean), the losers'
+    fitness within the FP64 tolerance, winners untouched (D = 200 takes the
+    large-D evaluation of the NP/2 loser rows)."""
+    seed, phi = 31, 0.1
+    p, q = S.Problem(500 + fam, fam, D), O.Problem(500 + fam, fam, D)
+    st = S.State(p, S.alg_params(S.CSO, NP, 10 ** 6, w=phi), seed)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    V = np.zeros((NP, D))
+    for gen in range(1, 6):
+        st.set(X=X, fx=fx, V=V, fes=NP)
+        assert st.pso_step(gen) == 0
+        g = st.get()
+        X2, V2, pair = O.cso_generation(seed, gen, X, V, fx, phi=phi)
+        assert np.array_equal(g["part"][:, 0], pair)
+        assert np.array_equal(g["X"], X2) and np.array_equal(g["V"], V2)
+        los, win = pair[1::2], pair[0::2]
+        want = q.eval(X2[los])
+        assert (np.abs(g["fx"][los] - want) <= tol64(want, q.scale(X2[los]))).all()
+        assert np.array_equal(g["fx"][win], fx[win])
+        fx2 = fx.copy()
+        fx2[los] = g["fx"][los]
+        X, V, fx = X2, V2, fx2
+
+
+def test_cso_full_run_and_grid(S):
+    """CSO (NP = 100, phi = 0.1) on the shifted-rotated Griewank at D = 30
+    reaches 1e-8 in 3e5 evaluations (NP/2 per generation) like the oracle's
+    control run; a grid of CSO runs equals the same runs driven alone."""
+    D, NP, budget = 30, 100, 300000
+    p = S.Problem(3, S.GRIEWANK, D)
+    a = S.alg_params(S.CSO, NP, budget, w=0.1)
+    res = S.sevo_run_grid([p], [a], [(0, 0, s) for s in (1, 2)])
+    assert res["success"].all(), res["best"]
+    assert (res["gens"] == (budget - NP) // (NP // 2)).all() and (res["fes"] == budget).all()
+    st = S.State(p, a, 2)
+    g = 0
+    while st.result()["fes"] < budget:
+        g += 1
+        st.pso_step(g)
+    assert st.result()["best"] == res["best"][1] and st.result()["gens"] == res["gens"][1]
+
+
+def test_cso_save_load_and_bad_population(S):
+    p = S.Problem(9, S.RASTRIGIN, 12)
+    with pytest.raises(S.SevoError):
+        S.State(p, S.alg_params(S.CSO, 41, 1000, w=0.1), 1)  # odd swarm
+    a = S.State(p, S.alg_params(S.CSO, 40, 10 ** 6, w=0.1), 4)
+    for g in range(1, 4):
+        a.pso_step(g)
+    blob = a.save()
+    b = S.State(p, S.alg_params(S.CSO, 40, 10 ** 6, w=0.1), 77)
+    b.load(blob)
+    for g in range(4, 8):
+        a.pso_step(g)
+        b.pso_step(g)
+    ga, gb = a.get(), b.get()
+    assert np.array_equal(ga["X"], gb["X"]) and np.array_equal(ga["V"], gb["V"])
+    assert a.result()["best"] == b.result()["best"]
