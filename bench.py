@@ -330,6 +330,63 @@ def c4_sample(S):
     return out
 
 
+def shade_sec31(S):
+    """The paper's SHADE timing shape (Sec. 3.1): population 100, 30,000
+    evaluations, 10 independent runs on the 30-D Rosenbrock (shifted and
+    rotated here) -- the 10 runs batched through sevo_run_grid in FP32 (the
+    paper's float) and FP64, against the oracle running the same 10 runs one
+    after another on one host core; mean time per run."""
+    import numpy as np
+    import oracle as O
+    D, NP, budget, runs = 30, 100, 30000, 10
+    p = S.Problem(0x5EB00001, 1, D)
+    out = {"workload": "SHADE NP=100, 30,000 evals, 10 runs, shifted-rotated Rosenbrock D=30"}
+    for name, prec in (("fp32", S.FP32), ("fp64", S.FP64)):
+        a = S.alg_params(S.DE_SHADE, NP, budget, prec=prec)
+        S.sevo_run_grid([p], [a], [(0, 0, 1)])  # warm-up
+        t0 = time.perf_counter()
+        r = S.sevo_run_grid([p], [a], [(0, 0, s) for s in range(1, runs + 1)])
+        wall = time.perf_counter() - t0
+        out[name] = {"wall_s_10_runs": round(wall, 4), "mean_s_per_run": round(wall / runs, 5),
+                     "median_final_error": float(np.median(r["best"]))}
+    q = O.Problem(0x5EB00001, 1, D)
+    t0 = time.perf_counter()
+    ob = [O.run(q, O.make_alg(O.ALG_DE_SHADE, NP, budget), s)["best"] for s in range(1, runs + 1)]
+    owall = time.perf_counter() - t0
+    out["oracle"] = {"wall_s_10_runs": round(owall, 4), "mean_s_per_run": round(owall / runs, 5),
+                     "median_final_error": float(np.median(ob)), "cores": 1}
+    return out
+
+
+def cso_sec33(S):
+    """The paper's CSO shape (Sec. 3.3): swarm 300, 1e6 evaluations, 1000-D,
+    5 runs, float -- here on the shifted-rotated Rastrigin (the trigonometric
+    group), the 5 runs batched through sevo_run_grid in FP32 CUDA-core mode
+    with FP64 refinement, against the oracle on one host core timed over a
+    bounded sample of 2,000 evaluations and extrapolated per evaluation."""
+    import numpy as np
+    import oracle as O
+    D, NP, budget, runs = 1000, 300, 1000000, 5
+    p = S.Problem(0x5EB00002, 2, D)
+    a = S.alg_params(S.CSO, NP, budget, w=0.1, prec=S.FP32)
+    t0 = time.perf_counter()
+    r = S.sevo_run_grid([p], [a], [(0, 0, s) for s in range(1, runs + 1)])
+    wall = time.perf_counter() - t0
+    q = O.Problem(0x5EB00002, 2, D)
+    sample = 2000
+    t0 = time.perf_counter()
+    O.run(q, O.make_alg(O.ALG_CSO, NP, sample, w=0.1), 1)
+    osec = time.perf_counter() - t0
+    per_eval = osec / sample
+    return {"workload": "CSO swarm 300, phi 0.1, 1e6 evals, D=1000, 5 runs, shifted-rotated "
+                        "Rastrigin, FP32 + FP64 refinement",
+            "gpu_wall_s_5_runs": round(wall, 3), "gpu_evals_per_s": round(r["evals"] / wall, 1),
+            "median_final_error": float(np.median(r["best"])),
+            "oracle": {"sample_evals": sample, "sample_wall_s": round(osec, 3), "cores": 1,
+                       "extrapolated_wall_s_5_runs": round(per_eval * runs * budget, 1)},
+            "speedup_vs_oracle_extrapolated": round(per_eval * runs * budget / wall, 1)}
+
+
 def c0_single_run(S):
     """The smallest configuration: DE/rand/1/bin, NP = 50, D = 10, FP64, one
     run of 1e5 evaluations on shifted-rotated Rastrigin, seed 1 -- GPU run
@@ -669,6 +726,8 @@ def main():
     large = None if args.no_large_d else large_d_rates(S, torch, peaks)
     c4 = None if args.no_large_d else c4_sample(S)
     c0 = c0_single_run(S)
+    sh31 = shade_sec31(S)
+    cso33 = None if args.no_large_d else cso_sec33(S)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     grid = None
     if not args.no_grid:
@@ -708,7 +767,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
             "kernel_shares": shares, "eval_only_evals_per_s": modes, "large_d": large,
-            "c4_sample": c4,
+            "c4_sample": c4, "shade_sec31": sh31, "cso_sec33": cso33,
             "c0_single_run": c0, "grid": grid}
     print(json.dumps(line), flush=True)
     if dist:
