@@ -188,26 +188,28 @@ __device__ __forceinline__ float sin_pi_red(float z) {
 }
 
 __device__ __forceinline__ float schwefel_term32f(float z, const ProblemDev& P) {
-  // both forms are computed and one is selected (no divergent branch)
   const float s = P.sch_s32;
   const float y = z + s;
+  if (fabsf(z) < 1.0f) {
+    // near the optimum the term is O(z^2) next to c ~ 418: the expansion
+    // around s avoids the cancellation (y > 0 and |y| <= 500 here)
+    const float B = P.sch_B32, sB = P.sch_sinB32, cB = P.sch_cosB32;
+    const float spt = y;
+    const float A = sqrtf(spt);
+    const float apb = A + B;
+    const float d = __fdividef(z, apb);
+    const float h = __sinf(0.5f * d);
+    const float t1 = spt * sB * 2.f * h * h;
+    const float t2 = -cB * spt * sin_minus_x(d);
+    const float t3 = -z * cB * (2.f * A + B) * __fdividef(d, 2.f * apb);
+    const float t4 = -z * P.sch_h032;
+    return t1 + t2 + t3 + t4;
+  }
   const float ay = fabsf(y);
-  const float B = P.sch_B32, sB = P.sch_sinB32, cB = P.sch_cosB32;
-  const float spt = fmaxf(s + z, 0.f);
-  const float A = sqrtf(spt);
-  const float apb = A + B;
-  const float d = __fdividef(z, apb);
-  const float h = __sinf(0.5f * d);
-  const float t1 = spt * sB * 2.f * h * h;
-  const float t2 = -cB * spt * sin_minus_x(d);
-  const float t3 = -z * cB * (2.f * A + B) * __fdividef(d, 2.f * apb);
-  const float t4 = -z * P.sch_h032;
-  const float near = t1 + t2 + t3 + t4;
   const float yc = fminf(ay, 500.f);
   const float bsgn = (y > 0.f) ? 1.f : -1.f;
   const float e = fmaxf(ay - 500.f, 0.f);
-  const float far = P.sch_c32 - bsgn * yc * __sinf(sqrtf(yc)) + 1e-4f * e * e;
-  return (y > 0.f && ay <= 500.f) ? near : far;
+  return P.sch_c32 - bsgn * yc * __sinf(sqrtf(yc)) + 1e-4f * e * e;
 }
 
 __device__ __forceinline__ void term32f(int body, float z, float aux, bool has_next, float znext,
