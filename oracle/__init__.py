@@ -101,6 +101,11 @@ def lib():
                                         C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_double]),
                 "orc_pso_update": (C.c_int, [dp, dp, dp, dp, C.c_int, C.c_int]),
+                "orc_psode_select": (None, [dp, dp, dp, dp, dp, C.c_int, C.c_int, dp, dp, dp]),
+                "orc_psode_generation": (None, [vp, C.c_uint64, C.c_uint64, C.c_int, dp, dp, dp,
+                                                dp, dp, ip, dp, dp, ip, C.c_double, C.c_double,
+                                                C.c_double, C.c_double, C.c_double, dp, dp, dp,
+                                                dp]),
                 "orc_run": (None, [vp, C.POINTER(Alg), C.c_uint64, C.POINTER(Result),
                                    C.POINTER(C.c_int64), dp, C.c_int64]),
                 "orc_run_many": (None, [C.POINTER(vp), C.POINTER(Alg), C.POINTER(C.c_uint64),
@@ -362,7 +367,45 @@ def pso_update(X, fx, P, fp):
     return P, fp, n
 
 
+def psode_select(X, Y, fy, X3, f3):
+    """PSODE's last two steps: returns (X', fx', V') -- V' = X3 - X, row i of
+    X' is Y's where fy < f3, else X3's."""
+    X, Y, fy, X3, f3 = f64(X), f64(Y), f64(fy), f64(X3), f64(f3)
+    NP, D = X.shape
+    Xn, fn, V = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, D))
+    lib().orc_psode_select(_dp(X), _dp(Y), _dp(fy), _dp(X3), _dp(f3), NP, D, _dp(Xn), _dp(fn),
+                           _dp(V))
+    return Xn, fn, V
+
+
+def psode_start(X, fx):
+    """The PSO component's memory made from the initial population: zero
+    velocity, personal bests = the population, ring guides."""
+    X, fx = f64(X), f64(fx)
+    return dict(V=np.zeros_like(X), P=X.copy(), fp=fx.copy(), guide=pso_guides(fx, 1))
+
+
+def psode_generation(problem, seed, gen, X, fx, V, P, fp, guide, MF, MCR, k, w=0.7298,
+                     c1=1.49618, c2=1.49618, lb=-100.0, ub=100.0):
+    """One PSODE generation; inputs are not modified.  Returns a dict with the
+    new X, fx, V, P, fp, guide, MF, MCR, k and the generation's evaluated rows
+    Y, fy (PSO) and U, fu (SHADE)."""
+    X, fx, V = f64(X).copy(), f64(fx).copy(), f64(V).copy()
+    P, fp = f64(P).copy(), f64(fp).copy()
+    g = np.ascontiguousarray(guide, dtype=np.int32).copy()
+    MF, MCR = f64(MF).copy(), f64(MCR).copy()
+    kk = C.c_int(k)
+    NP, D = X.shape
+    Y, fy, U, fu = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, D)), np.zeros(NP)
+    lib().orc_psode_generation(problem.h, seed, gen, NP, _dp(X), _dp(fx), _dp(V), _dp(P),
+                               _dp(fp), _ip(g), _dp(MF), _dp(MCR), C.byref(kk), w, c1, c2, lb,
+                               ub, _dp(Y), _dp(fy), _dp(U), _dp(fu))
+    return dict(X=X, fx=fx, V=V, P=P, fp=fp, guide=g, MF=MF, MCR=MCR, k=kk.value, Y=Y, fy=fy,
+                U=U, fu=fu)
+
+
 ALG_DE_RAND1, ALG_DE_CTPB, ALG_PSO_GBEST, ALG_PSO_RING, ALG_DE_SHADE, ALG_CSO = 0, 1, 2, 3, 4, 5
+ALG_PSODE = 6
 
 
 def make_alg(alg, NP, budget, F=0.5, CR=0.9, p=0.11, w=0.7298, c1=1.49618, c2=1.49618,

@@ -1066,6 +1066,59 @@ int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
   return n;
 }
 
+/* ---------------------------------------------------------------- PSODE */
+void orc_psode_select(const double* X, const double* Y, const double* fy, const double* X3,
+                      const double* f3, int NP, int D, double* Xn, double* fn, double* V) {
+  for (int i = 0; i < NP; ++i) {
+    const int from_pso = fy[i] < f3[i];
+    for (int j = 0; j < D; ++j) {
+      const size_t e = (size_t)i * D + j;
+      const double x = X[e], x3 = X3[e];
+      V[e] = x3 - x;
+      Xn[e] = from_pso ? Y[e] : x3;
+    }
+    fn[i] = from_pso ? fy[i] : f3[i];
+  }
+}
+
+void orc_psode_generation(const orc_problem* p, uint64_t seed, uint64_t gen, int NP,
+                          double* X, double* fx, double* V, double* P, double* fp,
+                          int32_t* guide, double* MF, double* MCR, int* mk, double w, double c1,
+                          double c2, double lb, double ub, double* Y, double* fy, double* U,
+                          double* fu) {
+  const int D = p->D;
+  const size_t n = (size_t)NP * D;
+  double* VY = (double*)malloc(sizeof(double) * n);
+  double* X3 = (double*)malloc(sizeof(double) * n);
+  double* f3 = (double*)malloc(sizeof(double) * NP);
+  double* Fi = (double*)malloc(sizeof(double) * NP);
+  double* CRi = (double*)malloc(sizeof(double) * NP);
+  int32_t* kpb = (int32_t*)malloc(sizeof(int32_t) * NP);
+  /* the PSO component moves a copy of the population */
+  memcpy(Y, X, sizeof(double) * n);
+  memcpy(VY, V, sizeof(double) * n);
+  orc_pso_move(seed, gen, Y, VY, P, guide, NP, D, w, c1, c2, lb, ub);
+  for (int i = 0; i < NP; ++i) fy[i] = orc_eval(p, Y + (size_t)i * D);
+  orc_pso_update(Y, fy, P, fp, NP, D);
+  orc_pso_guides(fp, NP, 1, guide);
+  /* SHADE on another copy */
+  orc_shade_params(seed, gen, NP, ORC_SHADE_H, MF, MCR, Fi, CRi, kpb);
+  orc_shade_trials(seed, gen, X, fx, NP, D, Fi, CRi, kpb, lb, ub, U, NULL);
+  for (int i = 0; i < NP; ++i) fu[i] = orc_eval(p, U + (size_t)i * D);
+  orc_shade_update(NP, ORC_SHADE_H, fx, fu, Fi, CRi, MF, MCR, mk);
+  memcpy(X3, X, sizeof(double) * n);
+  memcpy(f3, fx, sizeof(double) * NP);
+  orc_de_select(seed, gen, X3, f3, U, fu, NP, D, NULL, NULL, NULL);
+  /* velocity = DE displacement, then the pairwise/3 selection */
+  orc_psode_select(X, Y, fy, X3, f3, NP, D, X, fx, V);
+  free(VY);
+  free(X3);
+  free(f3);
+  free(Fi);
+  free(CRi);
+  free(kpb);
+}
+
 /* ======================================================================
  * Whole runs: the budget loop of Listing 4 (evaluate NP, count them, then
  * generations while fes < max_fes); only the first (budget - fes) rows of a
@@ -1109,7 +1162,7 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
   int mk = 0;
   double *Fi = NULL, *CRi = NULL;
   int32_t* kpb = NULL;
-  if (a->alg == 4) {
+  if (a->alg == 4 || a->alg == 6) {
     for (int h = 0; h < ORC_SHADE_H; ++h) MF[h] = MCR[h] = 0.5;
     Fi = (double*)malloc(sizeof(double) * NP);
     CRi = (double*)malloc(sizeof(double) * NP);
@@ -1120,20 +1173,34 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
     V = (double*)calloc(n, sizeof(double));
     pair = (int32_t*)malloc(sizeof(int32_t) * NP);
   }
-  if (a->alg == 2 || a->alg == 3) {
+  double *Y = NULL, *fy = NULL;
+  if (a->alg == 2 || a->alg == 3 || a->alg == 6) {
     V = (double*)calloc(n, sizeof(double));
     P = (double*)malloc(sizeof(double) * n);
     fp = (double*)malloc(sizeof(double) * NP);
     guide = (int32_t*)malloc(sizeof(int32_t) * NP);
     memcpy(P, X, sizeof(double) * n);
     memcpy(fp, fx, sizeof(double) * NP);
-    orc_pso_guides(fp, NP, a->alg - 2, guide);
+    orc_pso_guides(fp, NP, a->alg == 2 ? 0 : 1, guide);
+  }
+  if (a->alg == 6) {
+    Y = (double*)malloc(sizeof(double) * n);
+    fy = (double*)malloc(sizeof(double) * NP);
   }
   while (fes < a->budget) {
     ++gen;
     cnt = a->budget - fes;
     if (cnt > NP) cnt = NP;
-    if (a->alg == 5) {  /* CSO: NP/2 evaluations per generation */
+    if (a->alg == 6) {  /* PSODE: NP PSO rows, then NP DE rows */
+      cnt = a->budget - fes;
+      if (cnt > 2 * (int64_t)NP) cnt = 2 * (int64_t)NP;
+      orc_psode_generation(p, seed, (uint64_t)gen, NP, X, fx, V, P, fp, guide, MF, MCR, &mk,
+                           a->w, a->c1, a->c2, a->lb, a->ub, Y, fy, U, fu);
+      double b = min_first(fy, (int)(cnt < NP ? cnt : NP));
+      if (b < best) best = b;
+      b = min_first(fu, (int)(cnt > NP ? cnt - NP : 0));
+      if (b < best) best = b;
+    } else if (a->alg == 5) {  /* CSO: NP/2 evaluations per generation */
       cnt = a->budget - fes;
       if (cnt > NP / 2) cnt = NP / 2;
       orc_cso_generation(seed, (uint64_t)gen, X, V, fx, NP, D, a->w, a->lb, a->ub, pair);
@@ -1194,6 +1261,8 @@ void orc_run(const orc_problem* p, const orc_alg* a, uint64_t seed,
   free(kpb);
   free(pair);
   free(guide);
+  free(Y);
+  free(fy);
 }
 
 /* ---- thread pool over independent tasks (Sec. 2.4: tasks distributed over

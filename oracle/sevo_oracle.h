@@ -172,10 +172,34 @@ void orc_pso_move(uint64_t seed, uint64_t gen, double* X, double* V,
 int orc_pso_update(const double* X, const double* fx, double* P, double* fp,
                    int NP, int D);
 
+/* ---- PSODE (Sec. 4, case study 1; Listing 4's pairwise/3 hybrid of the
+ * PSO and SHADE components).  The PSO component keeps personal bests P, fp
+ * and ring {i-1,i,i+1} guides, made from the initial population; V starts at
+ * zero.  One generation on the population X, fx:
+ *   Y  = X moved by orc_pso_move with V, P and the guides (the moved velocity
+ *        is dropped), fy = f(Y); personal-best update from (Y, fy) and ring
+ *        guides refreshed from fp;
+ *   SHADE on X, fx (orc_shade_params, _trials, f(U), _update, then
+ *        orc_de_select on a copy) gives the survivors X3, f3;
+ *   V  = X3 - X (the DE displacement);
+ *   X  = Y where fy < f3, else X3 (a tie keeps the DE survivor).
+ * Y, fy, U, fu (NP rows each) receive the generation's 2 NP evaluated rows;
+ * the budget counts the PSO rows first, then the DE rows. */
+/* the last two steps alone: Xn, fn, V from X, Y, fy, X3, f3 (Xn may be X,
+ * fn may be f3) */
+void orc_psode_select(const double* X, const double* Y, const double* fy, const double* X3,
+                      const double* f3, int NP, int D, double* Xn, double* fn, double* V);
+void orc_psode_generation(const orc_problem* p, uint64_t seed, uint64_t gen, int NP,
+                          double* X, double* fx, double* V, double* P, double* fp,
+                          int32_t* guide, double* MF, double* MCR, int* mk, double w, double c1,
+                          double c2, double lb, double ub, double* Y, double* fy, double* U,
+                          double* fu);
+
 /* ---- whole runs ------------------------------------------------------- */
 typedef struct {
   int alg;          /* 0 DE rand/1/bin, 1 DE ctpb/1/bin+archive, 2 PSO gbest, 3 PSO ring,
-                       4 SHADE (F, CR, p unused), 5 CSO (phi in w) */
+                       4 SHADE (F, CR, p unused), 5 CSO (phi in w),
+                       6 PSODE (ring PSO with w, c1, c2 + SHADE; F, CR, p unused) */
   int NP;
   double F, CR, p;  /* DE */
   double w, c1, c2; /* PSO */

@@ -712,3 +712,113 @@ def test_cso_control_run_reaches_success():
     q = O.Problem(3, O.GRIEWANK, 30)
     r = O.run(q, O.make_alg(O.ALG_CSO, 100, 300000, w=0.1), 1)
     assert r["success"] and r["fes"] == 300000 and r["gens"] == (300000 - 100) // 50
+
+
+# ---------------------------------------------------------------- PSODE
+def test_psode_select_worked_example():
+    """Pairwise/3 selection by hand: row 0's PSO offspring is better and is
+    taken; row 1 ties (the DE survivor stays); row 2's PSO offspring is
+    worse.  V is the DE displacement X3 - X in every row."""
+    X = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0]])
+    Y = np.array([[0.5, 0.25], [7.0, 8.0], [9.0, 10.0]])
+    fy = np.array([1.0, 2.0, 5.0])
+    X3 = np.array([[1.5, 2.0], [3.0, 4.5], [5.0, 6.0]])
+    f3 = np.array([1.5, 2.0, 3.0])
+    Xn, fn, V = O.psode_select(X, Y, fy, X3, f3)
+    assert Xn.tolist() == [[0.5, 0.25], [3.0, 4.5], [5.0, 6.0]]
+    assert fn.tolist() == [1.0, 2.0, 3.0]
+    assert V.tolist() == [[0.5, 0.0], [0.0, 0.5], [0.0, 0.0]]
+
+
+@pytest.mark.parametrize("fam,D,NP", [(O.ELLIPSOID, 10, 20), (O.RASTRIGIN, 7, 16)])
+def test_psode_without_pso_coefficients_is_shade(fam, D, NP):
+    """With w = c1 = c2 = 0 the PSO offspring is the population itself, never
+    strictly better than the DE survivor, so PSODE follows SHADE's
+    trajectory exactly: the best-so-far after g generations (2 NP
+    evaluations each) equals SHADE's after g generations (NP each)."""
+    q, G = O.Problem(11, fam, D), 12
+    r6 = O.run(q, O.make_alg(O.ALG_PSODE, NP, NP + 2 * NP * G, w=0, c1=0, c2=0), 5,
+               trace_cap=G + 1)
+    r4 = O.run(q, O.make_alg(O.ALG_DE_SHADE, NP, NP + NP * G), 5, trace_cap=G + 1)
+    assert np.array_equal(r6["trace_best"], r4["trace_best"])
+    assert r6["trace_fes"].tolist() == [NP + 2 * NP * g for g in range(G + 1)]
+
+
+def _psode_parts(q, seed, gen, s, w=0.7298, c1=1.49618, c2=1.49618):
+    """One generation assembled from the pinned PSO and SHADE operators."""
+    Y, _ = O.pso_move(seed, gen, s["X"], s["V"], s["P"], s["guide"], w=w, c1=c1, c2=c2)
+    fy = q.eval(Y)
+    P, fp, _ = O.pso_update(Y, fy, s["P"], s["fp"])
+    guide = O.pso_guides(fp, 1)
+    F, CR, kpb = O.shade_params(seed, gen, len(s["fx"]), s["MF"], s["MCR"])
+    U, _ = O.shade_trials(seed, gen, s["X"], s["fx"], F, CR, kpb)
+    fu = q.eval(U)
+    MF, MCR, k, _ = O.shade_update(s["fx"], fu, F, CR, s["MF"], s["MCR"], s["k"])
+    X3, f3, _, _, _ = O.de_select(seed, gen, s["X"], s["fx"], U, fu)
+    take = fy < f3
+    return dict(X=np.where(take[:, None], Y, X3), fx=np.where(take, fy, f3), V=X3 - s["X"], P=P,
+                fp=fp, guide=guide, MF=MF, MCR=MCR, k=k, Y=Y, fy=fy, U=U, fu=fu)
+
+
+def test_psode_generation_assembles_pinned_parts():
+    """Three generations of the oracle's PSODE equal the same generations
+    assembled from the separately pinned PSO move, pbest update, ring
+    guides, SHADE operators and one-to-one selection (same counters), bit
+    for bit: the PSO offspring moves from the population with the carried
+    velocity, the velocity becomes the DE displacement, and the better of
+    the two offspring sets survives."""
+    NP, D, seed = 24, 9, 4242
+    q = O.Problem(21, O.ACKLEY, D)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    MF, MCR, k = O.shade_memory()
+    s = dict(X=X, fx=fx, MF=MF, MCR=MCR, k=k, **O.psode_start(X, fx))
+    assert not s["V"].any() and np.array_equal(s["guide"], O.pso_guides(fx, 1))
+    for gen in range(1, 4):
+        want = _psode_parts(q, seed, gen, s)
+        got = O.psode_generation(q, seed, gen, s["X"], s["fx"], s["V"], s["P"], s["fp"],
+                                 s["guide"], s["MF"], s["MCR"], s["k"])
+        for key in ("X", "fx", "V", "P", "fp", "guide", "MF", "MCR", "Y", "fy", "U", "fu"):
+            assert np.array_equal(got[key], want[key]), (gen, key)
+        assert got["k"] == want["k"]
+        s = got
+
+
+def test_psode_invariants_and_budget_accounting():
+    """Per generation: fitness never worsens row by row and is f of the row;
+    each row is its PSO offspring, its DE trial or its old self; personal
+    bests never
+    worsen and are f of their rows.  A budget ending inside a generation
+    counts the PSO rows first, then the DE rows: orc_run's best-so-far is
+    the minimum over exactly those evaluations."""
+    NP, D, seed = 16, 6, 99
+    q = O.Problem(5, O.GRIEWANK, D)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    MF, MCR, k = O.shade_memory()
+    s = dict(X=X, fx=fx, MF=MF, MCR=MCR, k=k, **O.psode_start(X, fx))
+    evals = [fx]
+    for gen in range(1, 5):
+        g = O.psode_generation(q, seed, gen, s["X"], s["fx"], s["V"], s["P"], s["fp"],
+                               s["guide"], s["MF"], s["MCR"], s["k"])
+        assert (g["fx"] <= s["fx"]).all() and (g["fp"] <= s["fp"]).all()
+        assert np.array_equal(q.eval(g["X"]), g["fx"]) and np.array_equal(q.eval(g["P"]), g["fp"])
+        for i in range(NP):  # pairwise/3: one of the three candidates
+            assert any(np.array_equal(g["X"][i], c[i]) for c in (g["Y"], g["U"], s["X"]))
+        evals.append(np.concatenate([g["fy"], g["fu"]]))
+        s = g
+    for extra in (NP // 2 + 3, NP + 5):  # last generation ends in the PSO / DE rows
+        budget = NP + 2 * NP * 3 + extra
+        r = O.run(q, O.make_alg(O.ALG_PSODE, NP, budget), seed)
+        want = min(np.min(e) for e in evals[:4])
+        want = min(want, np.min(evals[4][:extra]))
+        assert r["best"] == want and r["fes"] == budget and r["gens"] == 4
+
+
+def test_psode_control_run_reaches_success():
+    """Control: PSODE (NP = 50, ring PSO with w = 0.7298, c1 = c2 = 1.49618,
+    and SHADE) solves the shifted-rotated Rosenbrock at D = 10 to 1e-8
+    within 1e5 evaluations, 2 NP counted per generation."""
+    q = O.Problem(3, O.ROSENBROCK, 10)
+    r = O.run(q, O.make_alg(O.ALG_PSODE, 50, 100000), 1)
+    assert r["success"] and r["fes"] == 100000 and r["gens"] == 1000
