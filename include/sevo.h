@@ -204,7 +204,25 @@ enum sevo_alg {
    * the swarm's mean position, v = R1 v + R2 (x_w - x_l) + phi R3 (xbar - x_l),
    * x = x + v clamped to the bounds, and only the NP/2 losers are evaluated.
    * phi is the `w` field of sevo_alg_params; driven by sevo_pso_step. */
-  SEVO_CSO = 5
+  SEVO_CSO = 5,
+  /* PSODE, Sec. 4's first case study (Listing 4: the pairwise/3 hybrid of
+   * a PSO and SHADE iterated on copies of one population).  The PSO
+   * component is the inertia-weight PSO with ring {i-1,i,i+1} topology
+   * (w, c1, c2) and keeps its own personal bests P, fp and guides, made from
+   * the initial population; V starts at zero.  One generation (2 NP
+   * evaluations, the PSO rows counted first):
+   *   Y = X + v, v = w V + c1 r1 (P - X) + c2 r2 (P_guide - X), clamped to
+   *       [lb, ub] (the same draws as SEVO_PSO_RING); fy = f(Y); personal
+   *       bests from (Y, fy) (strict improvement), guides refreshed;
+   *   SHADE on X, fx exactly as SEVO_DE_SHADE: survivors X3, f3 and the
+   *       memory update;
+   *   V = X3 - X (the DE displacement);
+   *   X = Y where fy < f3, else X3 (a tie keeps the DE survivor).
+   * The F, CR and p fields are not used.  NP >= 4.  Driven by
+   * sevo_state_step only; sevo_state_get's U and fu then hold 2 NP rows
+   * per run (the PSO offspring Y, then the DE trials), part the DE partner
+   * draws, and sevo_state_get_shade / _set_shade reach the SHADE memory. */
+  SEVO_PSODE = 6
 };
 #define SEVO_SHADE_H 100   /* success-history memory slots per run */
 
@@ -256,7 +274,13 @@ int32_t sevo_state_best(const sevo_state* s, double* best);
  * SEVO_ERR_STATE if the budget is already spent or the algorithm is PSO. */
 int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
 
-/* One PSO generation (PSO algorithms only): velocity and position update
+/* One generation of any algorithm (sevo_de_step for DE kinds,
+ * sevo_pso_step for PSO kinds and CSO, the PSODE generation above for
+ * SEVO_PSODE); counts min(per-generation evaluations, budget - fes).
+ * SEVO_ERR_STATE if the budget is already spent. */
+int32_t sevo_state_step(sevo_state* s, uint64_t philox_counter);
+
+/* One PSO generation (PSO algorithms and CSO only): velocity and position update
  * with per-coordinate r1, r2 from the Philox stream at `philox_counter`,
  * clamp to [lb,ub] (velocity zeroed where clamped), evaluation, strict pbest
  * update and guide (gbest or ring lbest) refresh. */
@@ -272,11 +296,13 @@ int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes, int64
  * X, fx (current population and fitness), A (archive rows, asize of them),
  * V, P, fp (PSO velocity, pbest, pbest fitness), U, fu, part (last
  * generation's trial vectors, their fitness and the per-row draws:
- * DE r1,r2,r3,jrand or pbest,r1,r2,jrand; PSO: guide in part[4i]).
- * Arrays are NP x D row-major (ld = D). Synchronizes. */
+ * DE r1,r2,r3,jrand or pbest,r1,r2,jrand; PSO: guide in part[4i]; CSO:
+ * the pairing in part[4i]).  Arrays are NP x D row-major (ld = D); for
+ * SEVO_PSODE, U and fu are 2 NP rows per run (PSO offspring, then DE
+ * trials).  Synchronizes. */
 int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A, int32_t* asize,
                        double* V, double* P, double* fp, double* U, double* fu, int32_t* part);
-/* SHADE runs only (SEVO_ERR_ARG otherwise).  get: the memory (M_F, M_CR: R x
+/* SHADE and PSODE runs only (SEVO_ERR_ARG otherwise).  get: the memory (M_F, M_CR: R x
  * SEVO_SHADE_H, slot-major per run; k: R write positions) and the last
  * generation's per-row F, CR and pbest pool sizes (R x NP); any pointer may be
  * NULL; synchronizes.  set: overwrite the memory (NULL = leave as is). */

@@ -23,7 +23,7 @@ FAMILY_NAMES = ["ellipsoid", "rosenbrock", "rastrigin", "schwefel", "ackley", "g
                 "hybrid", "composition"]
 FP64, TF32, BF16X3, FP32 = 0, 1, 2, 3
 PREC_NAMES = {FP64: "fp64", TF32: "tf32", BF16X3: "bf16x3", FP32: "fp32"}
-DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING, DE_SHADE, CSO = 0, 1, 2, 3, 4, 5
+DE_RAND1, DE_CTPB, PSO_GBEST, PSO_RING, DE_SHADE, CSO, PSODE = 0, 1, 2, 3, 4, 5, 6
 SHADE_H = 100
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED, ERR_STATE = range(-1, -8, -1)
@@ -91,6 +91,7 @@ SIGNATURES = {
     "sevo_state_set_shade": (C.c_int32, [_vp, _dp, _dp, _ip]),
     "sevo_de_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_pso_step": (C.c_int32, [_vp, C.c_uint64]),
+    "sevo_state_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_state_result": (C.c_int32, [_vp, _dp, _i64p, _i64p, _i64p]),
     "sevo_state_get": (C.c_int32, [_vp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _ip]),
     "sevo_state_set": (C.c_int32, [_vp, _dp, _dp, _dp, C.c_int32, _dp, _dp, _dp, C.c_int64]),
@@ -309,9 +310,8 @@ class State:
         return _lib().sevo_pso_step(self.h, counter)
 
     def step(self, counter):
-        if self.params.alg in (DE_RAND1, DE_CTPB, DE_SHADE):
-            return self.de_step(counter)
-        return self.pso_step(counter)
+        """One generation of whatever algorithm the state runs."""
+        return _lib().sevo_state_step(self.h, counter)
 
     def result(self):
         b, f, g, r = C.c_double(), C.c_int64(), C.c_int64(), C.c_int64()
@@ -324,7 +324,8 @@ class State:
         NP, D = self.params.NP * self.R, self.problem.D
         X, fx, A = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, D))
         V, P, fp = np.zeros((NP, D)), np.zeros((NP, D)), np.zeros(NP)
-        U, fu, part = np.zeros((NP, D)), np.zeros(NP), np.zeros((NP, 4), np.int32)
+        ne = 2 * NP if self.params.alg == PSODE else NP  # evaluated rows per generation
+        U, fu, part = np.zeros((ne, D)), np.zeros(ne), np.zeros((NP, 4), np.int32)
         asz = C.c_int32()
         check(_lib().sevo_state_get(self.h, _np_dp(X), _np_dp(fx), _np_dp(A), C.byref(asz),
                                     _np_dp(V), _np_dp(P), _np_dp(fp), _np_dp(U), _np_dp(fu),

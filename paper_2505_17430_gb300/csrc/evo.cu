@@ -671,9 +671,11 @@ __global__ void __launch_bounds__(SEL_THREADS)
                      const GenCtl* __restrict__ ctl, int NP, int use_archive,
                      const double* __restrict__ Fi, const double* __restrict__ CRi,
                      double* __restrict__ MF, double* __restrict__ MCR, int32_t* __restrict__ mk,
-                     int H) {
+                     int H, int count_skip) {
   extern __shared__ __align__(16) unsigned char sel_sm[];
-  de_select_run(fx, fu, asize, action, best, seeds, ctl->count, ctl->gen, NP, use_archive,
+  // the trials follow count_skip rows of this generation in the budget order
+  const int count = max(0, min(ctl->count - count_skip, NP));
+  de_select_run(fx, fu, asize, action, best, seeds, count, ctl->gen, NP, use_archive,
                 blockIdx.x, sel_sm, Fi, CRi, MF, MCR, mk, H);
 }
 
@@ -831,7 +833,37 @@ __global__ void __launch_bounds__(SEL_THREADS)
 }
 
 // ---------------------------------------------------------------- PSO
-// coordinate j of run r's particle i (row ri = r * NP + i)
+// coordinate j of run r's particle i (row ri = r * NP + i), element e:
+// the moved position (returned) and velocity (*vn)
+__device__ __forceinline__ double pso_moved(const double* __restrict__ X,
+                                            const double* __restrict__ V,
+                                            const double* __restrict__ P,
+                                            const int32_t* __restrict__ guide,
+                                            const uint64_t* __restrict__ seeds,
+                                            unsigned long long gen, int NP, int ld, double w,
+                                            double c1, double c2, double lb, double ub, int r,
+                                            int i, int j, int64_t ri, int64_t e, double* vn) {
+  const uint4 rw = sv_draw(seeds[r], (uint32_t)j, (uint32_t)i, (uint32_t)gen, SV_P_PSO);
+  const double r1 = u53_int(rw.x, rw.y), r2 = u53_int(rw.z, rw.w);
+  const double a = __dmul_rn(c1, r1), b = __dmul_rn(c2, r2);
+  const int gi = guide[ri];
+  const double x = X[e];
+  const double gj = P[((int64_t)r * NP + gi) * ld + j];
+  double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
+  double xn = __dadd_rn(x, v);
+  if (lt_key(xn, ord_key(lb))) {
+    xn = lb;
+    v = 0.0;
+  }
+  if (gt_key(xn, ord_key(ub))) {
+    xn = ub;
+    v = 0.0;
+  }
+  *vn = v;
+  return xn;
+}
+
+// the same, in place: x <- moved x, v <- moved v
 __device__ __forceinline__ void pso_move_elem(double* __restrict__ X, double* __restrict__ V,
                                               const double* __restrict__ P,
                                               const int32_t* __restrict__ guide,
@@ -839,27 +871,12 @@ __device__ __forceinline__ void pso_move_elem(double* __restrict__ X, double* __
                                               unsigned long long gen, int NP, int ld, double w,
                                               double c1, double c2, double lb, double ub, int r,
                                               int i, int j, int64_t ri) {
-  {
-    const uint4 rw = sv_draw(seeds[r], (uint32_t)j, (uint32_t)i, (uint32_t)gen, SV_P_PSO);
-    const double r1 = u53_int(rw.x, rw.y), r2 = u53_int(rw.z, rw.w);
-    const double a = __dmul_rn(c1, r1), b = __dmul_rn(c2, r2);
-    const int64_t e = ri * ld + j;
-    const int gi = guide[ri];
-    const double x = X[e];
-    const double gj = P[((int64_t)r * NP + gi) * ld + j];
-    double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
-    double xn = __dadd_rn(x, v);
-    if (lt_key(xn, ord_key(lb))) {
-      xn = lb;
-      v = 0.0;
-    }
-    if (gt_key(xn, ord_key(ub))) {
-      xn = ub;
-      v = 0.0;
-    }
-    X[e] = xn;
-    V[e] = v;
-  }
+  const int64_t e = ri * ld + j;
+  double v;
+  const double xn = pso_moved(X, V, P, guide, seeds, gen, NP, ld, w, c1, c2, lb, ub, r, i, j, ri,
+                              e, &v);
+  X[e] = xn;
+  V[e] = v;
 }
 
 __global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
@@ -968,7 +985,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
                       double* __restrict__ best, const GenCtl* __restrict__ ctl, int NP,
                       int topology, int use_count, int update_best) {
   extern __shared__ double sp_sm[];  // the run's personal-best fitness
-  pso_update_run(fx, fp, flag, guide, best, use_count ? ctl->count : NP, NP, topology,
+  pso_update_run(fx, fp, flag, guide, best, use_count ? min(ctl->count, NP) : NP, NP, topology,
                  update_best, blockIdx.x, sp_sm);
 }
 
@@ -996,6 +1013,72 @@ __global__ void pso_copy_kernel(double* __restrict__ P, const double* __restrict
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fq, fnp);
     pso_copy_elem(P, X, flag, D, ld, sp.row, sp.lo);
+  }
+}
+
+// ---------------------------------------------------------------- PSODE
+// The PSO component's offspring: particle i moves from the population X with
+// the carried velocity V into Y; X and V are left as they are (the moved
+// velocity is not kept: the generation ends by setting V to the DE
+// displacement)
+__global__ void psode_move_kernel(const double* __restrict__ X, const double* __restrict__ V,
+                                  const double* __restrict__ P,
+                                  const int32_t* __restrict__ guide, double* __restrict__ Y,
+                                  const uint64_t* __restrict__ seeds,
+                                  const GenCtl* __restrict__ ctl, int R, int NP, int D, int ld,
+                                  double w, double c1, double c2, double lb, double ub,
+                                  FastDiv fd, FastDiv fnp) {
+  const int64_t total = (int64_t)R * NP * D;
+  const bool fast = total < (1ll << 31);
+  const unsigned long long gen = ctl->gen;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Split3 sp = split3(t, fast, fd, fnp);
+    const int64_t e = sp.row * ld + sp.lo;
+    double v;
+    Y[e] = pso_moved(X, V, P, guide, seeds, gen, NP, ld, w, c1, c2, lb, ub, sp.hi, sp.mid, sp.lo,
+                     sp.row, e, &v);
+  }
+}
+
+// pairwise/3 choice per row, after the DE selection left the survivor's
+// fitness f3 in fx: the PSO offspring is taken when strictly better.  action
+// becomes bit 0 = DE trial accepted, bit 1 = PSO offspring taken.
+__global__ void psode_pick_kernel(double* __restrict__ fx, const double* __restrict__ fy,
+                                  int32_t* __restrict__ action, int64_t rows) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double f3 = fx[t], y = fy[t];
+    const bool take = y < f3;
+    if (take) fx[t] = y;
+    action[t] = (action[t] != -2 ? 1 : 0) | (take ? 2 : 0);
+  }
+}
+
+// per element, one quad of row ri: x3 = u if the DE trial was accepted else
+// x; v <- x3 - x (the DE displacement); x <- y if the PSO offspring was
+// taken else x3
+__global__ void psode_combine_kernel(double* __restrict__ X, const double* __restrict__ U,
+                                     const double* __restrict__ Y, double* __restrict__ V,
+                                     const int32_t* __restrict__ action, int R, int NP, int D,
+                                     int ld, FastDiv fq, FastDiv fnp) {
+  const int nq = (D + 3) >> 2;
+  const int64_t total = (int64_t)R * NP * nq;
+  const bool fast = total < (1ll << 31);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Split3 sp = split3(t, fast, fq, fnp);
+    const int code = action[sp.row];
+    const int j0 = sp.lo * 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (j0 + q >= D) break;
+      const int64_t e = sp.row * ld + j0 + q;
+      const double x = X[e];
+      const double x3 = (code & 1) ? U[e] : x;
+      V[e] = __dsub_rn(x3, x);
+      X[e] = (code & 2) ? Y[e] : x3;
+    }
   }
 }
 
@@ -1376,13 +1459,14 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
     b->cr_thr = (unsigned long long)t;
   }
   b->pbest_k = sv_pbest_k(a->p, a->NP);
-  if (b->alg == SEVO_DE_SHADE) {  // largest pool: round(max(0.2, 2/NP) NP)
+  if (sv_has_shade(b->alg)) {  // largest pool: round(max(0.2, 2/NP) NP)
     const double pm = std::max(0.2, 2.0 / (double)a->NP);
     b->pbest_k = std::min(a->NP, std::max(1, (int)std::floor(pm * (double)a->NP + 0.5)));
   }
   b->small = g_policy_small_runs.load() != 0 && b->D <= SRK_MAX_D && b->NP <= SRK_MAX_NP &&
-             b->alg != SEVO_DE_SHADE && b->alg != SEVO_CSO;
-  b->per_gen = (b->alg == SEVO_CSO) ? b->NP / 2 : b->NP;
+             (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_PSO_GBEST ||
+              b->alg == SEVO_PSO_RING);
+  b->per_gen = (b->alg == SEVO_CSO) ? b->NP / 2 : (b->alg == SEVO_PSODE) ? 2 * b->NP : b->NP;
   b->run_prob = probs;
   b->seg_begin.clear();
   for (int r = 0; r < b->R; ++r)
@@ -1391,14 +1475,15 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   const int64_t rows = (int64_t)b->R * b->NP;
   const size_t mat = al256((size_t)rows * b->ld * 8), vec = al256((size_t)rows * 8),
                ivec = al256((size_t)rows * 4);
-  const bool de = (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE);
-  const bool ctpb = (b->alg == SEVO_DE_CTPB), shade = (b->alg == SEVO_DE_SHADE);
+  const bool de = sv_is_de(b->alg), psode = (b->alg == SEVO_PSODE);
+  const bool ctpb = (b->alg == SEVO_DE_CTPB), shade = sv_has_shade(b->alg);
   size_t bytes = mat /*X*/ + vec /*fx*/ + al256((size_t)b->R * 8) /*best*/ + al256(16) /*err*/ +
                  al256(8) /*refined*/ + al256((size_t)b->R * 8) /*rp*/ +
                  al256((size_t)b->R * 8) /*seeds*/ + al256(sizeof(GenCtl)) + ivec /*guide/flag*/ +
                  al256((size_t)rows * 16) /*part*/ + ivec /*action*/;
-  const bool cso = (b->alg == SEVO_CSO), pso = !de && !cso;
-  if (de || cso) bytes += mat /*U*/ + vec /*fu*/;
+  const bool cso = (b->alg == SEVO_CSO), pso = sv_has_pbest(b->alg);
+  if (de || cso || psode) bytes += mat /*U*/ + vec /*fu*/;
+  if (psode) bytes += mat /*Y*/ + vec /*fy*/;
   if (cso) bytes += mat /*V*/ + ivec /*pair*/ + al256((size_t)b->R * b->ld * 8) /*xbar*/;
   if (ctpb) bytes += mat /*A*/ + al256((size_t)b->R * 4) /*asize*/ + ivec /*order*/;
   if (shade)
@@ -1406,10 +1491,10 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
              al256((size_t)b->R * 4) /*mk*/ + 2 * vec /*Fi, CRi*/ + ivec /*kpb*/;
   if (pso) bytes += 2 * mat /*V,P*/ + vec /*fp*/;
   b->block_bytes = bytes;
-  if (ctpb && rsel_smem_bytes(b->NP) > 48 * 1024)
+  if ((ctpb || shade) && rsel_smem_bytes(b->NP) > 48 * 1024)
     SV_CUDA(cudaFuncSetAttribute(de_rank_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)rsel_smem_bytes(SV_MAX_NP)));
-  if (de && sel_smem_bytes(b->NP) > 48 * 1024)
+  if ((de || psode) && sel_smem_bytes(b->NP) > 48 * 1024)
     SV_CUDA(cudaFuncSetAttribute(de_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sel_smem_bytes(SV_MAX_NP)));
   SV_CUDA(cudaMalloc(&b->block, bytes));
@@ -1434,9 +1519,14 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->U = b->fu = b->A = b->V = b->P = b->fp = nullptr;
   b->asize = b->order = nullptr;
   b->xbar = nullptr;
-  if (de || cso) {
+  b->Y = b->fy = nullptr;
+  if (de || cso || psode) {
     b->U = (double*)take(mat);
     b->fu = (double*)take(vec);
+  }
+  if (psode) {
+    b->Y = (double*)take(mat);
+    b->fy = (double*)take(vec);
   }
   if (cso) {
     b->V = (double*)take(mat);
@@ -1532,7 +1622,7 @@ cudaError_t sv_batch_init(Batch* b) {
   const int tk4 = sv_trace_begin(SEVO_TK_CONTROL, st);
   fill_kernel<<<grid_for(b->R, T), T, 0, st>>>(b->best, b->R, INFINITY);
   sv_trace_end(tk4, st);
-  if (b->alg == SEVO_DE_SHADE) {  // memory: every slot 0.5, write position 0
+  if (sv_has_shade(b->alg)) {  // memory: every slot 0.5, write position 0
     const int64_t hm = (int64_t)b->R * SEVO_SHADE_H;
     const int tkm = sv_trace_begin(SEVO_TK_CONTROL, st);
     fill_kernel<<<grid_for(hm, T), T, 0, st>>>(b->MF, hm, 0.5);
@@ -1544,8 +1634,7 @@ cudaError_t sv_batch_init(Batch* b) {
   const int count0 = (int)std::min<int64_t>(b->budget, b->NP);
   if ((e = sv_ctl_set(b, 0ull, count0)) != cudaSuccess) return e;
   if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
-  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE ||
-      b->alg == SEVO_CSO) {
+  if (!sv_has_pbest(b->alg)) {
     // best-so-far of the initial population (the select kernel's min part
     // with no trials: fu == fx, every row "accepted" onto itself is avoided
     // by using the PSO-style per-run reducer on fx)
@@ -1561,7 +1650,7 @@ cudaError_t sv_batch_init(Batch* b) {
     sv_trace_end(tk6, st);
     const int tk7 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
     pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
-                                                    b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
+                                                    b->ctl, b->NP, sv_topology(b->alg), 1, 1);
     sv_trace_end(tk7, st);
   }
   return cudaGetLastError();
@@ -1585,6 +1674,66 @@ cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens) 
   return e;
 }
 
+// The DE part of a generation: (SHADE parameters,) p-best ranking, trials
+// U from X, their evaluation and the one-to-one selection, whose best-so-far
+// counts the trials after `count_skip` rows of the generation.  Leaves the
+// per-row action for de_apply_kernel / psode_pick_kernel.
+static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int nq = (b->D + 3) >> 2;
+  const int T = 256;
+  const bool shade = sv_has_shade(b->alg);
+  cudaError_t e;
+  if (shade) {
+    const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
+    shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl, b->R,
+                                                        b->NP, SEVO_SHADE_H, b->Fi, b->CRi,
+                                                        b->kpb);
+    sv_trace_end(tks, st);
+  }
+  if (b->alg == SEVO_DE_CTPB || shade) {
+    const int tk_rank = sv_trace_begin(SEVO_TK_DE_RANK, st);
+    // counting rank (O(NP^2) per run, parallel over row blocks) for small
+    // populations; radix select + sort of the candidates above that
+    if (b->NP <= 512) {
+      de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
+                       (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
+    } else {
+      de_rank_select_kernel<<<b->R, RSEL_THREADS, rsel_smem_bytes(b->NP), st>>>(
+          b->fx, b->order, b->NP, pow2_at_least(b->NP), b->pbest_k);
+    }
+    sv_trace_end(tk_rank, st);
+    const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
+    if (shade)
+      de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
+          b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+          b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
+          b->Fi, b->CRi, b->kpb);
+    else
+      de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
+          b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
+          make_fastdiv(b->NP), nullptr, nullptr, nullptr);
+    sv_trace_end(tk8, st);
+  } else {
+    const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
+    de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
+        b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
+        b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
+        nullptr, nullptr, nullptr);
+    sv_trace_end(tk9, st);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
+  const int tk10 = sv_trace_begin(SEVO_TK_DE_SELECT, st);
+  de_select_kernel<<<b->R, SEL_THREADS, sel_smem_bytes(b->NP), st>>>(
+      b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
+      b->alg == SEVO_DE_CTPB, b->Fi, b->CRi, b->MF, b->MCR, b->mk, SEVO_SHADE_H, count_skip);
+  sv_trace_end(tk10, st);
+  return cudaGetLastError();
+}
+
 cudaError_t sv_batch_generation(Batch* b) {
   cudaStream_t st = b->stream;
   if (b->small) {
@@ -1597,58 +1746,42 @@ cudaError_t sv_batch_generation(Batch* b) {
   const int nq = (b->D + 3) >> 2;
   const int T = 256;
   cudaError_t e;
-  if (b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
-    if (b->alg == SEVO_DE_SHADE) {
-      const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-      shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl, b->R,
-                                                          b->NP, SEVO_SHADE_H, b->Fi, b->CRi,
-                                                          b->kpb);
-      sv_trace_end(tks, st);
-    }
-    if (b->alg == SEVO_DE_CTPB || b->alg == SEVO_DE_SHADE) {
-      const int tk_rank = sv_trace_begin(SEVO_TK_DE_RANK, st);
-      // counting rank (O(NP^2) per run, parallel over row blocks) for small
-      // populations; radix select + sort of the candidates above that
-      if (b->NP <= 512) {
-        de_rank_kernel<<<dim3(b->R, (b->NP + RANK_ROWS - 1) / RANK_ROWS), RANK_ROWS,
-                         (size_t)b->NP * 8, st>>>(b->fx, b->order, b->NP, b->pbest_k);
-      } else {
-        de_rank_select_kernel<<<b->R, RSEL_THREADS, rsel_smem_bytes(b->NP), st>>>(
-            b->fx, b->order, b->NP, pow2_at_least(b->NP), b->pbest_k);
-      }
-      sv_trace_end(tk_rank, st);
-      const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-      if (b->alg == SEVO_DE_SHADE)
-        de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
-            b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-            b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
-            b->Fi, b->CRi, b->kpb);
-      else
-        de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
-            b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-            b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
-            make_fastdiv(b->NP), nullptr, nullptr, nullptr);
-      sv_trace_end(tk8, st);
-    } else {
-      const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-      de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
-          b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
-          nullptr, nullptr, nullptr);
-      sv_trace_end(tk9, st);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
-    const int tk10 = sv_trace_begin(SEVO_TK_DE_SELECT, st);
-    de_select_kernel<<<b->R, SEL_THREADS, sel_smem_bytes(b->NP), st>>>(
-        b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
-        b->alg == SEVO_DE_CTPB, b->Fi, b->CRi, b->MF, b->MCR, b->mk, SEVO_SHADE_H);
-    sv_trace_end(tk10, st);
+  if (sv_is_de(b->alg)) {
+    if ((e = de_trials_and_select(b, 0)) != cudaSuccess) return e;
     const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
     de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
                                                          b->D, b->ld, make_fastdiv(nq),
                                                          make_fastdiv(b->NP));
     sv_trace_end(tk11, st);
+  } else if (b->alg == SEVO_PSODE) {
+    // PSO component: offspring Y from the population, personal bests, guides
+    const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
+    psode_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(
+        b->X, b->V, b->P, b->guide, b->Y, b->seeds, b->ctl, b->R, b->NP, b->D, b->ld, b->w, b->c1,
+        b->c2, b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(b->NP));
+    sv_trace_end(tkm, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = eval_rows(b, b->Y, b->fy)) != cudaSuccess) return e;
+    const int tku = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(
+        b->fy, b->fp, b->action, b->guide, b->best, b->ctl, b->NP, 1, 1, 1);
+    sv_trace_end(tku, st);
+    const int tkc = sv_trace_begin(SEVO_TK_PSO_COPY, st);
+    pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->Y, b->action, b->R, b->NP,
+                                                         b->D, b->ld, make_fastdiv(nq),
+                                                         make_fastdiv(b->NP));
+    sv_trace_end(tkc, st);
+    // SHADE component on the population; its trials count after the NP
+    // PSO rows
+    if ((e = de_trials_and_select(b, b->NP)) != cudaSuccess) return e;
+    // pairwise/3 selection and the DE displacement as the next velocity
+    const int tkp = sv_trace_begin(SEVO_TK_DE_APPLY, st);
+    psode_pick_kernel<<<grid_for(rows, T), T, 0, st>>>(b->fx, b->fy, b->action, rows);
+    psode_combine_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(
+        b->X, b->U, b->Y, b->V, b->action, b->R, b->NP, b->D, b->ld, make_fastdiv(nq),
+        make_fastdiv(b->NP));
+    sv_trace_end(tkp, st);
+    sv_note_launch();
   } else if (b->alg == SEVO_CSO) {
     const int half = b->NP / 2;
     const int np2 = pow2_at_least(b->NP);
@@ -1681,7 +1814,7 @@ cudaError_t sv_batch_generation(Batch* b) {
     if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
     const int tk13 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
     pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
-                                                    b->ctl, b->NP, b->alg == SEVO_PSO_RING, 1, 1);
+                                                    b->ctl, b->NP, sv_topology(b->alg), 1, 1);
     sv_trace_end(tk13, st);
     const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
     pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
@@ -1697,7 +1830,7 @@ cudaError_t sv_batch_guides(Batch* b) {
   const int tk15 = sv_trace_begin(SEVO_TK_PSO_UPDATE, b->stream);
   pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, b->stream>>>(b->fp, b->fp, b->action, b->guide,
                                                          b->best, b->ctl, b->NP,
-                                                         b->alg == SEVO_PSO_RING, 0, 0);
+                                                         sv_topology(b->alg), 0, 0);
   sv_trace_end(tk15, b->stream);
   return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ struct Batch {
   double* xbar;                  // CSO: the swarm's mean position per run (R x ld)
   double *MF, *MCR, *Fi, *CRi;  // SHADE memory (R x SEVO_SHADE_H) and per-row F, CR
   int32_t *mk, *kpb;            // SHADE write positions (R) and per-row pbest pools
+  double *Y, *fy;               // PSODE: the PSO offspring and its fitness
   uint64_t* seeds;
   GenCtl* ctl;
   uint32_t* err;  // device error bits accumulated over every evaluation
@@ -64,3 +65,18 @@ cudaError_t sv_batch_guides(Batch* b);
 // read and clear the batch's device error bits (synchronizes its stream)
 int32_t sv_batch_status(Batch* b);
 #define SV_MAX_NP 4096
+
+// algorithm kinds
+inline bool sv_is_de(int alg) {
+  return alg == SEVO_DE_RAND1 || alg == SEVO_DE_CTPB || alg == SEVO_DE_SHADE;
+}
+inline bool sv_is_pso(int alg) {
+  return alg == SEVO_PSO_GBEST || alg == SEVO_PSO_RING || alg == SEVO_CSO;
+}
+// SHADE parameter adaptation (SHADE itself and PSODE's DE component)
+inline bool sv_has_shade(int alg) { return alg == SEVO_DE_SHADE || alg == SEVO_PSODE; }
+// personal bests and guides (PSO kinds except CSO, and PSODE's PSO component)
+inline bool sv_has_pbest(int alg) {
+  return alg == SEVO_PSO_GBEST || alg == SEVO_PSO_RING || alg == SEVO_PSODE;
+}
+inline int sv_topology(int alg) { return (alg == SEVO_PSO_RING || alg == SEVO_PSODE) ? 1 : 0; }

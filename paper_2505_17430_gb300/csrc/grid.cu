@@ -61,9 +61,9 @@ extern "C" int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, v
   }
   for (int a = 0; a < grid->nalgs; ++a) {
     const sevo_alg_params& p = grid->algs[a];
-    const bool de = (p.alg == SEVO_DE_RAND1 || p.alg == SEVO_DE_CTPB || p.alg == SEVO_DE_SHADE);
+    const bool de = sv_is_de(p.alg) || p.alg == SEVO_PSODE;  // NP >= 4
     if (p.alg == SEVO_CSO && (p.NP < 2 || (p.NP & 1))) return SEVO_ERR_ARG;
-    if (p.alg < 0 || p.alg > SEVO_CSO || p.NP > SV_MAX_NP || p.budget < 1 ||
+    if (p.alg < 0 || p.alg > SEVO_PSODE || p.NP > SV_MAX_NP || p.budget < 1 ||
         (de && p.NP < 4) || (!de && p.NP < 2) || !(p.lb < p.ub) || p.prec < 0 || p.prec > 3)
       return SEVO_ERR_ARG;
   }

@@ -14,18 +14,16 @@ struct sevo_state {
   int64_t fes, gens;
 };
 
-static bool is_de(int alg) {
-  return alg == SEVO_DE_RAND1 || alg == SEVO_DE_CTPB || alg == SEVO_DE_SHADE;
-}
+static bool is_de(int alg) { return sv_is_de(alg); }
 
 static int32_t check_params(const sevo_problem* p, const sevo_alg_params* a) {
   if (!p || !a) return SEVO_ERR_ARG;
-  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_CSO) return SEVO_ERR_ARG;
+  if (a->alg < SEVO_DE_RAND1 || a->alg > SEVO_PSODE) return SEVO_ERR_ARG;
   if (a->alg == SEVO_CSO && (a->NP < 2 || (a->NP & 1))) return SEVO_ERR_ARG;
   if (a->prec < SEVO_FP64 || a->prec > SEVO_FP32) return SEVO_ERR_ARG;
   if (a->NP > SV_MAX_NP || a->budget < 1) return SEVO_ERR_ARG;
-  if (is_de(a->alg) && a->NP < 4) return SEVO_ERR_ARG;
-  if (!is_de(a->alg) && a->NP < 2) return SEVO_ERR_ARG;
+  if ((is_de(a->alg) || a->alg == SEVO_PSODE) && a->NP < 4) return SEVO_ERR_ARG;
+  if (a->NP < 2) return SEVO_ERR_ARG;
   if (!(a->lb < a->ub) || !(a->CR >= 0.0 && a->CR <= 1.0)) return SEVO_ERR_ARG;
   if (a->alg == SEVO_DE_CTPB && !(a->p > 0.0 && a->p <= 1.0)) return SEVO_ERR_ARG;
   return SEVO_OK;
@@ -118,9 +116,12 @@ extern "C" int32_t sevo_state_destroy(sevo_state* s) {
   return SEVO_OK;
 }
 
-static int32_t step(sevo_state* s, uint64_t counter, bool want_de) {
+enum StepKind { STEP_DE, STEP_PSO, STEP_ANY };
+
+static int32_t step(sevo_state* s, uint64_t counter, StepKind kind) {
   if (!s) return SEVO_ERR_ARG;
-  if (is_de(s->params.alg) != want_de) return SEVO_ERR_STATE;
+  if (kind == STEP_DE && !is_de(s->params.alg)) return SEVO_ERR_STATE;
+  if (kind == STEP_PSO && !sv_is_pso(s->params.alg)) return SEVO_ERR_STATE;
   if (s->fes >= s->params.budget) return SEVO_ERR_STATE;
   const int count = (int)std::min<int64_t>(s->b.per_gen, s->params.budget - s->fes);
   cudaError_t e = sv_ctl_set(&s->b, (unsigned long long)counter, count);
@@ -135,11 +136,15 @@ static int32_t step(sevo_state* s, uint64_t counter, bool want_de) {
 }
 
 extern "C" int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter) {
-  return step(s, philox_counter, true);
+  return step(s, philox_counter, STEP_DE);
+}
+
+extern "C" int32_t sevo_state_step(sevo_state* s, uint64_t philox_counter) {
+  return step(s, philox_counter, STEP_ANY);
 }
 
 extern "C" int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter) {
-  return step(s, philox_counter, false);
+  return step(s, philox_counter, STEP_PSO);
 }
 
 extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes,
@@ -180,6 +185,36 @@ static cudaError_t get(double* dst, const double* src, const Batch& b) {
                            cudaMemcpyDeviceToHost, b.stream);
 }
 
+// the generation's evaluated rows: U, fu, or for PSODE per run the NP PSO
+// offspring (Y, fy) followed by the NP DE trials (U, fu)
+static cudaError_t get_evaluated(double* U, double* fu, const Batch& b) {
+  if (!b.Y) {
+    cudaError_t e = cudaSuccess;
+    if (U && b.U) e = get(U, b.U, b);
+    if (e == cudaSuccess && fu && b.fu)
+      e = cudaMemcpyAsync(fu, b.fu, (size_t)b.R * b.NP * 8, cudaMemcpyDeviceToHost, b.stream);
+    return e;
+  }
+  const size_t np = (size_t)b.NP;
+  for (int r = 0; r < b.R; ++r) {
+    for (int half = 0; half < 2; ++half) {
+      const double* M = half ? b.U : b.Y;
+      const double* f = half ? b.fu : b.fy;
+      const size_t hrow = (2 * (size_t)r + half) * np;  // first host row
+      cudaError_t e = cudaSuccess;
+      if (U)
+        e = cudaMemcpy2DAsync(U + hrow * b.D, (size_t)b.D * 8, M + (size_t)r * np * b.ld,
+                              (size_t)b.ld * 8, (size_t)b.D * 8, np, cudaMemcpyDeviceToHost,
+                              b.stream);
+      if (e == cudaSuccess && fu)
+        e = cudaMemcpyAsync(fu + hrow, f + (size_t)r * np, np * 8, cudaMemcpyDeviceToHost,
+                            b.stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, double* A,
                                   int32_t* asize, double* V, double* P, double* fp, double* U,
                                   double* fu, int32_t* part) {
@@ -194,8 +229,7 @@ extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, do
   if (V && b.V) SV_CUDA(get(V, b.V, b));
   if (P && b.P) SV_CUDA(get(P, b.P, b));
   if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(fp, b.fp, vb, cudaMemcpyDeviceToHost, b.stream));
-  if (U && b.U) SV_CUDA(get(U, b.U, b));
-  if (fu && b.fu) SV_CUDA(cudaMemcpyAsync(fu, b.fu, vb, cudaMemcpyDeviceToHost, b.stream));
+  SV_CUDA(get_evaluated(U, fu, b));
   if (part) {
     if (s->params.alg == SEVO_CSO) {  // the pairing: part[4i] = pair entry i
       std::vector<int32_t> g(rows);
@@ -205,7 +239,7 @@ extern "C" int32_t sevo_state_get(const sevo_state* s, double* X, double* fx, do
         part[4 * i] = g[i];
         part[4 * i + 1] = part[4 * i + 2] = part[4 * i + 3] = 0;
       }
-    } else if (is_de(s->params.alg)) {
+    } else if (is_de(s->params.alg) || s->params.alg == SEVO_PSODE) {
       SV_CUDA(cudaMemcpyAsync(part, b.part, rows * 16, cudaMemcpyDeviceToHost, b.stream));
     } else {
       std::vector<int32_t> g(rows);
@@ -237,7 +271,7 @@ static int32_t set_impl(sevo_state* s, const double* X, const double* fx, const 
   if (V && b.V) SV_CUDA(put(b.V, V, b));
   if (P && b.P) SV_CUDA(put(b.P, P, b));
   if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(b.fp, fp, vb, cudaMemcpyHostToDevice, b.stream));
-  if (!is_de(s->params.alg) && fp && b.fp) {  // PSO guides from the new pbest fitness
+  if (sv_has_pbest(s->params.alg) && fp && b.fp) {  // guides from the new pbest fitness
     cudaError_t e = sv_batch_guides(&b);
     if (e != cudaSuccess) {
       sv_set_last_cuda_error(e);
@@ -273,14 +307,13 @@ extern "C" int32_t sevo_state_get_async(const sevo_state* s, double* X, double* 
   if (V && b.V) SV_CUDA(get(V, b.V, b));
   if (P && b.P) SV_CUDA(get(P, b.P, b));
   if (fp && b.fp) SV_CUDA(cudaMemcpyAsync(fp, b.fp, vb, cudaMemcpyDeviceToHost, b.stream));
-  if (U && b.U) SV_CUDA(get(U, b.U, b));
-  if (fu && b.fu) SV_CUDA(cudaMemcpyAsync(fu, b.fu, vb, cudaMemcpyDeviceToHost, b.stream));
+  SV_CUDA(get_evaluated(U, fu, b));
   return SEVO_OK;
 }
 
 extern "C" int32_t sevo_state_get_shade(const sevo_state* s, double* MF, double* MCR, int32_t* k,
                                         double* F, double* CR, int32_t* kpb) {
-  if (!s || s->params.alg != SEVO_DE_SHADE) return SEVO_ERR_ARG;
+  if (!s || !sv_has_shade(s->params.alg)) return SEVO_ERR_ARG;
   const Batch& b = s->b;
   const size_t hm = (size_t)b.R * SEVO_SHADE_H * 8, rows = (size_t)b.R * b.NP;
   if (MF) SV_CUDA(cudaMemcpyAsync(MF, b.MF, hm, cudaMemcpyDeviceToHost, b.stream));
@@ -295,7 +328,7 @@ extern "C" int32_t sevo_state_get_shade(const sevo_state* s, double* MF, double*
 
 extern "C" int32_t sevo_state_set_shade(sevo_state* s, const double* MF, const double* MCR,
                                         const int32_t* k) {
-  if (!s || s->params.alg != SEVO_DE_SHADE) return SEVO_ERR_ARG;
+  if (!s || !sv_has_shade(s->params.alg)) return SEVO_ERR_ARG;
   const Batch& b = s->b;
   if (k)
     for (int r = 0; r < b.R; ++r)
@@ -322,11 +355,17 @@ static const uint32_t kMagic = 0x53455642u;  // "SEVB"
 static size_t save_bytes(const sevo_state* s) {
   const size_t m = (size_t)s->b.R * s->b.NP * s->b.D * 8, v = (size_t)s->b.R * s->b.NP * 8;
   size_t n = sizeof(SaveHeader) + m + v;  // X, fx
-  if (s->params.alg == SEVO_DE_CTPB) n += m;        // A
-  if (s->params.alg == SEVO_CSO) n += m;             // V
-  else if (!is_de(s->params.alg)) n += 2 * m + v;   // V, P, fp
-  if (s->params.alg == SEVO_DE_SHADE) n += 2 * SEVO_SHADE_H * 8 + 8;  // M_F, M_CR, k
+  if (s->params.alg == SEVO_DE_CTPB) n += m;              // A
+  if (s->params.alg == SEVO_CSO) n += m;                   // V
+  else if (sv_has_pbest(s->params.alg)) n += 2 * m + v;   // V, P, fp
+  if (sv_has_shade(s->params.alg)) n += 2 * SEVO_SHADE_H * 8 + 8;  // M_F, M_CR, k
   return n;
+}
+
+// offset of the SHADE memory in a saved state: after X, fx and, for PSODE,
+// the PSO component's V, P, fp
+static size_t shade_offset(const sevo_state* s, size_t m, size_t v) {
+  return m + v + (s->params.alg == SEVO_PSODE ? 2 * m + v : 0);
 }
 
 extern "C" int32_t sevo_state_save(const sevo_state* s, void* buf, size_t* size) {
@@ -352,8 +391,8 @@ extern "C" int32_t sevo_state_save(const sevo_state* s, void* buf, size_t* size)
                               is_de(s->params.alg) ? nullptr : (double*)(c + 3 * m + v), nullptr,
                               nullptr, nullptr);
   if (st != SEVO_OK) return st;
-  if (s->params.alg == SEVO_DE_SHADE) {  // memory after the population arrays
-    char* q = c + m + v;
+  if (sv_has_shade(s->params.alg)) {  // memory after the population arrays
+    char* q = c + shade_offset(s, m, v);
     int32_t k = 0;
     st = sevo_state_get_shade(s, (double*)q, (double*)(q + SEVO_SHADE_H * 8), &k, nullptr,
                               nullptr, nullptr);
@@ -384,8 +423,8 @@ extern "C" int32_t sevo_state_load(sevo_state* s, const void* buf, size_t size) 
                               de ? nullptr : (const double*)(c + 2 * m + v),
                               de ? nullptr : (const double*)(c + 3 * m + v), h.fes);
   if (st != SEVO_OK) return st;
-  if (s->params.alg == SEVO_DE_SHADE) {
-    const char* q = c + m + v;
+  if (sv_has_shade(s->params.alg)) {
+    const char* q = c + shade_offset(s, m, v);
     int32_t k = 0;
     std::memcpy(&k, q + 2 * SEVO_SHADE_H * 8, 4);
     st = sevo_state_set_shade(s, (const double*)q, (const double*)(q + SEVO_SHADE_H * 8), &k);

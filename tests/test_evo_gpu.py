@@ -575,3 +575,132 @@ def test_cso_save_load_and_bad_population(S):
     ga, gb = a.get(), b.get()
     assert np.array_equal(ga["X"], gb["X"]) and np.array_equal(ga["V"], gb["V"])
     assert a.result()["best"] == b.result()["best"]
+
+
+# ---------------------------------------------------------------- PSODE
+@pytest.mark.parametrize("fam,D,NP", [(2, 13, 64), (0, 30, 40), (5, 20, 600), (1, 200, 64)])
+def test_psode_lockstep(S, fam, D, NP):
+    """Four PSODE generations in lock step with the oracle's operators: the
+    PSO offspring bit-identical to the oracle's move (ring guides from the
+    personal bests, carried velocity), personal bests updated from the GPU's
+    fitness exactly as the oracle does, SHADE parameters, partners and
+    trials as in the SHADE lock-step test, and the pairwise/3 selection and
+    DE displacement bit-identical given the GPU's fitness; every fitness
+    within the FP64 tolerance.  NP = 600 takes the radix-select ranking,
+    D = 200 the large-D evaluation."""
+    seed = 41
+    p, q = S.Problem(600 + fam, fam, D), O.Problem(600 + fam, fam, D)
+    st = S.State(p, S.alg_params(S.PSODE, NP, 10 ** 7), seed)
+    X = O.init_population(seed, NP, D)
+    fx = q.eval(X)
+    V = np.random.default_rng(fam).uniform(-5, 5, (NP, D))
+    P = X + np.random.default_rng(fam + 1).uniform(-1, 1, (NP, D))
+    fp = q.eval(P)
+    MF, MCR, k = O.shade_memory()
+    for gen in range(1, 5):
+        st.set(X=X, fx=fx, V=V, P=P, fp=fp, fes=NP)
+        st.set_shade(MF, MCR, k)
+        assert st.step(gen) == 0
+        g, sh = st.get(), st.get_shade()
+        assert g["U"].shape == (2 * NP, D)
+        Y, _ = O.pso_move(seed, gen, X, V, P, O.pso_guides(fp, 1))
+        assert np.array_equal(g["U"][:NP], Y)
+        fy = g["fu"][:NP]
+        want = q.eval(Y)
+        assert (np.abs(fy - want) <= tol64(want, q.scale(Y))).all()
+        P2, fp2, _ = O.pso_update(Y, fy, P, fp)
+        assert np.array_equal(g["P"], P2) and np.array_equal(g["fp"], fp2)
+        Fo, CRo, kpbo = O.shade_params(seed, gen, NP, MF, MCR)
+        assert np.array_equal(sh["kpb"], kpbo)
+        assert np.allclose(sh["F"], Fo, rtol=1e-13, atol=0)
+        U, part = O.shade_trials(seed, gen, X, fx, sh["F"], sh["CR"], sh["kpb"])
+        assert np.array_equal(g["part"], part) and np.array_equal(g["U"][NP:], U)
+        fu = g["fu"][NP:]
+        want = q.eval(U)
+        assert (np.abs(fu - want) <= tol64(want, q.scale(U))).all()
+        MFo, MCRo, ko, _ = O.shade_update(fx, fu, sh["F"], sh["CR"], MF, MCR, k)
+        assert int(sh["k"][0]) == ko
+        assert np.allclose(sh["MF"][0], MFo, rtol=1e-13, atol=0)
+        X3, f3, _, _, _ = O.de_select(seed, gen, X, fx, U, fu)
+        Xn, fn, Vn = O.psode_select(X, Y, fy, X3, f3)
+        assert np.array_equal(g["X"], Xn) and np.array_equal(g["fx"], fn)
+        assert np.array_equal(g["V"], Vn)
+        X, fx, V, P, fp = Xn, fn, Vn, P2, fp2
+        MF, MCR, k = sh["MF"][0], sh["MCR"][0], int(sh["k"][0])
+
+
+def test_psode_budget_counts_pso_rows_first(S):
+    """A budget ending inside a generation: the last generation counts its
+    first PSO offspring only (budget - fes < NP) or all PSO offspring and
+    the first DE trials; the best-so-far is the minimum over exactly the
+    counted evaluations, fes stops at the budget, and a further step is
+    refused."""
+    NP, D = 24, 9
+    p = S.Problem(8, S.ACKLEY, D)
+    for extra in (NP // 2 + 1, NP + 7):
+        budget = NP + 2 * NP * 2 + extra
+        st = S.State(p, S.alg_params(S.PSODE, NP, budget), 5)
+        counted = [st.get()["fx"]]
+        for gen in range(1, 4):
+            assert st.step(gen) == 0
+            fe = st.get()["fu"]
+            counted.append(fe if gen < 3 else fe[:extra])
+        r = st.result()
+        assert r["fes"] == budget and r["gens"] == 3
+        assert r["best"] == min(float(np.min(c)) for c in counted)
+        assert st.step(4) == S.ERR_STATE
+
+
+def test_psode_full_run_and_grid(S):
+    """PSODE (NP = 50) on the shifted-rotated Rosenbrock at D = 10 reaches
+    1e-8 in 1e5 evaluations (2 NP per generation) like the oracle's control
+    run; a grid of PSODE runs equals the same runs driven alone."""
+    D, NP, budget = 10, 50, 100000
+    p = S.Problem(3, S.ROSENBROCK, D)
+    a = S.alg_params(S.PSODE, NP, budget)
+    res = S.sevo_run_grid([p], [a], [(0, 0, s) for s in (1, 2)])
+    assert res["success"].all(), res["best"]
+    assert (res["gens"] == 1000).all() and (res["fes"] == budget).all()
+    st = S.State(p, a, 2)
+    g = 0
+    while st.result()["fes"] < budget:
+        g += 1
+        st.step(g)
+    assert st.result()["best"] == res["best"][1] and st.result()["gens"] == res["gens"][1]
+
+
+def test_psode_save_load_and_step_kinds(S):
+    """A saved PSODE state (population, velocity, personal bests, SHADE
+    memory) resumes bit-identically; the DE-only and PSO-only step entries
+    refuse a PSODE state."""
+    p = S.Problem(9, S.RASTRIGIN, 12)
+    a = S.State(p, S.alg_params(S.PSODE, 40, 10 ** 6), 4)
+    assert a.de_step(1) == S.ERR_STATE and a.pso_step(1) == S.ERR_STATE
+    for g in range(1, 4):
+        assert a.step(g) == 0
+    blob = a.save()
+    b = S.State(p, S.alg_params(S.PSODE, 40, 10 ** 6), 77)
+    b.load(blob)
+    for g in range(4, 8):
+        a.step(g)
+        b.step(g)
+    ga, gb = a.get(), b.get()
+    for key in ("X", "fx", "V", "P", "fp"):
+        assert np.array_equal(ga[key], gb[key]), key
+    assert np.array_equal(a.get_shade()["MF"], b.get_shade()["MF"])
+    assert a.result()["best"] == b.result()["best"]
+
+
+@pytest.mark.parametrize("alg", ["DE_SHADE", "PSODE"])
+def test_shade_kinds_at_largest_population(S, alg):
+    """NP = 4096 (the largest population) needs more than the default 48 KB
+    of shared memory for the p-best ranking: two generations run and the
+    pools stay within 2 .. 0.2 NP."""
+    NP, D = 4096, 8
+    p = S.Problem(2, S.SCHWEFEL, D)
+    st = S.State(p, S.alg_params(getattr(S, alg), NP, 10 ** 7), 3)
+    for g in (1, 2):
+        assert st.step(g) == 0
+    sh = st.get_shade()
+    assert sh["kpb"].min() >= 2 and sh["kpb"].max() <= round(0.2 * NP)
+    assert np.isfinite(st.result()["best"])
