@@ -358,6 +358,34 @@ def shade_sec31(S):
     return out
 
 
+def psode_case1(S):
+    """The paper's PSODE case study shape (Sec. 4, Listing 4): population 100,
+    D = 30, 1000 D evaluations, bounds [-100, 100], Rosenbrock, float -- 10
+    runs batched through sevo_run_grid in FP32 and FP64, against the oracle
+    running the same 10 runs one after another on one host core."""
+    import numpy as np
+    import oracle as O
+    D, NP, budget, runs = 30, 100, 30000, 10
+    p = S.Problem(0x5EB00003, 1, D)
+    out = {"workload": "PSODE (ring PSO + SHADE, pairwise/3) NP=100, 30,000 evals, 10 runs, "
+                       "shifted-rotated Rosenbrock D=30"}
+    for name, prec in (("fp32", S.FP32), ("fp64", S.FP64)):
+        a = S.alg_params(S.PSODE, NP, budget, prec=prec)
+        S.sevo_run_grid([p], [a], [(0, 0, 1)])  # warm-up
+        t0 = time.perf_counter()
+        r = S.sevo_run_grid([p], [a], [(0, 0, s) for s in range(1, runs + 1)])
+        wall = time.perf_counter() - t0
+        out[name] = {"wall_s_10_runs": round(wall, 4), "mean_s_per_run": round(wall / runs, 5),
+                     "median_final_error": float(np.median(r["best"]))}
+    q = O.Problem(0x5EB00003, 1, D)
+    t0 = time.perf_counter()
+    ob = [O.run(q, O.make_alg(O.ALG_PSODE, NP, budget), s)["best"] for s in range(1, runs + 1)]
+    owall = time.perf_counter() - t0
+    out["oracle"] = {"wall_s_10_runs": round(owall, 4), "mean_s_per_run": round(owall / runs, 5),
+                     "median_final_error": float(np.median(ob)), "cores": 1}
+    return out
+
+
 def cso_sec33(S):
     """The paper's CSO shape (Sec. 3.3): swarm 300, 1e6 evaluations, 1000-D,
     5 runs, float -- here on the shifted-rotated Rastrigin (the trigonometric
@@ -727,6 +755,7 @@ def main():
     c4 = None if args.no_large_d else c4_sample(S)
     c0 = c0_single_run(S)
     sh31 = shade_sec31(S)
+    psode4 = psode_case1(S)
     cso33 = None if args.no_large_d else cso_sec33(S)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     grid = None
@@ -766,8 +795,9 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
-            "kernel_shares": shares, "eval_only_evals_per_s": modes, "large_d": large,
-            "c4_sample": c4, "shade_sec31": sh31, "cso_sec33": cso33,
+            "kernel_shares": shares, "kernel_shares_alone": shares1,
+            "eval_only_evals_per_s": modes, "large_d": large,
+            "c4_sample": c4, "shade_sec31": sh31, "psode_case1": psode4, "cso_sec33": cso33,
             "c0_single_run": c0, "grid": grid}
     print(json.dumps(line), flush=True)
     if dist:
