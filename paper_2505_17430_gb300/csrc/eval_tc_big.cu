@@ -473,14 +473,21 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   g.D = h.D;
   g.kpad = h.kpad;
   g.nkb = h.kpad / (bf16 ? 64 : 32);
-  // N tile: 256 columns (3/4 of the operand bytes per flop of a 128-column
-  // tile) when the jobs still fill every SM -- once for TF32 (4 stages of 48
-  // KB), twice for BF16X3, whose 96 KB stages leave room for only two and
-  // whose last partial wave then costs more (measured at D = 5000 x 1,024
-  // rows: 172 us with 256-column tiles, 153 us with 128)
+  // N tile: the width whose whole waves of persistent jobs finish first,
+  // ceil(jobs / SMs) x the cost of one job.  A 256-column job reads 3/4 of
+  // the operand bytes per flop of a 128-column one and measured 1.7x the
+  // flop rate in TF32 (4 stages either way) but only 1.2x in BF16X3 (its 96 KB
+  // stages leave room for two).  Measured whole calls (128 vs 256 columns):
+  // TF32 D = 5000 x 1,024 rows 256 vs 196 us, D = 300 x 10,200 rows 48 vs
+  // 52 us; BF16X3 D = 2000 x 4,096 rows 141 vs 122 us, D = 5000 x 1,024 rows
+  // 153 vs 172 us.
   const int64_t tiles = (N + BM - 1) / BM;
+  const int64_t sms = sv_num_sms();
   const int64_t jobs256 = tiles * ((h.npad + 255) / 256);
-  const int BN = (jobs256 >= (int64_t)sv_num_sms() * (bf16 ? 2 : 1)) ? 256 : 128;
+  const int64_t jobs128 = tiles * ((h.npad + 127) / 128);
+  const double t256 = (double)((jobs256 + sms - 1) / sms) * (2.0 / (bf16 ? 1.2 : 1.7));
+  const double t128 = (double)((jobs128 + sms - 1) / sms);
+  const int BN = (t256 < t128) ? 256 : 128;
   const int NB = BN / 128;
   g.nchunks = (h.npad + BN - 1) / BN;
   g.nsub = g.nchunks * WPQ;

@@ -221,12 +221,14 @@ def test_tensor_core_d5000_sampled(S):
 
 @pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
 @pytest.mark.parametrize("fam", FAMS)
-@pytest.mark.parametrize("D,N", [(300, 10200), (1000, 4990)])
+@pytest.mark.parametrize("D,N", [(300, 19456), (1000, 4990), (500, 9700)])
 def test_tensor_core_large_d_wide_tiles_sampled(S, prec, fam, D, N):
-    """Enough rows that the large-D GEMM uses 256-column N tiles (two TMEM
-    accumulators, 64-column epilogue slices; at D = 300 the second tile is
-    half past the padded rotation): sampled rows, the near-optimum probes and
-    the ragged last row tile checked against the oracle."""
+    """Enough rows that the large-D GEMM takes 256-column N tiles (two TMEM
+    accumulators, 64-column epilogue slices) by its wave-count rule: TF32 at
+    all three sizes (at D = 300 the second tile is half past the padded
+    rotation), BF16X3 at D = 500 x 9,700 rows (128-column tiles at the other
+    two); sampled rows, the near-optimum probes and the ragged last row tile
+    checked against the oracle."""
     seed = 901 + 11 * fam + D
     p, q = S.Problem(seed, fam, D), O.Problem(seed, fam, D)
     X = inputs.uniform_pop(N, D, seed=seed)
