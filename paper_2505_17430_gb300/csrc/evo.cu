@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "bodies.cuh"
+#include "bounds.cuh"
 #include "evo.cuh"
 #include "tc_ptx.cuh"
 
@@ -47,23 +48,6 @@ __device__ __forceinline__ long long fkey(double f) {
 }
 
 __device__ __forceinline__ double dmin_pos(double a, double b) { return (b < a) ? b : a; }
-
-// IEEE x < y and x > y against a finite bound, decided on the bit patterns
-// with integer instructions (GB300's FP64 pipe is the scarce unit in the
-// generation kernels): -0.0 and +0.0 get the same key, NaN compares false.
-__device__ __forceinline__ long long ord_key(double x) {
-  const long long b = __double_as_longlong(x);
-  return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFll) : b;
-}
-__device__ __forceinline__ bool not_nan(double x) {
-  return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) <= 0x7FF0000000000000ll;
-}
-__device__ __forceinline__ bool lt_key(double x, long long ky) {
-  return not_nan(x) && ord_key(x) < ky;
-}
-__device__ __forceinline__ bool gt_key(double x, long long ky) {
-  return not_nan(x) && ord_key(x) > ky;
-}
 
 // v * 0.5, exactly as IEEE multiplication rounds it, with integer
 // instructions: a normal result only loses one from the exponent; when the
@@ -262,7 +246,7 @@ __device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, doub
   load_quad(d1, j0, D, v1);
   load_quad(d2, j0, D, v2);
   load_quad(d3, j0, D, v3);
-  const long long lbk = ord_key(lb), ubk = ord_key(ub);
+  const SvBound lbb = sv_bound(lb), ubb = sv_bound(ub);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int j = j0 + q;
@@ -279,10 +263,10 @@ __device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, doub
     // With the parent inside the bounds at most one of them applies, so one
     // FP64 add with the bound chosen by a select; the second check only
     // fires for parents outside the bounds (populations set by the caller)
-    const bool lo = lt_key(u, lbk), hi = gt_key(u, ubk);
+    const bool lo = sv_lt_bound(u, lbb), hi = sv_gt_bound(u, ubb);
     if (lo || hi) {
       u = half_exact(__dadd_rn(lo ? lb : ub, x));
-      if (lo && gt_key(u, ubk)) u = half_exact(__dadd_rn(ub, x));
+      if (lo && sv_gt_bound(u, ubb)) u = half_exact(__dadd_rn(ub, x));
     }
     ui[j] = u;
   }
@@ -791,7 +775,7 @@ __global__ void cso_update_kernel(double* __restrict__ X, double* __restrict__ V
   const int64_t total = (int64_t)R * half * D;
   const bool fast = total < (1ll << 31);
   const unsigned long long gen = ctl->gen;
-  const long long lbk = ord_key(lb), ubk = ord_key(ub);
+  const SvBound lbb = sv_bound(lb), ubb = sv_bound(ub);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fd, fhalf);
@@ -809,8 +793,8 @@ __global__ void cso_update_kernel(double* __restrict__ X, double* __restrict__ V
                  __fma_rn(R2, __dsub_rn(xw, xl),
                           __dmul_rn(__dmul_rn(phi, R3), __dsub_rn(xbar[(int64_t)r * ld + j], xl))));
     double x = __dadd_rn(xl, v);
-    if (lt_key(x, lbk)) x = lb;
-    if (gt_key(x, ubk)) x = ub;
+    if (sv_lt_bound(x, lbb)) x = lb;
+    if (sv_gt_bound(x, ubb)) x = ub;
     V[el] = v;
     X[el] = x;
     U[((int64_t)r * half + k) * ld + j] = x;
@@ -851,11 +835,11 @@ __device__ __forceinline__ double pso_moved(const double* __restrict__ X,
   const double gj = P[((int64_t)r * NP + gi) * ld + j];
   double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
   double xn = __dadd_rn(x, v);
-  if (lt_key(xn, ord_key(lb))) {
+  if (sv_lt_bound(xn, sv_bound(lb))) {
     xn = lb;
     v = 0.0;
   }
-  if (gt_key(xn, ord_key(ub))) {
+  if (sv_gt_bound(xn, sv_bound(ub))) {
     xn = ub;
     v = 0.0;
   }
