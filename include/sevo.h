@@ -271,7 +271,8 @@ int32_t sevo_state_best(const sevo_state* s, double* best);
  * repair -- Listing 1), their evaluation, one-to-one selection f(u) <= f(x)
  * and, for current-to-pbest, archive insertion of replaced parents.
  * Counts min(NP, budget - fes) evaluations toward best-so-far.
- * SEVO_ERR_STATE if the budget is already spent or the algorithm is PSO. */
+ * SEVO_ERR_STATE if the budget is already spent or the algorithm is not one
+ * of SEVO_DE_RAND1, SEVO_DE_CTPB, SEVO_DE_SHADE. */
 int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
 
 /* One generation of any algorithm (sevo_de_step for DE kinds,
@@ -280,10 +281,12 @@ int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
  * SEVO_ERR_STATE if the budget is already spent. */
 int32_t sevo_state_step(sevo_state* s, uint64_t philox_counter);
 
-/* One PSO generation (PSO algorithms and CSO only): velocity and position update
- * with per-coordinate r1, r2 from the Philox stream at `philox_counter`,
- * clamp to [lb,ub] (velocity zeroed where clamped), evaluation, strict pbest
- * update and guide (gbest or ring lbest) refresh. */
+/* One PSO generation (SEVO_PSO_GBEST, SEVO_PSO_RING and SEVO_CSO only;
+ * SEVO_ERR_STATE otherwise or once the budget is spent): velocity and
+ * position update with per-coordinate r1, r2 from the Philox stream at
+ * `philox_counter`, clamp to [lb,ub] (velocity zeroed where clamped),
+ * evaluation, strict pbest update and guide (gbest or ring lbest) refresh;
+ * CSO runs the generation described at SEVO_CSO. */
 int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter);
 
 /* Synchronize the state's stream and read the run's bookkeeping (host).
