@@ -616,6 +616,24 @@ def cpu_baseline(npop=NP, steps=30):
                       f"NP={npop} (the workload's operators and evaluation, {ev} evals)"}
 
 
+def max_over_ranks(ms, dist=None):
+    """The timed region's milliseconds, the maximum over all ranks (every
+    rank receives it); the ranks then meet at a barrier.  One process: ms."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(evals_per_step, world, ms_per_step):
+    """Evaluations per second of the whole job: every rank runs its own
+    replica of the step's evaluations, timed by the slowest rank."""
+    return evals_per_step * world / (ms_per_step * 1e-3)
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -717,14 +735,10 @@ def main():
     ms, gen = time_steps(torch, states, gen, args.steps)
     launches = S.lib().sevo_kernel_launches() - l0
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(ms, dist)
     evals_per_step = sum(st.R * NP for st in states)
     ms_per_step = ms / args.steps
-    value = evals_per_step * world / (ms_per_step * 1e-3)
+    value = whole_job_rate(evals_per_step, world, ms_per_step)
 
     if rank != 0 or args.only_steps:
         if args.only_steps and rank == 0:

@@ -144,3 +144,43 @@ def test_comp_hybrid_generation_matches_oracle(D):
         assert np.array_equal(e["gsize"][:len(gs)], gs) and np.array_equal(e["gbody"][:len(gb)], gb)
         assert np.array_equal(e["sigma"], sig) and np.array_equal(e["lambda"], lam)
         assert np.array_equal(e["bias"], bias)
+
+
+def _grid_status(p, a):
+    """sevo_run_grid's status for one task of algorithm a on problem p
+    (called directly, default stream, no device needed to be refused)."""
+    import ctypes as C
+    ph = (C.c_void_p * 1)(p.h.value)
+    aa = (S.AlgParams * 1)(a)
+    tt = (S.Task * 1)(S.Task(0, 0, 1))
+    best, fes, gens = np.zeros(1), np.zeros(1, np.int64), np.zeros(1, np.int64)
+    succ = np.zeros(1, np.int32)
+    g = S.Grid(1, C.cast(ph, C.POINTER(C.c_void_p)), 1, C.cast(aa, C.POINTER(S.AlgParams)), 1,
+               C.cast(tt, C.POINTER(S.Task)), 0)
+    i64 = C.POINTER(C.c_int64)
+    r = S.GridResult(best.ctypes.data_as(C.POINTER(C.c_double)), fes.ctypes.data_as(i64),
+                     gens.ctypes.data_as(i64), succ.ctypes.data_as(C.POINTER(C.c_int32)), 0.0, 0)
+    return S.lib().sevo_run_grid(C.byref(g), C.byref(r), None)
+
+
+def test_algorithm_parameter_validation_without_device():
+    """Every algorithm's parameters are checked before any device work: the
+    state, the grid and the step entries refuse what the header rules out
+    (unknown algorithm, PSODE and the DE kinds below NP = 4, CSO with an odd
+    swarm, empty bounds) with SEVO_ERR_ARG, and a null state with
+    SEVO_ERR_ARG from every step entry."""
+    import ctypes as C
+    lib = S.lib()
+    p = S.Problem(3, S.RASTRIGIN, 10)
+    bad = [S.alg_params(7, 40, 1000), S.alg_params(-1, 40, 1000),
+           S.alg_params(S.PSODE, 3, 1000), S.alg_params(S.DE_SHADE, 3, 1000),
+           S.alg_params(S.CSO, 41, 1000), S.alg_params(S.PSODE, 40, 0),
+           S.alg_params(S.PSODE, 40, 1000, lb=5.0, ub=5.0)]
+    for a in bad:
+        out = C.c_void_p()
+        assert lib.sevo_state_create(p.h, C.byref(a), 1, None, C.byref(out)) == S.ERR_ARG
+        assert not out.value
+        assert _grid_status(p, a) == S.ERR_ARG
+    for step in (lib.sevo_state_step, lib.sevo_de_step, lib.sevo_pso_step):
+        assert step(None, 1) == S.ERR_ARG
+    assert lib.sevo_state_get_shade(None, None, None, None, None, None, None) == S.ERR_ARG
