@@ -136,7 +136,7 @@ def test_pso_lockstep(S, policy, alg):
 
 
 def test_c0_full_run_lockstep(S, policy):
-    """configs[0]: DE/rand/1/bin, NP=50, D=10, F=.5, CR=.9, FP64, budget 1e5
+    """The smallest workload: DE/rand/1/bin, NP=50, D=10, F=.5, CR=.9, FP64, budget 1e5
     on shifted-rotated Rastrigin; every one of the 1999 generations is
     compared in lock step (re-synchronised from the oracle each time)."""
     NP, D, budget, seed = 50, 10, 100000, 1
