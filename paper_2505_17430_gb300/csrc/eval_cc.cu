@@ -12,6 +12,8 @@
 // fixed shuffle order (deterministic), carrying the Rosenbrock pair across
 // chunk borders.
 #include "bodies.cuh"
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace {
@@ -286,15 +288,35 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
 
 }  // namespace
 
+namespace {
+constexpr int SV_MAX_DEVICES = 64;
+std::atomic<int> g_sms[SV_MAX_DEVICES];                 // 0: not read yet
+std::atomic<uint32_t> g_once[SV_MAX_DEVICES];           // bit k: slot k done
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SV_MAX_DEVICES) dev = 0;
+  return dev;
+}
+}  // namespace
+
 int sv_num_sms() {
-  static int n = 0;
+  const int dev = current_device();
+  int n = g_sms[dev].load(std::memory_order_acquire);
   if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+    g_sms[dev].store(n, std::memory_order_release);
   }
   return n;
+}
+
+cudaError_t sv_once_per_device(int slot, cudaError_t (*step)()) {
+  const int dev = current_device();
+  const uint32_t bit = 1u << slot;
+  if (g_once[dev].load(std::memory_order_acquire) & bit) return cudaSuccess;
+  const cudaError_t e = step();
+  if (e == cudaSuccess) g_once[dev].fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t row0,

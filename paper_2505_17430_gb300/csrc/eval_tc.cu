@@ -620,6 +620,17 @@ size_t sv_eval_tc_scratch_bytes(bool any_comp, int, int64_t rows) {
   return any_comp ? (size_t)rows * SV_MAXC * 16 : 0;
 }
 
+// the fused kernel's dynamic shared memory above the default 48 KB (once per device)
+static cudaError_t set_fused_smem() {
+  const int lim = 224 * 1024;  // opt-in maximum minus this kernel's static shared memory
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(eval_tc_fused<true, true>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<true, false>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, true>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, false>, a, lim);
+  return e;
+}
+
 cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const double* X,
                                 int64_t ld, double* out, int32_t* list, const int64_t* list_off,
                                 int32_t* counts, uint32_t* nonfinite, void* scratch,
@@ -641,22 +652,9 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
   const bool use_xtma = xtma && g.nxb >= 2;
   const size_t smem = use_xtma ? fixed + (size_t)g.nxb * g.xb_bytes
                                : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const int lim = 224 * 1024;  // opt-in maximum minus this kernel's static shared memory
-    cudaError_t e = cudaFuncSetAttribute(eval_tc_fused<true, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(eval_tc_fused<true, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(eval_tc_fused<false, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(eval_tc_fused<false, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  {
+    const cudaError_t e = sv_once_per_device(SV_ONCE_FUSED_SMEM, set_fused_smem);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   SegTable T;
   T.nseg = nseg;

@@ -456,6 +456,17 @@ size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
   return b;
 }
 
+// the GEMM's dynamic shared memory above the default 48 KB (once per device)
+static cudaError_t set_big_smem() {
+  const int lim = 200 * 1024;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(gemm_big_kernel<true, 128>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<true, 256>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 128>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 256>, a, lim);
+  return e;
+}
+
 cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int64_t ld,
                            double* out, int32_t* list, int64_t list_off, int32_t* count,
                            uint32_t* nonfinite, void* scratch, size_t scratch_bytes,
@@ -523,16 +534,9 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     mAlo = mA;
   }
   const size_t smem = (size_t)g.stages * g.stage_bytes + 1024;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const int lim = 200 * 1024;
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(gemm_big_kernel<true, 128>, a, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<true, 256>, a, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 128>, a, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 256>, a, lim);
+  {
+    const cudaError_t e = sv_once_per_device(SV_ONCE_BIG_SMEM, set_big_smem);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const int cvt_grid =
       (int)std::min<int64_t>((N + CVT_WARPS - 1) / CVT_WARPS, (int64_t)sv_num_sms() * 8);

@@ -30,7 +30,15 @@ struct RefineTable {
   unsigned long long* total;  // running count of refined rows (null: none)
 };
 
+// SM count of the current device (cached per device)
 int sv_num_sms();
+// Run a one-time setup step (kernel attributes, which are per device) on the
+// current device: `step` runs until it first succeeds on each device; `slot`
+// names the step (0 .. SV_ONCE_SLOTS - 1).  Safe to call from several host
+// threads (the step may then run more than once; it must be idempotent).
+constexpr int SV_ONCE_SLOTS = 8;
+enum : int { SV_ONCE_FUSED_SMEM = 0, SV_ONCE_BIG_SMEM = 1 };
+cudaError_t sv_once_per_device(int slot, cudaError_t (*step)());
 
 // CUDA-core evaluation of one segment: prec SEVO_FP64 (plain path) or SEVO_FP32
 cudaError_t sv_eval_cc(const ProblemDev* Pd, int prec, const double* X, int64_t ld, int64_t row0,
