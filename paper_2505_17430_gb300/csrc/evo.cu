@@ -1435,7 +1435,6 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->budget = a->budget;
   b->prec = a->prec;
   b->stream = st;
-  b->refined_host = 0;
   {
     double t = std::ceil(a->CR * 4294967296.0);
     if (t < 0) t = 0;

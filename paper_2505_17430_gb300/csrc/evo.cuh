@@ -44,7 +44,6 @@ struct Batch {
   size_t eval_bytes;
   bool any_comp;
   cudaStream_t stream;
-  int64_t refined_host;  // unused (the device counter `refined` is read instead)
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
