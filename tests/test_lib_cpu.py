@@ -184,3 +184,24 @@ def test_algorithm_parameter_validation_without_device():
     for step in (lib.sevo_state_step, lib.sevo_de_step, lib.sevo_pso_step):
         assert step(None, 1) == S.ERR_ARG
     assert lib.sevo_state_get_shade(None, None, None, None, None, None, None) == S.ERR_ARG
+
+
+def test_enum_constants_match_header_and_oracle():
+    """The binding's family, precision and algorithm numbers are the header's
+    enums, and the oracle (written independently) numbers families and
+    algorithms the same way."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sevo.h")).read(), flags=re.S)
+    enum = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bSEVO_([A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    fam = {"ELLIPSOID": S.ELLIPSOID, "ROSENBROCK": S.ROSENBROCK, "RASTRIGIN": S.RASTRIGIN,
+           "SCHWEFEL": S.SCHWEFEL, "ACKLEY": S.ACKLEY, "GRIEWANK": S.GRIEWANK,
+           "HYBRID": S.HYBRID, "COMPOSITION": S.COMPOSITION, "COMP_HYBRID": S.COMP_HYBRID}
+    alg = {"DE_RAND1": S.DE_RAND1, "DE_CTPB": S.DE_CTPB, "PSO_GBEST": S.PSO_GBEST,
+           "PSO_RING": S.PSO_RING, "DE_SHADE": S.DE_SHADE, "CSO": S.CSO, "PSODE": S.PSODE}
+    prec = {"FP64": S.FP64, "TF32": S.TF32, "BF16X3": S.BF16X3, "FP32": S.FP32}
+    for table in (fam, alg, prec):
+        for name, v in table.items():
+            assert enum.get(name) == v, name
+    assert [O.ELLIPSOID, O.ROSENBROCK, O.RASTRIGIN, O.SCHWEFEL, O.ACKLEY, O.GRIEWANK, O.HYBRID,
+            O.COMPOSITION, O.COMP_HYBRID] == [fam[k] for k in fam]
+    assert [O.ALG_DE_RAND1, O.ALG_DE_CTPB, O.ALG_PSO_GBEST, O.ALG_PSO_RING, O.ALG_DE_SHADE,
+            O.ALG_CSO, O.ALG_PSODE] == [alg[k] for k in alg]
