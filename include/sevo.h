@@ -14,9 +14,8 @@
  *   - the runner takes (algorithm, suite, observer, independent runs)
  *     (Sec. 2.4, Listing 3) and records the best-so-far error
  *     (Sec. 2.4, Sec. 3.2).
- * The paper prints no formula for any body, transform or operator; the
- * readings this library implements are listed, one by one, in the project's
- * design notes, and each function below says which it uses.
+ * The paper prints no formula for any body, transform or operator; each
+ * function below states the reading of the paper it implements.
  *
  * Conventions for every call:
  *   - returns int32 status: SEVO_OK (0) or a negative SEVO_ERR_* code; the
@@ -167,6 +166,13 @@ int32_t sevo_evaluate_sync(const sevo_problem* p, const double* pop, int64_t N, 
  * in one fixed device array of SEVO_NOALLOC_SCRATCH_BYTES owned by the
  * library; it calls no cudaMalloc/cudaFree and no allocating routine.
  *   - N must be at most SEVO_NOALLOC_MAX_ROWS, else SEVO_ERR_UNSUPPORTED;
+ *     in SEVO_TF32 / SEVO_BF16X3 at D > 128 the converted operand and the
+ *     per-slice records share the array too, so the limit is lower: with
+ *     a(x) = x rounded up to a multiple of 256, kpad = 64 ceil(D / 64) and
+ *     nsub = 4 ceil(D / 128), a call needs a(4N) + 512 + a(4 N kpad) +
+ *     a(104 N nsub) (+ a(160 N) for compositions) bytes, and N beyond what
+ *     fits in SEVO_NOALLOC_SCRATCH_BYTES returns SEVO_ERR_UNSUPPORTED
+ *     (D = 1000: 423 rows; D = 5000: 85 rows);
  *   - the problem must already have its device copy on the current device
  *     (any earlier sevo_evaluate / sevo_state_create call with it makes it),
  *     else SEVO_ERR_STATE -- making that copy would allocate;

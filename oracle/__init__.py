@@ -73,7 +73,8 @@ def lib():
                 "orc_problem_comp_hybrid": (C.c_int, [vp, C.c_int, ip, ip, ip]),
                 "orc_eval": (C.c_double, [vp, dp]),
                 "orc_eval_batch": (None, [vp, dp, C.c_int64, C.c_int64, dp]),
-                "orc_eval_scale": (C.c_double, [vp, dp]),
+                "orc_eval_bound": (None, [vp, dp, dp]),
+                "orc_eval_bound_batch": (None, [vp, dp, C.c_int64, C.c_int64, dp]),
                 "orc_body": (C.c_double, [C.c_int, dp, C.c_int]),
                 "orc_transform": (None, [vp, C.c_int, dp, dp]),
                 "orc_init_population": (None, [C.c_uint64, C.c_int, C.c_int, C.c_double,
@@ -218,11 +219,13 @@ class Problem:
         lib().orc_eval_batch(self.h, _dp(x), x.shape[0], x.shape[1], _dp(out))
         return out
 
-    def scale(self, x):
-        x = f64(x)
-        if x.ndim == 1:
-            return lib().orc_eval_scale(self.h, _dp(x))
-        return np.array([lib().orc_eval_scale(self.h, _dp(np.ascontiguousarray(r))) for r in x])
+    def bound(self, x):
+        """Rounding-error bound terms (E, G, Gd) of the plain FP64 evaluation
+        at each row of x (see orc_eval_bound); each an array of len(x)."""
+        x = np.atleast_2d(f64(x))
+        out = np.zeros((x.shape[0], 3))
+        lib().orc_eval_bound_batch(self.h, _dp(x), x.shape[0], x.shape[1], _dp(out))
+        return out[:, 0], out[:, 1], out[:, 2]
 
     def transform(self, x, comp=0):
         x = f64(x)

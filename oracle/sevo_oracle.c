@@ -93,55 +93,41 @@ static double schwefel_s(void) {
   return g_schwefel_s;
 }
 
-static double schwefel_term(double z, double s, double c, double* scale) {
+static double schwefel_term(double z, double s, double c) {
   double y = z + s;
   double ay = fabs(y);
-  if (ay <= 500.0) {
-    double v = y * sin(sqrt(ay));
-    if (scale) *scale += fabs(c) + fabs(v);
-    return c - v;
-  }
+  if (ay <= 500.0) return c - y * sin(sqrt(ay));
   double b = (y > 0.0) ? 500.0 : -500.0;
-  double vb = b * sin(sqrt(500.0));
-  double pen = 1e-4 * (ay - 500.0) * (ay - 500.0);
-  if (scale) *scale += fabs(c) + fabs(vb) + pen;
-  return c - vb + pen;
+  return c - b * sin(sqrt(500.0)) + 1e-4 * (ay - 500.0) * (ay - 500.0);
 }
 
-static double body_impl(int family, const double* z, int n, double* scale) {
-  double g = 0.0, S = 0.0;
-  if (n <= 0) {
-    if (scale) *scale = 0.0;
-    return 0.0;
-  }
+static double body_impl(int family, const double* z, int n) {
+  double g = 0.0;
+  if (n <= 0) return 0.0;
   switch (family) {
     case ORC_ELLIPSOID:
       for (int i = 1; i <= n; ++i) {
         double coef = (n > 1) ? pow(10.0, 6.0 * (double)(i - 1) / (double)(n - 1)) : 1.0;
         g += coef * z[i - 1] * z[i - 1];
       }
-      S = g;
       break;
     case ORC_ROSENBROCK:
       for (int i = 0; i + 1 < n; ++i) {
         double yi = z[i] + 1.0, yn = z[i + 1] + 1.0;
         double a = yi * yi - yn, b = yi - 1.0;
         g += 100.0 * a * a + b * b;
-        double ma = yi * yi + fabs(yn), mb = fabs(yi) + 1.0;
-        S += 100.0 * ma * ma + mb * mb;
       }
       break;
     case ORC_RASTRIGIN:
       for (int i = 0; i < n; ++i) {
         double cz = cos(ORC_TWO_PI * z[i]);
         g += z[i] * z[i] - 10.0 * cz + 10.0;
-        S += z[i] * z[i] + 10.0 * fabs(cz) + 10.0;
       }
       break;
     case ORC_SCHWEFEL: {
       double s = schwefel_s();
       double c = s * sin(sqrt(s));
-      for (int i = 0; i < n; ++i) g += schwefel_term(z[i], s, c, &S);
+      for (int i = 0; i < n; ++i) g += schwefel_term(z[i], s, c);
       break;
     }
     case ORC_ACKLEY: {
@@ -154,7 +140,6 @@ static double body_impl(int family, const double* z, int n, double* scale) {
       double b = exp(sc / (double)n);
       double e = exp(1.0);
       g = (20.0 - 20.0 * a) + (e - b);
-      S = 20.0 + 20.0 * a + e + b;
       break;
     }
     case ORC_GRIEWANK: {
@@ -164,67 +149,171 @@ static double body_impl(int family, const double* z, int n, double* scale) {
         pr *= cos(z[i - 1] / sqrt((double)i));
       }
       g = sq / 4000.0 + (1.0 - pr);
-      S = sq / 4000.0 + 1.0 + fabs(pr);
       break;
     }
     default:
       g = NAN;
-      S = NAN;
   }
-  if (scale) *scale = S;
   return g;
 }
 
-/* First-order sensitivity of a body to absolute errors in z:
- * sum_i |d body / d z_i| * za_i, where za_i = sum_j |M_ij d_j| bounds how
- * much a rounding of z_i can move it (used only to state tolerances). */
-static double body_sens(int family, const double* z, const double* za, int n) {
-  double S = 0.0;
-  if (n <= 0) return 0.0;
+/* ======================================================================
+ * Rounding-error bound of the plain FP64 evaluation (used only to state
+ * parity tolerances; not part of any definition).
+ *
+ * Linearised running-error analysis: every rounded intermediate r of the
+ * plain form contributes |dg/dr| * |r| * (its relative error).  The sums
+ * below are in units of u = 2^-53 and count two implementations of the same
+ * form (this oracle and any other), each IEEE operation <= u on either side
+ * (weight B_OP = 2), each libm / device transcendental <= 1 ulp on the host
+ * plus 2 ulp on a GPU (weight B_TR = 6); a sum of n terms adds n * sum|t|
+ * per side in any summation order.  The rotation enters through
+ *   G  = sum_i |dg/dz_i| * za_i,   za_i = sum_j |M_ij d_j|
+ *   Gd = sum_i |dg/dz_i| * ||d||_2
+ * (an error dz_i <= a * za_i + b * ||d||_2 in z moves g by at most
+ * a * G + b * Gd to first order), with the true derivative of each body.
+ * ====================================================================== */
+#define B_OP 2.0
+#define B_TR 6.0
+
+typedef struct {
+  double E, G, Gd;
+} orc_bnd;
+
+/* one body over n coordinates of z (za per coordinate, dn = ||d||_2) */
+static void body_bound(int family, const double* z, const double* za, double dn, int n,
+                       orc_bnd* out) {
+  double E = 0.0, G = 0.0, Gn = 0.0, T = 0.0;
+  if (n <= 0) return;
+  double* gi = (double*)calloc((size_t)n, sizeof(double));
   switch (family) {
     case ORC_ELLIPSOID:
       for (int i = 1; i <= n; ++i) {
         double coef = (n > 1) ? pow(10.0, 6.0 * (double)(i - 1) / (double)(n - 1)) : 1.0;
-        S += 2.0 * coef * fabs(z[i - 1]) * za[i - 1];
+        double t = coef * z[i - 1] * z[i - 1];
+        gi[i - 1] = 2.0 * coef * z[i - 1];
+        E += B_OP * 2.0 * t + B_TR * t; /* z*z, coef*(.), the coefficient (pow) */
+        T += t;
       }
       break;
     case ORC_ROSENBROCK:
       for (int i = 0; i + 1 < n; ++i) {
-        double yi = z[i] + 1.0, yn = z[i + 1] + 1.0, a = yi * yi - yn;
-        S += (fabs(400.0 * yi * a) + fabs(2.0 * (yi - 1.0))) * za[i] + fabs(200.0 * a) * za[i + 1];
+        double yi = z[i] + 1.0, yn = z[i + 1] + 1.0;
+        double a = yi * yi - yn, b = yi - 1.0;
+        double t = 100.0 * a * a + b * b;
+        gi[i] += 400.0 * a * yi + 2.0 * b;
+        gi[i + 1] += -200.0 * a;
+        /* yi*yi, -yn, a*a, 100*(.), yi-1, b*b, the sum */
+        E += B_OP * (200.0 * fabs(a) * yi * yi + 200.0 * a * a + 200.0 * a * a +
+                     2.0 * b * b + b * b + t);
+        T += t;
       }
+      for (int i = 0; i < n; ++i) E += B_OP * fabs(gi[i]) * fabs(z[i] + 1.0); /* y = z + 1 */
       break;
     case ORC_RASTRIGIN:
-      for (int i = 0; i < n; ++i)
-        S += (2.0 * fabs(z[i]) + 20.0 * ORC_PI * fabs(sin(ORC_TWO_PI * z[i]))) * za[i];
+      for (int i = 0; i < n; ++i) {
+        double w = ORC_TWO_PI * z[i], cz = cos(w), sz = sin(w);
+        double t = z[i] * z[i] - 10.0 * cz + 10.0;
+        gi[i] = 2.0 * z[i] + 10.0 * ORC_TWO_PI * sz;
+        /* z*z, 2 pi z, 10*cos, z^2 - 10 cos, + 10; the cosine */
+        E += B_OP * (z[i] * z[i] + 10.0 * fabs(sz * w) + 10.0 * fabs(cz) +
+                     fabs(z[i] * z[i] - 10.0 * cz) + fabs(t)) +
+             B_TR * 10.0 * fabs(cz);
+        T += fabs(t);
+      }
       break;
     case ORC_SCHWEFEL: {
       double s = schwefel_s();
+      double c = s * sin(sqrt(s));
       for (int i = 0; i < n; ++i) {
-        double ay = fabs(z[i] + s), r = sqrt(ay);
-        double dv = (ay <= 500.0) ? fabs(sin(r)) + 0.5 * r * fabs(cos(r)) : 2e-4 * (ay - 500.0);
-        S += dv * za[i];
+        double y = z[i] + s, ay = fabs(y), t;
+        if (ay <= 500.0) {
+          double r = sqrt(ay), sr = sin(r), cr = cos(r), v = y * sr;
+          t = c - v;
+          gi[i] = -(sr + 0.5 * r * cr);
+          /* y = z + s and the shift s itself, sqrt, y*sin, c - v; the sine;
+           * c = s sin sqrt s (its product and its host sine, <= 1 ulp each
+           * side; first order in s vanishes at the argmax) */
+          E += B_OP * (2.0 * fabs(gi[i]) * ay + fabs(y * cr) * r + fabs(v) + fabs(t) +
+                       3.0 * fabs(c)) +
+               B_TR * fabs(v);
+        } else {
+          double b = (y > 0.0) ? 500.0 : -500.0, q = ay - 500.0;
+          double vb = b * sin(sqrt(500.0)), pen = 1e-4 * q * q;
+          t = c - vb + pen;
+          gi[i] = ((y > 0.0) ? 2e-4 : -2e-4) * q;
+          /* y and s, |y| - 500, q*q, 1e-4*(.), sqrt 500 and b*sin, c - vb, + pen, c; the sine */
+          E += B_OP * (2.0 * fabs(gi[i]) * ay + 2e-4 * q * q + 2.0 * pen +
+                       fabs(vb) * (1.0 + 0.5 * sqrt(500.0)) + fabs(c - vb) + fabs(t) +
+                       3.0 * fabs(c)) +
+               B_TR * fabs(vb);
+        }
+        T += fabs(t);
       }
       break;
     }
     case ORC_ACKLEY: {
-      double sq = 0.0;
-      for (int i = 0; i < n; ++i) sq += z[i] * z[i];
-      double r = sqrt(sq / (double)n) + 1e-300;
-      for (int i = 0; i < n; ++i)
-        S += (4.0 * fabs(z[i]) / ((double)n * r) + ORC_TWO_PI * 3.0 / (double)n) * za[i];
+      double sq = 0.0, sc = 0.0, asc = 0.0, arg = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double w = ORC_TWO_PI * z[i];
+        sq += z[i] * z[i];
+        sc += cos(w);
+        asc += fabs(cos(w));
+        arg += fabs(sin(w) * w);
+      }
+      double r = sqrt(sq / (double)n);
+      double a = exp(-0.2 * r), b = exp(sc / (double)n), e = exp(1.0);
+      double g = (20.0 - 20.0 * a) + (e - b);
+      for (int i = 0; i < n; ++i) {
+        /* 4a z_i / (n r) is bounded by 4a / sqrt(n) (the Lipschitz constant of
+         * the norm), which also covers the cone point r = 0 */
+        double da = (sq > 0.0) ? 4.0 * a * fabs(z[i]) / sqrt((double)n * sq) : 4.0 * a / sqrt((double)n);
+        gi[i] = da + b * ORC_TWO_PI * fabs(sin(ORC_TWO_PI * z[i])) / (double)n;
+      }
+      /* sum of squares (n + 1 roundings, relative), /n, sqrt, *0.2 each
+       * relative on r (dg/dr = 4a; the sum's share halved by the sqrt);
+       * exp and 20*a; 20 - 20a; cos arguments and values, their sum, /n, exp;
+       * e = exp(1); e - b; the final add */
+      E += B_OP * (4.0 * a * r * (0.5 * (double)(n + 2) + 2.0) + 20.0 * a + fabs(20.0 - 20.0 * a)) +
+           B_TR * 20.0 * a;
+      E += B_OP * (b * arg / (double)n + b * asc + b * fabs(sc / (double)n) + fabs(e - b) + fabs(g)) +
+           B_TR * (b * asc / (double)n + b + e);
       break;
     }
-    case ORC_GRIEWANK:
-      for (int i = 1; i <= n; ++i)
-        S += (fabs(z[i - 1]) / 2000.0 + 1.0 / sqrt((double)i)) * za[i - 1];
+    case ORC_GRIEWANK: {
+      double sq = 0.0, pr = 1.0, arg = 0.0;
+      for (int i = 1; i <= n; ++i) {
+        double xi = z[i - 1] / sqrt((double)i);
+        sq += z[i - 1] * z[i - 1];
+        pr *= cos(xi);
+        arg += fabs(sin(xi) * xi);
+        /* |prod_{k != i} cos| <= 1 */
+        gi[i - 1] = z[i - 1] / 2000.0 + fabs(sin(xi)) / sqrt((double)i);
+      }
+      double g = sq / 4000.0 + (1.0 - pr);
+      /* z^2 sum, /4000; the cosine arguments (sqrt, division); each factor
+       * and product rounding (relative on pr); 1 - pr; the final add */
+      E += B_OP * ((double)(n + 2) * sq / 4000.0 + 2.0 * arg + (double)n * fabs(pr) +
+                   fabs(1.0 - pr) + fabs(g)) +
+           B_TR * (double)n * fabs(pr);
       break;
+    }
+    default:
+      E = NAN;
   }
-  return S;
+  E += B_OP * (double)n * T; /* the coordinate sum, any order */
+  for (int i = 0; i < n; ++i) {
+    G += fabs(gi[i]) * za[i];
+    Gn += fabs(gi[i]);
+  }
+  free(gi);
+  out->E += E;
+  out->G += G;
+  out->Gd += Gn * dn;
 }
 
 double orc_body(int family, const double* z, int n) {
-  return body_impl(family, z, n, NULL);
+  return body_impl(family, z, n);
 }
 
 /* ======================================================================
@@ -602,32 +691,38 @@ static void transform_abs(const orc_problem* p, int comp, const double* x, doubl
   }
 }
 
-static double eval_impl(const orc_problem* p, const double* x, double* scale) {
+static double eval_impl(const orc_problem* p, const double* x, orc_bnd* bnd) {
   int D = p->D;
   double* z = (double*)malloc(sizeof(double) * D);
-  double* za = scale ? (double*)malloc(sizeof(double) * D) : NULL;
-  double g = 0.0, S = 0.0;
-  if (p->family <= ORC_GRIEWANK) {
-    orc_transform(p, 0, x, z);
-    g = body_impl(p->family, z, D, &S);
-    if (za) {
+  double* za = bnd ? (double*)malloc(sizeof(double) * D) : NULL;
+  double g = 0.0;
+  if (p->family <= ORC_HYBRID) {
+    orc_transform(p, 0, x, z); /* hybrid rows already permuted: z' = P M d */
+    double dn = 0.0;
+    if (bnd) {
       transform_abs(p, 0, x, za);
-      S += body_sens(p->family, z, za, D);
+      for (int j = 0; j < D; ++j) dn += (x[j] - p->o[j]) * (x[j] - p->o[j]);
+      dn = sqrt(dn);
     }
-  } else if (p->family == ORC_HYBRID) {
-    orc_transform(p, 0, x, z); /* rows already permuted: z' = P M d */
-    if (za) transform_abs(p, 0, x, za);
-    int start = 0;
-    for (int k = 0; k < p->K; ++k) {
-      double sk = 0.0;
-      g += body_impl(p->gbody[k], z + start, p->gsize[k], &sk);
-      S += sk;
-      if (za) S += body_sens(p->gbody[k], z + start, za + start, p->gsize[k]);
-      start += p->gsize[k];
+    if (p->family <= ORC_GRIEWANK) {
+      g = body_impl(p->family, z, D);
+      if (bnd) body_bound(p->family, z, za, dn, D, bnd);
+    } else {
+      double ag = 0.0;
+      int start = 0;
+      for (int k = 0; k < p->K; ++k) {
+        double gk = body_impl(p->gbody[k], z + start, p->gsize[k]);
+        g += gk;
+        ag += fabs(gk);
+        if (bnd) body_bound(p->gbody[k], z + start, za + start, dn, p->gsize[k], bnd);
+        start += p->gsize[k];
+      }
+      if (bnd) bnd->E += B_OP * (double)p->K * ag; /* the sum over groups */
     }
   } else {
     int Nc = p->K;
-    double gc[16], sc[16], Sc[16], w[16], om[16];
+    double gc[16], sc[16], w[16], om[16], h[16];
+    orc_bnd bc[16];
     int exact = -1;
     for (int c = 0; c < Nc; ++c) {
       const double* oc = p->o + (size_t)c * D;
@@ -638,53 +733,88 @@ static double eval_impl(const orc_problem* p, const double* x, double* scale) {
       }
       sc[c] = s;
       orc_transform(p, c, x, z);
+      bc[c].E = bc[c].G = bc[c].Gd = 0.0;
       if (za) transform_abs(p, c, x, za);
-      if (p->family == ORC_COMP_HYBRID) {  /* component c is a hybrid */
+      if (p->family == ORC_COMP_HYBRID) { /* component c is a hybrid */
         gc[c] = 0.0;
-        Sc[c] = 0.0;
+        double ag = 0.0;
         int start = 0;
         for (int k = 0; k < p->cK[c]; ++k) {
           const int b = p->cgbody[8 * c + k], n = p->cgsize[8 * c + k];
-          double sk = 0.0;
-          gc[c] += body_impl(b, z + start, n, &sk);
-          Sc[c] += sk;
-          if (za) Sc[c] += body_sens(b, z + start, za + start, n);
+          double gk = body_impl(b, z + start, n);
+          gc[c] += gk;
+          ag += fabs(gk);
+          if (bnd) body_bound(b, z + start, za + start, sqrt(s), n, &bc[c]);
           start += n;
         }
+        bc[c].E += B_OP * (double)p->cK[c] * ag;
       } else {
-        gc[c] = body_impl(p->gbody[c], z, D, &Sc[c]);
-        if (za) Sc[c] += body_sens(p->gbody[c], z, za, D);
+        gc[c] = body_impl(p->gbody[c], z, D);
+        if (bnd) body_bound(p->gbody[c], z, za, sqrt(s), D, &bc[c]);
       }
       if (s == 0.0 && exact < 0) exact = c;
     }
+    double ex[16], W = 0.0;
     if (exact >= 0) {
       for (int c = 0; c < Nc; ++c) om[c] = (c == exact) ? 1.0 : 0.0;
     } else {
-      double W = 0.0;
       for (int c = 0; c < Nc; ++c) {
         double sg = p->sigma[c];
-        w[c] = (1.0 / sqrt(sc[c])) * exp(-sc[c] / (2.0 * (double)D * sg * sg));
+        ex[c] = sc[c] / (2.0 * (double)D * sg * sg);
+        w[c] = (1.0 / sqrt(sc[c])) * exp(-ex[c]);
         W += w[c];
       }
       for (int c = 0; c < Nc; ++c) om[c] = (W > 0.0) ? w[c] / W : 1.0 / (double)Nc;
     }
     for (int c = 0; c < Nc; ++c) {
-      g += om[c] * (p->lambda[c] * gc[c] + p->bias[c]);
-      S += om[c] * (p->lambda[c] * Sc[c] + p->bias[c]);
+      h[c] = p->lambda[c] * gc[c] + p->bias[c];
+      g += om[c] * h[c];
+    }
+    if (bnd) {
+      double E = 0.0, ah = 0.0;
+      for (int c = 0; c < Nc; ++c) {
+        double lw = om[c] * p->lambda[c];
+        E += lw * bc[c].E;
+        bnd->G += lw * bc[c].G;
+        bnd->Gd += lw * bc[c].Gd;
+        /* lambda * g_c, + bias, omega * h */
+        E += B_OP * om[c] * (p->lambda[c] * fabs(gc[c]) + 2.0 * fabs(h[c]));
+        ah += om[c] * fabs(h[c]);
+      }
+      E += B_OP * (double)Nc * ah; /* the sum over components */
+      if (exact < 0 && W > 0.0) {
+        /* weights: s_c (n + 2 roundings, relative), 1/sqrt, the exponent's
+         * relative error times its size, exp, the product; a common relative
+         * error of W cancels against the normalisation up to |g| */
+        for (int c = 0; c < Nc; ++c) {
+          double rs = B_OP * (double)(D + 2);
+          double rw = 0.5 * rs + 2.0 * B_OP + ex[c] * (rs + 4.0 * B_OP) + B_TR + B_OP;
+          E += om[c] * rw * fabs(h[c] - g);
+        }
+        E += B_OP * (double)(Nc + 1) * fabs(g);
+      }
+      bnd->E += E;
     }
   }
   free(z);
   free(za);
-  if (scale) *scale = S;
   return g;
 }
 
 double orc_eval(const orc_problem* p, const double* x) { return eval_impl(p, x, NULL); }
 
-double orc_eval_scale(const orc_problem* p, const double* x) {
-  double S = 0.0;
-  eval_impl(p, x, &S);
-  return S;
+void orc_eval_bound(const orc_problem* p, const double* x, double out[3]) {
+  orc_bnd b = {0.0, 0.0, 0.0};
+  eval_impl(p, x, &b);
+  out[0] = b.E;
+  out[1] = b.G;
+  out[2] = b.Gd;
+}
+
+void orc_eval_bound_batch(const orc_problem* p, const double* X, int64_t N, int64_t ld,
+                          double* out) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < N; ++i) orc_eval_bound(p, X + i * ld, out + 3 * i);
 }
 
 void orc_eval_batch(const orc_problem* p, const double* X, int64_t N, int64_t ld,

@@ -20,15 +20,15 @@
  *   - best-so-far record: Sec. 2.4 and Sec. 3.2;
  *   - runner over (problem, run) tasks on a thread pool: Sec. 2.4 (Listing 3).
  * The paper prints no formula for any body, transform or operator; every
- * formula here is one of the readings listed in the project's design notes
- * (body forms, Schwefel domain handling, hybrid grouping, composition
+ * formula here is a reading of it, stated at the function that implements
+ * it (body forms, Schwefel domain handling, hybrid grouping, composition
  * weighting, Philox counter layout, partner draws, archive policy, PSO
  * details, budget rule).
  *
- * Parity status per function is stated in oracle/README.md; all functions
- * below are pinned by tests under tests/ (closed forms, invariants, brute
- * force, published Philox vectors) except where that file says
- * "parity unpinned".
+ * Every function below is pinned by tests under tests/ (closed forms,
+ * invariants, brute force, published Philox vectors, exact arithmetic for
+ * the rounding bound) except one result: the final error of a full run on a
+ * multimodal instance, which the paper does not print (parity unpinned).
  */
 #ifndef SEVO_ORACLE_H
 #define SEVO_ORACLE_H
@@ -86,9 +86,18 @@ int orc_problem_comp_hybrid(const orc_problem* p, int c, int* perm, int* gsize, 
 double orc_eval(const orc_problem* p, const double* x);
 void orc_eval_batch(const orc_problem* p, const double* X, int64_t N, int64_t ld,
                     double* out);
-/* condition scale S(x): sum of magnitudes of the pieces that are added, used
- * to state the FP64 parity tolerance |f_gpu - f| <= tol * max(|f|, S). */
-double orc_eval_scale(const orc_problem* p, const double* x);
+/* rounding-error bound of the plain FP64 evaluation at x, used only to
+ * state parity tolerances (not a definition): out[0] = E, the first-order
+ * rounding magnitude of the body arithmetic of two implementations of the
+ * plain forms, in units of u = 2^-53; out[1] = G = sum_i |dg/dz_i| *
+ * sum_j |M_ij d_j|; out[2] = Gd = sum_i |dg/dz_i| * ||d||_2 (per component,
+ * weighted by omega_c * lambda_c for compositions).  An error in z of at
+ * most a * sum_j |M_ij d_j| + b * ||d||_2 per coordinate then moves g by at
+ * most a * G + b * Gd to first order. */
+void orc_eval_bound(const orc_problem* p, const double* x, double out[3]);
+/* the same for N rows of X (leading dimension ld); out is N x 3 */
+void orc_eval_bound_batch(const orc_problem* p, const double* X, int64_t N, int64_t ld,
+                          double* out);
 /* the bias-free body on an already-transformed vector z of length n */
 double orc_body(int family, const double* z, int n);
 /* z = M (x - o) for component c (hybrid: the permuted z) */

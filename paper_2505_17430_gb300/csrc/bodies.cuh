@@ -97,8 +97,17 @@ __device__ __forceinline__ double finalize64(int body, const Acc64& a, int n) {
 //   griewank   1 - prod cos(z/sqrt p) = -expm1(sum log cos), log cos x =
 //              log1p(-2 sin^2(x/2)), sign tracked for negative cosines
 //   schwefel   c - (s+t) sin sqrt(s+t) expanded around the optimum (t = z,
-//              B = sqrt s, A = sqrt(s+t), delta = t/(A+B)); every remaining
-//              piece is second order in t (derivation in the design notes).
+//              B = sqrt s, A = sqrt(s+t), d = A - B = t/(A+B), c = s sin B):
+//              sin A = sin B cos d + cos B sin d, cos d = 1 - 2 sin^2(d/2),
+//              sin d = d + (sin d - d), so with s + t = A^2
+//                c - A^2 sin A = A^2 sin B 2 sin^2(d/2)
+//                              - A^2 cos B (sin d - d)
+//                              - t sin B - A^2 d cos B.
+//              Writing -t sin B = t (B/2) cos B - t h0 with h0 = sin B +
+//              (B/2) cos B (zero at the exact argmax, its FP32 residual
+//              kept) and using B(A+B) - 2A^2 = -(2A+B) d, the last two
+//              pieces become -t cos B (2A+B) d / (2(A+B)) - t h0.  Every
+//              piece but t h0 is second order in t and none cancels.
 struct Acc32 {
   float a0, a1, a2;
 };

@@ -43,7 +43,8 @@ extern "C" int32_t sevo_evaluate_noalloc(const sevo_problem* p, const double* po
   // the problem's device copy must already exist here: making it allocates
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return SEVO_ERR_CUDA;
-  if (!p->desc_d || p->device != dev) return SEVO_ERR_STATE;
+  // checked under the upload lock: another thread may be making the copy
+  if (sv_problem_has_device_copy(p, dev) != SEVO_OK) return SEVO_ERR_STATE;
   if (N == 0) return SEVO_OK;
   const bool comp = sv_weighted_family(p->family);
   if (sv_eval_scratch_bytes(p->D, comp, prec, N) > SEVO_NOALLOC_SCRATCH_BYTES)

@@ -308,7 +308,6 @@ static int32_t upload(sevo_problem* p) {
     h.tmaplo[c] = (const CUtensorMap*)(base + otm) + 2 * SV_MAXC + c;
   }
   size_t od = take(sizeof(ProblemDev));
-  p->desc_d = (ProblemDev*)(base + od);
   // the descriptors encode device addresses, so they are built after the
   // operand pointers are known and copied into the block with the rest
   int32_t st = sv_build_tmaps(p);
@@ -321,6 +320,8 @@ static int32_t upload(sevo_problem* p) {
   }
   std::memcpy(&blob[od], &h, sizeof(ProblemDev));
   SV_CUDA(cudaMemcpy(p->dev_block, blob.data(), p->dev_bytes, cudaMemcpyHostToDevice));
+  // published only once the block holds the descriptor
+  p->desc_d = (ProblemDev*)(base + od);
   return SEVO_OK;
 }
 
@@ -370,6 +371,11 @@ int32_t sv_problem_ready(const sevo_problem* cp) {
     p->desc_d = nullptr;
   }
   return st;
+}
+
+int32_t sv_problem_has_device_copy(const sevo_problem* p, int dev) {
+  std::lock_guard<std::mutex> lk(g_upload_mu);
+  return (p->desc_d && p->device == dev) ? SEVO_OK : SEVO_ERR_STATE;
 }
 
 static int32_t finish(sevo_problem* p, sevo_problem** out) {

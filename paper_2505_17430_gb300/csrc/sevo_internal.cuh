@@ -183,6 +183,9 @@ void sv_trace_end(int token, cudaStream_t st);
 // upload the instance to the current device on first use (thread-safe);
 // SEVO_ERR_STATE if it already lives on another device
 int32_t sv_problem_ready(const sevo_problem* p);
+// SEVO_OK if p's device copy exists on device dev (read under the lock that
+// guards its upload), else SEVO_ERR_STATE
+int32_t sv_problem_has_device_copy(const sevo_problem* p, int dev);
 // composition kinds: the row error is a distance-weighted sum of components
 inline bool sv_weighted_family(int f) { return f == SEVO_COMPOSITION || f == SEVO_COMP_HYBRID; }
 
