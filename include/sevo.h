@@ -376,14 +376,21 @@ typedef struct {          /* caller-allocated host arrays, ntasks entries each *
 int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, void* stream);
 
 /* ---- execution policy (library infrastructure; the paper has no counterpart)
- * Process-wide switches, read when a state or a grid bucket is created. */
+ * Process-wide switches, read when a state or a grid bucket is created
+ * (SEVO_POLICY_REFINE: at each sevo_evaluate / sevo_evaluate_sync call). */
 enum sevo_policy {
   /* 1: runs with D <= 32 and NP <= 512 advance in one CTA per run, whole
    * generations per launch, evaluated by CUDA cores (FP64, or FP32 with the
    * operand rounding of the requested mode and FP64 refinement); 0 (default):
    * such runs use the batched kernels like every other run (faster on this
    * part for run grids: one SM's FP64 rate bounds a run-per-CTA generation) */
-  SEVO_POLICY_SMALL_RUNS = 0
+  SEVO_POLICY_SMALL_RUNS = 0,
+  /* 1 (default): sevo_evaluate / sevo_evaluate_sync re-evaluate in FP64 the
+   * mixed-precision rows below SEVO_REFINE_THRESHOLD; 0: they return the
+   * mixed values as computed (the rows are still counted in `refined`), to
+   * measure the mixed arithmetic's own error.  States, grids and
+   * sevo_evaluate_noalloc always refine. */
+  SEVO_POLICY_REFINE = 1
 };
 /* SEVO_ERR_ARG for an unknown key or value */
 int32_t sevo_set_policy(int32_t key, int64_t value);

@@ -109,6 +109,7 @@ SIGNATURES = {
 }
 SEVO_TRACE_KINDS = 17
 POLICY_SMALL_RUNS = 0
+POLICY_REFINE = 1
 
 _LIB = None
 

@@ -30,6 +30,7 @@ void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t r
   s->tc = s->tc_bytes ? (void*)c : nullptr;
   s->err = nullptr;
   s->refined = nullptr;
+  s->skip_refine = false;
 }
 
 // one pass: mixed evaluation of every segment, then one FP64 re-evaluation
@@ -76,6 +77,7 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
         if (e != cudaSuccess) return e;
       }
     }
+    if (s.skip_refine) continue;
     RefineTable RT;
     RT.nseg = n;
     RT.total = s.refined;
@@ -115,6 +117,7 @@ static int32_t evaluate_impl(const sevo_problem* p, const double* pop, int64_t N
   SV_CUDA(cudaMallocAsync(&base, bytes, s));
   EvalScratch sc;
   sv_eval_scratch_carve(base, p->D, comp, prec, N, &sc);
+  sc.skip_refine = sv_policy_refine() == 0;
   TcSegment seg{p, 0, N};
   cudaError_t e = sv_eval_segments(&seg, 1, prec, pop, ld, out, sc, s);
   int32_t host_c[SV_MAX_SEG + 4] = {0};

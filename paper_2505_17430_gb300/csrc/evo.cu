@@ -1396,15 +1396,26 @@ unsigned grid_for(int64_t work, int threads) {
 
 // ====================================================================== host
 static std::atomic<int> g_policy_small_runs{0};
+static std::atomic<int> g_policy_refine{1};
+
+int sv_policy_refine() { return g_policy_refine.load(); }
 
 extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
-  if (key != SEVO_POLICY_SMALL_RUNS || (value != 0 && value != 1)) return SEVO_ERR_ARG;
-  g_policy_small_runs.store((int)value);
+  if (value != 0 && value != 1) return SEVO_ERR_ARG;
+  if (key == SEVO_POLICY_SMALL_RUNS) {
+    g_policy_small_runs.store((int)value);
+  } else if (key == SEVO_POLICY_REFINE) {
+    g_policy_refine.store((int)value);
+  } else {
+    return SEVO_ERR_ARG;
+  }
   return SEVO_OK;
 }
 
 extern "C" int64_t sevo_get_policy(int32_t key) {
-  return key == SEVO_POLICY_SMALL_RUNS ? g_policy_small_runs.load() : -1;
+  if (key == SEVO_POLICY_SMALL_RUNS) return g_policy_small_runs.load();
+  if (key == SEVO_POLICY_REFINE) return g_policy_refine.load();
+  return -1;
 }
 
 int sv_pbest_k(double p, int NP) {

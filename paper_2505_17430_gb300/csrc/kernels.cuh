@@ -73,9 +73,12 @@ struct EvalScratch {
   size_t tc_bytes;
   uint32_t* err;      // persistent device error bits (null: use the counters' word)
   unsigned long long* refined;  // running count of refined rows (null: none)
+  bool skip_refine;   // list the rows but keep their mixed values (measurement)
 };
 #define SV_COUNTERS_BYTES ((SV_MAX_SEG + 4) * 4)
 size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
+// SEVO_POLICY_REFINE's current value (1: refine, the default)
+int sv_policy_refine();
 void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
                            EvalScratch* s);
 // evaluate segments (same D) into out with refinement; resets counters first

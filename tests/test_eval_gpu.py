@@ -301,3 +301,32 @@ def test_tensor_core_large_d_wide_tiles_sampled(S, prec, fam, D, N):
     _check_mixed(prec, got[rows], q.eval(X[rows]), bound(p, q, X[rows]))
     assert got[-1] == 0.0
     assert np.isfinite(got).all()
+
+
+def test_refine_policy_returns_mixed_values(S):
+    """SEVO_POLICY_REFINE = 0: sevo_evaluate returns the TF32 values of rows
+    below the refinement threshold instead of recomputing them in FP64 (they
+    are still counted), within the mixed bound; back on, the same rows come
+    back at the FP64 bound.  States keep refining either way."""
+    D = 30
+    p, q = S.Problem(61, S.RASTRIGIN, D), O.Problem(61, O.RASTRIGIN, D)
+    X = np.vstack([inputs.near(q.shift(0), 64, 1e-5, seed=61), inputs.uniform_pop(64, D, seed=61)])
+    want, bnd = q.eval(X), bound(p, q, X)
+    lib = S.lib()
+    assert lib.sevo_get_policy(S.POLICY_REFINE) == 1
+    assert lib.sevo_set_policy(S.POLICY_REFINE, 0) == 0
+    try:
+        raw, info0 = p.evaluate(to_dev(X), prec=S.TF32, sync=True)
+    finally:
+        assert lib.sevo_set_policy(S.POLICY_REFINE, 1) == 0
+    ref, info1 = p.evaluate(to_dev(X), prec=S.TF32, sync=True)
+    raw, ref = raw.cpu().numpy(), ref.cpu().numpy()
+    assert info0["refined"] == info1["refined"] >= 64
+    err_raw, err_ref = np.abs(raw - want), np.abs(ref - want)
+    assert (err_raw <= tol_mixed("TF32", want, bnd)).all()
+    below = want < 1e-5
+    assert below.sum() == 64
+    assert (err_ref[below] <= tol64(want, bnd)[below]).all()
+    assert (err_raw[below] > tol64(want, bnd)[below]).any()  # really the TF32 values
+    assert np.array_equal(raw[~below], ref[~below])
+    assert lib.sevo_set_policy(S.POLICY_REFINE, 2) == -1
