@@ -118,28 +118,27 @@ RESTART_EVERY = 25
 
 
 def run_steps(states, first_gen, n, serial=False):
-    """Generations first_gen .. first_gen + n - 1 of every state.  Every
+    """Generations first_gen .. first_gen + n - 1 of every state, one
+    sevo_state_step_many call per generation (each state's operators on its
+    own stream, every state's rows evaluated in one fused launch).  Every
     RESTART_EVERY generations each run restarts from a fresh uniform
     population (sevo_state_restart, new seeds; its work is inside the timed
     region, its evaluations are not counted), so the timed generations stay
     in the early phase the microbench describes (X ~ U[-100, 100]) instead
     of drifting into the refinement-heavy end of converged runs, which the
-    run-grid measurement covers."""
+    run-grid measurement covers.  serial: the device drains after every
+    generation, so generations do not overlap one another."""
     import torch
-    prev = None
+    import paper_2505_17430_gb300 as S
     for g in range(first_gen, first_gen + n):
         if g % RESTART_EVERY == 0:
             for k, st in enumerate(states):
                 st.restart([(g * 7919 + 1000 * k + r) & 0xFFFFFFFF for r in range(st.R)])
-        for st in states:
-            if serial and prev is not None:  # one state at a time: chain the streams
-                st.torch_stream.wait_event(prev)
-            rc = st.step(g)
-            if rc != 0:
-                raise RuntimeError(f"step failed: {rc}")
-            if serial:
-                prev = torch.cuda.Event()
-                prev.record(st.torch_stream)
+        rc = S.sevo_state_step_many(states, g)
+        if rc != 0:
+            raise RuntimeError(f"step failed: {rc}")
+        if serial:
+            torch.cuda.synchronize()
     return first_gen + n
 
 
@@ -195,7 +194,7 @@ FUSED_SOURCES = ("eval_tc.cu", "tc_walk.cuh", "bodies.cuh", "tc_ptx.cuh")
 def traced_step_kernels(S, torch, states, gen, K, serial=False):
     """Per-kernel device time from a traced repeat of the timed steps (CUDA
     events recorded on the launching stream around every launch); serial:
-    the states' streams chained so that no two kernels overlap."""
+    the device drains after every generation.  Returns (trace, gen, K)."""
     S.trace_enable(True)
     gen = run_steps(states, gen, K, serial=serial)
     torch.cuda.synchronize()
@@ -204,29 +203,33 @@ def traced_step_kernels(S, torch, states, gen, K, serial=False):
     return {k: v for k, v in t.items() if v[0] > 0}, gen
 
 
-def rooflines(trace, states, peaks):
+def rooflines(trace, states, peaks, K):
     """Dominant kernel (fused tcgen05 evaluation) and the streaming DE/PSO
-    kernels against the measured HBM copy bandwidth."""
+    kernels against the measured HBM copy bandwidth.  Rows per launch: every
+    state's rows for the fused evaluation (one launch per step), one state's
+    for a DE trial or PSO move launch."""
     peak = peaks.get("hbm_gbs")
     src = "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"
-    rows = FAMILIES * NP  # rows per launch: one state's six populations
     total_ms = sum(ms for _, ms in trace.values())
+    step_rows = sum(st.R * NP for st in states)
 
     def entry(kind, bytes_per_row, bound="hbm"):
         n, ms = trace.get(kind, (0, 0.0))
         if not n:
             return None
         per = ms / n
+        rows = step_rows * K // n if kind == "eval_tc_fused" else FAMILIES * NP
         algo = rows * bytes_per_row
         ach = algo / (per * 1e-3) / 1e9
         return {"kernel": kind, "bound": bound, "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4) if peak else None,
+                "rows_per_launch": rows,
                 "algorithmic_bytes_per_launch": algo, "launch_ms": round(per, 4),
                 "launches": n, "share_of_step": round(ms / total_ms, 4), "peak_source": src}
 
     main = entry("eval_tc_fused", D * 8 + 8)
     per_row = profiled_traffic("eval_tc_fused_tf32_d100.md", FUSED_SOURCES)
-    main["traffic"] = round(per_row * rows) if per_row else None
+    main["traffic"] = round(per_row * main["rows_per_launch"]) if per_row else None
     # DE trial: target + three donors read, trial written (FP64 rows) + 16 B
     # of partner indices; PSO move: x, v, pbest read, x, v written (the guide
     # row is one per run or neighbourhood and is served from L2)
@@ -456,10 +459,11 @@ def e2e_rate(S, torch, states, gen, K):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for g in range(gen, gen + K):
-        for st, hx, hf in zip(states, hostX, hostF):
+        for st, hx in zip(states, hostX):
             S.check(lib.sevo_state_set_async(st.h, C.cast(C.c_void_p(hx.data_ptr()), dp), None,
                                              None, 0, None, None, None, -1), "sevo_state_set_async")
-            S.check(st.step(g), "step")
+        S.check(S.sevo_state_step_many(states, g), "sevo_state_step_many")
+        for st, hf in zip(states, hostF):
             S.check(lib.sevo_state_get_async(st.h, None, C.cast(C.c_void_p(hf.data_ptr()), dp),
                                              None, None, None, None, None, None),
                     "sevo_state_get_async")
@@ -470,8 +474,9 @@ def e2e_rate(S, torch, states, gen, K):
     return {"value": round(evals / dt, 1), "unit": "evals/s",
             "h2d_bytes_per_step": sum(r * D * 8 for r in rows),
             "d2h_bytes_per_step": sum(r * 8 for r in rows),
-            "path": "sevo_state_set_async (pinned X in) + step + sevo_state_get_async (pinned "
-                    "fitness out) per state on its own stream, host waits for every step"}, gen + K
+            "path": "sevo_state_set_async (pinned X in) per state on its own stream, "
+                    "sevo_state_step_many, sevo_state_get_async (pinned fitness out) per state; "
+                    "host waits for every step"}, gen + K
 
 
 # ---------------------------------------------------------------- grid
@@ -755,10 +760,11 @@ def main():
     fp64 = {"value": round(evals_per_step / (ms64 / 2 * 1e-3), 1),
             "ms_per_step": round(ms64 / 2, 3)}
     del st64
-    traced, gen = traced_step_kernels(S, torch, states, gen, min(args.steps, 200))
-    roof, stream_roof, shares = rooflines(traced, states, peaks)
-    traced1, gen = traced_step_kernels(S, torch, states, gen, min(args.steps, 200), serial=True)
-    roof1, stream1, shares1 = rooflines(traced1, states, peaks)
+    KT = min(args.steps, 200)
+    traced, gen = traced_step_kernels(S, torch, states, gen, KT)
+    roof, stream_roof, shares = rooflines(traced, states, peaks, KT)
+    traced1, gen = traced_step_kernels(S, torch, states, gen, KT, serial=True)
+    roof1, stream1, shares1 = rooflines(traced1, states, peaks, KT)
     roof["alone"] = {k: roof1[k] for k in ("achieved", "frac", "launch_ms")}
     for k in stream_roof:
         if stream_roof[k] and stream1.get(k):
@@ -801,11 +807,14 @@ def main():
                        "l2": "working set ~160 MB per step > 129 MB L2 (no flush needed)",
                        "kernel_times": "per-kernel CUDA-event times from a traced repeat of "
                                        "the timed steps (events on the launching stream); "
-                                       "'alone': a second repeat with the states' streams "
-                                       "chained, so no two kernels overlap",
+                                       "'alone': a second repeat in which the device "
+                                       "drains after every generation",
                        "restart_every": RESTART_EVERY,
-                       "streams": "one CUDA stream per algorithm's state; the timed region is "
-                                  "forked from and joined to one stream by events",
+                       "streams": "one CUDA stream per algorithm's state, one "
+                                  "sevo_state_step_many call per step (operators on each "
+                                  "state's stream, one fused evaluation of all 73,728 rows, "
+                                  "selections on each stream); the timed region is forked "
+                                  "from and joined to one stream by events",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,

@@ -287,6 +287,25 @@ int32_t sevo_de_step(sevo_state* s, uint64_t philox_counter);
  * SEVO_ERR_STATE if the budget is already spent. */
 int32_t sevo_state_step(sevo_state* s, uint64_t philox_counter);
 
+/* One generation of each of n states (1 <= n <= SEVO_STEP_MANY_MAX), all at
+ * counter `philox_counter`, with the same results as sevo_state_step on each
+ * in turn: the runner's independent tasks advanced together (Sec. 2.4,
+ * Listing 3, whose thread pool runs (problem, run) tasks side by side).
+ * When every state is a batched DE, PSO or CSO state (not PSODE, not a
+ * run-per-CTA state) of one dimension and precision, each state's
+ * operators run on its own stream, then the rows of all states are
+ * evaluated in one pass on states[0]'s stream (for D <= 128 in the
+ * tensor-core modes one persistent fused launch over every state's rows),
+ * then each state's selection runs on its own stream after that pass;
+ * otherwise the states step one after another.  The first joint call with
+ * a given states[0] allocates that state's joint scratch (grown, never
+ * shrunk, freed with the state); make it before any stream capture.  Every
+ * state must be on the current device (else SEVO_ERR_STATE), appear once
+ * (else SEVO_ERR_ARG) and have budget left (else SEVO_ERR_STATE, checked
+ * before anything is launched). */
+#define SEVO_STEP_MANY_MAX 16
+int32_t sevo_state_step_many(sevo_state* const* states, int32_t n, uint64_t philox_counter);
+
 /* One PSO generation (SEVO_PSO_GBEST, SEVO_PSO_RING and SEVO_CSO only;
  * SEVO_ERR_STATE otherwise or once the budget is spent): velocity and
  * position update with per-coordinate r1, r2 from the Philox stream at

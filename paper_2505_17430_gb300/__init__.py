@@ -92,6 +92,7 @@ SIGNATURES = {
     "sevo_de_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_pso_step": (C.c_int32, [_vp, C.c_uint64]),
     "sevo_state_step": (C.c_int32, [_vp, C.c_uint64]),
+    "sevo_state_step_many": (C.c_int32, [C.POINTER(_vp), C.c_int32, C.c_uint64]),
     "sevo_state_result": (C.c_int32, [_vp, _dp, _i64p, _i64p, _i64p]),
     "sevo_state_get": (C.c_int32, [_vp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _ip]),
     "sevo_state_set": (C.c_int32, [_vp, _dp, _dp, _dp, C.c_int32, _dp, _dp, _dp, C.c_int64]),
@@ -355,6 +356,16 @@ class State:
     def load(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         check(_lib().sevo_state_load(self.h, buf, len(data)), "sevo_state_load")
+
+
+def sevo_state_step_many(states, counter):
+    """One generation of every state in `states`, their rows evaluated in
+    one pass (sevo_state_step_many); returns the status."""
+    hs = (_vp * len(states))(*[st.h.value for st in states])
+    return _lib().sevo_state_step_many(hs, len(states), counter)
+
+
+STEP_MANY_MAX = 16
 
 
 def sevo_state_create(problem, params, seed, stream=None):

@@ -41,7 +41,9 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
   cudaError_t e;
   for (int base = 0; base < nseg; base += SV_MAX_SEG) {
     const int n = std::min(SV_MAX_SEG, nseg - base);
-    const TcSegment* sg = segs + base;
+    // each segment's own rows, results, error word and refined counter,
+    // else the call's
+    TcSegment sg[SV_MAX_SEG];
     e = cudaMemsetAsync(s.counters, 0, SV_COUNTERS_BYTES, st);
     if (e != cudaSuccess) return e;
     uint32_t* nonfinite = (uint32_t*)(s.counters + SV_MAX_SEG);
@@ -49,13 +51,19 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
     int64_t off[SV_MAX_SEG];
     int64_t tot = 0;
     for (int k = 0; k < n; ++k) {
+      sg[k] = segs[base + k];
+      if (!sg[k].X) sg[k].X = X;
+      if (!sg[k].out) sg[k].out = out;
+      if (!sg[k].err) sg[k].err = dev_err;
+      if (!sg[k].refined) sg[k].refined = s.refined;
       off[k] = tot;
       tot += sg[k].nrows;
     }
     if (prec == SEVO_FP64) {
       for (int k = 0; k < n; ++k) {
         EvalAux aux{nullptr, nullptr, nonfinite};
-        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP64, X, ld, sg[k].row0, sg[k].nrows, out, aux, st);
+        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP64, sg[k].X, ld, sg[k].row0, sg[k].nrows,
+                       sg[k].out, aux, st);
         if (e != cudaSuccess) return e;
       }
       continue;
@@ -63,27 +71,30 @@ cudaError_t sv_eval_segments(const TcSegment* segs, int nseg, int prec, const do
     if (prec == SEVO_FP32) {
       for (int k = 0; k < n; ++k) {
         EvalAux aux{s.list + off[k], s.counters + k, nonfinite};
-        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP32, X, ld, sg[k].row0, sg[k].nrows, out, aux, st);
+        e = sv_eval_cc(sg[k].p->desc_d, SEVO_FP32, sg[k].X, ld, sg[k].row0, sg[k].nrows,
+                       sg[k].out, aux, st);
         if (e != cudaSuccess) return e;
       }
     } else if (sg[0].p->D <= 128) {
-      e = sv_eval_tc_segments(sg, n, prec, X, ld, out, s.list, off, s.counters, nonfinite, s.tc,
-                              s.tc_bytes, dev_err, st);
+      e = sv_eval_tc_segments(sg, n, prec, ld, s.list, off, s.counters, nonfinite, s.tc,
+                              s.tc_bytes, st);
       if (e != cudaSuccess) return e;
     } else {
       for (int k = 0; k < n; ++k) {
-        e = sv_eval_tc_big(sg[k], prec, X, ld, out, s.list, off[k], s.counters + k, nonfinite,
-                           s.tc, s.tc_bytes, dev_err, st);
+        e = sv_eval_tc_big(sg[k], prec, sg[k].X, ld, sg[k].out, s.list, off[k], s.counters + k,
+                           nonfinite, s.tc, s.tc_bytes, sg[k].err, st);
         if (e != cudaSuccess) return e;
       }
     }
     if (s.skip_refine) continue;
     RefineTable RT;
     RT.nseg = n;
-    RT.total = s.refined;
     for (int k = 0; k < n; ++k) {
       RT.P[k] = sg[k].p->desc_d;
       RT.list_off[k] = off[k];
+      RT.X[k] = sg[k].X;
+      RT.out[k] = sg[k].out;
+      RT.total[k] = sg[k].refined;
     }
     e = sv_eval_refine(RT, X, ld, tot, s.list, s.counters, out, st);
     if (e != cudaSuccess) return e;

@@ -134,13 +134,11 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
   if (LIST) {
     if (tid == 0) {
       cumS[0] = 0;
-      unsigned long long listed = 0;
-      for (int q = 0; q < RT.nseg; ++q) {
-        cumS[q + 1] = cumS[q] + (counts[q] + TR - 1) / TR;
-        listed += (unsigned long long)counts[q];
-      }
+      for (int q = 0; q < RT.nseg; ++q) cumS[q + 1] = cumS[q] + (counts[q] + TR - 1) / TR;
       curSeg = -1;
-      if (blockIdx.x == 0 && RT.total && listed) atomicAdd(RT.total, listed);
+      if (blockIdx.x == 0)
+        for (int q = 0; q < RT.nseg; ++q)
+          if (RT.total[q] && counts[q]) atomicAdd(RT.total[q], (unsigned long long)counts[q]);
     }
     __syncthreads();
     total_tiles = cumS[RT.nseg];
@@ -160,6 +158,9 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
     }
     const int D = P.D;
     const int nchunks = (D + CH - 1) / CH;
+    // a listed segment may name its own rows and results
+    const double* __restrict__ Xs = (LIST && RT.X[seg]) ? RT.X[seg] : X;
+    double* __restrict__ outs = (LIST && RT.out[seg]) ? RT.out[seg] : out;
     __syncthreads();
     if (tid < TR) {
       if (LIST) {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
         double s = 0.0;
         if (row >= 0)
           for (int j = lane; j < D; j += 32) {
-            double dv = X[row * ld + j] - o[j];
+            double dv = Xs[row * ld + j] - o[j];
             s += dv * dv;
           }
 #pragma unroll
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
           for (int r = 0; r < TR; ++r) {
             int64_t row = rowS[r];
             double dv = 0.0;
-            if (row >= 0 && j < D) dv = X[row * ld + j] - o[j];
+            if (row >= 0 && j < D) dv = Xs[row * ld + j] - o[j];
             dS[r][tid] = (T)dv;
           }
           __syncthreads();
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(NT) eval_cc_kernel(const ProblemDev* __restric
         int k = atomicAdd(aux.refine_count, 1);
         aux.refine_list[k] = (int32_t)row;
       }
-      out[row] = err;
+      outs[row] = err;
     }
   }
 }

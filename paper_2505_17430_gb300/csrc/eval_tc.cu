@@ -41,23 +41,34 @@ constexpr long long WAIT_BUDGET = 4000000000LL;  // ~2 s of clock64
 constexpr int TCOLS = 128;                      // TMEM columns per accumulator buffer
 constexpr int A_KB_BYTES = BM * 128;            // one 128-byte-wide K block of A
 constexpr int MAX_SEG = 64;
+constexpr int MAX_XMAPS = 4;                    // distinct populations per launch (staged mode)
 
 struct Seg {
   const ProblemDev* P;
+  const double* X;   // the segment's population (rows row0 ..)
+  double* out;       // its results
+  uint32_t* err;     // its device error word
   int64_t row0;      // first row of the segment in X / out
   int64_t list_off;  // start of the segment's refinement sub-list
+  int64_t stage0;    // composition staging: first slot row of the segment
   int32_t nrows;
   int32_t tile0;     // tiles of all earlier segments
   int32_t ncomp;
   int32_t comp;      // composition family
   int32_t sidx;      // index of the segment's refinement counter
-  int32_t pad;
+  int32_t xmap;      // staged mode: index of the tensor map over X
+};
+
+// tensor maps over the launch's distinct populations (staged mode)
+struct XMaps {
+  CUtensorMap m[MAX_XMAPS];
 };
 
 struct SegTable {
   int nseg, ntiles, D;
   Seg seg[MAX_SEG];
 };
+
 
 struct FusedGeom {
   int D, kpad, npad;
@@ -81,9 +92,12 @@ struct __align__(8) Bars {
   int abort;
 };
 
-__device__ __forceinline__ void raise_abort(Bars* bars, uint32_t* dev_err) {
+// a wait gave up: stop this CTA and flag every segment (its remaining jobs,
+// whichever segments they belong to, are not done)
+__device__ void raise_abort(Bars* bars, const SegTable& T) {
   bars->abort = 1;
-  if (dev_err) atomicOr(dev_err, SV_DEVERR_TIMEOUT);
+  for (int s = 0; s < T.nseg; ++s)
+    if (T.seg[s].err) atomicOr(T.seg[s].err, SV_DEVERR_TIMEOUT);
 }
 
 // The job sequence of one CTA: tiles blockIdx.x, +gridDim.x, ...; each tile
@@ -195,9 +209,8 @@ __device__ __forceinline__ void convert_store(int r, const double (&x)[4], int k
 template <bool BF16, bool XTMA>
 __global__ void __launch_bounds__(NTHREADS, 1)
     eval_tc_fused(const __grid_constant__ SegTable T, const FusedGeom geo,
-                  const __grid_constant__ CUtensorMap mapX, const double* __restrict__ X,
-                  int64_t ld, double* __restrict__ out, double* __restrict__ comp_g,
-                  double* __restrict__ comp_s, ListOut lo, uint32_t* dev_err) {
+                  const __grid_constant__ XMaps maps, int64_t ld, double* __restrict__ comp_g,
+                  double* __restrict__ comp_s, ListOut lo) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ Bars bars;
   __shared__ float sS[2][BM];
@@ -253,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (sg.P != curP || c != cur_c) {
           if (pending_done) {  // the previous job's MMAs must finish reading B
             if (!tc::mbar_wait(&bars.mma_done, done_phase, &bars.abort, WAIT_BUDGET)) {
-              raise_abort(&bars, dev_err);
+              raise_abort(&bars, T);
               break;
             }
             done_phase ^= 1u;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           if (!tc::mbar_wait(&bars.b_full, b_phase, &bars.abort, WAIT_BUDGET)) {
-            raise_abort(&bars, dev_err);
+            raise_abort(&bars, T);
             break;
           }
           b_phase ^= 1u;
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t apar = XTMA ? (uint32_t)(j & 1) : (u & 1u);
         if (!tc::mbar_wait(&bars.a_full[ab], apar, &bars.abort, WAIT_BUDGET) ||
             !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
-          raise_abort(&bars, dev_err);
+          raise_abort(&bars, T);
           break;
         }
         tc::tc_fence_after();
@@ -334,12 +347,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int b = (int)(q % (uint32_t)geo.nxb);
           const uint32_t use = q / (uint32_t)geo.nxb;
           if (!tc::mbar_wait(&bars.x_empty[b], (use & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
-            raise_abort(&bars, dev_err);
+            raise_abort(&bars, T);
             ok = false;
             break;
           }
           tc::mbar_arrive_expect_tx(&bars.x_full[b], (uint32_t)geo.xb_bytes);
-          tc::tma_load_2d(sX + (size_t)b * geo.xb_bytes, &mapX, &bars.x_full[b], 0,
+          tc::tma_load_2d(sX + (size_t)b * geo.xb_bytes, &maps.m[sg.xmap], &bars.x_full[b], 0,
                           (int32_t)(row0 + h * XQ));
         }
       }
@@ -363,7 +376,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t apar = XTMA ? (uint32_t)((j & 1) ^ 1) : ((u & 1u) ^ 1u);
       if (!tc::mbar_wait(&bars.a_empty[ab], apar, &bars.abort, WAIT_BUDGET) ||
           (comp && !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET))) {
-        if (lane == 0) raise_abort(&bars, dev_err);
+        if (lane == 0) raise_abort(&bars, T);
         break;
       }
       const float* __restrict__ oh = sg.P->oh32[c];
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int b = (int)(qi % (uint32_t)geo.nxb);
           const uint32_t use = qi / (uint32_t)geo.nxb;
           if (!tc::mbar_wait(&bars.x_full[b], use & 1u, &bars.abort, WAIT_BUDGET)) {
-            if (lane == 0) raise_abort(&bars, dev_err);
+            if (lane == 0) raise_abort(&bars, T);
             okq = false;
             break;
           }
@@ -426,7 +439,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
           if (lr < sg.nrows) {
-            const double* xr = X + (sg.row0 + lr) * ld;
+            const double* xr = sg.X + (sg.row0 + lr) * ld;
             if (full4) {
               const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
               const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k0 + 2));
@@ -475,7 +488,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (comp) ++comp_uses;
       if (!tc::mbar_wait(&bars.t_full[g], u & 1u, &bars.abort, WAIT_BUDGET) ||
           (comp && !tc::mbar_wait(&bars.s_full[g], sp, &bars.abort, WAIT_BUDGET))) {
-        raise_abort(&bars, dev_err);
+        raise_abort(&bars, T);
         break;
       }
       tc::tc_fence_after();
@@ -486,12 +499,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0) tc::mbar_arrive(&bars.t_empty[g]);
       const int64_t lr = (int64_t)it.local_tile() * BM + r;
       if (lr < sg.nrows) {
-        const int64_t row = sg.row0 + lr;
         if (comp) {
-          comp_g[row * SV_MAXC + c] = gsum;
-          comp_s[row * SV_MAXC + c] = (double)s_c;
+          const int64_t slot = (sg.stage0 + lr) * SV_MAXC + c;
+          comp_g[slot] = gsum;
+          comp_s[slot] = (double)s_c;
         } else {
-          emit(gsum, row, out, lo, sg);
+          emit(gsum, sg.row0 + lr, sg.out, lo, sg);
         }
       }
     }
@@ -510,15 +523,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // composition rows: weights from the FP32 distances of the tensor-core pass
 // (exactly 0 at x = o_c, where the weight collapses onto component c)
 __global__ void compose_rows_kernel(const __grid_constant__ SegTable T, const double* comp_g,
-                                    const double* comp_s, double* out, ListOut lo) {
+                                    const double* comp_s, ListOut lo) {
   for (int s = 0; s < T.nseg; ++s) {
     const Seg& sg = T.seg[s];
     if (!sg.comp) continue;
     const ProblemDev& P = *sg.P;
     for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < sg.nrows;
          lr += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t row = sg.row0 + lr;
-      emit(compose(P, comp_s + row * SV_MAXC, comp_g + row * SV_MAXC), row, out, lo, sg);
+      const int64_t slot = (sg.stage0 + lr) * SV_MAXC;
+      emit(compose(P, comp_s + slot, comp_g + slot), sg.row0 + lr, sg.out, lo, sg);
     }
   }
 }
@@ -631,27 +644,51 @@ static cudaError_t set_fused_smem() {
   return e;
 }
 
-cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const double* X,
-                                int64_t ld, double* out, int32_t* list, const int64_t* list_off,
-                                int32_t* counts, uint32_t* nonfinite, void* scratch,
-                                size_t scratch_bytes, uint32_t* dev_err, cudaStream_t st) {
+cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64_t ld,
+                                int32_t* list, const int64_t* list_off, int32_t* counts,
+                                uint32_t* nonfinite, void* scratch, size_t scratch_bytes,
+                                cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
   if (nseg > SV_MAX_SEG) return cudaErrorInvalidValue;
   const ProblemDev& h0 = segs[0].p->host_desc;
   if (h0.D > 128) return cudaErrorNotSupported;
   const bool bf16 = (prec == SEVO_BF16X3);
   FusedGeom g = fused_geom(h0, bf16);
-  g.vec_ok = (((uintptr_t)X & 15) == 0) && ((ld & 1) == 0);
-  // staged rows: TMA needs a 16-byte aligned base and row pitch
-  const bool xtma = g.vec_ok;
+  // the populations of the segments: vector loads and TMA staging need every
+  // one 16-byte aligned with an even pitch; staging takes one tensor map per
+  // distinct population (at most MAX_XMAPS)
+  const double* xs[MAX_XMAPS];
+  int64_t xrows[MAX_XMAPS];
+  int nx = 0;
+  bool aligned = (ld & 1) == 0, few = true;
+  int xmap_of[SV_MAX_SEG];
+  for (int k = 0; k < nseg; ++k) {
+    const TcSegment& s = segs[k];
+    aligned = aligned && (((uintptr_t)s.X & 15) == 0);
+    int m = 0;
+    while (m < nx && xs[m] != s.X) ++m;
+    if (m == nx) {
+      if (nx == MAX_XMAPS) {
+        few = false;
+        m = 0;
+      } else {
+        xs[nx] = s.X;
+        xrows[nx] = 0;
+        ++nx;
+      }
+    }
+    if (xs[m] == s.X) xrows[m] = std::max<int64_t>(xrows[m], s.row0 + s.nrows);
+    xmap_of[k] = m;
+  }
+  g.vec_ok = aligned;
   g.dbox = (h0.D + 1) & ~1;
   g.xb_bytes = XQ * g.dbox * 8;
   const size_t budget = 220 * 1024;
   const size_t fixed = (size_t)g.a_bytes + g.b_bytes + 1024;
   g.nxb = (int)std::min<size_t>(MAX_XB, (budget - fixed) / (size_t)g.xb_bytes);
-  const bool use_xtma = xtma && g.nxb >= 2;
-  const size_t smem = use_xtma ? fixed + (size_t)g.nxb * g.xb_bytes
-                               : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
+  bool staged = aligned && few && g.nxb >= 2;
+  const size_t smem = staged ? fixed + (size_t)g.nxb * g.xb_bytes
+                             : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   {
     const cudaError_t e = sv_once_per_device(SV_ONCE_FUSED_SMEM, set_fused_smem);
     if (e != cudaSuccess) return e;
@@ -660,12 +697,14 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
   T.nseg = nseg;
   T.D = h0.D;
   int tiles = 0;
-  bool any_comp = false;
-  int64_t row_lo = INT64_MAX, row_hi = 0;
+  int64_t stage_rows = 0;
   for (int k = 0; k < nseg; ++k) {
     const TcSegment& s = segs[k];
     Seg& d = T.seg[k];
     d.P = s.p->desc_d;
+    d.X = s.X;
+    d.out = s.out;
+    d.err = s.err;
     d.row0 = s.row0;
     d.list_off = list_off ? list_off[k] : 0;
     d.nrows = (int32_t)s.nrows;
@@ -673,61 +712,51 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const
     d.comp = sv_weighted_family(s.p->family);
     d.ncomp = s.p->ncomp;
     d.sidx = k;
-    d.pad = 0;
+    d.xmap = xmap_of[k];
+    d.stage0 = stage_rows;
     tiles += (int)((s.nrows + BM - 1) / BM);
-    if (d.comp) {
-      any_comp = true;
-      row_lo = std::min<int64_t>(row_lo, s.row0);
-      row_hi = std::max<int64_t>(row_hi, s.row0 + s.nrows);
-    }
+    if (d.comp) stage_rows += s.nrows;
   }
   T.ntiles = tiles;
   if (tiles == 0) return cudaSuccess;
-  // composition scratch rows are indexed relative to the first composition
-  // row: (row - row_lo) * SV_MAXC + component
+  // composition staging: SV_MAXC slots of g_c and of s_c per composition row
   double* comp_g = nullptr;
   double* comp_s = nullptr;
-  if (any_comp) {
-    const size_t need = (size_t)(row_hi - row_lo) * SV_MAXC * 16;
+  if (stage_rows > 0) {
+    const size_t need = (size_t)stage_rows * SV_MAXC * 16;
     if (!scratch || scratch_bytes < need) return cudaErrorInvalidValue;
-    comp_g = (double*)scratch - row_lo * SV_MAXC;
-    comp_s = (double*)scratch + (size_t)(row_hi - row_lo) * SV_MAXC - row_lo * SV_MAXC;
+    comp_g = (double*)scratch;
+    comp_s = (double*)scratch + (size_t)stage_rows * SV_MAXC;
   }
   const ListOut lo{list, counts, nonfinite};
   const int grid = std::min(tiles, sv_num_sms());
-  CUtensorMap mapX;
-  std::memset(&mapX, 0, sizeof(mapX));
-  bool staged = use_xtma;
-  if (staged) {
-    int64_t rows_total = 0;
-    for (int k = 0; k < nseg; ++k)
-      rows_total = std::max<int64_t>(rows_total, segs[k].row0 + segs[k].nrows);
-    staged = make_x_map(&mapX, X, h0.D, g.dbox, rows_total, ld);
-  }
+  XMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int m = 0; m < nx && staged; ++m)
+    staged = make_x_map(&maps.m[m], xs[m], h0.D, g.dbox, xrows[m], ld);
   const int tk = sv_trace_begin(SEVO_TK_EVAL_TC_FUSED, st);
   if (!staged) {
     const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
     if (bf16)
-      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, mapX, X, ld, out,
-                                                                      comp_g, comp_s, lo, dev_err);
+      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ld, comp_g,
+                                                                      comp_s, lo);
     else
-      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, mapX, X, ld, out,
-                                                                       comp_g, comp_s, lo, dev_err);
+      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ld, comp_g,
+                                                                       comp_s, lo);
   } else {
     if (bf16)
-      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, mapX, X, ld, out, comp_g,
-                                                              comp_s, lo, dev_err);
+      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ld, comp_g, comp_s, lo);
     else
-      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, mapX, X, ld, out, comp_g,
-                                                               comp_s, lo, dev_err);
+      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ld, comp_g, comp_s,
+                                                               lo);
   }
   sv_trace_end(tk, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (any_comp) {
-    const int cgrid = std::max(1, std::min(sv_num_sms() * 4, (int)((row_hi - row_lo + 255) / 256)));
+  if (stage_rows > 0) {
+    const int cgrid = std::max(1, std::min(sv_num_sms() * 4, (int)((stage_rows + 255) / 256)));
     const int tkc = sv_trace_begin(SEVO_TK_COMPOSE, st);
-    compose_rows_kernel<<<cgrid, 256, 0, st>>>(T, comp_g, comp_s, out, lo);
+    compose_rows_kernel<<<cgrid, 256, 0, st>>>(T, comp_g, comp_s, lo);
     sv_trace_end(tkc, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -1573,13 +1573,21 @@ void sv_batch_free(Batch* b) {
 // evaluate every row of `M` (X or U) into `f`: one pass over the batch's
 // problem segments (runs sharing a problem)
 // evaluate `rpr` rows per run of M (runs in blocks of rpr rows) into f
-static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1) {
-  if (rpr < 0) rpr = b->NP;
-  std::vector<TcSegment> segs;
+void sv_batch_segments(const Batch* b, const EvalReq& q, std::vector<TcSegment>* segs) {
   for (size_t s = 0; s + 1 < b->seg_begin.size(); ++s) {
     const int r0 = b->seg_begin[s], r1 = b->seg_begin[s + 1];
-    segs.push_back(TcSegment{b->run_prob[r0], (int64_t)r0 * rpr, (int64_t)(r1 - r0) * rpr});
+    TcSegment t{b->run_prob[r0], (int64_t)r0 * q.rpr, (int64_t)(r1 - r0) * q.rpr};
+    t.X = q.M;
+    t.out = q.f;
+    t.err = b->err;
+    t.refined = b->refined;
+    segs->push_back(t);
   }
+}
+
+static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1) {
+  std::vector<TcSegment> segs;
+  sv_batch_segments(b, EvalReq{M, f, rpr < 0 ? b->NP : rpr}, &segs);
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
   sc.err = b->err;
@@ -1668,11 +1676,9 @@ cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens) 
   return e;
 }
 
-// The DE part of a generation: (SHADE parameters,) p-best ranking, trials
-// U from X, their evaluation and the one-to-one selection, whose best-so-far
-// counts the trials after `count_skip` rows of the generation.  Leaves the
-// per-row action for de_apply_kernel / psode_pick_kernel.
-static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
+// The DE trials of a generation: (SHADE parameters,) p-best ranking, trials
+// U from X.
+static cudaError_t de_trials(Batch* b) {
   cudaStream_t st = b->stream;
   const int64_t rows = (int64_t)b->R * b->NP;
   const int nq = (b->D + 3) >> 2;
@@ -1718,8 +1724,14 @@ static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
         nullptr, nullptr, nullptr);
     sv_trace_end(tk9, st);
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The one-to-one selection of evaluated trials, whose best-so-far counts the
+// trials after `count_skip` rows of the generation.  Leaves the per-row
+// action for de_apply_kernel / psode_pick_kernel.
+static cudaError_t de_select(Batch* b, int count_skip) {
+  cudaStream_t st = b->stream;
   const int tk10 = sv_trace_begin(SEVO_TK_DE_SELECT, st);
   de_select_kernel<<<b->R, SEL_THREADS, sel_smem_bytes(b->NP), st>>>(
       b->fx, b->fu, b->asize, b->action, b->best, b->seeds, b->ctl, b->NP,
@@ -1728,55 +1740,24 @@ static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
   return cudaGetLastError();
 }
 
-cudaError_t sv_batch_generation(Batch* b) {
-  cudaStream_t st = b->stream;
-  if (b->small) {
-    const int tk = sv_trace_begin(SEVO_TK_SMALL_RUN, st);
-    const cudaError_t es = srk_launch(b, 1, 0);
-    sv_trace_end(tk, st);
-    return es;
-  }
-  const int64_t rows = (int64_t)b->R * b->NP;
-  const int nq = (b->D + 3) >> 2;
-  const int T = 256;
+static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
   cudaError_t e;
+  if ((e = de_trials(b)) != cudaSuccess) return e;
+  if ((e = eval_rows(b, b->U, b->fu)) != cudaSuccess) return e;
+  return de_select(b, count_skip);
+}
+
+bool sv_batch_splittable(const Batch* b) { return !b->small && b->alg != SEVO_PSODE; }
+
+cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int T = 256;
   if (sv_is_de(b->alg)) {
-    if ((e = de_trials_and_select(b, 0)) != cudaSuccess) return e;
-    const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
-    de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
-                                                         b->D, b->ld, make_fastdiv(nq),
-                                                         make_fastdiv(b->NP));
-    sv_trace_end(tk11, st);
-  } else if (b->alg == SEVO_PSODE) {
-    // PSO component: offspring Y from the population, personal bests, guides
-    const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
-    psode_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(
-        b->X, b->V, b->P, b->guide, b->Y, b->seeds, b->ctl, b->R, b->NP, b->D, b->ld, b->w, b->c1,
-        b->c2, b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(b->NP));
-    sv_trace_end(tkm, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = eval_rows(b, b->Y, b->fy)) != cudaSuccess) return e;
-    const int tku = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
-    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(
-        b->fy, b->fp, b->action, b->guide, b->best, b->ctl, b->NP, 1, 1, 1);
-    sv_trace_end(tku, st);
-    const int tkc = sv_trace_begin(SEVO_TK_PSO_COPY, st);
-    pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->Y, b->action, b->R, b->NP,
-                                                         b->D, b->ld, make_fastdiv(nq),
-                                                         make_fastdiv(b->NP));
-    sv_trace_end(tkc, st);
-    // SHADE component on the population; its trials count after the NP
-    // PSO rows
-    if ((e = de_trials_and_select(b, b->NP)) != cudaSuccess) return e;
-    // pairwise/3 selection and the DE displacement as the next velocity
-    const int tkp = sv_trace_begin(SEVO_TK_DE_APPLY, st);
-    psode_pick_kernel<<<grid_for(rows, T), T, 0, st>>>(b->fx, b->fy, b->action, rows);
-    psode_combine_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(
-        b->X, b->U, b->Y, b->V, b->action, b->R, b->NP, b->D, b->ld, make_fastdiv(nq),
-        make_fastdiv(b->NP));
-    sv_trace_end(tkp, st);
-    sv_note_launch();
-  } else if (b->alg == SEVO_CSO) {
+    *q = EvalReq{b->U, b->fu, b->NP};
+    return de_trials(b);
+  }
+  if (b->alg == SEVO_CSO) {
     const int half = b->NP / 2;
     const int np2 = pow2_at_least(b->NP);
     const int tkp = sv_trace_begin(SEVO_TK_DE_RANK, st);
@@ -1791,32 +1772,106 @@ cudaError_t sv_batch_generation(Batch* b) {
         b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(half));
     sv_trace_end(tkm, st);
     sv_note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = eval_rows(b, b->U, b->fu, half)) != cudaSuccess) return e;
+    *q = EvalReq{b->U, b->fu, half};
+    return cudaGetLastError();
+  }
+  const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
+  pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
+                                                         b->ctl, b->R, b->NP, b->D, b->ld, b->w,
+                                                         b->c1, b->c2, b->lb, b->ub,
+                                                         make_fastdiv(b->D), make_fastdiv(b->NP));
+  sv_trace_end(tk12, st);
+  *q = EvalReq{b->X, b->fx, b->NP};
+  return cudaGetLastError();
+}
+
+cudaError_t sv_batch_post_eval(Batch* b) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int nq = (b->D + 3) >> 2;
+  const int T = 256;
+  cudaError_t e;
+  if (sv_is_de(b->alg)) {
+    if ((e = de_select(b, 0)) != cudaSuccess) return e;
+    const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
+    de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
+                                                         b->D, b->ld, make_fastdiv(nq),
+                                                         make_fastdiv(b->NP));
+    sv_trace_end(tk11, st);
+    return cudaGetLastError();
+  }
+  if (b->alg == SEVO_CSO) {
     const int tks = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
     cso_scatter_kernel<<<b->R, SEL_THREADS, 0, st>>>(b->fx, b->fu, b->order, b->best, b->ctl,
                                                      b->NP);
     sv_trace_end(tks, st);
-  } else {
-    const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
-    pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
-                                                           b->ctl, b->R, b->NP, b->D, b->ld, b->w,
-                                                           b->c1, b->c2, b->lb, b->ub,
-                                                           make_fastdiv(b->D), make_fastdiv(b->NP));
-    sv_trace_end(tk12, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = eval_rows(b, b->X, b->fx)) != cudaSuccess) return e;
-    const int tk13 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
-    pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action, b->guide, b->best,
-                                                    b->ctl, b->NP, sv_topology(b->alg), 1, 1);
-    sv_trace_end(tk13, st);
-    const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
-    pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
-                                                         b->D, b->ld, make_fastdiv(nq),
-                                                         make_fastdiv(b->NP));
-    sv_trace_end(tk14, st);
+    return cudaGetLastError();
   }
+  const int tk13 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+  pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action,
+                                                                  b->guide, b->best, b->ctl, b->NP,
+                                                                  sv_topology(b->alg), 1, 1);
+  sv_trace_end(tk13, st);
+  const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
+  pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
+                                                       b->D, b->ld, make_fastdiv(nq),
+                                                       make_fastdiv(b->NP));
+  sv_trace_end(tk14, st);
   return cudaGetLastError();
+}
+
+// PSODE (two evaluations per generation): the PSO component's offspring and
+// personal bests, then SHADE on the population, then pairwise/3
+static cudaError_t psode_generation(Batch* b) {
+  cudaStream_t st = b->stream;
+  const int64_t rows = (int64_t)b->R * b->NP;
+  const int nq = (b->D + 3) >> 2;
+  const int T = 256;
+  cudaError_t e;
+  // PSO component: offspring Y from the population, personal bests, guides
+  const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
+  psode_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(
+      b->X, b->V, b->P, b->guide, b->Y, b->seeds, b->ctl, b->R, b->NP, b->D, b->ld, b->w, b->c1,
+      b->c2, b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(b->NP));
+  sv_trace_end(tkm, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = eval_rows(b, b->Y, b->fy)) != cudaSuccess) return e;
+  const int tku = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+  pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(
+      b->fy, b->fp, b->action, b->guide, b->best, b->ctl, b->NP, 1, 1, 1);
+  sv_trace_end(tku, st);
+  const int tkc = sv_trace_begin(SEVO_TK_PSO_COPY, st);
+  pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->Y, b->action, b->R, b->NP,
+                                                       b->D, b->ld, make_fastdiv(nq),
+                                                       make_fastdiv(b->NP));
+  sv_trace_end(tkc, st);
+  // SHADE component on the population; its trials count after the NP
+  // PSO rows
+  if ((e = de_trials_and_select(b, b->NP)) != cudaSuccess) return e;
+  // pairwise/3 selection and the DE displacement as the next velocity
+  const int tkp = sv_trace_begin(SEVO_TK_DE_APPLY, st);
+  psode_pick_kernel<<<grid_for(rows, T), T, 0, st>>>(b->fx, b->fy, b->action, rows);
+  psode_combine_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(
+      b->X, b->U, b->Y, b->V, b->action, b->R, b->NP, b->D, b->ld, make_fastdiv(nq),
+      make_fastdiv(b->NP));
+  sv_trace_end(tkp, st);
+  sv_note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t sv_batch_generation(Batch* b) {
+  if (b->small) {
+    const int tk = sv_trace_begin(SEVO_TK_SMALL_RUN, b->stream);
+    const cudaError_t es = srk_launch(b, 1, 0);
+    sv_trace_end(tk, b->stream);
+    return es;
+  }
+  if (b->alg == SEVO_PSODE) return psode_generation(b);
+  EvalReq q;
+  cudaError_t e;
+  if ((e = sv_batch_pre_eval(b, &q)) != cudaSuccess) return e;
+  if ((e = eval_rows(b, q.M, q.f, q.rpr)) != cudaSuccess) return e;
+  return sv_batch_post_eval(b);
 }
 
 // guides only (after the host overwrote pbest fitness)

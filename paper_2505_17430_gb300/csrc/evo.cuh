@@ -54,6 +54,22 @@ void sv_batch_free(Batch* b);
 cudaError_t sv_batch_init(Batch* b);
 // one generation; gen/count read from b->ctl (set by the caller's launch)
 cudaError_t sv_batch_generation(Batch* b);
+// A generation split at its one evaluation, so that a caller can evaluate
+// the rows of several batches in one pass: pre_eval launches the operators
+// that make the rows to evaluate (rpr rows per run of M, results into f),
+// post_eval the selection that reads the results.  Not for run-per-CTA
+// batches or PSODE (two evaluations per generation): sv_batch_splittable.
+struct EvalReq {
+  const double* M;
+  double* f;
+  int rpr;
+};
+bool sv_batch_splittable(const Batch* b);
+cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q);
+cudaError_t sv_batch_post_eval(Batch* b);
+// the evaluation segments of one batch's request (each naming the batch's
+// rows, results, error word and refined counter)
+void sv_batch_segments(const Batch* b, const EvalReq& q, std::vector<TcSegment>* segs);
 // small batches (b->small): generations gen0 + 1 .. gen0 + gens in run-per-CTA
 // launches; leaves ctl at generation gen0 + gens
 cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens);

@@ -14,20 +14,28 @@ struct EvalAux {
 
 #define SV_MAX_SEG 64
 
-// a run of rows [row0, row0 + nrows) of X evaluated on one problem
+// a run of rows [row0, row0 + nrows) of X evaluated on one problem; X, out,
+// err and refined may name the segment's own population, results, device
+// error word and refined-row counter (null: the evaluation call's)
 struct TcSegment {
   const sevo_problem* p;
   int64_t row0;
   int64_t nrows;
+  const double* X = nullptr;
+  double* out = nullptr;
+  uint32_t* err = nullptr;
+  unsigned long long* refined = nullptr;
 };
 
-// per-segment refinement sub-lists: segment s lists its rows (global row
-// indices) in list[list_off[s] ...] with count[s] entries
+// per-segment refinement sub-lists: segment s lists its rows (row indices of
+// its own X / out) in list[list_off[s] ...] with count[s] entries
 struct RefineTable {
   int nseg;
   const ProblemDev* P[SV_MAX_SEG];
   int64_t list_off[SV_MAX_SEG];
-  unsigned long long* total;  // running count of refined rows (null: none)
+  const double* X[SV_MAX_SEG];  // the segment's rows (null: the launch's X)
+  double* out[SV_MAX_SEG];      // the segment's results (null: the launch's out)
+  unsigned long long* total[SV_MAX_SEG];  // running count of refined rows (null: none)
 };
 
 // SM count of the current device (cached per device)
@@ -49,10 +57,11 @@ cudaError_t sv_eval_refine(const RefineTable& T, const double* X, int64_t ld, in
                            cudaStream_t st);
 // tcgen05 evaluation (TF32 or BF16X3) of segments sharing one D (<= 128);
 // refine lists per segment at list_off[s] with counters counts[s]
-cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, const double* X,
-                                int64_t ld, double* out, int32_t* list, const int64_t* list_off,
-                                int32_t* counts, uint32_t* nonfinite, void* scratch,
-                                size_t scratch_bytes, uint32_t* dev_err, cudaStream_t st);
+// (every segment names its X, out and error word; rows of all segments share ld)
+cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64_t ld,
+                                int32_t* list, const int64_t* list_off, int32_t* counts,
+                                uint32_t* nonfinite, void* scratch, size_t scratch_bytes,
+                                cudaStream_t st);
 // composition scratch of the fused tensor-core pass for `rows` rows
 size_t sv_eval_tc_scratch_bytes(bool any_comp, int prec, int64_t rows);
 // tensor-core evaluation of one segment with D > 128 (convert, GEMM, combine)

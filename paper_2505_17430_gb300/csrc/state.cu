@@ -12,6 +12,13 @@ struct sevo_state {
   sevo_alg_params params;
   uint64_t seed;
   int64_t fes, gens;
+  int device;
+  // sevo_state_step_many: this state's event (its operators done, or, on
+  // the state leading a group, the joint evaluation done) and, on a leading
+  // state, the joint evaluation's scratch (kept for the next group step)
+  cudaEvent_t ev = nullptr;
+  void* joint = nullptr;
+  size_t joint_bytes = 0;
 };
 
 static bool is_de(int alg) { return sv_is_de(alg); }
@@ -64,6 +71,7 @@ static int32_t create_impl(const sevo_problem* const* probs, int32_t R, const se
   }
   s->fes = std::min<int64_t>(a->budget, a->NP);
   s->gens = 0;
+  if (cudaGetDevice(&s->device) != cudaSuccess) s->device = -1;
   *out = s;
   return SEVO_OK;
 }
@@ -111,6 +119,8 @@ extern "C" int32_t sevo_state_best(const sevo_state* s, double* best) {
 extern "C" int32_t sevo_state_destroy(sevo_state* s) {
   if (!s) return SEVO_ERR_ARG;
   cudaStreamSynchronize(s->b.stream);
+  if (s->ev) cudaEventDestroy(s->ev);
+  if (s->joint) cudaFree(s->joint);
   sv_batch_free(&s->b);
   delete s;
   return SEVO_OK;
@@ -145,6 +155,104 @@ extern "C" int32_t sevo_state_step(sevo_state* s, uint64_t philox_counter) {
 
 extern "C" int32_t sevo_pso_step(sevo_state* s, uint64_t philox_counter) {
   return step(s, philox_counter, STEP_PSO);
+}
+
+static cudaError_t state_event(sevo_state* s) {
+  if (s->ev) return cudaSuccess;
+  return cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
+}
+
+// One generation of each state with every state's rows evaluated in one
+// pass: each state's operators on its own stream, then one evaluation of
+// all their rows on the first state's stream (the fused tensor-core kernel
+// then walks all of them in one persistent launch), then each state's
+// selection on its own stream.  Same results as sevo_state_step on each.
+static int32_t step_many(sevo_state* const* st, int32_t n, uint64_t counter) {
+  sevo_state* lead = st[0];
+  const Batch& b0 = lead->b;
+  std::vector<int> counts(n);
+  int64_t rows = 0;
+  bool any_comp = false;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n; ++i) {
+    Batch& b = st[i]->b;
+    counts[i] = (int)std::min<int64_t>(b.per_gen, st[i]->params.budget - st[i]->fes);
+    rows += (int64_t)b.R * b.NP;
+    any_comp = any_comp || b.any_comp;
+  }
+  // joint scratch on the leading state (stream-ordered after its earlier use)
+  const size_t need = sv_eval_scratch_bytes(b0.D, any_comp, b0.prec, rows);
+  if (lead->joint_bytes < need) {
+    if (lead->joint) {
+      if ((e = cudaStreamSynchronize(b0.stream)) != cudaSuccess) return SEVO_ERR_CUDA;
+      cudaFree(lead->joint);
+      lead->joint = nullptr;
+      lead->joint_bytes = 0;
+    }
+    if (cudaMalloc(&lead->joint, need) != cudaSuccess) return SEVO_ERR_OOM;
+    lead->joint_bytes = need;
+  }
+  for (int i = 0; i < n; ++i)
+    if ((e = state_event(st[i])) != cudaSuccess) break;
+  std::vector<TcSegment> segs;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    Batch& b = st[i]->b;
+    EvalReq q;
+    e = sv_ctl_set(&b, (unsigned long long)counter, counts[i]);
+    if (e == cudaSuccess) e = sv_batch_pre_eval(&b, &q);
+    if (e == cudaSuccess) sv_batch_segments(&b, q, &segs);
+    if (e == cudaSuccess && i > 0) {
+      e = cudaEventRecord(st[i]->ev, b.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b0.stream, st[i]->ev, 0);
+    }
+  }
+  if (e == cudaSuccess) {
+    EvalScratch sc;
+    sv_eval_scratch_carve(lead->joint, b0.D, any_comp, b0.prec, rows, &sc);
+    e = sv_eval_segments(segs.data(), (int)segs.size(), b0.prec, segs[0].X, b0.ld, segs[0].out,
+                         sc, b0.stream);
+  }
+  if (e == cudaSuccess && n > 1) e = cudaEventRecord(lead->ev, b0.stream);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    Batch& b = st[i]->b;
+    if (i > 0) e = cudaStreamWaitEvent(b.stream, lead->ev, 0);
+    if (e == cudaSuccess) e = sv_batch_post_eval(&b);
+  }
+  if (e != cudaSuccess) {
+    sv_set_last_cuda_error(e);
+    return SEVO_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    st[i]->fes += counts[i];
+    st[i]->gens += 1;
+  }
+  return SEVO_OK;
+}
+
+extern "C" int32_t sevo_state_step_many(sevo_state* const* states, int32_t n,
+                                        uint64_t philox_counter) {
+  if (!states || n < 1 || n > SEVO_STEP_MANY_MAX) return SEVO_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SEVO_ERR_CUDA;
+  bool joint = true;
+  for (int i = 0; i < n; ++i) {
+    const sevo_state* s = states[i];
+    if (!s) return SEVO_ERR_ARG;
+    for (int k = 0; k < i; ++k)
+      if (states[k] == s) return SEVO_ERR_ARG;
+    if (s->device != dev) return SEVO_ERR_STATE;
+    if (s->fes >= s->params.budget) return SEVO_ERR_STATE;
+    joint = joint && sv_batch_splittable(&s->b) && s->b.D == states[0]->b.D &&
+            s->b.prec == states[0]->b.prec && s->b.ld == states[0]->b.ld;
+  }
+  if (joint && n > 1) return step_many(states, n, philox_counter);
+  // nothing to share (one state, or states whose generations cannot share
+  // an evaluation): one generation each
+  for (int i = 0; i < n; ++i) {
+    const int32_t r = step(states[i], philox_counter, STEP_ANY);
+    if (r != SEVO_OK) return r;
+  }
+  return SEVO_OK;
 }
 
 extern "C" int32_t sevo_state_result(const sevo_state* s, double* best, int64_t* fes,

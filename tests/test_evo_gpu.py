@@ -703,3 +703,71 @@ def test_shade_kinds_at_largest_population(S, alg):
     sh = st.get_shade()
     assert sh["kpb"].min() >= 2 and sh["kpb"].max() <= round(0.2 * NP)
     assert np.isfinite(st.result()["best"])
+
+
+def _group(S, D, NP, prec, algs, torch, fams=(0, 2, 3, 6, 7)):
+    """One batched state per algorithm over the same problems, each on its
+    own stream (as a caller overlapping them would)."""
+    probs = [S.Problem(700 + f, f, D) for f in fams]
+    out = []
+    for k, alg in enumerate(algs):
+        stream = torch.cuda.Stream()
+        st = S.State(probs, S.alg_params(alg, NP, 10 ** 9, prec=prec),
+                     [31 + 100 * k + r for r in range(len(probs))], stream=stream)
+        st.torch_stream = stream
+        out.append(st)
+    return probs, out
+
+
+@pytest.mark.parametrize("prec,D", [("TF32", 30), ("BF16X3", 100), ("FP64", 30), ("FP32", 30),
+                                    ("TF32", 200)])
+def test_step_many_equals_separate_steps(S, prec, D):
+    """sevo_state_step_many over DE/rand/1, DE/current-to-pbest, SHADE,
+    ring PSO and CSO states evaluates all their rows in one pass (one fused
+    launch at D <= 128 in the tensor-core modes) and leaves every state
+    bit-identical to stepping each with sevo_state_step, over 4 generations."""
+    import torch
+    algs = [S.DE_RAND1, S.DE_CTPB, S.DE_SHADE, S.PSO_RING, S.CSO]
+    NP = 260
+    _, A = _group(S, D, NP, getattr(S, prec), algs, torch)
+    _, B = _group(S, D, NP, getattr(S, prec), algs, torch)
+    for g in range(1, 5):
+        assert S.sevo_state_step_many(A, g) == 0
+        for st in B:
+            assert st.step(g) == 0
+    torch.cuda.synchronize()
+    for a, b in zip(A, B):
+        ga, gb = a.get(), b.get()
+        for key in ("X", "fx", "U", "fu", "A", "V", "P", "fp", "part"):
+            assert np.array_equal(ga[key], gb[key]), key
+        assert ga["asize"] == gb["asize"]
+        ra, rb = a.result(), b.result()
+        assert ra["best"] == rb["best"] and ra["fes"] == rb["fes"] and ra["gens"] == 4
+        assert ra["refined"] == rb["refined"]
+        assert np.array_equal(a.best(), b.best())
+
+
+def test_step_many_falls_back_and_checks_arguments(S):
+    """With a PSODE state (two evaluations per generation) the states step
+    one after another, with the same results; repeated states, an empty
+    list and a spent budget are refused before anything is launched."""
+    import torch
+    D, NP = 20, 40
+    algs = [S.DE_CTPB, S.PSODE]
+    _, A = _group(S, D, NP, S.TF32, algs, torch, fams=(2, 4))
+    _, B = _group(S, D, NP, S.TF32, algs, torch, fams=(2, 4))
+    for g in range(1, 4):
+        assert S.sevo_state_step_many(A, g) == 0
+        for st in B:
+            assert st.step(g) == 0
+    for a, b in zip(A, B):
+        ga, gb = a.get(), b.get()
+        assert np.array_equal(ga["X"], gb["X"]) and np.array_equal(ga["fx"], gb["fx"])
+    assert S.sevo_state_step_many([A[0], A[0]], 9) == S.ERR_ARG
+    assert S.sevo_state_step_many([], 9) == S.ERR_ARG
+    p = S.Problem(3, S.RASTRIGIN, D)
+    done = S.State([p], S.alg_params(S.DE_RAND1, NP, NP + NP), [1])
+    assert done.step(1) == 0  # budget now spent
+    before = A[0].result()["gens"]
+    assert S.sevo_state_step_many([A[0], done], 9) == S.ERR_STATE
+    assert A[0].result()["gens"] == before
