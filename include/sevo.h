@@ -388,10 +388,17 @@ typedef struct {          /* caller-allocated host arrays, ntasks entries each *
   int64_t evals;          /* total evaluations performed                        */
 } sevo_grid_result;
 
-/* Run every task to its budget.  Tasks with equal (alg kind, D, NP, budget,
- * prec) advance together: one batched launch per kernel per generation over
- * all their runs, generations captured into CUDA graphs.  Results equal the
- * single-run state API's for the same (problem, alg, seed).  Synchronous. */
+/* Run every task to its budget (Sec. 2.4, Listing 3: the runner over
+ * (problem, run) tasks).  Tasks with the same algorithm entry and D form a
+ * bucket that advances together: one batched launch per kernel per
+ * generation over all their runs, generations captured into CUDA graphs.
+ * The buckets run side by side, each on its own stream that starts after
+ * the work already queued on `stream` (NULL: the legacy default stream);
+ * the call returns when all of them are done and `stream` is ordered after
+ * them.  Results equal the single-run state API's for the same (problem,
+ * alg, seed).  wall_ms is the device time from the start of the first
+ * bucket to the end of the last.  Synchronous; every bucket's state is
+ * allocated at once (device memory ~ the sum over buckets). */
 int32_t sevo_run_grid(const sevo_grid* grid, sevo_grid_result* res, void* stream);
 
 /* ---- execution policy (library infrastructure; the paper has no counterpart)
@@ -409,8 +416,17 @@ enum sevo_policy {
    * mixed values as computed (the rows are still counted in `refined`), to
    * measure the mixed arithmetic's own error.  States, grids and
    * sevo_evaluate_noalloc always refine. */
-  SEVO_POLICY_REFINE = 1
+  SEVO_POLICY_REFINE = 1,
+  /* for testing the failure path: > 0 makes every CTA of the fused
+   * tensor-core evaluation (TF32 / BF16X3, D <= 128) first wait on a
+   * barrier that nothing completes, bounded by this many clock cycles
+   * (1 .. SEVO_TEST_WAIT_MAX), before it issues any TMEM allocation, TMA
+   * copy or MMA; the wait gives up, the CTA leaves with nothing in flight
+   * and the call reports SEVO_ERR_TIMEOUT like a real timeout.  0 (default):
+   * off. */
+  SEVO_POLICY_TEST_WAIT = 2
 };
+#define SEVO_TEST_WAIT_MAX 100000000
 /* SEVO_ERR_ARG for an unknown key or value */
 int32_t sevo_set_policy(int32_t key, int64_t value);
 /* current value, or -1 for an unknown key */

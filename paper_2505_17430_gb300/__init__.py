@@ -111,6 +111,7 @@ SIGNATURES = {
 SEVO_TRACE_KINDS = 17
 POLICY_SMALL_RUNS = 0
 POLICY_REFINE = 1
+POLICY_TEST_WAIT = 2
 
 _LIB = None
 

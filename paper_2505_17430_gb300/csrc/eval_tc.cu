@@ -82,12 +82,14 @@ struct FusedGeom {
   int dbox;        // staged mode: columns per staged row (D rounded up to even)
   int xb_bytes;    // staged mode: bytes of one quarter-tile buffer
   int nxb;         // staged mode: number of quarter-tile buffers
+  long long probe_wait;  // > 0: test of the timeout path (SEVO_POLICY_TEST_WAIT)
 };
 
 struct __align__(8) Bars {
   uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], s_full[2];
   uint64_t x_full[MAX_XB], x_empty[MAX_XB];
   uint64_t b_full, mma_done;
+  uint64_t probe;  // never arrived on: the timeout test waits on it
   uint32_t tmem_base;
   int abort;
 };
@@ -236,8 +238,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc::mbar_init(&bars.b_full, 1);
     tc::mbar_init(&bars.mma_done, 1);
+    tc::mbar_init(&bars.probe, 1);
     bars.abort = 0;
     tc::fence_mbar_init();
+  }
+  if (geo.probe_wait > 0) {
+    // the timeout path under test: one bounded wait on a barrier nothing
+    // arrives on, before any TMEM allocation, TMA copy or MMA is issued, so
+    // that the CTA can leave with nothing in flight
+    __syncthreads();
+    if (tid == 0 && !tc::mbar_wait(&bars.probe, 0, &bars.abort, geo.probe_wait))
+      raise_abort(&bars, T);
+    __syncthreads();
+    if (bars.abort) return;
   }
   if (warp == WARP_MMA) {
     tc::tmem_alloc(&bars.tmem_base, 2 * TCOLS);
@@ -681,6 +694,7 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
     xmap_of[k] = m;
   }
   g.vec_ok = aligned;
+  g.probe_wait = sv_policy_test_wait();
   g.dbox = (h0.D + 1) & ~1;
   g.xb_bytes = XQ * g.dbox * 8;
   const size_t budget = 220 * 1024;

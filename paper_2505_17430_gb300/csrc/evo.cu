@@ -98,6 +98,19 @@ __global__ void ctl_advance_kernel(GenCtl* ctl, int NP, long long budget, int pe
   ctl->count = (int)(c < 0 ? 0 : (c > per_gen ? per_gen : c));
 }
 
+// The generation's counter for its first kernel: from the launch when the
+// caller set it (block 0 then publishes it to the control block for the
+// generation's later kernels, which run after this one in stream order),
+// else from the control block (generations replayed from a graph).
+__device__ __forceinline__ unsigned long long gen_of(GenCtl* ctl, const CtlSet& cs) {
+  if (!cs.on) return ctl->gen;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->gen = cs.gen;
+    ctl->count = cs.count;
+  }
+  return cs.gen;
+}
+
 // ---------------------------------------------------------------- indexing
 // n / d for 0 <= n < 2^31 by multiply-high (Granlund and Montgomery's
 // round-up method): q = (umulhi(n, m) + n) >> l with l = ceil(log2 d) and
@@ -276,7 +289,7 @@ template <int ALG>
 __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict__ U,
                                 const double* __restrict__ A, const int32_t* __restrict__ asize,
                                 const int32_t* __restrict__ order, int32_t* __restrict__ part,
-                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
+                                const uint64_t* __restrict__ seeds, GenCtl* ctl, CtlSet cs,
                                 int R, int NP, int D, int ld, double F, unsigned long long cr_thr,
                                 double lb, double ub, int pk, FastDiv fq, FastDiv fnp,
                                 const double* __restrict__ Fi, const double* __restrict__ CRi,
@@ -284,7 +297,7 @@ __global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict
   const int nq = (D + 3) >> 2;
   const int64_t total = (int64_t)R * NP * nq;
   const bool fast = total < (1ll << 31);
-  const unsigned long long gen = ctl->gen;
+  const unsigned long long gen = gen_of(ctl, cs);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fq, fnp);
@@ -301,11 +314,11 @@ constexpr double SV_PI = 3.14159265358979323846;
 
 __global__ void shade_param_kernel(const double* __restrict__ MF, const double* __restrict__ MCR,
                                    const uint64_t* __restrict__ seeds,
-                                   const GenCtl* __restrict__ ctl, int R, int NP, int H,
+                                   GenCtl* ctl, CtlSet cs, int R, int NP, int H,
                                    double* __restrict__ Fi, double* __restrict__ CRi,
                                    int32_t* __restrict__ kpb) {
   const int64_t rows = (int64_t)R * NP;
-  const unsigned long long gen = ctl->gen;
+  const unsigned long long gen = gen_of(ctl, cs);
   const double pmin = 2.0 / (double)NP;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -709,13 +722,13 @@ constexpr int CSO_THREADS = 512;
 
 __global__ void __launch_bounds__(CSO_THREADS)
     cso_pair_kernel(const double* __restrict__ fx, int32_t* __restrict__ pair,
-                    const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl, int NP,
+                    const uint64_t* __restrict__ seeds, GenCtl* ctl, CtlSet cs, int NP,
                     int npow2) {
   extern __shared__ __align__(16) unsigned char cs_sm[];
   uint32_t* key = reinterpret_cast<uint32_t*>(cs_sm);
   int32_t* idx = reinterpret_cast<int32_t*>(key + npow2);
   const int r = blockIdx.x, tid = threadIdx.x;
-  const unsigned long long gen = ctl->gen;
+  const unsigned long long gen = gen_of(ctl, cs);
   for (int i = tid; i < npow2; i += blockDim.x) {
     key[i] = (i < NP) ? sv_draw(seeds[r], 0u, (uint32_t)i, (uint32_t)gen, SV_P_CSO).x : 0xFFFFFFFFu;
     idx[i] = (i < NP) ? i : 0x7FFFFFFF;
@@ -865,12 +878,12 @@ __device__ __forceinline__ void pso_move_elem(double* __restrict__ X, double* __
 
 __global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
                                 const double* __restrict__ P, const int32_t* __restrict__ guide,
-                                const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl,
+                                const uint64_t* __restrict__ seeds, GenCtl* ctl, CtlSet cs,
                                 int R, int NP, int D, int ld, double w, double c1, double c2,
                                 double lb, double ub, FastDiv fd, FastDiv fnp) {
   const int64_t total = (int64_t)R * NP * D;
   const bool fast = total < (1ll << 31);
-  const unsigned long long gen = ctl->gen;
+  const unsigned long long gen = gen_of(ctl, cs);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fd, fnp);
@@ -1009,12 +1022,12 @@ __global__ void psode_move_kernel(const double* __restrict__ X, const double* __
                                   const double* __restrict__ P,
                                   const int32_t* __restrict__ guide, double* __restrict__ Y,
                                   const uint64_t* __restrict__ seeds,
-                                  const GenCtl* __restrict__ ctl, int R, int NP, int D, int ld,
+                                  GenCtl* ctl, CtlSet cs, int R, int NP, int D, int ld,
                                   double w, double c1, double c2, double lb, double ub,
                                   FastDiv fd, FastDiv fnp) {
   const int64_t total = (int64_t)R * NP * D;
   const bool fast = total < (1ll << 31);
-  const unsigned long long gen = ctl->gen;
+  const unsigned long long gen = gen_of(ctl, cs);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fd, fnp);
@@ -1397,10 +1410,17 @@ unsigned grid_for(int64_t work, int threads) {
 // ====================================================================== host
 static std::atomic<int> g_policy_small_runs{0};
 static std::atomic<int> g_policy_refine{1};
+static std::atomic<long long> g_policy_test_wait{0};
 
 int sv_policy_refine() { return g_policy_refine.load(); }
+long long sv_policy_test_wait() { return g_policy_test_wait.load(); }
 
 extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
+  if (key == SEVO_POLICY_TEST_WAIT) {
+    if (value < 0 || value > SEVO_TEST_WAIT_MAX) return SEVO_ERR_ARG;
+    g_policy_test_wait.store((long long)value);
+    return SEVO_OK;
+  }
   if (value != 0 && value != 1) return SEVO_ERR_ARG;
   if (key == SEVO_POLICY_SMALL_RUNS) {
     g_policy_small_runs.store((int)value);
@@ -1415,6 +1435,7 @@ extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
 extern "C" int64_t sevo_get_policy(int32_t key) {
   if (key == SEVO_POLICY_SMALL_RUNS) return g_policy_small_runs.load();
   if (key == SEVO_POLICY_REFINE) return g_policy_refine.load();
+  if (key == SEVO_POLICY_TEST_WAIT) return g_policy_test_wait.load();
   return -1;
 }
 
@@ -1602,6 +1623,17 @@ cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count) {
   return cudaGetLastError();
 }
 
+void sv_ctl_defer(Batch* b, unsigned long long gen, int count) {
+  b->pending = CtlSet{gen, count, 1};
+}
+
+// the pending control update, for the generation's first kernel
+static CtlSet take_ctl(Batch* b) {
+  const CtlSet c = b->pending;
+  b->pending.on = 0;
+  return c;
+}
+
 cudaError_t sv_ctl_advance(Batch* b) {
   const int tk2 = sv_trace_begin(SEVO_TK_CONTROL, b->stream);
   ctl_advance_kernel<<<1, 1, 0, b->stream>>>(b->ctl, b->NP, (long long)b->budget, b->per_gen);
@@ -1687,7 +1719,8 @@ static cudaError_t de_trials(Batch* b) {
   cudaError_t e;
   if (shade) {
     const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-    shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl, b->R,
+    shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl,
+                                                        take_ctl(b), b->R,
                                                         b->NP, SEVO_SHADE_H, b->Fi, b->CRi,
                                                         b->kpb);
     sv_trace_end(tks, st);
@@ -1707,20 +1740,20 @@ static cudaError_t de_trials(Batch* b) {
     const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     if (shade)
       de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
-          b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
+          b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
+          b->NP, b->D, b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
           b->Fi, b->CRi, b->kpb);
     else
       de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
-          b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-          b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
+          b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
+          b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
           make_fastdiv(b->NP), nullptr, nullptr, nullptr);
     sv_trace_end(tk8, st);
   } else {
     const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
-        b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, b->R, b->NP, b->D,
-        b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
+        b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
+        b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
         nullptr, nullptr, nullptr);
     sv_trace_end(tk9, st);
   }
@@ -1762,7 +1795,7 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
     const int np2 = pow2_at_least(b->NP);
     const int tkp = sv_trace_begin(SEVO_TK_DE_RANK, st);
     cso_pair_kernel<<<b->R, CSO_THREADS, (size_t)np2 * 8, st>>>(b->fx, b->order, b->seeds, b->ctl,
-                                                                b->NP, np2);
+                                                                take_ctl(b), b->NP, np2);
     sv_trace_end(tkp, st);
     const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
     cso_mean_kernel<<<dim3((b->D + 127) / 128, std::min(b->R, 65535)), 128, 0, st>>>(
@@ -1777,7 +1810,7 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
   }
   const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
   pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
-                                                         b->ctl, b->R, b->NP, b->D, b->ld, b->w,
+                                                         b->ctl, take_ctl(b), b->R, b->NP, b->D, b->ld, b->w,
                                                          b->c1, b->c2, b->lb, b->ub,
                                                          make_fastdiv(b->D), make_fastdiv(b->NP));
   sv_trace_end(tk12, st);
@@ -1831,7 +1864,8 @@ static cudaError_t psode_generation(Batch* b) {
   // PSO component: offspring Y from the population, personal bests, guides
   const int tkm = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
   psode_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(
-      b->X, b->V, b->P, b->guide, b->Y, b->seeds, b->ctl, b->R, b->NP, b->D, b->ld, b->w, b->c1,
+      b->X, b->V, b->P, b->guide, b->Y, b->seeds, b->ctl, take_ctl(b), b->R, b->NP, b->D, b->ld,
+      b->w, b->c1,
       b->c2, b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(b->NP));
   sv_trace_end(tkm, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -13,6 +13,15 @@ struct GenCtl {
   int pad;
 };
 
+// A generation's counter and count handed to its first kernel as a launch
+// argument (on = 1), which publishes them to the control block: no separate
+// launch to set the block.  on = 0: the kernel reads the block.
+struct CtlSet {
+  unsigned long long gen;
+  int count;
+  int on;
+};
+
 struct Batch {
   int alg, D, NP, R, ld;  // R runs of NP rows each, row stride ld (even)
   int per_gen;            // evaluations counted per generation (CSO: NP / 2)
@@ -44,6 +53,7 @@ struct Batch {
   size_t eval_bytes;
   bool any_comp;
   cudaStream_t stream;
+  CtlSet pending{0ull, 0, 0};   // set by sv_ctl_defer, taken by the next generation's first kernel
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
@@ -74,6 +84,9 @@ void sv_batch_segments(const Batch* b, const EvalReq& q, std::vector<TcSegment>*
 // launches; leaves ctl at generation gen0 + gens
 cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens);
 cudaError_t sv_ctl_set(Batch* b, unsigned long long gen, int count);
+// the next generation's first kernel sets the control block (no launch of
+// its own); for batches stepped by sv_batch_generation, not run-per-CTA ones
+void sv_ctl_defer(Batch* b, unsigned long long gen, int count);
 cudaError_t sv_ctl_advance(Batch* b);  // gen += 1, count from gen and budget
 int sv_pbest_k(double p, int NP);
 cudaError_t sv_batch_guides(Batch* b);

@@ -88,6 +88,8 @@ struct EvalScratch {
 size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
 // SEVO_POLICY_REFINE's current value (1: refine, the default)
 int sv_policy_refine();
+// SEVO_POLICY_TEST_WAIT's current value (0: off, the default)
+long long sv_policy_test_wait();
 void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
                            EvalScratch* s);
 // evaluate segments (same D) into out with refinement; resets counters first

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/sevo.h"
+#include "u53.cuh"
 
 #define SV_MAXG SEVO_MAX_GROUPS
 #define SV_MAXC SEVO_MAX_COMPONENTS
@@ -56,7 +57,7 @@ __host__ __device__ __forceinline__ uint4 sv_draw(uint64_t seed, uint32_t c0, ui
 __host__ __device__ __forceinline__ double sv_u53(uint32_t w0, uint32_t w1) {
   const uint64_t m = ((uint64_t)(w0 >> 5) << 26) | (uint64_t)(w1 >> 6);
 #ifdef __CUDA_ARCH__
-  return __ull2double_rn(m) * 0x1p-53;
+  return sv_u53_of(m);  // integer operations only (u53.cuh)
 #else
   return (double)m * 0x1p-53;
 #endif

@@ -134,7 +134,11 @@ static int32_t step(sevo_state* s, uint64_t counter, StepKind kind) {
   if (kind == STEP_PSO && !sv_is_pso(s->params.alg)) return SEVO_ERR_STATE;
   if (s->fes >= s->params.budget) return SEVO_ERR_STATE;
   const int count = (int)std::min<int64_t>(s->b.per_gen, s->params.budget - s->fes);
-  cudaError_t e = sv_ctl_set(&s->b, (unsigned long long)counter, count);
+  cudaError_t e = cudaSuccess;
+  if (s->b.small)
+    e = sv_ctl_set(&s->b, (unsigned long long)counter, count);
+  else
+    sv_ctl_defer(&s->b, (unsigned long long)counter, count);
   if (e == cudaSuccess) e = sv_batch_generation(&s->b);
   if (e != cudaSuccess) {
     sv_set_last_cuda_error(e);
@@ -198,8 +202,8 @@ static int32_t step_many(sevo_state* const* st, int32_t n, uint64_t counter) {
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     Batch& b = st[i]->b;
     EvalReq q;
-    e = sv_ctl_set(&b, (unsigned long long)counter, counts[i]);
-    if (e == cudaSuccess) e = sv_batch_pre_eval(&b, &q);
+    sv_ctl_defer(&b, (unsigned long long)counter, counts[i]);
+    e = sv_batch_pre_eval(&b, &q);
     if (e == cudaSuccess) sv_batch_segments(&b, q, &segs);
     if (e == cudaSuccess && i > 0) {
       e = cudaEventRecord(st[i]->ev, b.stream);

@@ -67,3 +67,44 @@ def test_bound_compare_matches_ieee():
         subprocess.check_call([cxx, "-O2", "-I", CSRC, src, "-o", exe])
         bad, n = map(int, subprocess.check_output([exe]).split())
     assert n > 4_000_000 and bad == 0
+
+
+U53_HARNESS = r"""
+#include "u53.cuh"
+#include <stdio.h>
+int main() {
+  long bad = 0, n = 0;
+  uint64_t edge[] = {0ull, 1ull, 2ull, 3ull, (1ull << 52) - 1, 1ull << 52, (1ull << 52) + 1,
+                     (1ull << 53) - 1, (1ull << 53) - 2, 1ull << 26, (1ull << 26) - 1};
+  for (unsigned i = 0; i < sizeof(edge) / sizeof(edge[0]); ++i, ++n)
+    bad += sv_u53_of(edge[i]) != (double)edge[i] * 0x1p-53;
+  for (int b = 0; b < 53; ++b, n += 2) {
+    bad += sv_u53_of(1ull << b) != (double)(1ull << b) * 0x1p-53;
+    bad += sv_u53_of((2ull << b) - 1) != (double)((2ull << b) - 1) * 0x1p-53;
+  }
+  uint64_t s = 0x243F6A8885A308D3ull;
+  for (int t = 0; t < 5000000; ++t, ++n) {
+    s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+    const uint64_t m = (s >> (11 + (t % 40)));  /* every magnitude below 2^53 */
+    bad += sv_u53_of(m) != (double)m * 0x1p-53;
+  }
+  printf("%ld %ld\n", bad, n);
+  return 0;
+}
+"""
+
+
+def test_u53_integer_construction_matches_conversion():
+    """The 53-bit uniform is assembled from integer operations on the GPU
+    (u53.cuh, no FP64-pipe conversion); it must be exactly the double of
+    m * 2^-53 for every 53-bit m, which the oracle forms by conversion."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "t.cpp"), os.path.join(d, "t")
+        with open(src, "w") as f:
+            f.write(U53_HARNESS)
+        subprocess.check_call([cxx, "-O2", "-I", CSRC, src, "-o", exe])
+        bad, n = map(int, subprocess.check_output([exe]).split())
+    assert n > 5_000_000 and bad == 0

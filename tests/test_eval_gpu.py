@@ -330,3 +330,35 @@ def test_refine_policy_returns_mixed_values(S):
     assert (err_raw[below] > tol64(want, bnd)[below]).any()  # really the TF32 values
     assert np.array_equal(raw[~below], ref[~below])
     assert lib.sevo_set_policy(S.POLICY_REFINE, 2) == -1
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+def test_bounded_wait_times_out_and_library_stays_usable(S, prec):
+    """SEVO_POLICY_TEST_WAIT makes every CTA of the fused kernel wait on a
+    barrier nothing completes, for 20,000 clock cycles, before it issues any
+    TMEM, TMA or MMA work: the wait gives up, sevo_evaluate_sync reports
+    SEVO_ERR_TIMEOUT, and the next call on the same problem (policy off)
+    succeeds and matches the oracle."""
+    D = 30
+    p, q = S.Problem(71, S.ACKLEY, D), O.Problem(71, O.ACKLEY, D)
+    X = inputs.uniform_pop(300, D, seed=71)
+    lib = S.lib()
+    assert lib.sevo_set_policy(S.POLICY_TEST_WAIT, -1) == S.ERR_ARG
+    assert lib.sevo_set_policy(S.POLICY_TEST_WAIT, 20000) == 0
+    try:
+        import ctypes as C
+        import torch
+        xt = to_dev(X)
+        out = torch.zeros(300, dtype=torch.float64, device="cuda")
+        ref, nf = C.c_int64(), C.c_int64()
+        rc = lib.sevo_evaluate_sync(p.h, C.c_void_p(xt.data_ptr()), 300, D, D,
+                                    C.c_void_p(out.data_ptr()), getattr(S, prec),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                    C.byref(ref), C.byref(nf))
+        assert rc == S.ERR_TIMEOUT
+    finally:
+        assert lib.sevo_set_policy(S.POLICY_TEST_WAIT, 0) == 0
+    assert lib.sevo_get_policy(S.POLICY_TEST_WAIT) == 0
+    got, info = p.evaluate(to_dev(X), prec=getattr(S, prec), sync=True)
+    assert info["status"] == 0
+    _check_mixed(prec, got.cpu().numpy(), q.eval(X), bound(p, q, X), info)

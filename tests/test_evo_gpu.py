@@ -771,3 +771,37 @@ def test_step_many_falls_back_and_checks_arguments(S):
     before = A[0].result()["gens"]
     assert S.sevo_state_step_many([A[0], done], 9) == S.ERR_STATE
     assert A[0].result()["gens"] == before
+
+
+def test_grid_buckets_concurrent_on_caller_stream(S):
+    """Buckets of several (algorithm, D) pairs run side by side on streams
+    forked from the caller's: the grid started behind other work on a side
+    stream gives the same results as on the current stream, and matches a
+    run driven alone through the state API."""
+    import torch
+    probs = [S.Problem(11, S.RASTRIGIN, 10), S.Problem(12, S.HYBRID, 30),
+             S.Problem(13, S.COMPOSITION, 10)]
+    algs = [S.alg_params(S.DE_CTPB, 30, 1500, prec=S.TF32),
+            S.alg_params(S.PSO_GBEST, 20, 1510, prec=S.TF32),
+            S.alg_params(S.CSO, 20, 1200, prec=S.FP64)]
+    tasks = [(pi, ai, 500 + 7 * pi + 31 * ai + k) for pi in range(3) for ai in range(3)
+             for k in range(2)]
+    ref = S.sevo_run_grid(probs, algs, tasks, gens_per_graph=4)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        big = torch.empty(1 << 26, device="cuda").uniform_()  # work queued before the grid
+        res = S.sevo_run_grid(probs, algs, tasks, gens_per_graph=4, stream=side)
+        after = big.sum()
+    torch.cuda.synchronize()
+    assert torch.isfinite(after)
+    for key in ("best", "fes", "gens", "success"):
+        assert np.array_equal(res[key], ref[key]), key
+    assert res["wall_ms"] > 0 and res["evals"] == ref["evals"]
+    t = 5
+    pi, ai, seed = tasks[t]
+    st = S.State(probs[pi], algs[ai], seed)
+    gen = 0
+    while st.result()["fes"] < algs[ai].budget:
+        gen += 1
+        st.step(gen)
+    assert st.result()["best"] == res["best"][t]
