@@ -112,6 +112,7 @@ SEVO_TRACE_KINDS = 17
 POLICY_SMALL_RUNS = 0
 POLICY_REFINE = 1
 POLICY_TEST_WAIT = 2
+POLICY_FUSE_OPS = 3
 
 _LIB = None
 

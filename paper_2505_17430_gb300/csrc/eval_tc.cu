@@ -25,6 +25,7 @@
 
 #include "bodies.cuh"
 #include "kernels.cuh"
+#include "ops.cuh"
 #include "tc_ptx.cuh"
 #include "tc_walk.cuh"
 
@@ -42,6 +43,7 @@ constexpr int TCOLS = 128;                      // TMEM columns per accumulator 
 constexpr int A_KB_BYTES = BM * 128;            // one 128-byte-wide K block of A
 constexpr int MAX_SEG = 64;
 constexpr int MAX_XMAPS = 4;                    // distinct populations per launch (staged mode)
+constexpr int MAX_OPS = 8;                      // distinct operators per launch
 
 struct Seg {
   const ProblemDev* P;
@@ -57,11 +59,19 @@ struct Seg {
   int32_t comp;      // composition family
   int32_t sidx;      // index of the segment's refinement counter
   int32_t xmap;      // staged mode: index of the tensor map over X
+  int32_t op;        // index into the launch's operators (-1: rows are loaded from X)
+  int32_t pad;
 };
 
 // tensor maps over the launch's distinct populations (staged mode)
 struct XMaps {
   CUtensorMap m[MAX_XMAPS];
+};
+
+// the launch's operators (segments whose rows the producers make)
+struct GenOps {
+  int n;
+  GenOp op[MAX_OPS];
 };
 
 struct SegTable {
@@ -205,14 +215,56 @@ __device__ __forceinline__ void convert_store(int r, const double (&x)[4], int k
   }
 }
 
+// quad jq of batch row `row` made by the operator: a DE trial quad (written
+// to U) or four moved coordinates of a particle (written to X and V in
+// place), returned in v
+__device__ __forceinline__ void make_row_quad(const GenOp& op, unsigned long long gen,
+                                              int64_t row, int jq, double (&v)[4]) {
+  const int r = (int)(row / op.NP), i = (int)(row - (int64_t)r * op.NP);
+  switch (op.alg) {
+    case SEVO_DE_RAND1:
+      de_trial_elem<SEVO_DE_RAND1>(op.X, op.U, nullptr, nullptr, nullptr, op.part, op.seeds,
+                                   op.NP, op.D, op.ld, op.F, op.cr_thr, op.lb, op.ub, 0, gen, r,
+                                   i, jq, nullptr, nullptr, nullptr, v);
+      break;
+    case SEVO_DE_CTPB:
+      de_trial_elem<SEVO_DE_CTPB>(op.X, op.U, op.A, op.asize, op.order, op.part, op.seeds, op.NP,
+                                  op.D, op.ld, op.F, op.cr_thr, op.lb, op.ub, op.pk, gen, r, i,
+                                  jq, nullptr, nullptr, nullptr, v);
+      break;
+    case SEVO_DE_SHADE:
+      de_trial_elem<SEVO_DE_SHADE>(op.X, op.U, nullptr, nullptr, op.order, op.part, op.seeds,
+                                   op.NP, op.D, op.ld, 0.0, 0ull, op.lb, op.ub, op.pk, gen, r, i,
+                                   jq, op.Fi, op.CRi, op.kpb, v);
+      break;
+    default: {  // PSO move, in place
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = jq * 4 + q;
+        v[q] = 0.0;
+        if (j < op.D) {
+          const int64_t e = row * op.ld + j;
+          double vn;
+          const double xn = pso_moved(op.U, op.V, op.P, op.guide, op.seeds, gen, op.NP, op.ld,
+                                      op.w, op.c1, op.c2, op.lb, op.ub, r, i, j, row, e, &vn);
+          op.U[e] = xn;
+          op.V[e] = vn;
+          v[q] = xn;
+        }
+      }
+    }
+  }
+}
+
 // XTMA: FP64 rows are streamed by TMA (32-row quarter tiles) into a ring of
 // shared-memory buffers and converted from there; the A tile is then single
 // buffered.  Otherwise producers load rows from global memory directly.
 template <bool BF16, bool XTMA>
 __global__ void __launch_bounds__(NTHREADS, 1)
     eval_tc_fused(const __grid_constant__ SegTable T, const FusedGeom geo,
-                  const __grid_constant__ XMaps maps, int64_t ld, double* __restrict__ comp_g,
-                  double* __restrict__ comp_s, ListOut lo) {
+                  const __grid_constant__ XMaps maps, const __grid_constant__ GenOps ops,
+                  int64_t ld, double* __restrict__ comp_g, double* __restrict__ comp_s,
+                  ListOut lo) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ Bars bars;
   __shared__ float sS[2][BM];
@@ -241,6 +293,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc::mbar_init(&bars.probe, 1);
     bars.abort = 0;
     tc::fence_mbar_init();
+  }
+  if (blockIdx.x == 0 && tid == 0) {  // the operators' counters, for the later kernels
+    for (int k = 0; k < ops.n; ++k)
+      if (ops.op[k].cs.on) {
+        ops.op[k].ctl->gen = ops.op[k].cs.gen;
+        ops.op[k].ctl->count = ops.op[k].cs.count;
+      }
   }
   if (geo.probe_wait > 0) {
     // the timeout path under test: one bounded wait on a barrier nothing
@@ -442,6 +501,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (lane == 0) tc::mbar_arrive(&bars.x_empty[b]);
         }
         if (!okq) break;
+      } else if (sg.op >= 0) {
+        // rows made here: DE trials or moved particles (component 0), read
+        // back from the segment's rows by later components of a composition
+        const GenOp& op = ops.op[sg.op];
+        const unsigned long long gen = op.cs.on ? op.cs.gen : op.ctl->gen;
+        for (int rb = 0; rb < RPW; rb += 4) {
+          double xv[4][4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int r = pw * RPW + rb + t;
+            const int64_t lr = lrow0 + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
+            if (lr < sg.nrows && k0 < D) {
+              const int64_t row = sg.row0 + lr;
+              if (c == 0)
+                make_row_quad(op, gen, row, lane, xv[t]);
+              else
+                load_quad(sg.X + row * ld, k0, D, xv[t]);
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            convert_store<BF16>(pw * RPW + rb + t, xv[t], k0, D, geo, ohv, olv, comp, lane, sS[a], At);
+        }
       } else
       for (int rb = 0; rb < RPW; rb += 4) {
         double xv[4][4];
@@ -693,6 +777,23 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
     if (xs[m] == s.X) xrows[m] = std::max<int64_t>(xrows[m], s.row0 + s.nrows);
     xmap_of[k] = m;
   }
+  // operators: rows made by the producers (DE trials, PSO moves)
+  GenOps ops;
+  std::memset(&ops, 0, sizeof(ops));
+  int op_of[SV_MAX_SEG];
+  const GenOp* op_src[MAX_OPS];
+  for (int k = 0; k < nseg; ++k) {
+    op_of[k] = -1;
+    if (!segs[k].op) continue;
+    int m = 0;
+    while (m < ops.n && op_src[m] != segs[k].op) ++m;
+    if (m == ops.n) {
+      if (ops.n == MAX_OPS) return cudaErrorInvalidValue;
+      op_src[m] = segs[k].op;
+      ops.op[ops.n++] = *segs[k].op;
+    }
+    op_of[k] = m;
+  }
   g.vec_ok = aligned;
   g.probe_wait = sv_policy_test_wait();
   g.dbox = (h0.D + 1) & ~1;
@@ -700,7 +801,8 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
   const size_t budget = 220 * 1024;
   const size_t fixed = (size_t)g.a_bytes + g.b_bytes + 1024;
   g.nxb = (int)std::min<size_t>(MAX_XB, (budget - fixed) / (size_t)g.xb_bytes);
-  bool staged = aligned && few && g.nxb >= 2;
+  // staged rows come from TMA loads of X, which an operator's rows do not have yet
+  bool staged = aligned && few && g.nxb >= 2 && ops.n == 0;
   const size_t smem = staged ? fixed + (size_t)g.nxb * g.xb_bytes
                              : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   {
@@ -727,6 +829,8 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
     d.ncomp = s.p->ncomp;
     d.sidx = k;
     d.xmap = xmap_of[k];
+    d.op = op_of[k];
+    d.pad = 0;
     d.stage0 = stage_rows;
     tiles += (int)((s.nrows + BM - 1) / BM);
     if (d.comp) stage_rows += s.nrows;
@@ -752,16 +856,16 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
   if (!staged) {
     const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
     if (bf16)
-      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ld, comp_g,
+      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld, comp_g,
                                                                       comp_s, lo);
     else
-      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ld, comp_g,
+      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld, comp_g,
                                                                        comp_s, lo);
   } else {
     if (bf16)
-      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ld, comp_g, comp_s, lo);
+      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g, comp_s, lo);
     else
-      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ld, comp_g, comp_s,
+      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g, comp_s,
                                                                lo);
   }
   sv_trace_end(tk, st);

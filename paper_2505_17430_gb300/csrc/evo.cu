@@ -26,19 +26,10 @@
 #include "bodies.cuh"
 #include "bounds.cuh"
 #include "evo.cuh"
+#include "ops.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
-
-// exact 53-bit uniform from two Philox words using integer operations only
-// (same value as sv_u53; the int->double conversion unit is slow here)
-__device__ __forceinline__ double u53_int(uint32_t w0, uint32_t w1) {
-  const unsigned long long m = ((unsigned long long)(w0 >> 5) << 26) | (unsigned long long)(w1 >> 6);
-  if (m == 0ull) return 0.0;
-  const int e = 63 - __clzll((long long)m);  // 0..52
-  const unsigned long long mant = (m << (52 - e)) & 0xFFFFFFFFFFFFFull;
-  return __longlong_as_double((long long)(((unsigned long long)(1023 - 53 + e) << 52) | mant));
-}
 
 // order-preserving integer key of a double (NaN sorts last)
 __device__ __forceinline__ long long fkey(double f) {
@@ -48,41 +39,6 @@ __device__ __forceinline__ long long fkey(double f) {
 }
 
 __device__ __forceinline__ double dmin_pos(double a, double b) { return (b < a) ? b : a; }
-
-// v * 0.5, exactly as IEEE multiplication rounds it, with integer
-// instructions: a normal result only loses one from the exponent; when the
-// result is subnormal the significand shifts right once with round to nearest
-// even; zeros, infinities and NaN are returned unchanged (all exact halves).
-__device__ __forceinline__ double half_exact(double v) {
-  const long long b = __double_as_longlong(v);
-  const long long sign = b & (long long)0x8000000000000000ull;
-  const long long mag = b & 0x7FFFFFFFFFFFFFFFll;
-  const int e = (int)(mag >> 52);
-  if (e > 1 && e < 0x7FF) return __longlong_as_double(b - (1ll << 52));
-  if (e == 0x7FF || mag == 0) return v;
-  // e == 1 or subnormal: the significand with its implicit bit, halved
-  const long long s = mag;  // for e == 1 the exponent bit is the implicit 1
-  long long h = s >> 1;
-  if ((s & 1) && (h & 1)) ++h;  // tie: round to even
-  return __longlong_as_double(sign | h);
-}
-
-// four consecutive coordinates j0..j0+3 of a row (16-byte loads when the
-// quad is whole: rows start 16-byte aligned and j0 is a multiple of 4)
-__device__ __forceinline__ void load_quad(const double* __restrict__ row, int j0, int D,
-                                          double (&v)[4]) {
-  if (j0 + 3 < D) {
-    const double2 a = *reinterpret_cast<const double2*>(row + j0);
-    const double2 b = *reinterpret_cast<const double2*>(row + j0 + 2);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (j0 + q < D) ? row[j0 + q] : 0.0;
-  }
-}
 
 // ---------------------------------------------------------------- control
 __global__ void ctl_set_kernel(GenCtl* ctl, unsigned long long gen, int count) {
@@ -167,121 +123,6 @@ __global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restri
     const int j = 2 * jp;
     xr[j] = __dadd_rn(lb, __dmul_rn(span, u53_int(w.x, w.y)));
     if (j + 1 < D) xr[j + 1] = __dadd_rn(lb, __dmul_rn(span, u53_int(w.z, w.w)));
-  }
-}
-
-// ---------------------------------------------------------------- DE trials
-// one quad (coordinates 4 jq .. 4 jq + 3) of run r's trial row i
-template <int ALG>
-__device__ __forceinline__ void de_trial_elem(const double* __restrict__ X, double* __restrict__ U,
-                                              const double* __restrict__ A,
-                                              const int32_t* __restrict__ asize,
-                                              const int32_t* __restrict__ order,
-                                              int32_t* __restrict__ part,
-                                              const uint64_t* __restrict__ seeds, int NP, int D,
-                                              int ld, double F, unsigned long long cr_thr,
-                                              double lb, double ub, int pk,
-                                              unsigned long long gen, int r, int i, int jq,
-                                              const double* __restrict__ Fi = nullptr,
-                                              const double* __restrict__ CRi = nullptr,
-                                              const int32_t* __restrict__ kpb = nullptr) {
-  // SHADE: this row's F, crossover threshold and pbest pool
-  if (ALG == SEVO_DE_SHADE) {
-    const int64_t row = (int64_t)r * NP + i;
-    F = Fi[row];
-    cr_thr = (unsigned long long)ceil(__dmul_rn(CRi[row], 4294967296.0));
-    pk = kpb[row];
-  }
-  const uint64_t seed = seeds[r];
-  const uint4 w = sv_draw(seed, 0u, (uint32_t)i, (uint32_t)gen, SV_P_PART);
-  const double* Xr = X + (int64_t)r * NP * ld;
-  const double* xi = Xr + (int64_t)i * ld;
-  const double *d1, *d2, *d3;
-  int p0, p1, p2, jr;
-  if (ALG == SEVO_DE_RAND1) {
-    int a = (int)sv_below(w.x, (uint32_t)(NP - 1));
-    if (a >= i) ++a;
-    const int lo = min(i, a), hi = max(i, a);
-    int b = (int)sv_below(w.y, (uint32_t)(NP - 2));
-    if (b >= lo) ++b;
-    if (b >= hi) ++b;
-    int e0 = lo, e1 = hi, e2 = b;  // sort {i, a, b}
-    if (e2 < e1) {
-      int tt = e1;
-      e1 = e2;
-      e2 = tt;
-    }
-    if (e1 < e0) {
-      int tt = e0;
-      e0 = e1;
-      e1 = tt;
-    }
-    int c = (int)sv_below(w.z, (uint32_t)(NP - 3));
-    if (c >= e0) ++c;
-    if (c >= e1) ++c;
-    if (c >= e2) ++c;
-    p0 = a;
-    p1 = b;
-    p2 = c;
-    d1 = Xr + (int64_t)a * ld;
-    d2 = Xr + (int64_t)b * ld;
-    d3 = Xr + (int64_t)c * ld;
-  } else {
-    const int as = (ALG == SEVO_DE_CTPB) ? asize[r] : 0;  // SHADE: no archive
-    const int pb = order[(int64_t)r * NP + (int)sv_below(w.x, (uint32_t)pk)];
-    int r1 = (int)sv_below(w.y, (uint32_t)(NP - 1));
-    if (r1 >= i) ++r1;
-    const int lo = min(i, r1), hi = max(i, r1);
-    int r2 = (int)sv_below(w.z, (uint32_t)(NP + as - 2));
-    if (r2 >= lo) ++r2;
-    if (r2 >= hi) ++r2;
-    p0 = pb;
-    p1 = r1;
-    p2 = r2;
-    d1 = Xr + (int64_t)pb * ld;
-    d2 = Xr + (int64_t)r1 * ld;
-    d3 = (r2 < NP) ? Xr + (int64_t)r2 * ld : A + ((int64_t)r * NP + (r2 - NP)) * ld;
-  }
-  jr = (int)sv_below(w.w, (uint32_t)D);
-  if (jq == 0 && part) {
-    int32_t* pp = part + ((int64_t)r * NP + i) * 4;
-    pp[0] = p0;
-    pp[1] = p1;
-    pp[2] = p2;
-    pp[3] = jr;
-  }
-  const uint4 cw = sv_draw(seed, (uint32_t)jq, (uint32_t)i, (uint32_t)gen, SV_P_CROSS);
-  const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
-  double* ui = U + ((int64_t)r * NP + i) * ld;
-  const int j0 = jq * 4;
-  double xv[4], v1[4], v2[4], v3[4];
-  load_quad(xi, j0, D, xv);
-  load_quad(d1, j0, D, v1);
-  load_quad(d2, j0, D, v2);
-  load_quad(d3, j0, D, v3);
-  const SvBound lbb = sv_bound(lb), ubb = sv_bound(ub);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int j = j0 + q;
-    if (j >= D) break;
-    const double x = xv[q];
-    double u = x;
-    if ((unsigned long long)cws[q] < cr_thr || j == jr) {
-      if (ALG == SEVO_DE_RAND1)
-        u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), v1[q]);
-      else
-        u = __fma_rn(F, __dsub_rn(v2[q], v3[q]), __fma_rn(F, __dsub_rn(v1[q], x), x));
-    }
-    // repair: if u < lb then u = (lb + x) / 2; then if u > ub, u = (ub + x) / 2.
-    // With the parent inside the bounds at most one of them applies, so one
-    // FP64 add with the bound chosen by a select; the second check only
-    // fires for parents outside the bounds (populations set by the caller)
-    const bool lo = sv_lt_bound(u, lbb), hi = sv_gt_bound(u, ubb);
-    if (lo || hi) {
-      u = half_exact(__dadd_rn(lo ? lb : ub, x));
-      if (lo && sv_gt_bound(u, ubb)) u = half_exact(__dadd_rn(ub, x));
-    }
-    ui[j] = u;
   }
 }
 
@@ -827,37 +668,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
     if (k < count) m = dmin_pos(m, v);
   }
   block_min_update(m, best + r);
-}
-
-// ---------------------------------------------------------------- PSO
-// coordinate j of run r's particle i (row ri = r * NP + i), element e:
-// the moved position (returned) and velocity (*vn)
-__device__ __forceinline__ double pso_moved(const double* __restrict__ X,
-                                            const double* __restrict__ V,
-                                            const double* __restrict__ P,
-                                            const int32_t* __restrict__ guide,
-                                            const uint64_t* __restrict__ seeds,
-                                            unsigned long long gen, int NP, int ld, double w,
-                                            double c1, double c2, double lb, double ub, int r,
-                                            int i, int j, int64_t ri, int64_t e, double* vn) {
-  const uint4 rw = sv_draw(seeds[r], (uint32_t)j, (uint32_t)i, (uint32_t)gen, SV_P_PSO);
-  const double r1 = u53_int(rw.x, rw.y), r2 = u53_int(rw.z, rw.w);
-  const double a = __dmul_rn(c1, r1), b = __dmul_rn(c2, r2);
-  const int gi = guide[ri];
-  const double x = X[e];
-  const double gj = P[((int64_t)r * NP + gi) * ld + j];
-  double v = __fma_rn(w, V[e], __fma_rn(a, __dsub_rn(P[e], x), __dmul_rn(b, __dsub_rn(gj, x))));
-  double xn = __dadd_rn(x, v);
-  if (sv_lt_bound(xn, sv_bound(lb))) {
-    xn = lb;
-    v = 0.0;
-  }
-  if (sv_gt_bound(xn, sv_bound(ub))) {
-    xn = ub;
-    v = 0.0;
-  }
-  *vn = v;
-  return xn;
 }
 
 // the same, in place: x <- moved x, v <- moved v
@@ -1411,6 +1221,9 @@ unsigned grid_for(int64_t work, int threads) {
 static std::atomic<int> g_policy_small_runs{0};
 static std::atomic<int> g_policy_refine{1};
 static std::atomic<long long> g_policy_test_wait{0};
+static std::atomic<int> g_policy_fuse_ops{1};
+
+int sv_policy_fuse_ops() { return g_policy_fuse_ops.load(); }
 
 int sv_policy_refine() { return g_policy_refine.load(); }
 long long sv_policy_test_wait() { return g_policy_test_wait.load(); }
@@ -1426,6 +1239,8 @@ extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
     g_policy_small_runs.store((int)value);
   } else if (key == SEVO_POLICY_REFINE) {
     g_policy_refine.store((int)value);
+  } else if (key == SEVO_POLICY_FUSE_OPS) {
+    g_policy_fuse_ops.store((int)value);
   } else {
     return SEVO_ERR_ARG;
   }
@@ -1436,6 +1251,7 @@ extern "C" int64_t sevo_get_policy(int32_t key) {
   if (key == SEVO_POLICY_SMALL_RUNS) return g_policy_small_runs.load();
   if (key == SEVO_POLICY_REFINE) return g_policy_refine.load();
   if (key == SEVO_POLICY_TEST_WAIT) return g_policy_test_wait.load();
+  if (key == SEVO_POLICY_FUSE_OPS) return g_policy_fuse_ops.load();
   return -1;
 }
 
@@ -1602,13 +1418,15 @@ void sv_batch_segments(const Batch* b, const EvalReq& q, std::vector<TcSegment>*
     t.out = q.f;
     t.err = b->err;
     t.refined = b->refined;
+    t.op = q.op;
     segs->push_back(t);
   }
 }
 
-static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1) {
+static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1,
+                             const GenOp* op = nullptr) {
   std::vector<TcSegment> segs;
-  sv_batch_segments(b, EvalReq{M, f, rpr < 0 ? b->NP : rpr}, &segs);
+  sv_batch_segments(b, EvalReq{M, f, rpr < 0 ? b->NP : rpr, op}, &segs);
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
   sc.err = b->err;
@@ -1708,15 +1526,61 @@ cudaError_t sv_batch_run_small(Batch* b, unsigned long long gen0, int64_t gens) 
   return e;
 }
 
+// Whether this batch's operator (DE trial or PSO move) is applied by the
+// producer warps of the fused tensor-core evaluation instead of a kernel of
+// its own: TF32 / BF16X3 at D <= 128, batched kernels, the policy on.
+static bool fusable(const Batch* b) {
+  return !b->small && sv_policy_fuse_ops() && b->D <= 128 &&
+         (b->prec == SEVO_TF32 || b->prec == SEVO_BF16X3) &&
+         (sv_is_de(b->alg) || b->alg == SEVO_PSO_GBEST || b->alg == SEVO_PSO_RING);
+}
+
+// the operator descriptor of this generation (the counter as the next
+// kernel would take it)
+static void fill_op(Batch* b) {
+  GenOp& o = b->gop;
+  std::memset(&o, 0, sizeof(o));
+  o.alg = b->alg;
+  o.NP = b->NP;
+  o.D = b->D;
+  o.ld = b->ld;
+  o.pk = b->pbest_k;
+  o.F = b->F;
+  o.lb = b->lb;
+  o.ub = b->ub;
+  o.w = b->w;
+  o.c1 = b->c1;
+  o.c2 = b->c2;
+  o.cr_thr = b->cr_thr;
+  o.seeds = b->seeds;
+  o.ctl = b->ctl;
+  o.cs = take_ctl(b);
+  if (sv_is_de(b->alg)) {
+    o.X = b->X;
+    o.U = b->U;
+    o.A = (b->alg == SEVO_DE_CTPB) ? b->A : nullptr;
+    o.asize = (b->alg == SEVO_DE_CTPB) ? b->asize : nullptr;
+    o.order = b->order;
+    o.part = b->part;
+    o.Fi = b->Fi;
+    o.CRi = b->CRi;
+    o.kpb = b->kpb;
+  } else {
+    o.U = b->X;  // moved in place
+    o.V = b->V;
+    o.P = b->P;
+    o.guide = b->guide;
+  }
+}
+
 // The DE trials of a generation: (SHADE parameters,) p-best ranking, trials
-// U from X.
-static cudaError_t de_trials(Batch* b) {
+// U from X (fused: everything but the trials themselves).
+static cudaError_t de_trials(Batch* b, bool fused = false) {
   cudaStream_t st = b->stream;
   const int64_t rows = (int64_t)b->R * b->NP;
   const int nq = (b->D + 3) >> 2;
   const int T = 256;
   const bool shade = sv_has_shade(b->alg);
-  cudaError_t e;
   if (shade) {
     const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     shade_param_kernel<<<grid_for(rows, T), T, 0, st>>>(b->MF, b->MCR, b->seeds, b->ctl,
@@ -1737,6 +1601,12 @@ static cudaError_t de_trials(Batch* b) {
           b->fx, b->order, b->NP, pow2_at_least(b->NP), b->pbest_k);
     }
     sv_trace_end(tk_rank, st);
+  }
+  if (fused) {  // the evaluation's producers make the trials
+    fill_op(b);
+    return cudaGetLastError();
+  }
+  if (b->alg == SEVO_DE_CTPB || shade) {
     const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     if (shade)
       de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
@@ -1786,9 +1656,10 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
   cudaStream_t st = b->stream;
   const int64_t rows = (int64_t)b->R * b->NP;
   const int T = 256;
+  const bool fused = fusable(b);
   if (sv_is_de(b->alg)) {
-    *q = EvalReq{b->U, b->fu, b->NP};
-    return de_trials(b);
+    *q = EvalReq{b->U, b->fu, b->NP, fused ? &b->gop : nullptr};
+    return de_trials(b, fused);
   }
   if (b->alg == SEVO_CSO) {
     const int half = b->NP / 2;
@@ -1805,7 +1676,12 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
         b->lb, b->ub, make_fastdiv(b->D), make_fastdiv(half));
     sv_trace_end(tkm, st);
     sv_note_launch();
-    *q = EvalReq{b->U, b->fu, half};
+    *q = EvalReq{b->U, b->fu, half, nullptr};
+    return cudaGetLastError();
+  }
+  if (fused) {  // the evaluation's producers move the particles
+    fill_op(b);
+    *q = EvalReq{b->X, b->fx, b->NP, &b->gop};
     return cudaGetLastError();
   }
   const int tk12 = sv_trace_begin(SEVO_TK_PSO_MOVE, st);
@@ -1814,7 +1690,7 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
                                                          b->c1, b->c2, b->lb, b->ub,
                                                          make_fastdiv(b->D), make_fastdiv(b->NP));
   sv_trace_end(tk12, st);
-  *q = EvalReq{b->X, b->fx, b->NP};
+  *q = EvalReq{b->X, b->fx, b->NP, nullptr};
   return cudaGetLastError();
 }
 
@@ -1904,7 +1780,7 @@ cudaError_t sv_batch_generation(Batch* b) {
   EvalReq q;
   cudaError_t e;
   if ((e = sv_batch_pre_eval(b, &q)) != cudaSuccess) return e;
-  if ((e = eval_rows(b, q.M, q.f, q.rpr)) != cudaSuccess) return e;
+  if ((e = eval_rows(b, q.M, q.f, q.rpr, q.op)) != cudaSuccess) return e;
   return sv_batch_post_eval(b);
 }
 

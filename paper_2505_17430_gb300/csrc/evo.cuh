@@ -5,23 +5,6 @@
 
 #include "kernels.cuh"
 
-// Per-generation control block, device-resident so that generations captured
-// in a CUDA graph read their Philox counter and evaluation count at run time.
-struct GenCtl {
-  unsigned long long gen;  // Philox counter of the current generation
-  int count;               // rows of this generation that count toward the budget
-  int pad;
-};
-
-// A generation's counter and count handed to its first kernel as a launch
-// argument (on = 1), which publishes them to the control block: no separate
-// launch to set the block.  on = 0: the kernel reads the block.
-struct CtlSet {
-  unsigned long long gen;
-  int count;
-  int on;
-};
-
 struct Batch {
   int alg, D, NP, R, ld;  // R runs of NP rows each, row stride ld (even)
   int per_gen;            // evaluations counted per generation (CSO: NP / 2)
@@ -54,6 +37,7 @@ struct Batch {
   bool any_comp;
   cudaStream_t stream;
   CtlSet pending{0ull, 0, 0};   // set by sv_ctl_defer, taken by the next generation's first kernel
+  GenOp gop;                    // this generation's operator, when the evaluation applies it
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
@@ -73,6 +57,7 @@ struct EvalReq {
   const double* M;
   double* f;
   int rpr;
+  const GenOp* op;  // the operator the evaluation applies first (fused path), or null
 };
 bool sv_batch_splittable(const Batch* b);
 cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q);

@@ -14,6 +14,50 @@ struct EvalAux {
 
 #define SV_MAX_SEG 64
 
+// Per-generation control block, device-resident so that generations captured
+// in a CUDA graph read their Philox counter and evaluation count at run time.
+struct GenCtl {
+  unsigned long long gen;  // Philox counter of the current generation
+  int count;               // rows of this generation that count toward the budget
+  int pad;
+};
+
+// A generation's counter and count handed to its first kernel as a launch
+// argument (on = 1), which publishes them to the control block: no separate
+// launch to set the block.  on = 0: the kernel reads the block.
+struct CtlSet {
+  unsigned long long gen;
+  int count;
+  int on;
+};
+
+// An operator the fused tensor-core evaluation applies in its producer warps
+// in place of loading the rows it evaluates: DE trials (rand/1,
+// current-to-pbest with archive, SHADE) written to U, or the PSO move
+// written in place to X and V; the generation's counter from cs (published
+// to ctl by the launch) or, when cs.on == 0, from ctl.
+struct GenOp {
+  int alg;  // SEVO_DE_RAND1, SEVO_DE_CTPB, SEVO_DE_SHADE, SEVO_PSO_GBEST or SEVO_PSO_RING
+  int NP, D, ld, pk;
+  double F, lb, ub, w, c1, c2;
+  unsigned long long cr_thr;
+  const double* X;  // DE: the population
+  double* U;        // DE: the trials;  PSO: the population (moved in place)
+  const double* A;
+  const int32_t* asize;
+  const int32_t* order;
+  int32_t* part;
+  const uint64_t* seeds;
+  const double* Fi;
+  const double* CRi;
+  const int32_t* kpb;
+  double* V;
+  const double* P;
+  const int32_t* guide;
+  GenCtl* ctl;
+  CtlSet cs;
+};
+
 // a run of rows [row0, row0 + nrows) of X evaluated on one problem; X, out,
 // err and refined may name the segment's own population, results, device
 // error word and refined-row counter (null: the evaluation call's)
@@ -25,6 +69,7 @@ struct TcSegment {
   double* out = nullptr;
   uint32_t* err = nullptr;
   unsigned long long* refined = nullptr;
+  const GenOp* op = nullptr;  // rows made by this operator (fused tensor-core path only)
 };
 
 // per-segment refinement sub-lists: segment s lists its rows (row indices of
@@ -90,6 +135,8 @@ size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
 int sv_policy_refine();
 // SEVO_POLICY_TEST_WAIT's current value (0: off, the default)
 long long sv_policy_test_wait();
+// SEVO_POLICY_FUSE_OPS's current value (1: on, the default)
+int sv_policy_fuse_ops();
 void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
                            EvalScratch* s);
 // evaluate segments (same D) into out with refinement; resets counters first

@@ -805,3 +805,33 @@ def test_grid_buckets_concurrent_on_caller_stream(S):
         gen += 1
         st.step(gen)
     assert st.result()["best"] == res["best"][t]
+
+
+@pytest.mark.parametrize("prec,D", [("TF32", 30), ("BF16X3", 17), ("TF32", 100), ("BF16X3", 128)])
+def test_fused_operators_equal_operator_kernels(S, prec, D):
+    """SEVO_POLICY_FUSE_OPS: the fused evaluation's producers form the DE
+    trials and PSO moves themselves; every state (DE/rand/1,
+    current-to-pbest with archive, SHADE, global and ring PSO; single,
+    hybrid, composition and composition-of-hybrid problems, whose later
+    components read the rows back) stays bit-identical to the run whose
+    operators are kernels of their own, over 5 generations."""
+    import torch
+    lib = S.lib()
+    algs = [S.DE_RAND1, S.DE_CTPB, S.DE_SHADE, S.PSO_GBEST, S.PSO_RING]
+    NP = 150
+    runs = {}
+    for fuse in (1, 0):
+        assert lib.sevo_set_policy(S.POLICY_FUSE_OPS, fuse) == 0
+        try:
+            _, sts = _group(S, D, NP, getattr(S, prec), algs, torch, fams=(1, 3, 6, 7, 8))
+            for g in range(1, 6):
+                for st in sts:
+                    assert st.step(g) == 0
+            runs[fuse] = [(st.get(), st.result(), st.best()) for st in sts]
+        finally:
+            lib.sevo_set_policy(S.POLICY_FUSE_OPS, 1)
+    for (ga, ra, ba), (gb, rb, bb) in zip(runs[1], runs[0]):
+        for key in ("X", "fx", "U", "fu", "A", "V", "P", "fp", "part"):
+            assert np.array_equal(ga[key], gb[key]), key
+        assert ga["asize"] == gb["asize"]
+        assert ra == rb and np.array_equal(ba, bb)
