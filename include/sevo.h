@@ -425,13 +425,15 @@ enum sevo_policy {
    * and the call reports SEVO_ERR_TIMEOUT like a real timeout.  0 (default):
    * off. */
   SEVO_POLICY_TEST_WAIT = 2,
-  /* 1 (default): in SEVO_TF32 / SEVO_BF16X3 at D <= 128 the DE trials
-   * (rand/1, current-to-pbest, SHADE) and the PSO move (global and ring)
-   * are formed by the producer warps of the fused tensor-core evaluation,
-   * which write them and feed them to the MMA in one pass; 0: each operator
-   * runs as a kernel of its own before the evaluation.  The results are the
-   * same bits either way (the same operator code); read when a generation
-   * is launched. */
+  /* 1: in SEVO_TF32 / SEVO_BF16X3 at D <= 128 the DE trials (rand/1,
+   * current-to-pbest, SHADE) and the PSO move (global and ring) are formed
+   * by the producer warps of the fused tensor-core evaluation, which write
+   * them and feed them to the MMA in one pass; 0 (default): each operator
+   * runs as a kernel of its own before the evaluation (faster on GB300,
+   * whose operator kernels hide their random row loads with far more warps
+   * than the fused kernel's producers have).  The results are the same bits
+   * either way (the same operator code); read when a generation is
+   * launched. */
   SEVO_POLICY_FUSE_OPS = 3
 };
 #define SEVO_TEST_WAIT_MAX 100000000

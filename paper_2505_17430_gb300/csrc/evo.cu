@@ -1221,7 +1221,7 @@ unsigned grid_for(int64_t work, int threads) {
 static std::atomic<int> g_policy_small_runs{0};
 static std::atomic<int> g_policy_refine{1};
 static std::atomic<long long> g_policy_test_wait{0};
-static std::atomic<int> g_policy_fuse_ops{1};
+static std::atomic<int> g_policy_fuse_ops{0};
 
 int sv_policy_fuse_ops() { return g_policy_fuse_ops.load(); }
 

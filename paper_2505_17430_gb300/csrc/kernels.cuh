@@ -135,7 +135,7 @@ size_t sv_eval_scratch_bytes(int D, bool any_comp, int prec, int64_t rows);
 int sv_policy_refine();
 // SEVO_POLICY_TEST_WAIT's current value (0: off, the default)
 long long sv_policy_test_wait();
-// SEVO_POLICY_FUSE_OPS's current value (1: on, the default)
+// SEVO_POLICY_FUSE_OPS's current value (0: off, the default)
 int sv_policy_fuse_ops();
 void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
                            EvalScratch* s);

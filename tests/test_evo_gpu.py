@@ -316,6 +316,14 @@ def test_kernel_trace_counts_and_times(S):
     t = S.trace_read()
     for k in ("de_rank", "de_trial", "eval_tc_fused", "de_select", "de_apply"):
         assert t[k][0] == 1 and t[k][1] > 0.0, (k, t[k])
+    # fused operators: the trials are formed inside the evaluation
+    old_fuse = lib.sevo_get_policy(S.POLICY_FUSE_OPS)
+    lib.sevo_set_policy(S.POLICY_FUSE_OPS, 1)
+    S.trace_enable(True)
+    assert st.de_step(2) == 0
+    t = S.trace_read()
+    lib.sevo_set_policy(S.POLICY_FUSE_OPS, old_fuse)
+    assert t["de_trial"][0] == 0 and t["eval_tc_fused"][0] == 1 and t["de_rank"][0] == 1
     S.trace_enable(True)
     lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 0)
     S.sevo_run_grid([p], [S.alg_params(S.PSO_RING, 20, 20 * 40)], [(0, 0, 3)], gens_per_graph=8)
@@ -820,6 +828,7 @@ def test_fused_operators_equal_operator_kernels(S, prec, D):
     algs = [S.DE_RAND1, S.DE_CTPB, S.DE_SHADE, S.PSO_GBEST, S.PSO_RING]
     NP = 150
     runs = {}
+    old = lib.sevo_get_policy(S.POLICY_FUSE_OPS)
     for fuse in (1, 0):
         assert lib.sevo_set_policy(S.POLICY_FUSE_OPS, fuse) == 0
         try:
@@ -829,7 +838,7 @@ def test_fused_operators_equal_operator_kernels(S, prec, D):
                     assert st.step(g) == 0
             runs[fuse] = [(st.get(), st.result(), st.best()) for st in sts]
         finally:
-            lib.sevo_set_policy(S.POLICY_FUSE_OPS, 1)
+            lib.sevo_set_policy(S.POLICY_FUSE_OPS, old)
     for (ga, ra, ba), (gb, rb, bb) in zip(runs[1], runs[0]):
         for key in ("X", "fx", "U", "fu", "A", "V", "P", "fp", "part"):
             assert np.array_equal(ga[key], gb[key]), key
