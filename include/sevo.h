@@ -434,7 +434,18 @@ enum sevo_policy {
    * than the fused kernel's producers have).  The results are the same bits
    * either way (the same operator code); read when a generation is
    * launched. */
-  SEVO_POLICY_FUSE_OPS = 3
+  SEVO_POLICY_FUSE_OPS = 3,
+  /* 1 (default): launch choices that only change speed (today the N-tile
+   * width, 64, 128 or 256 columns, of the large-D rotation GEMM) are
+   * measured with CUDA events the first time a (D, row count rounded up to
+   * a power of two, precision) is evaluated outside stream capture, and
+   * cached in memory and in a file ($SEVO_TUNE_FILE, else
+   * $XDG_CACHE_HOME/sevo/tune-<gpu>.txt, else $HOME/.cache/sevo/
+   * tune-<gpu>.txt); that first call synchronizes its stream.  Every width
+   * gives the same result bits.  0: a fixed rule (whole waves of jobs times
+   * their cost) instead.  2: forget the cached choices and read the file
+   * again (the value then reads back as 1). */
+  SEVO_POLICY_AUTOTUNE = 4
 };
 #define SEVO_TEST_WAIT_MAX 100000000
 /* SEVO_ERR_ARG for an unknown key or value */

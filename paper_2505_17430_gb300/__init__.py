@@ -113,6 +113,7 @@ POLICY_SMALL_RUNS = 0
 POLICY_REFINE = 1
 POLICY_TEST_WAIT = 2
 POLICY_FUSE_OPS = 3
+POLICY_AUTOTUNE = 4
 
 _LIB = None
 

@@ -28,14 +28,18 @@ namespace {
 constexpr int BM = 128;
 constexpr int WPQ = 4;               // epilogue warps per TMEM lane quarter
 constexpr int NEPI = 4 * WPQ;
-constexpr int SUB_MIN = 128 / WPQ;   // narrowest record slice (N tile 128): sizes the scratch
-constexpr int MAX_NBUF = 4;
-// N tile of one job (128 or 256 columns of z): NBUF TMEM accumulators of BN
-// columns fill the 512-column TMEM; an epilogue warp walks SUB columns; the
-// B operand of a stage is NB boxes of 128 rotation rows
+constexpr int SUB = 32;              // columns of z per record slice, for every N tile
+constexpr int MAX_NBUF = 8;
+constexpr int MAX_STAGES = 6;
+// N tile of one job (64, 128 or 256 columns of z): NBUF TMEM accumulators of
+// BN columns fill the 512-column TMEM; a job has NSL record slices of SUB
+// columns, walked by the epilogue warps of each lane quarter in turn; the B
+// operand of a stage is NB boxes of 128 rotation rows (a 64-column tile uses
+// the first 64 rows of its box).  The slices, hence the per-row sums and
+// every result bit, are the same for every BN.
 template <int BN>
 struct Tile {
-  static constexpr int NBUF = 512 / BN, SUB = BN / WPQ, NB = BN / 128;
+  static constexpr int NBUF = 512 / BN, NSL = BN / SUB, NB = BN >= 128 ? BN / 128 : 1;
 };
 constexpr int WARP_TMA = NEPI, WARP_MMA = NEPI + 1;
 constexpr int NTHREADS = (NEPI + 2) * 32;
@@ -50,7 +54,7 @@ struct BigGeom {
 };
 
 struct __align__(8) BigBars {
-  uint64_t full[4], empty[4], t_full[MAX_NBUF], t_empty[MAX_NBUF];
+  uint64_t full[MAX_STAGES], empty[MAX_STAGES], t_full[MAX_NBUF], t_empty[MAX_NBUF];
   uint32_t tmem_base;
   int abort;
 };
@@ -61,25 +65,28 @@ __device__ __forceinline__ void big_abort(BigBars* b, uint32_t* dev_err) {
 }
 
 // ---------------------------------------------------------------- convert
-// One warp per row (grid-stride), lane = 4 consecutive columns per step:
-// 16-byte FP64 loads when rows are 16-byte aligned, 16-byte (TF32) or 8-byte
-// (BF16 hi and lo) stores; s_c = |x - o_c|^2 in FP32 by a warp reduction.
-constexpr int CVT_WARPS = 8;
+// One block per row (grid-stride over rows), thread t = quads t, t + 256, ...
+// of 4 consecutive columns: 16-byte FP64 loads when rows are 16-byte
+// aligned, 16-byte (TF32) or 8-byte (BF16 hi and lo) stores, every quad of
+// the row in flight at once; s_c = |x - o_c|^2 in FP32 by a block reduction
+// in a fixed order (warp shuffles, then the warps' partial sums in index
+// order), so the result does not depend on scheduling.
+constexpr int CVT_THREADS = 256;
 
 template <bool BF16>
-__global__ void __launch_bounds__(CVT_WARPS * 32)
+__global__ void __launch_bounds__(CVT_THREADS)
     convert_kernel(const ProblemDev* __restrict__ P, int c, const double* __restrict__ X,
                    int64_t ld, int64_t row0, int64_t N, int D, int kpad, bool vec,
                    float* __restrict__ A32, __nv_bfloat16* __restrict__ Ahi,
                    __nv_bfloat16* __restrict__ Alo, double* __restrict__ s_out) {
+  __shared__ float wsum[CVT_THREADS / 32];
   const float* __restrict__ oh = P->oh32[c];
   const float* __restrict__ ol = P->ol32[c];
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * CVT_WARPS;
-  for (int64_t r = (int64_t)blockIdx.x * CVT_WARPS + (threadIdx.x >> 5); r < N; r += nw) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
     const double* xr = X + (row0 + r) * ld;
     float sq = 0.f;
-    for (int k0 = lane * 4; k0 < kpad; k0 += 128) {
+    for (int k0 = tid * 4; k0 < kpad; k0 += CVT_THREADS * 4) {
       double xv[4] = {0.0, 0.0, 0.0, 0.0};
       if (vec && k0 + 3 < D) {
         const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
@@ -127,7 +134,14 @@ __global__ void __launch_bounds__(CVT_WARPS * 32)
     if (s_out) {
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, m);
-      if (lane == 0) s_out[(row0 + r) * SV_MAXC + c] = (double)sq;
+      if (lane == 0) wsum[warp] = sq;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < CVT_THREADS / 32; ++w) t += wsum[w];
+        s_out[(row0 + r) * SV_MAXC + c] = (double)t;
+      }
+      __syncthreads();
     }
   }
 }
@@ -143,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = geo.stages;
-  constexpr int NBUF = Tile<BN>::NBUF, SUB = Tile<BN>::SUB, NB = Tile<BN>::NB;
+  constexpr int NBUF = Tile<BN>::NBUF, NSL = Tile<BN>::NSL, NB = Tile<BN>::NB;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&bars.full[s], 1);
@@ -252,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else {
     // epilogue: warp w reads TMEM lane quarter w % 4 (thread = row of the
-    // tile) and columns [SUB * (w / 4), SUB * (w / 4 + 1)) of the chunk
+    // tile) and the job's slices w / 4, w / 4 + 4, ... (SUB columns each)
     const int r = (warp & 3) * 32 + lane;
     const int sl = warp >> 2;
     const int64_t N = geo.N;
@@ -266,26 +280,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       tc::tc_fence_after();
-      const int sb = nb * WPQ + sl;  // slice index within the row
-      const int c0 = sb * SUB, c1 = min(geo.D, c0 + SUB);
       const int64_t row = (int64_t)tile * BM + r;
-      float* rec = part + (int64_t)sb * REC * N + row;  // slot k at rec[k * N]
       const bool live = row < N;
-      float zf = 0.f, zl = 0.f;
-      const uint32_t taddr =
-          tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(a * BN + sl * SUB);
-      if (c0 < c1) {
-        walk_cols<!BF16>(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
-          if (live) {
-            rec[(3 * g) * N] = acc.a0;
-            rec[(3 * g + 1) * N] = acc.a1;
-            rec[(3 * g + 2) * N] = acc.a2;
-          }
-        });
-      }
-      if (live) {
-        rec[(3 * SV_MAXG) * N] = zf;
-        rec[(3 * SV_MAXG + 1) * N] = zl;
+      for (int ls = sl; ls < NSL; ls += WPQ) {
+        const int sb = nb * NSL + ls;  // slice index within the row
+        const int c0 = sb * SUB, c1 = min(geo.D, c0 + SUB);
+        float* rec = part + (int64_t)sb * REC * N + row;  // slot k at rec[k * N]
+        float zf = 0.f, zl = 0.f;
+        const uint32_t taddr =
+            tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(a * BN + ls * SUB);
+        if (c0 < c1) {
+          walk_cols<!BF16>(taddr, c0, c1, c, comp, *P, zf, zl, [&](int g, const Acc32& acc) {
+            if (live) {
+              rec[(3 * g) * N] = acc.a0;
+              rec[(3 * g + 1) * N] = acc.a1;
+              rec[(3 * g + 2) * N] = acc.a2;
+            }
+          });
+        }
+        if (live) {
+          rec[(3 * SV_MAXG) * N] = zf;
+          rec[(3 * SV_MAXG + 1) * N] = zl;
+        }
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -316,25 +332,32 @@ __device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, i
   return P.gid[c][i];
 }
 
-// one warp per row: lane l merges slices l, l + 32, ... into per-group
-// accumulators (adding the Rosenbrock pair across a slice border from the
-// previous slice's last z), then the groups are summed across the warp
-constexpr int CMB_WARPS = 4;
+// A block per 32 rows (lane = row, so every record load is a coalesced 128
+// bytes): warp w merges slices w, w + 8, ... of its rows into per-group
+// accumulators, adding the Rosenbrock pair across a slice border from the
+// previous slice's last z; the eight warps' partial sums are then added in
+// warp order (a fixed order: the result does not depend on scheduling), the
+// groups finished and the row's FP64 error written.
+constexpr int CMB_WARPS = 8;
+constexpr int CMB_ROWS = 32;
 
 __global__ void __launch_bounds__(CMB_WARPS * 32)
-    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub, int SUB,
+    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub, int sub,
                    const float* __restrict__ part, int64_t row0, int64_t N,
                    double* __restrict__ out, double* __restrict__ comp_g, ListOutB lo) {
+  __shared__ float red[CMB_WARPS][3 * SV_MAXG][CMB_ROWS];
   const ProblemDev& P = *Pp;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ng = P.ngc[c];
-  const int64_t nw = (int64_t)gridDim.x * CMB_WARPS;
-  for (int64_t lr = (int64_t)blockIdx.x * CMB_WARPS + (threadIdx.x >> 5); lr < N; lr += nw) {
+  const int64_t nblk = (N + CMB_ROWS - 1) / CMB_ROWS;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t lr = blk * CMB_ROWS + lane;
+    const bool live = lr < N;
     Acc32 acc[SV_MAXG];
 #pragma unroll
     for (int g = 0; g < SV_MAXG; ++g) acc32_init(acc[g]);
-    for (int sb = lane; sb < nsub; sb += 32) {
-      const int c0 = sb * SUB, c1 = min(D, c0 + SUB);
+    for (int sb = warp; sb < nsub && live; sb += CMB_WARPS) {
+      const int c0 = sb * sub, c1 = min(D, c0 + sub);
       if (c0 >= c1) break;
       const float* rec = part + (int64_t)sb * REC * N + lr;  // slot k at rec[k * N]
       const int g0 = group_of(P, c, comp, c0), g1 = group_of(P, c, comp, c1 - 1);
@@ -357,41 +380,46 @@ __global__ void __launch_bounds__(CMB_WARPS * 32)
         }
       }
     }
-    double gsum = 0.0;
 #pragma unroll
     for (int g = 0; g < SV_MAXG; ++g) {
-      if (g < ng) {
-        float a0 = acc[g].a0, a1 = acc[g].a1, a2 = acc[g].a2;
+      red[warp][3 * g][lane] = acc[g].a0;
+      red[warp][3 * g + 1][lane] = acc[g].a1;
+      red[warp][3 * g + 2][lane] = acc[g].a2;
+    }
+    __syncthreads();
+    if (warp == 0 && live) {
+      double gsum = 0.0;
 #pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-          a0 += __shfl_xor_sync(0xffffffffu, a0, m);
-          a1 += __shfl_xor_sync(0xffffffffu, a1, m);
-          a2 += __shfl_xor_sync(0xffffffffu, a2, m);
+      for (int g = 0; g < SV_MAXG; ++g) {
+        if (g < ng) {
+          Acc32 t;
+          t.a0 = t.a1 = t.a2 = 0.f;
+          for (int w = 0; w < CMB_WARPS; ++w) {
+            t.a0 += red[w][3 * g][lane];
+            t.a1 += red[w][3 * g + 1][lane];
+            t.a2 += red[w][3 * g + 2][lane];
+          }
+          const int body = P.gbody[c][g];
+          const int n = P.gstart[c][g + 1] - P.gstart[c][g];
+          gsum += (double)finalize32(body, t, n);
         }
-        Acc32 t;
-        t.a0 = a0;
-        t.a1 = a1;
-        t.a2 = a2;
-        const int body = P.gbody[c][g];
-        const int n = P.gstart[c][g + 1] - P.gstart[c][g];
-        gsum += (double)finalize32(body, t, n);
+      }
+      const int64_t row = row0 + lr;
+      if (comp) {
+        comp_g[row * SV_MAXC + c] = gsum;
+      } else {
+        double err = gsum;
+        if (!isfinite(err)) {
+          err = __longlong_as_double(0x7ff8000000000000ll);
+          if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
+        } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
+          int k = atomicAdd(lo.count, 1);
+          lo.list[lo.list_off + k] = (int32_t)row;
+        }
+        out[row] = err;
       }
     }
-    if (lane != 0) continue;
-    const int64_t row = row0 + lr;
-    if (comp) {
-      comp_g[row * SV_MAXC + c] = gsum;
-      continue;
-    }
-    double err = gsum;
-    if (!isfinite(err)) {
-      err = __longlong_as_double(0x7ff8000000000000ll);
-      if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
-    } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
-      int k = atomicAdd(lo.count, 1);
-      lo.list[lo.list_off + k] = (int32_t)row;
-    }
-    out[row] = err;
+    __syncthreads();
   }
 }
 
@@ -450,7 +478,7 @@ size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
   (void)prec;
   const int kpad = (D + 63) / 64 * 64;
-  const int nsub = ((D + 127) / 128 * 128) / SUB_MIN;
+  const int nsub = ((D + 127) / 128 * 128) / SUB;
   size_t b = al256b((size_t)rows * kpad * 4) + al256b((size_t)rows * nsub * REC * 4);
   if (any_comp) b += al256b((size_t)rows * SV_MAXC * 16);
   return b;
@@ -460,8 +488,10 @@ size_t sv_eval_big_scratch_bytes(int D, bool any_comp, int prec, int64_t rows) {
 static cudaError_t set_big_smem() {
   const int lim = 200 * 1024;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(gemm_big_kernel<true, 128>, a, lim);
+  cudaError_t e = cudaFuncSetAttribute(gemm_big_kernel<true, 64>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<true, 128>, a, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<true, 256>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 64>, a, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 128>, a, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_big_kernel<false, 256>, a, lim);
   return e;
@@ -480,33 +510,45 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   if (h.npad % 128 != 0 || p->tmap_rows != 128) return cudaErrorNotSupported;
   if (!scratch || scratch_bytes < sv_eval_big_scratch_bytes(h.D, comp, prec, N))
     return cudaErrorInvalidValue;
-  BigGeom g;
-  g.D = h.D;
-  g.kpad = h.kpad;
-  g.nkb = h.kpad / (bf16 ? 64 : 32);
-  // N tile: the width whose whole waves of persistent jobs finish first,
-  // ceil(jobs / SMs) x the cost of one job.  A 256-column job reads 3/4 of
-  // the operand bytes per flop of a 128-column one and measured 1.7x the
-  // flop rate in TF32 (4 stages either way) but only 1.2x in BF16X3 (its 96 KB
-  // stages leave room for two).  Measured whole calls (128 vs 256 columns):
-  // TF32 D = 5000 x 1,024 rows 256 vs 196 us, D = 300 x 10,200 rows 48 vs
-  // 52 us; BF16X3 D = 2000 x 4,096 rows 141 vs 122 us, D = 5000 x 1,024 rows
-  // 153 vs 172 us.
+  // N tile of a job: 64, 128 or 256 columns of z, all giving the same bits.
+  // Measured (SEVO_POLICY_AUTOTUNE) the first time a (D, row bucket,
+  // precision) is seen outside stream capture, else a rule: the width whose
+  // whole waves of persistent jobs, ceil(jobs / SMs) x the cost of one job,
+  // finish first (a 256-column job measured 1.7x the flop rate of a
+  // 128-column one in TF32, 1.2x in BF16X3; a 64-column job half the flops
+  // for about 0.6 of the time).
   const int64_t tiles = (N + BM - 1) / BM;
   const int64_t sms = sv_num_sms();
-  const int64_t jobs256 = tiles * ((h.npad + 255) / 256);
-  const int64_t jobs128 = tiles * ((h.npad + 127) / 128);
-  const double t256 = (double)((jobs256 + sms - 1) / sms) * (2.0 / (bf16 ? 1.2 : 1.7));
-  const double t128 = (double)((jobs128 + sms - 1) / sms);
-  const int BN = (t256 < t128) ? 256 : 128;
-  const int NB = BN / 128;
-  g.nchunks = (h.npad + BN - 1) / BN;
-  g.nsub = g.nchunks * WPQ;
-  g.ntiles = (int)((N + BM - 1) / BM);
-  g.N = N;
-  g.stage_bytes = (bf16 ? 2 : 1) * (1 + NB) * KB_BYTES;
-  g.stages = bf16 ? (BN == 256 ? 2 : 3) : 4;  // at most 192 KB of stages
-  g.idesc = tc::idesc_make(bf16 ? 1 : 2, BM, BN);
+  auto waves = [&](int bn) { return (double)((tiles * ((h.npad + bn - 1) / bn) + sms - 1) / sms); };
+  const double t256 = waves(256) * (2.0 / (bf16 ? 1.2 : 1.7));
+  const double t128 = waves(128), t64 = waves(64) * 0.6;
+  int BN = (t256 < t128) ? 256 : 128;
+  if (t64 < std::min(t128, t256)) BN = 64;
+  bool tune = false;
+  if (sv_policy_autotune()) {
+    const int cached = sv_tune_lookup(SV_TUNE_BIG_NTILE, h.D, N, prec);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cached)
+      BN = cached;
+    else if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+      tune = true;
+  }
+  auto geom = [&](int bn) {
+    BigGeom g;
+    g.D = h.D;
+    g.kpad = h.kpad;
+    g.nkb = h.kpad / (bf16 ? 64 : 32);
+    g.nchunks = (h.npad + bn - 1) / bn;
+    g.nsub = h.npad / SUB;
+    g.ntiles = (int)tiles;
+    g.N = N;
+    const int nb = bn >= 128 ? bn / 128 : 1;
+    g.stage_bytes = (bf16 ? 2 : 1) * (1 + nb) * KB_BYTES;
+    g.stages = std::min(MAX_STAGES, (192 * 1024) / g.stage_bytes);
+    g.idesc = tc::idesc_make(bf16 ? 1 : 2, BM, bn);
+    return g;
+  };
+  BigGeom g = geom(BN);
   // scratch: A (N x kpad fp32, or hi then lo bf16), chunk records, composition
   char* cp = (char*)scratch;
   void* Abase = cp;
@@ -533,50 +575,94 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     if (!make_a_map(&mA, A32, false, h.kpad, N)) return cudaErrorInvalidValue;
     mAlo = mA;
   }
-  const size_t smem = (size_t)g.stages * g.stage_bytes + 1024;
   {
     const cudaError_t e = sv_once_per_device(SV_ONCE_BIG_SMEM, set_big_smem);
     if (e != cudaSuccess) return e;
   }
-  const int cvt_grid =
-      (int)std::min<int64_t>((N + CVT_WARPS - 1) / CVT_WARPS, (int64_t)sv_num_sms() * 8);
+  const int cvt_grid = (int)std::min<int64_t>(N, (int64_t)sv_num_sms() * 16);
   const bool vec = ((uintptr_t)X % 16 == 0) && (ld % 2 == 0);
-  const int njobs = g.ntiles * g.nchunks;
-  const int ggrid = std::min(njobs, sv_num_sms());
   const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 127) / 128, sv_num_sms() * 4));
   const int mgrid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((N + CMB_WARPS - 1) / CMB_WARPS, (int64_t)sv_num_sms() * 16));
+      1, std::min<int64_t>((N + CMB_ROWS - 1) / CMB_ROWS, (int64_t)sv_num_sms() * 8));
   const ListOutB lo{list, count, nonfinite, list_off};
+  auto gemm = [&](int bn, const BigGeom& gg, int c) {
+    const int njobs = gg.ntiles * gg.nchunks;
+    const int ggrid = std::min(njobs, sv_num_sms());
+    const size_t smem = (size_t)gg.stages * gg.stage_bytes + 1024;
+    if (bf16) {
+      if (bn == 256)
+        gemm_big_kernel<true, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c, comp,
+                                                                  part, dev_err);
+      else if (bn == 128)
+        gemm_big_kernel<true, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c, comp,
+                                                                  part, dev_err);
+      else
+        gemm_big_kernel<true, 64><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c, comp,
+                                                                 part, dev_err);
+    } else {
+      if (bn == 256)
+        gemm_big_kernel<false, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c,
+                                                                   comp, part, dev_err);
+      else if (bn == 128)
+        gemm_big_kernel<false, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c,
+                                                                   comp, part, dev_err);
+      else
+        gemm_big_kernel<false, 64><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, gg, c, comp,
+                                                                  part, dev_err);
+    }
+    return cudaGetLastError();
+  };
   cudaError_t e;
   for (int c = 0; c < h.ncomp; ++c) {
     int tk = sv_trace_begin(SEVO_TK_CONVERT, st);
     if (bf16)
-      convert_kernel<true><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
+      convert_kernel<true><<<cvt_grid, CVT_THREADS, 0, st>>>(
           p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, nullptr, Ahi, Alo,
           comp ? comp_s : nullptr);
     else
-      convert_kernel<false><<<cvt_grid, CVT_WARPS * 32, 0, st>>>(
+      convert_kernel<false><<<cvt_grid, CVT_THREADS, 0, st>>>(
           p->desc_d, c, X, ld, seg.row0, N, h.D, h.kpad, vec, A32, nullptr, nullptr,
           comp ? comp_s : nullptr);
     sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (tune) {  // time every width on this data (one warm-up, then two runs each)
+      tune = false;
+      const int cand[3] = {64, 128, 256};
+      float ms[3] = {0.f, 0.f, 0.f};
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      e = cudaEventCreate(&e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&e1);
+      for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        const BigGeom gi = geom(cand[i]);
+        int tkt = sv_trace_begin(SEVO_TK_GEMM_BIG, st);
+        e = gemm(cand[i], gi, c);
+        sv_trace_end(tkt, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+          tkt = sv_trace_begin(SEVO_TK_GEMM_BIG, st);
+          e = gemm(cand[i], gi, c);
+          sv_trace_end(tkt, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], e0, e1);
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (e != cudaSuccess) return e;
+      int best = 1;
+      for (int i = 0; i < 3; ++i)
+        if (ms[i] < ms[best]) best = i;
+      BN = cand[best];
+      g = geom(BN);
+      sv_tune_store(SV_TUNE_BIG_NTILE, h.D, N, prec, BN, ms, cand, 3);
+    }
     tk = sv_trace_begin(SEVO_TK_GEMM_BIG, st);
-    if (bf16 && BN == 256)
-      gemm_big_kernel<true, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
-                                                                part, dev_err);
-    else if (bf16)
-      gemm_big_kernel<true, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
-                                                                part, dev_err);
-    else if (BN == 256)
-      gemm_big_kernel<false, 256><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
-                                                                 part, dev_err);
-    else
-      gemm_big_kernel<false, 128><<<ggrid, NTHREADS, smem, st>>>(mA, mAlo, p->desc_d, g, c, comp,
-                                                                 part, dev_err);
+    e = gemm(BN, g, c);
     sv_trace_end(tk, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     tk = sv_trace_begin(SEVO_TK_COMBINE, st);
-    combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, BN / WPQ,
+    combine_kernel<<<mgrid, CMB_WARPS * 32, 0, st>>>(p->desc_d, c, comp, h.D, g.nsub, SUB,
                                                      part, seg.row0, N, out, comp_g, lo);
     sv_trace_end(tk, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

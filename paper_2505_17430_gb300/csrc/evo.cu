@@ -1229,6 +1229,7 @@ int sv_policy_refine() { return g_policy_refine.load(); }
 long long sv_policy_test_wait() { return g_policy_test_wait.load(); }
 
 extern "C" int32_t sevo_set_policy(int32_t key, int64_t value) {
+  if (key == SEVO_POLICY_AUTOTUNE) return sv_tune_set_policy(value);
   if (key == SEVO_POLICY_TEST_WAIT) {
     if (value < 0 || value > SEVO_TEST_WAIT_MAX) return SEVO_ERR_ARG;
     g_policy_test_wait.store((long long)value);
@@ -1252,6 +1253,7 @@ extern "C" int64_t sevo_get_policy(int32_t key) {
   if (key == SEVO_POLICY_REFINE) return g_policy_refine.load();
   if (key == SEVO_POLICY_TEST_WAIT) return g_policy_test_wait.load();
   if (key == SEVO_POLICY_FUSE_OPS) return g_policy_fuse_ops.load();
+  if (key == SEVO_POLICY_AUTOTUNE) return sv_policy_autotune();
   return -1;
 }
 

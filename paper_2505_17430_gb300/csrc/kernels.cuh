@@ -137,6 +137,15 @@ int sv_policy_refine();
 long long sv_policy_test_wait();
 // SEVO_POLICY_FUSE_OPS's current value (0: off, the default)
 int sv_policy_fuse_ops();
+// measured launch choices (tune.cu): SEVO_POLICY_AUTOTUNE's value (1: on,
+// the default); a cached choice for (kind, D, rows, prec), 0 if none; a new
+// measured choice with its candidates' times
+enum : int { SV_TUNE_BIG_NTILE = 0 };
+int sv_policy_autotune();
+int32_t sv_tune_set_policy(int64_t value);
+int sv_tune_lookup(int kind, int D, int64_t rows, int prec);
+void sv_tune_store(int kind, int D, int64_t rows, int prec, int choice, const float* ms,
+                   const int* cand, int n);
 void sv_eval_scratch_carve(void* base, int D, bool any_comp, int prec, int64_t rows,
                            EvalScratch* s);
 // evaluate segments (same D) into out with refinement; resets counters first

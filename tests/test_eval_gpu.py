@@ -362,3 +362,78 @@ def test_bounded_wait_times_out_and_library_stays_usable(S, prec):
     got, info = p.evaluate(to_dev(X), prec=getattr(S, prec), sync=True)
     assert info["status"] == 0
     _check_mixed(prec, got.cpu().numpy(), q.eval(X), bound(p, q, X), info)
+
+
+def _tune_file(tmp_path, lines=()):
+    path = tmp_path / "tune.txt"
+    path.write_text("".join(l + "\n" for l in lines))
+    return str(path)
+
+
+@pytest.mark.parametrize("prec", ["TF32", "BF16X3"])
+@pytest.mark.parametrize("fam,D,N", [(6, 1000, 1024), (1, 300, 2000), (8, 257, 700)])
+def test_large_d_tile_widths_give_the_same_bits(S, tmp_path, monkeypatch, prec, fam, D, N):
+    """The large-D GEMM's N tile (64, 128 or 256 columns, chosen through the
+    tuning cache) changes only the speed: records are kept per 32-column
+    slice for every width, so all three give bit-identical results, which
+    match the oracle (hybrid Rosenbrock pairs and groups across slices,
+    compositions of hybrids)."""
+    import os
+    lib = S.lib()
+    p, q = S.Problem(2100 + fam, fam, D), O.Problem(2100 + fam, fam, D)
+    X = np.vstack([inputs.uniform_pop(N - 4, D, seed=fam), inputs.near(q.shift(0), 4, 1e-3, seed=fam)])
+    xt = to_dev(X)
+    pid = getattr(S, prec)
+    bucket = 1 << (N - 1).bit_length()
+    outs = []
+    try:
+        for bn in (64, 128, 256):
+            monkeypatch.setenv("SEVO_TUNE_FILE", _tune_file(tmp_path, [f"0 {D} {bucket} {pid} {bn}"]))
+            assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2) == 0
+            outs.append(p.evaluate(xt, prec=pid).cpu().numpy())
+    finally:
+        monkeypatch.delenv("SEVO_TUNE_FILE")
+        lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    _check_mixed(prec, outs[0], q.eval(X), bound(p, q, X))
+
+
+def test_autotuner_measures_once_and_caches(S, tmp_path, monkeypatch):
+    """SEVO_POLICY_AUTOTUNE: the first large-D call of a (D, row bucket,
+    precision) times every width (extra GEMM launches) and writes the choice
+    to the cache file; the next call, and a call after the cache is dropped
+    and read back from the file, launch the GEMM once; all give the same
+    bits, and the same bits as the fixed rule (autotuning off)."""
+    import os
+    lib = S.lib()
+    D, N = 600, 1500
+    p = S.Problem(2300, S.RASTRIGIN, D)
+    xt = to_dev(inputs.uniform_pop(N, D, seed=23))
+    path = _tune_file(tmp_path)
+    monkeypatch.setenv("SEVO_TUNE_FILE", path)
+    try:
+        assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2) == 0
+        assert lib.sevo_get_policy(S.POLICY_AUTOTUNE) == 1
+        outs, gemms = [], []
+        for reload in (False, False, True):
+            if reload:
+                assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2) == 0
+            S.trace_enable(True)
+            outs.append(p.evaluate(xt, prec=S.TF32).cpu().numpy())
+            t = S.trace_read()
+            S.trace_enable(False)
+            gemms.append(t["gemm_big"][0])
+        lines = open(path).read().split("\n")
+        assert len([l for l in lines if l.strip()]) == 1
+        kind, d, bucket, prec, choice = lines[0].split()[:5]
+        assert (kind, d, bucket, prec) == ("0", str(D), "2048", str(S.TF32))
+        assert int(choice) in (64, 128, 256)
+        assert gemms[0] > 1 and gemms[1] == 1 and gemms[2] == 1
+        assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 0) == 0
+        outs.append(p.evaluate(xt, prec=S.TF32).cpu().numpy())
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o)
+        assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 3) == S.ERR_ARG
+    finally:
+        monkeypatch.delenv("SEVO_TUNE_FILE")
+        lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2)
