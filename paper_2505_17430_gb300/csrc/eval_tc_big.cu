@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool live = row < N;
       for (int ls = sl; ls < NSL; ls += WPQ) {
         const int sb = nb * NSL + ls;  // slice index within the row
+        if (sb >= geo.nsub) break;     // a wide tile past the padded rotation: no record
         const int c0 = sb * SUB, c1 = min(geo.D, c0 + SUB);
         float* rec = part + (int64_t)sb * REC * N + row;  // slot k at rec[k * N]
         float zf = 0.f, zl = 0.f;
@@ -332,32 +333,25 @@ __device__ __forceinline__ int group_of(const ProblemDev& P, int c, bool comp, i
   return P.gid[c][i];
 }
 
-// A block per 32 rows (lane = row, so every record load is a coalesced 128
-// bytes): warp w merges slices w, w + 8, ... of its rows into per-group
-// accumulators, adding the Rosenbrock pair across a slice border from the
-// previous slice's last z; the eight warps' partial sums are then added in
-// warp order (a fixed order: the result does not depend on scheduling), the
-// groups finished and the row's FP64 error written.
-constexpr int CMB_WARPS = 8;
-constexpr int CMB_ROWS = 32;
+// one warp per row: lane l merges slices l, l + 32, ... into per-group
+// accumulators (adding the Rosenbrock pair across a slice border from the
+// previous slice's last z), then the groups are summed across the warp
+constexpr int CMB_WARPS = 4;
 
 __global__ void __launch_bounds__(CMB_WARPS * 32)
-    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub, int sub,
+    combine_kernel(const ProblemDev* __restrict__ Pp, int c, bool comp, int D, int nsub, int SUB,
                    const float* __restrict__ part, int64_t row0, int64_t N,
                    double* __restrict__ out, double* __restrict__ comp_g, ListOutB lo) {
-  __shared__ float red[CMB_WARPS][3 * SV_MAXG][CMB_ROWS];
   const ProblemDev& P = *Pp;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int ng = P.ngc[c];
-  const int64_t nblk = (N + CMB_ROWS - 1) / CMB_ROWS;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t lr = blk * CMB_ROWS + lane;
-    const bool live = lr < N;
+  const int64_t nw = (int64_t)gridDim.x * CMB_WARPS;
+  for (int64_t lr = (int64_t)blockIdx.x * CMB_WARPS + (threadIdx.x >> 5); lr < N; lr += nw) {
     Acc32 acc[SV_MAXG];
 #pragma unroll
     for (int g = 0; g < SV_MAXG; ++g) acc32_init(acc[g]);
-    for (int sb = warp; sb < nsub && live; sb += CMB_WARPS) {
-      const int c0 = sb * sub, c1 = min(D, c0 + sub);
+    for (int sb = lane; sb < nsub; sb += 32) {
+      const int c0 = sb * SUB, c1 = min(D, c0 + SUB);
       if (c0 >= c1) break;
       const float* rec = part + (int64_t)sb * REC * N + lr;  // slot k at rec[k * N]
       const int g0 = group_of(P, c, comp, c0), g1 = group_of(P, c, comp, c1 - 1);
@@ -380,46 +374,41 @@ __global__ void __launch_bounds__(CMB_WARPS * 32)
         }
       }
     }
+    double gsum = 0.0;
 #pragma unroll
     for (int g = 0; g < SV_MAXG; ++g) {
-      red[warp][3 * g][lane] = acc[g].a0;
-      red[warp][3 * g + 1][lane] = acc[g].a1;
-      red[warp][3 * g + 2][lane] = acc[g].a2;
-    }
-    __syncthreads();
-    if (warp == 0 && live) {
-      double gsum = 0.0;
+      if (g < ng) {
+        float a0 = acc[g].a0, a1 = acc[g].a1, a2 = acc[g].a2;
 #pragma unroll
-      for (int g = 0; g < SV_MAXG; ++g) {
-        if (g < ng) {
-          Acc32 t;
-          t.a0 = t.a1 = t.a2 = 0.f;
-          for (int w = 0; w < CMB_WARPS; ++w) {
-            t.a0 += red[w][3 * g][lane];
-            t.a1 += red[w][3 * g + 1][lane];
-            t.a2 += red[w][3 * g + 2][lane];
-          }
-          const int body = P.gbody[c][g];
-          const int n = P.gstart[c][g + 1] - P.gstart[c][g];
-          gsum += (double)finalize32(body, t, n);
+        for (int m = 16; m >= 1; m >>= 1) {
+          a0 += __shfl_xor_sync(0xffffffffu, a0, m);
+          a1 += __shfl_xor_sync(0xffffffffu, a1, m);
+          a2 += __shfl_xor_sync(0xffffffffu, a2, m);
         }
-      }
-      const int64_t row = row0 + lr;
-      if (comp) {
-        comp_g[row * SV_MAXC + c] = gsum;
-      } else {
-        double err = gsum;
-        if (!isfinite(err)) {
-          err = __longlong_as_double(0x7ff8000000000000ll);
-          if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
-        } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
-          int k = atomicAdd(lo.count, 1);
-          lo.list[lo.list_off + k] = (int32_t)row;
-        }
-        out[row] = err;
+        Acc32 t;
+        t.a0 = a0;
+        t.a1 = a1;
+        t.a2 = a2;
+        const int body = P.gbody[c][g];
+        const int n = P.gstart[c][g + 1] - P.gstart[c][g];
+        gsum += (double)finalize32(body, t, n);
       }
     }
-    __syncthreads();
+    if (lane != 0) continue;
+    const int64_t row = row0 + lr;
+    if (comp) {
+      comp_g[row * SV_MAXC + c] = gsum;
+      continue;
+    }
+    double err = gsum;
+    if (!isfinite(err)) {
+      err = __longlong_as_double(0x7ff8000000000000ll);
+      if (lo.nonfinite) atomicAdd(lo.nonfinite, 1u);
+    } else if (lo.list && err < SEVO_REFINE_THRESHOLD) {
+      int k = atomicAdd(lo.count, 1);
+      lo.list[lo.list_off + k] = (int32_t)row;
+    }
+    out[row] = err;
   }
 }
 
@@ -583,7 +572,7 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   const bool vec = ((uintptr_t)X % 16 == 0) && (ld % 2 == 0);
   const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 127) / 128, sv_num_sms() * 4));
   const int mgrid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((N + CMB_ROWS - 1) / CMB_ROWS, (int64_t)sv_num_sms() * 8));
+      1, std::min<int64_t>((N + CMB_WARPS - 1) / CMB_WARPS, (int64_t)sv_num_sms() * 16));
   const ListOutB lo{list, count, nonfinite, list_off};
   auto gemm = [&](int bn, const BigGeom& gg, int c) {
     const int njobs = gg.ntiles * gg.nchunks;
