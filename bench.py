@@ -203,7 +203,7 @@ def traced_step_kernels(S, torch, states, gen, K, serial=False):
     return {k: v for k, v in t.items() if v[0] > 0}, gen
 
 
-def rooflines(trace, states, peaks, K):
+def rooflines(trace, states, peaks, K, fp64=None):
     """Dominant kernel (fused tcgen05 evaluation) and the streaming DE/PSO
     kernels against the measured HBM copy bandwidth.  Rows per launch: every
     state's rows for the fused evaluation (one launch per step), one state's
@@ -234,6 +234,20 @@ def rooflines(trace, states, peaks, K):
     # of partner indices; PSO move: x, v, pbest read, x, v written (the guide
     # row is one per run or neighbourhood and is served from L2)
     stream = {k: entry(k, b) for k, b in (("de_trial", 5 * 8 * D + 16), ("pso_move", 5 * 8 * D))}
+    # the FP64 pipe, which binds both: the formula's FP64 operations per
+    # coordinate (DE/rand/1 2, current-to-pbest 4 -- one launch of each per
+    # step -- and the PSO move 8) against the DGEMM rate measured here
+    if fp64:
+        for k, ops in (("de_trial", (2 + 4) / 2), ("pso_move", 8)):
+            n, ms = trace.get(k, (0, 0.0))
+            if n and stream.get(k):
+                ach = n * FAMILIES * NP * D * ops / (ms * 1e-3)
+                stream[k]["fp64_pipe"] = {"bound": "alu", "unit": "FP64 op/s",
+                                          "ops_per_coordinate": ops,
+                                          "achieved": round(ach / 1e9, 2) * 1e9,
+                                          "peak": round(fp64 / 1e9, 2) * 1e9,
+                                          "frac": round(ach / fp64, 4),
+                                          "peak_source": "cuBLAS DGEMM 4096^3 timed here"}
     shares = {k: {"launches": n, "ms": round(ms, 3), "share": round(ms / total_ms, 4)}
               for k, (n, ms) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
     return main, stream, shares
@@ -505,23 +519,92 @@ def grid_algs(S, D, prec):
 
 
 def run_grid_bench(S, dims, prec, runs=GRID_RUNS):
-    res = {"wall_ms": 0.0, "evals": 0, "tasks": 0, "success": {}}
+    """The whole grid in one sevo_run_grid call: one bucket per (algorithm,
+    D), all buckets running side by side."""
     names = ("de_ctpb", "pso_gbest", "pso_ring")
-    succ = {n: [0, 0] for n in names}
+    probs, algs, tasks = [], [], []
     for D in dims:
-        probs = grid_problems(S, D, lambda seed, fam, d: S.Problem(seed, fam, d))
-        algs = grid_algs(S, D, prec)
-        tasks = [(pi, ai, 1 + r + 1000 * pi) for pi in range(len(probs)) for ai in range(3)
-                 for r in range(runs)]
-        r = S.sevo_run_grid(probs, algs, tasks)
-        res["wall_ms"] += r["wall_ms"]
-        res["evals"] += int(r["evals"])
-        res["tasks"] += len(tasks)
-        for (pi, ai, _), ok in zip(tasks, r["success"]):
-            succ[names[ai]][0] += int(ok)
-            succ[names[ai]][1] += 1
-    res["success"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in succ.items()}
-    return res
+        p0, a0 = len(probs), len(algs)
+        ps = grid_problems(S, D, lambda seed, fam, d: S.Problem(seed, fam, d))
+        probs += ps
+        algs += grid_algs(S, D, prec)
+        tasks += [(p0 + pi, a0 + ai, 1 + r + 1000 * pi) for pi in range(len(ps)) for ai in range(3)
+                  for r in range(runs)]
+    r = S.sevo_run_grid(probs, algs, tasks)
+    succ = {n: [0, 0] for n in names}
+    for (pi, ai, _), ok in zip(tasks, r["success"]):
+        succ[names[ai % 3]][0] += int(ok)
+        succ[names[ai % 3]][1] += 1
+    return {"wall_ms": r["wall_ms"], "evals": int(r["evals"]), "tasks": len(tasks),
+            "success": {k: round(v[0] / max(v[1], 1), 4) for k, v in succ.items()}}
+
+
+def wilson(k, n, z=1.959963984540054):
+    """95 % Wilson score interval of a success proportion k / n."""
+    if n == 0:
+        return [0.0, 1.0]
+    p = k / n
+    den = 1.0 + z * z / n
+    mid = (p + z * z / (2 * n)) / den
+    half = z * ((p * (1 - p) / n + z * z / (4 * n * n)) ** 0.5) / den
+    return [round(mid - half, 4), round(mid + half, 4)]
+
+
+def success_vs_fp64(S, large=True):
+    """Mixed precision (TF32 rotation + FP64 refinement) against the plain
+    FP64 GPU path on the same runs (same seeds): success rate at 1e-8 with
+    its 95 % interval, median final error and evaluations per second.
+    D = 100: 5 problems (Rastrigin, Griewank, Ackley, hybrid, composition)
+    x 11 seeds x {DE current-to-pbest NP = 18 D, PSO ring NP = 40} at the
+    full budget 1e4 D.  D = 1000: 2 hybrid + 2 composition instances x 3
+    seeds x {DE NP = 200, PSO NP = 1000} at 3e5 evaluations (a tenth of the
+    3e6 budget, so that the FP64 path's runs fit the benchmark's time)."""
+    import numpy as np
+    out = {}
+    cases = [(100, [(0x5EB10000 + f, f) for f in (2, 5, 4, 6, 7)], 11,
+              [(1, 18 * 100), (3, 40)], 10 ** 6)]
+    if large:
+        cases.append((1000, [(0x5EB20000 + i, 6) for i in range(2)] +
+                      [(0x5EB20100 + i, 7) for i in range(2)], 3, [(1, 200), (3, 1000)], 300000))
+    for D, plist, seeds, alg_np, budget in cases:
+        probs = [S.Problem(sd, f, D) for sd, f in plist]
+        tasks = [(pi, ai, 7 + s + 100 * pi) for pi in range(len(probs)) for ai in range(len(alg_np))
+                 for s in range(seeds)]
+        row = {"problems": len(probs), "seeds": seeds, "budget": budget}
+        for name, prec in (("tf32", S.TF32), ("fp64", S.FP64)):
+            algs = [S.alg_params(a, npop, budget, prec=prec) for a, npop in alg_np]
+            r = S.sevo_run_grid(probs, algs, tasks)
+            per = {}
+            for ai, (a, npop) in enumerate(alg_np):
+                idx = [t for t, (_, aj, _) in enumerate(tasks) if aj == ai]
+                ok = int(np.sum(np.asarray(r["success"])[idx]))
+                key = ("de_ctpb" if a == 1 else "pso_ring") + f"_np{npop}"
+                per[key] = {"success": ok, "runs": len(idx), "ci95": wilson(ok, len(idx)),
+                            "median_final_error": float(np.median(np.asarray(r["best"])[idx]))}
+            row[name] = {"wall_s": round(r["wall_ms"] / 1e3, 3),
+                         "evals_per_s": round(r["evals"] / (r["wall_ms"] / 1e3), 1), "algs": per}
+        row["tf32_speedup"] = round(row["tf32"]["evals_per_s"] / row["fp64"]["evals_per_s"], 2)
+        out[f"d{D}"] = row
+    return out
+
+
+def fp64_peak(torch):
+    """FP64 rate of this GPU, measured here: a cuBLAS DGEMM of 4096^3 timed
+    with CUDA events (best of 5), in FP64 operations per second."""
+    n = 4096
+    a = torch.rand((n, n), dtype=torch.float64, device="cuda")
+    b = torch.rand((n, n), dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * n ** 3 / (best * 1e-3)
 
 
 def oracle_grid_sample(dims, frac=0.1):
@@ -761,14 +844,17 @@ def main():
             "ms_per_step": round(ms64 / 2, 3)}
     del st64
     KT = min(args.steps, 200)
+    f64peak = fp64_peak(torch)
     traced, gen = traced_step_kernels(S, torch, states, gen, KT)
-    roof, stream_roof, shares = rooflines(traced, states, peaks, KT)
+    roof, stream_roof, shares = rooflines(traced, states, peaks, KT, f64peak)
     traced1, gen = traced_step_kernels(S, torch, states, gen, KT, serial=True)
-    roof1, stream1, shares1 = rooflines(traced1, states, peaks, KT)
+    roof1, stream1, shares1 = rooflines(traced1, states, peaks, KT, f64peak)
     roof["alone"] = {k: roof1[k] for k in ("achieved", "frac", "launch_ms")}
     for k in stream_roof:
         if stream_roof[k] and stream1.get(k):
             stream_roof[k]["alone"] = {q: stream1[k][q] for q in ("achieved", "frac", "launch_ms")}
+            if stream1[k].get("fp64_pipe"):
+                stream_roof[k]["alone"]["fp64_frac"] = stream1[k]["fp64_pipe"]["frac"]
     e2e, gen = e2e_rate(S, torch, states, gen, max(3, min(args.steps // 4, 400)))
     modes = mode_eval_rates(S, torch, probs)
     large = None if args.no_large_d else large_d_rates(S, torch, peaks)
@@ -777,6 +863,7 @@ def main():
     sh31 = shade_sec31(S)
     psode4 = psode_case1(S)
     cso33 = None if args.no_large_d else cso_sec33(S)
+    svf = success_vs_fp64(S, large=not args.no_large_d)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     grid = None
     if not args.no_grid:
@@ -821,7 +908,8 @@ def main():
             "kernel_shares": shares, "kernel_shares_alone": shares1,
             "eval_only_evals_per_s": modes, "large_d": large,
             "c4_sample": c4, "shade_sec31": sh31, "psode_case1": psode4, "cso_sec33": cso33,
-            "c0_single_run": c0, "grid": grid}
+            "c0_single_run": c0, "grid": grid, "success_vs_fp64": svf,
+            "fp64_peak_op_per_s": round(f64peak / 1e9, 2) * 1e9}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

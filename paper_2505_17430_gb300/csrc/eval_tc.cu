@@ -719,6 +719,15 @@ int32_t sv_build_tmaps(sevo_problem* p) {
         !make_map(&p->tmap_lo[c], h.Mlo[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h.kpad, h.npad,
                   64, rows))
       return SEVO_ERR_CUDA;
+    // 64-row boxes for the large-D GEMM's 64-column tiles
+    if (h.D > 128 &&
+        (!make_map(&p->tmap_f32h[c], h.M32[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.kpad, h.npad,
+                   32, 64) ||
+         !make_map(&p->tmap_hih[c], h.Mhi[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h.kpad, h.npad,
+                   64, 64) ||
+         !make_map(&p->tmap_loh[c], h.Mlo[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h.kpad,
+                   h.npad, 64, 64)))
+      return SEVO_ERR_CUDA;
   }
   p->tmap_rows = rows;
   p->tmaps_ready = true;

@@ -30,7 +30,7 @@ constexpr int WPQ = 4;               // epilogue warps per TMEM lane quarter
 constexpr int NEPI = 4 * WPQ;
 constexpr int SUB = 32;              // columns of z per record slice, for every N tile
 constexpr int MAX_NBUF = 8;
-constexpr int MAX_STAGES = 6;
+constexpr int MAX_STAGES = 8;
 // N tile of one job (64, 128 or 256 columns of z): NBUF TMEM accumulators of
 // BN columns fill the 512-column TMEM; a job has NSL record slices of SUB
 // columns, walked by the epilogue warps of each lane quarter in turn; the B
@@ -40,6 +40,8 @@ constexpr int MAX_STAGES = 6;
 template <int BN>
 struct Tile {
   static constexpr int NBUF = 512 / BN, NSL = BN / SUB, NB = BN >= 128 ? BN / 128 : 1;
+  static constexpr int BBOX = BN >= 128 ? 128 : 64;  // rotation rows per B box
+  static constexpr int B_BYTES = NB * BBOX * 128;   // one operand copy's B per stage
 };
 constexpr int WARP_TMA = NEPI, WARP_MMA = NEPI + 1;
 constexpr int NTHREADS = (NEPI + 2) * 32;
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = geo.stages;
   constexpr int NBUF = Tile<BN>::NBUF, NSL = Tile<BN>::NSL, NB = Tile<BN>::NB;
+  constexpr int BBOX = Tile<BN>::BBOX, B_BYTES = Tile<BN>::B_BYTES;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&bars.full[s], 1);
@@ -183,8 +186,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
-      const CUtensorMap* mB = BF16 ? P->tmaphi[c] : P->tmap32[c];
-      const CUtensorMap* mBlo = P->tmaplo[c];
+      const CUtensorMap* mB = BBOX == 64 ? (BF16 ? P->tmaphih[c] : P->tmap32h[c])
+                                         : (BF16 ? P->tmaphi[c] : P->tmap32[c]);
+      const CUtensorMap* mBlo = BBOX == 64 ? P->tmaploh[c] : P->tmaplo[c];
       uint32_t it = 0;
       bool ok = true;
       for (int job = blockIdx.x; job < njobs_total && ok; job += gridDim.x) {
@@ -204,12 +208,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc::tma_load_2d(st, &mapA, &bars.full[s], kb * KBLK, tile * BM);
 #pragma unroll
           for (int q = 0; q < NB; ++q)
-            tc::tma_load_2d(st + (1 + q) * KB_BYTES, mB, &bars.full[s], kb * KBLK, nb * BN + q * 128);
+            tc::tma_load_2d(st + KB_BYTES + q * BBOX * 128, mB, &bars.full[s], kb * KBLK,
+                            nb * BN + q * 128);
           if (BF16) {
-            tc::tma_load_2d(st + (1 + NB) * KB_BYTES, &mapAlo, &bars.full[s], kb * KBLK, tile * BM);
+            unsigned char* lo = st + KB_BYTES + B_BYTES;
+            tc::tma_load_2d(lo, &mapAlo, &bars.full[s], kb * KBLK, tile * BM);
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-              tc::tma_load_2d(st + (2 + NB + q) * KB_BYTES, mBlo, &bars.full[s], kb * KBLK,
+              tc::tma_load_2d(lo + KB_BYTES + q * BBOX * 128, mBlo, &bars.full[s], kb * KBLK,
                               nb * BN + q * 128);
           }
         }
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int ks = 0; ks < 4; ++ks) {
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (BF16) {
-              const uint32_t aLo = aS + (1 + NB) * KB_BYTES, bLo = aS + (2 + NB) * KB_BYTES;
+              const uint32_t aLo = aS + KB_BYTES + B_BYTES, bLo = aLo + KB_BYTES;
               tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bS + ks * 32),
                           geo.idesc, acc);
               tc::mma_f16(d_tmem, tc::sdesc_sw128(aS + ks * 32), tc::sdesc_sw128(bLo + ks * 32),
@@ -531,8 +537,8 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
     g.nsub = h.npad / SUB;
     g.ntiles = (int)tiles;
     g.N = N;
-    const int nb = bn >= 128 ? bn / 128 : 1;
-    g.stage_bytes = (bf16 ? 2 : 1) * (1 + nb) * KB_BYTES;
+    const int nb = bn >= 128 ? bn / 128 : 1, bbox = bn >= 128 ? 128 : 64;
+    g.stage_bytes = (bf16 ? 2 : 1) * (KB_BYTES + nb * bbox * 128);
     g.stages = std::min(MAX_STAGES, (192 * 1024) / g.stage_bytes);
     g.idesc = tc::idesc_make(bf16 ? 1 : 2, BM, bn);
     return g;

@@ -301,11 +301,15 @@ static int32_t upload(sevo_problem* p) {
     h.oh32[c] = (const float*)(base + ooh);
     h.ol32[c] = (const float*)(base + ool);
   }
-  size_t otm = take((size_t)3 * SV_MAXC * sizeof(CUtensorMap));
+  size_t otm = take((size_t)6 * SV_MAXC * sizeof(CUtensorMap));
   for (int c = 0; c < nc; ++c) {
-    h.tmap32[c] = (const CUtensorMap*)(base + otm) + c;
-    h.tmaphi[c] = (const CUtensorMap*)(base + otm) + SV_MAXC + c;
-    h.tmaplo[c] = (const CUtensorMap*)(base + otm) + 2 * SV_MAXC + c;
+    const CUtensorMap* m = (const CUtensorMap*)(base + otm);
+    h.tmap32[c] = m + c;
+    h.tmaphi[c] = m + SV_MAXC + c;
+    h.tmaplo[c] = m + 2 * SV_MAXC + c;
+    h.tmap32h[c] = m + 3 * SV_MAXC + c;
+    h.tmaphih[c] = m + 4 * SV_MAXC + c;
+    h.tmaploh[c] = m + 5 * SV_MAXC + c;
   }
   size_t od = take(sizeof(ProblemDev));
   // the descriptors encode device addresses, so they are built after the
@@ -316,6 +320,12 @@ static int32_t upload(sevo_problem* p) {
     std::memcpy(&blob[otm + c * sizeof(CUtensorMap)], &p->tmap_f32[c], sizeof(CUtensorMap));
     std::memcpy(&blob[otm + (SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_hi[c], sizeof(CUtensorMap));
     std::memcpy(&blob[otm + (2 * SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_lo[c],
+                sizeof(CUtensorMap));
+    std::memcpy(&blob[otm + (3 * SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_f32h[c],
+                sizeof(CUtensorMap));
+    std::memcpy(&blob[otm + (4 * SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_hih[c],
+                sizeof(CUtensorMap));
+    std::memcpy(&blob[otm + (5 * SV_MAXC + c) * sizeof(CUtensorMap)], &p->tmap_loh[c],
                 sizeof(CUtensorMap));
   }
   std::memcpy(&blob[od], &h, sizeof(ProblemDev));

@@ -95,6 +95,9 @@ struct ProblemDev {
   const CUtensorMap* tmap32[SV_MAXC];   // device copies of the TMA descriptors
   const CUtensorMap* tmaphi[SV_MAXC];
   const CUtensorMap* tmaplo[SV_MAXC];
+  const CUtensorMap* tmap32h[SV_MAXC];  // the same with 64-row boxes (D > 128)
+  const CUtensorMap* tmaphih[SV_MAXC];
+  const CUtensorMap* tmaploh[SV_MAXC];
   const float* oh32[SV_MAXC];           // D: o split as oh + ol (see sv_split_hi_lo)
   const float* ol32[SV_MAXC];
   int32_t ngc[SV_MAXC];                 // groups of component c
@@ -125,6 +128,9 @@ struct sevo_problem {
   CUtensorMap tmap_f32[SV_MAXC];   // M32: npad x kpad fp32, box (32, rows)
   CUtensorMap tmap_hi[SV_MAXC];    // Mhi: npad x kpad bf16, box (64, rows)
   CUtensorMap tmap_lo[SV_MAXC];
+  CUtensorMap tmap_f32h[SV_MAXC];  // 64-row boxes (D > 128: 64-column GEMM tiles)
+  CUtensorMap tmap_hih[SV_MAXC];
+  CUtensorMap tmap_loh[SV_MAXC];
   int32_t tmap_rows;               // box rows used when the maps were built
 };
 
