@@ -235,12 +235,22 @@ static int32_t upload(sevo_problem* p) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t per = al(D * 8) + al(DD * 8) + al(DD * 4) + al(NK * 4) + 2 * al(NK * 2) +
                      al(D * 8) + al(D * 4) + al(D * 4) + 2 * al(D * 4);
-  p->dev_bytes = per * nc + al(3 * SV_MAXC * sizeof(CUtensorMap)) + al(sizeof(ProblemDev));
+  // six TMA descriptors per component slot: fp32, bf16 hi and lo, each with
+  // full-height and 64-row boxes
+  constexpr size_t kMaps = 6 * SV_MAXC;
+  p->dev_bytes = per * nc + al(kMaps * sizeof(CUtensorMap)) + al(sizeof(ProblemDev));
   SV_CUDA(cudaMalloc(&p->dev_block, p->dev_bytes));
   std::vector<unsigned char> blob(p->dev_bytes, 0);
   char* base = (char*)p->dev_block;
   size_t off = 0;
+  bool overflow = false;
+  // placement in the block; a request past its size is refused (offset 0,
+  // reported below) rather than written out of bounds
   auto take = [&](size_t b) {
+    if (off + al(b) > p->dev_bytes) {
+      overflow = true;
+      return (size_t)0;
+    }
     size_t o = off;
     off += al(b);
     return o;
@@ -301,7 +311,7 @@ static int32_t upload(sevo_problem* p) {
     h.oh32[c] = (const float*)(base + ooh);
     h.ol32[c] = (const float*)(base + ool);
   }
-  size_t otm = take((size_t)6 * SV_MAXC * sizeof(CUtensorMap));
+  size_t otm = take(kMaps * sizeof(CUtensorMap));
   for (int c = 0; c < nc; ++c) {
     const CUtensorMap* m = (const CUtensorMap*)(base + otm);
     h.tmap32[c] = m + c;
@@ -312,6 +322,7 @@ static int32_t upload(sevo_problem* p) {
     h.tmaploh[c] = m + 5 * SV_MAXC + c;
   }
   size_t od = take(sizeof(ProblemDev));
+  if (overflow) return SEVO_ERR_STATE;  // layout and size out of step: nothing is published
   // the descriptors encode device addresses, so they are built after the
   // operand pointers are known and copied into the block with the rest
   int32_t st = sv_build_tmaps(p);
