@@ -96,20 +96,31 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- our arm
-def make_states(S, prec, seed0, torch):
-    """One batched state per algorithm, each on its own CUDA stream: the three
-    algorithms' runs are independent, so their generations overlap on the
-    GPU (the fused evaluation of one state leaves issue slots that another
-    state's DE/PSO kernels use)."""
+GROUPS = 2  # groups of states stepped by one sevo_state_step_many call each
+
+
+def make_states(S, prec, seed0, torch, groups=None):
+    """One batched state per algorithm and group of families, each on its
+    own CUDA stream; a group holds one state per algorithm over FAMILIES /
+    groups of the six problems.  Each step advances every state by one
+    generation: one sevo_state_step_many call per group, so that one group's
+    joint evaluation (tensor cores, FP32) runs while the other group's DE and
+    PSO operators (FP64 pipe) run.  The work per step is the same for any
+    number of groups: 3 algorithms x 6 populations of NP rows."""
+    groups = groups or GROUPS
     probs = [S.Problem(0x5EB00000 + f, f, D) for f in range(FAMILIES)]
+    per = FAMILIES // groups
     states = []
-    for k, (name, alg) in enumerate(ALGS):
-        params = S.alg_params(alg, NP, 10 ** 12, prec=prec)
-        seeds = [seed0 + 1000 * k + f for f in range(FAMILIES)]
-        stream = torch.cuda.Stream()
-        st = S.State(probs, params, seeds, stream=stream)
-        st.torch_stream = stream  # keep the stream alive with its state
-        states.append(st)
+    for gi in range(groups):
+        fams = list(range(gi * per, (gi + 1) * per))
+        for k, (name, alg) in enumerate(ALGS):
+            params = S.alg_params(alg, NP, 10 ** 12, prec=prec)
+            seeds = [seed0 + 1000 * k + f for f in fams]
+            stream = torch.cuda.Stream()
+            st = S.State([probs[f] for f in fams], params, seeds, stream=stream)
+            st.torch_stream = stream  # keep the stream alive with its state
+            st.group = gi
+            states.append(st)
     torch.cuda.synchronize()
     return probs, states
 
@@ -117,10 +128,19 @@ def make_states(S, prec, seed0, torch):
 RESTART_EVERY = 25
 
 
+def groups_of(states):
+    """The states of each group, in group order."""
+    out = {}
+    for st in states:
+        out.setdefault(getattr(st, "group", 0), []).append(st)
+    return [out[k] for k in sorted(out)]
+
+
 def run_steps(states, first_gen, n, serial=False):
     """Generations first_gen .. first_gen + n - 1 of every state, one
-    sevo_state_step_many call per generation (each state's operators on its
-    own stream, every state's rows evaluated in one fused launch).  Every
+    sevo_state_step_many call per group and generation (each state's
+    operators on its own stream, the group's rows evaluated in one fused
+    launch).  Every
     RESTART_EVERY generations each run restarts from a fresh uniform
     population (sevo_state_restart, new seeds; its work is inside the timed
     region, its evaluations are not counted), so the timed generations stay
@@ -134,9 +154,10 @@ def run_steps(states, first_gen, n, serial=False):
         if g % RESTART_EVERY == 0:
             for k, st in enumerate(states):
                 st.restart([(g * 7919 + 1000 * k + r) & 0xFFFFFFFF for r in range(st.R)])
-        rc = S.sevo_state_step_many(states, g)
-        if rc != 0:
-            raise RuntimeError(f"step failed: {rc}")
+        for grp in groups_of(states):
+            rc = S.sevo_state_step_many(grp, g)
+            if rc != 0:
+                raise RuntimeError(f"step failed: {rc}")
         if serial:
             torch.cuda.synchronize()
     return first_gen + n
@@ -194,16 +215,19 @@ FUSED_SOURCES = ("eval_tc.cu", "tc_walk.cuh", "bodies.cuh", "tc_ptx.cuh")
 def traced_step_kernels(S, torch, states, gen, K, serial=False):
     """Per-kernel device time from a traced repeat of the timed steps (CUDA
     events recorded on the launching stream around every launch); serial:
-    the device drains after every generation.  Returns (trace, gen, K)."""
+    the device drains after every generation.  Returns (trace, next gen,
+    restarts in the window: each adds one evaluation of every state's rows)."""
     S.trace_enable(True)
+    g0 = gen
     gen = run_steps(states, gen, K, serial=serial)
     torch.cuda.synchronize()
     t = S.trace_read()
     S.trace_enable(False)
-    return {k: v for k, v in t.items() if v[0] > 0}, gen
+    restarts = sum(1 for g in range(g0, g0 + K) if g % RESTART_EVERY == 0)
+    return {k: v for k, v in t.items() if v[0] > 0}, gen, restarts
 
 
-def rooflines(trace, states, peaks, K, fp64=None):
+def rooflines(trace, states, peaks, K, fp64=None, restarts=0):
     """Dominant kernel (fused tcgen05 evaluation) and the streaming DE/PSO
     kernels against the measured HBM copy bandwidth.  Rows per launch: every
     state's rows for the fused evaluation (one launch per step), one state's
@@ -218,7 +242,8 @@ def rooflines(trace, states, peaks, K, fp64=None):
         if not n:
             return None
         per = ms / n
-        rows = step_rows * K // n if kind == "eval_tc_fused" else FAMILIES * NP
+        rows = (step_rows * (K + restarts) // n if kind == "eval_tc_fused"
+                else states[0].R * NP)
         algo = rows * bytes_per_row
         ach = algo / (per * 1e-3) / 1e9
         return {"kernel": kind, "bound": bound, "achieved": round(ach, 1), "peak": peak,
@@ -241,7 +266,7 @@ def rooflines(trace, states, peaks, K, fp64=None):
         for k, ops in (("de_trial", (2 + 4) / 2), ("pso_move", 8)):
             n, ms = trace.get(k, (0, 0.0))
             if n and stream.get(k):
-                ach = n * FAMILIES * NP * D * ops / (ms * 1e-3)
+                ach = n * states[0].R * NP * D * ops / (ms * 1e-3)
                 stream[k]["fp64_pipe"] = {"bound": "alu", "unit": "FP64 op/s",
                                           "ops_per_coordinate": ops,
                                           "achieved": round(ach / 1e9, 2) * 1e9,
@@ -477,7 +502,8 @@ def e2e_rate(S, torch, states, gen, K):
         for st, hx in zip(states, hostX):
             S.check(lib.sevo_state_set_async(st.h, C.cast(C.c_void_p(hx.data_ptr()), dp), None,
                                              None, 0, None, None, None, -1), "sevo_state_set_async")
-        S.check(S.sevo_state_step_many(states, g), "sevo_state_step_many")
+        for grp in groups_of(states):
+            S.check(S.sevo_state_step_many(grp, g), "sevo_state_step_many")
         for st, hf in zip(states, hostF):
             S.check(lib.sevo_state_get_async(st.h, None, C.cast(C.c_void_p(hf.data_ptr()), dp),
                                              None, None, None, None, None, None),
@@ -850,10 +876,10 @@ def main():
     del st64
     KT = min(args.steps, 200)
     f64peak = fp64_peak(torch)
-    traced, gen = traced_step_kernels(S, torch, states, gen, KT)
-    roof, stream_roof, shares = rooflines(traced, states, peaks, KT, f64peak)
-    traced1, gen = traced_step_kernels(S, torch, states, gen, KT, serial=True)
-    roof1, stream1, shares1 = rooflines(traced1, states, peaks, KT, f64peak)
+    traced, gen, rs = traced_step_kernels(S, torch, states, gen, KT)
+    roof, stream_roof, shares = rooflines(traced, states, peaks, KT, f64peak, rs)
+    traced1, gen, rs1 = traced_step_kernels(S, torch, states, gen, KT, serial=True)
+    roof1, stream1, shares1 = rooflines(traced1, states, peaks, KT, f64peak, rs1)
     roof["alone"] = {k: roof1[k] for k in ("achieved", "frac", "launch_ms")}
     for k in stream_roof:
         if stream_roof[k] and stream1.get(k):
@@ -902,11 +928,13 @@ def main():
                                        "'alone': a second repeat in which the device "
                                        "drains after every generation",
                        "restart_every": RESTART_EVERY,
-                       "streams": "one CUDA stream per algorithm's state, one "
-                                  "sevo_state_step_many call per step (operators on each "
-                                  "state's stream, one fused evaluation of all 73,728 rows, "
-                                  "selections on each stream); the timed region is forked "
-                                  "from and joined to one stream by events",
+                       "streams": f"{GROUPS} groups of 3 states (one per algorithm, "
+                                  f"{FAMILIES // GROUPS} populations each), one CUDA stream "
+                                  "per state; each step one sevo_state_step_many call per "
+                                  "group (operators on each state's stream, one fused "
+                                  "evaluation of the group's rows, selections on each "
+                                  "stream); the timed region is forked from and joined to "
+                                  "one stream by events",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,

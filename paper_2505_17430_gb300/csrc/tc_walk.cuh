@@ -50,9 +50,19 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
   acc32_init(acc);
   float zprev = 0.f;
   zfirst = 0.f;
+  // software pipeline: the next chunk's TMEM load is in flight while this
+  // chunk's bodies are computed
+  uint32_t cur[16], nxt[16];
+  if (c0 < c1) {
+    tc::tmem_ld16_issue(taddr, cur);
+    tc::tmem_wait16(cur);
+  }
   for (int col0 = c0; col0 < c1; col0 += 16) {
+    const bool more = col0 + 16 < c1;
+    if (more) tc::tmem_ld16_issue(taddr + (uint32_t)(col0 + 16 - c0), nxt);
     float v[16];
-    tc::tmem_ld16(taddr + (uint32_t)(col0 - c0), v);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(cur[k]);
     if (col0 == c0) zfirst = v[0];
     while (col0 >= gend) {  // close groups that ended before this chunk
       close(g, acc);
@@ -94,6 +104,11 @@ __device__ __forceinline__ void walk_cols(uint32_t taddr, int c0, int c1, int c,
           if (i == c1 - 1) zlast = z;
         }
       }
+    }
+    if (more) {
+      tc::tmem_wait16(nxt);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) cur[k] = nxt[k];
     }
   }
   close(g, acc);
