@@ -270,12 +270,19 @@ __global__ void __launch_bounds__(RSEL_THREADS)
   if (tid == 0) s_ncand = 0;
   unsigned long long prefix = 0ull, pmask = 0ull;
   int rem = k;  // rank (1-based) of the wanted key among the keys matching prefix
+  // loops over rows run whole warps (rows past NP inactive) so that warp-wide
+  // votes can aggregate the shared-memory atomics: fitness keys of one run
+  // share their high bytes, so per-key atomics would all hit one bin
+  const int NPw = (NP + (int)blockDim.x - 1) / (int)blockDim.x * (int)blockDim.x;
   for (int shift = 56; shift >= 0; shift -= 8) {
     for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0u;
     __syncthreads();
-    for (int i = tid; i < NP; i += blockDim.x) {
-      const unsigned long long v = uk[i];
-      if ((v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+    for (int i = tid; i < NPw; i += blockDim.x) {
+      const unsigned long long v = (i < NP) ? uk[i] : 0ull;
+      const bool act = (i < NP) && (v & pmask) == prefix;
+      const unsigned bin = act ? (unsigned)((v >> shift) & 255u) : 0xFFFFFFFFu;
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      if (act && (__ffs(same) - 1) == lane) atomicAdd(&hist[bin], (unsigned)__popc(same));
     }
     __syncthreads();
     if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7
@@ -311,11 +318,18 @@ __global__ void __launch_bounds__(RSEL_THREADS)
     rem = s_rem;
     pmask |= 255ull << shift;
   }
-  // prefix is now the k-th smallest key: gather every key <= it
-  for (int i = tid; i < NP; i += blockDim.x) {
-    const unsigned long long v = uk[i];
-    if (v <= prefix) {
-      const int slot = atomicAdd(&s_ncand, 1);
+  // prefix is now the k-th smallest key: gather every key <= it (one atomic
+  // per warp; the candidates' order does not matter, they are sorted by
+  // (key, index) below)
+  for (int i = tid; i < NPw; i += blockDim.x) {
+    const unsigned long long v = (i < NP) ? uk[i] : ~0ull;
+    const bool c = (i < NP) && v <= prefix;
+    const unsigned bal = __ballot_sync(0xffffffffu, c);
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (c) {
+      const int slot = base + __popc(bal & ((1u << lane) - 1u));
       ck[slot] = v;
       ci[slot] = i;
     }
