@@ -163,6 +163,21 @@ def run_steps(states, first_gen, n, serial=False):
     return first_gen + n
 
 
+def write_timeline(S, torch, states, gen, K, path):
+    """K steps traced launch by launch (each launch bracketed by events on
+    its stream): the spans go to path as JSON, with the step count and the
+    wall span of the K steps."""
+    torch.cuda.synchronize()
+    S.trace_enable(True, timeline=True)
+    gen = run_steps(states, gen, K)
+    torch.cuda.synchronize()
+    spans = S.trace_timeline()
+    S.trace_enable(False)
+    with open(path, "w") as f:
+        json.dump({"steps": K, "spans": spans}, f)
+    return gen
+
+
 def time_steps(torch, states, gen, K):
     """K steps between two events on the current stream: the states' streams
     start after the first event and the second waits for all of them."""
@@ -818,6 +833,9 @@ def main():
                          "(tf32|bf16x3|fp32|fp64) on one family (0-7); for profiling")
     ap.add_argument("--only-steps", action="store_true",
                     help="time the steps only (for launch-list profiling)")
+    ap.add_argument("--timeline", metavar="PATH",
+                    help="after the timed steps, trace 20 more steps launch by launch and "
+                         "write the spans (kind, stream, start ms, end ms) to PATH as JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -859,6 +877,8 @@ def main():
     ms_per_step = ms / args.steps
     value = whole_job_rate(evals_per_step, world, ms_per_step)
 
+    if args.timeline and rank == 0:
+        gen = write_timeline(S, torch, states, gen, 20, args.timeline)
     if rank != 0 or args.only_steps:
         if args.only_steps and rank == 0:
             print(json.dumps({"only_steps": True, "value": round(value, 1),

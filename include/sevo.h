@@ -479,8 +479,9 @@ enum sevo_trace_kind {
   SEVO_TK_SMALL_RUN,         /* run-per-CTA generations of small runs          */
   SEVO_TRACE_KINDS
 };
-/* on != 0: clear the accumulators and start tracing; on == 0: stop (the
- * accumulated figures stay readable).  Host-side; cheap when off. */
+/* on = 1 or 2: clear the accumulators and start tracing (2 also keeps the
+ * per-launch timeline below); on = 0: stop (the accumulated figures stay
+ * readable); SEVO_ERR_ARG for any other value.  Host-side; cheap when off. */
 int32_t sevo_trace_enable(int32_t on);
 /* Wait for every traced launch to finish and add its event-measured time to
  * the per-kind totals; counts and ms are caller arrays of SEVO_TRACE_KINDS
@@ -488,6 +489,17 @@ int32_t sevo_trace_enable(int32_t on);
 int32_t sevo_trace_read(int64_t* counts, double* ms);
 /* static name of a kind ("" if out of range) */
 const char* sevo_trace_name(int32_t kind);
+/* The timeline of tracing mode 2: every traced launch finished so far (at
+ * most 2^20) as its kind, a stream id (0, 1, ... in order of the streams'
+ * first traced launch), and its start and end in ms from the start of the
+ * first launch traced since sevo_trace_enable (event resolution, about half
+ * a microsecond; a launch on another stream may start before it, giving a
+ * negative time), sorted by start.  Waits for every traced launch.  Writes
+ * the first min(cap, total) entries into the caller's arrays (each of cap
+ * entries; may be NULL when cap is 0) and returns the total count, or
+ * SEVO_ERR_ARG / SEVO_ERR_CUDA (negative). */
+int64_t sevo_trace_timeline(int64_t cap, int32_t* kinds, int32_t* streams, double* t0,
+                            double* t1);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,7 @@ SIGNATURES = {
     "sevo_trace_enable": (C.c_int32, [C.c_int32]),
     "sevo_trace_read": (C.c_int32, [_i64p, _dp]),
     "sevo_trace_name": (C.c_char_p, [C.c_int32]),
+    "sevo_trace_timeline": (C.c_int64, [C.c_int64, _ip, _ip, _dp, _dp]),
 }
 SEVO_TRACE_KINDS = 17
 POLICY_SMALL_RUNS = 0
@@ -393,9 +394,26 @@ def sevo_run_grid(problems, algs, tasks, gens_per_graph=0, stream=None):
             "wall_ms": r.wall_ms, "evals": r.evals}
 
 
-def trace_enable(on=True):
-    """Start (clearing the totals) or stop per-kernel event tracing."""
-    check(_lib().sevo_trace_enable(1 if on else 0), "sevo_trace_enable")
+def trace_enable(on=True, timeline=False):
+    """Start (clearing the totals; timeline: also keep every launch's span)
+    or stop per-kernel event tracing."""
+    check(_lib().sevo_trace_enable((2 if timeline else 1) if on else 0), "sevo_trace_enable")
+
+
+def trace_timeline():
+    """The launches traced with timeline=True: a list of (kind name, stream
+    id, start ms, end ms), sorted by start."""
+    import numpy as np
+    n = _lib().sevo_trace_timeline(0, None, None, None, None)
+    check(n if n < 0 else 0, "sevo_trace_timeline")
+    kinds, streams = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    t0, t1 = np.zeros(n), np.zeros(n)
+    m = _lib().sevo_trace_timeline(n, kinds.ctypes.data_as(_ip), streams.ctypes.data_as(_ip),
+                                   _np_dp(t0), _np_dp(t1))
+    check(m if m < 0 else 0, "sevo_trace_timeline")
+    m = min(n, m)
+    names = [_lib().sevo_trace_name(k).decode() for k in range(SEVO_TRACE_KINDS)]
+    return [(names[kinds[i]], int(streams[i]), float(t0[i]), float(t1[i])) for i in range(m)]
 
 
 def trace_read():

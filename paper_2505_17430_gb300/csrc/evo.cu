@@ -126,8 +126,10 @@ __global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restri
   }
 }
 
+constexpr int TRIAL_THREADS = 128;
+
 template <int ALG>
-__global__ void de_trial_kernel(const double* __restrict__ X, double* __restrict__ U,
+__global__ void __launch_bounds__(TRIAL_THREADS) de_trial_kernel(const double* __restrict__ X, double* __restrict__ U,
                                 const double* __restrict__ A, const int32_t* __restrict__ asize,
                                 const int32_t* __restrict__ order, int32_t* __restrict__ part,
                                 const uint64_t* __restrict__ seeds, GenCtl* ctl, CtlSet cs,
@@ -236,11 +238,11 @@ __device__ __forceinline__ void rank_run_block(const double* __restrict__ f,
   __syncthreads();
 }
 
-// Larger populations: one CTA per run finds the k-th smallest key by an
-// MSB-first radix select (8-bit digits, shared-memory histograms), gathers
-// the rows whose key is at most that threshold (the k best plus any rows
-// tied with the k-th) and sorts only those by (key, index) with a bitonic
-// network; the first k indices are the p-best pool, identical to the
+// Larger populations: one CTA per run narrows down the k-th smallest key by
+// an MSB-first radix select (8-bit digits, shared-memory histograms), gathers
+// the rows whose key is at most the threshold it reaches (the k best plus the
+// rest of the last selected bin) and sorts only those by (key, index) with a
+// bitonic network; the first k indices are the p-best pool, identical to the
 // counting rank.
 constexpr int RSEL_THREADS = 512;
 
@@ -261,69 +263,107 @@ __global__ void __launch_bounds__(RSEL_THREADS)
   unsigned long long* ck = uk + NP;                                       // candidates
   int* ci = reinterpret_cast<int*>(ck + npow2);
   __shared__ unsigned int hist[256];
-  __shared__ unsigned long long s_prefix;
-  __shared__ int s_rem, s_ncand;
-  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  __shared__ unsigned long long s_prefix, s_lo[RSEL_THREADS / 32], s_hi[RSEL_THREADS / 32];
+  __shared__ int s_rem, s_below, s_cnt, s_ncand;
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* f = fx + (int64_t)r * NP;
-  for (int i = tid; i < NP; i += blockDim.x)
-    uk[i] = (unsigned long long)fkey(f[i]) ^ 0x8000000000000000ull;  // unsigned order
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int i = tid; i < NP; i += blockDim.x) {
+    const unsigned long long v = (unsigned long long)fkey(f[i]) ^ 0x8000000000000000ull;  // unsigned order
+    uk[i] = v;
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if (lane == 0) {
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+  }
   if (tid == 0) s_ncand = 0;
-  unsigned long long prefix = 0ull, pmask = 0ull;
-  int rem = k;  // rank (1-based) of the wanted key among the keys matching prefix
-  // loops over rows run whole warps (rows past NP inactive) so that warp-wide
-  // votes can aggregate the shared-memory atomics: fitness keys of one run
-  // share their high bytes, so per-key atomics would all hit one bin
-  const int NPw = (NP + (int)blockDim.x - 1) / (int)blockDim.x * (int)blockDim.x;
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0u;
-    __syncthreads();
-    for (int i = tid; i < NPw; i += blockDim.x) {
-      const unsigned long long v = (i < NP) ? uk[i] : 0ull;
-      const bool act = (i < NP) && (v & pmask) == prefix;
-      const unsigned bin = act ? (unsigned)((v >> shift) & 255u) : 0xFFFFFFFFu;
-      const unsigned same = __match_any_sync(0xffffffffu, bin);
-      if (act && (__ffs(same) - 1) == lane) atomicAdd(&hist[bin], (unsigned)__popc(same));
-    }
-    __syncthreads();
-    if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7
-      unsigned c[8], sum = 0u;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        c[q] = hist[lane * 8 + q];
-        sum += c[q];
+  __syncthreads();
+  lo = ~0ull;
+  hi = 0ull;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    lo = s_lo[w] < lo ? s_lo[w] : lo;
+    hi = s_hi[w] > hi ? s_hi[w] : hi;
+  }
+  // The digits above the highest bit where the smallest and largest keys
+  // differ are common to every key: the select starts at the digit holding
+  // that bit.  It stops as soon as the keys up to the selected digit's bin
+  // are few enough to be sorted directly (at most cap: the sort size that k
+  // keys need anyway); the gather below then takes every key whose digits so
+  // far are at most the selected ones.
+  const int cap = pow2_at_least(k);
+  unsigned long long thresh = lo;  // all keys equal: every key is a candidate
+  if (lo != hi) {
+    int shift = ((63 - __clzll((long long)(lo ^ hi))) >> 3) << 3;
+    unsigned long long pmask = shift == 56 ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+    unsigned long long prefix = lo & pmask;
+    int rem = k;    // rank (1-based) of the k-th key among the keys matching prefix
+    int below = 0;  // keys below the prefix's range (all among the k best)
+    for (;;) {
+      for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0u;
+      __syncthreads();
+      for (int i = tid; i < NP; i += blockDim.x) {
+        const unsigned long long v = uk[i];
+        if ((v & pmask) == prefix) atomicAdd(&hist[(unsigned)((v >> shift) & 255u)], 1u);
       }
-      unsigned incl = sum;
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const unsigned excl = incl - sum;
-      if (excl < (unsigned)rem && (unsigned)rem <= incl) {
-        unsigned acc = excl;
-        int b = lane * 8 + 7;
+      __syncthreads();
+      if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7
+        unsigned c[8], sum = 0u;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          if (acc + c[q] >= (unsigned)rem) {
-            b = lane * 8 + q;
-            break;
-          }
-          acc += c[q];
+          c[q] = hist[lane * 8 + q];
+          sum += c[q];
         }
-        s_prefix = prefix | ((unsigned long long)b << shift);
-        s_rem = rem - (int)acc;
+        unsigned incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const unsigned excl = incl - sum;
+        if (excl < (unsigned)rem && (unsigned)rem <= incl) {
+          unsigned acc = excl;
+          int b = lane * 8 + 7;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (acc + c[q] >= (unsigned)rem) {
+              b = lane * 8 + q;
+              break;
+            }
+            acc += c[q];
+          }
+          s_prefix = prefix | ((unsigned long long)b << shift);
+          s_rem = rem - (int)acc;
+          s_below = below + (int)acc;
+          s_cnt = (int)hist[b];
+        }
       }
+      __syncthreads();
+      prefix = s_prefix;
+      rem = s_rem;
+      below = s_below;
+      const int cnt = s_cnt;
+      if (shift == 0 || below + cnt <= cap) {
+        thresh = prefix | (shift == 0 ? 0ull : (1ull << shift) - 1ull);
+        break;
+      }
+      pmask |= 255ull << shift;
+      shift -= 8;
     }
-    __syncthreads();
-    prefix = s_prefix;
-    rem = s_rem;
-    pmask |= 255ull << shift;
   }
-  // prefix is now the k-th smallest key: gather every key <= it (one atomic
-  // per warp; the candidates' order does not matter, they are sorted by
-  // (key, index) below)
+  // gather every key <= thresh: the k best and the rest of the last selected
+  // bin (one atomic per warp; the candidates' order does not matter, they are
+  // sorted by (key, index) below)
+  const int NPw = (NP + (int)blockDim.x - 1) / (int)blockDim.x * (int)blockDim.x;
   for (int i = tid; i < NPw; i += blockDim.x) {
     const unsigned long long v = (i < NP) ? uk[i] : ~0ull;
-    const bool c = (i < NP) && v <= prefix;
+    const bool c = (i < NP) && v <= thresh;
     const unsigned bal = __ballot_sync(0xffffffffu, c);
     int base = 0;
     if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
@@ -1231,6 +1271,8 @@ unsigned grid_for(int64_t work, int threads) {
 
 }  // namespace
 
+#include "post.cuh"
+
 // ====================================================================== host
 static std::atomic<int> g_policy_small_runs{0};
 static std::atomic<int> g_policy_refine{1};
@@ -1341,6 +1383,9 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   if ((ctpb || shade) && rsel_smem_bytes(b->NP) > 48 * 1024)
     SV_CUDA(cudaFuncSetAttribute(de_rank_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)rsel_smem_bytes(SV_MAX_NP)));
+  if (ctpb && post_cand_bytes(pow2_at_least(b->pbest_k)) > 48 * 1024)
+    SV_CUDA(cudaFuncSetAttribute(de_post_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)post_cand_bytes(SV_MAX_NP)));
   if ((de || psode) && sel_smem_bytes(b->NP) > 48 * 1024)
     SV_CUDA(cudaFuncSetAttribute(de_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sel_smem_bytes(SV_MAX_NP)));
@@ -1479,6 +1524,7 @@ cudaError_t sv_batch_init(Batch* b) {
   cudaStream_t st = b->stream;
   const int64_t rows = (int64_t)b->R * b->NP;
   const int T = 256;
+  b->rank_fresh = false;
   const int tk3 = sv_trace_begin(SEVO_TK_INIT, st);
   init_pop_kernel<<<grid_for(rows * ((b->D + 1) / 2), T), T, 0, st>>>(b->X, b->seeds, b->R, b->NP,
                                                                      b->D, b->ld, b->lb, b->ub,
@@ -1596,6 +1642,10 @@ static cudaError_t de_trials(Batch* b, bool fused = false) {
   const int64_t rows = (int64_t)b->R * b->NP;
   const int nq = (b->D + 3) >> 2;
   const int T = 256;
+  // trial CTAs of 128 threads (about 9K registers) fit on an SM beside a
+  // resident fused-evaluation CTA, so one batch's trials run while another
+  // batch's evaluation holds the SMs
+  const int TT = TRIAL_THREADS;
   const bool shade = sv_has_shade(b->alg);
   if (shade) {
     const int tks = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
@@ -1605,7 +1655,11 @@ static cudaError_t de_trials(Batch* b, bool fused = false) {
                                                         b->kpb);
     sv_trace_end(tks, st);
   }
-  if (b->alg == SEVO_DE_CTPB || shade) {
+  // current-to-pbest: the previous generation's selection ranked the
+  // population it left (de_post_kernel) unless the host changed it since
+  const bool ranked = b->rank_fresh && !shade;
+  b->rank_fresh = false;
+  if ((b->alg == SEVO_DE_CTPB || shade) && !ranked) {
     const int tk_rank = sv_trace_begin(SEVO_TK_DE_RANK, st);
     // counting rank (O(NP^2) per run, parallel over row blocks) for small
     // populations; radix select + sort of the candidates above that
@@ -1625,19 +1679,19 @@ static cudaError_t de_trials(Batch* b, bool fused = false) {
   if (b->alg == SEVO_DE_CTPB || shade) {
     const int tk8 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     if (shade)
-      de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, T), T, 0, st>>>(
+      de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, TT), TT, 0, st>>>(
           b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
           b->NP, b->D, b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
           b->Fi, b->CRi, b->kpb);
     else
-      de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, T), T, 0, st>>>(
+      de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, TT), TT, 0, st>>>(
           b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
           b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
           make_fastdiv(b->NP), nullptr, nullptr, nullptr);
     sv_trace_end(tk8, st);
   } else {
     const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
-    de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, T), T, 0, st>>>(
+    de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, TT), TT, 0, st>>>(
         b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
         b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
         nullptr, nullptr, nullptr);
@@ -1657,6 +1711,59 @@ static cudaError_t de_select(Batch* b, int count_skip) {
       b->alg == SEVO_DE_CTPB, b->Fi, b->CRi, b->MF, b->MCR, b->mk, SEVO_SHADE_H, count_skip);
   sv_trace_end(tk10, st);
   return cudaGetLastError();
+}
+
+// cluster launch of a per-run post kernel: R clusters of post_cluster(NP) CTAs
+template <class... K, class... A>
+static cudaError_t post_launch(const Batch* b, size_t smem, void (*kern)(K...), A... args) {
+  const int C = post_cluster(b->NP);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(b->R * C));
+  cfg.blockDim = dim3(POST_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// DE/rand/1 and current-to-pbest selection in one cluster launch per batch;
+// current-to-pbest also ranks the new population for the next generation
+static bool de_post_applies(const Batch* b) {
+  return b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB;
+}
+static cudaError_t de_post(Batch* b) {
+  cudaStream_t st = b->stream;
+  const bool arch = b->alg == SEVO_DE_CTPB;
+  const int cap = arch ? pow2_at_least(b->pbest_k) : 1;
+  const int tk = sv_trace_begin(SEVO_TK_DE_SELECT, st);
+  cudaError_t e;
+  if (arch)
+    e = post_launch(b, post_cand_bytes(cap), de_post_kernel<true>, b->fx, (const double*)b->fu,
+                    b->asize, b->action, b->order, b->best, (const uint64_t*)b->seeds,
+                    (const GenCtl*)b->ctl, b->NP, b->pbest_k, cap);
+  else
+    e = post_launch(b, 0, de_post_kernel<false>, b->fx, (const double*)b->fu, (int32_t*)nullptr,
+                    b->action, (int32_t*)nullptr, b->best, (const uint64_t*)b->seeds,
+                    (const GenCtl*)b->ctl, b->NP, 0, cap);
+  sv_trace_end(tk, st);
+  b->rank_fresh = arch && e == cudaSuccess;
+  return e;
+}
+
+static cudaError_t pso_post(Batch* b) {
+  cudaStream_t st = b->stream;
+  const int tk = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
+  const cudaError_t e = post_launch(b, 0, pso_post_kernel, (const double*)b->fx, b->fp, b->action,
+                                    b->guide, b->best, (const GenCtl*)b->ctl, b->NP,
+                                    sv_topology(b->alg));
+  sv_trace_end(tk, st);
+  return e;
 }
 
 static cudaError_t de_trials_and_select(Batch* b, int count_skip) {
@@ -1717,7 +1824,7 @@ cudaError_t sv_batch_post_eval(Batch* b) {
   const int T = 256;
   cudaError_t e;
   if (sv_is_de(b->alg)) {
-    if ((e = de_select(b, 0)) != cudaSuccess) return e;
+    if ((e = de_post_applies(b) ? de_post(b) : de_select(b, 0)) != cudaSuccess) return e;
     const int tk11 = sv_trace_begin(SEVO_TK_DE_APPLY, st);
     de_apply_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->X, b->U, b->A, b->action, b->R, b->NP,
                                                          b->D, b->ld, make_fastdiv(nq),
@@ -1732,11 +1839,7 @@ cudaError_t sv_batch_post_eval(Batch* b) {
     sv_trace_end(tks, st);
     return cudaGetLastError();
   }
-  const int tk13 = sv_trace_begin(SEVO_TK_PSO_UPDATE, st);
-  pso_update_kernel<<<b->R, SEL_THREADS, (size_t)b->NP * 8, st>>>(b->fx, b->fp, b->action,
-                                                                  b->guide, b->best, b->ctl, b->NP,
-                                                                  sv_topology(b->alg), 1, 1);
-  sv_trace_end(tk13, st);
+  if ((e = pso_post(b)) != cudaSuccess) return e;
   const int tk14 = sv_trace_begin(SEVO_TK_PSO_COPY, st);
   pso_copy_kernel<<<grid_for(rows * nq, T), T, 0, st>>>(b->P, b->X, b->action, b->R, b->NP,
                                                        b->D, b->ld, make_fastdiv(nq),

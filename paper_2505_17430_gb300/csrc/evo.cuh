@@ -38,6 +38,9 @@ struct Batch {
   cudaStream_t stream;
   CtlSet pending{0ull, 0, 0};   // set by sv_ctl_defer, taken by the next generation's first kernel
   GenOp gop;                    // this generation's operator, when the evaluation applies it
+  // the p-best order was ranked from the current fitness by the last
+  // selection (current-to-pbest); cleared whenever the host changes fx
+  bool rank_fresh = false;
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,

@@ -375,6 +375,7 @@ static int32_t set_impl(sevo_state* s, const double* X, const double* fx, const 
   Batch& b = s->b;
   const size_t vb = (size_t)b.R * b.NP * 8;
   if (asize < 0 || asize > b.NP || (A && b.R != 1)) return SEVO_ERR_ARG;
+  b.rank_fresh = false;  // the p-best order is ranked again from the new fitness
   if (X) SV_CUDA(put(b.X, X, b));
   if (fx) SV_CUDA(cudaMemcpyAsync(b.fx, fx, vb, cudaMemcpyHostToDevice, b.stream));
   if (A && b.A) SV_CUDA(put(b.A, A, b));

@@ -1,6 +1,7 @@
 // trace.cu -- per-kernel device timing with CUDA events on the launching
 // stream (sevo_trace_*), and the launch accounting that every launch site
 // reports through sv_trace_end.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -11,7 +12,12 @@ namespace {
 
 struct Pending {
   cudaEvent_t a, b;
-  int kind, dev;
+  int kind, dev, stream;
+};
+
+struct Span {
+  int kind, stream;
+  double t0, t1;
 };
 
 std::mutex g_mu;
@@ -21,6 +27,14 @@ std::vector<int> g_free_tokens;  // reusable slots of g_open
 std::vector<std::pair<int, cudaEvent_t>> g_pool;  // (device, event) ready for reuse
 int64_t g_count[SEVO_TRACE_KINDS];
 double g_ms[SEVO_TRACE_KINDS];
+// timeline (tracing mode 2): every drained launch as (kind, stream, start,
+// end) in ms from the start event of the first launch traced since enable
+bool g_keep = false;
+cudaEvent_t g_origin = nullptr;
+int g_origin_dev = -1;
+std::vector<Span> g_spans;
+std::vector<cudaStream_t> g_streams;  // stream ids: order of first appearance
+constexpr size_t kMaxSpans = size_t(1) << 20;
 
 const char* const k_names[SEVO_TRACE_KINDS] = {
     "eval_tc_fused", "eval_cc", "refine", "compose", "convert", "gemm_big", "combine", "init",
@@ -53,8 +67,19 @@ cudaError_t drain_locked() {
     if (e == cudaSuccess) {
       g_count[p.kind] += 1;
       g_ms[p.kind] += ms;
+      float s0 = 0.f;
+      if (g_keep && g_origin && p.dev == g_origin_dev && g_spans.size() < kMaxSpans &&
+          (p.a == g_origin || cudaEventElapsedTime(&s0, g_origin, p.a) == cudaSuccess))
+        g_spans.push_back({p.kind, p.stream, (double)s0, (double)s0 + ms});
     } else if (first == cudaSuccess) {
       first = e;
+    }
+    if (p.a == g_origin) {
+      p.a = nullptr;  // kept as the origin until tracing restarts
+      g_pool.push_back({p.dev, p.b});
+      p.b = nullptr;
+      g_free_tokens.push_back((int)t);
+      continue;
     }
     g_pool.push_back({p.dev, p.a});
     g_pool.push_back({p.dev, p.b});
@@ -77,11 +102,24 @@ int sv_trace_begin(int kind, cudaStream_t st) {
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_open.size() - g_free_tokens.size() > 65536) drain_locked();  // bound the backlog
-  Pending p{take_event(dev), take_event(dev), kind, dev};
+  int sid = -1;
+  if (g_keep) {
+    for (size_t i = 0; i < g_streams.size() && sid < 0; ++i)
+      if (g_streams[i] == st) sid = (int)i;
+    if (sid < 0) {
+      sid = (int)g_streams.size();
+      g_streams.push_back(st);
+    }
+  }
+  Pending p{take_event(dev), take_event(dev), kind, dev, sid};
   if (!p.a || !p.b || cudaEventRecord(p.a, st) != cudaSuccess) {
     if (p.a) g_pool.push_back({dev, p.a});
     if (p.b) g_pool.push_back({dev, p.b});
     return -1;
+  }
+  if (g_keep && !g_origin) {
+    g_origin = p.a;
+    g_origin_dev = dev;
   }
   int tok;
   if (!g_free_tokens.empty()) {
@@ -111,6 +149,7 @@ void sv_trace_end(int token, cudaStream_t st) {
 }
 
 extern "C" int32_t sevo_trace_enable(int32_t on) {
+  if (on < 0 || on > 2) return SEVO_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   if (on) {
     drain_locked();
@@ -118,9 +157,31 @@ extern "C" int32_t sevo_trace_enable(int32_t on) {
       g_count[k] = 0;
       g_ms[k] = 0.0;
     }
+    if (g_origin) g_pool.push_back({g_origin_dev, g_origin});
+    g_origin = nullptr;
+    g_origin_dev = -1;
+    g_spans.clear();
+    g_streams.clear();
+    g_keep = on == 2;
   }
   g_on.store(on != 0);
   return SEVO_OK;
+}
+
+extern "C" int64_t sevo_trace_timeline(int64_t cap, int32_t* kinds, int32_t* streams, double* t0,
+                                       double* t1) {
+  if (cap < 0 || (cap > 0 && (!kinds || !streams || !t0 || !t1))) return SEVO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (drain_locked() != cudaSuccess) return SEVO_ERR_CUDA;
+  std::vector<Span> v(g_spans);
+  std::stable_sort(v.begin(), v.end(), [](const Span& x, const Span& y) { return x.t0 < y.t0; });
+  for (int64_t i = 0; i < cap && i < (int64_t)v.size(); ++i) {
+    kinds[i] = v[i].kind;
+    streams[i] = v[i].stream;
+    t0[i] = v[i].t0;
+    t1[i] = v[i].t1;
+  }
+  return (int64_t)v.size();
 }
 
 extern "C" int32_t sevo_trace_read(int64_t* counts, double* ms) {

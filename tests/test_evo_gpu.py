@@ -108,6 +108,68 @@ def test_de_ctpb_archive_lockstep(S, policy):
     assert asize == NP  # the archive filled and random eviction was exercised
 
 
+@pytest.mark.parametrize("alg,NP,fam,D", [
+    (1, 4096, 2, 10), (1, 600, 4, 17), (1, 60, 0, 8), (0, 1800, 1, 12), (0, 4096, 5, 9)])
+def test_de_free_running_selection_and_rank_bit_exact(S, alg, NP, fam, D):
+    """Generations stepped back to back with no host write in between, so that
+    each generation's p-best pool is the one the previous selection ranked in
+    its cluster launch (not a separate ranking of host-set fitness).  Before
+    every step the state is read back; the oracle, given that state and the
+    library's trial fitness, must produce the same partners and trials and the
+    same selection, fitness, archive and archive size, bit for bit (the
+    fitness values themselves are the library's, so no tolerance enters a
+    decision)."""
+    seed = 31 + NP
+    p, q, st = _state(S, fam, D, alg, NP, 10 ** 9, seed, prec=S.TF32)
+    best = st.get()["fx"].min()  # the initial population's
+    assert st.best()[0] == best
+    for gen in range(1, 9):
+        g0 = st.get()
+        A0 = np.zeros((NP, D))
+        A0[:g0["asize"]] = g0["A"]
+        assert st.de_step(gen) == 0
+        g = st.get()
+        if alg == 1:
+            U, part = O.de_ctpb_trials(seed, gen, g0["X"], g0["fx"], A0, g0["asize"])
+        else:
+            U, part = O.de_rand1_trials(seed, gen, g0["X"])
+        assert np.array_equal(g["part"], part), gen
+        assert np.array_equal(g["U"], U), gen
+        if alg == 1:
+            X2, fx2, A2, as2, _ = O.de_select(seed, gen, g0["X"], g0["fx"], U, g["fu"], A0,
+                                              g0["asize"])
+            assert g["asize"] == as2 and np.array_equal(g["A"], A2[:as2]), gen
+        else:
+            X2, fx2, _, _, _ = O.de_select(seed, gen, g0["X"], g0["fx"], U, g["fu"])
+        assert np.array_equal(g["X"], X2), gen
+        assert np.array_equal(g["fx"], fx2), gen
+        best = min(best, g["fu"].min())
+        assert st.best()[0] == best, gen
+    if alg == 1 and NP <= 600:
+        assert g["asize"] == NP  # the archive filled: random slots and overwrites ran
+
+
+@pytest.mark.parametrize("alg,NP", [(2, 4096), (3, 4096), (3, 700), (2, 50)])
+def test_pso_free_running_update_bit_exact(S, alg, NP):
+    """PSO generations back to back: from the state read before each step, the
+    oracle's move, personal-best update (with the library's fitness) and
+    guides (gbest / ring) equal the library's bit for bit."""
+    fam, D, seed = S.GRIEWANK, 11, 17 + NP
+    topo = alg - 2
+    p, q, st = _state(S, fam, D, alg, NP, 10 ** 9, seed, prec=S.TF32)
+    for gen in range(1, 7):
+        g0 = st.get()
+        guide = O.pso_guides(g0["fp"], topo)
+        assert np.array_equal(g0["part"][:, 0], guide), gen
+        assert st.pso_step(gen) == 0
+        g = st.get()
+        X2, V2 = O.pso_move(seed, gen, g0["X"], g0["V"], g0["P"], guide)
+        assert np.array_equal(g["X"], X2) and np.array_equal(g["V"], V2), gen
+        P2, fp2, _ = O.pso_update(X2, g["fx"], g0["P"], g0["fp"])
+        assert np.array_equal(g["P"], P2) and np.array_equal(g["fp"], fp2), gen
+    assert np.array_equal(st.get()["part"][:, 0], O.pso_guides(fp2, topo))
+
+
 @pytest.mark.parametrize("alg", [2, 3])
 def test_pso_lockstep(S, policy, alg):
     fam, D, NP = S.GRIEWANK, 25, 40
@@ -247,16 +309,29 @@ def test_mixed_precision_runs_reach_oracle_quality(S, policy, prec):
     assert res["success"].sum() >= sum(ref) - 2
 
 
-@pytest.mark.parametrize("NP", [600, 1800, 4096])
-def test_de_ctpb_large_population_sorted_pbest(S, NP):
+@pytest.mark.parametrize("NP,ties", [(600, "stride"), (1800, "stride"), (4096, "stride"),
+                                      (4096, "all"), (4096, "kth"), (2000, "near")])
+def test_de_ctpb_large_population_sorted_pbest(S, NP, ties):
     """NP > 512 ranks by radix select of the k-th key plus a sort of the
     candidates (ties by index); trial vectors must still match the oracle
-    bit for bit."""
+    bit for bit.  Fitness patterns: every 7th row tied with row 0; every row
+    equal (the select has nothing to split); 300 rows tied with the k-th
+    smallest value (the select runs to the last digit and the sort takes all
+    of them); values one ulp apart (the keys differ only in the low digits)."""
     fam, D = S.RASTRIGIN, 10
     p, q, st = _state(S, fam, D, S.DE_CTPB, NP, 10 ** 7, 21)
     X = O.init_population(21, NP, D)
     fx = q.eval(X)
-    fx[::7] = fx[0]  # ties, broken by index
+    if ties == "stride":
+        fx[::7] = fx[0]
+    elif ties == "all":
+        fx[:] = 123.25
+    elif ties == "kth":
+        k = max(2, int(np.ceil(0.11 * NP)))
+        kth = np.sort(fx)[k - 1]
+        fx[np.random.default_rng(5).choice(NP, 300, replace=False)] = kth
+    else:
+        fx = 1000.0 + np.random.default_rng(6).permutation(NP) * np.spacing(1000.0)
     A = np.zeros((NP, D))
     st.set(X=X, fx=fx, A=A[:0], asize=0, fes=NP)
     assert st.de_step(3) == 0
@@ -296,7 +371,8 @@ def test_batched_mixed_segments_many_jobs_per_cta(S, prec):
 def test_kernel_trace_counts_and_times(S):
     """Tracing brackets every launch outside graph capture with events on its
     stream: one DE/ctpb step traces rank, trial, evaluation, select and apply
-    launches with positive device time; a run grid (graph-captured
+    launches with positive device time (the next step needs no rank launch:
+    its selection ranked the population); a run grid (graph-captured
     generations) adds no captured launch to the totals."""
     D, NP = 30, 64
     p = S.Problem(77, S.RASTRIGIN, D)
@@ -323,7 +399,9 @@ def test_kernel_trace_counts_and_times(S):
     assert st.de_step(2) == 0
     t = S.trace_read()
     lib.sevo_set_policy(S.POLICY_FUSE_OPS, old_fuse)
-    assert t["de_trial"][0] == 0 and t["eval_tc_fused"][0] == 1 and t["de_rank"][0] == 1
+    # the first step's selection already ranked the population it left
+    assert t["de_trial"][0] == 0 and t["eval_tc_fused"][0] == 1 and t["de_rank"][0] == 0
+    assert t["de_select"][0] == 1
     S.trace_enable(True)
     lib.sevo_set_policy(S.POLICY_SMALL_RUNS, 0)
     S.sevo_run_grid([p], [S.alg_params(S.PSO_RING, 20, 20 * 40)], [(0, 0, 3)], gens_per_graph=8)
@@ -332,6 +410,38 @@ def test_kernel_trace_counts_and_times(S):
     S.trace_enable(False)
     assert t["pso_move"][0] < 39  # most generations ran inside graphs
     assert t["init"][0] == 1
+
+
+def test_trace_timeline_spans_match_totals(S):
+    """Tracing mode 2 keeps every traced launch as (kind, stream id, start,
+    end): two states on their own streams stepped together give spans on two
+    stream ids, sorted by start, each with end >= start, whose per-kind counts
+    and summed durations equal the per-kind totals; mode 1 keeps none."""
+    import torch
+    D, NP = 30, 600
+    p = S.Problem(78, S.RASTRIGIN, D)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    sts = [S.State(p, S.alg_params(alg, NP, 10 ** 6, prec=S.TF32), 5 + k, stream=s)
+           for k, (alg, s) in enumerate(zip((S.DE_RAND1, S.PSO_RING), streams))]
+    torch.cuda.synchronize()
+    S.trace_enable(True, timeline=True)
+    for g in range(1, 4):
+        assert S.sevo_state_step_many(sts, g) == 0
+    torch.cuda.synchronize()
+    spans = S.trace_timeline()
+    t = S.trace_read()
+    S.trace_enable(True)
+    assert sts[0].de_step(4) == 0
+    torch.cuda.synchronize()
+    assert S.trace_timeline() == []
+    S.trace_enable(False)
+    assert len(spans) == sum(c for c, _ in t.values()) > 0
+    assert {s for _, s, _, _ in spans} == {0, 1}
+    starts = [a for _, _, a, _ in spans]
+    assert starts == sorted(starts) and all(b >= a for _, _, a, b in spans)
+    for k, (c, ms) in t.items():
+        mine = [b - a for kk, _, a, b in spans if kk == k]
+        assert len(mine) == c and abs(sum(mine) - ms) <= 1e-3 * (1 + ms), k
 
 
 @pytest.mark.parametrize("alg", [1, 3])

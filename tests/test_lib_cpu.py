@@ -105,10 +105,14 @@ def test_trace_kinds_match_header_and_read_without_gpu():
     assert all(names) and len(set(names)) == len(names)
     assert lib.sevo_trace_name(S.SEVO_TRACE_KINDS) == b""
     assert lib.sevo_trace_name(-1) == b""
-    S.trace_enable(True)
+    S.trace_enable(True, timeline=True)
     t = S.trace_read()
+    assert S.trace_timeline() == []
     S.trace_enable(False)
     assert set(t) == set(names) and all(v == (0, 0.0) for v in t.values())
+    assert lib.sevo_trace_enable(3) == S.ERR_ARG
+    assert lib.sevo_trace_timeline(-1, None, None, None, None) == S.ERR_ARG
+    assert lib.sevo_trace_timeline(4, None, None, None, None) == S.ERR_ARG
 
 
 def test_last_cuda_error_empty_before_any_failure():
