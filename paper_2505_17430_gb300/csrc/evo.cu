@@ -18,6 +18,7 @@
 // beyond the stated fma), so trial vectors equal the oracle's bit for bit.
 // Streaming kernels move 4 consecutive coordinates per thread (one Philox
 // call covers the four crossover words).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -1261,9 +1262,13 @@ cudaError_t srk_launch(const Batch* b, int G, int advance) {
   }
 }
 
+// Grid of a grid-stride streaming kernel: at most 1024 threads per SM, so
+// that the whole grid is dispatched at once and kernels of other streams
+// queued behind it still find room on every SM (the CTA dispatcher serves
+// grids of equal priority in launch order)
 unsigned grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
-  int64_t cap = (int64_t)sv_num_sms() * 16;
+  int64_t cap = (int64_t)sv_num_sms() * std::max(1, 1024 / threads);
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;

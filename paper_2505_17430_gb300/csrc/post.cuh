@@ -42,20 +42,36 @@ __host__ __device__ inline int post_cluster(int NP) {
   return c;
 }
 
-// dynamic shared memory: the candidate buffer of the p-best sort (CTA 0):
-// cap = (k rounded up to a power of two) keys and indices
+// dynamic shared memory: every CTA's copy of the p-best candidates, cap =
+// (k rounded up to a power of two) keys and indices
 __host__ __device__ inline size_t post_cand_bytes(int cap) { return (size_t)cap * 12 + 16; }
 
+// Cross-CTA exchange is pushed, not pulled: before a cluster barrier each CTA
+// writes (or reduces with a remote atomic) its partial results into the
+// shared memory of every CTA of the cluster, so that after the barrier every
+// CTA reads them locally.  Remote stores do not stall the writer; a remote
+// load costs a round trip to another SM.
+//
+// A CTA's shared memory may be accessed remotely only once the CTA runs and
+// has initialised what others write into: each CTA arrives at a cluster
+// barrier (release) right after its initialisation and waits on it (acquire)
+// just before its first remote access, so the wait usually costs nothing.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- reductions
-// block minimum (dmin_pos) of v; the result in thread 0
+// block minimum (dmin_pos) of v, returned to every thread
 __device__ __forceinline__ double post_block_min(double v, double* red) {
   for (int m = 16; m >= 1; m >>= 1) v = dmin_pos(v, __shfl_xor_sync(0xffffffffu, v, m));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double b = red[0];
-  if (threadIdx.x == 0)
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = dmin_pos(b, red[w]);
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = dmin_pos(b, red[w]);
   __syncthreads();
   return b;
 }
@@ -87,6 +103,7 @@ __device__ __forceinline__ int post_block_scan(const unsigned char* fl, int n, i
   return woff + incl - cnt;
 }
 
+
 // ---------------------------------------------------------------- DE
 template <bool ARCHIVE>
 __global__ void __launch_bounds__(POST_THREADS)
@@ -95,18 +112,27 @@ __global__ void __launch_bounds__(POST_THREADS)
                    int32_t* __restrict__ order, double* __restrict__ best,
                    const uint64_t* __restrict__ seeds, const GenCtl* __restrict__ ctl, int NP,
                    int k, int cap) {
-  extern __shared__ __align__(16) unsigned char pc_sm[];  // CTA 0: p-best candidates
-  __shared__ double sf[POST_ROWS], sg[POST_ROWS];
-  __shared__ unsigned long long sk[POST_ROWS];
+  constexpr int HB = ARCHIVE ? 256 : 1;  // histogram bins (current-to-pbest only)
+  extern __shared__ __align__(16) unsigned char pc_sm[];  // the p-best candidates
+  __shared__ double sf[POST_ROWS];
+  __shared__ union {
+    double g[POST_ROWS];              // trial fitness (selection)
+    unsigned long long k[POST_ROWS];  // keys of the new fitness (ranking)
+  } su;
   __shared__ int owner[POST_ROWS], sact[POST_ROWS];
   __shared__ unsigned char sfl[POST_ROWS];
-  __shared__ unsigned int hist[2][256];
+  __shared__ unsigned int hloc[HB], htot[2][HB];  // this CTA's / the cluster's histogram
   __shared__ double red[POST_THREADS / 32];
   __shared__ unsigned long long klo[POST_THREADS / 32], khi[POST_THREADS / 32];
   __shared__ int wsum[POST_THREADS / 32];
-  __shared__ double s_min;
-  __shared__ unsigned long long s_lo, s_hi, s_prefix;
-  __shared__ int s_cnt, s_rem, s_below, s_bin, s_tie, s_ncand;
+  // pushed by CTA q into entry q of every CTA
+  __shared__ int x_cnt[POST_MAX_C], x_tie[POST_MAX_C];
+  __shared__ double x_min[POST_MAX_C];
+  __shared__ unsigned long long x_lo[POST_MAX_C], x_hi[POST_MAX_C];
+  __shared__ int x_nc;     // candidates in the buffer (max over CTAs of base + count)
+  __shared__ int s_alloc;  // CTA 0: buffer allocation counter
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_rem, s_below, s_bin, s_base;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), c = (int)cl.block_rank();
   const int r = (int)blockIdx.x / C;
@@ -120,32 +146,38 @@ __global__ void __launch_bounds__(POST_THREADS)
   for (int i = tid; i < n; i += blockDim.x) {
     const double a = f[i], b = g[i];
     sf[i] = a;
-    sg[i] = b;
+    su.g[i] = b;
     sfl[i] = b <= a;  // accepted
   }
   for (int i = tid; i < L; i += blockDim.x) owner[i] = -1;
-  if (tid == 0) s_ncand = 0;
+  if (ARCHIVE)
+    for (int b = tid; b < HB; b += blockDim.x) htot[0][b] = htot[1][b] = 0u;
+  if (tid == 0) {
+    x_nc = 0;
+    s_alloc = 0;
+  }
   __syncthreads();
+  cluster_arrive();  // initialised: the tables may be written remotely
   // best-so-far over the trials that count toward the budget
   double m = INFINITY;
-  for (int i = tid; i < n && i0 + i < count; i += blockDim.x) m = dmin_pos(m, sg[i]);
+  for (int i = tid; i < n && i0 + i < count; i += blockDim.x) m = dmin_pos(m, su.g[i]);
   m = post_block_min(m, red);
   int ctot;
   const int kpre = post_block_scan(sfl, n, wsum, &ctot);
-  if (tid == 0) {
-    s_min = m;
-    s_cnt = ctot;
+  cluster_wait();  // every CTA initialised
+  if (tid < C) {
+    *cl.map_shared_rank(&x_cnt[c], tid) = ctot;
+    *cl.map_shared_rank(&x_min[c], tid) = m;
   }
-  cl.sync();  // every CTA's accepted count and minimum; owner tables cleared
+  cl.sync();  // every CTA's accepted count and minimum, here
   int off = 0, tot = 0;
   for (int q = 0; q < C; ++q) {
-    const int v = *cl.map_shared_rank(&s_cnt, q);
-    if (q < c) off += v;
-    tot += v;
+    if (q < c) off += x_cnt[q];
+    tot += x_cnt[q];
   }
   if (c == 0 && tid == 0) {
     double b = best[r];
-    for (int q = 0; q < C; ++q) b = dmin_pos(b, *cl.map_shared_rank(&s_min, q));
+    for (int q = 0; q < C; ++q) b = dmin_pos(b, x_min[q]);
     best[r] = b;
   }
   // actions in row order: the accepted row of global accepted index kk
@@ -176,31 +208,35 @@ __global__ void __launch_bounds__(POST_THREADS)
       sact[i] = a;
     }
   }
-  cl.sync();  // slot owners final
+  if (ARCHIVE)
+    cl.sync();  // slot owners final (and this CTA's actions)
+  else
+    __syncthreads();  // this CTA's actions (written in row chunks, read strided)
   int32_t* act = action + (int64_t)r * NP + i0;
   for (int i = tid; i < n; i += blockDim.x) {
     int a = sact[i];
     if (ARCHIVE && a >= 0 && *cl.map_shared_rank(&owner[a % L], a / L) != i0 + i) a = -1;
     act[i] = a;
     if (a != -2) {
-      f[i] = sg[i];
-      sf[i] = sg[i];
+      f[i] = su.g[i];
+      sf[i] = su.g[i];
     }
   }
   if (ARCHIVE && c == 0 && tid == 0) asize[r] = min(NP, as0 + tot);
-  if (!ARCHIVE) return;  // no later access to another CTA's shared memory
+  if (!ARCHIVE) return;  // nothing of another CTA is read after the last barrier
 
   // ---- the k best of the new population, sorted by (fitness, index)
   // Radix select over the cluster's keys (8-bit digits, MSB first, starting
   // at the highest bit where the smallest and largest keys differ) until the
-  // keys up to the selected digit's bin fit the sort (at most cap of them);
-  // if they never do (a run of keys equal to the k-th), the candidates are
-  // the keys below the k-th one plus the first ties in row order.
+  // keys up to the selected digit's bin fit the candidate buffer (at most cap
+  // of them); if they never do (a run of keys equal to the k-th), the
+  // candidates are the keys below the k-th one plus the first ties in row
+  // order.  Every CTA then ranks a share of the candidates by counting.
   __syncthreads();
   unsigned long long lo = ~0ull, hi = 0ull;
   for (int i = tid; i < n; i += blockDim.x) {
     const unsigned long long v = (unsigned long long)fkey(sf[i]) ^ 0x8000000000000000ull;
-    sk[i] = v;
+    su.k[i] = v;
     lo = v < lo ? v : lo;
     hi = v > hi ? v : hi;
   }
@@ -215,21 +251,18 @@ __global__ void __launch_bounds__(POST_THREADS)
     khi[warp] = hi;
   }
   __syncthreads();
-  if (tid == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      lo = klo[w] < lo ? klo[w] : lo;
-      hi = khi[w] > hi ? khi[w] : hi;
-    }
-    s_lo = lo;
-    s_hi = hi;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    lo = klo[w] < lo ? klo[w] : lo;
+    hi = khi[w] > hi ? khi[w] : hi;
   }
-  cl.sync();  // every CTA's key range
-  lo = ~0ull;
-  hi = 0ull;
+  if (tid < C) {
+    *cl.map_shared_rank(&x_lo[c], tid) = lo;
+    *cl.map_shared_rank(&x_hi[c], tid) = hi;
+  }
+  cl.sync();  // every CTA's key range, here
   for (int q = 0; q < C; ++q) {
-    const unsigned long long a = *cl.map_shared_rank(&s_lo, q), b = *cl.map_shared_rank(&s_hi, q);
-    lo = a < lo ? a : lo;
-    hi = b > hi ? b : hi;
+    lo = x_lo[q] < lo ? x_lo[q] : lo;
+    hi = x_hi[q] > hi ? x_hi[q] : hi;
   }
   unsigned long long thresh = lo;
   int rem = k;
@@ -240,25 +273,28 @@ __global__ void __launch_bounds__(POST_THREADS)
     unsigned long long prefix = lo & pmask;
     int below = 0;  // keys below the prefix's range: all among the k best
     for (int pass = 0;; ++pass) {
-      unsigned int* h = hist[pass & 1];
-      for (int b = tid; b < 256; b += blockDim.x) h[b] = 0u;
+      unsigned int* ht = htot[pass & 1];
+      for (int b = tid; b < 256; b += blockDim.x) hloc[b] = 0u;
       __syncthreads();
       for (int i = tid; i < n; i += blockDim.x) {
-        const unsigned long long v = sk[i];
-        if ((v & pmask) == prefix) atomicAdd(&h[(unsigned)((v >> shift) & 255u)], 1u);
+        const unsigned long long v = su.k[i];
+        if ((v & pmask) == prefix) atomicAdd(&hloc[(unsigned)((v >> shift) & 255u)], 1u);
       }
-      cl.sync();  // every CTA's histogram of this pass
-      if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7, summed over the cluster
+      __syncthreads();
+      // add this CTA's bins into every CTA's cluster histogram of this pass
+      for (int b = tid; b < 256; b += blockDim.x) {
+        const unsigned v = hloc[b];
+        if (v)
+          for (int q = 0; q < C; ++q) atomicAdd(cl.map_shared_rank(&ht[b], q), v);
+      }
+      cl.sync();  // the cluster histogram of this pass, here
+      if (tid < 32) {  // lane owns bins 8*lane .. 8*lane+7
         unsigned cb[8], sum = 0u;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) cb[q] = 0u;
-        for (int t = 0; t < C; ++t) {
-          const unsigned int* ht = cl.map_shared_rank(h, t);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) cb[q] += ht[lane * 8 + q];
+        for (int q = 0; q < 8; ++q) {
+          cb[q] = ht[lane * 8 + q];
+          sum += cb[q];
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) sum += cb[q];
         unsigned incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
           const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -287,6 +323,9 @@ __global__ void __launch_bounds__(POST_THREADS)
       rem = s_rem;
       below = s_below;
       const int cnt = s_bin;
+      // this pass's cluster histogram is read: clear it for pass + 2 (no CTA
+      // adds into it before every CTA has passed the next pass's barrier)
+      for (int b = tid; b < 256; b += blockDim.x) ht[b] = 0u;
       if (below + cnt <= cap) {
         thresh = prefix | (shift == 0 ? 0ull : (1ull << shift) - 1ull);
         exact = false;
@@ -301,72 +340,78 @@ __global__ void __launch_bounds__(POST_THREADS)
       shift -= 8;
     }
   }
-  // gather the candidates into CTA 0's buffer (their order there does not
-  // matter: the sort orders them by (key, index))
-  unsigned long long* ck0 = cl.map_shared_rank(reinterpret_cast<unsigned long long*>(pc_sm), 0);
-  int* ci0 = cl.map_shared_rank(reinterpret_cast<int*>(pc_sm + (size_t)cap * 8), 0);
-  int* nc0 = cl.map_shared_rank(&s_ncand, 0);
+  // the candidates of this CTA, flagged
   if (!exact) {
-    for (int i = tid; i < n; i += blockDim.x) {
-      if (sk[i] <= thresh) {
-        const int s = atomicAdd(nc0, 1);
-        ck0[s] = sk[i];
-        ci0[s] = i0 + i;
-      }
-    }
+    for (int i = tid; i < n; i += blockDim.x) sfl[i] = su.k[i] <= thresh;
   } else {
     // ties with the k-th key: the first rem of them in row order
-    for (int i = tid; i < n; i += blockDim.x) sfl[i] = sk[i] == thresh;
+    for (int i = tid; i < n; i += blockDim.x) sfl[i] = su.k[i] == thresh;
     __syncthreads();
     int ttot;
     const int tpre = post_block_scan(sfl, n, wsum, &ttot);
-    if (tid == 0) s_tie = ttot;
-    cl.sync();  // every CTA's tie count
+    if (tid < C) *cl.map_shared_rank(&x_tie[c], tid) = ttot;
+    cl.sync();  // every CTA's tie count, here
     int t = tpre;
-    for (int q = 0; q < c; ++q) t += *cl.map_shared_rank(&s_tie, q);
+    for (int q = 0; q < c; ++q) t += x_tie[q];
     const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
     const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
     for (int i = j0; i < j1; ++i) {
-      const unsigned long long v = sk[i];
+      const unsigned long long v = su.k[i];
       bool take = v < thresh;
       if (v == thresh) take = t++ < rem;
-      if (take) {
-        const int s = atomicAdd(nc0, 1);
-        ck0[s] = v;
-        ci0[s] = i0 + i;
-      }
+      sfl[i] = take;
     }
-  }
-  cl.sync();  // every candidate is in CTA 0; no shared memory is read remotely after this
-  if (c != 0) return;
-  unsigned long long* ck = reinterpret_cast<unsigned long long*>(pc_sm);
-  int* ci = reinterpret_cast<int*>(pc_sm + (size_t)cap * 8);
-  const int nc = s_ncand;  // k <= nc <= cap
-  const int mm = pow2_at_least(nc);
-  for (int i = nc + tid; i < mm; i += blockDim.x) {
-    ck[i] = ~0ull;
-    ci[i] = 0x7FFFFFFF;
   }
   __syncthreads();
-  for (int size = 2; size <= mm; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = tid; t < mm / 2; t += blockDim.x) {
-        const int a = 2 * t - (t & (stride - 1)), b = a + stride;
-        const bool up = (a & size) == 0;
-        const unsigned long long ka = ck[a], kb = ck[b];
-        const int ia = ci[a], ib = ci[b];
-        const bool a_gt_b = (ka > kb) || (ka == kb && ia > ib);
-        if (a_gt_b == up) {
-          ck[a] = kb;
-          ck[b] = ka;
-          ci[a] = ib;
-          ci[b] = ia;
-        }
+  // one remote atomic reserves this CTA's block of the buffer; the
+  // candidates are written into every CTA's copy of it
+  unsigned long long* ck = reinterpret_cast<unsigned long long*>(pc_sm);
+  int* ci = reinterpret_cast<int*>(pc_sm + (size_t)cap * 8);
+  {
+    int ntake;
+    const int pre = post_block_scan(sfl, n, wsum, &ntake);
+    if (tid == 0) {
+      const int base = ntake > 0 ? atomicAdd(cl.map_shared_rank(&s_alloc, 0), ntake) : 0;
+      s_base = base;
+      for (int q = 0; q < C; ++q) atomicMax(cl.map_shared_rank(&x_nc, q), base + ntake);
+    }
+    __syncthreads();
+    int slot = s_base + pre;
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+    for (int i = j0; i < j1; ++i) {
+      if (!sfl[i] || slot >= cap) continue;  // (never past cap: the select bounds the count)
+      for (int q = 0; q < C; ++q) {
+        *cl.map_shared_rank(&ck[slot], q) = su.k[i];
+        *cl.map_shared_rank(&ci[slot], q) = i0 + i;
       }
-      __syncthreads();
+      ++slot;
     }
   }
-  for (int q = tid; q < k; q += blockDim.x) order[(int64_t)r * NP + q] = ci[q];
+  cl.sync();  // every candidate in every CTA's buffer; no remote access follows
+  // rank by counting: candidate j's position among all candidates by (key,
+  // index).  CTA c takes candidates c, c + C, c + 2C, ...; eight lanes share
+  // one candidate, four candidates per warp (the loop bound is per warp, so
+  // that every lane reaches the shuffles)
+  const int nc = min(x_nc, cap);  // k <= nc <= cap
+  const int gl = lane & 7;
+  const int nw = (int)(blockDim.x >> 5);
+  for (int mb = warp * 4; c + mb * C < nc; mb += nw * 4) {
+    const int j = c + (mb + (lane >> 3)) * C;
+    const bool valid = j < nc;
+    const unsigned long long kj = valid ? ck[j] : 0ull;
+    const int ij = valid ? ci[j] : 0;
+    int lower = 0;
+    if (valid)
+      for (int t = gl; t < nc; t += 8) {
+        const unsigned long long kt = ck[t];
+        lower += (kt < kj) || (kt == kj && ci[t] < ij);
+      }
+    lower += __shfl_xor_sync(0xffffffffu, lower, 1);
+    lower += __shfl_xor_sync(0xffffffffu, lower, 2);
+    lower += __shfl_xor_sync(0xffffffffu, lower, 4);
+    if (valid && gl == 0 && lower < k) order[(int64_t)r * NP + lower] = ij;
+  }
 }
 
 // ---------------------------------------------------------------- PSO
@@ -379,14 +424,19 @@ __global__ void __launch_bounds__(POST_THREADS)
   __shared__ double red[POST_THREADS / 32];
   __shared__ long long kbw[POST_THREADS / 32];
   __shared__ int ibw[POST_THREADS / 32];
-  __shared__ double s_min;
-  __shared__ long long s_kb;
-  __shared__ int s_ib;
+  // pushed by CTA q into entry q of every CTA
+  __shared__ double x_min[POST_MAX_C];
+  __shared__ long long x_kb[POST_MAX_C];
+  __shared__ int x_ib[POST_MAX_C];
+  // ring: personal bests of the rows just before and just after this CTA's
+  // rows (cyclically), pushed by the neighbouring CTAs
+  __shared__ double x_edge[2];
+  cluster_arrive();  // nothing to initialise: every pushed entry is overwritten
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), c = (int)cl.block_rank();
   const int r = (int)blockIdx.x / C;
   const int L = (NP + C - 1) / C;
-  const int i0 = min(NP, c * L), n = min(NP, i0 + L) - i0;
+  const int i0 = min(NP, c * L), n = min(NP, i0 + L) - i0;  // n >= 1
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = max(0, min(ctl->count, NP));
   const double* f = fx + (int64_t)r * NP + i0;
@@ -427,35 +477,38 @@ __global__ void __launch_bounds__(POST_THREADS)
     ibw[warp] = ib;
   }
   __syncthreads();
-  if (tid == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+  cluster_wait();  // every CTA runs
+  if (tid < C) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       if (kbw[w] < kb || (kbw[w] == kb && ibw[w] < ib)) {
         kb = kbw[w];
         ib = ibw[w];
       }
-    s_kb = kb;
-    s_ib = ib;
-    s_min = m;
+    *cl.map_shared_rank(&x_kb[c], tid) = kb;
+    *cl.map_shared_rank(&x_ib[c], tid) = ib;
+    *cl.map_shared_rank(&x_min[c], tid) = m;
+    if (tid == 0) {
+      *cl.map_shared_rank(&x_edge[1], (c + C - 1) % C) = sp[0];  // row i0: after CTA c-1's rows
+      *cl.map_shared_rank(&x_edge[0], (c + 1) % C) = sp[n - 1];  // row i0+n-1: before CTA c+1's
+    }
   }
-  cl.sync();  // every CTA's personal bests, minimum and best (key, index)
+  cl.sync();  // every pushed entry, here; no remote access follows
   if (c == 0 && tid == 0) {
     double b = best[r];
-    for (int q = 0; q < C; ++q) b = dmin_pos(b, *cl.map_shared_rank(&s_min, q));
+    for (int q = 0; q < C; ++q) b = dmin_pos(b, x_min[q]);
     best[r] = b;
   }
   if (topology == 0) {
     kb = 0x7FFFFFFFFFFFFFFFll;
     ib = 0x7FFFFFFF;
-    for (int q = 0; q < C; ++q) {
-      const long long k2 = *cl.map_shared_rank(&s_kb, q);
-      const int i2 = *cl.map_shared_rank(&s_ib, q);
-      if (k2 < kb || (k2 == kb && i2 < ib)) {
-        kb = k2;
-        ib = i2;
+    for (int q = 0; q < C; ++q)
+      if (x_kb[q] < kb || (x_kb[q] == kb && x_ib[q] < ib)) {
+        kb = x_kb[q];
+        ib = x_ib[q];
       }
-    }
     for (int i = tid; i < n; i += blockDim.x) gd[i] = ib;
   } else {
+    const int before = (i0 + NP - 1) % NP;  // the other row outside is (i0 + n) % NP
     for (int i = tid; i < n; i += blockDim.x) {
       const int gi = i0 + i;
       int nb[3] = {(gi + NP - 1) % NP, gi, (gi + 1) % NP};
@@ -469,16 +522,16 @@ __global__ void __launch_bounds__(POST_THREADS)
           }
       double v[3];
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
-        v[t] = (nb[t] >= i0 && nb[t] < i0 + n) ? sp[nb[t] - i0]
-                                               : *cl.map_shared_rank(&sp[nb[t] % L], nb[t] / L);
+      for (int t = 0; t < 3; ++t) {
+        const int j = nb[t];
+        v[t] = (j >= i0 && j < i0 + n) ? sp[j - i0] : (j == before ? x_edge[0] : x_edge[1]);
+      }
       int b = 0;
       for (int t = 1; t < 3; ++t)
         if (v[t] < v[b]) b = t;
       gd[i] = nb[b];
     }
   }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 }  // namespace
