@@ -178,11 +178,7 @@ __device__ __forceinline__ void convert_store(int r, const double (&x)[4], int k
   // unconditional: columns past D hold x = 0 and o = 0, so d = 0 there
   float d[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float xh, xl;
-    sv_split_hi_lo(x[q], xh, xl);
-    d[q] = (xh - ohv[q]) + (xl - olv[q]);
-  }
+  for (int q = 0; q < 4; ++q) d[q] = sv_operand_d(x[q], ohv[q], olv[q]);
   if (comp) {
     float sq = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
 #pragma unroll
@@ -256,10 +252,18 @@ __device__ __forceinline__ void make_row_quad(const GenOp& op, unsigned long lon
   }
 }
 
-// XTMA: FP64 rows are streamed by TMA (32-row quarter tiles) into a ring of
-// shared-memory buffers and converted from there; the A tile is then single
-// buffered.  Otherwise producers load rows from global memory directly.
-template <bool BF16, bool XTMA>
+// Where the A tile comes from (XM):
+//   XM_DIRECT  producers load FP64 rows from global memory and convert them
+//              (A double-buffered);
+//   XM_STAGED  FP64 rows are streamed by TMA (32-row quarter tiles) into a
+//              ring of shared-memory buffers and converted from there (A
+//              single-buffered);
+//   XM_OPERAND the operator that made the rows also wrote their converted
+//              operand (TF32, the same bits sv_operand_d gives here); the
+//              loader warp TMA-loads it straight into the 128B-swizzled A tile
+//              (double-buffered) and the producers have nothing to do.
+constexpr int XM_DIRECT = 0, XM_STAGED = 1, XM_OPERAND = 2;
+template <bool BF16, int XM>
 __global__ void __launch_bounds__(NTHREADS, 1)
     eval_tc_fused(const __grid_constant__ SegTable T, const FusedGeom geo,
                   const __grid_constant__ XMaps maps, const __grid_constant__ GenOps ops,
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // staged: [A][B][x ring]; direct: [A0][A1][B]
+  constexpr bool XTMA = XM == XM_STAGED;
   unsigned char* sA[2] = {base, XTMA ? base : base + geo.a_bytes};
   unsigned char* sB = base + (XTMA ? 1 : 2) * geo.a_bytes;
   unsigned char* sX = sB + geo.b_bytes;
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&bars.a_full[b], NPROD);
+      tc::mbar_init(&bars.a_full[b], XM == XM_OPERAND ? 1 : NPROD);
       tc::mbar_init(&bars.a_empty[b], 1);
       tc::mbar_init(&bars.t_full[b], 1);
       tc::mbar_init(&bars.t_empty[b], NEPI / 2);
@@ -407,6 +412,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else if (warp == WARP_LOAD) {
     // ------------------------------------------------------------ row loader
+    if (XM == XM_OPERAND && lane == 0) {
+      // the operand tiles: buffer j & 1, free again once job j - 2's MMAs
+      // have read it
+      JobIter it;
+      it.init(&T);
+      for (int64_t j = 0; it.valid(); ++j, it.next()) {
+        const Seg& sg = it.seg();
+        const int a = (int)(j & 1);
+        const uint32_t u = (uint32_t)(j >> 1);
+        if (!tc::mbar_wait(&bars.a_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET)) {
+          raise_abort(&bars, T);
+          break;
+        }
+        const int32_t row0 = (int32_t)(sg.row0 + (int64_t)it.local_tile() * BM);
+        tc::mbar_arrive_expect_tx(&bars.a_full[a], (uint32_t)geo.a_bytes);
+        for (int kb = 0; kb < geo.nkb; ++kb)
+          tc::tma_load_2d(sA[a] + kb * A_KB_BYTES, &maps.m[sg.xmap], &bars.a_full[a], kb * 32,
+                          row0);
+      }
+    }
     if (XTMA && lane == 0) {
       JobIter it;
       it.init(&T);
@@ -432,80 +457,103 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else if (warp >= NEPI && warp < WARP_MMA) {
     // ------------------------------------------------------------ producers
-    const int pw = warp - NEPI;
-    constexpr int RPW = BM / NPROD;  // rows per producer warp
-    const int k0 = lane * 4;         // lane owns columns k0..k0+3 (kpad <= 128)
-    const bool full4 = (k0 + 3 < D) && geo.vec_ok;
-    JobIter it;
-    it.init(&T);
-    for (int64_t j = 0; it.valid(); ++j, it.next()) {
-      const Seg& sg = it.seg();
-      const int c = it.c;
-      const bool comp = sg.comp;
-      const int a = (int)(j & 1);
-      const uint32_t u = (uint32_t)(j >> 1);
-      const int ab = XTMA ? 0 : a;
-      const uint32_t apar = XTMA ? (uint32_t)((j & 1) ^ 1) : ((u & 1u) ^ 1u);
-      if (!tc::mbar_wait(&bars.a_empty[ab], apar, &bars.abort, WAIT_BUDGET) ||
-          (comp && !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET))) {
-        if (lane == 0) raise_abort(&bars, T);
-        break;
-      }
-      const float* __restrict__ oh = sg.P->oh32[c];
-      const float* __restrict__ ol = sg.P->ol32[c];
-      float ohv[4], olv[4];
+    // (idle when the loader brings the operand: the role is compiled out)
+    if (XM != XM_OPERAND) {
+      const int pw = warp - NEPI;
+      constexpr int RPW = BM / NPROD;  // rows per producer warp
+      const int k0 = lane * 4;         // lane owns columns k0..k0+3 (kpad <= 128)
+      const bool full4 = (k0 + 3 < D) && geo.vec_ok;
+      JobIter it;
+      it.init(&T);
+      for (int64_t j = 0; it.valid(); ++j, it.next()) {
+        const Seg& sg = it.seg();
+        const int c = it.c;
+        const bool comp = sg.comp;
+        const int a = (int)(j & 1);
+        const uint32_t u = (uint32_t)(j >> 1);
+        const int ab = XTMA ? 0 : a;
+        const uint32_t apar = XTMA ? (uint32_t)((j & 1) ^ 1) : ((u & 1u) ^ 1u);
+        if (!tc::mbar_wait(&bars.a_empty[ab], apar, &bars.abort, WAIT_BUDGET) ||
+            (comp && !tc::mbar_wait(&bars.t_empty[a], (u & 1u) ^ 1u, &bars.abort, WAIT_BUDGET))) {
+          if (lane == 0) raise_abort(&bars, T);
+          break;
+        }
+        const float* __restrict__ oh = sg.P->oh32[c];
+        const float* __restrict__ ol = sg.P->ol32[c];
+        float ohv[4], olv[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int k = k0 + t;
-        ohv[t] = (k < D) ? __ldg(oh + k) : 0.f;
-        olv[t] = (k < D) ? __ldg(ol + k) : 0.f;
-      }
-      const int64_t lrow0 = (int64_t)it.local_tile() * BM;
-      unsigned char* At = sA[ab];
-      if (XTMA) {
-        // quarter-tiles of 32 rows from the staged ring: warp pw converts 4 rows
-        bool okq = true;
-        for (int h = 0; h < BM / XQ; ++h) {
-          const uint32_t qi = (uint32_t)j * (BM / XQ) + (uint32_t)h;
-          const int b = (int)(qi % (uint32_t)geo.nxb);
-          const uint32_t use = qi / (uint32_t)geo.nxb;
-          if (!tc::mbar_wait(&bars.x_full[b], use & 1u, &bars.abort, WAIT_BUDGET)) {
-            if (lane == 0) raise_abort(&bars, T);
-            okq = false;
-            break;
+        for (int t = 0; t < 4; ++t) {
+          const int k = k0 + t;
+          ohv[t] = (k < D) ? __ldg(oh + k) : 0.f;
+          olv[t] = (k < D) ? __ldg(ol + k) : 0.f;
+        }
+        const int64_t lrow0 = (int64_t)it.local_tile() * BM;
+        unsigned char* At = sA[ab];
+        if (XTMA) {
+          // quarter-tiles of 32 rows from the staged ring: warp pw converts 4 rows
+          bool okq = true;
+          for (int h = 0; h < BM / XQ; ++h) {
+            const uint32_t qi = (uint32_t)j * (BM / XQ) + (uint32_t)h;
+            const int b = (int)(qi % (uint32_t)geo.nxb);
+            const uint32_t use = qi / (uint32_t)geo.nxb;
+            if (!tc::mbar_wait(&bars.x_full[b], use & 1u, &bars.abort, WAIT_BUDGET)) {
+              if (lane == 0) raise_abort(&bars, T);
+              okq = false;
+              break;
+            }
+            const double* xs = reinterpret_cast<const double*>(sX + (size_t)b * geo.xb_bytes);
+#pragma unroll
+            for (int t = 0; t < XQ / NPROD; ++t) {
+              const int rq = pw * (XQ / NPROD) + t;  // row within the quarter
+              const int r = h * XQ + rq;             // row within the tile
+              double xv[4] = {0.0, 0.0, 0.0, 0.0};
+              if (lrow0 + r < sg.nrows) {
+                const double* xr = xs + rq * geo.dbox;
+                if (k0 + 3 < D) {
+                  const double2 p0 = *reinterpret_cast<const double2*>(xr + k0);
+                  const double2 p1 = *reinterpret_cast<const double2*>(xr + k0 + 2);
+                  xv[0] = p0.x;
+                  xv[1] = p0.y;
+                  xv[2] = p1.x;
+                  xv[3] = p1.y;
+                } else {
+#pragma unroll
+                  for (int qq = 0; qq < 4; ++qq)
+                    if (k0 + qq < D) xv[qq] = xr[k0 + qq];
+                }
+              }
+              convert_store<BF16>(r, xv, k0, D, geo, ohv, olv, comp, lane, sS[a], At);
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bars.x_empty[b]);
           }
-          const double* xs = reinterpret_cast<const double*>(sX + (size_t)b * geo.xb_bytes);
+          if (!okq) break;
+        } else if (sg.op >= 0) {
+          // rows made here: DE trials or moved particles (component 0), read
+          // back from the segment's rows by later components of a composition
+          const GenOp& op = ops.op[sg.op];
+          const unsigned long long gen = op.cs.on ? op.cs.gen : op.ctl->gen;
+          for (int rb = 0; rb < RPW; rb += 4) {
+            double xv[4][4];
 #pragma unroll
-          for (int t = 0; t < XQ / NPROD; ++t) {
-            const int rq = pw * (XQ / NPROD) + t;  // row within the quarter
-            const int r = h * XQ + rq;             // row within the tile
-            double xv[4] = {0.0, 0.0, 0.0, 0.0};
-            if (lrow0 + r < sg.nrows) {
-              const double* xr = xs + rq * geo.dbox;
-              if (k0 + 3 < D) {
-                const double2 p0 = *reinterpret_cast<const double2*>(xr + k0);
-                const double2 p1 = *reinterpret_cast<const double2*>(xr + k0 + 2);
-                xv[0] = p0.x;
-                xv[1] = p0.y;
-                xv[2] = p1.x;
-                xv[3] = p1.y;
-              } else {
+            for (int t = 0; t < 4; ++t) {
+              const int r = pw * RPW + rb + t;
+              const int64_t lr = lrow0 + r;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq)
-                  if (k0 + qq < D) xv[qq] = xr[k0 + qq];
+              for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
+              if (lr < sg.nrows && k0 < D) {
+                const int64_t row = sg.row0 + lr;
+                if (c == 0)
+                  make_row_quad(op, gen, row, lane, xv[t]);
+                else
+                  load_quad(sg.X + row * ld, k0, D, xv[t]);
               }
             }
-            convert_store<BF16>(r, xv, k0, D, geo, ohv, olv, comp, lane, sS[a], At);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              convert_store<BF16>(pw * RPW + rb + t, xv[t], k0, D, geo, ohv, olv, comp, lane, sS[a], At);
           }
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&bars.x_empty[b]);
-        }
-        if (!okq) break;
-      } else if (sg.op >= 0) {
-        // rows made here: DE trials or moved particles (component 0), read
-        // back from the segment's rows by later components of a composition
-        const GenOp& op = ops.op[sg.op];
-        const unsigned long long gen = op.cs.on ? op.cs.gen : op.ctl->gen;
+        } else
         for (int rb = 0; rb < RPW; rb += 4) {
           double xv[4][4];
 #pragma unroll
@@ -514,53 +562,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t lr = lrow0 + r;
 #pragma unroll
             for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
-            if (lr < sg.nrows && k0 < D) {
-              const int64_t row = sg.row0 + lr;
-              if (c == 0)
-                make_row_quad(op, gen, row, lane, xv[t]);
-              else
-                load_quad(sg.X + row * ld, k0, D, xv[t]);
+            if (lr < sg.nrows) {
+              const double* xr = sg.X + (sg.row0 + lr) * ld;
+              if (full4) {
+                const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
+                const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k0 + 2));
+                xv[t][0] = p0.x;
+                xv[t][1] = p0.y;
+                xv[t][2] = p1.x;
+                xv[t][3] = p1.y;
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (k0 + q < D) xv[t][q] = __ldg(xr + k0 + q);
+              }
             }
           }
 #pragma unroll
           for (int t = 0; t < 4; ++t)
             convert_store<BF16>(pw * RPW + rb + t, xv[t], k0, D, geo, ohv, olv, comp, lane, sS[a], At);
         }
-      } else
-      for (int rb = 0; rb < RPW; rb += 4) {
-        double xv[4][4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int r = pw * RPW + rb + t;
-          const int64_t lr = lrow0 + r;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) xv[t][q] = 0.0;
-          if (lr < sg.nrows) {
-            const double* xr = sg.X + (sg.row0 + lr) * ld;
-            if (full4) {
-              const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k0));
-              const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k0 + 2));
-              xv[t][0] = p0.x;
-              xv[t][1] = p0.y;
-              xv[t][2] = p1.x;
-              xv[t][3] = p1.y;
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                if (k0 + q < D) xv[t][q] = __ldg(xr + k0 + q);
-            }
-          }
+        __syncwarp();
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(&bars.a_full[XTMA ? 0 : a]);
+          if (comp) tc::mbar_arrive(&bars.s_full[a]);
         }
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          convert_store<BF16>(pw * RPW + rb + t, xv[t], k0, D, geo, ohv, olv, comp, lane, sS[a], At);
-      }
-      __syncwarp();
-      tc::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        tc::mbar_arrive(&bars.a_full[XTMA ? 0 : a]);
-        if (comp) tc::mbar_arrive(&bars.s_full[a]);
       }
     }
   } else {
@@ -681,6 +709,26 @@ bool make_x_map(CUtensorMap* m, const double* X, int D, int dbox, int64_t rows_t
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// The operators' TF32 operand of a batch: rows x D floats with a pitch of
+// `pitch` floats (a multiple of 4), box = one 128-byte K block (32 floats) x
+// BM rows, 128-byte swizzle (the layout the A tile wants); columns D..kpad-1
+// and rows past the end read as zeros
+bool sv_make_operand_map(CUtensorMap* m, const float* A, int D, int64_t rows, int pitch) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || rows <= 0 || (pitch & 3) || ((uintptr_t)A & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+  cuuint32_t box[2] = {32u, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
 FusedGeom fused_geom(const ProblemDev& h, bool bf16) {
   FusedGeom g;
   g.D = h.D;
@@ -743,10 +791,11 @@ size_t sv_eval_tc_scratch_bytes(bool any_comp, int, int64_t rows) {
 static cudaError_t set_fused_smem() {
   const int lim = 224 * 1024;  // opt-in maximum minus this kernel's static shared memory
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(eval_tc_fused<true, true>, a, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<true, false>, a, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, true>, a, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, false>, a, lim);
+  cudaError_t e = cudaFuncSetAttribute(eval_tc_fused<true, XM_STAGED>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<true, XM_DIRECT>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, XM_STAGED>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, XM_DIRECT>, a, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_tc_fused<false, XM_OPERAND>, a, lim);
   return e;
 }
 
@@ -810,8 +859,31 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
   const size_t budget = 220 * 1024;
   const size_t fixed = (size_t)g.a_bytes + g.b_bytes + 1024;
   g.nxb = (int)std::min<size_t>(MAX_XB, (budget - fixed) / (size_t)g.xb_bytes);
+  // operand mode: every segment's rows come with their converted operand,
+  // written by the operator that made them (TF32, one component, no weights)
+  int amap_of[SV_MAX_SEG];
+  const CUtensorMap* am[MAX_XMAPS];
+  int na = 0;
+  bool operand = !bf16 && ops.n == 0;
+  for (int k = 0; k < nseg && operand; ++k) {
+    const TcSegment& s = segs[k];
+    if (!s.amap || s.p->ncomp != 1 || sv_weighted_family(s.p->family)) {
+      operand = false;
+      break;
+    }
+    int m = 0;
+    while (m < na && am[m] != s.amap) ++m;
+    if (m == na) {
+      if (na == MAX_XMAPS) {
+        operand = false;
+        break;
+      }
+      am[na++] = s.amap;
+    }
+    amap_of[k] = m;
+  }
   // staged rows come from TMA loads of X, which an operator's rows do not have yet
-  bool staged = aligned && few && g.nxb >= 2 && ops.n == 0;
+  bool staged = !operand && aligned && few && g.nxb >= 2 && ops.n == 0;
   const size_t smem = staged ? fixed + (size_t)g.nxb * g.xb_bytes
                              : (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   {
@@ -837,7 +909,7 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
     d.comp = sv_weighted_family(s.p->family);
     d.ncomp = s.p->ncomp;
     d.sidx = k;
-    d.xmap = xmap_of[k];
+    d.xmap = operand ? amap_of[k] : xmap_of[k];
     d.op = op_of[k];
     d.pad = 0;
     d.stage0 = stage_rows;
@@ -859,23 +931,28 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
   const int grid = std::min(tiles, sv_num_sms());
   XMaps maps;
   std::memset(&maps, 0, sizeof(maps));
+  for (int m = 0; m < na && operand; ++m) maps.m[m] = *am[m];
   for (int m = 0; m < nx && staged; ++m)
     staged = make_x_map(&maps.m[m], xs[m], h0.D, g.dbox, xrows[m], ld);
+  const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   const int tk = sv_trace_begin(SEVO_TK_EVAL_TC_FUSED, st);
-  if (!staged) {
-    const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
+  if (operand) {
+    eval_tc_fused<false, XM_OPERAND><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld,
+                                                                          comp_g, comp_s, lo);
+  } else if (!staged) {
     if (bf16)
-      eval_tc_fused<true, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld, comp_g,
-                                                                      comp_s, lo);
+      eval_tc_fused<true, XM_DIRECT><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld,
+                                                                          comp_g, comp_s, lo);
     else
-      eval_tc_fused<false, false><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld, comp_g,
-                                                                       comp_s, lo);
+      eval_tc_fused<false, XM_DIRECT><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld,
+                                                                           comp_g, comp_s, lo);
   } else {
     if (bf16)
-      eval_tc_fused<true, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g, comp_s, lo);
+      eval_tc_fused<true, XM_STAGED><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g,
+                                                                   comp_s, lo);
     else
-      eval_tc_fused<false, true><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g, comp_s,
-                                                               lo);
+      eval_tc_fused<false, XM_STAGED><<<grid, NTHREADS, smem, st>>>(T, g, maps, ops, ld, comp_g,
+                                                                    comp_s, lo);
   }
   sv_trace_end(tk, st);
   cudaError_t e = cudaGetLastError();

@@ -127,6 +127,39 @@ __global__ void init_pop_kernel(double* __restrict__ X, const uint64_t* __restri
   }
 }
 
+// every run's o as its float hi/lo split (Osp: R rows of hi, then R rows of
+// lo, apitch floats each, zero past D), gathered once so that the operators
+// read it with one load per value
+__global__ void gather_osplit_kernel(const ProblemDev* const* __restrict__ rp, int R, int D,
+                                     int apitch, float* __restrict__ Osp) {
+  const int64_t total = (int64_t)2 * R * apitch;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rr = t / apitch;
+    const int j = (int)(t - rr * apitch);
+    const int r = (int)(rr < R ? rr : rr - R);
+    const float* src = rr < R ? rp[r]->oh32[0] : rp[r]->ol32[0];
+    Osp[t] = j < D ? src[j] : 0.f;
+  }
+}
+
+// the TF32 operand of trial quad j0..j0+3 of run r's batch row `row` (one
+// component) for the fused evaluation, which then loads it instead of
+// converting the row (the same function, hence the same bits, either way);
+// columns past D hold 0 and are never read
+__device__ __forceinline__ void write_operand4(float* __restrict__ Ad, int apitch,
+                                               const float* __restrict__ Osp, int R, int r,
+                                               int64_t row, int j0, int D, const double (&u)[4]) {
+  const float4 oh = __ldg(reinterpret_cast<const float4*>(Osp + (int64_t)r * apitch + j0));
+  const float4 ol = __ldg(reinterpret_cast<const float4*>(Osp + (int64_t)(R + r) * apitch + j0));
+  const float ohv[4] = {oh.x, oh.y, oh.z, oh.w}, olv[4] = {ol.x, ol.y, ol.z, ol.w};
+  float d[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    d[q] = (j0 + q < D) ? tc::to_tf32(sv_operand_d(u[q], ohv[q], olv[q])) : 0.f;
+  *reinterpret_cast<float4*>(Ad + row * apitch + j0) = make_float4(d[0], d[1], d[2], d[3]);
+}
+
 constexpr int TRIAL_THREADS = 128;
 
 template <int ALG>
@@ -137,7 +170,8 @@ __global__ void __launch_bounds__(TRIAL_THREADS) de_trial_kernel(const double* _
                                 int R, int NP, int D, int ld, double F, unsigned long long cr_thr,
                                 double lb, double ub, int pk, FastDiv fq, FastDiv fnp,
                                 const double* __restrict__ Fi, const double* __restrict__ CRi,
-                                const int32_t* __restrict__ kpb) {
+                                const int32_t* __restrict__ kpb, float* __restrict__ Ad,
+                                int apitch, const float* __restrict__ Osp) {
   const int nq = (D + 3) >> 2;
   const int64_t total = (int64_t)R * NP * nq;
   const bool fast = total < (1ll << 31);
@@ -145,8 +179,10 @@ __global__ void __launch_bounds__(TRIAL_THREADS) de_trial_kernel(const double* _
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fq, fnp);
+    double uq[4];
     de_trial_elem<ALG>(X, U, A, asize, order, part, seeds, NP, D, ld, F, cr_thr, lb, ub, pk, gen,
-                       sp.hi, sp.mid, sp.lo, Fi, CRi, kpb);
+                       sp.hi, sp.mid, sp.lo, Fi, CRi, kpb, Ad ? uq : nullptr);
+    if (Ad) write_operand4(Ad, apitch, Osp, R, sp.hi, sp.row, sp.lo * 4, D, uq);
   }
 }
 
@@ -745,15 +781,26 @@ __global__ void pso_move_kernel(double* __restrict__ X, double* __restrict__ V,
                                 const double* __restrict__ P, const int32_t* __restrict__ guide,
                                 const uint64_t* __restrict__ seeds, GenCtl* ctl, CtlSet cs,
                                 int R, int NP, int D, int ld, double w, double c1, double c2,
-                                double lb, double ub, FastDiv fd, FastDiv fnp) {
+                                double lb, double ub, FastDiv fd, FastDiv fnp,
+                                float* __restrict__ Ad, int apitch,
+                                const float* __restrict__ Osp) {
   const int64_t total = (int64_t)R * NP * D;
   const bool fast = total < (1ll << 31);
   const unsigned long long gen = gen_of(ctl, cs);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const Split3 sp = split3(t, fast, fd, fnp);
-    pso_move_elem(X, V, P, guide, seeds, gen, NP, ld, w, c1, c2, lb, ub, sp.hi, sp.mid, sp.lo,
-                  sp.row);
+    const int64_t e = sp.row * ld + sp.lo;
+    double v;
+    const double xn = pso_moved(X, V, P, guide, seeds, gen, NP, ld, w, c1, c2, lb, ub, sp.hi,
+                                sp.mid, sp.lo, sp.row, e, &v);
+    X[e] = xn;
+    V[e] = v;
+    if (Ad) {
+      const int64_t o = (int64_t)sp.hi * apitch + sp.lo;
+      Ad[sp.row * apitch + sp.lo] = tc::to_tf32(
+          sv_operand_d(xn, __ldg(Osp + o), __ldg(Osp + o + (int64_t)R * apitch)));
+    }
   }
 }
 
@@ -1464,13 +1511,40 @@ int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
   b->any_comp = any_comp;
   b->eval_bytes = sv_eval_scratch_bytes(b->D, any_comp, b->prec, rows);
   SV_CUDA(cudaMalloc(&b->eval_block, b->eval_bytes));
+  // the operators hand the evaluation its TF32 operand when every problem has
+  // one component (the operand is d = x - o of that component)
+  bool single = true;
+  for (const sevo_problem* q : probs) single = single && q->ncomp == 1 && !sv_weighted_family(q->family);
+  const bool makes_rows = b->alg == SEVO_DE_RAND1 || b->alg == SEVO_DE_CTPB ||
+                          b->alg == SEVO_DE_SHADE || b->alg == SEVO_PSO_GBEST ||
+                          b->alg == SEVO_PSO_RING;
+  b->Ad = nullptr;
+  b->Osp = nullptr;
+  if (b->prec == SEVO_TF32 && b->D <= 128 && single && makes_rows && !b->small) {
+    b->apitch = (b->D + 3) & ~3;
+    const size_t osp = (size_t)2 * b->R * b->apitch;
+    SV_CUDA(cudaMalloc(&b->Ad, (size_t)rows * b->apitch * 4 + osp * 4));
+    b->Osp = b->Ad + (size_t)rows * b->apitch;
+    if (!sv_make_operand_map(&b->amap, b->Ad, b->D, rows, b->apitch)) {
+      cudaFree(b->Ad);
+      b->Ad = nullptr;
+      b->Osp = nullptr;
+    } else {
+      gather_osplit_kernel<<<grid_for((int64_t)osp, 256), 256, 0, st>>>(b->rp, b->R, b->D,
+                                                                       b->apitch, b->Osp);
+      sv_note_launch();
+      SV_CUDA(cudaGetLastError());
+    }
+  }
   return SEVO_OK;
 }
 
 void sv_batch_free(Batch* b) {
   if (b->block) cudaFree(b->block);
   if (b->eval_block) cudaFree(b->eval_block);
+  if (b->Ad) cudaFree(b->Ad);
   b->block = b->eval_block = nullptr;
+  b->Ad = nullptr;
 }
 
 // evaluate every row of `M` (X or U) into `f`: one pass over the batch's
@@ -1485,14 +1559,15 @@ void sv_batch_segments(const Batch* b, const EvalReq& q, std::vector<TcSegment>*
     t.err = b->err;
     t.refined = b->refined;
     t.op = q.op;
+    t.amap = q.amap;
     segs->push_back(t);
   }
 }
 
 static cudaError_t eval_rows(Batch* b, const double* M, double* f, int rpr = -1,
-                             const GenOp* op = nullptr) {
+                             const GenOp* op = nullptr, const CUtensorMap* amap = nullptr) {
   std::vector<TcSegment> segs;
-  sv_batch_segments(b, EvalReq{M, f, rpr < 0 ? b->NP : rpr, op}, &segs);
+  sv_batch_segments(b, EvalReq{M, f, rpr < 0 ? b->NP : rpr, op, amap}, &segs);
   EvalScratch sc;
   sv_eval_scratch_carve(b->eval_block, b->D, b->any_comp, b->prec, (int64_t)b->R * b->NP, &sc);
   sc.err = b->err;
@@ -1687,19 +1762,19 @@ static cudaError_t de_trials(Batch* b, bool fused = false) {
       de_trial_kernel<SEVO_DE_SHADE><<<grid_for(rows * nq, TT), TT, 0, st>>>(
           b->X, b->U, nullptr, nullptr, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
           b->NP, b->D, b->ld, 0.0, 0ull, b->lb, b->ub, b->pbest_k, make_fastdiv(nq), make_fastdiv(b->NP),
-          b->Fi, b->CRi, b->kpb);
+          b->Fi, b->CRi, b->kpb, b->Ad, b->apitch, b->Osp);
     else
       de_trial_kernel<SEVO_DE_CTPB><<<grid_for(rows * nq, TT), TT, 0, st>>>(
           b->X, b->U, b->A, b->asize, b->order, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
           b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, b->pbest_k, make_fastdiv(nq),
-          make_fastdiv(b->NP), nullptr, nullptr, nullptr);
+          make_fastdiv(b->NP), nullptr, nullptr, nullptr, b->Ad, b->apitch, b->Osp);
     sv_trace_end(tk8, st);
   } else {
     const int tk9 = sv_trace_begin(SEVO_TK_DE_TRIAL, st);
     de_trial_kernel<SEVO_DE_RAND1><<<grid_for(rows * nq, TT), TT, 0, st>>>(
         b->X, b->U, nullptr, nullptr, nullptr, b->part, b->seeds, b->ctl, take_ctl(b), b->R,
         b->NP, b->D, b->ld, b->F, b->cr_thr, b->lb, b->ub, 0, make_fastdiv(nq), make_fastdiv(b->NP),
-        nullptr, nullptr, nullptr);
+        nullptr, nullptr, nullptr, b->Ad, b->apitch, b->Osp);
     sv_trace_end(tk9, st);
   }
   return cudaGetLastError();
@@ -1786,7 +1861,8 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
   const int T = 256;
   const bool fused = fusable(b);
   if (sv_is_de(b->alg)) {
-    *q = EvalReq{b->U, b->fu, b->NP, fused ? &b->gop : nullptr};
+    *q = EvalReq{b->U, b->fu, b->NP, fused ? &b->gop : nullptr,
+                 (b->Ad && !fused) ? &b->amap : nullptr};
     return de_trials(b, fused);
   }
   if (b->alg == SEVO_CSO) {
@@ -1816,9 +1892,10 @@ cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q) {
   pso_move_kernel<<<grid_for(rows * b->D, T), T, 0, st>>>(b->X, b->V, b->P, b->guide, b->seeds,
                                                          b->ctl, take_ctl(b), b->R, b->NP, b->D, b->ld, b->w,
                                                          b->c1, b->c2, b->lb, b->ub,
-                                                         make_fastdiv(b->D), make_fastdiv(b->NP));
+                                                         make_fastdiv(b->D), make_fastdiv(b->NP),
+                                                         b->Ad, b->apitch, b->Osp);
   sv_trace_end(tk12, st);
-  *q = EvalReq{b->X, b->fx, b->NP, nullptr};
+  *q = EvalReq{b->X, b->fx, b->NP, nullptr, b->Ad ? &b->amap : nullptr};
   return cudaGetLastError();
 }
 
@@ -1904,7 +1981,7 @@ cudaError_t sv_batch_generation(Batch* b) {
   EvalReq q;
   cudaError_t e;
   if ((e = sv_batch_pre_eval(b, &q)) != cudaSuccess) return e;
-  if ((e = eval_rows(b, q.M, q.f, q.rpr, q.op)) != cudaSuccess) return e;
+  if ((e = eval_rows(b, q.M, q.f, q.rpr, q.op, q.amap)) != cudaSuccess) return e;
   return sv_batch_post_eval(b);
 }
 

@@ -41,6 +41,15 @@ struct Batch {
   // the p-best order was ranked from the current fitness by the last
   // selection (current-to-pbest); cleared whenever the host changes fx
   bool rank_fresh = false;
+  // the operators' TF32 operand of the rows they make (d = x - o, R*NP rows
+  // of apitch floats) and its tensor map, for the fused tensor-core
+  // evaluation (TF32, D <= 128, single-component problems); null otherwise
+  float* Ad = nullptr;
+  int apitch = 0;
+  CUtensorMap amap;
+  // o of every run's problem as its float hi/lo split, R x apitch each (hi
+  // rows, then lo rows), zero past D: read by the operators that write Ad
+  float* Osp = nullptr;
 };
 
 int32_t sv_batch_alloc(Batch* b, const std::vector<const sevo_problem*>& probs,
@@ -61,6 +70,7 @@ struct EvalReq {
   double* f;
   int rpr;
   const GenOp* op;  // the operator the evaluation applies first (fused path), or null
+  const CUtensorMap* amap = nullptr;  // the rows' operand, written by their operator
 };
 bool sv_batch_splittable(const Batch* b);
 cudaError_t sv_batch_pre_eval(Batch* b, EvalReq* q);

@@ -70,7 +70,14 @@ struct TcSegment {
   uint32_t* err = nullptr;
   unsigned long long* refined = nullptr;
   const GenOp* op = nullptr;  // rows made by this operator (fused tensor-core path only)
+  // the rows' TF32 operand (d = x - o), written by the operator that made
+  // them, as a tensor map over the batch's operand buffer (null: convert here)
+  const CUtensorMap* amap = nullptr;
 };
+
+// tensor map over an operand buffer (rows x D floats, pitch a multiple of 4)
+// as the fused evaluation's loader wants it; false if it cannot be built
+bool sv_make_operand_map(CUtensorMap* m, const float* A, int D, int64_t rows, int pitch);
 
 // per-segment refinement sub-lists: segment s lists its rows (row indices of
 // its own X / out) in list[list_off[s] ...] with count[s] entries

@@ -158,7 +158,7 @@ __host__ __device__ __forceinline__ void sv_split_hi_lo(double x, float& hi, flo
   const uint32_t sb = (uint32_t)(e - 948) << 23;  // 2^(e - 1075) as float bits
 #ifdef __CUDA_ARCH__
   const float hv = __uint_as_float(hb);
-  const float v = __uint2float_rn(r) * __uint_as_float(sb);
+  const float v = __fmul_rn(__uint2float_rn(r), __uint_as_float(sb));
 #else
   float hv, scl;
   __builtin_memcpy(&hv, &hb, 4);
@@ -168,6 +168,19 @@ __host__ __device__ __forceinline__ void sv_split_hi_lo(double x, float& hi, flo
   hi = ok ? hv : 0.f;
   lo = ok ? (sign ? -v : v) : 0.f;
 }
+
+#ifdef __CUDACC__
+// One coordinate of the tensor-core operand: d = x - o, formed from the
+// float hi/lo splits of x and of o (oh, ol) as (xh - oh) + (xl - ol) in
+// round-to-nearest FP32 (no contraction).  The fused evaluation's producers
+// and the operators that hand their rows to it both call this, so the operand
+// has the same bits whichever forms it.
+__device__ __forceinline__ float sv_operand_d(double x, float oh, float ol) {
+  float xh, xl;
+  sv_split_hi_lo(x, xh, xl);
+  return __fadd_rn(__fsub_rn(xh, oh), __fsub_rn(xl, ol));
+}
+#endif
 
 // status helpers --------------------------------------------------------
 #define SV_CUDA(call)                                     \

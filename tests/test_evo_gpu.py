@@ -149,6 +149,33 @@ def test_de_free_running_selection_and_rank_bit_exact(S, alg, NP, fam, D):
         assert g["asize"] == NP  # the archive filled: random slots and overwrites ran
 
 
+@pytest.mark.parametrize("alg", [0, 1, 4, 2, 3])
+@pytest.mark.parametrize("fam", [2, 6, 7])
+def test_operand_handoff_equals_converting_evaluation(S, alg, fam):
+    """With TF32 and one-component problems the DE trial and PSO move kernels
+    also write the rows' tensor-core operand, and the fused evaluation loads
+    it instead of converting the rows.  The generation's fitness must equal,
+    bit for bit, a plain TF32 sevo_evaluate of the same rows (which converts
+    them); a composition (no hand-off) must match too.  Two runs on two
+    problems check the per-run offsets of the operand buffer."""
+    import torch
+    D, NP = 37, 300
+    probs = [S.Problem(900 + fam, fam, D), S.Problem(901 + fam, fam, D)]
+    st = S.State(probs, S.alg_params(alg, NP, 10 ** 9, prec=S.TF32), [5, 6])
+    for gen in (1, 2):
+        if alg in (2, 3):
+            assert st.pso_step(gen) == 0
+        else:
+            assert st.de_step(gen) == 0
+        g = st.get()
+        rows, fit = (g["X"], g["fx"]) if alg in (2, 3) else (g["U"], g["fu"])
+        for r, p in enumerate(probs):
+            Xr = torch.tensor(rows[r * NP:(r + 1) * NP], dtype=torch.float64, device="cuda")
+            ref = p.evaluate(Xr, prec=S.TF32).cpu().numpy()
+            got = fit[r * NP:(r + 1) * NP]
+            assert np.array_equal(got.view(np.int64), ref.view(np.int64)), (gen, r)
+
+
 @pytest.mark.parametrize("alg,NP", [(2, 4096), (3, 4096), (3, 700), (2, 50)])
 def test_pso_free_running_update_bit_exact(S, alg, NP):
     """PSO generations back to back: from the state read before each step, the
