@@ -252,7 +252,7 @@ def rooflines(trace, states, peaks, K, fp64=None, restarts=0):
     total_ms = sum(ms for _, ms in trace.values())
     step_rows = sum(st.R * NP for st in states)
 
-    def entry(kind, bytes_per_row, bound="hbm"):
+    def entry(kind, bytes_per_row, bound="hbm", restart_bytes_per_row=None):
         n, ms = trace.get(kind, (0, 0.0))
         if not n:
             return None
@@ -260,6 +260,9 @@ def rooflines(trace, states, peaks, K, fp64=None, restarts=0):
         rows = (step_rows * (K + restarts) // n if kind == "eval_tc_fused"
                 else states[0].R * NP)
         algo = rows * bytes_per_row
+        if restart_bytes_per_row is not None:  # the restarts' evaluations read FP64 rows
+            algo = (step_rows * K * bytes_per_row +
+                    step_rows * restarts * restart_bytes_per_row) // n
         ach = algo / (per * 1e-3) / 1e9
         return {"kernel": kind, "bound": bound, "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4) if peak else None,
@@ -267,13 +270,18 @@ def rooflines(trace, states, peaks, K, fp64=None, restarts=0):
                 "algorithmic_bytes_per_launch": algo, "launch_ms": round(per, 4),
                 "launches": n, "share_of_step": round(ms / total_ms, 4), "peak_source": src}
 
-    main = entry("eval_tc_fused", D * 8 + 8)
+    # the fused evaluation of a generation reads the TF32 operand its rows'
+    # operator wrote (4 B per coordinate) and writes the fitness; evaluations
+    # of fresh populations (restarts) read the FP64 rows instead
+    main = entry("eval_tc_fused", D * 4 + 8, restart_bytes_per_row=D * 8 + 8)
     per_row = profiled_traffic("eval_tc_fused_tf32_d100.md", FUSED_SOURCES)
     main["traffic"] = round(per_row * main["rows_per_launch"]) if per_row else None
     # DE trial: target + three donors read, trial written (FP64 rows) + 16 B
     # of partner indices; PSO move: x, v, pbest read, x, v written (the guide
-    # row is one per run or neighbourhood and is served from L2)
-    stream = {k: entry(k, b) for k, b in (("de_trial", 5 * 8 * D + 16), ("pso_move", 5 * 8 * D))}
+    # row is one per run or neighbourhood and is served from L2); both also
+    # write the rows' TF32 operand for the evaluation (4 B per coordinate)
+    stream = {k: entry(k, b) for k, b in (("de_trial", 5 * 8 * D + 16 + 4 * D),
+                                            ("pso_move", 5 * 8 * D + 4 * D))}
     # the FP64 pipe, which binds both: the formula's FP64 operations per
     # coordinate (DE/rand/1 2, current-to-pbest 4 -- one launch of each per
     # step -- and the PSO move 8) against the DGEMM rate measured here

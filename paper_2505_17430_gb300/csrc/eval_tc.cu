@@ -36,6 +36,7 @@ constexpr int NEPI = 8, NPROD = 8;
 constexpr int WARP_MMA = NEPI + NPROD;
 constexpr int WARP_LOAD = NEPI + NPROD + 1;    // TMA loader of FP64 rows (staged mode)
 constexpr int NTHREADS = (NEPI + NPROD + 2) * 32;
+constexpr int NTHREADS_OPERAND = (NEPI + 2) * 32;  // epilogue, MMA and loader warps only
 constexpr int XQ = 32;                        // rows per staged quarter-tile
 constexpr int MAX_XB = 4;                     // staged row buffers (ring)
 constexpr long long WAIT_BUDGET = 4000000000LL;  // ~2 s of clock64
@@ -280,6 +281,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   unsigned char* sB = base + (XTMA ? 1 : 2) * geo.a_bytes;
   unsigned char* sX = sB + geo.b_bytes;
 
+  // roles: operand mode has no producer warps, and launches without them
+  constexpr int W_MMA = XM == XM_OPERAND ? NEPI : WARP_MMA;
+  constexpr int W_LOAD = W_MMA + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     if (bars.abort) return;
   }
-  if (warp == WARP_MMA) {
+  if (warp == W_MMA) {
     tc::tmem_alloc(&bars.tmem_base, 2 * TCOLS);
     tc::tmem_relinquish();
   }
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = bars.tmem_base;
   const int D = geo.D;
 
-  if (warp == WARP_MMA) {
+  if (warp == W_MMA) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
       JobIter it;
@@ -410,7 +414,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp == WARP_LOAD) {
+  } else if (warp == W_LOAD) {
     // ------------------------------------------------------------ row loader
     if (XM == XM_OPERAND && lane == 0) {
       // the operand tiles: buffer j & 1, free again once job j - 2's MMAs
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp >= NEPI && warp < WARP_MMA) {
+  } else if (warp >= NEPI && warp < W_MMA) {
     // ------------------------------------------------------------ producers
     // (idle when the loader brings the operand: the role is compiled out)
     if (XM != XM_OPERAND) {
@@ -636,7 +640,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == WARP_MMA) {
+  if (warp == W_MMA) {
     if (bars.abort) {  // let any MMA still in flight finish before freeing TMEM
       for (int k = 0; k < 1000; ++k) __nanosleep(1000);
     }
@@ -937,7 +941,7 @@ cudaError_t sv_eval_tc_segments(const TcSegment* segs, int nseg, int prec, int64
   const size_t smem_direct = (size_t)2 * g.a_bytes + g.b_bytes + 1024;
   const int tk = sv_trace_begin(SEVO_TK_EVAL_TC_FUSED, st);
   if (operand) {
-    eval_tc_fused<false, XM_OPERAND><<<grid, NTHREADS, smem_direct, st>>>(T, g, maps, ops, ld,
+    eval_tc_fused<false, XM_OPERAND><<<grid, NTHREADS_OPERAND, smem_direct, st>>>(T, g, maps, ops, ld,
                                                                           comp_g, comp_s, lo);
   } else if (!staged) {
     if (bf16)
