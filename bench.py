@@ -302,6 +302,30 @@ def rooflines(trace, states, peaks, K, fp64=None, restarts=0):
     return main, stream, shares
 
 
+STREAM_SOURCES = ("evo.cu", "ops.cuh", "bounds.cuh", "sevo_internal.cuh", "u53.cuh")
+
+
+def dominant_roofline(shares, eval_roof, stream_roof):
+    """The roofline of the kernel with the largest measured share of the step's
+    device time among the fused evaluation, the DE trials and the PSO move:
+    the evaluation against HBM, the operators against the FP64 rate that binds
+    them (bound "alu"; their HBM figures kept under "hbm")."""
+    cands = {k: shares.get(k, {}).get("ms", 0.0) for k in ("eval_tc_fused", "de_trial", "pso_move")}
+    k = max(cands, key=cands.get)
+    if k == "eval_tc_fused" or not (stream_roof.get(k) or {}).get("fp64_pipe"):
+        return eval_roof
+    r, f = stream_roof[k], stream_roof[k]["fp64_pipe"]
+    per_row = profiled_traffic("streaming_fp64_de_trial_pso_move_d100.md", STREAM_SOURCES)
+    return {"kernel": k, "bound": "alu", "achieved": f["achieved"], "peak": f["peak"],
+            "unit": "FP64 op/s", "frac": f["frac"], "ops_per_coordinate": f["ops_per_coordinate"],
+            "rows_per_launch": r["rows_per_launch"], "launch_ms": r["launch_ms"],
+            "launches": r["launches"], "share_of_step": r["share_of_step"],
+            "peak_source": f["peak_source"],
+            "traffic": round(per_row * r["rows_per_launch"]) if per_row else None,
+            "hbm": {"achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s", "frac": r["frac"],
+                    "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}}
+
+
 def mode_eval_rates(S, torch, probs):
     """Evaluation-only throughput per precision mode on the step's rows."""
     rows = FAMILIES * NP
@@ -914,6 +938,10 @@ def main():
             stream_roof[k]["alone"] = {q: stream1[k][q] for q in ("achieved", "frac", "launch_ms")}
             if stream1[k].get("fp64_pipe"):
                 stream_roof[k]["alone"]["fp64_frac"] = stream1[k]["fp64_pipe"]["frac"]
+    dom = dominant_roofline(shares, roof, stream_roof)
+    if dom is not roof and stream_roof[dom["kernel"]].get("alone"):
+        a = stream_roof[dom["kernel"]]["alone"]
+        dom["alone"] = {"frac": a.get("fp64_frac"), "launch_ms": a["launch_ms"]}
     e2e, gen = e2e_rate(S, torch, states, gen, max(3, min(args.steps // 4, 400)))
     modes = mode_eval_rates(S, torch, probs)
     large = None if args.no_large_d else large_d_rates(S, torch, peaks)
@@ -964,7 +992,7 @@ def main():
                                   "stream); the timed region is forked from and joined to "
                                   "one stream by events",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": dom, "eval_roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_path": fp64, "streaming_rooflines": stream_roof,
             "kernel_shares": shares, "kernel_shares_alone": shares1,
             "eval_only_evals_per_s": modes, "large_d": large,
