@@ -176,8 +176,12 @@ int32_t sevo_evaluate_sync(const sevo_problem* p, const double* pop, int64_t N, 
  *   - the problem must already have its device copy on the current device
  *     (any earlier sevo_evaluate / sevo_state_create call with it makes it),
  *     else SEVO_ERR_STATE -- making that copy would allocate;
- *   - the first call on a device looks up the array's device address once
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call looks up the array's device address in the current
+ *     context (cudaGetSymbolAddress, which allocates nothing and is legal
+ *     during stream capture once the library's module is loaded: make one
+ *     call of any kind on the device before capturing); after a device reset
+ *     every library object (problems, states) is invalid and must be made
+ *     again, as for any CUDA allocation;
  *   - every call shares the one array and the array keeps the last call's
  *     contents (the counters are cleared on the stream by each call): calls
  *     whose work overlaps on the GPU (different streams, or different host

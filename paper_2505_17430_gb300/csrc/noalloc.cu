@@ -1,34 +1,24 @@
 // noalloc.cu -- sevo_evaluate_noalloc: sevo_evaluate with its scratch in one
 // fixed device array instead of a stream-ordered allocation, for callers
 // that cannot allocate device memory at the point of the call.
-#include <mutex>
-
 #include "kernels.cuh"
 
 // one array per device that loads the library (held until process exit)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SEVO_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// the array's device address on the current device, looked up once per
-// device with that device current (host code cannot use the symbol itself)
+// the array's device address in the current context, looked up on every
+// call (host code cannot use the symbol itself; the lookup allocates nothing,
+// and an address kept from an earlier context would be stale after a device
+// reset)
 int32_t scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SEVO_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      sv_set_last_cuda_error(e);
-      return SEVO_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    sv_set_last_cuda_error(e);
+    return SEVO_ERR_CUDA;
   }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return SEVO_OK;
 }
 }  // namespace
