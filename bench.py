@@ -198,11 +198,17 @@ def time_steps(torch, states, gen, K):
 
 
 def _source_hash(files):
+    """Hash of the kernels' code: comments and whitespace are left out, so
+    that a change to a comment does not retire a profile of the same code."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2505_17430_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2505_17430_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -16,7 +16,13 @@
 //               written as the 128B-swizzled K-major A tile;
 //   warp 16     TMA loads of the rotation (B operand, reloaded only when the
 //               problem or component changes), tcgen05.mma into the job's
-//               TMEM buffer, TMEM allocation.
+//               TMEM buffer, TMEM allocation;
+//   warp 17     row loader: TMA of the FP64 rows into a shared ring when the
+//               producers convert from shared memory (idle otherwise).
+// When the operator that made the rows (a DE trial, a PSO move) already wrote
+// their TF32 d = x - o, the producer warps are not launched: warp 8 issues the
+// MMAs and warp 9 TMA-loads the A tile straight from that operand (320 threads
+// in all).  The three ways of filling A are listed above eval_tc_fused.
 // BF16X3 accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi into the same TMEM.
 // Composition components are written per row (g_c, s_c) and combined by a
 // second small kernel.  Every mbarrier wait is bounded; on a timeout the

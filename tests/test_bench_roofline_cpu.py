@@ -57,3 +57,15 @@ def test_dominant_kernel_is_the_largest_measured_share():
     assert bench.dominant_roofline(shares, ev, stream) is ev
     ev, stream, shares = bench.rooflines(_trace(1.0, 2.0, 3.0), states, peaks, 10, 5e11, 0)
     assert bench.dominant_roofline(shares, ev, stream)["kernel"] == "pso_move"
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    d = tmp_path / "paper_2505_17430_gb300" / "csrc"
+    d.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (d / "k.cu").write_text("// note\nint f(int a) { return a + 1; }  /* old */\n")
+    h0 = bench._source_hash(("k.cu",))
+    (d / "k.cu").write_text("// a longer note\n/* block\n   comment */\nint f(int a) {\n  return a + 1;\n}\n")
+    assert bench._source_hash(("k.cu",)) == h0
+    (d / "k.cu").write_text("int f(int a) { return a + 2; }\n")
+    assert bench._source_hash(("k.cu",)) != h0
