@@ -108,6 +108,33 @@ def test_de_ctpb_archive_lockstep(S, policy):
     assert asize == NP  # the archive filled and random eviction was exercised
 
 
+@pytest.mark.parametrize("alg", [0, 1])
+def test_de_trials_repair_parents_outside_the_box(S, policy, alg):
+    """Parents set outside [lb, ub] by the caller: a trial below lb whose
+    midpoint with its parent still lies above ub takes the second repair,
+    (ub + x) / 2 (the rare branch of the repair); U and the partners must
+    match the oracle bit for bit."""
+    fam, D, NP, seed = S.RASTRIGIN, 23, 50, 31
+    p, q, st = _state(S, fam, D, alg, NP, 10 ** 6, seed)
+    rng = np.random.default_rng(7)
+    X = O.init_population(seed, NP, D)
+    X[rng.random((NP, D)) < 0.3] *= 10.0  # about 30 % of the coordinates in [-1000, 1000]
+    fx = q.eval(X)
+    st.set(X=X, fx=fx, fes=NP)
+    assert st.de_step(1) == 0
+    g = st.get()
+    if alg == S.DE_RAND1:
+        U, part = O.de_rand1_trials(seed, 1, X)
+        v = X[part[:, 0]] + 0.5 * (X[part[:, 1]] - X[part[:, 2]])
+    else:
+        U, part = O.de_ctpb_trials(seed, 1, X, fx, None, 0)
+        v = X + 0.5 * (X[part[:, 0]] - X) + 0.5 * (X[part[:, 1]] - X[part[:, 2]])
+    # the rare branch is reached: mutants well below lb with parents above 2 ub - lb
+    assert ((v < -101.0) & (X > 301.0)).sum() >= 10
+    assert np.array_equal(g["part"], part)
+    assert np.array_equal(g["U"], U)
+
+
 @pytest.mark.parametrize("alg,NP,fam,D", [
     (1, 4096, 2, 10), (1, 600, 4, 17), (1, 60, 0, 8), (0, 1800, 1, 12), (0, 4096, 5, 9)])
 def test_de_free_running_selection_and_rank_bit_exact(S, alg, NP, fam, D):
