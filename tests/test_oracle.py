@@ -345,6 +345,23 @@ def test_de_midpoint_repair():
                 assert U[i, j] == (-100 + X[i, j]) * 0.5
 
 
+def test_de_repair_order_parent_outside_box():
+    """The repair tests u < lb first, then u > ub on the result, each once
+    (Sec. 2.2's midpoint repair; the order is a reading where the paper is
+    silent).  Parent 500 and a mutant below lb: (lb + 500)/2 = 200 is above ub,
+    so the upper step follows, (ub + 500)/2 = 300.  Parent -500 and a mutant
+    above ub: (ub - 500)/2 = -200 stays, below lb, as there is no second lower
+    test."""
+    NP, D = 6, 9
+    for x0, rest, want in ((500.0, -150.0, 300.0), (-500.0, 150.0, -200.0)):
+        X = np.full((NP, D), rest)
+        X[0] = x0
+        # row 0's partners all come from the other rows: v = rest + F (rest - rest)
+        U, part = O.de_rand1_trials(11, 1, X, F=0.5, CR=1.0)
+        assert 0 not in part[0, :3]
+        assert np.array_equal(U[0], np.full(D, want))
+
+
 def test_pbest_k_and_rank():
     assert O.pbest_k(0.11, 100) == 11 and O.pbest_k(0.11, 900) == 99
     assert O.pbest_k(0.11, 180) == 20 and O.pbest_k(0.11, 5) == 1
