@@ -328,6 +328,57 @@ def test_de_rand1_crossover_special_cases():
         assert np.allclose(U2[i], v, rtol=0, atol=1e-15)
 
 
+def test_init_population_from_pinned_draws():
+    """x_ij = lb + (ub - lb) u, u = u53 of the known-answer-pinned Philox at
+    counter (j >> 1, i, 0, INIT << 24): words 0, 1 for even j and 2, 3 for odd
+    j (an odd D uses half of its last call).  Recomputed in exact rational
+    arithmetic: the oracle is within 2 u of |lb| + |(ub - lb) u|.  A swapped
+    word pair, a counter per coordinate instead of per pair, or the row and
+    column counters exchanged fail."""
+    from fractions import Fraction as Fr
+    NP, D, seed, lb, ub = 7, 11, 0x5EED0000ABCD, -3.5, 12.25
+    X = O.init_population(seed, NP, D, lb, ub)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    u = Fr(1, 2 ** 53)
+    for i in range(NP):
+        for j in range(D):
+            w = O.philox((j >> 1, i, 0, O.P_INIT << 24), key)
+            r = Fr(O.u53(w[2 * (j & 1)], w[2 * (j & 1) + 1]))
+            t = (Fr(ub) - Fr(lb)) * r
+            assert abs(Fr(float(X[i, j])) - (Fr(lb) + t)) <= 2 * u * (abs(Fr(lb)) + t), (i, j)
+            assert lb <= X[i, j] < ub
+
+
+def test_de_rand1_crossover_from_pinned_draws():
+    """Binomial crossover at an intermediate CR: coordinate j takes the mutant
+    exactly when w_(j mod 4) 2^-32 < CR, w from the pinned Philox at counter
+    (j >> 2, i, gen, CROSS << 24), or when j = j_rand = below(w3, D) of the
+    partner call (0, i, gen, PART << 24); other coordinates keep the parent's
+    bits.  The mutant is x_r1 + F (x_r2 - x_r3) within 2 u of its terms.  The
+    population sits well inside the box, so no repair applies."""
+    from fractions import Fraction as Fr
+    NP, D, seed, gen, F, CR = 10, 13, 0xABCDEF12345, 4, 0.5, 0.5
+    X = O.init_population(seed, NP, D, -1.0, 1.0)
+    U, part = O.de_rand1_trials(seed, gen, X, F=F, CR=CR)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    u = Fr(1, 2 ** 53)
+    crossed = kept = 0
+    for i in range(NP):
+        a, b, c, jr = (int(t) for t in part[i])
+        wp = O.philox((0, i, gen, O.P_PART << 24), key)
+        assert jr == O.below(wp[3], D)
+        for j in range(D):
+            w = O.philox((j >> 2, i, gen, O.P_CROSS << 24), key)
+            if w[j & 3] / 2 ** 32 < CR or j == jr:
+                crossed += 1
+                t1, t2 = Fr(float(X[a, j])), Fr(F) * (Fr(float(X[b, j])) - Fr(float(X[c, j])))
+                assert abs(Fr(float(U[i, j])) - (t1 + t2)) <= 2 * u * (abs(t1) + abs(t2)), (i, j)
+            else:
+                kept += 1
+                assert U[i, j] == X[i, j], (i, j)
+    assert crossed > 30 and kept > 30
+
+
 def test_de_midpoint_repair():
     NP, D = 8, 5
     X = np.full((NP, D), 99.0)
