@@ -379,6 +379,46 @@ def test_de_rand1_crossover_from_pinned_draws():
     assert crossed > 30 and kept > 30
 
 
+def _kth_allowed(v, n, excluded):
+    """The v-th smallest index of [0, n) not in `excluded` (v from 0)."""
+    allowed = [t for t in range(n) if t not in excluded]
+    return allowed[v]
+
+
+def test_de_partners_from_pinned_draws():
+    """Partners from the pinned Philox call (0, i, gen, PART << 24), w0..w3:
+    rand/1 r1, r2, r3 are the below(w0, NP-1)-th, below(w1, NP-2)-th and
+    below(w2, NP-3)-th index not yet excluded ({i}, then {i, r1}, then
+    {i, r1, r2}); current-to-pbest takes pb = order[below(w0, k)] of the
+    fitness ranking, r1 the below(w1, NP-1)-th index other than i and r2 the
+    below(w2, NP + |A| - 2)-th index of population + archive other than i and
+    r1; j_rand = below(w3, D) for both.  Recomputed here from that definition,
+    not by the oracle's skip-over-sorted-exclusions loop."""
+    NP, D, seed = 23, 5, 0x1234567890
+    X = O.init_population(seed, NP, D)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for gen in range(1, 9):
+        _, part = O.de_rand1_trials(seed, gen, X)
+        for i in range(NP):
+            w = O.philox((0, i, gen, O.P_PART << 24), key)
+            a = _kth_allowed(O.below(w[0], NP - 1), NP, {i})
+            b = _kth_allowed(O.below(w[1], NP - 2), NP, {i, a})
+            c = _kth_allowed(O.below(w[2], NP - 3), NP, {i, a, b})
+            assert list(part[i]) == [a, b, c, O.below(w[3], D)], (gen, i)
+    fx = np.random.default_rng(3).permutation(NP).astype(float)
+    A = O.init_population(seed + 1, NP, D)
+    k = O.pbest_k(0.11, NP)
+    order = list(np.argsort(fx, kind="stable"))
+    for asize, gen in [(a, g) for a in (0, 6) for g in range(1, 9)]:
+        _, part = O.de_ctpb_trials(seed, gen, X, fx, A, asize)
+        for i in range(NP):
+            w = O.philox((0, i, gen, O.P_PART << 24), key)
+            pb = order[O.below(w[0], k)]
+            r1 = _kth_allowed(O.below(w[1], NP - 1), NP, {i})
+            r2 = _kth_allowed(O.below(w[2], NP + asize - 2), NP + asize, {i, r1})
+            assert list(part[i]) == [pb, r1, r2, O.below(w[3], D)], (asize, i)
+
+
 def test_de_midpoint_repair():
     NP, D = 8, 5
     X = np.full((NP, D), 99.0)
