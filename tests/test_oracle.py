@@ -507,6 +507,35 @@ def test_de_select_and_archive():
     assert all(tuple(r) in rows for r in A3)
 
 
+def test_de_archive_eviction_from_pinned_draws():
+    """An accepted parent (f_u <= f_x) enters the archive at the next free
+    slot while it has fewer than NP rows, and once full replaces the slot
+    below(w0, NP) of the pinned Philox call (0, i, gen, ARCH << 24), rows taken
+    in index order.  Starting 3 rows short of full, the first three accepted
+    parents fill it and the rest evict; a slot that no parent drew keeps its
+    old row, and a slot drawn twice holds the later parent."""
+    NP, D, seed, gen = 16, 3, 0xFEEDBEEF, 6
+    X = O.init_population(seed, NP, D)
+    U = O.init_population(seed + 7, NP, D)
+    fx = np.ones(NP)
+    fu = np.where(np.arange(NP) % 4 == 1, 2.0, 1.0)  # rows 1, 5, 9, 13 rejected; ties accepted
+    A0 = O.init_population(seed + 9, NP, D)
+    asize0 = NP - 3
+    X2, fx2, A2, asz, acc = O.de_select(seed, gen, X, fx, U, fu, A0, asize0)
+    assert list(acc) == [0 if i % 4 == 1 else 1 for i in range(NP)] and asz == NP
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    want = A0.copy()
+    fill = asize0
+    for i in np.nonzero(acc)[0]:
+        if fill < NP:
+            slot, fill = fill, fill + 1
+        else:
+            slot = O.below(O.philox((0, int(i), gen, O.P_ARCH << 24), key)[0], NP)
+        want[slot] = X[i]
+    assert np.array_equal(A2, want)
+    assert np.array_equal(X2[acc == 1], U[acc == 1]) and np.array_equal(X2[acc == 0], X[acc == 0])
+
+
 # ------------------------------------------------------------------ PSO operators
 def test_pso_guides():
     fp = np.array([5.0, 1.0, 3.0, 1.0, 7.0, 0.5])
