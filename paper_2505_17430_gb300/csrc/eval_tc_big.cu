@@ -521,7 +521,10 @@ cudaError_t sv_eval_tc_big(const TcSegment& seg, int prec, const double* X, int6
   if (t64 < std::min(t128, t256)) BN = 64;
   bool tune = false;
   if (sv_policy_autotune()) {
-    const int cached = sv_tune_lookup(SV_TUNE_BIG_NTILE, h.D, N, prec);
+    // a cached width that is not a candidate (an edited or foreign cache
+    // file) is ignored and measured again
+    int cached = sv_tune_lookup(SV_TUNE_BIG_NTILE, h.D, N, prec);
+    if (cached != 64 && cached != 128 && cached != 256) cached = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cached)
       BN = cached;

@@ -398,6 +398,32 @@ def test_large_d_tile_widths_give_the_same_bits(S, tmp_path, monkeypatch, prec, 
     _check_mixed(prec, outs[0], q.eval(X), bound(p, q, X))
 
 
+def test_autotuner_ignores_a_width_that_is_not_a_candidate(S, tmp_path, monkeypatch):
+    """A cache line whose width is not one of 64, 128, 256 (an edited or
+    foreign file) is not used: the call measures the candidates again, appends
+    a valid line, and gives the fixed rule's bits."""
+    lib = S.lib()
+    D, N = 600, 1500
+    p = S.Problem(2300, S.RASTRIGIN, D)
+    xt = to_dev(inputs.uniform_pop(N, D, seed=23))
+    path = _tune_file(tmp_path, [f"0 {D} 2048 {S.TF32} 100"])
+    monkeypatch.setenv("SEVO_TUNE_FILE", path)
+    try:
+        assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2) == 0
+        S.trace_enable(True)
+        got = p.evaluate(xt, prec=S.TF32).cpu().numpy()
+        t = S.trace_read()
+        S.trace_enable(False)
+        assert t["gemm_big"][0] > 1
+        lines = [l for l in open(path).read().split("\n") if l.strip()]
+        assert len(lines) == 2 and int(lines[1].split()[4]) in (64, 128, 256)
+        assert lib.sevo_set_policy(S.POLICY_AUTOTUNE, 0) == 0
+        assert np.array_equal(got, p.evaluate(xt, prec=S.TF32).cpu().numpy())
+    finally:
+        monkeypatch.delenv("SEVO_TUNE_FILE")
+        lib.sevo_set_policy(S.POLICY_AUTOTUNE, 2)
+
+
 def test_autotuner_measures_once_and_caches(S, tmp_path, monkeypatch):
     """SEVO_POLICY_AUTOTUNE: the first large-D call of a (D, row bucket,
     precision) times every width (extra GEMM launches) and writes the choice
