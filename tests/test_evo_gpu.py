@@ -1008,3 +1008,69 @@ def test_fused_operators_equal_operator_kernels(S, prec, D):
             assert np.array_equal(ga[key], gb[key]), key
         assert ga["asize"] == gb["asize"]
         assert ra == rb and np.array_equal(ba, bb)
+
+
+def test_bench_step_configuration_bit_exact(S):
+    """The benchmark step as it is timed: two groups of DE/rand/1,
+    DE/current-to-pbest and ring PSO states (3 runs x NP 4096 at D = 100 each,
+    TF32, each state on its own stream; bench.make_states) advanced by one
+    sevo_state_step_many per group (bench.run_steps).  Over two generations:
+    every run's DE/rand/1 trials and partners and every run's PSO moves,
+    velocities and guides equal the oracle's bit for bit; run 0 of each
+    current-to-pbest state (the run whose archive the binding returns) has the
+    oracle's partners, trials and selection; and 64 sampled rows of every state
+    have the fitness of a plain TF32 sevo_evaluate of the same rows, bit for
+    bit (that evaluation is compared with the oracle at this shape in
+    test_bench_shape_sampled)."""
+    import torch
+
+    import bench
+    seed0 = 7
+    probs, states = bench.make_states(S, S.TF32, seed0, torch)
+    NP, per = bench.NP, bench.FAMILIES // bench.GROUPS
+    rng = np.random.default_rng(3)
+    gen = 1
+    for _ in range(2):
+        torch.cuda.synchronize()
+        before = [st.get() for st in states]
+        gen_used = gen
+        gen = bench.run_steps(states, gen, 1)
+        torch.cuda.synchronize()
+        for s, (st, g0) in enumerate(zip(states, before)):
+            g = st.get()
+            gi, k = s // len(bench.ALGS), s % len(bench.ALGS)
+            alg = st.params.alg
+            for r in range(st.R):
+                seed = seed0 + 1000 * k + gi * per + r
+                sl = slice(r * NP, (r + 1) * NP)
+                if alg == S.DE_RAND1:
+                    U, part = O.de_rand1_trials(seed, gen_used, g0["X"][sl])
+                    assert np.array_equal(g["part"][sl], part), (s, r)
+                    assert np.array_equal(g["U"][sl], U), (s, r)
+                elif alg == S.PSO_RING:
+                    guide = O.pso_guides(g0["fp"][sl], 1)
+                    assert np.array_equal(g0["part"][sl][:, 0], guide), (s, r)
+                    X2, V2 = O.pso_move(seed, gen_used, g0["X"][sl], g0["V"][sl], g0["P"][sl],
+                                        guide)
+                    assert np.array_equal(g["X"][sl], X2), (s, r)
+                    assert np.array_equal(g["V"][sl], V2), (s, r)
+                elif r == 0:
+                    A0 = np.zeros((NP, bench.D))
+                    A0[:g0["asize"]] = g0["A"]
+                    U, part = O.de_ctpb_trials(seed, gen_used, g0["X"][sl], g0["fx"][sl], A0,
+                                               g0["asize"])
+                    assert np.array_equal(g["part"][sl], part), s
+                    assert np.array_equal(g["U"][sl], U), s
+                    X2, fx2, A2, as2, _ = O.de_select(seed, gen_used, g0["X"][sl], g0["fx"][sl],
+                                                      U, g["fu"][sl], A0, g0["asize"])
+                    assert g["asize"] == as2 and np.array_equal(g["A"], A2[:as2]), s
+                    assert np.array_equal(g["X"][sl], X2) and np.array_equal(g["fx"][sl], fx2), s
+            rows, fit = (g["X"], g["fx"]) if alg == S.PSO_RING else (g["U"], g["fu"])
+            pick = np.sort(rng.choice(st.R * NP, 64, replace=False))
+            for r in range(st.R):
+                mine = pick[(pick >= r * NP) & (pick < (r + 1) * NP)]
+                if len(mine) == 0:
+                    continue
+                Xr = torch.tensor(rows[mine], dtype=torch.float64, device="cuda")
+                ref = probs[gi * per + r].evaluate(Xr, prec=S.TF32).cpu().numpy()
+                assert np.array_equal(fit[mine].view(np.int64), ref.view(np.int64)), (s, r)
