@@ -69,3 +69,14 @@ def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench._source_hash(("k.cu",)) == h0
     (d / "k.cu").write_text("int f(int a) { return a + 2; }\n")
     assert bench._source_hash(("k.cu",)) != h0
+
+
+def test_wilson_interval_matches_scipy():
+    """bench.py's success-rate interval is the 95 % Wilson score interval
+    (rounded to 4 places), as scipy computes it."""
+    st = __import__("pytest").importorskip("scipy.stats")
+    for k, n in [(0, 51), (1, 51), (31, 51), (50, 51), (51, 51), (3, 11), (7, 7)]:
+        ci = st.binomtest(k, n).proportion_ci(confidence_level=0.95, method="wilson")
+        lo, hi = bench.wilson(k, n)
+        assert abs(lo - ci.low) <= 5e-5 and abs(hi - ci.high) <= 5e-5, (k, n)
+    assert bench.wilson(0, 0) == [0.0, 1.0]
