@@ -445,8 +445,9 @@ enum sevo_policy {
    * a power of two, precision) is evaluated outside stream capture, and
    * cached in memory and in a file ($SEVO_TUNE_FILE, else
    * $XDG_CACHE_HOME/sevo/tune-<gpu>.txt, else $HOME/.cache/sevo/
-   * tune-<gpu>.txt); that first call synchronizes its stream.  Every width
-   * gives the same result bits.  0: a fixed rule (whole waves of jobs times
+   * tune-<gpu>.txt); that first call synchronizes its stream.  A cached
+   * width other than 64, 128 or 256 is ignored and measured again.  Every
+   * width gives the same result bits.  0: a fixed rule (whole waves of jobs times
    * their cost) instead.  2: forget the cached choices and read the file
    * again (the value then reads back as 1). */
   SEVO_POLICY_AUTOTUNE = 4
