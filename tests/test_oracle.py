@@ -84,6 +84,25 @@ def test_shift_range_and_determinism():
     assert not np.array_equal(o[:100], O.Problem(3, O.RASTRIGIN, 100).shift())
 
 
+def test_shift_from_pinned_draws():
+    """o_j = -80 + 160 u, u = u53 of the known-answer-pinned Philox at
+    counter (j >> 1, 0, D, SHIFT << 24 | component): words 0, 1 for even j and
+    2, 3 for odd j.  Recomputed in exact rational arithmetic (within 2 u of
+    80 + 160 u) for a plain instance and for two components of a composition,
+    whose salt is the component index."""
+    from fractions import Fraction as Fr
+    u = Fr(1, 2 ** 53)
+    for seed, fam, D, comps in ((0x51F7, O.RASTRIGIN, 9, (0,)),
+                                (0x51F8, O.COMPOSITION, 6, (0, 1, 2))):
+        p = O.Problem(seed, fam, D)
+        for c in comps:
+            o = p.shift(c)
+            for j in range(D):
+                w = O.philox([j >> 1, 0, D, (16 << 24) | c], [seed & 0xFFFFFFFF, seed >> 32])
+                t = 160 * Fr(O.u53(w[2 * (j & 1)], w[2 * (j & 1) + 1]))
+                assert abs(Fr(float(o[j])) - (t - 80)) <= 2 * u * (80 + t), (fam, c, j)
+
+
 def test_norm_preserved():
     p = O.Problem(9, O.GRIEWANK, 50)
     X = inputs.uniform_pop(20, 50, seed=1)
