@@ -277,6 +277,26 @@ def test_composition_value_at_each_optimum(D):
     assert (p.eval(X) >= 0.0).all()
 
 
+def test_composition_parameters_from_pinned_draws():
+    """A random composition from the known-answer-pinned Philox: N_c = 3 +
+    below(w0, 8) of call (0, 0, D, COMP << 24); component c's sigma =
+    10 (1 + below(w0, 6)), lambda = 10^(-6 + 6 u53(w1, w2)) and body
+    below(w3, 6) of call (1 + c, 0, D, COMP << 24); bias = 100 c."""
+    for seed, D in ((0xC0C0, 10), (0xC0C1, 30), (0xC0C2, 7), (0xC0C3, 64)):
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        q = O.Problem(seed, O.COMPOSITION, D)
+        body, sigma, lam, bias = q.comp()
+        Nc = 3 + O.below(O.philox([0, 0, D, 20 << 24], key)[0], 8)
+        assert len(body) == Nc, seed
+        for c in range(Nc):
+            w = O.philox([1 + c, 0, D, 20 << 24], key)
+            assert sigma[c] == 10.0 * (1 + O.below(w[0], 6)), (seed, c)
+            want = 10.0 ** (-6.0 + 6.0 * O.u53(w[1], w[2]))
+            assert abs(lam[c] - want) <= 4e-16 * want, (seed, c)
+            assert body[c] == O.below(w[3], 6), (seed, c)
+            assert bias[c] == 100.0 * c
+
+
 def test_composition_component_zero_is_the_single_instance():
     """Approaching o_1 along a ray x = o_1 + r u, the residual
     R(r) = (F(x) - f*) - lambda_1 g_1(x) vanishes linearly in r: component 1
