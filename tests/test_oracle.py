@@ -196,34 +196,55 @@ def test_hybrid_structure():
         assert (gs >= np.floor(0.1 * D) - 1).all()
 
 
+def _hybrid_from_draws(seed, D, salt):
+    """(K, bodies, E, permutation) of a hybrid structure from the
+    known-answer-pinned Philox, salt 0 for a hybrid instance, 1 + c for
+    component c of a composition of hybrids."""
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    K = 3 + O.below(O.philox([0, 0, D, (19 << 24) | salt], key)[0], 3)
+    E, bodies = [], []
+    for k in range(K):
+        w = O.philox([1 + k, 0, D, (19 << 24) | salt], key)
+        E.append(-math.log(1.0 - O.u53(w[0], w[1])))
+        bodies.append(O.below(w[2], 6))
+    perm = list(range(D))
+    for i in range(D - 1, 0, -1):
+        j = O.below(O.philox([i, 0, D, (18 << 24) | salt], key)[0], i + 1)
+        perm[i], perm[j] = perm[j], perm[i]
+    return K, bodies, E, perm
+
+
+def _check_hybrid(got, want, D, what):
+    perm, gs, gb = got
+    K, bodies, E, wperm = want
+    assert len(gs) == K and list(gb) == bodies, what
+    for k in range(K - 1):
+        t = (0.1 + (1.0 - 0.1 * K) * E[k] / sum(E)) * D
+        if abs(t - round(t)) > 1e-9:  # away from a floor boundary
+            assert gs[k] == math.floor(t), (what, k)
+    assert gs.sum() == D and list(perm) == wperm, what
+
+
 def test_hybrid_structure_from_pinned_draws():
     """A random hybrid instance from the known-answer-pinned Philox: K = 3 +
-    below(w0, 3) of call (0, 0, D, HYB << 24); group k's body below(w2, 6) and
-    E_k = -log(1 - u53(w0, w1)) of call (1 + k, 0, D, HYB << 24); sizes
-    floor((0.1 + (1 - 0.1 K) E_k / sum E) D), the last group the remainder;
-    the permutation by Fisher-Yates from the last index down, swapping i
-    with below(w0, i + 1) of call (i, 0, D, PERM << 24)."""
+    below(w0, 3) of call (0, 0, D, HYB << 24 | salt); group k's body
+    below(w2, 6) and E_k = -log(1 - u53(w0, w1)) of call (1 + k, 0, D,
+    HYB << 24 | salt); sizes floor((0.1 + (1 - 0.1 K) E_k / sum E) D), the
+    last group the remainder; the permutation by Fisher-Yates from the last
+    index down, swapping i with below(w0, i + 1) of call (i, 0, D,
+    PERM << 24 | salt).  Salt 0 for a hybrid instance; for component c of a
+    composition of hybrids salt 1 + c, with N_c = 3 + below(w0, 3) of the
+    composition call (0, 0, D, COMP << 24)."""
     for seed, D in ((0x4B1D, 50), (0x4B1E, 31), (0x4B1F, 100)):
+        got = O.Problem(seed, O.HYBRID, D).hybrid()
+        _check_hybrid(got, _hybrid_from_draws(seed, D, 0), D, seed)
+    for seed, D in ((0x4C1D, 40), (0x4C1E, 23)):
+        q = O.Problem(seed, O.COMP_HYBRID, D)
         key = [seed & 0xFFFFFFFF, seed >> 32]
-        perm, gs, gb = O.Problem(seed, O.HYBRID, D).hybrid()
-        K = 3 + O.below(O.philox([0, 0, D, 19 << 24], key)[0], 3)
-        assert len(gs) == K, seed
-        E, bodies = [], []
-        for k in range(K):
-            w = O.philox([1 + k, 0, D, 19 << 24], key)
-            E.append(-math.log(1.0 - O.u53(w[0], w[1])))
-            bodies.append(O.below(w[2], 6))
-        assert list(gb) == bodies, seed
-        for k in range(K - 1):
-            t = (0.1 + (1.0 - 0.1 * K) * E[k] / sum(E)) * D
-            if abs(t - round(t)) > 1e-9:  # away from a floor boundary
-                assert gs[k] == math.floor(t), (seed, k)
-        assert gs.sum() == D
-        want = list(range(D))
-        for i in range(D - 1, 0, -1):
-            j = O.below(O.philox([i, 0, D, 18 << 24], key)[0], i + 1)
-            want[i], want[j] = want[j], want[i]
-        assert list(perm) == want, seed
+        Nc = 3 + O.below(O.philox([0, 0, D, 20 << 24], key)[0], 3)
+        assert q.K == Nc, seed
+        for c in range(Nc):
+            _check_hybrid(q.comp_hybrid(c), _hybrid_from_draws(seed, D, 1 + c), D, (seed, c))
 
 
 def test_hybrid_fixed_fractions():
