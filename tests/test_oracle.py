@@ -800,6 +800,41 @@ def test_shade_memory_slot_uniform_and_pool_range():
     assert O.shade_kmax(8) == 2  # 2/NP > 0.2 for NP < 10
 
 
+def test_shade_params_from_pinned_draws():
+    """SHADE's per-row parameters from the known-answer-pinned Philox, call
+    (t, i, gen, SHADE << 24): t = 0 gives the memory slot below(w0, H) and the
+    pool fraction p = 2/NP + (0.2 - 2/NP) u53(w1, w2), k = floor(p NP + 0.5)
+    in [1, NP]; t = 1 gives CR = M_CR + 0.1 z, z = sqrt(-2 ln(1 - u1))
+    cos(2 pi u2) (u1 = u53(w0, w1), u2 = u53(w2, w3)), clipped to [0, 1];
+    t = 2, 3, ... give Cauchy candidates M_F + 0.1 tan(pi (u53(w0, w1) - 0.5))
+    until one is positive, capped at 1.  Distinct memory slots make the slot
+    choice visible."""
+    NP, H, seed, gen = 37, 6, 0x5AADE, 3
+    MF = np.array([0.05, 0.2, 0.35, 0.5, 0.65, 0.8])
+    MCR = np.array([0.9, 0.1, 0.7, 0.3, 0.5, 0.95])
+    F, CR, kpb = O.shade_params(seed, gen, NP, MF, MCR)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    pmin = 2.0 / NP
+    for i in range(NP):
+        w = O.philox([0, i, gen, 6 << 24], key)
+        h = O.below(w[0], H)
+        t = (pmin + (0.2 - pmin) * O.u53(w[1], w[2])) * NP + 0.5
+        if abs(t - round(t)) > 1e-9:
+            assert kpb[i] == min(NP, max(1, math.floor(t))), i
+        w = O.philox([1, i, gen, 6 << 24], key)
+        u1, u2 = O.u53(w[0], w[1]), O.u53(w[2], w[3])
+        cr = MCR[h] + 0.1 * math.sqrt(-2.0 * math.log(1.0 - u1)) * math.cos(2.0 * math.pi * u2)
+        assert abs(CR[i] - min(1.0, max(0.0, cr))) <= 1e-13, i
+        f = MF[h]
+        for a in range(64):
+            w = O.philox([2 + a, i, gen, 6 << 24], key)
+            c = MF[h] + 0.1 * math.tan(math.pi * (O.u53(w[0], w[1]) - 0.5))
+            if c > 0.0:
+                f = c
+                break
+        assert abs(F[i] - min(1.0, f)) <= 1e-12 * max(1.0, abs(f)), i
+
+
 def test_shade_memory_update_closed_form():
     """Weights proportional to the improvement fx - fu over strict
     improvements: M_F[k] = sum w F^2 / sum w F, M_CR[k] = sum w CR / sum w,
