@@ -196,6 +196,28 @@ def test_hybrid_structure():
         assert (gs >= np.floor(0.1 * D) - 1).all()
 
 
+def test_schwefel_outside_the_box_penalty():
+    """Outside |y| <= 500 (y = z + s) the Schwefel term is its boundary value
+    c - b sin sqrt|b| (b = 500 sign y) plus 1e-4 (|y| - 500)^2: continuous at
+    |y| = 500 and checked at far points on both sides, with s found here by
+    scipy's bracketing root finder on the stationarity condition
+    sin u + (u / 2) cos u = 0, u = sqrt t, and c = s sin sqrt s."""
+    opt = pytest.importorskip("scipy.optimize")
+    u = opt.brentq(lambda v: math.sin(v) + 0.5 * v * math.cos(v), 20.0, 21.0, xtol=1e-15)
+    s0 = u * u
+    c = s0 * math.sin(u)
+    edge = c - 500.0 * math.sin(math.sqrt(500.0))
+    for z in (2000.0, 600.0, -2000.0, -1200.0):
+        y = z + s0
+        b = 500.0 if y > 0 else -500.0
+        want = c - b * math.sin(math.sqrt(500.0)) + 1e-4 * (abs(y) - 500.0) ** 2
+        assert O.body(O.SCHWEFEL, np.array([z])) == pytest.approx(want, rel=1e-10), z
+    # continuity at y = 500: the two forms meet
+    lo = O.body(O.SCHWEFEL, np.array([500.0 - s0 - 1e-9]))
+    hi = O.body(O.SCHWEFEL, np.array([500.0 - s0 + 1e-9]))
+    assert abs(lo - edge) < 1e-6 and abs(hi - edge) < 1e-6
+
+
 def _hybrid_from_draws(seed, D, salt):
     """(K, bodies, E, permutation) of a hybrid structure from the
     known-answer-pinned Philox, salt 0 for a hybrid instance, 1 + c for
