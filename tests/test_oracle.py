@@ -340,6 +340,33 @@ def test_composition_parameters_from_pinned_draws():
             assert bias[c] == 100.0 * c
 
 
+def test_composition_value_assembled_from_pinned_parts():
+    """At generic points (uniform, and within a few units of one component's
+    shift), F equals sum_c omega_c (lambda_c g_c(M_c (x - o_c)) + bias_c),
+    omega = w / sum w with w_c = s_c^(-1/2) exp(-s_c / (2 D sigma_c^2)),
+    s_c = |x - o_c|^2, assembled here from the exported shifts and rotations,
+    the draw-pinned parameters and the closed-form-pinned bodies: a wrong
+    weight exponent, a missing D or a swapped lambda/bias fails by far more
+    than the tolerance."""
+    for seed, D in ((0xA5A5, 12), (0xA5A6, 30)):
+        q = O.Problem(seed, O.COMPOSITION, D)
+        body, sig, lam, bias = q.comp()
+        rng = np.random.default_rng(seed)
+        X = np.vstack([rng.uniform(-100, 100, (5, D)),
+                       q.shift(1) + 4.0 * rng.standard_normal((3, D)),
+                       q.shift(2) + 0.5 * rng.standard_normal((2, D))])
+        for x in X:
+            g, sc = np.zeros(q.K), np.zeros(q.K)
+            for c in range(q.K):
+                d = x - q.shift(c)
+                sc[c] = d @ d
+                g[c] = O.body(int(body[c]), q.rotation(c) @ d)
+            w = (1.0 / np.sqrt(sc)) * np.exp(-sc / (2.0 * D * sig * sig))
+            om = w / w.sum() if w.sum() > 0 else np.full(q.K, 1.0 / q.K)
+            want = float(om @ (lam * g + bias))
+            assert q.eval(x[None, :])[0] == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
 def test_composition_component_zero_is_the_single_instance():
     """Approaching o_1 along a ray x = o_1 + r u, the residual
     R(r) = (F(x) - f*) - lambda_1 g_1(x) vanishes linearly in r: component 1
