@@ -269,6 +269,27 @@ def test_hybrid_structure_from_pinned_draws():
             _check_hybrid(q.comp_hybrid(c), _hybrid_from_draws(seed, D, 1 + c), D, (seed, c))
 
 
+def test_hybrid_value_assembled_from_pinned_parts():
+    """At generic points a random hybrid's value is sum_k body_k over group
+    k's contiguous range of z' = M' (x - o), M' the rotation with its rows
+    permuted (the exported rotation), assembled here from the exported parts
+    and the pinned bodies: a group applied to the wrong range, the wrong body
+    per group, or a body's index restarting at the wrong place fails."""
+    for seed, D in ((0x4D1D, 20), (0x4D1E, 47)):
+        q = O.Problem(seed, O.HYBRID, D)
+        perm, gs, gb = q.hybrid()
+        assert len(set(int(b) for b in gb)) > 1 or len(gb) == 1
+        rng = np.random.default_rng(seed)
+        X = np.vstack([rng.uniform(-100, 100, (4, D)), q.shift() + rng.standard_normal((3, D))])
+        for x in X:
+            z = q.rotation() @ (x - q.shift())
+            want, start = 0.0, 0
+            for n, b in zip(gs, gb):
+                want += O.body(int(b), z[start:start + n]) if n > 0 else 0.0
+                start += n
+            assert q.eval(x[None, :])[0] == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
 def test_hybrid_fixed_fractions():
     p = O.Problem(5, O.HYBRID, 100, hybrid=([0.3, 0.3, 0.4], [O.RASTRIGIN, O.ELLIPSOID, O.SCHWEFEL]))
     _, gs, gb = p.hybrid()
