@@ -103,6 +103,25 @@ def test_shift_from_pinned_draws():
                 assert abs(Fr(float(o[j])) - (t - 80)) <= 2 * u * (80 + t), (fam, c, j)
 
 
+def test_plain_value_is_body_of_rotated_shift():
+    """For the six plain families F - f* = body(M (x - o)) with M the exported
+    rotation (the Q of the QR of the draw-pinned Gaussian matrix) applied as
+    z_i = sum_j M_ij d_j, not its transpose (which would preserve norms and
+    the optimum alike)."""
+    for fam in range(6):
+        D = 9
+        q = O.Problem(0x7A00 + fam, fam, D)
+        M, o = q.rotation(), q.shift()
+        assert np.abs(M - M.T).max() > 1e-3  # the orientation is observable
+        rng = np.random.default_rng(fam)
+        for x in rng.uniform(-100, 100, (4, D)):
+            z = M @ (x - o)
+            assert np.allclose(q.transform(x), z, rtol=0, atol=1e-12)
+            want = O.body(fam, z)
+            assert q.eval(x[None, :])[0] == pytest.approx(want, rel=1e-12, abs=1e-12), fam
+            assert abs(O.body(fam, M.T @ (x - o)) - want) > 1e-6 * abs(want), fam
+
+
 def test_norm_preserved():
     p = O.Problem(9, O.GRIEWANK, 50)
     X = inputs.uniform_pop(20, 50, seed=1)
